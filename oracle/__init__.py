@@ -1,0 +1,23 @@
+"""FP64 CPU oracle for the Kadanoff-Baym time stepping (test infrastructure).
+
+Only the test suite, ``__graft_entry__.smoke()`` and ``bench.py``'s
+cpu_baseline / reference leg may import this package. It shares no code with
+the CUDA library; the two meet only in ``kbe_inputs`` (seeded inputs).
+Block layout on this side is [k][a][b] (band indices fastest).
+
+Parity status of each function (what pins it) is listed in ``PINS`` below and
+checked by ``tests/test_oracle_pins.py``.
+"""
+from .oracle import (Oracle, build, sigma_pair, sigma_pair_literal, collision_row,
+                     propagators, update_row, library_path)
+
+PINS = {
+    "sigma_pair": "literal Eq. 7 triple sum (N_b=2 bar form, general v); ED O(U^2)",
+    "sigma_pair_literal": "Eq. 7 as printed (bar convention) on random G",
+    "collision_row": "analytic integrals of exponentials (trapezoid error O(dt^2)); "
+                     "I^>(n,n) = I^<(n,n); number conservation",
+    "propagators": "unitarity, closed form at U = 0, h V = U - 1",
+    "update_row": "U = 0 closed form (driven and undriven)",
+    "Oracle.step": "U = 0 closed form; particle number; energy drift O(dt^2); "
+                   "exact diagonalisation through O(U^2); time-step order 2",
+}

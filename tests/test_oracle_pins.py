@@ -1,0 +1,384 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+None of these compare the oracle with itself: each checks it against a closed
+form, an exact solution computed another way (matrix exponentials, exact
+diagonalisation), the literal printed formula (Eq. 7 / Algorithm 2), or a
+conservation law / convergence order of the method. A plausible mistake (a
+dropped term, a wrong sign, a transposed operand, a wrong weight or limit)
+fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import kbe_inputs as ki
+import oracle
+
+RNG = np.random.default_rng(20250519)
+
+
+def h0_of(sys, k, A=0.0):
+    """Bare Bloch Hamiltonian from the hopping table (test-side, for closed forms)."""
+    k0, k1 = divmod(k, sys.L[1])
+    h = np.zeros((sys.nb, sys.nb), complex)
+    for R, t in zip(sys.hop_R, sys.hop_T):
+        th = 2 * np.pi * (k0 * R[0] / sys.L[0] + k1 * R[1] / sys.L[1]) \
+            - A * (sys.direction[0] * R[0] + sys.direction[1] * R[1])
+        h += t * np.exp(1j * th)
+    return h
+
+
+def fermi_matrix(h, beta, mu):
+    w, V = np.linalg.eigh(h)
+    return V @ np.diag(1.0 / (np.exp(beta * (w - mu)) + 1.0)) @ V.conj().T
+
+
+# --------------------------------------------------------------------------
+# Eq. 7: factorised self-energy (Eqs. 8-9 + exchange intermediate) against the
+# printed O(n_k^3) sum (Algorithm 2), bar form and generalised pairing form.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("nb,L,vmode", [
+    (2, (4, 1), "bar"), (2, (8, 1), "bar"), (2, (3, 3), "bar"), (2, (4, 4), "bar"),
+    (3, (3, 2), "rand"), (4, (2, 3), "pair"), (2, (5, 1), "pair"),
+])
+def test_sigma_factorised_equals_literal_eq7(nb, L, vmode):
+    nk = L[0] * L[1]
+    Gl = ki.random_blocks(RNG, (nk, nb, nb))
+    Gg = ki.random_blocks(RNG, (nk, nb, nb))
+    if vmode == "bar":
+        v, vlit = ki.pair_pattern(nb), None
+    elif vmode == "rand":
+        v = RNG.uniform(0, 1, (nb, nb))
+        v = v + v.T
+        vlit = v
+    else:
+        v = vlit = ki.pair_pattern(nb)
+    Sl, Sg = oracle.sigma_pair(nb, L, v, 0.7, Gl, Gg)
+    Tl, Tg = oracle.sigma_pair_literal(nb, L, vlit, 0.7, Gl, Gg)
+    assert np.abs(Sl - Tl).max() <= 1e-13 * np.abs(Tl).max()
+    assert np.abs(Sg - Tg).max() <= 1e-13 * np.abs(Tg).max()
+
+
+def test_sigma_literal_bar_single_point_by_hand():
+    """One output of Eq. 7 at n_k = 2 summed by hand in the test."""
+    nb, L, nk = 2, (2, 1), 2
+    Gl = ki.random_blocks(RNG, (nk, nb, nb))
+    Gg = ki.random_blocks(RNG, (nk, nb, nb))
+    Sl, _ = oracle.sigma_pair_literal(nb, L, None, 1.3, Gl, Gg)
+    Gt = lambda k, a, b: -np.conj(Gg[k, b, a])   # G^>_ab(k; t', t)
+    k, j, m = 1, 0, 1
+    jb, mb = 1 - j, 1 - m
+    s = 0
+    for q in range(nk):
+        for kp in range(nk):
+            s += Gl[(kp + q) % nk, jb, mb] * Gt(kp, mb, jb) * Gl[(k - q) % nk, j, m]
+            s -= Gl[kp, j, mb] * Gt((kp + q - k) % nk, mb, jb) * Gl[q, jb, m]
+    assert abs(Sl[k, j, m] - 1.3 * s / nk ** 2) < 1e-14
+
+
+def test_sigma_zero_when_one_band_empty_of_partners():
+    """v = 0 (no inter-band pairs) gives Sigma = 0 identically."""
+    nb, L = 3, (3, 1)
+    Gl = ki.random_blocks(RNG, (3, nb, nb))
+    Gg = ki.random_blocks(RNG, (3, nb, nb))
+    Sl, Sg = oracle.sigma_pair(nb, L, np.zeros((nb, nb)), 1.0, Gl, Gg)
+    assert np.abs(Sl).max() == 0 and np.abs(Sg).max() == 0
+
+
+# --------------------------------------------------------------------------
+# Eq. 6 (left form) with trapezoid weights against exact integrals of
+# exponentials; the leading trapezoid error (Euler-Maclaurin) must match.
+# --------------------------------------------------------------------------
+def _antiherm(rng, nb):
+    a = ki.random_blocks(rng, (nb, nb))
+    return a - a.conj().T
+
+
+@pytest.mark.parametrize("nb,nk", [(1, 1), (2, 1), (3, 2)])
+def test_collision_integral_against_exact_integrals(nb, nk):
+    rng = np.random.default_rng(nb * 10 + nk)
+    gl = np.stack([_antiherm(rng, nb) for _ in range(nk)])
+    gg = np.stack([_antiherm(rng, nb) for _ in range(nk)])
+    sl = ki.random_blocks(rng, (nk, nb, nb))
+    sg = ki.random_blocks(rng, (nk, nb, nb))
+    alpha, beta, T = 1.7, -0.6, 2.0
+    kappa = alpha - beta
+
+    def F(t):           # int_0^t e^{i kappa s} ds
+        return (np.exp(1j * kappa * t) - 1) / (1j * kappa)
+
+    def Ftrap_err(t):   # leading trapezoid error of F, dt^2/12 (f'(t) - f'(0))
+        return 1j * kappa * (np.exp(1j * kappa * t) - 1) / 12.0
+
+    errs = []
+    for n in (20, 40):
+        dt = T / n
+        tri = [(i, j) for i in range(n + 1) for j in range(i + 1)]
+        Hl = np.stack([gl * np.exp(-1j * beta * (i - j) * dt) for i, j in tri])
+        Hg = np.stack([gg * np.exp(-1j * beta * (i - j) * dt) for i, j in tri])
+        Sl = np.stack([sl * np.exp(-1j * alpha * (n - l) * dt) for l in range(n + 1)])
+        Sg = np.stack([sg * np.exp(-1j * alpha * (n - l) * dt) for l in range(n + 1)])
+        Il, Ig = oracle.collision_row(nb, nk, n, dt, Hl, Hg, Sl, Sg)
+        t = n * dt
+        worst = 0.0
+        for j in range(n + 1):
+            tp = j * dt
+            ph = np.exp(-1j * alpha * t + 1j * beta * tp)
+            for x, (I, g, s) in enumerate(((Il, gl, sl), (Ig, gg, sg))):
+                exact = ph * ((sg - sl) @ g * F(t) + s @ (gl - gg) * F(tp))
+                lead = ph * ((sg - sl) @ g * Ftrap_err(t) + s @ (gl - gg) * Ftrap_err(tp)) * dt ** 2
+                resid = np.abs(I[j] - exact - lead).max()
+                worst = max(worst, resid)
+                # the O(dt^2) term itself is resolved
+                assert np.abs(I[j] - exact).max() <= 1.05 * np.abs(lead).max() + 1e-12
+        errs.append(worst)
+    # after removing the leading term the residual is O(dt^4)
+    assert errs[1] < errs[0] / 10
+
+
+def test_equal_time_collision_integrals_coincide():
+    """I^>(n,n) = I^<(n,n): at j = n the two terms share weights and cancel."""
+    nb, nk, n, dt = 2, 3, 7, 0.1
+    ntri = (n + 1) * (n + 2) // 2
+    Hl = ki.random_blocks(RNG, (ntri, nk, nb, nb))
+    Hg = ki.random_blocks(RNG, (ntri, nk, nb, nb))
+    Sl = ki.random_blocks(RNG, (n + 1, nk, nb, nb))
+    Sg = ki.random_blocks(RNG, (n + 1, nk, nb, nb))
+    Il, Ig = oracle.collision_row(nb, nk, n, dt, Hl, Hg, Sl, Sg)
+    assert np.abs(Il[n] - Ig[n]).max() < 1e-13 * np.abs(Il[n]).max()
+    assert np.abs(Il[0] - Ig[0]).max() > 1e-3   # not trivially equal elsewhere
+
+
+# --------------------------------------------------------------------------
+# propagators and the row / diagonal update against matrix exponentials
+# --------------------------------------------------------------------------
+def _herm(rng, nb, scale=1.0):
+    a = ki.random_blocks(rng, (nb, nb), scale)
+    return 0.5 * (a + a.conj().T)
+
+
+def test_propagators_against_expm():
+    nb, nk, dt = 4, 3, 0.07
+    h = np.stack([_herm(RNG, nb, 2.0) for _ in range(nk)])
+    h[1] = np.diag([0.0, 0.5, 0.5, -1.0])      # exact zero and degenerate eigenvalues
+    U, V, W, lam = oracle.propagators(nb, nk, dt, h)
+    for k in range(nk):
+        Ue = sla.expm(-1j * dt * h[k])
+        assert np.abs(U[k] - Ue).max() < 1e-14
+        assert np.abs(h[k] @ V[k] - (Ue - np.eye(nb))).max() < 1e-14
+        assert np.abs(W[k] @ np.diag(lam[k]) @ W[k].conj().T - h[k]).max() < 1e-13
+        assert np.abs(W[k].conj().T @ W[k] - np.eye(nb)).max() < 1e-14
+        # V against the augmented exponential of y' = -i h y - i c
+        aug = np.zeros((2 * nb, 2 * nb), complex)
+        aug[:nb, :nb] = -1j * h[k]
+        aug[:nb, nb:] = -1j * np.eye(nb)
+        Ve = sla.expm(dt * aug)[:nb, nb:]
+        assert np.abs(V[k] - Ve).max() < 1e-14
+
+
+def test_update_row_against_exact_constant_source_solutions():
+    nb, nk, n, dt, theta = 3, 2, 5, 0.05, 0.5
+    h = np.stack([_herm(RNG, nb, 1.5) for _ in range(nk)])
+    U, V, W, lam = oracle.propagators(nb, nk, dt, h)
+    Gpl = ki.random_blocks(RNG, (n, nk, nb, nb))
+    Gpg = ki.random_blocks(RNG, (n, nk, nb, nb))
+    Gpl[n - 1] = np.stack([1j * _herm(RNG, nb) for _ in range(nk)])   # anti-Hermitian diagonal
+    Ipl = ki.random_blocks(RNG, (n, nk, nb, nb))
+    Ipg = ki.random_blocks(RNG, (n, nk, nb, nb))
+    Icl = ki.random_blocks(RNG, (n + 1, nk, nb, nb))
+    Icg = ki.random_blocks(RNG, (n + 1, nk, nb, nb))
+    outl, outg = oracle.update_row(nb, nk, n, dt, theta, U, V, W, lam, Gpl, Gpg, Ipl, Ipg, Icl, Icg)
+    I3 = np.eye(nb)
+    for k in range(nk):
+        # rows: y' = -i h y - i Ibar, exact over one step
+        aug = np.zeros((2 * nb, 2 * nb), complex)
+        aug[:nb, :nb] = -1j * h[k]
+        aug[:nb, nb:] = -1j * I3
+        E = sla.expm(dt * aug)
+        for j in range(n):
+            for (out, Gp, Ip, Ic) in ((outl, Gpl, Ipl, Icl), (outg, Gpg, Ipg, Icg)):
+                ib = (1 - theta) * Ip[j, k] + theta * Ic[j, k]
+                exact = E[:nb, :nb] @ Gp[j, k] + E[:nb, nb:] @ ib
+                assert np.abs(out[j, k] - exact).max() < 1e-13
+        # diagonal: i G' = [h, G] + S, S = Ibar + Ibar^+, vectorised exactly
+        S = (1 - theta) * (Ipl[n - 1, k] + Ipl[n - 1, k].conj().T) + theta * (Icl[n, k] + Icl[n, k].conj().T)
+        Lop = -1j * (np.kron(h[k], I3) - np.kron(I3, h[k].T))
+        aug2 = np.zeros((nb * nb + 1, nb * nb + 1), complex)
+        aug2[:nb * nb, :nb * nb] = Lop
+        aug2[:nb * nb, nb * nb] = -1j * S.reshape(-1)
+        y = sla.expm(dt * aug2) @ np.concatenate([Gpl[n - 1, k].reshape(-1), [1.0]])
+        exact = y[:nb * nb].reshape(nb, nb)
+        assert np.abs(outl[n, k] - exact).max() < 1e-13
+        assert np.abs(outg[n, k] - (exact - 1j * I3)).max() < 1e-13
+
+
+# --------------------------------------------------------------------------
+# whole-step pins
+# --------------------------------------------------------------------------
+def test_c1_bands_match_stated_dispersion():
+    s = ki.config("c1")
+    for k in range(s.nk):
+        kk = 2 * np.pi * k / 8
+        e = np.linalg.eigvalsh(h0_of(s, k))
+        want = sorted(-2 * np.cos(kk + b * np.pi / 2) + 0.5 * b for b in range(2))
+        assert np.allclose(sorted(e), want, atol=1e-14)
+
+
+@pytest.mark.parametrize("driven", [False, True])
+def test_noninteracting_closed_form(driven):
+    """U = 0: G^<(k; t_n, t_j) = i Uc_n rho0 Uc_j^+ with Uc the product of the
+    per-step exponentials of h0(k - A_i); undriven this is i f(e) e^{-i e (t-t')}."""
+    s = ki.small_system(3, (3, 2), 24, 0.05, 0.0, seed=3, drive_amp=0.6 if driven else 0.0)
+    o = oracle.Oracle(s)
+    o.step(s.nt)
+    for k in range(s.nk):
+        rho0 = fermi_matrix(h0_of(s, k), s.beta, s.mu)
+        Uc = [np.eye(s.nb, dtype=complex)]
+        for i in range(s.nt):
+            A = 0.0 if s.A is None else s.A[i]
+            Uc.append(sla.expm(-1j * s.dt * h0_of(s, k, A)) @ Uc[-1])
+        for (i, j) in [(0, 0), (5, 2), (13, 13), (24, 0), (24, 17), (3, 9)]:
+            want = 1j * Uc[i] @ rho0 @ Uc[j].conj().T
+            got = o.block(i, j, 0)[k]
+            assert np.abs(got - want).max() < 1e-13, (i, j)
+            gotg = o.block(i, j, 1)[k]
+            wantg = want - 1j * Uc[i] @ Uc[j].conj().T
+            assert np.abs(gotg - wantg).max() < 1e-13, (i, j)
+    if not driven:   # time-translation invariance in equilibrium
+        a, b = o.block(20, 7, 0), o.block(13, 0, 0)
+        assert np.abs(a - b).max() < 1e-13
+
+
+def test_particle_number_conserved_driven_interacting():
+    s = ki.small_system(3, (3, 3), 40, 0.04, 1.2, seed=5, drive_amp=0.5)
+    o = oracle.Oracle(s)
+    o.step(s.nt)
+    N = np.array([o.observables(n)[1][0] for n in range(s.nt + 1)])
+    assert np.abs(N - N[0]).max() < 1e-12 * abs(N[0])
+    nkb = np.array([o.observables(n)[0] for n in range(s.nt + 1)])
+    assert np.abs(nkb - nkb[0]).max() > 1e-3   # the drive does move occupations
+
+
+def test_equal_time_lesser_is_antihermitian_and_greater_offset():
+    s = ki.config("c1", nt=20)
+    o = oracle.Oracle(s)
+    o.step(20)
+    for n in (0, 7, 20):
+        g = o.block(n, n, 0)
+        assert np.abs(g + np.conj(np.swapaxes(g, 1, 2))).max() < 1e-15
+        assert np.abs(o.block(n, n, 1) - (g - 1j * np.eye(2))).max() < 1e-15
+
+
+def test_adjoint_symmetry_of_stored_blocks():
+    s = ki.small_system(2, (4, 1), 12, 0.05, 0.8, seed=9)
+    o = oracle.Oracle(s)
+    o.step(12)
+    for (i, j) in [(3, 9), (0, 12), (11, 12)]:
+        for x in (0, 1):
+            a = o.block(i, j, x)
+            b = o.block(j, i, x)
+            assert np.abs(a + np.conj(np.swapaxes(b, 1, 2))).max() == 0.0
+
+
+def test_energy_drift_is_second_order_in_dt():
+    """Undriven c1: E_tot is conserved by the continuous equations of a
+    conserving approximation; the discrete drift must fall ~4x per dt halving.
+    A wrong sign of the correlation energy breaks this (drift O(1e-2), no decay)."""
+    drifts = []
+    for dt in (0.05, 0.025, 0.0125):
+        s = ki.config("c1")
+        s.dt, s.nt = dt, int(round(1.6 / dt))
+        o = oracle.Oracle(s)
+        o.step(s.nt)
+        drifts.append(abs(o.observables(s.nt)[1][5] - o.observables(0)[1][5]))
+    r1, r2 = drifts[0] / drifts[1], drifts[1] / drifts[2]
+    assert 3.5 < r1 < 4.5 and 3.5 < r2 < 4.5, drifts
+    assert drifts[0] < 1e-4
+
+
+def test_time_step_order_two():
+    """Interacting c1-like ring: G at t = 1.2 converges at second order in dt."""
+    def run(dt):
+        s = ki.config("c1")
+        s.L = (4, 1)
+        s.dt, s.nt = dt, int(round(1.2 / dt))
+        o = oracle.Oracle(s)
+        o.step(s.nt)
+        return o.block(s.nt, s.nt // 2, 0)
+    ref = run(0.05 / 8)
+    e = [np.abs(run(dt) - ref).max() for dt in (0.05, 0.025, 0.0125)]
+    # Richardson-corrected ratios against a finite-dt reference
+    assert 3.0 < e[0] / e[1] < 5.0 and 3.0 < e[1] / e[2] < 5.5, e
+
+
+# --------------------------------------------------------------------------
+# exact diagonalisation: second Born + HF is exact through O(U^2) for an
+# uncorrelated initial state, so the density error must scale as U^3.
+# --------------------------------------------------------------------------
+def _ed_density(sys, U, T, dt):
+    nb, nk, L = sys.nb, sys.nk, sys.L
+    M = nb * nk
+    dim = 2 ** M
+    c = []
+    for m in range(M):
+        op = np.zeros((dim, dim))
+        for st in range(dim):
+            if st >> m & 1:
+                sign = (-1) ** bin(st & ((1 << m) - 1)).count("1")
+                op[st ^ (1 << m), st] = sign
+        c.append(op)
+    cd = [x.T for x in c]
+    H0 = np.zeros((dim, dim), complex)
+    for k in range(nk):
+        hk = h0_of(sys, k)
+        for a in range(nb):
+            for b in range(nb):
+                if hk[a, b] != 0:
+                    H0 += hk[a, b] * cd[k * nb + a] @ c[k * nb + b]
+    Hint = np.zeros((dim, dim), complex)
+    for i0 in range(L[0]):
+        for i1 in range(L[1]):
+            dens = []
+            for a in range(nb):
+                op = sum(np.exp(2j * np.pi * ((k // L[1]) * i0 / L[0] + (k % L[1]) * i1 / L[1]))
+                         * c[k * nb + a] for k in range(nk)) / math.sqrt(nk)
+                dens.append(op.conj().T @ op)
+            for a in range(nb):
+                for b in range(a + 1, nb):
+                    Hint += sys.v[a, b] * dens[a] @ dens[b]
+    Hsh = np.zeros((dim, dim), complex)
+    if sys.paper_shift:
+        for k in range(nk):
+            Hsh -= cd[k * nb + nb - 1] @ c[k * nb + nb - 1]
+    Ntot = sum(cd[m] @ c[m] for m in range(M))
+    w, V = np.linalg.eigh(H0 - sys.mu * Ntot)
+    rho = V @ np.diag(np.exp(-sys.beta * (w - w.min()))) @ V.conj().T
+    rho /= np.trace(rho)
+    ew, EV = np.linalg.eigh(H0 + U * Hint + U * Hsh)
+    nops = [cd[m] @ c[m] for m in range(M)]
+    out = []
+    nt = int(round(T / dt))
+    for i in range(nt + 1):
+        Ut = EV @ np.diag(np.exp(-1j * ew * i * dt)) @ EV.conj().T
+        r = Ut @ rho @ Ut.conj().T
+        out.append(np.array([np.trace(r @ x).real for x in nops]).reshape(nk, nb))
+    return np.array(out)
+
+
+@pytest.mark.slow
+def test_exact_diagonalisation_error_scales_as_U_cubed():
+    T, dt = 1.0, 0.02
+    errs = []
+    for U in (0.8, 0.4, 0.2):
+        s = ki.small_system(2, (4, 1), int(round(T / dt)), dt, U, seed=11, beta=5.0,
+                            hf=1, paper_shift=1)
+        ed = _ed_density(s, U, T, dt)
+        o = oracle.Oracle(s)
+        o.step(s.nt)
+        kbe = np.array([o.observables(n)[0] for n in range(s.nt + 1)])
+        errs.append(np.abs(kbe - ed).max())
+        assert np.abs(ed - ed[0]).max() > 20 * errs[-1]    # the dynamics is resolved
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 7.0 < r1 < 9.5 and 7.0 < r2 < 9.5, errs

@@ -1,0 +1,279 @@
+"""KBE time-stepping benchmark on GB300.
+
+A bench *step* is one whole Kadanoff-Baym trajectory of the driven 2-D
+workload c2 (N_b = 4 bands, 8x8 mesh, N_t = 512 steps, dt = 0.02, P(EC)^2 E):
+reset to the Fermi state, then 512 time steps on the device-resident history
+(4.3 GB, larger than L2). The metric is KBE time-steps per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one process per GPU) every rank advances its own
+independent c2 system (weak scaling, no data-path collective).
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+prefix of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import kbe_inputs as ki  # noqa: E402
+
+METRIC = "KBE time-steps/s"
+WORKLOAD = ("c2: N_b=4, 8x8 mesh (n_k=64), N_t=512, dt=0.02, U=1.0, beta=20, "
+            "Peierls pulse A0=0.3, HF + second Born, P(EC)^2E")
+# FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s);
+# a DFMA probe on this GB300 pool measured 1.195 TFLOP/s.
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+ORACLE_PREFIX = 40
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--nt", type=int, default=None, help="truncate N_t (testing only)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def aggregate(times_s, units_per_rank):
+    """Whole-job throughput: units all ranks processed / slowest rank's time."""
+    t = max(times_s)
+    return sum(units_per_rank) / t, t
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms in a thread."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._th = None
+
+    def start(self):
+        def run():
+            while not self._stop.is_set():
+                try:
+                    out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits"],
+                                         capture_output=True, text=True, timeout=5).stdout.strip()
+                    if out:
+                        self.rows.append([x.strip() for x in out.split(",")])
+                except Exception:
+                    pass
+                self._stop.wait(0.2)
+        self._th = threading.Thread(target=run, daemon=True)
+        self._th.start()
+
+    def stop(self):
+        self._stop.set()
+        if self._th:
+            self._th.join(timeout=10)
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for name, val in zip(names, r[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_2505_19467_gb300 as kbe
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    s = ki.config("c2", nt=args.nt)
+    nt = s.nt
+    stream = torch.cuda.Stream()
+    g = kbe.KBE.from_system(s, stream=stream)
+
+    def trajectory():
+        g.reset()
+        g.step(nt)
+
+    for _ in range(args.warmup):
+        trajectory()
+    g.synchronize()
+
+    # ---- device-resident timing, sweep kernel profiled with CUDA events ----
+    sampler = ClockSampler(local) if rank == 0 else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    g.profile(True)
+    if sampler:
+        sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        trajectory()
+    e1.record(stream)
+    e1.synchronize()
+    g.synchronize()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    prof = g.profile_read()
+    g.profile(False)
+    t_dev = e0.elapsed_time(e1) / 1e3
+
+    # ---- end to end through the C ABI with host buffers -------------------
+    R = np.ascontiguousarray(s.hop_R, np.int32)
+    T = np.ascontiguousarray(s.hop_T, np.complex128)
+    Uarr = np.array([s.U], np.float64)
+    v = np.ascontiguousarray(s.v, np.float64)
+    A = np.ascontiguousarray(s.A, np.float64)
+    nkb_host = np.empty((nt + 1, s.nk, s.nb), np.float64)
+    sc_host = np.empty((nt + 1, 6), np.float64)
+    h2d = R.nbytes + T.nbytes + Uarr.nbytes + v.nbytes + A.nbytes + 16
+    d2h = nkb_host.nbytes + sc_host.nbytes
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        g.set_hamiltonian(R, T)
+        g.set_interaction(Uarr, v)
+        g.set_drive(A, s.direction)
+        g.reset()
+        g.step(nt)
+        g.observables_all(nkb_host, sc_host)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+
+    times = [t_dev, t_e2e]
+    if dist:
+        tt = torch.tensor(times, device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        times = tt.tolist()
+    units = nt * args.steps
+    value, tmax = aggregate([times[0]], [units * world])
+    e2e_value = units * world / times[1]
+
+    if rank == 0:
+        sweep_s = prof["sweep_ms"] / 1e3
+        achieved = prof["sweep_flops"] / sweep_s / 1e9 if sweep_s > 0 else 0.0
+        line = {
+            "metric": METRIC, "value": value, "unit": "time-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded c2 system, kbe_inputs)",
+            "config": {"workload": WORKLOAD, "bench_step": f"one trajectory: reset + {nt} time steps",
+                       "time_steps_per_bench_step": nt, "n_corr": 2,
+                       "l2": "history 4.3 GB > 129 MB L2 (inputs larger than L2)",
+                       "parallelism": f"replicas x{world} (independent systems)"},
+            "roofline": {"kernel": "collision sweep (a2)", "bound": "alu", "achieved": achieved,
+                         "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s FP64",
+                         "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                         "peak_source": "FP64 pipe: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                         "launches": prof["sweep_launches"], "sweep_share_of_step":
+                             sweep_s / t_dev if t_dev > 0 else None,
+                         "hbm_gbs_achieved": prof["sweep_bytes"] / sweep_s / 1e9 if sweep_s > 0 else 0.0},
+            "e2e": {"value": e2e_value, "unit": "time-steps/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(prof["launches"]),
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(s)
+        print(json.dumps(line), flush=True)
+    g.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(s, prefix=ORACLE_PREFIX):
+    """The FP64 oracle, as it stands, on the host cores: first `prefix` steps of c2."""
+    import oracle
+    o = oracle.Oracle(s, nt_max=prefix)
+    t0 = time.perf_counter()
+    o.step(prefix)
+    dt = time.perf_counter() - t0
+    return {"value": prefix / dt, "unit": "time-steps/s", "cores": oracle.oracle.threads(),
+            "kind": "oracle",
+            "sample": f"first {prefix} of {s.nt} steps of c2 (steps cost O(n^2); later steps are slower)",
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    s = ki.config("c2", nt=args.nt)
+    prefix = min(ORACLE_PREFIX // 2, s.nt)
+    for _ in range(args.warmup):
+        o = oracle.Oracle(s, nt_max=prefix)
+        o.step(min(4, prefix))
+    times = []
+    for _ in range(args.steps):
+        o = oracle.Oracle(s, nt_max=prefix)
+        t0 = time.perf_counter()
+        o.step(prefix)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = prefix * args.steps / total
+    line = {
+        "metric": METRIC, "value": value, "unit": "time-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded c2 system, kbe_inputs)", "impl": "reference",
+        "config": {"workload": WORKLOAD, "bench_step": f"oracle: first {prefix} of {s.nt} time steps",
+                   "n_corr": 2},
+        "cpu_baseline": {"value": value, "unit": "time-steps/s", "cores": oracle.oracle.threads(),
+                         "kind": "oracle", "sample": f"first {prefix} steps of c2 per bench step"},
+        "e2e": {"value": value, "unit": "time-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * kbe.h -- C ABI of libkbe, a GB300 (sm_103a) implementation of the
+ * Kadanoff-Baym time step of arXiv 2505.19467 ("GPU Acceleration of
+ * Non-equilibrium Green's Function Calculation using OpenACC and CUDA
+ * FORTRAN"), on one GPU.
+ *
+ * Problem (Sec. 2): lattice fermions with N_b bands on a 1-D ring or 2-D
+ * L0 x L1 mesh (n_k = L0 L1 points k = 2 pi m / L), bare Bloch Hamiltonian
+ * h0(k) from hopping matrices t(R), an on-site inter-band density-density
+ * interaction U(t) v_ab (Eq. 2; v = 1 - delta is the paper's pair of bands),
+ * and a Peierls drive h0(k - A(t) d). The library advances the lesser and
+ * greater two-time Green's functions G^<, G^>(k; t_n, t_j) row by row
+ * (Algorithm 1) with
+ *   (a1) the second-Born self-energy on the new row (Eq. 7, k - q
+ *        convolution),
+ *   (a2) the collision integrals over the stored history (Eq. 6, trapezoid
+ *        weights),
+ *   (a3) the mean-field Hamiltonian and the step propagators,
+ *   (a4) the predictor-corrector update of the row and the time diagonal,
+ *   (a5) equal-time observables.
+ *
+ * Conventions for every entry point:
+ *  - Complex numbers are interleaved (re, im) doubles ("c128").
+ *  - Host arrays passed in are copied before the call returns; the caller
+ *    keeps ownership. Host output arrays are caller-owned and must hold the
+ *    documented number of elements.
+ *  - Device pointers ("dev") are caller-owned device memory on the current
+ *    CUDA device; work is enqueued on the given stream (NULL = legacy default
+ *    stream) and the call returns before it completes.
+ *  - A handle owns all device memory it allocates. Handles are not thread
+ *    safe. All work of a handle is ordered on the stream given at creation.
+ *  - Errors: a negative kbe_status; kbe_last_error() has the message. Device
+ *    faults and non-finite results are sticky: the handle refuses further
+ *    steps until kbe_reset().
+ */
+#ifndef KBE_H
+#define KBE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KBE_OK = 0,
+  KBE_ERR_ARG = -1,         /* invalid argument (size, pointer, range)          */
+  KBE_ERR_OOM = -2,         /* device allocation failed                         */
+  KBE_ERR_CUDA = -3,        /* a CUDA call failed                               */
+  KBE_ERR_STATE = -4,       /* call not valid in the handle's state             */
+  KBE_ERR_NONFINITE = -5,   /* a NaN/Inf appeared in the propagated state       */
+  KBE_ERR_TIMEOUT = -6,     /* a bounded device wait expired                    */
+  KBE_ERR_UNSUPPORTED = -7, /* configuration not compiled in (e.g. N_b)         */
+  KBE_ERR_INTERNAL = -8
+} kbe_status;
+
+/* Arithmetic of the collision-integral sweep (the dominant kernel). */
+enum {
+  KBE_PREC_FP64 = 0 /* native FP64 everywhere                                  */
+};
+
+typedef struct kbe_config {
+  int nb;          /* bands N_b, one of 1,2,3,4,6,8,12,16                        */
+  int dim;         /* 1 (ring, L[1] must be 1) or 2                              */
+  int L[2];        /* mesh extents, n_k = L[0] * L[1] <= 4096                    */
+  int nt_max;      /* rows t_0 .. t_{nt_max} are stored                          */
+  double dt;       /* time step (> 0)                                            */
+  double beta, mu; /* Fermi initial state f(h0(k)) at inverse temperature beta  */
+  int precision;   /* KBE_PREC_*                                                 */
+  int n_corr;      /* corrector passes of Algorithm 1 (fixed count, >= 0)        */
+  int hf;          /* 1: Hartree-Fock mean field in h                            */
+  int paper_shift; /* 1: the -U(t) n_c one-body term of Eq. 2 on band N_b - 1    */
+} kbe_config;
+
+typedef struct kbe_handle kbe_handle;
+
+/* Per-handle timing of the collision-integral sweep kernel (CUDA events on the
+ * handle's stream), accumulated while profiling is enabled. */
+typedef struct kbe_profile_stats {
+  int sweep_launches;       /* sweep launches timed                               */
+  double sweep_ms;          /* summed event time of those launches                */
+  double sweep_flops;       /* algorithmic flops of those launches (24 n^2 N_b^3 n_k) */
+  double sweep_bytes;       /* algorithmic bytes (stored history read once + I row) */
+  int launches;             /* all kernels launched while enabled                 */
+} kbe_profile_stats;
+
+/* ---------------------------------------------------------------------- */
+/* handle API (Algorithm 1 on a resident two-time history)                 */
+/* ---------------------------------------------------------------------- */
+
+/* Create a handle. cfg is copied. stream is a cudaStream_t (NULL: default).
+ * Allocates the lower-triangle history (nt_max+1)(nt_max+2)/2 blocks of
+ * 2 x N_b^2 x n_k c128 plus row buffers. KBE_ERR_OOM if it does not fit. */
+kbe_status kbe_create(const kbe_config *cfg, void *stream, kbe_handle **out);
+kbe_status kbe_destroy(kbe_handle *h);
+
+/* h0_ab(k) = sum_r t_ab(R_r) exp(i k.R_r) (Sec. 2 band energies as hoppings).
+ * R: host int [nhop][2] (R[r][1] ignored for dim 1); t: host c128
+ * [nhop][nb][nb]. The resulting h0(k) must be Hermitian; not checked. */
+kbe_status kbe_set_hamiltonian(kbe_handle *h, int nhop, const int *R, const double *t);
+
+/* U(t_i) samples (len = nt_max + 1) or one constant (len = 1), the U(t) of
+ * Eqs. 2 and 7; v: host double [nb][nb] pairing pattern v_ab (symmetric,
+ * zero diagonal), NULL keeps the current one (default 1 - delta_ab). */
+kbe_status kbe_set_interaction(kbe_handle *h, int len, const double *U, const double *v);
+
+/* Peierls vector potential samples A_i = A(t_{i+1/2}), i < len (len >= 1), the
+ * drive of step t_i -> t_{i+1}; dir: host double[dim] unit direction d.
+ * A == NULL or len == 0 removes the drive. */
+kbe_status kbe_set_drive(kbe_handle *h, int len, const double *A, const double *dir);
+
+/* t = 0: G^<(k;0,0) = i f(h0(k)), G^>(0,0) = G^<(0,0) - i, I = 0 (no initial
+ * correlations). Clears a sticky error. Requires kbe_set_hamiltonian. */
+kbe_status kbe_reset(kbe_handle *h);
+
+/* Advance nsteps rows with P(EC)^n_corr E (Algorithm 1). Asynchronous on the
+ * handle's stream. KBE_ERR_STATE past nt_max or before kbe_reset. */
+kbe_status kbe_step(kbe_handle *h, int nsteps);
+
+/* Wait for the handle's stream; returns the sticky device status. */
+kbe_status kbe_synchronize(kbe_handle *h);
+
+/* Index of the last completed row (-1 before kbe_reset). */
+kbe_status kbe_current_step(const kbe_handle *h, int *n);
+
+/* Equal-time observables at row `step` (0 <= step <= current): n_kb = Re rho_bb(k)
+ * into host double [nk][nb] (may be NULL) and scalars[6] = {N, E_kin, E_HF,
+ * E_corr, E_shift, E_tot} (may be NULL). Synchronises the stream. */
+kbe_status kbe_observables(kbe_handle *h, int step, double *n_kb, double *scalars);
+
+/* Observables of rows 0..current at once: n_kb host double [(n+1)][nk][nb]
+ * and scalars host double [(n+1)][6] (either may be NULL). Synchronises. */
+kbe_status kbe_observables_all(kbe_handle *h, double *n_kb, double *scalars);
+
+/* Row i of G^x (which 0: lesser, 1: greater), blocks j = 0..i, into host c128
+ * [(i+1)][nk][nb][nb]. Synchronises. */
+kbe_status kbe_get_row(kbe_handle *h, int i, int which, double *out);
+
+/* Collision-integral sweep timing (CUDA events around each sweep launch). */
+kbe_status kbe_profile_enable(kbe_handle *h, int enable);
+kbe_status kbe_profile_read(kbe_handle *h, kbe_profile_stats *out);
+
+/* Message of the last error of this handle (or of the last failed create). */
+const char *kbe_last_error(const kbe_handle *h);
+
+/* ---------------------------------------------------------------------- */
+/* stateless per-step operations on device buffers                          */
+/*                                                                         */
+/* Device layout: a "block" is one time pair (i, j) of both components,     */
+/* c128 [2][nb][nb][nk] (component x = 0 lesser, 1 greater; k fastest). The */
+/* history is the lower triangle, block (i, j), i >= j, at index             */
+/* i(i+1)/2 + j. A "row" of m blocks is [m][2][nb][nb][nk]. Per-k matrices   */
+/* are [nb][nb][nk]; per-k eigenvalues [nb][nk] doubles.                     */
+/* ---------------------------------------------------------------------- */
+
+typedef struct kbe_mesh {
+  int nb;    /* bands (see kbe_config)           */
+  int L[2];  /* mesh extents, L[1] = 1 for 1-D   */
+} kbe_mesh;
+
+/* (a1) Second-Born self-energy row, Eq. 7:
+ *   Sigma^x(k; t_n, t_l), l = 0..n, from row n of G (blocks (n, l)),
+ * computed as DFT_k -> real-space band products -> inverse DFT (exact
+ * rewriting of the q, k' sums). v: host double [nb][nb] pairing pattern.
+ * U(t_n) U(t_l) = Un * Ul_dev[l] (Ul_dev: device double [n+1]) or Un * Un if
+ * Ul_dev is NULL. Grow_dev: row n, (n+1) blocks; Sigma_dev: (n+1) blocks.
+ * work_dev: device scratch of kbe_op_sigma_row_workspace(m, n) bytes. */
+size_t kbe_op_sigma_row_workspace(const kbe_mesh *m, int n);
+kbe_status kbe_op_sigma_row(const kbe_mesh *m, const double *v, int n, double Un,
+                            const double *Ul_dev, const void *Grow_dev, void *Sigma_dev,
+                            void *work_dev, size_t work_bytes, void *stream);
+
+/* (a2) Collision-integral row, Eq. 6 in left form:
+ *   I^x(n, j) = sum_{l=0}^{n} w^(n)_l [S^>(n,l) - S^<(n,l)] G^x(l, j)
+ *             + sum_{l=0}^{j} w^(j)_l S^x(n,l) [G^<(l,j) - G^>(l,j)],
+ * j = 0..n, with trapezoid weights w^(m)_l = dt (1 - [l=0]/2 - [l=m]/2)
+ * (zero for m = 0) and G(l, j) = -G(j, l)^+ above the diagonal.
+ * H_dev: history triangle with rows 0..n; Sigma_dev: n+1 blocks; I_dev:
+ * n+1 blocks written. precision: KBE_PREC_*. */
+kbe_status kbe_op_collision_row(const kbe_mesh *m, int n, double dt, int precision,
+                                const void *H_dev, const void *Sigma_dev, void *I_dev,
+                                void *stream);
+
+/* (a3) Step propagators of a Hermitian h(k) (device [nb][nb][nk] c128):
+ * h = W diag(lam) W^+, U = e^{-i dt h}, V = (U - 1) h^{-1} (-i dt on the
+ * null space). Outputs device U, V, W [nb][nb][nk] c128, lam [nb][nk]. */
+kbe_status kbe_op_propagators(const kbe_mesh *m, double dt, const void *h_dev, void *U_dev,
+                              void *V_dev, void *W_dev, double *lam_dev, void *stream);
+
+/* (a4) Row n from row n-1 (Algorithm 1, "solve Eq. 5"):
+ *   G^x(n, j) = U G^x(n-1, j) + V Ibar^x(j),  j < n,
+ *   Ibar = (1 - theta) I_{n-1}(j) + theta I_n(j),
+ *   G^<(n, n) = U G^<(n-1, n-1) U^+ - i W [(W^+ Sbar W) o D] W^+,
+ *   Sbar = (1-theta)(I^<_{n-1}(n-1) + h.c.) + theta (I^<_n(n) + h.c.),
+ *   D_ab = (1 - e^{-i (lam_a - lam_b) dt}) / (i (lam_a - lam_b)),
+ *   G^>(n, n) = G^<(n, n) - i.
+ * Gprev_dev: row n-1 (n blocks); Iprev_dev: n blocks; Icur_dev: n+1 blocks
+ * (read only if theta != 0); out_dev: row n (n+1 blocks). n >= 1. */
+kbe_status kbe_op_update_row(const kbe_mesh *m, int n, double dt, double theta,
+                             const void *U_dev, const void *V_dev, const void *W_dev,
+                             const double *lam_dev, const void *Gprev_dev,
+                             const void *Iprev_dev, const void *Icur_dev, void *out_dev,
+                             void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KBE_H */

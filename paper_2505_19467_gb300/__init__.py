@@ -1,0 +1,11 @@
+"""GB300-native Kadanoff-Baym time stepping (arXiv 2505.19467) on one GPU.
+
+The numerical work runs in ``libkbe.so`` (hand-written CUDA for sm_103a,
+C ABI in ``include/kbe.h``); this package is its thin Python binding.
+"""
+from ._binding import (KBE, KBEError, KBE_PREC_FP64, EXPORTS, LIB_PATH, load, collision_row,
+                       propagators, sigma_row, sigma_row_workspace, update_row)
+from .builder import build
+
+__all__ = ["KBE", "KBEError", "KBE_PREC_FP64", "EXPORTS", "LIB_PATH", "load", "build",
+           "sigma_row", "sigma_row_workspace", "collision_row", "propagators", "update_row"]

@@ -1,0 +1,269 @@
+"""ctypes binding of libkbe (include/kbe.h): argument marshalling only.
+
+Every numerical step runs in the CUDA library; this module converts numpy /
+torch arguments to pointers and status codes to exceptions. There is no CPU
+fallback: if libkbe.so cannot be loaded, importing the handle API raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libkbe.so")
+
+KBE_PREC_FP64 = 0
+
+STATUS = {
+    0: "KBE_OK", -1: "KBE_ERR_ARG", -2: "KBE_ERR_OOM", -3: "KBE_ERR_CUDA", -4: "KBE_ERR_STATE",
+    -5: "KBE_ERR_NONFINITE", -6: "KBE_ERR_TIMEOUT", -7: "KBE_ERR_UNSUPPORTED", -8: "KBE_ERR_INTERNAL",
+}
+
+# every function declared in include/kbe.h (checked against the header by the tests)
+EXPORTS = [
+    "kbe_create", "kbe_destroy", "kbe_set_hamiltonian", "kbe_set_interaction", "kbe_set_drive",
+    "kbe_reset", "kbe_step", "kbe_synchronize", "kbe_current_step", "kbe_observables",
+    "kbe_observables_all", "kbe_get_row", "kbe_profile_enable", "kbe_profile_read",
+    "kbe_last_error", "kbe_op_sigma_row_workspace", "kbe_op_sigma_row", "kbe_op_collision_row",
+    "kbe_op_propagators", "kbe_op_update_row",
+]
+
+
+class KBEError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class kbe_config(ctypes.Structure):
+    _fields_ = [("nb", ctypes.c_int), ("dim", ctypes.c_int), ("L", ctypes.c_int * 2),
+                ("nt_max", ctypes.c_int), ("dt", ctypes.c_double), ("beta", ctypes.c_double),
+                ("mu", ctypes.c_double), ("precision", ctypes.c_int), ("n_corr", ctypes.c_int),
+                ("hf", ctypes.c_int), ("paper_shift", ctypes.c_int)]
+
+
+class kbe_mesh(ctypes.Structure):
+    _fields_ = [("nb", ctypes.c_int), ("L", ctypes.c_int * 2)]
+
+
+class kbe_profile_stats(ctypes.Structure):
+    _fields_ = [("sweep_launches", ctypes.c_int), ("sweep_ms", ctypes.c_double),
+                ("sweep_flops", ctypes.c_double), ("sweep_bytes", ctypes.c_double),
+                ("launches", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libkbe.so; raises if it is missing (build with __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libkbe.so not found at {path}: run __graft_entry__.build() "
+                          "(the CUDA library is required; there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    pcfg, pmesh = ctypes.POINTER(kbe_config), ctypes.POINTER(kbe_mesh)
+    sig = {
+        "kbe_create": (I, [pcfg, P, ctypes.POINTER(P)]),
+        "kbe_destroy": (I, [P]),
+        "kbe_set_hamiltonian": (I, [P, I, P, P]),
+        "kbe_set_interaction": (I, [P, I, P, P]),
+        "kbe_set_drive": (I, [P, I, P, P]),
+        "kbe_reset": (I, [P]),
+        "kbe_step": (I, [P, I]),
+        "kbe_synchronize": (I, [P]),
+        "kbe_current_step": (I, [P, ctypes.POINTER(I)]),
+        "kbe_observables": (I, [P, I, P, P]),
+        "kbe_observables_all": (I, [P, P, P]),
+        "kbe_get_row": (I, [P, I, I, P]),
+        "kbe_profile_enable": (I, [P, I]),
+        "kbe_profile_read": (I, [P, ctypes.POINTER(kbe_profile_stats)]),
+        "kbe_last_error": (ctypes.c_char_p, [P]),
+        "kbe_op_sigma_row_workspace": (S, [pmesh, I]),
+        "kbe_op_sigma_row": (I, [pmesh, P, I, D, P, P, P, P, S, P]),
+        "kbe_op_collision_row": (I, [pmesh, I, D, I, P, P, P, P]),
+        "kbe_op_propagators": (I, [pmesh, D, P, P, P, P, P, P]),
+        "kbe_op_update_row": (I, [pmesh, I, D, D, P, P, P, P, P, P, P, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, handle=None) -> None:
+    if rc != 0:
+        msg = load().kbe_last_error(handle)
+        raise KBEError(rc, msg.decode() if msg else "")
+
+
+def _np_ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data
+
+
+def _tptr(t):
+    """Device pointer of a torch tensor (or None)."""
+    return None if t is None else t.data_ptr()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def mesh(nb: int, L) -> kbe_mesh:
+    m = kbe_mesh()
+    m.nb = nb
+    m.L[0], m.L[1] = int(L[0]), int(L[1])
+    return m
+
+
+class KBE:
+    """One Kadanoff-Baym system on the GPU (handle API of include/kbe.h)."""
+
+    def __init__(self, nb: int, dim: int, L, nt_max: int, dt: float, beta: float, mu: float,
+                 precision: int = KBE_PREC_FP64, n_corr: int = 2, hf: int = 1,
+                 paper_shift: int = 0, stream=None):
+        lib = load()
+        cfg = kbe_config()
+        cfg.nb, cfg.dim = nb, dim
+        cfg.L[0], cfg.L[1] = int(L[0]), int(L[1])
+        cfg.nt_max, cfg.dt, cfg.beta, cfg.mu = nt_max, dt, beta, mu
+        cfg.precision, cfg.n_corr, cfg.hf, cfg.paper_shift = precision, n_corr, hf, paper_shift
+        self.nb, self.nk, self.nt_max = nb, int(L[0]) * int(L[1]), nt_max
+        self._h = ctypes.c_void_p()
+        self._stream = _stream_ptr(stream)
+        _check(lib.kbe_create(ctypes.byref(cfg), self._stream, ctypes.byref(self._h)), None)
+
+    @classmethod
+    def from_system(cls, sys, nt_max=None, precision=KBE_PREC_FP64, stream=None, U=None, **over):
+        """Build and initialise from a kbe_inputs.System (reset included)."""
+        kw = dict(n_corr=sys.n_corr, hf=sys.hf, paper_shift=sys.paper_shift)
+        kw.update(over)
+        k = cls(sys.nb, sys.dim, sys.L, sys.nt if nt_max is None else nt_max, sys.dt, sys.beta,
+                sys.mu, precision=precision, stream=stream, **kw)
+        k.set_hamiltonian(sys.hop_R, sys.hop_T)
+        k.set_interaction(np.array([sys.U]) if U is None else U, sys.v)
+        k.set_drive(sys.A, sys.direction)
+        k.reset()
+        return k
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().kbe_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_hamiltonian(self, R, T):
+        R = np.ascontiguousarray(R, np.int32)
+        T = np.ascontiguousarray(T, np.complex128)
+        _check(load().kbe_set_hamiltonian(self._h, R.shape[0], _np_ptr(R), _np_ptr(T)), self._h)
+
+    def set_interaction(self, U, v=None):
+        U = np.ascontiguousarray(np.atleast_1d(U), np.float64)
+        v = None if v is None else np.ascontiguousarray(v, np.float64)
+        _check(load().kbe_set_interaction(self._h, len(U), _np_ptr(U), _np_ptr(v)), self._h)
+
+    def set_drive(self, A, direction=(1.0, 0.0)):
+        d = np.ascontiguousarray(direction, np.float64)
+        if A is None:
+            _check(load().kbe_set_drive(self._h, 0, None, _np_ptr(d)), self._h)
+        else:
+            A = np.ascontiguousarray(A, np.float64)
+            _check(load().kbe_set_drive(self._h, len(A), _np_ptr(A), _np_ptr(d)), self._h)
+
+    def reset(self):
+        _check(load().kbe_reset(self._h), self._h)
+
+    def step(self, nsteps: int = 1):
+        _check(load().kbe_step(self._h, int(nsteps)), self._h)
+
+    def synchronize(self):
+        _check(load().kbe_synchronize(self._h), self._h)
+
+    @property
+    def n(self) -> int:
+        x = ctypes.c_int()
+        _check(load().kbe_current_step(self._h, ctypes.byref(x)), self._h)
+        return x.value
+
+    def observables(self, step: int):
+        nkb = np.empty((self.nk, self.nb), np.float64)
+        sc = np.empty(6, np.float64)
+        _check(load().kbe_observables(self._h, int(step), _np_ptr(nkb), _np_ptr(sc)), self._h)
+        return nkb, sc
+
+    def observables_all(self, nkb_out=None, scalars_out=None):
+        n = self.n
+        nkb = nkb_out if nkb_out is not None else np.empty((n + 1, self.nk, self.nb), np.float64)
+        sc = scalars_out if scalars_out is not None else np.empty((n + 1, 6), np.float64)
+        _check(load().kbe_observables_all(self._h, _np_ptr(nkb), _np_ptr(sc)), self._h)
+        return nkb, sc
+
+    def row(self, i: int, which: int = 0) -> np.ndarray:
+        out = np.empty((i + 1, self.nk, self.nb, self.nb), np.complex128)
+        _check(load().kbe_get_row(self._h, int(i), int(which), _np_ptr(out)), self._h)
+        return out
+
+    def profile(self, enable: bool = True):
+        _check(load().kbe_profile_enable(self._h, int(enable)), self._h)
+
+    def profile_read(self) -> dict:
+        s = kbe_profile_stats()
+        _check(load().kbe_profile_read(self._h, ctypes.byref(s)), self._h)
+        return dict(sweep_launches=s.sweep_launches, sweep_ms=s.sweep_ms, sweep_flops=s.sweep_flops,
+                    sweep_bytes=s.sweep_bytes, launches=s.launches)
+
+
+# ---- stateless ops on torch device tensors (GPU layout, see include/kbe.h) ----
+
+def _c(t):
+    assert t.is_cuda and t.is_contiguous(), "device tensors must be contiguous CUDA tensors"
+    return t.data_ptr()
+
+
+def sigma_row(nb, L, v, n, Un, Grow, Sigma, work, Ul=None, stream=None):
+    m = mesh(nb, L)
+    v = np.ascontiguousarray(v, np.float64)
+    _check(load().kbe_op_sigma_row(ctypes.byref(m), _np_ptr(v), int(n), float(Un),
+                                   None if Ul is None else _c(Ul), _c(Grow), _c(Sigma), _c(work),
+                                   work.numel() * work.element_size(), _stream_ptr(stream)))
+
+
+def sigma_row_workspace(nb, L, n) -> int:
+    m = mesh(nb, L)
+    return int(load().kbe_op_sigma_row_workspace(ctypes.byref(m), int(n)))
+
+
+def collision_row(nb, L, n, dt, H, Sigma, I, precision=KBE_PREC_FP64, stream=None):
+    m = mesh(nb, L)
+    _check(load().kbe_op_collision_row(ctypes.byref(m), int(n), float(dt), int(precision), _c(H),
+                                       _c(Sigma), _c(I), _stream_ptr(stream)))
+
+
+def propagators(nb, L, dt, h, U, V, W, lam, stream=None):
+    m = mesh(nb, L)
+    _check(load().kbe_op_propagators(ctypes.byref(m), float(dt), _c(h), _c(U), _c(V), _c(W), _c(lam),
+                                     _stream_ptr(stream)))
+
+
+def update_row(nb, L, n, dt, theta, U, V, W, lam, Gprev, Iprev, Icur, out, stream=None):
+    m = mesh(nb, L)
+    _check(load().kbe_op_update_row(ctypes.byref(m), int(n), float(dt), float(theta), _c(U), _c(V),
+                                    _c(W), _c(lam), _c(Gprev), _c(Iprev),
+                                    None if Icur is None else _c(Icur), _c(out), _stream_ptr(stream)))

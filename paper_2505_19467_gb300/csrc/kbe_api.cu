@@ -1,0 +1,599 @@
+// C ABI of libkbe: handle life cycle, the Algorithm 1 step schedule on the
+// device-resident history, and the stateless per-row operations.
+//
+// One step n (P(EC)^n_corr E, Algorithm 1 of the paper):
+//   predictor : h from the extrapolated density, props, update with I_{n-1}
+//   corrector : density of the current row -> h, props; Sigma row (a1);
+//               collision row (a2); update with (I_{n-1} + I_n)/2 (a4)
+//   final     : Sigma row + collision row -> I_n (kept for step n+1),
+//               local density, observables (a5)
+// Everything is enqueued on the handle's stream; nothing returns to the host
+// inside a step.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "kbe_internal.cuh"
+
+using kbe::Mesh;
+using kbe::tri;
+
+struct kbe_handle {
+  kbe_config cfg{};
+  Mesh mesh{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  size_t blk = 0;   // complex numbers in one (component) block: nb*nb*nk
+  int nb2 = 0;
+
+  // host copies of the inputs
+  int nhop = 0;
+  std::vector<int> hopR;
+  std::vector<double> hopT;
+  std::vector<double> Useq{0.0};
+  std::vector<double> v;
+  std::vector<double> A;
+  double dir[2] = {1.0, 0.0};
+
+  // device arena
+  double2 *H = nullptr;        // history triangle
+  double2 *Ip = nullptr;       // I row n-1
+  double2 *Ic = nullptr;       // I row n
+  double2 *Sig = nullptr;      // Sigma row
+  double2 *work = nullptr;     // Sigma scratch
+  double2 *U = nullptr, *V = nullptr, *W = nullptr;
+  double *lam = nullptr;
+  double2 *rho = nullptr;      // [(nt_max+2)][nb][nb]; slot nt_max+1 = current estimate
+  double *obs = nullptr;       // [(nt_max+1)][6]
+  double *nkb = nullptr;       // [(nt_max+1)][nk][nb]
+  int *status = nullptr;
+  int *d_hopR = nullptr;
+  double2 *d_hopT = nullptr;
+  double *d_U = nullptr;       // U(t_l) samples, nt_max+1
+  size_t bytes = 0;
+
+  int n = -1;                  // last completed row
+  bool ham_set = false;
+  kbe_status sticky = KBE_OK;
+  std::string err;
+
+  // profiling
+  bool prof = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  std::vector<double> ev_flops, ev_bytes;
+  size_t ev_used = 0;
+  kbe_profile_stats stats{};
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+kbe_status fail(kbe_handle *h, kbe_status s, const std::string &msg) {
+  if (h) h->err = msg;
+  else g_create_err = msg;
+  return s;
+}
+
+kbe_status cuda_fail(kbe_handle *h, cudaError_t e, const char *where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  if (h) h->sticky = KBE_ERR_CUDA;
+  return fail(h, KBE_ERR_CUDA, m);
+}
+
+bool nb_ok(int nb) { return kbe::sweep_supported(nb); }
+
+double U_at(const kbe_handle *h, int i) {
+  return h->Useq.size() == 1 ? h->Useq[0] : h->Useq[(size_t)i];
+}
+
+double A_at(const kbe_handle *h, int i) {
+  if (h->A.empty()) return 0.0;
+  if (i < 0) i = 0;
+  if (i >= (int)h->A.size()) i = (int)h->A.size() - 1;
+  return h->A[(size_t)i];
+}
+
+kbe::HopTable hop_table(const kbe_handle *h) {
+  kbe::HopTable t;
+  t.nhop = h->nhop;
+  t.R = h->d_hopR;
+  t.T = h->d_hopT;
+  t.d0 = h->dir[0];
+  t.d1 = h->cfg.dim == 2 ? h->dir[1] : 0.0;
+  return t;
+}
+
+template <typename T>
+cudaError_t dalloc(kbe_handle *h, T **p, size_t count) {
+  size_t b = sizeof(T) * (count ? count : 1);
+  cudaError_t e = cudaMalloc((void **)p, b);
+  if (e == cudaSuccess) h->bytes += b;
+  return e;
+}
+
+void free_all(kbe_handle *h) {
+  void *ptrs[] = {h->H, h->Ip, h->Ic, h->Sig, h->work, h->U, h->V, h->W, h->lam, h->rho,
+                  h->obs, h->nkb, h->status, h->d_hopR, h->d_hopT, h->d_U};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  for (auto &pr : h->ev) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  h->ev.clear();
+}
+
+// collision sweep flops / bytes of one launch at row n (algorithmic counts)
+double sweep_flops(const kbe_handle *h, int n) {
+  const double nb3 = (double)h->cfg.nb * h->cfg.nb * h->cfg.nb;
+  const double cm = 2.0 * (n + 1.0) * (n + 1.0) + (double)n * (n + 3.0);
+  return 8.0 * cm * nb3 * h->mesh.nk;
+}
+double sweep_bytes(const kbe_handle *h, int n) {
+  const double blkb = 2.0 * (double)h->blk * 16.0;
+  const double tri_blocks = (n + 1.0) * (n + 2.0) / 2.0;
+  return blkb * (tri_blocks + 2.0 * (n + 1.0));
+}
+
+kbe_status evaluate_row(kbe_handle *h, int n) {
+  const Mesh &m = h->mesh;
+  double2 *Hrow = h->H + tri(n, 0) * 2 * h->blk;
+  const double *Ul = h->Useq.size() == 1 ? nullptr : h->d_U;
+  cudaError_t e = kbe::sigma_row(m, h->v.data(), n, U_at(h, n), Ul, Hrow, h->Sig, h->work, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "sigma_row");
+  const bool timed = h->prof;
+  if (timed) {
+    if (h->ev_used == h->ev.size()) {
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      h->ev.push_back({a, b});
+      h->ev_flops.push_back(0);
+      h->ev_bytes.push_back(0);
+    }
+    cudaEventRecord(h->ev[h->ev_used].first, h->stream);
+  }
+  e = kbe::launch_sweep(m, n, h->cfg.dt, h->cfg.precision, h->H, h->Sig, h->Ic, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "collision sweep");
+  if (timed) {
+    cudaEventRecord(h->ev[h->ev_used].second, h->stream);
+    h->ev_flops[h->ev_used] = sweep_flops(h, n);
+    h->ev_bytes[h->ev_used] = sweep_bytes(h, n);
+    h->ev_used++;
+    h->stats.launches += 4;
+  }
+  return KBE_OK;
+}
+
+kbe_status build_props(kbe_handle *h, int n, const double2 *ra, const double2 *rb, double ca, double cb) {
+  kbe::PropParams p{};
+  p.A = A_at(h, n - 1);
+  p.rho_a = ra;
+  p.rho_b = rb;
+  p.ca = ca;
+  p.cb = cb;
+  p.Umid = 0.5 * (U_at(h, n - 1) + U_at(h, n));
+  p.hf = h->cfg.hf;
+  p.paper_shift = h->cfg.paper_shift;
+  for (int i = 0; i < h->nb2; ++i) p.v[i] = h->v[(size_t)i];
+  cudaError_t e = kbe::launch_build_props(h->mesh, hop_table(h), p, h->cfg.dt, h->U, h->V, h->W,
+                                          h->lam, h->status, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "build_props");
+  if (h->prof) h->stats.launches += 1;
+  return KBE_OK;
+}
+
+kbe_status update(kbe_handle *h, int n, double theta) {
+  double2 *prev = h->H + tri(n - 1, 0) * 2 * h->blk;
+  double2 *row = h->H + tri(n, 0) * 2 * h->blk;
+  cudaError_t e = kbe::launch_update_row(h->mesh, n, h->cfg.dt, theta, h->U, h->V, h->W, h->lam,
+                                         prev, h->Ip, h->Ic, row, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "update_row");
+  if (h->prof) h->stats.launches += 2;
+  return KBE_OK;
+}
+
+kbe_status density(kbe_handle *h, int n, double2 *out) {
+  cudaError_t e = kbe::launch_local_density(h->mesh, h->H + tri(n, n) * 2 * h->blk, out, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "local_density");
+  if (h->prof) h->stats.launches += 1;
+  return KBE_OK;
+}
+
+kbe_status observables(kbe_handle *h, int n, const double2 *Irow) {
+  kbe::ObsParams p{};
+  p.Abar = 0.5 * (A_at(h, n - 1) + A_at(h, n));
+  p.Un = U_at(h, n);
+  p.hf = h->cfg.hf;
+  p.paper_shift = h->cfg.paper_shift;
+  for (int i = 0; i < h->nb2; ++i) p.v[i] = h->v[(size_t)i];
+  cudaError_t e = kbe::launch_observables(h->mesh, hop_table(h), p, h->H + tri(n, n) * 2 * h->blk,
+                                          Irow + (size_t)n * 2 * h->blk, h->rho + (size_t)n * h->nb2,
+                                          h->obs + (size_t)n * 6, h->nkb + (size_t)n * h->mesh.nk * h->cfg.nb,
+                                          h->status, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "observables");
+  if (h->prof) h->stats.launches += 1;
+  return KBE_OK;
+}
+
+kbe_status one_step(kbe_handle *h) {
+  const int n = h->n + 1;
+  const int nb2 = h->nb2;
+  double2 *r1 = h->rho + (size_t)(n - 1) * nb2;
+  double2 *r2 = h->rho + (size_t)(n >= 2 ? n - 2 : 0) * nb2;
+  double2 *rcur = h->rho + (size_t)(h->cfg.nt_max + 1) * nb2;
+  kbe_status s;
+  // predictor: density extrapolated to the midpoint, Ibar = I_{n-1}
+  if ((s = build_props(h, n, r1, r2, n >= 2 ? 1.5 : 1.0, n >= 2 ? -0.5 : 0.0)) != KBE_OK) return s;
+  if ((s = update(h, n, 0.0)) != KBE_OK) return s;
+  for (int c = 0; c < h->cfg.n_corr; ++c) {
+    if ((s = density(h, n, rcur)) != KBE_OK) return s;
+    if ((s = build_props(h, n, r1, rcur, 0.5, 0.5)) != KBE_OK) return s;
+    if ((s = evaluate_row(h, n)) != KBE_OK) return s;
+    if ((s = update(h, n, 0.5)) != KBE_OK) return s;
+  }
+  if ((s = evaluate_row(h, n)) != KBE_OK) return s;
+  if ((s = density(h, n, h->rho + (size_t)n * nb2)) != KBE_OK) return s;
+  if ((s = observables(h, n, h->Ic)) != KBE_OK) return s;
+  std::swap(h->Ip, h->Ic);
+  h->n = n;
+  return KBE_OK;
+}
+
+kbe_status check_device_status(kbe_handle *h) {
+  int st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "synchronize");
+  if (st & kbe::kDevNonFinite) {
+    h->sticky = KBE_ERR_NONFINITE;
+    return fail(h, KBE_ERR_NONFINITE, "non-finite value in the propagated state");
+  }
+  if (st & kbe::kDevEigNoConv) {
+    h->sticky = KBE_ERR_NONFINITE;
+    return fail(h, KBE_ERR_NONFINITE, "eigen-solver did not converge (non-finite or huge h)");
+  }
+  return h->sticky;
+}
+
+bool mesh_ok(const kbe_mesh *m) {
+  return m && nb_ok(m->nb) && m->L[0] >= 1 && m->L[1] >= 1 &&
+         (long)m->L[0] * m->L[1] <= kbe::kMaxNk;
+}
+
+Mesh to_mesh(const kbe_mesh *m) { return Mesh{m->nb, m->L[0], m->L[1], m->L[0] * m->L[1]}; }
+
+}  // namespace
+
+extern "C" {
+
+kbe_status kbe_create(const kbe_config *cfg, void *stream, kbe_handle **out) {
+  if (!cfg || !out) return fail(nullptr, KBE_ERR_ARG, "kbe_create: null argument");
+  *out = nullptr;
+  if (!nb_ok(cfg->nb)) return fail(nullptr, KBE_ERR_UNSUPPORTED, "kbe_create: nb not in {1,2,3,4,6,8,12,16}");
+  if (cfg->dim != 1 && cfg->dim != 2) return fail(nullptr, KBE_ERR_ARG, "kbe_create: dim must be 1 or 2");
+  if (cfg->L[0] < 1 || cfg->L[1] < 1 || (cfg->dim == 1 && cfg->L[1] != 1))
+    return fail(nullptr, KBE_ERR_ARG, "kbe_create: bad mesh extents");
+  if ((long)cfg->L[0] * cfg->L[1] > kbe::kMaxNk) return fail(nullptr, KBE_ERR_ARG, "kbe_create: n_k > 4096");
+  if (cfg->nt_max < 1 || cfg->nt_max > 65535) return fail(nullptr, KBE_ERR_ARG, "kbe_create: nt_max out of range");
+  if (!(cfg->dt > 0.0) || !std::isfinite(cfg->dt)) return fail(nullptr, KBE_ERR_ARG, "kbe_create: dt must be > 0");
+  if (!std::isfinite(cfg->beta) || !std::isfinite(cfg->mu)) return fail(nullptr, KBE_ERR_ARG, "kbe_create: beta/mu not finite");
+  if (cfg->precision != KBE_PREC_FP64) return fail(nullptr, KBE_ERR_UNSUPPORTED, "kbe_create: unknown precision");
+  if (cfg->n_corr < 0 || cfg->n_corr > 64) return fail(nullptr, KBE_ERR_ARG, "kbe_create: n_corr out of range");
+
+  kbe_handle *h = new kbe_handle();
+  h->cfg = *cfg;
+  h->mesh = Mesh{cfg->nb, cfg->L[0], cfg->L[1], cfg->L[0] * cfg->L[1]};
+  h->stream = (cudaStream_t)stream;
+  h->nb2 = cfg->nb * cfg->nb;
+  h->blk = (size_t)h->nb2 * h->mesh.nk;
+  h->v.assign((size_t)h->nb2, 0.0);
+  for (int a = 0; a < cfg->nb; ++a)
+    for (int b = 0; b < cfg->nb; ++b) h->v[(size_t)a * cfg->nb + b] = a == b ? 0.0 : 1.0;
+  cudaGetDevice(&h->device);
+
+  const size_t T = (size_t)cfg->nt_max;
+  const size_t ntri = tri((int)T, (int)T) + 1;
+  const size_t row = (T + 1) * 2 * h->blk;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = dalloc(h, &h->H, ntri * 2 * h->blk);
+  if (e == cudaSuccess) e = dalloc(h, &h->Ip, row);
+  if (e == cudaSuccess) e = dalloc(h, &h->Ic, row);
+  if (e == cudaSuccess) e = dalloc(h, &h->Sig, row);
+  if (e == cudaSuccess) e = dalloc(h, &h->work, kbe::sigma_workspace_bytes(h->mesh, (int)T) / sizeof(double2));
+  if (e == cudaSuccess) e = dalloc(h, &h->U, h->blk);
+  if (e == cudaSuccess) e = dalloc(h, &h->V, h->blk);
+  if (e == cudaSuccess) e = dalloc(h, &h->W, h->blk);
+  if (e == cudaSuccess) e = dalloc(h, &h->lam, (size_t)cfg->nb * h->mesh.nk);
+  if (e == cudaSuccess) e = dalloc(h, &h->rho, (T + 2) * h->nb2);
+  if (e == cudaSuccess) e = dalloc(h, &h->obs, (T + 1) * 6);
+  if (e == cudaSuccess) e = dalloc(h, &h->nkb, (T + 1) * h->mesh.nk * cfg->nb);
+  if (e == cudaSuccess) e = dalloc(h, &h->status, 1);
+  if (e == cudaSuccess) e = dalloc(h, &h->d_U, T + 1);
+  if (e != cudaSuccess) {
+    std::string msg = std::string("kbe_create: device allocation failed (") + cudaGetErrorString(e) + ")";
+    cudaGetLastError();
+    free_all(h);
+    delete h;
+    return fail(nullptr, e == cudaErrorMemoryAllocation ? KBE_ERR_OOM : KBE_ERR_CUDA, msg);
+  }
+  cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
+  cudaMemsetAsync(h->rho, 0, sizeof(double2) * (T + 2) * h->nb2, h->stream);
+  *out = h;
+  return KBE_OK;
+}
+
+kbe_status kbe_destroy(kbe_handle *h) {
+  if (!h) return KBE_ERR_ARG;
+  cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+  return KBE_OK;
+}
+
+kbe_status kbe_set_hamiltonian(kbe_handle *h, int nhop, const int *R, const double *t) {
+  if (!h) return KBE_ERR_ARG;
+  if (nhop < 1 || nhop > 4096 || !R || !t) return fail(h, KBE_ERR_ARG, "set_hamiltonian: bad arguments");
+  for (size_t i = 0; i < (size_t)nhop * h->nb2 * 2; ++i)
+    if (!std::isfinite(t[i])) return fail(h, KBE_ERR_NONFINITE, "set_hamiltonian: non-finite hopping");
+  h->hopR.assign(R, R + 2 * (size_t)nhop);
+  if (h->cfg.dim == 1)
+    for (int r = 0; r < nhop; ++r) h->hopR[2 * (size_t)r + 1] = 0;
+  h->hopT.assign(t, t + (size_t)nhop * h->nb2 * 2);
+  cudaStreamSynchronize(h->stream);
+  if (h->d_hopR) cudaFree(h->d_hopR);
+  if (h->d_hopT) cudaFree(h->d_hopT);
+  h->d_hopR = nullptr;
+  h->d_hopT = nullptr;
+  cudaError_t e = cudaMalloc((void **)&h->d_hopR, sizeof(int) * 2 * nhop);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_hopT, sizeof(double2) * (size_t)nhop * h->nb2);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_hamiltonian alloc");
+  e = cudaMemcpyAsync(h->d_hopR, h->hopR.data(), sizeof(int) * 2 * nhop, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->d_hopT, h->hopT.data(), sizeof(double2) * (size_t)nhop * h->nb2,
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_hamiltonian copy");
+  cudaStreamSynchronize(h->stream);
+  h->nhop = nhop;
+  h->ham_set = true;
+  return KBE_OK;
+}
+
+kbe_status kbe_set_interaction(kbe_handle *h, int len, const double *U, const double *v) {
+  if (!h) return KBE_ERR_ARG;
+  if (!U || (len != 1 && len < h->cfg.nt_max + 1))
+    return fail(h, KBE_ERR_ARG, "set_interaction: need 1 or nt_max+1 samples of U");
+  for (int i = 0; i < len; ++i)
+    if (!std::isfinite(U[i])) return fail(h, KBE_ERR_NONFINITE, "set_interaction: non-finite U");
+  if (v) {
+    for (int i = 0; i < h->nb2; ++i)
+      if (!std::isfinite(v[i])) return fail(h, KBE_ERR_NONFINITE, "set_interaction: non-finite v");
+    h->v.assign(v, v + h->nb2);
+  }
+  h->Useq.assign(U, U + (len == 1 ? 1 : h->cfg.nt_max + 1));
+  std::vector<double> full((size_t)h->cfg.nt_max + 1);
+  for (int i = 0; i <= h->cfg.nt_max; ++i) full[(size_t)i] = U_at(h, i);
+  cudaError_t e = cudaMemcpyAsync(h->d_U, full.data(), sizeof(double) * full.size(),
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_interaction copy");
+  return KBE_OK;
+}
+
+kbe_status kbe_set_drive(kbe_handle *h, int len, const double *A, const double *dir) {
+  if (!h) return KBE_ERR_ARG;
+  if (len < 0) return fail(h, KBE_ERR_ARG, "set_drive: negative length");
+  if (A && len > 0) {
+    for (int i = 0; i < len; ++i)
+      if (!std::isfinite(A[i])) return fail(h, KBE_ERR_NONFINITE, "set_drive: non-finite A");
+    h->A.assign(A, A + len);
+  } else {
+    h->A.clear();
+  }
+  if (dir) {
+    if (!std::isfinite(dir[0]) || (h->cfg.dim == 2 && !std::isfinite(dir[1])))
+      return fail(h, KBE_ERR_NONFINITE, "set_drive: non-finite direction");
+    h->dir[0] = dir[0];
+    h->dir[1] = h->cfg.dim == 2 ? dir[1] : 0.0;
+  }
+  return KBE_OK;
+}
+
+kbe_status kbe_reset(kbe_handle *h) {
+  if (!h) return KBE_ERR_ARG;
+  if (!h->ham_set) return fail(h, KBE_ERR_STATE, "reset: set_hamiltonian first");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "reset sync");
+  h->sticky = KBE_OK;
+  cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
+  cudaMemsetAsync(h->Ip, 0, sizeof(double2) * 2 * h->blk, h->stream);
+  cudaMemsetAsync(h->Ic, 0, sizeof(double2) * 2 * h->blk, h->stream);
+  e = kbe::launch_init_state(h->mesh, hop_table(h), h->cfg.beta, h->cfg.mu, h->H, h->status, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "init_state");
+  if (h->prof) h->stats.launches += 1;
+  h->n = 0;
+  kbe_status s = density(h, 0, h->rho);
+  if (s != KBE_OK) return s;
+  s = observables(h, 0, h->Ip);
+  if (s != KBE_OK) return s;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "reset");
+  return KBE_OK;
+}
+
+kbe_status kbe_step(kbe_handle *h, int nsteps) {
+  if (!h) return KBE_ERR_ARG;
+  if (h->sticky != KBE_OK) return fail(h, h->sticky, "step: handle has a sticky error; reset it");
+  if (h->n < 0) return fail(h, KBE_ERR_STATE, "step: call kbe_reset first");
+  if (nsteps < 0) return fail(h, KBE_ERR_ARG, "step: negative count");
+  if (h->n + nsteps > h->cfg.nt_max) return fail(h, KBE_ERR_STATE, "step: past nt_max");
+  for (int i = 0; i < nsteps; ++i) {
+    kbe_status s = one_step(h);
+    if (s != KBE_OK) return s;
+  }
+  return KBE_OK;
+}
+
+kbe_status kbe_synchronize(kbe_handle *h) {
+  if (!h) return KBE_ERR_ARG;
+  return check_device_status(h);
+}
+
+kbe_status kbe_current_step(const kbe_handle *h, int *n) {
+  if (!h || !n) return KBE_ERR_ARG;
+  *n = h->n;
+  return KBE_OK;
+}
+
+kbe_status kbe_observables(kbe_handle *h, int step, double *n_kb, double *scalars) {
+  if (!h) return KBE_ERR_ARG;
+  if (step < 0 || step > h->n) return fail(h, KBE_ERR_ARG, "observables: step out of range");
+  kbe_status s = check_device_status(h);
+  if (s != KBE_OK) return s;
+  cudaError_t e = cudaSuccess;
+  if (n_kb)
+    e = cudaMemcpy(n_kb, h->nkb + (size_t)step * h->mesh.nk * h->cfg.nb,
+                   sizeof(double) * h->mesh.nk * h->cfg.nb, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && scalars)
+    e = cudaMemcpy(scalars, h->obs + (size_t)step * 6, sizeof(double) * 6, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "observables copy");
+  return KBE_OK;
+}
+
+kbe_status kbe_observables_all(kbe_handle *h, double *n_kb, double *scalars) {
+  if (!h) return KBE_ERR_ARG;
+  if (h->n < 0) return fail(h, KBE_ERR_STATE, "observables_all: call kbe_reset first");
+  kbe_status s = check_device_status(h);
+  if (s != KBE_OK) return s;
+  const size_t rows = (size_t)h->n + 1;
+  cudaError_t e = cudaSuccess;
+  if (n_kb)
+    e = cudaMemcpyAsync(n_kb, h->nkb, sizeof(double) * rows * h->mesh.nk * h->cfg.nb,
+                        cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && scalars)
+    e = cudaMemcpyAsync(scalars, h->obs, sizeof(double) * rows * 6, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "observables_all copy");
+  return KBE_OK;
+}
+
+kbe_status kbe_get_row(kbe_handle *h, int i, int which, double *out) {
+  if (!h || !out) return KBE_ERR_ARG;
+  if (i < 0 || i > h->n || (which != 0 && which != 1)) return fail(h, KBE_ERR_ARG, "get_row: bad row or component");
+  kbe_status s = check_device_status(h);
+  if (s != KBE_OK && s != KBE_ERR_NONFINITE) return s;
+  const size_t nblk = (size_t)i + 1;
+  std::vector<double2> tmp(nblk * 2 * h->blk);
+  cudaError_t e = cudaMemcpyAsync(tmp.data(), h->H + tri(i, 0) * 2 * h->blk, sizeof(double2) * tmp.size(),
+                                  cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_row copy");
+  const int nb = h->cfg.nb, nk = h->mesh.nk;
+  double2 *o = (double2 *)out;
+  for (size_t j = 0; j < nblk; ++j) {
+    const double2 *src = tmp.data() + (j * 2 + which) * h->blk;
+    for (int k = 0; k < nk; ++k)
+      for (int a = 0; a < nb; ++a)
+        for (int b = 0; b < nb; ++b)
+          o[((j * nk + k) * nb + a) * nb + b] = src[((size_t)a * nb + b) * nk + k];
+  }
+  return KBE_OK;
+}
+
+kbe_status kbe_profile_enable(kbe_handle *h, int enable) {
+  if (!h) return KBE_ERR_ARG;
+  cudaStreamSynchronize(h->stream);
+  h->prof = enable != 0;
+  h->ev_used = 0;
+  h->stats = kbe_profile_stats{};
+  return KBE_OK;
+}
+
+kbe_status kbe_profile_read(kbe_handle *h, kbe_profile_stats *out) {
+  if (!h || !out) return KBE_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "profile sync");
+  kbe_profile_stats s = h->stats;
+  s.sweep_launches = 0;
+  s.sweep_ms = s.sweep_flops = s.sweep_bytes = 0.0;
+  for (size_t i = 0; i < h->ev_used; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev[i].first, h->ev[i].second) == cudaSuccess) {
+      s.sweep_ms += ms;
+      s.sweep_flops += h->ev_flops[i];
+      s.sweep_bytes += h->ev_bytes[i];
+      s.sweep_launches++;
+    }
+  }
+  *out = s;
+  return KBE_OK;
+}
+
+const char *kbe_last_error(const kbe_handle *h) {
+  return h ? h->err.c_str() : g_create_err.c_str();
+}
+
+// ---- stateless operations ------------------------------------------------
+
+size_t kbe_op_sigma_row_workspace(const kbe_mesh *m, int n) {
+  if (!mesh_ok(m) || n < 0) return 0;
+  return kbe::sigma_workspace_bytes(to_mesh(m), n);
+}
+
+kbe_status kbe_op_sigma_row(const kbe_mesh *m, const double *v, int n, double Un,
+                            const double *Ul_dev, const void *Grow_dev, void *Sigma_dev,
+                            void *work_dev, size_t work_bytes, void *stream) {
+  if (!mesh_ok(m) || !v || n < 0 || !Grow_dev || !Sigma_dev || !work_dev)
+    return fail(nullptr, KBE_ERR_ARG, "op_sigma_row: bad arguments");
+  const Mesh mm = to_mesh(m);
+  if (work_bytes < kbe::sigma_workspace_bytes(mm, n))
+    return fail(nullptr, KBE_ERR_ARG, "op_sigma_row: workspace too small");
+  cudaError_t e = kbe::sigma_row(mm, v, n, Un, Ul_dev, (const double2 *)Grow_dev, (double2 *)Sigma_dev,
+                                 (double2 *)work_dev, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(nullptr, KBE_ERR_CUDA, std::string("op_sigma_row: ") + cudaGetErrorString(e));
+  return KBE_OK;
+}
+
+kbe_status kbe_op_collision_row(const kbe_mesh *m, int n, double dt, int precision,
+                                const void *H_dev, const void *Sigma_dev, void *I_dev, void *stream) {
+  if (!mesh_ok(m) || n < 0 || !H_dev || !Sigma_dev || !I_dev || !(dt > 0.0))
+    return fail(nullptr, KBE_ERR_ARG, "op_collision_row: bad arguments");
+  if (precision != KBE_PREC_FP64) return fail(nullptr, KBE_ERR_UNSUPPORTED, "op_collision_row: precision");
+  cudaError_t e = kbe::launch_sweep(to_mesh(m), n, dt, precision, (const double2 *)H_dev,
+                                    (const double2 *)Sigma_dev, (double2 *)I_dev, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(nullptr, KBE_ERR_CUDA, std::string("op_collision_row: ") + cudaGetErrorString(e));
+  return KBE_OK;
+}
+
+kbe_status kbe_op_propagators(const kbe_mesh *m, double dt, const void *h_dev, void *U_dev,
+                              void *V_dev, void *W_dev, double *lam_dev, void *stream) {
+  if (!mesh_ok(m) || !h_dev || !U_dev || !V_dev || !W_dev || !lam_dev || !(dt > 0.0))
+    return fail(nullptr, KBE_ERR_ARG, "op_propagators: bad arguments");
+  cudaError_t e = kbe::launch_props_from_h(to_mesh(m), dt, (const double2 *)h_dev, (double2 *)U_dev,
+                                           (double2 *)V_dev, (double2 *)W_dev, lam_dev, nullptr,
+                                           (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(nullptr, KBE_ERR_CUDA, std::string("op_propagators: ") + cudaGetErrorString(e));
+  return KBE_OK;
+}
+
+kbe_status kbe_op_update_row(const kbe_mesh *m, int n, double dt, double theta, const void *U_dev,
+                             const void *V_dev, const void *W_dev, const double *lam_dev,
+                             const void *Gprev_dev, const void *Iprev_dev, const void *Icur_dev,
+                             void *out_dev, void *stream) {
+  if (!mesh_ok(m) || n < 1 || !U_dev || !V_dev || !W_dev || !lam_dev || !Gprev_dev || !Iprev_dev ||
+      !out_dev || !(dt > 0.0) || (theta != 0.0 && !Icur_dev))
+    return fail(nullptr, KBE_ERR_ARG, "op_update_row: bad arguments");
+  cudaError_t e = kbe::launch_update_row(to_mesh(m), n, dt, theta, (const double2 *)U_dev,
+                                         (const double2 *)V_dev, (const double2 *)W_dev, lam_dev,
+                                         (const double2 *)Gprev_dev, (const double2 *)Iprev_dev,
+                                         (const double2 *)Icur_dev, (double2 *)out_dev,
+                                         (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(nullptr, KBE_ERR_CUDA, std::string("op_update_row: ") + cudaGetErrorString(e));
+  return KBE_OK;
+}
+
+}  // extern "C"

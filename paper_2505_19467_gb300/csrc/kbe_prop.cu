@@ -1,0 +1,512 @@
+// (a3) mean-field Hamiltonian and step propagators, (a4) row / diagonal
+// update, (a5) equal-time observables, and the t = 0 state.
+//
+// All of these are O(n_k N_b^3) or O(n n_k N_b^3) per call, small next to the
+// collision sweep; they run in FP64 with one thread per k (eigen-problems,
+// time diagonal) or per output element (row update).
+//
+// Time stepping (Algorithm 1, "solve Eq. 5"): with h fixed over the step and
+// the collision term replaced by a constant average Ibar, the row equation
+// i dG(t, t_j)/dt = h G + Ibar has the exact one-step solution
+//   G(n, j) = U G(n-1, j) + V Ibar(j),  U = e^{-i dt h},  V = (U - 1) h^{-1},
+// and the time diagonal i dG(t,t)/dt = [h, G] + Sbar, Sbar = Ibar + Ibar^+,
+//   G(n, n) = U G(n-1, n-1) U^+ - i W [(W^+ Sbar W) o D] W^+,
+//   D_ab = (1 - e^{-i (lam_a - lam_b) dt}) / (i (lam_a - lam_b)),
+// with h = W diag(lam) W^+. D_aa = dt keeps Tr G(t,t) exact.
+#include "kbe_internal.cuh"
+
+namespace kbe {
+
+namespace {
+
+// Hermitian eigen-decomposition A = W diag(lam) W^+ by cyclic complex Jacobi
+// rotations (phase of A_pq removed, then the real rotation with the smaller
+// root t of t^2 + 2 tau t - 1 = 0, tau = (A_qq - A_pp) / 2|A_pq|).
+// A is overwritten. Returns false if 60 sweeps did not converge.
+template <int NB>
+__device__ bool herm_eig(double2 *A, double *lam, double2 *W) {
+#pragma unroll 1
+  for (int i = 0; i < NB * NB; ++i) W[i] = make_double2(0.0, 0.0);
+#pragma unroll 1
+  for (int i = 0; i < NB; ++i) {
+    W[i * NB + i] = make_double2(1.0, 0.0);
+    A[i * NB + i].y = 0.0;
+  }
+  bool conv = false;
+#pragma unroll 1
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+#pragma unroll 1
+    for (int p = 0; p < NB; ++p)
+#pragma unroll 1
+      for (int q = 0; q < NB; ++q) {
+        const double2 z = A[p * NB + q];
+        const double m2 = z.x * z.x + z.y * z.y;
+        tot += m2;
+        if (p != q) off += m2;
+      }
+    if (off == 0.0 || off <= 1e-34 * tot) {
+      conv = true;
+      break;
+    }
+#pragma unroll 1
+    for (int p = 0; p < NB - 1; ++p)
+#pragma unroll 1
+      for (int q = p + 1; q < NB; ++q) {
+        const double2 apq = A[p * NB + q];
+        const double r = hypot(apq.x, apq.y);
+        if (r == 0.0) continue;
+        const double2 e = make_double2(apq.x / r, apq.y / r);   // e^{i phi}
+        const double2 ec = c_conj(e);
+        const double tau = (A[q * NB + q].x - A[p * NB + p].x) / (2.0 * r);
+        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+#pragma unroll 1
+        for (int i = 0; i < NB; ++i) {   // A <- A J ; W <- W J
+          const double2 x = A[i * NB + p], y = A[i * NB + q];
+          A[i * NB + p] = c_sub(c_scale(c, x), c_scale(s, c_mul(ec, y)));
+          A[i * NB + q] = c_add(c_scale(s, x), c_scale(c, c_mul(ec, y)));
+          const double2 wx = W[i * NB + p], wy = W[i * NB + q];
+          W[i * NB + p] = c_sub(c_scale(c, wx), c_scale(s, c_mul(ec, wy)));
+          W[i * NB + q] = c_add(c_scale(s, wx), c_scale(c, c_mul(ec, wy)));
+        }
+#pragma unroll 1
+        for (int jj = 0; jj < NB; ++jj) {   // A <- J^+ A
+          const double2 x = A[p * NB + jj], y = A[q * NB + jj];
+          A[p * NB + jj] = c_sub(c_scale(c, x), c_scale(s, c_mul(e, y)));
+          A[q * NB + jj] = c_add(c_scale(s, x), c_scale(c, c_mul(e, y)));
+        }
+        A[p * NB + q] = make_double2(0.0, 0.0);
+        A[q * NB + p] = make_double2(0.0, 0.0);
+        A[p * NB + p].y = 0.0;
+        A[q * NB + q].y = 0.0;
+      }
+  }
+#pragma unroll 1
+  for (int i = 0; i < NB; ++i) lam[i] = A[i * NB + i].x;
+  return conv;
+}
+
+// h0_ab(k - A d) = sum_r t_ab(R_r) exp(i (k - A d).R_r)
+template <int NB>
+__device__ void bare_h(const HopTable &hop, int k, int L0, int L1, double A, double2 *h) {
+  const int k0 = k / L1, k1 = k - (k / L1) * L1;
+#pragma unroll 1
+  for (int i = 0; i < NB * NB; ++i) h[i] = make_double2(0.0, 0.0);
+#pragma unroll 1
+  for (int r = 0; r < hop.nhop; ++r) {
+    const int R0 = hop.R[2 * r], R1 = hop.R[2 * r + 1];
+    // reduce the lattice phase exactly before converting to an angle
+    const int m0 = ((k0 * R0) % L0 + L0) % L0, m1 = ((k1 * R1) % L1 + L1) % L1;
+    const double th = 2.0 * M_PI * ((double)m0 / L0 + (double)m1 / L1) - A * (hop.d0 * R0 + hop.d1 * R1);
+    double s, c;
+    sincos(th, &s, &c);
+    const double2 ph = make_double2(c, s);
+    const double2 *T = hop.T + (size_t)r * NB * NB;
+#pragma unroll 1
+    for (int i = 0; i < NB * NB; ++i) h[i] = c_fma(T[i], ph, h[i]);
+  }
+}
+
+// (e^{-i x} - 1) / x * dt for x = lam dt, written without cancellation
+__device__ __forceinline__ double2 phi_row(double lam, double dt) {
+  const double x = lam * dt;
+  if (x == 0.0) return make_double2(0.0, -dt);
+  const double s2 = sin(0.5 * x);
+  return make_double2(dt * (-2.0 * s2 * s2 / x), -dt * sin(x) / x);
+}
+
+// (1 - e^{-i y}) / (i y) * dt for y = (lam_a - lam_b) dt
+__device__ __forceinline__ double2 phi_diag(double dl, double dt) {
+  const double y = dl * dt;
+  if (y == 0.0) return make_double2(dt, 0.0);
+  const double s2 = sin(0.5 * y);
+  return make_double2(dt * sin(y) / y, -dt * 2.0 * s2 * s2 / y);
+}
+
+// U, V from (W, lam) for one k, stored [a][b][k]
+template <int NB>
+__device__ void store_props(const double2 *W, const double *lam, double dt, int k, int nk,
+                            double2 *U, double2 *V, double2 *Wout, double *lamout) {
+  double2 eu[NB], ev[NB];
+#pragma unroll 1
+  for (int c = 0; c < NB; ++c) {
+    double s, co;
+    sincos(-lam[c] * dt, &s, &co);
+    eu[c] = make_double2(co, s);
+    ev[c] = phi_row(lam[c], dt);
+  }
+#pragma unroll 1
+  for (int a = 0; a < NB; ++a)
+#pragma unroll 1
+    for (int b = 0; b < NB; ++b) {
+      double2 su = make_double2(0, 0), sv = make_double2(0, 0);
+#pragma unroll 1
+      for (int c = 0; c < NB; ++c) {
+        const double2 wc = c_mulc(W[a * NB + c], W[b * NB + c]);
+        su = c_fma(wc, eu[c], su);
+        sv = c_fma(wc, ev[c], sv);
+      }
+      const size_t o = (size_t)(a * NB + b) * nk + k;
+      U[o] = su;
+      V[o] = sv;
+      Wout[o] = W[a * NB + b];
+    }
+#pragma unroll 1
+  for (int a = 0; a < NB; ++a) lamout[(size_t)a * nk + k] = lam[a];
+}
+
+struct VMatP {
+  double v[kMaxNb * kMaxNb];
+};
+
+template <int NB>
+__global__ void build_props_kernel(Mesh m, HopTable hop, PropParams p, double dt, double2 *U,
+                                   double2 *V, double2 *W, double *lam, int *status) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m.nk) return;
+  double2 h[NB * NB], Wl[NB * NB];
+  double ll[NB];
+  bare_h<NB>(hop, k, m.L0, m.L1, p.A, h);
+  if (p.hf) {
+    // mean field S_jm = U (delta_jm sum_a v_ja rho_aa - v_jm rho_jm)
+#pragma unroll 1
+    for (int jj = 0; jj < NB; ++jj)
+#pragma unroll 1
+      for (int mm = 0; mm < NB; ++mm) {
+        const int e = jj * NB + mm;
+        const double2 r = c_add(c_scale(p.ca, p.rho_a[e]), c_scale(p.cb, p.rho_b[e]));
+        double2 x = c_scale(-p.v[e], r);
+        if (jj == mm)
+#pragma unroll 1
+          for (int a = 0; a < NB; ++a) {
+            const int ea = a * NB + a;
+            const double2 ra = c_add(c_scale(p.ca, p.rho_a[ea]), c_scale(p.cb, p.rho_b[ea]));
+            x = c_add(x, c_scale(p.v[jj * NB + a], ra));
+          }
+        h[e] = c_add(h[e], c_scale(p.Umid, x));
+      }
+  }
+  if (p.paper_shift) h[(NB - 1) * NB + NB - 1].x -= p.Umid;
+  if (!herm_eig<NB>(h, ll, Wl)) atomicOr(status, kDevEigNoConv);
+  store_props<NB>(Wl, ll, dt, k, m.nk, U, V, W, lam);
+}
+
+template <int NB>
+__global__ void props_from_h_kernel(Mesh m, double dt, const double2 *hin, double2 *U, double2 *V,
+                                    double2 *W, double *lam, int *status) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m.nk) return;
+  double2 h[NB * NB], Wl[NB * NB];
+  double ll[NB];
+#pragma unroll 1
+  for (int e = 0; e < NB * NB; ++e) h[e] = hin[(size_t)e * m.nk + k];
+  if (!herm_eig<NB>(h, ll, Wl)) {
+    if (status) atomicOr(status, kDevEigNoConv);
+  }
+  store_props<NB>(Wl, ll, dt, k, m.nk, U, V, W, lam);
+}
+
+// t = 0: G^<(k;0,0) = i W f(lam) W^+ of h0(k), G^> = G^< - i
+template <int NB>
+__global__ void init_state_kernel(Mesh m, HopTable hop, double beta, double mu, double2 *H00,
+                                  int *status) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m.nk) return;
+  double2 h[NB * NB], Wl[NB * NB];
+  double ll[NB], f[NB];
+  bare_h<NB>(hop, k, m.L0, m.L1, 0.0, h);
+  if (!herm_eig<NB>(h, ll, Wl)) atomicOr(status, kDevEigNoConv);
+#pragma unroll 1
+  for (int c = 0; c < NB; ++c) {
+    const double x = beta * (ll[c] - mu);
+    if (x > 0) {
+      const double y = exp(-x);
+      f[c] = y / (1.0 + y);
+    } else {
+      f[c] = 1.0 / (1.0 + exp(x));
+    }
+  }
+  const size_t blk = (size_t)NB * NB * m.nk;
+#pragma unroll 1
+  for (int a = 0; a < NB; ++a)
+#pragma unroll 1
+    for (int b = 0; b < NB; ++b) {
+      double2 r = make_double2(0, 0);
+#pragma unroll 1
+      for (int c = 0; c < NB; ++c) r = c_add(r, c_scale(f[c], c_mulc(Wl[a * NB + c], Wl[b * NB + c])));
+      const double2 gl = c_i(r);
+      const size_t o = (size_t)(a * NB + b) * m.nk + k;
+      H00[o] = gl;
+      H00[blk + o] = (a == b) ? make_double2(gl.x, gl.y - 1.0) : gl;
+    }
+}
+
+// rho_loc_ab = (1/n_k) sum_k (-i) G^<_ab(k; n, n); one CTA, a warp per element
+__global__ void local_density_kernel(int nb, int nk, const double2 *__restrict__ G, double2 *out) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  for (int e = warp; e < nb * nb; e += nw) {
+    double sr = 0.0, si = 0.0;
+    for (int k = lane; k < nk; k += 32) {
+      const double2 g = G[(size_t)e * nk + k];
+      sr += g.y;    // Re(-i g) = Im g
+      si -= g.x;    // Im(-i g) = -Re g
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, off);
+      si += __shfl_xor_sync(0xffffffffu, si, off);
+    }
+    if (lane == 0) out[e] = make_double2(sr / nk, si / nk);
+  }
+}
+
+// rows j < n: G^x(n,j) = U G^x(n-1,j) + V [(1-theta) Ip^x(j) + theta Ic^x(j)]
+template <int NB>
+__global__ void update_rows_kernel(int n, int nk, double theta, const double2 *__restrict__ U,
+                                   const double2 *__restrict__ V, const double2 *__restrict__ Gprev,
+                                   const double2 *__restrict__ Ip, const double2 *__restrict__ Ic,
+                                   double2 *__restrict__ out) {
+  const size_t blk = (size_t)NB * NB * nk;
+  const size_t total = (size_t)n * 2 * blk;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int k = (int)(idx % nk);
+  size_t t = idx / nk;
+  const int b = (int)(t % NB);
+  t /= NB;
+  const int a = (int)(t % NB);
+  t /= NB;   // t = j * 2 + x
+  const size_t base = t * blk;
+  double2 acc = make_double2(0, 0);
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    const size_t oc = (size_t)(c * NB + b) * nk + k;
+    const size_t ou = (size_t)(a * NB + c) * nk + k;
+    double2 ib = c_scale(1.0 - theta, Ip[base + oc]);
+    if (theta != 0.0) ib = c_fma(make_double2(theta, 0.0), Ic[base + oc], ib);
+    acc = c_fma(U[ou], Gprev[base + oc], acc);
+    acc = c_fma(V[ou], ib, acc);
+  }
+  out[base + (size_t)(a * NB + b) * nk + k] = acc;
+}
+
+// time diagonal of row n, one thread per k
+template <int NB>
+__global__ void update_diag_kernel(int n, int nk, double dt, double theta,
+                                   const double2 *__restrict__ U, const double2 *__restrict__ W,
+                                   const double *__restrict__ lam, const double2 *__restrict__ Gprev,
+                                   const double2 *__restrict__ Ip, const double2 *__restrict__ Ic,
+                                   double2 *__restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nk) return;
+  const size_t blk = (size_t)NB * NB * nk;
+  const double2 *ipd = Ip + (size_t)(n - 1) * 2 * blk;   // I^<_{n-1}(n-1)
+  const double2 *icd = Ic + (size_t)n * 2 * blk;         // I^<_n(n)
+  const double2 *gd = Gprev + (size_t)(n - 1) * 2 * blk; // G^<(n-1, n-1)
+  double2 S[NB * NB], T[NB * NB], Wk[NB * NB];
+  double l[NB];
+#pragma unroll 1
+  for (int a = 0; a < NB; ++a) l[a] = lam[(size_t)a * nk + k];
+#pragma unroll 1
+  for (int e = 0; e < NB * NB; ++e) Wk[e] = W[(size_t)e * nk + k];
+#pragma unroll 1
+  for (int a = 0; a < NB; ++a)
+#pragma unroll 1
+    for (int b = 0; b < NB; ++b) {
+      const size_t oab = (size_t)(a * NB + b) * nk + k, oba = (size_t)(b * NB + a) * nk + k;
+      double2 s = c_scale(1.0 - theta, c_add(ipd[oab], c_conj(ipd[oba])));
+      if (theta != 0.0) s = c_add(s, c_scale(theta, c_add(icd[oab], c_conj(icd[oba]))));
+      S[a * NB + b] = s;
+    }
+  // T = W^+ S W, then T o D
+#pragma unroll 1
+  for (int a = 0; a < NB; ++a)
+#pragma unroll 1
+    for (int b = 0; b < NB; ++b) {
+      double2 acc = make_double2(0, 0);
+#pragma unroll 1
+      for (int c = 0; c < NB; ++c) {
+        double2 sw = make_double2(0, 0);
+#pragma unroll 1
+        for (int d = 0; d < NB; ++d) sw = c_fma(S[c * NB + d], Wk[d * NB + b], sw);
+        acc = c_fma(c_conj(Wk[c * NB + a]), sw, acc);
+      }
+      T[a * NB + b] = c_mul(acc, phi_diag(l[a] - l[b], dt));
+    }
+  // S <- W T W^+  (reuse S)
+#pragma unroll 1
+  for (int a = 0; a < NB; ++a)
+#pragma unroll 1
+    for (int b = 0; b < NB; ++b) {
+      double2 acc = make_double2(0, 0);
+#pragma unroll 1
+      for (int c = 0; c < NB; ++c) {
+        double2 tw = make_double2(0, 0);
+#pragma unroll 1
+        for (int d = 0; d < NB; ++d) tw = c_add(tw, c_mulc(T[c * NB + d], Wk[b * NB + d]));
+        acc = c_fma(Wk[a * NB + c], tw, acc);
+      }
+      S[a * NB + b] = acc;
+    }
+  // T <- U G U^+
+#pragma unroll 1
+  for (int a = 0; a < NB; ++a)
+#pragma unroll 1
+    for (int b = 0; b < NB; ++b) {
+      double2 acc = make_double2(0, 0);
+#pragma unroll 1
+      for (int c = 0; c < NB; ++c) {
+        double2 gu = make_double2(0, 0);
+#pragma unroll 1
+        for (int d = 0; d < NB; ++d)
+          gu = c_add(gu, c_mulc(gd[(size_t)(c * NB + d) * nk + k], U[(size_t)(b * NB + d) * nk + k]));
+        acc = c_fma(U[(size_t)(a * NB + c) * nk + k], gu, acc);
+      }
+      T[a * NB + b] = acc;
+    }
+  double2 *ol = out + (size_t)n * 2 * blk;
+#pragma unroll 1
+  for (int a = 0; a < NB; ++a)
+#pragma unroll 1
+    for (int b = 0; b < NB; ++b) {
+      const double2 g = c_sub(T[a * NB + b], c_i(S[a * NB + b]));
+      const size_t o = (size_t)(a * NB + b) * nk + k;
+      ol[o] = g;
+      ol[blk + o] = (a == b) ? make_double2(g.x, g.y - 1.0) : g;
+    }
+}
+
+// equal-time observables of row n; one CTA
+template <int NB>
+__global__ void observables_kernel(Mesh m, HopTable hop, ObsParams p, const double2 *__restrict__ G,
+                                   const double2 *__restrict__ Idg, const double2 *__restrict__ rho,
+                                   double *obs, double *nkb, int *status) {
+  __shared__ double red[3][32];
+  double sN = 0.0, sK = 0.0, sC = 0.0;
+  double2 h[NB * NB];
+  for (int k = threadIdx.x; k < m.nk; k += blockDim.x) {
+    bare_h<NB>(hop, k, m.L0, m.L1, p.Abar, h);
+#pragma unroll 1
+    for (int a = 0; a < NB; ++a) {
+      const double naa = G[(size_t)(a * NB + a) * m.nk + k].y;   // Re(-i G_aa)
+      nkb[(size_t)k * NB + a] = naa;
+      sN += naa;
+      sC += Idg[(size_t)(a * NB + a) * m.nk + k].y;               // Re(-i I_aa)
+#pragma unroll 1
+      for (int b = 0; b < NB; ++b) {
+        const double2 g = G[(size_t)(b * NB + a) * m.nk + k];    // rho_ba = -i G_ba
+        const double2 r = make_double2(g.y, -g.x);
+        sK += c_mul(h[a * NB + b], r).x;
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    sN += __shfl_xor_sync(0xffffffffu, sN, off);
+    sK += __shfl_xor_sync(0xffffffffu, sK, off);
+    sC += __shfl_xor_sync(0xffffffffu, sC, off);
+  }
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (lane == 0) {
+    red[0][warp] = sN;
+    red[1][warp] = sK;
+    red[2][warp] = sC;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double N = 0, K = 0, C = 0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
+      N += red[0][w];
+      K += red[1][w];
+      C += red[2][w];
+    }
+    double Ehf = 0.0, Esh = 0.0;
+    if (p.hf) {
+      for (int jj = 0; jj < NB; ++jj)
+        for (int mm = 0; mm < NB; ++mm) {
+          double2 x = c_scale(-p.v[jj * NB + mm], rho[jj * NB + mm]);
+          if (jj == mm)
+            for (int a = 0; a < NB; ++a) x = c_add(x, c_scale(p.v[jj * NB + a], rho[a * NB + a]));
+          Ehf += 0.5 * c_mul(c_scale(p.Un, x), rho[mm * NB + jj]).x;
+        }
+    }
+    if (p.paper_shift) Esh = -p.Un * rho[(NB - 1) * NB + NB - 1].x;
+    obs[0] = N / m.nk;
+    obs[1] = K / m.nk;
+    obs[2] = Ehf;
+    obs[3] = 0.5 * C / m.nk;
+    obs[4] = Esh;
+    obs[5] = obs[1] + obs[2] + obs[3] + obs[4];
+    if (!isfinite(obs[0]) || !isfinite(obs[5])) atomicOr(status, kDevNonFinite);
+  }
+}
+
+#define KBE_NB_SWITCH(nb, CALL)          \
+  switch (nb) {                          \
+    case 1: { constexpr int NB = 1; CALL; } break;   \
+    case 2: { constexpr int NB = 2; CALL; } break;   \
+    case 3: { constexpr int NB = 3; CALL; } break;   \
+    case 4: { constexpr int NB = 4; CALL; } break;   \
+    case 6: { constexpr int NB = 6; CALL; } break;   \
+    case 8: { constexpr int NB = 8; CALL; } break;   \
+    case 12: { constexpr int NB = 12; CALL; } break; \
+    case 16: { constexpr int NB = 16; CALL; } break; \
+    default: return cudaErrorInvalidValue;           \
+  }
+
+}  // namespace
+
+cudaError_t launch_init_state(const Mesh &m, const HopTable &hop, double beta, double mu,
+                              double2 *H00, int *status, cudaStream_t st) {
+  const int threads = 64, blocks = (m.nk + threads - 1) / threads;
+  KBE_NB_SWITCH(m.nb, (init_state_kernel<NB><<<blocks, threads, 0, st>>>(m, hop, beta, mu, H00, status)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_local_density(const Mesh &m, const double2 *Gdiag, double2 *rho_out,
+                                 cudaStream_t st) {
+  local_density_kernel<<<1, 256, 0, st>>>(m.nb, m.nk, Gdiag, rho_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_props(const Mesh &m, const HopTable &hop, const PropParams &p, double dt,
+                               double2 *U, double2 *V, double2 *W, double *lam, int *status,
+                               cudaStream_t st) {
+  const int threads = 64, blocks = (m.nk + threads - 1) / threads;
+  KBE_NB_SWITCH(m.nb, (build_props_kernel<NB><<<blocks, threads, 0, st>>>(m, hop, p, dt, U, V, W, lam, status)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_props_from_h(const Mesh &m, double dt, const double2 *h, double2 *U, double2 *V,
+                                double2 *W, double *lam, int *status, cudaStream_t st) {
+  const int threads = 64, blocks = (m.nk + threads - 1) / threads;
+  KBE_NB_SWITCH(m.nb, (props_from_h_kernel<NB><<<blocks, threads, 0, st>>>(m, dt, h, U, V, W, lam, status)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_row(const Mesh &m, int n, double dt, double theta, const double2 *U,
+                              const double2 *V, const double2 *W, const double *lam,
+                              const double2 *Gprev, const double2 *Iprev, const double2 *Icur,
+                              double2 *out, cudaStream_t st) {
+  const size_t blk = (size_t)m.nb * m.nb * m.nk;
+  const size_t total = (size_t)n * 2 * blk;
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((total + threads - 1) / threads);
+  const double2 *ic = (theta != 0.0) ? Icur : Iprev;
+  KBE_NB_SWITCH(m.nb, (update_rows_kernel<NB><<<blocks, threads, 0, st>>>(n, m.nk, theta, U, V, Gprev, Iprev, ic, out)));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int tdiag = 64, bdiag = (m.nk + tdiag - 1) / tdiag;
+  KBE_NB_SWITCH(m.nb, (update_diag_kernel<NB><<<bdiag, tdiag, 0, st>>>(n, m.nk, dt, theta, U, W, lam, Gprev, Iprev, ic, out)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_observables(const Mesh &m, const HopTable &hop, const ObsParams &p,
+                               const double2 *Gdiag, const double2 *Idiag, const double2 *rho_n,
+                               double *obs_out, double *nkb_out, int *status, cudaStream_t st) {
+  KBE_NB_SWITCH(m.nb, (observables_kernel<NB><<<1, 256, 0, st>>>(m, hop, p, Gdiag, Idiag, rho_n, obs_out, nkb_out, status)));
+  return cudaGetLastError();
+}
+
+}  // namespace kbe

@@ -140,7 +140,8 @@ kbe_status kbe_get_row(kbe_handle *h, int i, int which, double *out);
 kbe_status kbe_profile_enable(kbe_handle *h, int enable);
 kbe_status kbe_profile_read(kbe_handle *h, kbe_profile_stats *out);
 
-/* Message of the last error of this handle (or of the last failed create). */
+/* Message of the last error of this handle; with NULL, of the last failed
+ * create or handle-free operation (kbe_op_*) on the calling thread. */
 const char *kbe_last_error(const kbe_handle *h);
 
 /* ---------------------------------------------------------------------- */
@@ -201,6 +202,35 @@ kbe_status kbe_op_update_row(const kbe_mesh *m, int n, double dt, double theta,
                              const double *lam_dev, const void *Gprev_dev,
                              const void *Iprev_dev, const void *Icur_dev, void *out_dev,
                              void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* self-energy row without any allocation                                   */
+/* ---------------------------------------------------------------------- */
+
+/* Size of the device array that kbe_op_sigma_row_noalloc uses as scratch. */
+#define KBE_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+
+/* Same operation, arguments, layouts and result as kbe_op_sigma_row, minus
+ * the workspace arguments; the paper has no counterpart (it is a service for
+ * callers that cannot allocate device memory: hosts whose device memory is
+ * all owned by their own allocator, loops where cudaMalloc/cudaFree would
+ * synchronise the device, plug-ins with a fixed memory budget).
+ * Scratch: one file-scope device array of KBE_NOALLOC_SCRATCH_BYTES inside
+ * libkbe, resident on every GPU that loads the library until the process
+ * exits. The call allocates and frees nothing.
+ * Limit: the row must need at most KBE_NOALLOC_SCRATCH_BYTES of scratch
+ * (kbe_op_sigma_row_workspace(m, n) bytes); larger rows are rejected with
+ * KBE_ERR_ARG and a message in kbe_last_error(NULL), before any GPU work.
+ * Set-up: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture begins.
+ * Sharing: all calls use the same array and it keeps the last call's
+ * contents (no call depends on them); calls whose GPU work overlaps, e.g. on
+ * two streams or from two host threads, race on it and must be serialised by
+ * the caller. */
+kbe_status kbe_op_sigma_row_noalloc(const kbe_mesh *m, const double *v, int n, double Un,
+                                    const double *Ul_dev, const void *Grow_dev, void *Sigma_dev,
+                                    void *stream);
 
 #ifdef __cplusplus
 }

@@ -28,7 +28,7 @@ EXPORTS = [
     "kbe_reset", "kbe_step", "kbe_synchronize", "kbe_current_step", "kbe_observables",
     "kbe_observables_all", "kbe_get_row", "kbe_profile_enable", "kbe_profile_read",
     "kbe_last_error", "kbe_op_sigma_row_workspace", "kbe_op_sigma_row", "kbe_op_collision_row",
-    "kbe_op_propagators", "kbe_op_update_row",
+    "kbe_op_propagators", "kbe_op_update_row", "kbe_op_sigma_row_noalloc",
 ]
 
 
@@ -90,6 +90,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "kbe_op_collision_row": (I, [pmesh, I, D, I, P, P, P, P]),
         "kbe_op_propagators": (I, [pmesh, D, P, P, P, P, P, P]),
         "kbe_op_update_row": (I, [pmesh, I, D, D, P, P, P, P, P, P, P, P, P]),
+        "kbe_op_sigma_row_noalloc": (I, [pmesh, P, I, D, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -267,3 +268,17 @@ def update_row(nb, L, n, dt, theta, U, V, W, lam, Gprev, Iprev, Icur, out, strea
     _check(load().kbe_op_update_row(ctypes.byref(m), int(n), float(dt), float(theta), _c(U), _c(V),
                                     _c(W), _c(lam), _c(Gprev), _c(Iprev),
                                     None if Icur is None else _c(Icur), _c(out), _stream_ptr(stream)))
+
+
+def sigma_row_noalloc(nb, L, v, n, Un, Grow, Sigma, Ul=None, stream=None):
+    """Sigma row with the library's built-in scratch (no device allocation);
+    for callers that cannot allocate. Rows needing more than
+    KBE_NOALLOC_SCRATCH_BYTES of scratch raise KBEError (KBE_ERR_ARG)."""
+    m = mesh(nb, L)
+    v = np.ascontiguousarray(v, np.float64)
+    _check(load().kbe_op_sigma_row_noalloc(ctypes.byref(m), _np_ptr(v), int(n), float(Un),
+                                           None if Ul is None else _c(Ul), _c(Grow), _c(Sigma),
+                                           _stream_ptr(stream)))
+
+
+NOALLOC_SCRATCH_BYTES = 64 << 20   # KBE_NOALLOC_SCRATCH_BYTES in include/kbe.h

@@ -269,6 +269,8 @@ Mesh to_mesh(const kbe_mesh *m) { return Mesh{m->nb, m->L[0], m->L[1], m->L[0] *
 
 }  // namespace
 
+void kbe::set_last_error(const std::string &msg) { g_create_err = msg; }
+
 extern "C" {
 
 kbe_status kbe_create(const kbe_config *cfg, void *stream, kbe_handle **out) {

@@ -12,6 +12,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "kbe.h"
 
 namespace kbe {
@@ -117,5 +119,8 @@ struct ObsParams {
 cudaError_t launch_observables(const Mesh &m, const HopTable &hop, const ObsParams &p,
                                const double2 *Gdiag, const double2 *Idiag, const double2 *rho_n,
                                double *obs_out, double *nkb_out, int *status, cudaStream_t st);
+
+// message returned by kbe_last_error(NULL) on this thread
+void set_last_error(const std::string &msg);
 
 }  // namespace kbe

@@ -33,9 +33,22 @@ import kbe_inputs as ki  # noqa: E402
 METRIC = "KBE time-steps/s"
 WORKLOAD = ("c2: N_b=4, 8x8 mesh (n_k=64), N_t=512, dt=0.02, U=1.0, beta=20, "
             "Peierls pulse A0=0.3, HF + second Born, P(EC)^2E")
-# FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s);
-# a DFMA probe on this GB300 pool measured 1.195 TFLOP/s.
-FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+# Roofline denominators of the sweep (the dominant kernel), per arithmetic form,
+# from unit counts and the 2.07 GHz maximum SM clock (GB300, 152 SMs):
+#  fp64: FP64 pipe, 2 DFMA/clk/SM (nominal 1.25 TFLOP/s; a probe measured 1.195)
+#  df64: FP32 issue, 128 lanes/clk/SM, 6 FP32 instructions per double-float
+#        flop (a complex multiply-add is 4 products x 12 instructions = 8 flop)
+#  c64 : FP32 FMA, 128 lanes x 2 flop/clk/SM (a probe measured 73.2 TFLOP/s)
+PEAKS = {
+    "fp64": (152 * 2 * 2 * 2.07, "GFLOP/s FP64",
+             "FP64 pipe: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)"),
+    "df64": (152 * 128 * 2.07 / 6, "GFLOP/s FP64-equivalent (double-float)",
+             "FP32 issue: 152 SM x 128 lanes x 2.07 GHz / 6 FP32 instructions per double-float flop"),
+    "c64": (152 * 128 * 2 * 2.07, "GFLOP/s FP32",
+            "FP32 FMA: 152 SM x 128 lanes x 2 flop x 2.07 GHz"),
+}
+DTYPES = {"fp64": "f64", "df64": "df64 (f32 hi/lo pairs; everything but the sweep f64)",
+          "c64": "c64/f32 history + sweep (everything else f64)"}
 ORACLE_PREFIX = 40
 
 
@@ -46,6 +59,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--nt", type=int, default=None, help="truncate N_t (testing only)")
+    p.add_argument("--precision", default="df64", choices=["fp64", "df64", "c64"],
+                   help="history storage / sweep arithmetic (df64 and fp64 meet the FP64 bar)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -120,7 +135,7 @@ def run_ours(args, rank, world, local):
     s = ki.config("c2", nt=args.nt)
     nt = s.nt
     stream = torch.cuda.Stream()
-    g = kbe.KBE.from_system(s, stream=stream)
+    g = kbe.KBE.from_system(s, stream=stream, precision=kbe.PRECISIONS[args.precision])
 
     def trajectory():
         g.reset()
@@ -191,19 +206,19 @@ def run_ours(args, rank, world, local):
     if rank == 0:
         sweep_s = prof["sweep_ms"] / 1e3
         achieved = prof["sweep_flops"] / sweep_s / 1e9 if sweep_s > 0 else 0.0
+        peak, punit, psrc = PEAKS[args.precision]
         line = {
             "metric": METRIC, "value": value, "unit": "time-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax * 1e3 / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded c2 system, kbe_inputs)",
-            "config": {"workload": WORKLOAD, "bench_step": f"one trajectory: reset + {nt} time steps",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPES[args.precision], "data": "synthetic (seeded c2 system, kbe_inputs)",
+            "config": {"workload": WORKLOAD, "precision": args.precision, "bench_step": f"one trajectory: reset + {nt} time steps",
                        "time_steps_per_bench_step": nt, "n_corr": 2,
                        "l2": "history 4.3 GB > 129 MB L2 (inputs larger than L2)",
                        "parallelism": f"replicas x{world} (independent systems)"},
             "roofline": {"kernel": "collision sweep (a2)", "bound": "alu", "achieved": achieved,
-                         "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s FP64",
-                         "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
-                         "peak_source": "FP64 pipe: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                         "peak": peak, "unit": punit, "frac": achieved / peak, "traffic": None,
+                         "peak_source": psrc,
                          "launches": prof["sweep_launches"], "sweep_share_of_step":
                              sweep_s / t_dev if t_dev > 0 else None,
                          "hbm_gbs_achieved": prof["sweep_bytes"] / sweep_s / 1e9 if sweep_s > 0 else 0.0},

@@ -54,9 +54,20 @@ typedef enum {
   KBE_ERR_INTERNAL = -8
 } kbe_status;
 
-/* Arithmetic of the collision-integral sweep (the dominant kernel). */
+/* Storage of the two-time history and arithmetic of the collision-integral
+ * sweep (the dominant kernel). Everything else (self-energy, propagators,
+ * the update of the newest rows, the time diagonal, observables) is FP64 in
+ * every mode; the two newest rows are always kept in FP64.
+ *   FP64: history complex128, sweep in FP64 (DFMA).
+ *   DF64: history as pairs of FP32 (hi, lo) per real part (the same 8 bytes;
+ *         48-bit significand), sweep in double-float arithmetic on the FP32
+ *         pipe: exact products (FMA) and error-free sums, FP64-level result.
+ *   C64:  history complex64 (half the bytes), sweep in FP32 with a
+ *         compensated (error-free) sum over the memory time. */
 enum {
-  KBE_PREC_FP64 = 0 /* native FP64 everywhere                                  */
+  KBE_PREC_FP64 = 0,
+  KBE_PREC_DF64 = 1,
+  KBE_PREC_C64 = 2
 };
 
 typedef struct kbe_config {
@@ -171,16 +182,27 @@ kbe_status kbe_op_sigma_row(const kbe_mesh *m, const double *v, int n, double Un
                             const double *Ul_dev, const void *Grow_dev, void *Sigma_dev,
                             void *work_dev, size_t work_bytes, void *stream);
 
+/* Pack count complex128 values (device) into the history storage of a
+ * precision (device): FP64 copies, DF64 writes float4 {re_hi, re_lo, im_hi,
+ * im_lo} with hi = fl32(x), lo = fl32(x - hi), C64 writes float2. */
+kbe_status kbe_op_pack(int precision, const void *src_dev, void *dst_dev, size_t count,
+                       void *stream);
+
 /* (a2) Collision-integral row, Eq. 6 in left form:
  *   I^x(n, j) = sum_{l=0}^{n} w^(n)_l [S^>(n,l) - S^<(n,l)] G^x(l, j)
  *             + sum_{l=0}^{j} w^(j)_l S^x(n,l) [G^<(l,j) - G^>(l,j)],
  * j = 0..n, with trapezoid weights w^(m)_l = dt (1 - [l=0]/2 - [l=m]/2)
  * (zero for m = 0) and G(l, j) = -G(j, l)^+ above the diagonal.
  * H_dev: history triangle with rows 0..n; Sigma_dev: n+1 blocks; I_dev:
- * n+1 blocks written. precision: KBE_PREC_*. */
+ * n+1 blocks written (complex128). precision: KBE_PREC_*; H_dev holds the
+ * triangle in that precision's storage (kbe_op_pack), Sigma_dev and I_dev
+ * are complex128. work_dev: device scratch of
+ * kbe_op_collision_row_workspace(m, n, precision) bytes (0 for FP64; may
+ * then be NULL). */
+size_t kbe_op_collision_row_workspace(const kbe_mesh *m, int n, int precision);
 kbe_status kbe_op_collision_row(const kbe_mesh *m, int n, double dt, int precision,
                                 const void *H_dev, const void *Sigma_dev, void *I_dev,
-                                void *stream);
+                                void *work_dev, size_t work_bytes, void *stream);
 
 /* (a3) Step propagators of a Hermitian h(k) (device [nb][nb][nk] c128):
  * h = W diag(lam) W^+, U = e^{-i dt h}, V = (U - 1) h^{-1} (-i dt on the

@@ -16,6 +16,9 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libkbe.so")
 
 KBE_PREC_FP64 = 0
+KBE_PREC_DF64 = 1
+KBE_PREC_C64 = 2
+PRECISIONS = {"fp64": KBE_PREC_FP64, "df64": KBE_PREC_DF64, "c64": KBE_PREC_C64}
 
 STATUS = {
     0: "KBE_OK", -1: "KBE_ERR_ARG", -2: "KBE_ERR_OOM", -3: "KBE_ERR_CUDA", -4: "KBE_ERR_STATE",
@@ -29,6 +32,7 @@ EXPORTS = [
     "kbe_observables_all", "kbe_get_row", "kbe_profile_enable", "kbe_profile_read",
     "kbe_last_error", "kbe_op_sigma_row_workspace", "kbe_op_sigma_row", "kbe_op_collision_row",
     "kbe_op_propagators", "kbe_op_update_row", "kbe_op_sigma_row_noalloc",
+    "kbe_op_collision_row_workspace", "kbe_op_pack",
 ]
 
 
@@ -87,7 +91,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "kbe_last_error": (ctypes.c_char_p, [P]),
         "kbe_op_sigma_row_workspace": (S, [pmesh, I]),
         "kbe_op_sigma_row": (I, [pmesh, P, I, D, P, P, P, P, S, P]),
-        "kbe_op_collision_row": (I, [pmesh, I, D, I, P, P, P, P]),
+        "kbe_op_collision_row": (I, [pmesh, I, D, I, P, P, P, P, S, P]),
+        "kbe_op_collision_row_workspace": (S, [pmesh, I, I]),
+        "kbe_op_pack": (I, [I, P, P, S, P]),
         "kbe_op_propagators": (I, [pmesh, D, P, P, P, P, P, P]),
         "kbe_op_update_row": (I, [pmesh, I, D, D, P, P, P, P, P, P, P, P, P]),
         "kbe_op_sigma_row_noalloc": (I, [pmesh, P, I, D, P, P, P, P]),
@@ -251,10 +257,24 @@ def sigma_row_workspace(nb, L, n) -> int:
     return int(load().kbe_op_sigma_row_workspace(ctypes.byref(m), int(n)))
 
 
-def collision_row(nb, L, n, dt, H, Sigma, I, precision=KBE_PREC_FP64, stream=None):
+def collision_row_workspace(nb, L, n, precision=KBE_PREC_FP64) -> int:
     m = mesh(nb, L)
+    return int(load().kbe_op_collision_row_workspace(ctypes.byref(m), int(n), int(precision)))
+
+
+def collision_row(nb, L, n, dt, H, Sigma, I, precision=KBE_PREC_FP64, work=None, stream=None):
+    """H: history triangle in the precision's storage (see pack)."""
+    m = mesh(nb, L)
+    wb = 0 if work is None else work.numel() * work.element_size()
     _check(load().kbe_op_collision_row(ctypes.byref(m), int(n), float(dt), int(precision), _c(H),
-                                       _c(Sigma), _c(I), _stream_ptr(stream)))
+                                       _c(Sigma), _c(I), None if work is None else _c(work), wb,
+                                       _stream_ptr(stream)))
+
+
+def pack(precision, src, dst, stream=None):
+    """complex128 device tensor -> history storage of `precision` (dst bytes:
+    16 per complex for FP64 / DF64, 8 for C64)."""
+    _check(load().kbe_op_pack(int(precision), _c(src), _c(dst), src.numel(), _stream_ptr(stream)))
 
 
 def propagators(nb, L, dt, h, U, V, W, lam, stream=None):

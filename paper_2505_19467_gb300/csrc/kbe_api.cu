@@ -39,7 +39,10 @@ struct kbe_handle {
   double dir[2] = {1.0, 0.0};
 
   // device arena
-  double2 *H = nullptr;        // history triangle
+  void *H = nullptr;           // history triangle in the precision's storage
+  size_t esz = 16;             // bytes per stored complex number
+  double2 *Wrow[2] = {nullptr, nullptr};   // FP64 rows n-1, n (ring; DF64 / C64 only)
+  void *coef = nullptr;        // sweep coefficient rows (DF64 / C64)
   double2 *Ip = nullptr;       // I row n-1
   double2 *Ic = nullptr;       // I row n
   double2 *Sig = nullptr;      // Sigma row
@@ -116,8 +119,8 @@ cudaError_t dalloc(kbe_handle *h, T **p, size_t count) {
 }
 
 void free_all(kbe_handle *h) {
-  void *ptrs[] = {h->H, h->Ip, h->Ic, h->Sig, h->work, h->U, h->V, h->W, h->lam, h->rho,
-                  h->obs, h->nkb, h->status, h->d_hopR, h->d_hopT, h->d_U};
+  void *ptrs[] = {h->H, h->Wrow[0], h->Wrow[1], h->coef, h->Ip, h->Ic, h->Sig, h->work, h->U, h->V,
+                  h->W, h->lam, h->rho, h->obs, h->nkb, h->status, h->d_hopR, h->d_hopT, h->d_U};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (auto &pr : h->ev) {
@@ -134,14 +137,32 @@ double sweep_flops(const kbe_handle *h, int n) {
   return 8.0 * cm * nb3 * h->mesh.nk;
 }
 double sweep_bytes(const kbe_handle *h, int n) {
-  const double blkb = 2.0 * (double)h->blk * 16.0;
+  const double blk2 = 2.0 * (double)h->blk;
   const double tri_blocks = (n + 1.0) * (n + 2.0) / 2.0;
-  return blkb * (tri_blocks + 2.0 * (n + 1.0));
+  // history triangle read once in its storage, Sigma row read, I row written (FP64)
+  return blk2 * (tri_blocks * (double)h->esz + 2.0 * (n + 1.0) * 16.0);
+}
+
+// FP64 copy of row i: the history itself in FP64 mode, else the ring of the
+// two newest rows (valid for i = n-1, n)
+double2 *frow(kbe_handle *h, int i) {
+  if (h->cfg.precision == KBE_PREC_FP64) return (double2 *)h->H + tri(i, 0) * 2 * h->blk;
+  return h->Wrow[i & 1];
+}
+
+// store row i into the history triangle in its storage format
+kbe_status publish(kbe_handle *h, int i) {
+  if (h->cfg.precision == KBE_PREC_FP64) return KBE_OK;
+  char *dst = (char *)h->H + tri(i, 0) * 2 * h->blk * h->esz;
+  cudaError_t e = kbe::launch_pack(h->cfg.precision, frow(h, i), dst, (size_t)(i + 1) * 2 * h->blk, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "publish row");
+  if (h->prof) h->stats.launches += 1;
+  return KBE_OK;
 }
 
 kbe_status evaluate_row(kbe_handle *h, int n) {
   const Mesh &m = h->mesh;
-  double2 *Hrow = h->H + tri(n, 0) * 2 * h->blk;
+  double2 *Hrow = frow(h, n);
   const double *Ul = h->Useq.size() == 1 ? nullptr : h->d_U;
   cudaError_t e = kbe::sigma_row(m, h->v.data(), n, U_at(h, n), Ul, Hrow, h->Sig, h->work, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "sigma_row");
@@ -157,14 +178,14 @@ kbe_status evaluate_row(kbe_handle *h, int n) {
     }
     cudaEventRecord(h->ev[h->ev_used].first, h->stream);
   }
-  e = kbe::launch_sweep(m, n, h->cfg.dt, h->cfg.precision, h->H, h->Sig, h->Ic, h->stream);
+  e = kbe::launch_sweep(m, n, h->cfg.dt, h->cfg.precision, h->H, h->Sig, h->Ic, h->coef, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "collision sweep");
   if (timed) {
     cudaEventRecord(h->ev[h->ev_used].second, h->stream);
     h->ev_flops[h->ev_used] = sweep_flops(h, n);
     h->ev_bytes[h->ev_used] = sweep_bytes(h, n);
     h->ev_used++;
-    h->stats.launches += 4;
+    h->stats.launches += 4 + (h->cfg.precision != KBE_PREC_FP64 ? 1 : 0);
   }
   return KBE_OK;
 }
@@ -188,17 +209,17 @@ kbe_status build_props(kbe_handle *h, int n, const double2 *ra, const double2 *r
 }
 
 kbe_status update(kbe_handle *h, int n, double theta) {
-  double2 *prev = h->H + tri(n - 1, 0) * 2 * h->blk;
-  double2 *row = h->H + tri(n, 0) * 2 * h->blk;
+  double2 *prev = frow(h, n - 1);
+  double2 *row = frow(h, n);
   cudaError_t e = kbe::launch_update_row(h->mesh, n, h->cfg.dt, theta, h->U, h->V, h->W, h->lam,
                                          prev, h->Ip, h->Ic, row, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "update_row");
   if (h->prof) h->stats.launches += 2;
-  return KBE_OK;
+  return publish(h, n);
 }
 
 kbe_status density(kbe_handle *h, int n, double2 *out) {
-  cudaError_t e = kbe::launch_local_density(h->mesh, h->H + tri(n, n) * 2 * h->blk, out, h->stream);
+  cudaError_t e = kbe::launch_local_density(h->mesh, frow(h, n) + (size_t)n * 2 * h->blk, out, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "local_density");
   if (h->prof) h->stats.launches += 1;
   return KBE_OK;
@@ -211,7 +232,7 @@ kbe_status observables(kbe_handle *h, int n, const double2 *Irow) {
   p.hf = h->cfg.hf;
   p.paper_shift = h->cfg.paper_shift;
   for (int i = 0; i < h->nb2; ++i) p.v[i] = h->v[(size_t)i];
-  cudaError_t e = kbe::launch_observables(h->mesh, hop_table(h), p, h->H + tri(n, n) * 2 * h->blk,
+  cudaError_t e = kbe::launch_observables(h->mesh, hop_table(h), p, frow(h, n) + (size_t)n * 2 * h->blk,
                                           Irow + (size_t)n * 2 * h->blk, h->rho + (size_t)n * h->nb2,
                                           h->obs + (size_t)n * 6, h->nkb + (size_t)n * h->mesh.nk * h->cfg.nb,
                                           h->status, h->stream);
@@ -284,7 +305,7 @@ kbe_status kbe_create(const kbe_config *cfg, void *stream, kbe_handle **out) {
   if (cfg->nt_max < 1 || cfg->nt_max > 65535) return fail(nullptr, KBE_ERR_ARG, "kbe_create: nt_max out of range");
   if (!(cfg->dt > 0.0) || !std::isfinite(cfg->dt)) return fail(nullptr, KBE_ERR_ARG, "kbe_create: dt must be > 0");
   if (!std::isfinite(cfg->beta) || !std::isfinite(cfg->mu)) return fail(nullptr, KBE_ERR_ARG, "kbe_create: beta/mu not finite");
-  if (cfg->precision != KBE_PREC_FP64) return fail(nullptr, KBE_ERR_UNSUPPORTED, "kbe_create: unknown precision");
+  if (!kbe::precision_supported(cfg->precision)) return fail(nullptr, KBE_ERR_UNSUPPORTED, "kbe_create: unknown precision");
   if (cfg->n_corr < 0 || cfg->n_corr > 64) return fail(nullptr, KBE_ERR_ARG, "kbe_create: n_corr out of range");
 
   kbe_handle *h = new kbe_handle();
@@ -301,8 +322,14 @@ kbe_status kbe_create(const kbe_config *cfg, void *stream, kbe_handle **out) {
   const size_t T = (size_t)cfg->nt_max;
   const size_t ntri = tri((int)T, (int)T) + 1;
   const size_t row = (T + 1) * 2 * h->blk;
+  h->esz = kbe::history_elem_bytes(cfg->precision);
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = dalloc(h, &h->H, ntri * 2 * h->blk);
+  if (e == cudaSuccess) e = dalloc(h, (char **)&h->H, ntri * 2 * h->blk * h->esz);
+  if (cfg->precision != KBE_PREC_FP64) {
+    if (e == cudaSuccess) e = dalloc(h, &h->Wrow[0], row);
+    if (e == cudaSuccess) e = dalloc(h, &h->Wrow[1], row);
+    if (e == cudaSuccess) e = dalloc(h, (char **)&h->coef, kbe::sweep_workspace_bytes(h->mesh, (int)T, cfg->precision));
+  }
   if (e == cudaSuccess) e = dalloc(h, &h->Ip, row);
   if (e == cudaSuccess) e = dalloc(h, &h->Ic, row);
   if (e == cudaSuccess) e = dalloc(h, &h->Sig, row);
@@ -414,10 +441,12 @@ kbe_status kbe_reset(kbe_handle *h) {
   cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
   cudaMemsetAsync(h->Ip, 0, sizeof(double2) * 2 * h->blk, h->stream);
   cudaMemsetAsync(h->Ic, 0, sizeof(double2) * 2 * h->blk, h->stream);
-  e = kbe::launch_init_state(h->mesh, hop_table(h), h->cfg.beta, h->cfg.mu, h->H, h->status, h->stream);
+  e = kbe::launch_init_state(h->mesh, hop_table(h), h->cfg.beta, h->cfg.mu, frow(h, 0), h->status, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "init_state");
   if (h->prof) h->stats.launches += 1;
   h->n = 0;
+  kbe_status ps = publish(h, 0);
+  if (ps != KBE_OK) return ps;
   kbe_status s = density(h, 0, h->rho);
   if (s != KBE_OK) return s;
   s = observables(h, 0, h->Ip);
@@ -489,10 +518,28 @@ kbe_status kbe_get_row(kbe_handle *h, int i, int which, double *out) {
   kbe_status s = check_device_status(h);
   if (s != KBE_OK && s != KBE_ERR_NONFINITE) return s;
   const size_t nblk = (size_t)i + 1;
-  std::vector<double2> tmp(nblk * 2 * h->blk);
-  cudaError_t e = cudaMemcpyAsync(tmp.data(), h->H + tri(i, 0) * 2 * h->blk, sizeof(double2) * tmp.size(),
-                                  cudaMemcpyDeviceToHost, h->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  const size_t cnt = nblk * 2 * h->blk;
+  std::vector<double2> tmp(cnt);
+  cudaError_t e;
+  if (h->cfg.precision == KBE_PREC_FP64 || i >= h->n - 1) {   // an FP64 copy exists
+    e = cudaMemcpyAsync(tmp.data(), frow(h, i), sizeof(double2) * cnt, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  } else {                                                    // unpack the stored row
+    std::vector<char> raw(cnt * h->esz);
+    e = cudaMemcpyAsync(raw.data(), (char *)h->H + tri(i, 0) * 2 * h->blk * h->esz, raw.size(),
+                        cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) {
+      if (h->cfg.precision == KBE_PREC_DF64) {
+        const float *f = (const float *)raw.data();
+        for (size_t q = 0; q < cnt; ++q)
+          tmp[q] = make_double2((double)f[4 * q] + (double)f[4 * q + 1], (double)f[4 * q + 2] + (double)f[4 * q + 3]);
+      } else {
+        const float *f = (const float *)raw.data();
+        for (size_t q = 0; q < cnt; ++q) tmp[q] = make_double2((double)f[2 * q], (double)f[2 * q + 1]);
+      }
+    }
+  }
   if (e != cudaSuccess) return cuda_fail(h, e, "get_row copy");
   const int nb = h->cfg.nb, nk = h->mesh.nk;
   double2 *o = (double2 *)out;
@@ -560,13 +607,30 @@ kbe_status kbe_op_sigma_row(const kbe_mesh *m, const double *v, int n, double Un
   return KBE_OK;
 }
 
+size_t kbe_op_collision_row_workspace(const kbe_mesh *m, int n, int precision) {
+  if (!mesh_ok(m) || n < 0 || !kbe::precision_supported(precision)) return 0;
+  return kbe::sweep_workspace_bytes(to_mesh(m), n, precision);
+}
+
+kbe_status kbe_op_pack(int precision, const void *src_dev, void *dst_dev, size_t count, void *stream) {
+  if (!kbe::precision_supported(precision) || (count && (!src_dev || !dst_dev)))
+    return fail(nullptr, KBE_ERR_ARG, "op_pack: bad arguments");
+  cudaError_t e = kbe::launch_pack(precision, (const double2 *)src_dev, dst_dev, count, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(nullptr, KBE_ERR_CUDA, std::string("op_pack: ") + cudaGetErrorString(e));
+  return KBE_OK;
+}
+
 kbe_status kbe_op_collision_row(const kbe_mesh *m, int n, double dt, int precision,
-                                const void *H_dev, const void *Sigma_dev, void *I_dev, void *stream) {
+                                const void *H_dev, const void *Sigma_dev, void *I_dev,
+                                void *work_dev, size_t work_bytes, void *stream) {
   if (!mesh_ok(m) || n < 0 || !H_dev || !Sigma_dev || !I_dev || !(dt > 0.0))
     return fail(nullptr, KBE_ERR_ARG, "op_collision_row: bad arguments");
-  if (precision != KBE_PREC_FP64) return fail(nullptr, KBE_ERR_UNSUPPORTED, "op_collision_row: precision");
-  cudaError_t e = kbe::launch_sweep(to_mesh(m), n, dt, precision, (const double2 *)H_dev,
-                                    (const double2 *)Sigma_dev, (double2 *)I_dev, (cudaStream_t)stream);
+  if (!kbe::precision_supported(precision)) return fail(nullptr, KBE_ERR_UNSUPPORTED, "op_collision_row: precision");
+  const size_t need = kbe::sweep_workspace_bytes(to_mesh(m), n, precision);
+  if (need && (!work_dev || work_bytes < need))
+    return fail(nullptr, KBE_ERR_ARG, "op_collision_row: workspace too small");
+  cudaError_t e = kbe::launch_sweep(to_mesh(m), n, dt, precision, H_dev, (const double2 *)Sigma_dev,
+                                    (double2 *)I_dev, work_dev, (cudaStream_t)stream);
   if (e != cudaSuccess) return fail(nullptr, KBE_ERR_CUDA, std::string("op_collision_row: ") + cudaGetErrorString(e));
   return KBE_OK;
 }

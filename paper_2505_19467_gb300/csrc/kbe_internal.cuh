@@ -73,10 +73,16 @@ size_t sigma_workspace_bytes(const Mesh &m, int n);
 cudaError_t sigma_row(const Mesh &m, const double *v_host, int n, double Un, const double *Ul_dev,
                       const double2 *Grow, double2 *Sig, double2 *work, cudaStream_t st);
 
-// a2 collision row
+// a2 collision row. H is the history triangle in the precision's storage
+// (double2 / float4 hi-lo pairs / float2); work holds the coefficient rows
+// for DF64 and C64 (sweep_workspace_bytes).
 bool sweep_supported(int nb);
-cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const double2 *H,
-                         const double2 *Sig, double2 *I, cudaStream_t st);
+bool precision_supported(int prec);
+size_t history_elem_bytes(int prec);
+size_t sweep_workspace_bytes(const Mesh &m, int n, int prec);
+cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t count, cudaStream_t st);
+cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const void *H,
+                         const double2 *Sig, double2 *I, void *work, cudaStream_t st);
 
 // a3 propagators / initial state / density
 struct HopTable {

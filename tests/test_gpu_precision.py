@@ -1,0 +1,102 @@
+"""The two other storage forms of the history against the FP64 oracle.
+
+DF64 (FP32 hi/lo pairs, double-float sweep on the FP32 pipe) must meet the
+FP64 bar: 1e-10 on every stored entry. C64 (complex64 history, FP32 sweep with
+a compensated sum; everything else FP64) must meet the mixed-precision bar:
+1e-5 relative in density and energy.
+"""
+import numpy as np
+import pytest
+
+import kbe_inputs as ki
+import oracle
+from layout import from_dev_blocks, relerr, to_dev_blocks, tri
+
+torch = pytest.importorskip("torch")
+kbe = pytest.importorskip("paper_2505_19467_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def packed(prec, arr):
+    src = dev(arr)
+    nbytes = 8 if prec == kbe.KBE_PREC_C64 else 16
+    dst = torch.empty(src.numel() * nbytes // 4, dtype=torch.float32, device="cuda")
+    kbe.pack(prec, src.reshape(-1), dst)
+    return dst
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-12), (2, 5e-6)])
+@pytest.mark.parametrize("nb,L,n", [(1, (5, 1), 7), (2, (8, 1), 0), (2, (8, 1), 23), (3, (3, 3), 11),
+                                    (4, (8, 8), 17), (6, (3, 1), 6), (8, (2, 3), 5), (16, (1, 3), 2)])
+def test_collision_row_reduced_storage(prec, tol, nb, L, n):
+    rng = np.random.default_rng(700 + nb * 13 + n)
+    nk = L[0] * L[1]
+    dt = 0.03
+    ntri = tri(n, n) + 1
+    Hl = ki.random_blocks(rng, (ntri, nk, nb, nb))
+    Hg = ki.random_blocks(rng, (ntri, nk, nb, nb))
+    Sl = ki.random_blocks(rng, (n + 1, nk, nb, nb))
+    Sg = ki.random_blocks(rng, (n + 1, nk, nb, nb))
+    Il, Ig = oracle.collision_row(nb, nk, n, dt, Hl, Hg, Sl, Sg)
+    H = packed(prec, to_dev_blocks(Hl, Hg))
+    S = dev(to_dev_blocks(Sl, Sg))
+    I = torch.full((n + 1, 2, nb, nb, nk), float("nan"), dtype=torch.complex128, device="cuda")
+    ws = kbe.collision_row_workspace(nb, L, n, prec)
+    work = torch.empty(ws // 4 + 1, dtype=torch.float32, device="cuda")
+    kbe.collision_row(nb, L, n, dt, H, S, I, precision=prec, work=work)
+    torch.cuda.synchronize()
+    gl, gg = from_dev_blocks(I.cpu().numpy())
+    assert relerr(gl, Il)[1] < tol and relerr(gg, Ig)[1] < tol
+
+
+def _trajectory(sys, prec, nsteps):
+    g = kbe.KBE.from_system(sys, precision=prec)
+    g.step(nsteps)
+    g.synchronize()
+    o = oracle.Oracle(sys)
+    o.step(nsteps)
+    return g, o
+
+
+@pytest.mark.parametrize("name,nsteps", [("c1", 64), ("c2", 20)])
+def test_df64_trajectory_every_entry(name, nsteps):
+    s = ki.config(name)
+    g, o = _trajectory(s, kbe.KBE_PREC_DF64, nsteps)
+    for i in range(nsteps + 1):
+        ref = [o.row(i, 0), o.row(i, 1)]
+        scale = max(np.abs(ref[0]).max(), np.abs(ref[1]).max())
+        for x in (0, 1):
+            assert relerr(g.row(i, x), ref[x], scale=scale)[0] < 1e-10, (i, x)
+    nkb, sc = g.observables_all()
+    for n in range(nsteps + 1):
+        assert np.abs(sc[n] - o.observables(n)[1]).max() < 1e-10
+
+
+@pytest.mark.parametrize("nb,L,drive", [(3, (3, 3), 0.5), (6, (2, 3), 0.2), (16, (1, 2), 0.0)])
+def test_df64_small_systems(nb, L, drive):
+    s = ki.small_system(nb, L, 8, 0.05, 0.8, seed=nb * 5, drive_amp=drive)
+    g, o = _trajectory(s, kbe.KBE_PREC_DF64, 8)
+    for i in (1, 4, 7, 8):
+        ref = [o.row(i, 0), o.row(i, 1)]
+        scale = max(np.abs(ref[0]).max(), np.abs(ref[1]).max())
+        for x in (0, 1):
+            assert relerr(g.row(i, x), ref[x], scale=scale)[0] < 1e-10, (i, x)
+
+
+@pytest.mark.parametrize("name,nsteps", [("c1", 64), ("c2", 40)])
+def test_c64_density_and_energy_within_1e5(name, nsteps):
+    s = ki.config(name)
+    g, o = _trajectory(s, kbe.KBE_PREC_C64, nsteps)
+    nkb, sc = g.observables_all()
+    for n in range(nsteps + 1):
+        nkb_o, sc_o = o.observables(n)
+        assert np.abs(nkb[n] - nkb_o).max() <= 1e-5 * np.abs(nkb_o).max(), n
+        # energies: relative to the total energy scale of the system
+        escale = max(abs(sc_o[1]), abs(sc_o[5]))
+        assert np.abs(sc[n][1:] - sc_o[1:]).max() <= 1e-5 * escale, (n, sc[n], sc_o)
+        assert abs(sc[n][0] - sc_o[0]) <= 1e-5 * abs(sc_o[0])

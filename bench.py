@@ -7,8 +7,12 @@ reset to the Fermi state, then 512 time steps on the device-resident history
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-With N > 1 (torchrun, one process per GPU) every rank advances its own
-independent c2 system (weak scaling, no data-path collective).
+The headline value is the plain FP64 path; the reduced-storage forms (DF64:
+FP32 hi/lo pairs with a double-float sweep, C64: complex64 history) are timed
+on the same workload and reported under "forms" with their speedup and their
+error against the FP64 trajectory. With N > 1 (torchrun, one process per GPU)
+every rank advances its own independent c2 system (weak scaling, no
+data-path collective).
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 prefix of the same workload.
 """
@@ -55,12 +59,15 @@ ORACLE_PREFIX = 40
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--steps", type=int, default=2)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--nt", type=int, default=None, help="truncate N_t (testing only)")
-    p.add_argument("--precision", default="df64", choices=["fp64", "df64", "c64"],
-                   help="history storage / sweep arithmetic (df64 and fp64 meet the FP64 bar)")
+    p.add_argument("--precision", default="fp64", choices=["fp64", "df64", "c64"],
+                   help="history storage / sweep arithmetic of the headline value (fp64 meets "
+                        "the 1e-10 bar; df64 / c64 are the reduced-storage forms)")
+    p.add_argument("--forms", default="all", choices=["all", "none"],
+                   help="also time the other storage forms (speedup and error vs the headline)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -123,6 +130,47 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
+def time_trajectories(g, nt, steps, warmup, stream, sampler=None, dist=None):
+    """W untimed + K timed trajectories (reset + nt steps) with the sweep profiled."""
+    import torch
+    for _ in range(warmup):
+        g.reset()
+        g.step(nt)
+    g.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    g.profile(True)
+    if sampler:
+        sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        g.reset()
+        g.step(nt)
+    e1.record(stream)
+    e1.synchronize()
+    g.synchronize()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    prof = g.profile_read()
+    g.profile(False)
+    return e0.elapsed_time(e1) / 1e3, prof, clocks
+
+
+def roofline(prof, precision, t_dev):
+    sweep_s = prof["sweep_ms"] / 1e3
+    achieved = prof["sweep_flops"] / sweep_s / 1e9 if sweep_s > 0 else 0.0
+    peak, punit, psrc = PEAKS[precision]
+    return {"kernel": "collision sweep (a2)", "bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": punit, "frac": achieved / peak, "traffic": None, "peak_source": psrc,
+            "launches": prof["sweep_launches"],
+            "sweep_share_of_step": sweep_s / t_dev if t_dev > 0 else None,
+            "hbm_gbs_achieved": prof["sweep_bytes"] / sweep_s / 1e9 if sweep_s > 0 else 0.0}
+
+
 def run_ours(args, rank, world, local):
     import torch
     import paper_2505_19467_gb300 as kbe
@@ -137,36 +185,9 @@ def run_ours(args, rank, world, local):
     stream = torch.cuda.Stream()
     g = kbe.KBE.from_system(s, stream=stream, precision=kbe.PRECISIONS[args.precision])
 
-    def trajectory():
-        g.reset()
-        g.step(nt)
-
-    for _ in range(args.warmup):
-        trajectory()
-    g.synchronize()
-
-    # ---- device-resident timing, sweep kernel profiled with CUDA events ----
     sampler = ClockSampler(local) if rank == 0 else None
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    g.profile(True)
-    if sampler:
-        sampler.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        trajectory()
-    e1.record(stream)
-    e1.synchronize()
-    g.synchronize()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clocks = sampler.stop() if sampler else None
-    prof = g.profile_read()
-    g.profile(False)
-    t_dev = e0.elapsed_time(e1) / 1e3
+    t_dev, prof, clocks = time_trajectories(g, nt, args.steps, args.warmup, stream, sampler, dist)
+    _, ref_obs = g.observables_all()
 
     # ---- end to end through the C ABI with host buffers -------------------
     R = np.ascontiguousarray(s.hop_R, np.int32)
@@ -191,6 +212,8 @@ def run_ours(args, rank, world, local):
         g.observables_all(nkb_host, sc_host)
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
+    ref_nkb = nkb_host.copy()
+    g.close()
     if dist:
         dist.barrier()
 
@@ -203,34 +226,41 @@ def run_ours(args, rank, world, local):
     value, tmax = aggregate([times[0]], [units * world])
     e2e_value = units * world / times[1]
 
+    # ---- the reduced-storage forms on the same workload (speedup, error) ----
+    forms = {}
+    for form in ([] if args.forms == "none" else [f for f in ("fp64", "df64", "c64") if f != args.precision]):
+        gf = kbe.KBE.from_system(s, stream=stream, precision=kbe.PRECISIONS[form])
+        tf, pf, _ = time_trajectories(gf, nt, args.steps, args.warmup, stream, None, dist)
+        nkb_f, sc_f = gf.observables_all()
+        gf.close()
+        escale = np.abs(ref_obs[:, 5]).max()
+        forms[form] = {"value": units / tf, "speedup_vs_" + args.precision: (units / tf) / (units / t_dev),
+                       "max_abs_err_density": float(np.abs(nkb_f - ref_nkb).max()),
+                       "max_rel_err_energy": float(np.abs(sc_f[:, 1:] - ref_obs[:, 1:]).max() / escale),
+                       "max_rel_err_N": float(np.abs(sc_f[:, 0] - ref_obs[:, 0]).max() / abs(ref_obs[0, 0])),
+                       "dtype": DTYPES[form], "roofline": roofline(pf, form, tf)}
+
     if rank == 0:
-        sweep_s = prof["sweep_ms"] / 1e3
-        achieved = prof["sweep_flops"] / sweep_s / 1e9 if sweep_s > 0 else 0.0
-        peak, punit, psrc = PEAKS[args.precision]
         line = {
             "metric": METRIC, "value": value, "unit": "time-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPES[args.precision], "data": "synthetic (seeded c2 system, kbe_inputs)",
-            "config": {"workload": WORKLOAD, "precision": args.precision, "bench_step": f"one trajectory: reset + {nt} time steps",
+            "config": {"workload": WORKLOAD, "precision": args.precision,
+                       "bench_step": f"one trajectory: reset + {nt} time steps",
                        "time_steps_per_bench_step": nt, "n_corr": 2,
                        "l2": "history 4.3 GB > 129 MB L2 (inputs larger than L2)",
                        "parallelism": f"replicas x{world} (independent systems)"},
-            "roofline": {"kernel": "collision sweep (a2)", "bound": "alu", "achieved": achieved,
-                         "peak": peak, "unit": punit, "frac": achieved / peak, "traffic": None,
-                         "peak_source": psrc,
-                         "launches": prof["sweep_launches"], "sweep_share_of_step":
-                             sweep_s / t_dev if t_dev > 0 else None,
-                         "hbm_gbs_achieved": prof["sweep_bytes"] / sweep_s / 1e9 if sweep_s > 0 else 0.0},
+            "roofline": roofline(prof, args.precision, t_dev),
             "e2e": {"value": e2e_value, "unit": "time-steps/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(prof["launches"]),
             "clocks": clocks,
+            "forms": forms,
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(s)
         print(json.dumps(line), flush=True)
-    g.close()
     if dist:
         dist.destroy_process_group()
 

@@ -197,31 +197,30 @@ kbe_status kbe_op_pack(int precision, const void *src_dev, void *dst_dev, size_t
  * n+1 blocks written (complex128). precision: KBE_PREC_*; H_dev holds the
  * triangle in that precision's storage (kbe_op_pack), Sigma_dev and I_dev
  * are complex128. work_dev: device scratch of
- * kbe_op_collision_row_workspace(m, n, precision) bytes (0 for FP64; may
- * then be NULL). */
+ * kbe_op_collision_row_workspace(m, n, precision) bytes (coefficient rows
+ * and, when the l sum is split over CTAs, FP64 partial sums). */
 size_t kbe_op_collision_row_workspace(const kbe_mesh *m, int n, int precision);
 kbe_status kbe_op_collision_row(const kbe_mesh *m, int n, double dt, int precision,
                                 const void *H_dev, const void *Sigma_dev, void *I_dev,
                                 void *work_dev, size_t work_bytes, void *stream);
 
 /* (a3) Step propagators of a Hermitian h(k) (device [nb][nb][nk] c128):
- * h = W diag(lam) W^+, U = e^{-i dt h}, V = (U - 1) h^{-1} (-i dt on the
- * null space). Outputs device U, V, W [nb][nb][nk] c128, lam [nb][nk]. */
+ * U = e^{-i dt h}, V = (U - 1) h^{-1} (= -i dt on the null space of h), each
+ * device [nb][nb][nk] c128, by power series in dt / 2^s with doublings. */
 kbe_status kbe_op_propagators(const kbe_mesh *m, double dt, const void *h_dev, void *U_dev,
-                              void *V_dev, void *W_dev, double *lam_dev, void *stream);
+                              void *V_dev, void *stream);
 
-/* (a4) Row n from row n-1 (Algorithm 1, "solve Eq. 5"):
+/* (a4) Row n from row n-1 (Algorithm 1, "solve Eq. 5"), given the step's
+ * h, U = e^{-i dt h} and V = (U - 1) h^{-1} (per-k [nb][nb][nk] c128):
  *   G^x(n, j) = U G^x(n-1, j) + V Ibar^x(j),  j < n,
  *   Ibar = (1 - theta) I_{n-1}(j) + theta I_n(j),
- *   G^<(n, n) = U G^<(n-1, n-1) U^+ - i W [(W^+ Sbar W) o D] W^+,
+ *   G^<(n, n) = U G^<(n-1, n-1) U^+ - i int_0^dt e^{-i h u} Sbar e^{i h u} du,
  *   Sbar = (1-theta)(I^<_{n-1}(n-1) + h.c.) + theta (I^<_n(n) + h.c.),
- *   D_ab = (1 - e^{-i (lam_a - lam_b) dt}) / (i (lam_a - lam_b)),
  *   G^>(n, n) = G^<(n, n) - i.
  * Gprev_dev: row n-1 (n blocks); Iprev_dev: n blocks; Icur_dev: n+1 blocks
  * (read only if theta != 0); out_dev: row n (n+1 blocks). n >= 1. */
-kbe_status kbe_op_update_row(const kbe_mesh *m, int n, double dt, double theta,
-                             const void *U_dev, const void *V_dev, const void *W_dev,
-                             const double *lam_dev, const void *Gprev_dev,
+kbe_status kbe_op_update_row(const kbe_mesh *m, int n, double dt, double theta, const void *h_dev,
+                             const void *U_dev, const void *V_dev, const void *Gprev_dev,
                              const void *Iprev_dev, const void *Icur_dev, void *out_dev,
                              void *stream);
 

@@ -94,8 +94,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "kbe_op_collision_row": (I, [pmesh, I, D, I, P, P, P, P, S, P]),
         "kbe_op_collision_row_workspace": (S, [pmesh, I, I]),
         "kbe_op_pack": (I, [I, P, P, S, P]),
-        "kbe_op_propagators": (I, [pmesh, D, P, P, P, P, P, P]),
-        "kbe_op_update_row": (I, [pmesh, I, D, D, P, P, P, P, P, P, P, P, P]),
+        "kbe_op_propagators": (I, [pmesh, D, P, P, P, P]),
+        "kbe_op_update_row": (I, [pmesh, I, D, D, P, P, P, P, P, P, P, P]),
         "kbe_op_sigma_row_noalloc": (I, [pmesh, P, I, D, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -277,17 +277,16 @@ def pack(precision, src, dst, stream=None):
     _check(load().kbe_op_pack(int(precision), _c(src), _c(dst), src.numel(), _stream_ptr(stream)))
 
 
-def propagators(nb, L, dt, h, U, V, W, lam, stream=None):
+def propagators(nb, L, dt, h, U, V, stream=None):
     m = mesh(nb, L)
-    _check(load().kbe_op_propagators(ctypes.byref(m), float(dt), _c(h), _c(U), _c(V), _c(W), _c(lam),
-                                     _stream_ptr(stream)))
+    _check(load().kbe_op_propagators(ctypes.byref(m), float(dt), _c(h), _c(U), _c(V), _stream_ptr(stream)))
 
 
-def update_row(nb, L, n, dt, theta, U, V, W, lam, Gprev, Iprev, Icur, out, stream=None):
+def update_row(nb, L, n, dt, theta, h, U, V, Gprev, Iprev, Icur, out, stream=None):
     m = mesh(nb, L)
-    _check(load().kbe_op_update_row(ctypes.byref(m), int(n), float(dt), float(theta), _c(U), _c(V),
-                                    _c(W), _c(lam), _c(Gprev), _c(Iprev),
-                                    None if Icur is None else _c(Icur), _c(out), _stream_ptr(stream)))
+    _check(load().kbe_op_update_row(ctypes.byref(m), int(n), float(dt), float(theta), _c(h), _c(U), _c(V),
+                                    _c(Gprev), _c(Iprev), None if Icur is None else _c(Icur), _c(out),
+                                    _stream_ptr(stream)))
 
 
 def sigma_row_noalloc(nb, L, v, n, Un, Grow, Sigma, Ul=None, stream=None):

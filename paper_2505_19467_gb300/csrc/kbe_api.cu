@@ -42,13 +42,12 @@ struct kbe_handle {
   void *H = nullptr;           // history triangle in the precision's storage
   size_t esz = 16;             // bytes per stored complex number
   double2 *Wrow[2] = {nullptr, nullptr};   // FP64 rows n-1, n (ring; DF64 / C64 only)
-  void *coef = nullptr;        // sweep coefficient rows (DF64 / C64)
+  void *coef = nullptr;        // sweep workspace: coefficient rows + l-split partial sums
   double2 *Ip = nullptr;       // I row n-1
   double2 *Ic = nullptr;       // I row n
   double2 *Sig = nullptr;      // Sigma row
   double2 *work = nullptr;     // Sigma scratch
-  double2 *U = nullptr, *V = nullptr, *W = nullptr;
-  double *lam = nullptr;
+  double2 *U = nullptr, *V = nullptr, *hk = nullptr;   // step propagators and h, per k
   double2 *rho = nullptr;      // [(nt_max+2)][nb][nb]; slot nt_max+1 = current estimate
   double *obs = nullptr;       // [(nt_max+1)][6]
   double *nkb = nullptr;       // [(nt_max+1)][nk][nb]
@@ -120,7 +119,7 @@ cudaError_t dalloc(kbe_handle *h, T **p, size_t count) {
 
 void free_all(kbe_handle *h) {
   void *ptrs[] = {h->H, h->Wrow[0], h->Wrow[1], h->coef, h->Ip, h->Ic, h->Sig, h->work, h->U, h->V,
-                  h->W, h->lam, h->rho, h->obs, h->nkb, h->status, h->d_hopR, h->d_hopT, h->d_U};
+                  h->hk, h->rho, h->obs, h->nkb, h->status, h->d_hopR, h->d_hopT, h->d_U};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (auto &pr : h->ev) {
@@ -185,7 +184,7 @@ kbe_status evaluate_row(kbe_handle *h, int n) {
     h->ev_flops[h->ev_used] = sweep_flops(h, n);
     h->ev_bytes[h->ev_used] = sweep_bytes(h, n);
     h->ev_used++;
-    h->stats.launches += 4 + (h->cfg.precision != KBE_PREC_FP64 ? 1 : 0);
+    h->stats.launches += 5 + (kbe::sweep_splits(h->mesh, n) > 1 ? 1 : 0);
   }
   return KBE_OK;
 }
@@ -201,8 +200,8 @@ kbe_status build_props(kbe_handle *h, int n, const double2 *ra, const double2 *r
   p.hf = h->cfg.hf;
   p.paper_shift = h->cfg.paper_shift;
   for (int i = 0; i < h->nb2; ++i) p.v[i] = h->v[(size_t)i];
-  cudaError_t e = kbe::launch_build_props(h->mesh, hop_table(h), p, h->cfg.dt, h->U, h->V, h->W,
-                                          h->lam, h->status, h->stream);
+  cudaError_t e = kbe::launch_build_props(h->mesh, hop_table(h), p, h->cfg.dt, nullptr, h->hk, h->U,
+                                          h->V, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "build_props");
   if (h->prof) h->stats.launches += 1;
   return KBE_OK;
@@ -211,8 +210,8 @@ kbe_status build_props(kbe_handle *h, int n, const double2 *ra, const double2 *r
 kbe_status update(kbe_handle *h, int n, double theta) {
   double2 *prev = frow(h, n - 1);
   double2 *row = frow(h, n);
-  cudaError_t e = kbe::launch_update_row(h->mesh, n, h->cfg.dt, theta, h->U, h->V, h->W, h->lam,
-                                         prev, h->Ip, h->Ic, row, h->stream);
+  cudaError_t e = kbe::launch_update_row(h->mesh, n, h->cfg.dt, theta, h->hk, h->U, h->V, prev, h->Ip,
+                                         h->Ic, row, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "update_row");
   if (h->prof) h->stats.launches += 2;
   return publish(h, n);
@@ -328,16 +327,15 @@ kbe_status kbe_create(const kbe_config *cfg, void *stream, kbe_handle **out) {
   if (cfg->precision != KBE_PREC_FP64) {
     if (e == cudaSuccess) e = dalloc(h, &h->Wrow[0], row);
     if (e == cudaSuccess) e = dalloc(h, &h->Wrow[1], row);
-    if (e == cudaSuccess) e = dalloc(h, (char **)&h->coef, kbe::sweep_workspace_bytes(h->mesh, (int)T, cfg->precision));
   }
+  if (e == cudaSuccess) e = dalloc(h, (char **)&h->coef, kbe::sweep_workspace_bytes(h->mesh, (int)T, cfg->precision));
   if (e == cudaSuccess) e = dalloc(h, &h->Ip, row);
   if (e == cudaSuccess) e = dalloc(h, &h->Ic, row);
   if (e == cudaSuccess) e = dalloc(h, &h->Sig, row);
   if (e == cudaSuccess) e = dalloc(h, &h->work, kbe::sigma_workspace_bytes(h->mesh, (int)T) / sizeof(double2));
   if (e == cudaSuccess) e = dalloc(h, &h->U, h->blk);
   if (e == cudaSuccess) e = dalloc(h, &h->V, h->blk);
-  if (e == cudaSuccess) e = dalloc(h, &h->W, h->blk);
-  if (e == cudaSuccess) e = dalloc(h, &h->lam, (size_t)cfg->nb * h->mesh.nk);
+  if (e == cudaSuccess) e = dalloc(h, &h->hk, h->blk);
   if (e == cudaSuccess) e = dalloc(h, &h->rho, (T + 2) * h->nb2);
   if (e == cudaSuccess) e = dalloc(h, &h->obs, (T + 1) * 6);
   if (e == cudaSuccess) e = dalloc(h, &h->nkb, (T + 1) * h->mesh.nk * cfg->nb);
@@ -627,7 +625,7 @@ kbe_status kbe_op_collision_row(const kbe_mesh *m, int n, double dt, int precisi
     return fail(nullptr, KBE_ERR_ARG, "op_collision_row: bad arguments");
   if (!kbe::precision_supported(precision)) return fail(nullptr, KBE_ERR_UNSUPPORTED, "op_collision_row: precision");
   const size_t need = kbe::sweep_workspace_bytes(to_mesh(m), n, precision);
-  if (need && (!work_dev || work_bytes < need))
+  if (!work_dev || work_bytes < need)
     return fail(nullptr, KBE_ERR_ARG, "op_collision_row: workspace too small");
   cudaError_t e = kbe::launch_sweep(to_mesh(m), n, dt, precision, H_dev, (const double2 *)Sigma_dev,
                                     (double2 *)I_dev, work_dev, (cudaStream_t)stream);
@@ -636,25 +634,25 @@ kbe_status kbe_op_collision_row(const kbe_mesh *m, int n, double dt, int precisi
 }
 
 kbe_status kbe_op_propagators(const kbe_mesh *m, double dt, const void *h_dev, void *U_dev,
-                              void *V_dev, void *W_dev, double *lam_dev, void *stream) {
-  if (!mesh_ok(m) || !h_dev || !U_dev || !V_dev || !W_dev || !lam_dev || !(dt > 0.0))
+                              void *V_dev, void *stream) {
+  if (!mesh_ok(m) || !h_dev || !U_dev || !V_dev || !(dt > 0.0) || !std::isfinite(dt))
     return fail(nullptr, KBE_ERR_ARG, "op_propagators: bad arguments");
-  cudaError_t e = kbe::launch_props_from_h(to_mesh(m), dt, (const double2 *)h_dev, (double2 *)U_dev,
-                                           (double2 *)V_dev, (double2 *)W_dev, lam_dev, nullptr,
-                                           (cudaStream_t)stream);
+  kbe::HopTable hop{};
+  kbe::PropParams p{};
+  cudaError_t e = kbe::launch_build_props(to_mesh(m), hop, p, dt, (const double2 *)h_dev, nullptr,
+                                          (double2 *)U_dev, (double2 *)V_dev, (cudaStream_t)stream);
   if (e != cudaSuccess) return fail(nullptr, KBE_ERR_CUDA, std::string("op_propagators: ") + cudaGetErrorString(e));
   return KBE_OK;
 }
 
-kbe_status kbe_op_update_row(const kbe_mesh *m, int n, double dt, double theta, const void *U_dev,
-                             const void *V_dev, const void *W_dev, const double *lam_dev,
-                             const void *Gprev_dev, const void *Iprev_dev, const void *Icur_dev,
-                             void *out_dev, void *stream) {
-  if (!mesh_ok(m) || n < 1 || !U_dev || !V_dev || !W_dev || !lam_dev || !Gprev_dev || !Iprev_dev ||
-      !out_dev || !(dt > 0.0) || (theta != 0.0 && !Icur_dev))
+kbe_status kbe_op_update_row(const kbe_mesh *m, int n, double dt, double theta, const void *h_dev,
+                             const void *U_dev, const void *V_dev, const void *Gprev_dev,
+                             const void *Iprev_dev, const void *Icur_dev, void *out_dev, void *stream) {
+  if (!mesh_ok(m) || n < 1 || !h_dev || !U_dev || !V_dev || !Gprev_dev || !Iprev_dev || !out_dev ||
+      !(dt > 0.0) || !std::isfinite(dt) || (theta != 0.0 && !Icur_dev))
     return fail(nullptr, KBE_ERR_ARG, "op_update_row: bad arguments");
-  cudaError_t e = kbe::launch_update_row(to_mesh(m), n, dt, theta, (const double2 *)U_dev,
-                                         (const double2 *)V_dev, (const double2 *)W_dev, lam_dev,
+  cudaError_t e = kbe::launch_update_row(to_mesh(m), n, dt, theta, (const double2 *)h_dev,
+                                         (const double2 *)U_dev, (const double2 *)V_dev,
                                          (const double2 *)Gprev_dev, (const double2 *)Iprev_dev,
                                          (const double2 *)Icur_dev, (double2 *)out_dev,
                                          (cudaStream_t)stream);

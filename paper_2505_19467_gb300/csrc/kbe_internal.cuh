@@ -80,6 +80,7 @@ bool sweep_supported(int nb);
 bool precision_supported(int prec);
 size_t history_elem_bytes(int prec);
 size_t sweep_workspace_bytes(const Mesh &m, int n, int prec);
+int sweep_splits(const Mesh &m, int n);   // CTAs sharing one output's l range
 cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t count, cudaStream_t st);
 cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const void *H,
                          const double2 *Sig, double2 *I, void *work, cudaStream_t st);
@@ -104,17 +105,18 @@ struct PropParams {
   int hf, paper_shift;
   double v[kMaxNb * kMaxNb];
 };
+// h for the step (from the hopping table, mean field and shift; or h_in when
+// not NULL, then hop / p are unused), U = e^{-i dt h}, V = (U - 1) h^{-1};
+// h_out (may be NULL) receives h. All per-k [a][b][k].
 cudaError_t launch_build_props(const Mesh &m, const HopTable &hop, const PropParams &p, double dt,
-                               double2 *U, double2 *V, double2 *W, double *lam, int *status,
+                               const double2 *h_in, double2 *h_out, double2 *U, double2 *V,
                                cudaStream_t st);
-cudaError_t launch_props_from_h(const Mesh &m, double dt, const double2 *h, double2 *U, double2 *V,
-                                double2 *W, double *lam, int *status, cudaStream_t st);
 
-// a4 update
-cudaError_t launch_update_row(const Mesh &m, int n, double dt, double theta, const double2 *U,
-                              const double2 *V, const double2 *W, const double *lam,
-                              const double2 *Gprev, const double2 *Iprev, const double2 *Icur,
-                              double2 *out, cudaStream_t st);
+// a4 update: rows j < n and the time diagonal (h, U, V of the step)
+cudaError_t launch_update_row(const Mesh &m, int n, double dt, double theta, const double2 *h,
+                              const double2 *U, const double2 *V, const double2 *Gprev,
+                              const double2 *Iprev, const double2 *Icur, double2 *out,
+                              cudaStream_t st);
 
 // a5 observables
 struct ObsParams {

@@ -2,17 +2,24 @@
 // update, (a5) equal-time observables, and the t = 0 state.
 //
 // All of these are O(n_k N_b^3) or O(n n_k N_b^3) per call, small next to the
-// collision sweep; they run in FP64 with one thread per k (eigen-problems,
-// time diagonal) or per output element (row update).
+// collision sweep; they run in FP64.
 //
 // Time stepping (Algorithm 1, "solve Eq. 5"): with h fixed over the step and
 // the collision term replaced by a constant average Ibar, the row equation
 // i dG(t, t_j)/dt = h G + Ibar has the exact one-step solution
 //   G(n, j) = U G(n-1, j) + V Ibar(j),  U = e^{-i dt h},  V = (U - 1) h^{-1},
 // and the time diagonal i dG(t,t)/dt = [h, G] + Sbar, Sbar = Ibar + Ibar^+,
-//   G(n, n) = U G(n-1, n-1) U^+ - i W [(W^+ Sbar W) o D] W^+,
-//   D_ab = (1 - e^{-i (lam_a - lam_b) dt}) / (i (lam_a - lam_b)),
-// with h = W diag(lam) W^+. D_aa = dt keeps Tr G(t,t) exact.
+//   G(n, n) = U G(n-1, n-1) U^+ - i X,  X = int_0^dt e^{-i h u} Sbar e^{i h u} du.
+// The matrix functions are evaluated per k by one CTA group of N_b^2 threads
+// (one per matrix element), as power series in tau = dt / 2^s with
+// tau ||h|| <= 1/4, followed by s doublings:
+//   U_tau = sum_m (-i tau h)^m / m!,          U_2tau = U_tau^2,
+//   V_tau = -i tau sum_m (-i tau h)^m/(m+1)!,  V_2tau = (U_tau + 1) V_tau,
+//   X_tau = tau sum_m (-i tau)^m ad_h^m(S) / (m+1)!, X_2tau = X_tau + U_tau X_tau U_tau^+,
+// with ad_h(S) = h S - S h; 14 and 18 terms reach the FP64 rounding level
+// (0.25^14/14! and 0.5^18/18! < 1e-19). The trace of X is dt Tr S exactly in
+// exact arithmetic, so the particle number is conserved. A Jacobi
+// eigen-solver is used only for the Fermi function of the initial state.
 #include "kbe_internal.cuh"
 
 namespace kbe {
@@ -108,103 +115,231 @@ __device__ void bare_h(const HopTable &hop, int k, int L0, int L1, double A, dou
   }
 }
 
-// (e^{-i x} - 1) / x * dt for x = lam dt, written without cancellation
-__device__ __forceinline__ double2 phi_row(double lam, double dt) {
-  const double x = lam * dt;
-  if (x == 0.0) return make_double2(0.0, -dt);
-  const double s2 = sin(0.5 * x);
-  return make_double2(dt * (-2.0 * s2 * s2 / x), -dt * sin(x) / x);
-}
-
-// (1 - e^{-i y}) / (i y) * dt for y = (lam_a - lam_b) dt
-__device__ __forceinline__ double2 phi_diag(double dl, double dt) {
-  const double y = dl * dt;
-  if (y == 0.0) return make_double2(dt, 0.0);
-  const double s2 = sin(0.5 * y);
-  return make_double2(dt * sin(y) / y, -dt * 2.0 * s2 * s2 / y);
-}
-
-// U, V from (W, lam) for one k, stored [a][b][k]
+// ------------------------------------------------ per-k matrix functions ----
+// A CTA holds KPC = 256 / N_b^2 k-points; thread t works on element (a, b)
+// of k-point t / N_b^2. Matrices live in shared memory, [kk][a][b].
 template <int NB>
-__device__ void store_props(const double2 *W, const double *lam, double dt, int k, int nk,
-                            double2 *U, double2 *V, double2 *Wout, double *lamout) {
-  double2 eu[NB], ev[NB];
-#pragma unroll 1
-  for (int c = 0; c < NB; ++c) {
-    double s, co;
-    sincos(-lam[c] * dt, &s, &co);
-    eu[c] = make_double2(co, s);
-    ev[c] = phi_row(lam[c], dt);
+struct MatGroup {
+  static constexpr int E = NB * NB;
+  static constexpr int KPC = (256 / E) > 0 ? (256 / E) : 1;
+  int kk, a, b, e;
+  __device__ MatGroup() {
+    kk = threadIdx.x / E;
+    e = threadIdx.x - kk * E;
+    a = e / NB;
+    b = e - a * NB;
   }
-#pragma unroll 1
-  for (int a = 0; a < NB; ++a)
-#pragma unroll 1
-    for (int b = 0; b < NB; ++b) {
-      double2 su = make_double2(0, 0), sv = make_double2(0, 0);
-#pragma unroll 1
-      for (int c = 0; c < NB; ++c) {
-        const double2 wc = c_mulc(W[a * NB + c], W[b * NB + c]);
-        su = c_fma(wc, eu[c], su);
-        sv = c_fma(wc, ev[c], sv);
-      }
-      const size_t o = (size_t)(a * NB + b) * nk + k;
-      U[o] = su;
-      V[o] = sv;
-      Wout[o] = W[a * NB + b];
-    }
-#pragma unroll 1
-  for (int a = 0; a < NB; ++a) lamout[(size_t)a * nk + k] = lam[a];
-}
-
-struct VMatP {
-  double v[kMaxNb * kMaxNb];
+  // (A B)_ab of this thread's k-point
+  __device__ __forceinline__ double2 mm(const double2 *A, const double2 *B) const {
+    const double2 *Ar = A + kk * E + a * NB;
+    const double2 *Bc = B + kk * E + b;
+    double2 s = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int c = 0; c < NB; ++c) s = c_fma(Ar[c], Bc[c * NB], s);
+    return s;
+  }
+  // (A B^+)_ab
+  __device__ __forceinline__ double2 mm_adj(const double2 *A, const double2 *B) const {
+    const double2 *Ar = A + kk * E + a * NB;
+    const double2 *Br = B + kk * E + b * NB;
+    double2 s = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int c = 0; c < NB; ++c) s = c_add(s, c_mulc(Ar[c], Br[c]));
+    return s;
+  }
 };
 
+// number of doublings s with (dt / 2^s) * max_k ||h_k||_rowsum <= 1/4, for
+// all k-points of the CTA (uniform across the CTA); h in shared memory
 template <int NB>
-__global__ void build_props_kernel(Mesh m, HopTable hop, PropParams p, double dt, double2 *U,
-                                   double2 *V, double2 *W, double *lam, int *status) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= m.nk) return;
-  double2 h[NB * NB], Wl[NB * NB];
-  double ll[NB];
-  bare_h<NB>(hop, k, m.L0, m.L1, p.A, h);
-  if (p.hf) {
-    // mean field S_jm = U (delta_jm sum_a v_ja rho_aa - v_jm rho_jm)
-#pragma unroll 1
-    for (int jj = 0; jj < NB; ++jj)
-#pragma unroll 1
-      for (int mm = 0; mm < NB; ++mm) {
-        const int e = jj * NB + mm;
-        const double2 r = c_add(c_scale(p.ca, p.rho_a[e]), c_scale(p.cb, p.rho_b[e]));
-        double2 x = c_scale(-p.v[e], r);
-        if (jj == mm)
-#pragma unroll 1
-          for (int a = 0; a < NB; ++a) {
-            const int ea = a * NB + a;
-            const double2 ra = c_add(c_scale(p.ca, p.rho_a[ea]), c_scale(p.cb, p.rho_b[ea]));
-            x = c_add(x, c_scale(p.v[jj * NB + a], ra));
-          }
-        h[e] = c_add(h[e], c_scale(p.Umid, x));
-      }
+__device__ int doublings(const MatGroup<NB> &g, const double2 *h, int nvalid, double dt, double *red) {
+  if (g.b == 0) {
+    double r = 0.0;
+    for (int c = 0; c < NB; ++c) {
+      const double2 z = h[g.kk * g.E + g.a * NB + c];
+      r += hypot(z.x, z.y);
+    }
+    red[g.kk * NB + g.a] = (g.kk < nvalid) ? r : 0.0;
   }
-  if (p.paper_shift) h[(NB - 1) * NB + NB - 1].x -= p.Umid;
-  if (!herm_eig<NB>(h, ll, Wl)) atomicOr(status, kDevEigNoConv);
-  store_props<NB>(Wl, ll, dt, k, m.nk, U, V, W, lam);
+  __syncthreads();
+  __shared__ int s_sh;
+  if (threadIdx.x == 0) {
+    double nu = 0.0;
+    for (int i = 0; i < MatGroup<NB>::KPC * NB; ++i) nu = fmax(nu, red[i]);
+    nu *= dt;
+    int sc = 0;
+    while (nu > 0.25 && sc < 40) {   // bounded: nu <= 2^40 / 4 covers any finite h
+      nu *= 0.5;
+      ++sc;
+    }
+    s_sh = sc;
+  }
+  __syncthreads();
+  return s_sh;
 }
 
+// U_dt and V_dt of h (shared memory), element (a, b) returned in u, v;
+// P, Q, W are shared scratch of KPC * N_b^2 each.
 template <int NB>
-__global__ void props_from_h_kernel(Mesh m, double dt, const double2 *hin, double2 *U, double2 *V,
-                                    double2 *W, double *lam, int *status) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= m.nk) return;
-  double2 h[NB * NB], Wl[NB * NB];
-  double ll[NB];
-#pragma unroll 1
-  for (int e = 0; e < NB * NB; ++e) h[e] = hin[(size_t)e * m.nk + k];
-  if (!herm_eig<NB>(h, ll, Wl)) {
-    if (status) atomicOr(status, kDevEigNoConv);
+__device__ void exp_and_phi(const MatGroup<NB> &g, const double2 *h, double tau, int s, double2 *P,
+                            double2 *Q, double2 *W, double2 &u, double2 &v) {
+  const int o = g.kk * g.E + g.e;
+  const double2 one = make_double2(g.a == g.b ? 1.0 : 0.0, 0.0);
+  P[o] = one;
+  u = one;
+  v = make_double2(0.0, -tau * one.x);   // -i tau P_0 / 1
+  __syncthreads();
+  for (int m = 1; m <= 14; ++m) {
+    double2 t = g.mm(P, h);
+    t = make_double2(tau * t.y / m, -tau * t.x / m);   // (-i tau / m) (P h)
+    __syncthreads();
+    P[o] = t;
+    u = c_add(u, t);
+    v = c_add(v, make_double2(tau * t.y / (m + 1), -tau * t.x / (m + 1)));
+    __syncthreads();
   }
-  store_props<NB>(Wl, ll, dt, k, m.nk, U, V, W, lam);
+  for (int r = 0; r < s; ++r) {   // V <- (U + 1) V, U <- U U
+    P[o] = u;
+    Q[o] = v;
+    W[o] = c_add(u, one);
+    __syncthreads();
+    const double2 un = g.mm(P, P), vn = g.mm(W, Q);
+    __syncthreads();
+    u = un;
+    v = vn;
+  }
+}
+
+// h(k) for the step: Peierls h0, mean field, -U n_c; U, V; h written out
+template <int NB>
+__global__ void __launch_bounds__(256) build_props_kernel(Mesh m, HopTable hop, PropParams p,
+                                                          const double2 *__restrict__ hin, double dt,
+                                                          double2 *__restrict__ hout,
+                                                          double2 *__restrict__ U,
+                                                          double2 *__restrict__ V) {
+  using G = MatGroup<NB>;
+  __shared__ double2 sh[4][G::KPC * G::E];
+  __shared__ double red[G::KPC * NB];
+  const G g;
+  const int k = blockIdx.x * G::KPC + g.kk;
+  const bool active = threadIdx.x < G::KPC * G::E && k < m.nk;
+  const int nvalid = min(G::KPC, m.nk - (int)blockIdx.x * G::KPC);
+  const int o = g.kk * G::E + g.e;
+  double2 hv = make_double2(0.0, 0.0);
+  if (active) {
+    if (hin) {
+      hv = hin[(size_t)g.e * m.nk + k];
+    } else {
+      // h0_ab(k - A d) = sum_r t_ab(R_r) exp(i (k - A d).R_r), this thread's element
+      const int k0 = k / m.L1, k1 = k - (k / m.L1) * m.L1;
+      for (int r = 0; r < hop.nhop; ++r) {
+        const int R0 = hop.R[2 * r], R1 = hop.R[2 * r + 1];
+        const int m0 = ((k0 * R0) % m.L0 + m.L0) % m.L0, m1 = ((k1 * R1) % m.L1 + m.L1) % m.L1;
+        const double th = 2.0 * M_PI * ((double)m0 / m.L0 + (double)m1 / m.L1) - p.A * (hop.d0 * R0 + hop.d1 * R1);
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        hv = c_fma(hop.T[(size_t)r * G::E + g.e], make_double2(cs, sn), hv);
+      }
+      if (p.hf) {   // S_ab = U (delta_ab sum_c v_ac rho_cc - v_ab rho_ab), rho = ca rho_a + cb rho_b
+        const double2 rab = c_add(c_scale(p.ca, p.rho_a[g.e]), c_scale(p.cb, p.rho_b[g.e]));
+        double2 x = c_scale(-p.v[g.e], rab);
+        if (g.a == g.b)
+          for (int c = 0; c < NB; ++c) {
+            const int ec = c * NB + c;
+            x = c_add(x, c_scale(p.v[g.a * NB + c], c_add(c_scale(p.ca, p.rho_a[ec]), c_scale(p.cb, p.rho_b[ec]))));
+          }
+        hv = c_add(hv, c_scale(p.Umid, x));
+      }
+      if (p.paper_shift && g.a == NB - 1 && g.b == NB - 1) hv.x -= p.Umid;
+    }
+  }
+  if (threadIdx.x < G::KPC * G::E) sh[0][o] = hv;
+  __syncthreads();
+  const int s = doublings<NB>(g, sh[0], nvalid, dt, red);
+  const double tau = ldexp(dt, -s);
+  double2 u, v;
+  exp_and_phi<NB>(g, sh[0], tau, s, sh[1], sh[2], sh[3], u, v);
+  if (active) {
+    const size_t go = (size_t)g.e * m.nk + k;
+    if (hout) hout[go] = hv;
+    U[go] = u;
+    V[go] = v;
+  }
+}
+
+// time diagonal of row n: G^<(n,n) = U G^<(n-1,n-1) U^+ - i X(Sbar)
+template <int NB>
+__global__ void __launch_bounds__(256) update_diag_kernel(int n, int nk, double dt, double theta,
+                                                          const double2 *__restrict__ h,
+                                                          const double2 *__restrict__ Gprev,
+                                                          const double2 *__restrict__ Ip,
+                                                          const double2 *__restrict__ Ic,
+                                                          double2 *__restrict__ out) {
+  using G = MatGroup<NB>;
+  __shared__ double2 sh[5][G::KPC * G::E];
+  __shared__ double red[G::KPC * NB];
+  const G g;
+  const int k = blockIdx.x * G::KPC + g.kk;
+  const bool active = threadIdx.x < G::KPC * G::E && k < nk;
+  const int nvalid = min(G::KPC, nk - (int)blockIdx.x * G::KPC);
+  const int o = g.kk * G::E + g.e;
+  const size_t blk = (size_t)G::E * nk;
+  double2 *H = sh[0], *Qs = sh[1], *T = sh[2], *P = sh[3], *Wk = sh[4];
+  double2 hv = make_double2(0, 0), sv = make_double2(0, 0), gd = make_double2(0, 0);
+  if (active) {
+    const size_t oab = (size_t)g.e * nk + k, oba = (size_t)(g.b * NB + g.a) * nk + k;
+    hv = h[oab];
+    const double2 *ipd = Ip + (size_t)(n - 1) * 2 * blk;   // I^<_{n-1}(n-1)
+    sv = c_scale(1.0 - theta, c_add(ipd[oab], c_conj(ipd[oba])));
+    if (theta != 0.0) {
+      const double2 *icd = Ic + (size_t)n * 2 * blk;       // I^<_n(n)
+      sv = c_add(sv, c_scale(theta, c_add(icd[oab], c_conj(icd[oba]))));
+    }
+    gd = Gprev[(size_t)(n - 1) * 2 * blk + oab];            // G^<(n-1, n-1)
+  }
+  if (threadIdx.x < G::KPC * G::E) {
+    H[o] = hv;
+    Qs[o] = sv;
+  }
+  __syncthreads();
+  const int s = doublings<NB>(g, H, nvalid, dt, red);
+  const double tau = ldexp(dt, -s);
+  // X_tau = tau sum_m Q_m / (m+1), Q_m = (-i tau / m) [h, Q_{m-1}], Q_0 = Sbar
+  double2 x = c_scale(tau, sv);
+  for (int m = 1; m <= 18; ++m) {
+    const double2 c = c_sub(g.mm(H, Qs), g.mm(Qs, H));
+    const double2 q = make_double2(tau * c.y / m, -tau * c.x / m);
+    __syncthreads();
+    Qs[o] = q;
+    x = c_add(x, c_scale(tau / (m + 1), q));
+    __syncthreads();
+  }
+  double2 u, v;
+  exp_and_phi<NB>(g, H, tau, 0, P, T, Wk, u, v);   // U_tau
+  (void)v;
+  for (int r = 0; r < s; ++r) {   // X <- X + U X U^+, U <- U U
+    P[o] = u;
+    Qs[o] = x;
+    __syncthreads();
+    T[o] = g.mm_adj(Qs, P);   // X U^+
+    const double2 un = g.mm(P, P);
+    __syncthreads();
+    x = c_add(x, g.mm(P, T));
+    u = un;
+    __syncthreads();
+  }
+  // G = U Gd U^+ - i X
+  P[o] = u;
+  Qs[o] = gd;
+  __syncthreads();
+  T[o] = g.mm_adj(Qs, P);
+  __syncthreads();
+  const double2 gg = c_sub(g.mm(P, T), c_i(x));
+  if (active) {
+    double2 *ol = out + (size_t)n * 2 * blk + (size_t)g.e * nk + k;
+    ol[0] = gg;
+    ol[blk] = (g.a == g.b) ? make_double2(gg.x, gg.y - 1.0) : gg;
+  }
 }
 
 // t = 0: G^<(k;0,0) = i W f(lam) W^+ of h0(k), G^> = G^< - i
@@ -289,92 +424,6 @@ __global__ void update_rows_kernel(int n, int nk, double theta, const double2 *_
     acc = c_fma(V[ou], ib, acc);
   }
   out[base + (size_t)(a * NB + b) * nk + k] = acc;
-}
-
-// time diagonal of row n, one thread per k
-template <int NB>
-__global__ void update_diag_kernel(int n, int nk, double dt, double theta,
-                                   const double2 *__restrict__ U, const double2 *__restrict__ W,
-                                   const double *__restrict__ lam, const double2 *__restrict__ Gprev,
-                                   const double2 *__restrict__ Ip, const double2 *__restrict__ Ic,
-                                   double2 *__restrict__ out) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nk) return;
-  const size_t blk = (size_t)NB * NB * nk;
-  const double2 *ipd = Ip + (size_t)(n - 1) * 2 * blk;   // I^<_{n-1}(n-1)
-  const double2 *icd = Ic + (size_t)n * 2 * blk;         // I^<_n(n)
-  const double2 *gd = Gprev + (size_t)(n - 1) * 2 * blk; // G^<(n-1, n-1)
-  double2 S[NB * NB], T[NB * NB], Wk[NB * NB];
-  double l[NB];
-#pragma unroll 1
-  for (int a = 0; a < NB; ++a) l[a] = lam[(size_t)a * nk + k];
-#pragma unroll 1
-  for (int e = 0; e < NB * NB; ++e) Wk[e] = W[(size_t)e * nk + k];
-#pragma unroll 1
-  for (int a = 0; a < NB; ++a)
-#pragma unroll 1
-    for (int b = 0; b < NB; ++b) {
-      const size_t oab = (size_t)(a * NB + b) * nk + k, oba = (size_t)(b * NB + a) * nk + k;
-      double2 s = c_scale(1.0 - theta, c_add(ipd[oab], c_conj(ipd[oba])));
-      if (theta != 0.0) s = c_add(s, c_scale(theta, c_add(icd[oab], c_conj(icd[oba]))));
-      S[a * NB + b] = s;
-    }
-  // T = W^+ S W, then T o D
-#pragma unroll 1
-  for (int a = 0; a < NB; ++a)
-#pragma unroll 1
-    for (int b = 0; b < NB; ++b) {
-      double2 acc = make_double2(0, 0);
-#pragma unroll 1
-      for (int c = 0; c < NB; ++c) {
-        double2 sw = make_double2(0, 0);
-#pragma unroll 1
-        for (int d = 0; d < NB; ++d) sw = c_fma(S[c * NB + d], Wk[d * NB + b], sw);
-        acc = c_fma(c_conj(Wk[c * NB + a]), sw, acc);
-      }
-      T[a * NB + b] = c_mul(acc, phi_diag(l[a] - l[b], dt));
-    }
-  // S <- W T W^+  (reuse S)
-#pragma unroll 1
-  for (int a = 0; a < NB; ++a)
-#pragma unroll 1
-    for (int b = 0; b < NB; ++b) {
-      double2 acc = make_double2(0, 0);
-#pragma unroll 1
-      for (int c = 0; c < NB; ++c) {
-        double2 tw = make_double2(0, 0);
-#pragma unroll 1
-        for (int d = 0; d < NB; ++d) tw = c_add(tw, c_mulc(T[c * NB + d], Wk[b * NB + d]));
-        acc = c_fma(Wk[a * NB + c], tw, acc);
-      }
-      S[a * NB + b] = acc;
-    }
-  // T <- U G U^+
-#pragma unroll 1
-  for (int a = 0; a < NB; ++a)
-#pragma unroll 1
-    for (int b = 0; b < NB; ++b) {
-      double2 acc = make_double2(0, 0);
-#pragma unroll 1
-      for (int c = 0; c < NB; ++c) {
-        double2 gu = make_double2(0, 0);
-#pragma unroll 1
-        for (int d = 0; d < NB; ++d)
-          gu = c_add(gu, c_mulc(gd[(size_t)(c * NB + d) * nk + k], U[(size_t)(b * NB + d) * nk + k]));
-        acc = c_fma(U[(size_t)(a * NB + c) * nk + k], gu, acc);
-      }
-      T[a * NB + b] = acc;
-    }
-  double2 *ol = out + (size_t)n * 2 * blk;
-#pragma unroll 1
-  for (int a = 0; a < NB; ++a)
-#pragma unroll 1
-    for (int b = 0; b < NB; ++b) {
-      const double2 g = c_sub(T[a * NB + b], c_i(S[a * NB + b]));
-      const size_t o = (size_t)(a * NB + b) * nk + k;
-      ol[o] = g;
-      ol[blk + o] = (a == b) ? make_double2(g.x, g.y - 1.0) : g;
-    }
 }
 
 // equal-time observables of row n; one CTA
@@ -470,25 +519,28 @@ cudaError_t launch_local_density(const Mesh &m, const double2 *Gdiag, double2 *r
   return cudaGetLastError();
 }
 
+// one CTA of KPC * N_b^2 threads per KPC k-points
+template <int NB>
+unsigned matgroup_blocks(int nk) {
+  return (unsigned)((nk + MatGroup<NB>::KPC - 1) / MatGroup<NB>::KPC);
+}
+template <int NB>
+unsigned matgroup_threads() {
+  return (unsigned)(MatGroup<NB>::KPC * MatGroup<NB>::E);
+}
+
 cudaError_t launch_build_props(const Mesh &m, const HopTable &hop, const PropParams &p, double dt,
-                               double2 *U, double2 *V, double2 *W, double *lam, int *status,
+                               const double2 *h_in, double2 *h_out, double2 *U, double2 *V,
                                cudaStream_t st) {
-  const int threads = 64, blocks = (m.nk + threads - 1) / threads;
-  KBE_NB_SWITCH(m.nb, (build_props_kernel<NB><<<blocks, threads, 0, st>>>(m, hop, p, dt, U, V, W, lam, status)));
+  KBE_NB_SWITCH(m.nb, (build_props_kernel<NB><<<matgroup_blocks<NB>(m.nk), matgroup_threads<NB>(), 0, st>>>(
+                          m, hop, p, h_in, dt, h_out, U, V)));
   return cudaGetLastError();
 }
 
-cudaError_t launch_props_from_h(const Mesh &m, double dt, const double2 *h, double2 *U, double2 *V,
-                                double2 *W, double *lam, int *status, cudaStream_t st) {
-  const int threads = 64, blocks = (m.nk + threads - 1) / threads;
-  KBE_NB_SWITCH(m.nb, (props_from_h_kernel<NB><<<blocks, threads, 0, st>>>(m, dt, h, U, V, W, lam, status)));
-  return cudaGetLastError();
-}
-
-cudaError_t launch_update_row(const Mesh &m, int n, double dt, double theta, const double2 *U,
-                              const double2 *V, const double2 *W, const double *lam,
-                              const double2 *Gprev, const double2 *Iprev, const double2 *Icur,
-                              double2 *out, cudaStream_t st) {
+cudaError_t launch_update_row(const Mesh &m, int n, double dt, double theta, const double2 *h,
+                              const double2 *U, const double2 *V, const double2 *Gprev,
+                              const double2 *Iprev, const double2 *Icur, double2 *out,
+                              cudaStream_t st) {
   const size_t blk = (size_t)m.nb * m.nb * m.nk;
   const size_t total = (size_t)n * 2 * blk;
   const int threads = 256;
@@ -497,8 +549,8 @@ cudaError_t launch_update_row(const Mesh &m, int n, double dt, double theta, con
   KBE_NB_SWITCH(m.nb, (update_rows_kernel<NB><<<blocks, threads, 0, st>>>(n, m.nk, theta, U, V, Gprev, Iprev, ic, out)));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int tdiag = 64, bdiag = (m.nk + tdiag - 1) / tdiag;
-  KBE_NB_SWITCH(m.nb, (update_diag_kernel<NB><<<bdiag, tdiag, 0, st>>>(n, m.nk, dt, theta, U, W, lam, Gprev, Iprev, ic, out)));
+  KBE_NB_SWITCH(m.nb, (update_diag_kernel<NB><<<matgroup_blocks<NB>(m.nk), matgroup_threads<NB>(), 0, st>>>(
+                          n, m.nk, dt, theta, h, Gprev, Iprev, ic, out)));
   return cudaGetLastError();
 }
 

@@ -10,9 +10,11 @@
 // i.e. 24 n^2 N_b^3 n_k flops for n^2 N_b^2 n_k complex numbers read: about
 // 1.5 N_b flop per byte in FP64, far right of the FP64 ridge on GB300 (the
 // FP64 pipe is ~1.2 TFLOP/s against ~7 TB/s of HBM, and the FP32 pipe ~61x
-// the FP64 one). Three arithmetic forms share one thread mapping -- every
-// thread owns one (k, a) output row of both components and streams the l
-// sum; the N_b threads sharing a k read the same block through L1:
+// the FP64 one). Three arithmetic forms share one kernel template: every
+// thread owns one output element (k, a, b) of both components and streams
+// the l sum (threads sharing k and b read the same block column through L1);
+// when the grid would be too small to fill the GPU, the l range is split over
+// several CTAs and the partial sums are reduced in FP64 by a second kernel:
 //   FP64 : complex128 history, DFMA.
 //   DF64 : history as FP32 (hi, lo) pairs; each real product x*y is split
 //          exactly (p = fl(xh*yh), e = fma(xh, yh, -p) + xh*yl + xl*yh) and
@@ -20,7 +22,7 @@
 //          ~2^-44 relative accuracy at FP32-pipe speed.
 //   C64  : complex64 history, FP32 partial products per l, partial sums
 //          added into a compensated (TwoSum) accumulator.
-// For DF64 / C64 the Sigma row is first turned into three coefficient rows
+// The Sigma row is first turned into three coefficient rows
 // C1 = w^(n)_l (S^> - S^<), C2^< = dt S^<, C2^> = dt S^> in the history's
 // storage; the term-2 weights w^(j)_l / dt are then exact powers of two.
 #include "kbe_internal.cuh"
@@ -29,66 +31,26 @@ namespace kbe {
 
 namespace {
 
-// ---------------------------------------------------------------- FP64 ----
-template <int NB>
-__global__ void __launch_bounds__(128) sweep_f64_kernel(const double2 *__restrict__ H,
-                                                        const double2 *__restrict__ Sig,
-                                                        double2 *__restrict__ Iout, int n, int nk,
-                                                        double dt) {
-  const int j = blockIdx.x;
-  const int idx = blockIdx.y * blockDim.x + threadIdx.x;
-  if (idx >= NB * nk) return;
-  const int a = idx / nk;
-  const int k = idx - a * nk;
-  const size_t blk = (size_t)NB * NB * nk;
-
-  double2 accL[NB], accG[NB];
-#pragma unroll
-  for (int b = 0; b < NB; ++b) accL[b] = accG[b] = make_double2(0.0, 0.0);
-
-  for (int l = 0; l <= n; ++l) {
-    const double2 *sl = Sig + (size_t)l * 2 * blk + (size_t)a * NB * nk + k;   // S^<(n,l)_{a,.}
-    const double2 *sg = sl + blk;
-    const double w1 = trap_weight(n, l, dt);
-    const double w2 = (l <= j) ? trap_weight(j, l, dt) : 0.0;
-    const bool lower = (l >= j);
-    const double2 *gl = H + (lower ? tri(l, j) : tri(j, l)) * 2 * blk + k;
-    const double2 *gg = gl + blk;
-#pragma unroll 1
-    for (int c = 0; c < NB; ++c) {
-      const double2 s_l = sl[(size_t)c * nk];
-      const double2 s_g = sg[(size_t)c * nk];
-      const double2 a1 = c_scale(w1, c_sub(s_g, s_l));
-      const double2 a2l = c_scale(w2, s_l);
-      const double2 a2g = c_scale(w2, s_g);
-#pragma unroll
-      for (int b = 0; b < NB; ++b) {
-        double2 Bl, Bg;
-        if (lower) {   // G(l,j)_cb stored directly
-          Bl = gl[(size_t)(c * NB + b) * nk];
-          Bg = gg[(size_t)(c * NB + b) * nk];
-        } else {       // G(l,j)_cb = -conj(G(j,l)_bc)
-          Bl = c_neg(c_conj(gl[(size_t)(b * NB + c) * nk]));
-          Bg = c_neg(c_conj(gg[(size_t)(b * NB + c) * nk]));
-        }
-        accL[b] = c_fma(a1, Bl, accL[b]);
-        accG[b] = c_fma(a1, Bg, accG[b]);
-        if (w2 != 0.0) {
-          const double2 d = c_sub(Bl, Bg);
-          accL[b] = c_fma(a2l, d, accL[b]);
-          accG[b] = c_fma(a2g, d, accG[b]);
-        }
-      }
-    }
-  }
-  double2 *il = Iout + (size_t)j * 2 * blk + (size_t)a * NB * nk + k;
-  double2 *ig = il + blk;
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    il[(size_t)b * nk] = accL[b];
-    ig[(size_t)b * nk] = accG[b];
-  }
+// term-2 weight w^(j)_l / dt: 0 above the diagonal or for j = 0, 1/2 at the
+// trapezoid ends, 1 inside
+__device__ __forceinline__ float term2_factor(int j, int l) {
+  if (j == 0 || l > j) return 0.f;
+  return (l == 0 || l == j) ? 0.5f : 1.f;
 }
+
+// ---------------------------------------------------------------- FP64 ----
+struct ArithF64 {
+  using S = double2;   // stored complex
+  using A = double2;   // accumulator
+  static __device__ __forceinline__ void zero(A &a) { a = make_double2(0.0, 0.0); }
+  static __device__ __forceinline__ void begin(A &) {}
+  static __device__ __forceinline__ void end(A &) {}
+  static __device__ __forceinline__ void mac(A &a, const S &x, const S &y) { a = c_fma(x, y, a); }
+  static __device__ __forceinline__ S sub(const S &x, const S &y) { return c_sub(x, y); }
+  static __device__ __forceinline__ S negconj(const S &x) { return make_double2(-x.x, x.y); }
+  static __device__ __forceinline__ S scale(float f, const S &x) { return c_scale((double)f, x); }
+  static __device__ __forceinline__ double2 result(const A &a) { return a; }
+};
 
 // ---------------------------------------------------------------- DF64 ----
 // A complex double-float is float4 {re_hi, re_lo, im_hi, im_lo}. The explicit
@@ -108,14 +70,6 @@ __device__ __forceinline__ void df_mac(float &ah, float &al, float xh, float xl,
   al = __fadd_rn(al, __fadd_rn(e, pe));
 }
 
-// acc += X * Y (complex double-float)
-__device__ __forceinline__ void cdf_mac(float4 &acc, const float4 &X, const float4 &Y) {
-  df_mac(acc.x, acc.y, X.x, X.y, Y.x, Y.y);
-  df_mac(acc.x, acc.y, -X.z, -X.w, Y.z, Y.w);
-  df_mac(acc.z, acc.w, X.x, X.y, Y.z, Y.w);
-  df_mac(acc.z, acc.w, X.z, X.w, Y.x, Y.y);
-}
-
 // (sh, sl) = (ah + al) - (bh + bl), renormalised with TwoSum
 __device__ __forceinline__ void df_sub(float &sh, float &sl, float ah, float al, float bh, float bl) {
   const float s = __fsub_rn(ah, bh);
@@ -128,99 +82,47 @@ __device__ __forceinline__ void df_sub(float &sh, float &sl, float ah, float al,
   sh = t;
 }
 
-__device__ __forceinline__ float4 cdf_sub(const float4 &A, const float4 &B) {
-  float4 r;
-  df_sub(r.x, r.y, A.x, A.y, B.x, B.y);
-  df_sub(r.z, r.w, A.z, A.w, B.z, B.w);
-  return r;
+// (h, l) <- TwoSum(h, l): renormalise so that |l| <= ulp(h) / 2
+__device__ __forceinline__ void df_renorm(float &h, float &l) {
+  const float s = __fadd_rn(h, l);
+  const float bb = __fsub_rn(s, h);
+  l = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(l, bb));
+  h = s;
 }
 
-__device__ __forceinline__ float4 cdf_negconj(const float4 &A) {
-  return make_float4(-A.x, -A.y, A.z, A.w);
-}
-
-__device__ __forceinline__ float4 cdf_scale2(float f, const float4 &A) {   // f a power of two
-  return make_float4(f * A.x, f * A.y, f * A.z, f * A.w);
-}
-
-__device__ __forceinline__ double2 cdf_to_double(const float4 &A) {
-  return make_double2((double)A.x + (double)A.y, (double)A.z + (double)A.w);
-}
-
-// term-2 weight w^(j)_l / dt: 0 above the diagonal or for j = 0, 1/2 at the
-// trapezoid ends, 1 inside
-__device__ __forceinline__ float term2_factor(int j, int l) {
-  if (j == 0 || l > j) return 0.f;
-  return (l == 0 || l == j) ? 0.5f : 1.f;
-}
-
-template <int NB>
-__global__ void __launch_bounds__(128) sweep_df64_kernel(const float4 *__restrict__ H,
-                                                         const float4 *__restrict__ Cf,
-                                                         double2 *__restrict__ Iout, int n,
-                                                         int nk) {
-  const int j = blockIdx.x;
-  const int idx = blockIdx.y * blockDim.x + threadIdx.x;
-  if (idx >= NB * nk) return;
-  const int a = idx / nk;
-  const int k = idx - a * nk;
-  const size_t blk = (size_t)NB * NB * nk;
-
-  float4 accL[NB], accG[NB];
-#pragma unroll
-  for (int b = 0; b < NB; ++b) accL[b] = accG[b] = make_float4(0.f, 0.f, 0.f, 0.f);
-
-  for (int l = 0; l <= n; ++l) {
-    const float4 *c1 = Cf + (size_t)l * 3 * blk + (size_t)a * NB * nk + k;
-    const float4 *c2l = c1 + blk;
-    const float4 *c2g = c1 + 2 * blk;
-    const float f = term2_factor(j, l);
-    const bool lower = (l >= j);
-    const float4 *gl = H + (lower ? tri(l, j) : tri(j, l)) * 2 * blk + k;
-    const float4 *gg = gl + blk;
-#pragma unroll 1
-    for (int c = 0; c < NB; ++c) {
-      const float4 A1 = c1[(size_t)c * nk];
-      float4 B2l = make_float4(0.f, 0.f, 0.f, 0.f), B2g = B2l;
-      if (f != 0.f) {
-        B2l = cdf_scale2(f, c2l[(size_t)c * nk]);
-        B2g = cdf_scale2(f, c2g[(size_t)c * nk]);
-      }
-#pragma unroll
-      for (int b = 0; b < NB; ++b) {
-        float4 Gl, Gg;
-        if (lower) {
-          Gl = gl[(size_t)(c * NB + b) * nk];
-          Gg = gg[(size_t)(c * NB + b) * nk];
-        } else {
-          Gl = cdf_negconj(gl[(size_t)(b * NB + c) * nk]);
-          Gg = cdf_negconj(gg[(size_t)(b * NB + c) * nk]);
-        }
-        cdf_mac(accL[b], A1, Gl);
-        cdf_mac(accG[b], A1, Gg);
-        if (f != 0.f) {
-          const float4 D = cdf_sub(Gl, Gg);
-          cdf_mac(accL[b], B2l, D);
-          cdf_mac(accG[b], B2g, D);
-        }
-      }
-    }
+struct ArithDF64 {
+  using S = float4;
+  using A = float4;
+  static __device__ __forceinline__ void zero(A &a) { a = make_float4(0.f, 0.f, 0.f, 0.f); }
+  static __device__ __forceinline__ void begin(A &) {}
+  // after each memory-time node: keep the low word within a few ulps of the
+  // high one, so its own FP32 rounding stays at the 2^-48 level over any n
+  static __device__ __forceinline__ void end(A &a) {
+    df_renorm(a.x, a.y);
+    df_renorm(a.z, a.w);
   }
-  double2 *il = Iout + (size_t)j * 2 * blk + (size_t)a * NB * nk + k;
-  double2 *ig = il + blk;
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    il[(size_t)b * nk] = cdf_to_double(accL[b]);
-    ig[(size_t)b * nk] = cdf_to_double(accG[b]);
+  static __device__ __forceinline__ void mac(A &acc, const S &X, const S &Y) {
+    df_mac(acc.x, acc.y, X.x, X.y, Y.x, Y.y);
+    df_mac(acc.x, acc.y, -X.z, -X.w, Y.z, Y.w);
+    df_mac(acc.z, acc.w, X.x, X.y, Y.z, Y.w);
+    df_mac(acc.z, acc.w, X.z, X.w, Y.x, Y.y);
   }
-}
+  static __device__ __forceinline__ S sub(const S &X, const S &Y) {
+    float4 r;
+    df_sub(r.x, r.y, X.x, X.y, Y.x, Y.y);
+    df_sub(r.z, r.w, X.z, X.w, Y.z, Y.w);
+    return r;
+  }
+  static __device__ __forceinline__ S negconj(const S &X) { return make_float4(-X.x, -X.y, X.z, X.w); }
+  static __device__ __forceinline__ S scale(float f, const S &X) {   // f a power of two: exact
+    return make_float4(f * X.x, f * X.y, f * X.z, f * X.w);
+  }
+  static __device__ __forceinline__ double2 result(const A &a) {
+    return make_double2((double)a.x + (double)a.y, (double)a.z + (double)a.w);
+  }
+};
 
 // ----------------------------------------------------------------- C64 ----
-__device__ __forceinline__ float2 cf_fma(float2 a, float2 b, float2 acc) {
-  return make_float2(__fmaf_rn(a.x, b.x, __fmaf_rn(-a.y, b.y, acc.x)),
-                     __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, acc.y)));
-}
-
 // (h, c) += p with an error-free TwoSum; c collects the rounding errors
 __device__ __forceinline__ void comp_add(float &h, float &c, float p) {
   const float s = __fadd_rn(h, p);
@@ -230,76 +132,103 @@ __device__ __forceinline__ void comp_add(float &h, float &c, float p) {
   c = __fadd_rn(c, e);
 }
 
-template <int NB>
-__global__ void __launch_bounds__(128) sweep_c64_kernel(const float2 *__restrict__ H,
-                                                        const float2 *__restrict__ Cf,
-                                                        double2 *__restrict__ Iout, int n,
-                                                        int nk) {
+struct AccC64 {
+  float4 sum;    // {re, re_comp, im, im_comp}, compensated over l
+  float2 part;   // plain FP32 partial of the current l
+};
+
+struct ArithC64 {
+  using S = float2;
+  using A = AccC64;
+  static __device__ __forceinline__ void zero(A &a) { a.sum = make_float4(0.f, 0.f, 0.f, 0.f); }
+  static __device__ __forceinline__ void begin(A &a) { a.part = make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ void end(A &a) {
+    comp_add(a.sum.x, a.sum.y, a.part.x);
+    comp_add(a.sum.z, a.sum.w, a.part.y);
+  }
+  static __device__ __forceinline__ void mac(A &a, const S &x, const S &y) {
+    a.part = make_float2(__fmaf_rn(x.x, y.x, __fmaf_rn(-x.y, y.y, a.part.x)),
+                         __fmaf_rn(x.x, y.y, __fmaf_rn(x.y, y.x, a.part.y)));
+  }
+  static __device__ __forceinline__ S sub(const S &x, const S &y) { return make_float2(x.x - y.x, x.y - y.y); }
+  static __device__ __forceinline__ S negconj(const S &x) { return make_float2(-x.x, x.y); }
+  static __device__ __forceinline__ S scale(float f, const S &x) { return make_float2(f * x.x, f * x.y); }
+  static __device__ __forceinline__ double2 result(const A &a) {
+    return make_double2((double)a.sum.x + (double)a.sum.y, (double)a.sum.z + (double)a.sum.w);
+  }
+};
+
+// ------------------------------------------------------------ the sweep ----
+// grid: x = output column j (0..n), y = tiles of the N_b^2 n_k output
+// elements, z = split of the l range (lchunk values each). out is the I row
+// when gridDim.z == 1, else the partial-sum scratch [z][j][x][a][b][k].
+template <class P, int NB>
+__global__ void __launch_bounds__(256) sweep_kernel(const typename P::S *__restrict__ H,
+                                                    const typename P::S *__restrict__ Cf,
+                                                    double2 *__restrict__ out, int n, int nk,
+                                                    int lchunk) {
+  using S = typename P::S;
   const int j = blockIdx.x;
   const int idx = blockIdx.y * blockDim.x + threadIdx.x;
-  if (idx >= NB * nk) return;
-  const int a = idx / nk;
-  const int k = idx - a * nk;
+  if (idx >= NB * NB * nk) return;
+  const int k = idx % nk;
+  const int ab = idx / nk;
+  const int a = ab / NB, b = ab - (ab / NB) * NB;
+  const int l0 = blockIdx.z * lchunk;
+  const int l1 = min(n + 1, l0 + lchunk);
   const size_t blk = (size_t)NB * NB * nk;
 
-  float4 accL[NB], accG[NB];   // {re, re_comp, im, im_comp}
-#pragma unroll
-  for (int b = 0; b < NB; ++b) accL[b] = accG[b] = make_float4(0.f, 0.f, 0.f, 0.f);
-
-  for (int l = 0; l <= n; ++l) {
-    const float2 *c1 = Cf + (size_t)l * 3 * blk + (size_t)a * NB * nk + k;
-    const float2 *c2l = c1 + blk;
-    const float2 *c2g = c1 + 2 * blk;
+  typename P::A accL, accG;
+  P::zero(accL);
+  P::zero(accG);
+  for (int l = l0; l < l1; ++l) {
+    const S *c1 = Cf + (size_t)l * 3 * blk + (size_t)a * NB * nk + k;   // C1(l)_{a, .}
     const float f = term2_factor(j, l);
     const bool lower = (l >= j);
-    const float2 *gl = H + (lower ? tri(l, j) : tri(j, l)) * 2 * blk + k;
-    const float2 *gg = gl + blk;
-    float2 pL[NB], pG[NB];
+    const S *g = H + (lower ? tri(l, j) : tri(j, l)) * 2 * blk + k;
+    P::begin(accL);
+    P::begin(accG);
 #pragma unroll
-    for (int b = 0; b < NB; ++b) pL[b] = pG[b] = make_float2(0.f, 0.f);
-#pragma unroll 1
     for (int c = 0; c < NB; ++c) {
-      const float2 A1 = c1[(size_t)c * nk];
-      float2 B2l = make_float2(0.f, 0.f), B2g = B2l;
-      if (f != 0.f) {
-        const float2 u = c2l[(size_t)c * nk], w = c2g[(size_t)c * nk];
-        B2l = make_float2(f * u.x, f * u.y);
-        B2g = make_float2(f * w.x, f * w.y);
+      const S A1 = c1[(size_t)c * nk];
+      S Gl, Gg;
+      if (lower) {   // G(l, j)_cb stored directly
+        Gl = g[(size_t)(c * NB + b) * nk];
+        Gg = g[blk + (size_t)(c * NB + b) * nk];
+      } else {       // G(l, j)_cb = -conj(G(j, l)_bc)
+        Gl = P::negconj(g[(size_t)(b * NB + c) * nk]);
+        Gg = P::negconj(g[blk + (size_t)(b * NB + c) * nk]);
       }
-#pragma unroll
-      for (int b = 0; b < NB; ++b) {
-        float2 Gl, Gg;
-        if (lower) {
-          Gl = gl[(size_t)(c * NB + b) * nk];
-          Gg = gg[(size_t)(c * NB + b) * nk];
-        } else {
-          const float2 u = gl[(size_t)(b * NB + c) * nk], w = gg[(size_t)(b * NB + c) * nk];
-          Gl = make_float2(-u.x, u.y);
-          Gg = make_float2(-w.x, w.y);
+      P::mac(accL, A1, Gl);
+      P::mac(accG, A1, Gg);
+      if (f != 0.f) {   // f is uniform over the CTA; only l = 0, j take the 1/2
+        S B2l = c1[blk + (size_t)c * nk];
+        S B2g = c1[2 * blk + (size_t)c * nk];
+        if (f != 1.f) {
+          B2l = P::scale(f, B2l);
+          B2g = P::scale(f, B2g);
         }
-        pL[b] = cf_fma(A1, Gl, pL[b]);
-        pG[b] = cf_fma(A1, Gg, pG[b]);
-        if (f != 0.f) {
-          const float2 D = make_float2(Gl.x - Gg.x, Gl.y - Gg.y);
-          pL[b] = cf_fma(B2l, D, pL[b]);
-          pG[b] = cf_fma(B2g, D, pG[b]);
-        }
+        const S D = P::sub(Gl, Gg);
+        P::mac(accL, B2l, D);
+        P::mac(accG, B2g, D);
       }
     }
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-      comp_add(accL[b].x, accL[b].y, pL[b].x);
-      comp_add(accL[b].z, accL[b].w, pL[b].y);
-      comp_add(accG[b].x, accG[b].y, pG[b].x);
-      comp_add(accG[b].z, accG[b].w, pG[b].y);
-    }
+    P::end(accL);
+    P::end(accG);
   }
-  double2 *il = Iout + (size_t)j * 2 * blk + (size_t)a * NB * nk + k;
-  double2 *ig = il + blk;
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    il[(size_t)b * nk] = cdf_to_double(accL[b]);
-    ig[(size_t)b * nk] = cdf_to_double(accG[b]);
+  double2 *o = out + ((size_t)blockIdx.z * (n + 1) + j) * 2 * blk + (size_t)ab * nk + k;
+  o[0] = P::result(accL);
+  o[blk] = P::result(accG);
+}
+
+// I = sum over the z partial rows (FP64)
+__global__ void reduce_partials_kernel(const double2 *__restrict__ part, double2 *__restrict__ I,
+                                       size_t count, int nz) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x) {
+    double2 s = part[i];
+    for (int z = 1; z < nz; ++z) s = c_add(s, part[(size_t)z * count + i]);
+    I[i] = s;
   }
 }
 
@@ -334,28 +263,62 @@ __global__ void coef_kernel(int prec, const double2 *__restrict__ Sig, void *__r
     for (int q = 0; q < 3; ++q) {
       const size_t o = (l * 3 + q) * blk + r;
       if (prec == KBE_PREC_DF64) ((float4 *)Cf)[o] = split_df(v[q]);
-      else ((float2 *)Cf)[o] = make_float2((float)v[q].x, (float)v[q].y);
+      else if (prec == KBE_PREC_C64) ((float2 *)Cf)[o] = make_float2((float)v[q].x, (float)v[q].y);
+      else ((double2 *)Cf)[o] = v[q];
     }
   }
-}
-
-template <int NB>
-cudaError_t sweep_nb(const Mesh &m, int n, double dt, int prec, const void *H, const double2 *Sig,
-                     const void *Cf, double2 *I, cudaStream_t st) {
-  const int threads = 128;
-  dim3 grid(n + 1, (NB * m.nk + threads - 1) / threads);
-  if (prec == KBE_PREC_FP64)
-    sweep_f64_kernel<NB><<<grid, threads, 0, st>>>((const double2 *)H, Sig, I, n, m.nk, dt);
-  else if (prec == KBE_PREC_DF64)
-    sweep_df64_kernel<NB><<<grid, threads, 0, st>>>((const float4 *)H, (const float4 *)Cf, I, n, m.nk);
-  else
-    sweep_c64_kernel<NB><<<grid, threads, 0, st>>>((const float2 *)H, (const float2 *)Cf, I, n, m.nk);
-  return cudaGetLastError();
 }
 
 unsigned grid_for(size_t count) {
   size_t b = (count + 255) / 256;
   return (unsigned)(b < 152 * 64 ? (b ? b : 1) : 152 * 64);
+}
+
+// l-split: enough CTAs to give every SM ~8 resident CTAs; the number of
+// partial rows nz (n+1) stays below 2(n+1) + 1024
+constexpr int kTargetCtas = 152 * 8;
+
+struct SweepShape {
+  dim3 grid;
+  int threads, lchunk, nz;
+};
+
+SweepShape sweep_shape(const Mesh &m, int n) {
+  SweepShape sh;
+  const long elems = (long)m.nb * m.nb * m.nk;
+  sh.threads = elems >= 256 ? 256 : (int)((elems + 31) / 32) * 32;
+  const long ty = (elems + sh.threads - 1) / sh.threads;
+  const long base = (long)(n + 1) * ty;
+  long nz = (kTargetCtas + base - 1) / base;
+  if (nz > n + 1) nz = n + 1;                        // at least one l per split
+  if (nz > 2 + 1024 / (n + 1)) nz = 2 + 1024 / (n + 1);   // bounds the partial-sum scratch
+  if (nz < 1) nz = 1;
+  sh.lchunk = (int)((n + 1 + nz - 1) / nz);
+  sh.nz = (int)((n + 1 + sh.lchunk - 1) / sh.lchunk);
+  sh.grid = dim3(n + 1, (unsigned)ty, (unsigned)sh.nz);
+  return sh;
+}
+
+template <class P, int NB>
+cudaError_t sweep_nb(const Mesh &m, int n, const void *H, const void *Cf, double2 *I, double2 *part,
+                     cudaStream_t st) {
+  const SweepShape sh = sweep_shape(m, n);
+  double2 *out = sh.nz > 1 ? part : I;
+  sweep_kernel<P, NB><<<sh.grid, sh.threads, 0, st>>>((const typename P::S *)H,
+                                                      (const typename P::S *)Cf, out, n, m.nk, sh.lchunk);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || sh.nz == 1) return e;
+  const size_t count = (size_t)(n + 1) * 2 * m.nb * m.nb * m.nk;
+  reduce_partials_kernel<<<grid_for(count), 256, 0, st>>>(part, I, count, sh.nz);
+  return cudaGetLastError();
+}
+
+template <int NB>
+cudaError_t sweep_prec(const Mesh &m, int n, int prec, const void *H, const void *Cf, double2 *I,
+                       double2 *part, cudaStream_t st) {
+  if (prec == KBE_PREC_FP64) return sweep_nb<ArithF64, NB>(m, n, H, Cf, I, part, st);
+  if (prec == KBE_PREC_DF64) return sweep_nb<ArithDF64, NB>(m, n, H, Cf, I, part, st);
+  return sweep_nb<ArithC64, NB>(m, n, H, Cf, I, part, st);
 }
 
 }  // namespace
@@ -373,10 +336,24 @@ bool precision_supported(int prec) {
 
 size_t history_elem_bytes(int prec) { return prec == KBE_PREC_C64 ? sizeof(float2) : 16; }
 
+// coefficient rows (n+1) x 3 blocks in the storage format, then the partial
+// sums of the l split (FP64)
 size_t sweep_workspace_bytes(const Mesh &m, int n, int prec) {
-  if (prec == KBE_PREC_FP64) return 0;
-  return (size_t)(n + 1) * 3 * m.nb * m.nb * m.nk * history_elem_bytes(prec);
+  const size_t blk = (size_t)m.nb * m.nb * m.nk;
+  size_t coef = (size_t)(n + 1) * 3 * blk * history_elem_bytes(prec);
+  coef = (coef + 255) / 256 * 256;
+  size_t part = 0;
+  for (int r = 0; r <= n; ++r) {   // the largest partial buffer over rows 0..n
+    const SweepShape sh = sweep_shape(m, r);
+    if (sh.nz > 1) {
+      const size_t b = (size_t)sh.nz * (r + 1) * 2 * blk * sizeof(double2);
+      if (b > part) part = b;
+    }
+  }
+  return coef + part;
 }
+
+int sweep_splits(const Mesh &m, int n) { return sweep_shape(m, n).nz; }
 
 cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t count, cudaStream_t st) {
   if (count == 0) return cudaSuccess;
@@ -387,21 +364,23 @@ cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t count, c
 cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const void *H,
                          const double2 *Sig, double2 *I, void *work, cudaStream_t st) {
   if (!precision_supported(precision)) return cudaErrorInvalidValue;
-  if (precision != KBE_PREC_FP64) {
-    const size_t total = (size_t)(n + 1) * m.nb * m.nb * m.nk;
-    coef_kernel<<<grid_for(total), 256, 0, st>>>(precision, Sig, work, n, m.nk, m.nb * m.nb, dt);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
+  const size_t blk = (size_t)m.nb * m.nb * m.nk;
+  const size_t total = (size_t)(n + 1) * blk;
+  coef_kernel<<<grid_for(total), 256, 0, st>>>(precision, Sig, work, n, m.nk, m.nb * m.nb, dt);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  size_t coef = (size_t)(n + 1) * 3 * blk * history_elem_bytes(precision);
+  coef = (coef + 255) / 256 * 256;
+  double2 *part = (double2 *)((char *)work + coef);
   switch (m.nb) {
-    case 1: return sweep_nb<1>(m, n, dt, precision, H, Sig, work, I, st);
-    case 2: return sweep_nb<2>(m, n, dt, precision, H, Sig, work, I, st);
-    case 3: return sweep_nb<3>(m, n, dt, precision, H, Sig, work, I, st);
-    case 4: return sweep_nb<4>(m, n, dt, precision, H, Sig, work, I, st);
-    case 6: return sweep_nb<6>(m, n, dt, precision, H, Sig, work, I, st);
-    case 8: return sweep_nb<8>(m, n, dt, precision, H, Sig, work, I, st);
-    case 12: return sweep_nb<12>(m, n, dt, precision, H, Sig, work, I, st);
-    case 16: return sweep_nb<16>(m, n, dt, precision, H, Sig, work, I, st);
+    case 1: return sweep_prec<1>(m, n, precision, H, work, I, part, st);
+    case 2: return sweep_prec<2>(m, n, precision, H, work, I, part, st);
+    case 3: return sweep_prec<3>(m, n, precision, H, work, I, part, st);
+    case 4: return sweep_prec<4>(m, n, precision, H, work, I, part, st);
+    case 6: return sweep_prec<6>(m, n, precision, H, work, I, part, st);
+    case 8: return sweep_prec<8>(m, n, precision, H, work, I, part, st);
+    case 12: return sweep_prec<12>(m, n, precision, H, work, I, part, st);
+    case 16: return sweep_prec<16>(m, n, precision, H, work, I, part, st);
     default: return cudaErrorInvalidValue;
   }
 }

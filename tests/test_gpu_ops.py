@@ -66,7 +66,8 @@ def test_collision_row_matches_oracle(nb, L, n):
     H = dev(to_dev_blocks(Hl, Hg))
     S = dev(to_dev_blocks(Sl, Sg))
     I = torch.full((n + 1, 2, nb, nb, nk), float("nan"), dtype=torch.complex128, device="cuda")
-    kbe.collision_row(nb, L, n, dt, H, S, I)
+    work = torch.empty(kbe.collision_row_workspace(nb, L, n) // 4 + 1, dtype=torch.float32, device="cuda")
+    kbe.collision_row(nb, L, n, dt, H, S, I, work=work)
     torch.cuda.synchronize()
     gl, gg = from_dev_blocks(I.cpu().numpy())
     assert relerr(gl, Il)[1] < TOL and relerr(gg, Ig)[1] < TOL
@@ -77,35 +78,35 @@ def _herm_batch(rng, nk, nb, scale=1.5):
     return 0.5 * (a + np.conj(np.swapaxes(a, 1, 2)))
 
 
-@pytest.mark.parametrize("nb,nk", [(1, 3), (2, 65), (4, 64), (6, 7), (8, 33), (12, 5), (16, 3)])
-def test_propagators_match_oracle(nb, nk):
+@pytest.mark.parametrize("nb,nk,dt,scale", [(1, 3, 0.02, 1.5), (2, 65, 0.02, 1.5), (4, 64, 0.02, 1.5),
+                                         (6, 7, 0.02, 1.5), (8, 33, 0.05, 3.0), (12, 5, 0.02, 1.5),
+                                         (16, 3, 0.02, 1.5), (4, 9, 0.7, 4.0), (3, 5, 2.5, 8.0)])
+def test_propagators_match_oracle(nb, nk, dt, scale):
+    """U, V against the oracle's eigen-decomposition route; the last two cases
+    have dt ||h|| >> 1 and exercise the doublings."""
     rng = np.random.default_rng(300 + nb)
-    dt = 0.02
-    h = _herm_batch(rng, nk, nb)
+    h = _herm_batch(rng, nk, nb, scale)
     h[0] = np.diag(np.linspace(-1, 1, nb))                     # already diagonal
     if nb >= 2:
         h[1] = np.diag(np.r_[np.zeros(nb - 1), 0.7])           # degenerate zero eigenvalues
     U, V, W, lam = oracle.propagators(nb, nk, dt, h)
     L = (nk, 1)
     hd = dev(to_dev_perk(h))
-    Ud, Vd, Wd = torch.empty_like(hd), torch.empty_like(hd), torch.empty_like(hd)
-    ld = torch.empty((nb, nk), dtype=torch.float64, device="cuda")
-    kbe.propagators(nb, L, dt, hd, Ud, Vd, Wd, ld)
+    Ud, Vd = torch.empty_like(hd), torch.empty_like(hd)
+    kbe.propagators(nb, L, dt, hd, Ud, Vd)
     torch.cuda.synchronize()
-    Ug, Vg, Wg = (from_dev_perk(x.cpu().numpy()) for x in (Ud, Vd, Wd))
-    lg = ld.cpu().numpy().T
-    assert np.abs(Ug - U).max() < 1e-13
-    assert np.abs(Vg - V).max() < 1e-13
-    assert np.abs(np.sort(lg, 1) - np.sort(lam, 1)).max() < 1e-13
-    rec = np.einsum("kac,kc,kbc->kab", Wg, lg, np.conj(Wg))
-    assert np.abs(rec - h).max() < 1e-13
+    Ug, Vg = (from_dev_perk(x.cpu().numpy()) for x in (Ud, Vd))
+    tol = 1e-13 * max(1.0, dt * scale * nb)
+    assert np.abs(Ug - U).max() < tol
+    assert np.abs(Vg - V).max() < tol * max(dt, 1.0)
 
 
-@pytest.mark.parametrize("nb,nk,n,theta", [(2, 8, 1, 0.0), (2, 8, 9, 0.5), (4, 64, 6, 0.5),
-                                          (3, 9, 4, 0.0), (8, 5, 3, 0.5), (16, 2, 2, 0.5)])
-def test_update_row_matches_oracle(nb, nk, n, theta):
+@pytest.mark.parametrize("nb,nk,n,theta,dt", [(2, 8, 1, 0.0, 0.04), (2, 8, 9, 0.5, 0.04),
+                                              (4, 64, 6, 0.5, 0.04), (3, 9, 4, 0.0, 0.04),
+                                              (8, 5, 3, 0.5, 0.04), (16, 2, 2, 0.5, 0.04),
+                                              (4, 7, 3, 0.5, 0.9)])
+def test_update_row_matches_oracle(nb, nk, n, theta, dt):
     rng = np.random.default_rng(400 + nb + n)
-    dt = 0.04
     h = _herm_batch(rng, nk, nb)
     U, V, W, lam = oracle.propagators(nb, nk, dt, h)
     Gpl = ki.random_blocks(rng, (n, nk, nb, nb))
@@ -117,9 +118,9 @@ def test_update_row_matches_oracle(nb, nk, n, theta):
     ol, og = oracle.update_row(nb, nk, n, dt, theta, U, V, W, lam, Gpl, Gpg, Ipl, Ipg, Icl, Icg)
     L = (nk, 1)
     out = torch.full((n + 1, 2, nb, nb, nk), float("nan"), dtype=torch.complex128, device="cuda")
-    kbe.update_row(nb, L, n, dt, theta, dev(to_dev_perk(U)), dev(to_dev_perk(V)), dev(to_dev_perk(W)),
-                   dev(np.ascontiguousarray(lam.T)), dev(to_dev_blocks(Gpl, Gpg)),
-                   dev(to_dev_blocks(Ipl, Ipg)), dev(to_dev_blocks(Icl, Icg)), out)
+    kbe.update_row(nb, L, n, dt, theta, dev(to_dev_perk(h)), dev(to_dev_perk(U)), dev(to_dev_perk(V)),
+                   dev(to_dev_blocks(Gpl, Gpg)), dev(to_dev_blocks(Ipl, Ipg)), dev(to_dev_blocks(Icl, Icg)),
+                   out)
     torch.cuda.synchronize()
     gl, gg = from_dev_blocks(out.cpu().numpy())
     assert relerr(gl, ol)[1] < 1e-13 and relerr(gg, og)[1] < 1e-13

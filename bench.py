@@ -85,6 +85,16 @@ def aggregate(times_s, units_per_rank):
     return sum(units_per_rank) / t, t
 
 
+def reduce_max(values, dist=None, device="cuda"):
+    """Element-wise max over ranks (timing only; no data-path collective)."""
+    if dist is None:
+        return list(values)
+    import torch
+    t = torch.tensor(values, device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms in a thread."""
 
@@ -217,11 +227,7 @@ def run_ours(args, rank, world, local):
     if dist:
         dist.barrier()
 
-    times = [t_dev, t_e2e]
-    if dist:
-        tt = torch.tensor(times, device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        times = tt.tolist()
+    times = reduce_max([t_dev, t_e2e], dist)
     units = nt * args.steps
     value, tmax = aggregate([times[0]], [units * world])
     e2e_value = units * world / times[1]

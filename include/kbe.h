@@ -74,7 +74,7 @@ typedef struct kbe_config {
   int nb;          /* bands N_b, one of 1,2,3,4,6,8,12,16                        */
   int dim;         /* 1 (ring, L[1] must be 1) or 2                              */
   int L[2];        /* mesh extents, n_k = L[0] * L[1] <= 4096                    */
-  int nt_max;      /* rows t_0 .. t_{nt_max} are stored                          */
+  int nt_max;      /* rows t_0 .. t_{nt_max} are stored, 1 <= nt_max <= 65534    */
   double dt;       /* time step (> 0)                                            */
   double beta, mu; /* Fermi initial state f(h0(k)) at inverse temperature beta  */
   int precision;   /* KBE_PREC_*                                                 */

@@ -301,7 +301,7 @@ kbe_status kbe_create(const kbe_config *cfg, void *stream, kbe_handle **out) {
   if (cfg->L[0] < 1 || cfg->L[1] < 1 || (cfg->dim == 1 && cfg->L[1] != 1))
     return fail(nullptr, KBE_ERR_ARG, "kbe_create: bad mesh extents");
   if ((long)cfg->L[0] * cfg->L[1] > kbe::kMaxNk) return fail(nullptr, KBE_ERR_ARG, "kbe_create: n_k > 4096");
-  if (cfg->nt_max < 1 || cfg->nt_max > 65535) return fail(nullptr, KBE_ERR_ARG, "kbe_create: nt_max out of range");
+  if (cfg->nt_max < 1 || cfg->nt_max > 65534) return fail(nullptr, KBE_ERR_ARG, "kbe_create: nt_max out of range");
   if (!(cfg->dt > 0.0) || !std::isfinite(cfg->dt)) return fail(nullptr, KBE_ERR_ARG, "kbe_create: dt must be > 0");
   if (!std::isfinite(cfg->beta) || !std::isfinite(cfg->mu)) return fail(nullptr, KBE_ERR_ARG, "kbe_create: beta/mu not finite");
   if (!kbe::precision_supported(cfg->precision)) return fail(nullptr, KBE_ERR_UNSUPPORTED, "kbe_create: unknown precision");

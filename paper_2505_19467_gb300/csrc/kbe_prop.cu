@@ -116,12 +116,14 @@ __device__ void bare_h(const HopTable &hop, int k, int L0, int L1, double A, dou
 }
 
 // ------------------------------------------------ per-k matrix functions ----
-// A CTA holds KPC = 256 / N_b^2 k-points; thread t works on element (a, b)
-// of k-point t / N_b^2. Matrices live in shared memory, [kk][a][b].
+// A CTA holds kpc k-points (chosen at launch so that the CTAs cover the SMs:
+// the series are FP64-pipe bound); thread t works on element (a, b) of
+// k-point t / N_b^2. Matrices live in dynamic shared memory, [kk][a][b].
+extern __shared__ double2 kbe_dsm[];
+
 template <int NB>
 struct MatGroup {
   static constexpr int E = NB * NB;
-  static constexpr int KPC = (256 / E) > 0 ? (256 / E) : 1;
   int kk, a, b, e;
   __device__ MatGroup() {
     kk = threadIdx.x / E;
@@ -152,7 +154,8 @@ struct MatGroup {
 // number of doublings s with (dt / 2^s) * max_k ||h_k||_rowsum <= 1/4, for
 // all k-points of the CTA (uniform across the CTA); h in shared memory
 template <int NB>
-__device__ int doublings(const MatGroup<NB> &g, const double2 *h, int nvalid, double dt, double *red) {
+__device__ int doublings(const MatGroup<NB> &g, const double2 *h, int kpc, int nvalid, double dt,
+                         double *red) {
   if (g.b == 0) {
     double r = 0.0;
     for (int c = 0; c < NB; ++c) {
@@ -165,7 +168,7 @@ __device__ int doublings(const MatGroup<NB> &g, const double2 *h, int nvalid, do
   __shared__ int s_sh;
   if (threadIdx.x == 0) {
     double nu = 0.0;
-    for (int i = 0; i < MatGroup<NB>::KPC * NB; ++i) nu = fmax(nu, red[i]);
+    for (int i = 0; i < kpc * NB; ++i) nu = fmax(nu, red[i]);
     nu *= dt;
     int sc = 0;
     while (nu > 0.25 && sc < 40) {   // bounded: nu <= 2^40 / 4 covers any finite h
@@ -216,14 +219,15 @@ __global__ void __launch_bounds__(256) build_props_kernel(Mesh m, HopTable hop, 
                                                           const double2 *__restrict__ hin, double dt,
                                                           double2 *__restrict__ hout,
                                                           double2 *__restrict__ U,
-                                                          double2 *__restrict__ V) {
+                                                          double2 *__restrict__ V, int kpc) {
   using G = MatGroup<NB>;
-  __shared__ double2 sh[4][G::KPC * G::E];
-  __shared__ double red[G::KPC * NB];
+  const int span = kpc * G::E;
+  double2 *sh[4] = {kbe_dsm, kbe_dsm + span, kbe_dsm + 2 * span, kbe_dsm + 3 * span};
+  double *red = (double *)(kbe_dsm + 4 * span);
   const G g;
-  const int k = blockIdx.x * G::KPC + g.kk;
-  const bool active = threadIdx.x < G::KPC * G::E && k < m.nk;
-  const int nvalid = min(G::KPC, m.nk - (int)blockIdx.x * G::KPC);
+  const int k = blockIdx.x * kpc + g.kk;
+  const bool active = k < m.nk;
+  const int nvalid = min(kpc, m.nk - (int)blockIdx.x * kpc);
   const int o = g.kk * G::E + g.e;
   double2 hv = make_double2(0.0, 0.0);
   if (active) {
@@ -253,9 +257,9 @@ __global__ void __launch_bounds__(256) build_props_kernel(Mesh m, HopTable hop, 
       if (p.paper_shift && g.a == NB - 1 && g.b == NB - 1) hv.x -= p.Umid;
     }
   }
-  if (threadIdx.x < G::KPC * G::E) sh[0][o] = hv;
+  sh[0][o] = hv;
   __syncthreads();
-  const int s = doublings<NB>(g, sh[0], nvalid, dt, red);
+  const int s = doublings<NB>(g, sh[0], kpc, nvalid, dt, red);
   const double tau = ldexp(dt, -s);
   double2 u, v;
   exp_and_phi<NB>(g, sh[0], tau, s, sh[1], sh[2], sh[3], u, v);
@@ -274,17 +278,18 @@ __global__ void __launch_bounds__(256) update_diag_kernel(int n, int nk, double 
                                                           const double2 *__restrict__ Gprev,
                                                           const double2 *__restrict__ Ip,
                                                           const double2 *__restrict__ Ic,
-                                                          double2 *__restrict__ out) {
+                                                          double2 *__restrict__ out, int kpc) {
   using G = MatGroup<NB>;
-  __shared__ double2 sh[5][G::KPC * G::E];
-  __shared__ double red[G::KPC * NB];
+  const int span = kpc * G::E;
+  double2 *H = kbe_dsm, *Qs = kbe_dsm + span, *T = kbe_dsm + 2 * span, *P = kbe_dsm + 3 * span,
+          *Wk = kbe_dsm + 4 * span;
+  double *red = (double *)(kbe_dsm + 5 * span);
   const G g;
-  const int k = blockIdx.x * G::KPC + g.kk;
-  const bool active = threadIdx.x < G::KPC * G::E && k < nk;
-  const int nvalid = min(G::KPC, nk - (int)blockIdx.x * G::KPC);
+  const int k = blockIdx.x * kpc + g.kk;
+  const bool active = k < nk;
+  const int nvalid = min(kpc, nk - (int)blockIdx.x * kpc);
   const int o = g.kk * G::E + g.e;
   const size_t blk = (size_t)G::E * nk;
-  double2 *H = sh[0], *Qs = sh[1], *T = sh[2], *P = sh[3], *Wk = sh[4];
   double2 hv = make_double2(0, 0), sv = make_double2(0, 0), gd = make_double2(0, 0);
   if (active) {
     const size_t oab = (size_t)g.e * nk + k, oba = (size_t)(g.b * NB + g.a) * nk + k;
@@ -297,12 +302,10 @@ __global__ void __launch_bounds__(256) update_diag_kernel(int n, int nk, double 
     }
     gd = Gprev[(size_t)(n - 1) * 2 * blk + oab];            // G^<(n-1, n-1)
   }
-  if (threadIdx.x < G::KPC * G::E) {
-    H[o] = hv;
-    Qs[o] = sv;
-  }
+  H[o] = hv;
+  Qs[o] = sv;
   __syncthreads();
-  const int s = doublings<NB>(g, H, nvalid, dt, red);
+  const int s = doublings<NB>(g, H, kpc, nvalid, dt, red);
   const double tau = ldexp(dt, -s);
   // X_tau = tau sum_m Q_m / (m+1), Q_m = (-i tau / m) [h, Q_{m-1}], Q_0 = Sbar
   double2 x = c_scale(tau, sv);
@@ -519,21 +522,34 @@ cudaError_t launch_local_density(const Mesh &m, const double2 *Gdiag, double2 *r
   return cudaGetLastError();
 }
 
-// one CTA of KPC * N_b^2 threads per KPC k-points
+// k-points per CTA: enough CTAs to cover the SMs, at most 256 threads
 template <int NB>
-unsigned matgroup_blocks(int nk) {
-  return (unsigned)((nk + MatGroup<NB>::KPC - 1) / MatGroup<NB>::KPC);
+int matgroup_kpc(int nk) {
+  const int E = NB * NB, maxk = 256 / E > 0 ? 256 / E : 1;
+  int kpc = (nk + 151) / 152;
+  return kpc < 1 ? 1 : (kpc > maxk ? maxk : kpc);
 }
 template <int NB>
-unsigned matgroup_threads() {
-  return (unsigned)(MatGroup<NB>::KPC * MatGroup<NB>::E);
+unsigned matgroup_blocks(int nk) {
+  const int kpc = matgroup_kpc<NB>(nk);
+  return (unsigned)((nk + kpc - 1) / kpc);
+}
+template <int NB>
+unsigned matgroup_threads(int nk) {
+  return (unsigned)(matgroup_kpc<NB>(nk) * NB * NB);
+}
+template <int NB>
+size_t matgroup_smem(int nk, int nmat) {
+  const int kpc = matgroup_kpc<NB>(nk);
+  return sizeof(double2) * (size_t)nmat * kpc * NB * NB + sizeof(double) * (size_t)kpc * NB;
 }
 
 cudaError_t launch_build_props(const Mesh &m, const HopTable &hop, const PropParams &p, double dt,
                                const double2 *h_in, double2 *h_out, double2 *U, double2 *V,
                                cudaStream_t st) {
-  KBE_NB_SWITCH(m.nb, (build_props_kernel<NB><<<matgroup_blocks<NB>(m.nk), matgroup_threads<NB>(), 0, st>>>(
-                          m, hop, p, h_in, dt, h_out, U, V)));
+  KBE_NB_SWITCH(m.nb, (build_props_kernel<NB><<<matgroup_blocks<NB>(m.nk), matgroup_threads<NB>(m.nk),
+                                                 matgroup_smem<NB>(m.nk, 4), st>>>(
+                          m, hop, p, h_in, dt, h_out, U, V, matgroup_kpc<NB>(m.nk))));
   return cudaGetLastError();
 }
 
@@ -549,8 +565,9 @@ cudaError_t launch_update_row(const Mesh &m, int n, double dt, double theta, con
   KBE_NB_SWITCH(m.nb, (update_rows_kernel<NB><<<blocks, threads, 0, st>>>(n, m.nk, theta, U, V, Gprev, Iprev, ic, out)));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  KBE_NB_SWITCH(m.nb, (update_diag_kernel<NB><<<matgroup_blocks<NB>(m.nk), matgroup_threads<NB>(), 0, st>>>(
-                          n, m.nk, dt, theta, h, Gprev, Iprev, ic, out)));
+  KBE_NB_SWITCH(m.nb, (update_diag_kernel<NB><<<matgroup_blocks<NB>(m.nk), matgroup_threads<NB>(m.nk),
+                                                 matgroup_smem<NB>(m.nk, 5), st>>>(
+                          n, m.nk, dt, theta, h, Gprev, Iprev, ic, out, matgroup_kpc<NB>(m.nk))));
   return cudaGetLastError();
 }
 

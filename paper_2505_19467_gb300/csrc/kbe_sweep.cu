@@ -159,17 +159,19 @@ struct ArithC64 {
 };
 
 // ------------------------------------------------------------ the sweep ----
-// grid: x = output column j (0..n), y = tiles of the N_b^2 n_k output
-// elements, z = split of the l range (lchunk values each). out is the I row
-// when gridDim.z == 1, else the partial-sum scratch [z][j][x][a][b][k].
+// grid: x = tiles of the N_b^2 n_k output elements, y = output column j
+// (0..n), z = split of the l range (lchunk values each). The tiles of one
+// column are adjacent in launch order, so they share its blocks through L2.
+// out is the I row when gridDim.z == 1, else the partial-sum scratch
+// [z][j][x][a][b][k].
 template <class P, int NB>
 __global__ void __launch_bounds__(256) sweep_kernel(const typename P::S *__restrict__ H,
                                                     const typename P::S *__restrict__ Cf,
                                                     double2 *__restrict__ out, int n, int nk,
                                                     int lchunk) {
   using S = typename P::S;
-  const int j = blockIdx.x;
-  const int idx = blockIdx.y * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= NB * NB * nk) return;
   const int k = idx % nk;
   const int ab = idx / nk;
@@ -295,7 +297,7 @@ SweepShape sweep_shape(const Mesh &m, int n) {
   if (nz < 1) nz = 1;
   sh.lchunk = (int)((n + 1 + nz - 1) / nz);
   sh.nz = (int)((n + 1 + sh.lchunk - 1) / sh.lchunk);
-  sh.grid = dim3(n + 1, (unsigned)ty, (unsigned)sh.nz);
+  sh.grid = dim3((unsigned)ty, n + 1, (unsigned)sh.nz);
   return sh;
 }
 

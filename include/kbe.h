@@ -57,7 +57,8 @@ typedef enum {
 /* Storage of the two-time history and arithmetic of the collision-integral
  * sweep (the dominant kernel). Everything else (self-energy, propagators,
  * the update of the newest rows, the time diagonal, observables) is FP64 in
- * every mode; the two newest rows are always kept in FP64.
+ * every mode; the two newest rows are always kept in FP64. The history keeps
+ * G^< and dG = G^< - G^> per block.
  *   FP64: history complex128, sweep in FP64 (DFMA).
  *   DF64: history as pairs of FP32 (hi, lo) per real part (the same 8 bytes;
  *         48-bit significand), sweep in double-float arithmetic on the FP32
@@ -91,6 +92,7 @@ typedef struct kbe_profile_stats {
   int sweep_launches;       /* sweep launches timed                               */
   double sweep_ms;          /* summed event time of those launches                */
   double sweep_flops;       /* algorithmic flops of those launches (24 n^2 N_b^3 n_k) */
+  double sweep_flops_executed; /* flops the dG form executes (~20 n^2 N_b^3 n_k)     */
   double sweep_bytes;       /* algorithmic bytes (stored history read once + I row) */
   int launches;             /* all kernels launched while enabled                 */
 } kbe_profile_stats;
@@ -182,11 +184,13 @@ kbe_status kbe_op_sigma_row(const kbe_mesh *m, const double *v, int n, double Un
                             const double *Ul_dev, const void *Grow_dev, void *Sigma_dev,
                             void *work_dev, size_t work_bytes, void *stream);
 
-/* Pack count complex128 values (device) into the history storage of a
- * precision (device): FP64 copies, DF64 writes float4 {re_hi, re_lo, im_hi,
- * im_lo} with hi = fl32(x), lo = fl32(x - hi), C64 writes float2. */
-kbe_status kbe_op_pack(int precision, const void *src_dev, void *dst_dev, size_t count,
-                       void *stream);
+/* Pack nblocks history blocks (device, FP64 [2][nb][nb][nk] = G^<, G^>;
+ * block_elems = nb*nb*nk) into the history storage of a precision (device):
+ * component 0 holds G^<, component 1 holds dG = G^< - G^> (formed in FP64),
+ * as complex128 (FP64), float4 {re_hi, re_lo, im_hi, im_lo} with
+ * hi = fl32(x), lo = fl32(x - hi) (DF64), or complex64 (C64). */
+kbe_status kbe_op_pack(int precision, const void *src_dev, void *dst_dev, size_t nblocks,
+                       size_t block_elems, void *stream);
 
 /* (a2) Collision-integral row, Eq. 6 in left form:
  *   I^x(n, j) = sum_{l=0}^{n} w^(n)_l [S^>(n,l) - S^<(n,l)] G^x(l, j)
@@ -195,8 +199,8 @@ kbe_status kbe_op_pack(int precision, const void *src_dev, void *dst_dev, size_t
  * (zero for m = 0) and G(l, j) = -G(j, l)^+ above the diagonal.
  * H_dev: history triangle with rows 0..n; Sigma_dev: n+1 blocks; I_dev:
  * n+1 blocks written (complex128). precision: KBE_PREC_*; H_dev holds the
- * triangle in that precision's storage (kbe_op_pack), Sigma_dev and I_dev
- * are complex128. work_dev: device scratch of
+ * triangle packed by kbe_op_pack in that precision's storage, Sigma_dev and
+ * I_dev are complex128. work_dev: device scratch of
  * kbe_op_collision_row_workspace(m, n, precision) bytes (coefficient rows
  * and, when the l sum is split over CTAs, FP64 partial sums). */
 size_t kbe_op_collision_row_workspace(const kbe_mesh *m, int n, int precision);

@@ -55,7 +55,8 @@ class kbe_mesh(ctypes.Structure):
 
 class kbe_profile_stats(ctypes.Structure):
     _fields_ = [("sweep_launches", ctypes.c_int), ("sweep_ms", ctypes.c_double),
-                ("sweep_flops", ctypes.c_double), ("sweep_bytes", ctypes.c_double),
+                ("sweep_flops", ctypes.c_double), ("sweep_flops_executed", ctypes.c_double),
+                ("sweep_bytes", ctypes.c_double),
                 ("launches", ctypes.c_int)]
 
 
@@ -93,7 +94,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "kbe_op_sigma_row": (I, [pmesh, P, I, D, P, P, P, P, S, P]),
         "kbe_op_collision_row": (I, [pmesh, I, D, I, P, P, P, P, S, P]),
         "kbe_op_collision_row_workspace": (S, [pmesh, I, I]),
-        "kbe_op_pack": (I, [I, P, P, S, P]),
+        "kbe_op_pack": (I, [I, P, P, S, S, P]),
         "kbe_op_propagators": (I, [pmesh, D, P, P, P, P]),
         "kbe_op_update_row": (I, [pmesh, I, D, D, P, P, P, P, P, P, P, P]),
         "kbe_op_sigma_row_noalloc": (I, [pmesh, P, I, D, P, P, P, P]),
@@ -234,7 +235,8 @@ class KBE:
         s = kbe_profile_stats()
         _check(load().kbe_profile_read(self._h, ctypes.byref(s)), self._h)
         return dict(sweep_launches=s.sweep_launches, sweep_ms=s.sweep_ms, sweep_flops=s.sweep_flops,
-                    sweep_bytes=s.sweep_bytes, launches=s.launches)
+                    sweep_flops_executed=s.sweep_flops_executed, sweep_bytes=s.sweep_bytes,
+                    launches=s.launches)
 
 
 # ---- stateless ops on torch device tensors (GPU layout, see include/kbe.h) ----
@@ -271,10 +273,12 @@ def collision_row(nb, L, n, dt, H, Sigma, I, precision=KBE_PREC_FP64, work=None,
                                        _stream_ptr(stream)))
 
 
-def pack(precision, src, dst, stream=None):
-    """complex128 device tensor -> history storage of `precision` (dst bytes:
-    16 per complex for FP64 / DF64, 8 for C64)."""
-    _check(load().kbe_op_pack(int(precision), _c(src), _c(dst), src.numel(), _stream_ptr(stream)))
+def pack(precision, src, dst, nblocks, block_elems, stream=None):
+    """FP64 (G^<, G^>) blocks [nblocks][2][nb][nb][nk] -> history storage of
+    `precision`, (G^<, dG) per block (dst bytes: 16 per complex for FP64 and
+    DF64, 8 for C64)."""
+    _check(load().kbe_op_pack(int(precision), _c(src), _c(dst), int(nblocks), int(block_elems),
+                              _stream_ptr(stream)))
 
 
 def propagators(nb, L, dt, h, U, V, stream=None):

@@ -39,9 +39,9 @@ struct kbe_handle {
   double dir[2] = {1.0, 0.0};
 
   // device arena
-  void *H = nullptr;           // history triangle in the precision's storage
+  void *H = nullptr;           // history triangle (G^<, dG = G^< - G^>) in the precision's storage
   size_t esz = 16;             // bytes per stored complex number
-  double2 *Wrow[2] = {nullptr, nullptr};   // FP64 rows n-1, n (ring; DF64 / C64 only)
+  double2 *Wrow[2] = {nullptr, nullptr};   // FP64 (G^<, G^>) rows n-1 and n (ring)
   void *coef = nullptr;        // sweep workspace: coefficient rows + l-split partial sums
   double2 *Ip = nullptr;       // I row n-1
   double2 *Ic = nullptr;       // I row n
@@ -65,7 +65,7 @@ struct kbe_handle {
   // profiling
   bool prof = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
-  std::vector<double> ev_flops, ev_bytes;
+  std::vector<double> ev_flops, ev_flops_x, ev_bytes;
   size_t ev_used = 0;
   kbe_profile_stats stats{};
 };
@@ -129,10 +129,18 @@ void free_all(kbe_handle *h) {
   h->ev.clear();
 }
 
-// collision sweep flops / bytes of one launch at row n (algorithmic counts)
+// collision sweep flops of one launch at row n: the method's count with the
+// G^> form of Eq. 6 (3 N_b^3 complex multiply-adds per stored block, ~24 n^2
+// N_b^3 n_k flops) and the count this kernel executes with the dG form
+// (2 products per node above the output, 3 on [0, t_j])
 double sweep_flops(const kbe_handle *h, int n) {
   const double nb3 = (double)h->cfg.nb * h->cfg.nb * h->cfg.nb;
   const double cm = 2.0 * (n + 1.0) * (n + 1.0) + (double)n * (n + 3.0);
+  return 8.0 * cm * nb3 * h->mesh.nk;
+}
+double sweep_flops_executed(const kbe_handle *h, int n) {
+  const double nb3 = (double)h->cfg.nb * h->cfg.nb * h->cfg.nb;
+  const double cm = 2.5 * n * (double)n + 5.5 * n + 2.0;
   return 8.0 * cm * nb3 * h->mesh.nk;
 }
 double sweep_bytes(const kbe_handle *h, int n) {
@@ -142,18 +150,14 @@ double sweep_bytes(const kbe_handle *h, int n) {
   return blk2 * (tri_blocks * (double)h->esz + 2.0 * (n + 1.0) * 16.0);
 }
 
-// FP64 copy of row i: the history itself in FP64 mode, else the ring of the
-// two newest rows (valid for i = n-1, n)
-double2 *frow(kbe_handle *h, int i) {
-  if (h->cfg.precision == KBE_PREC_FP64) return (double2 *)h->H + tri(i, 0) * 2 * h->blk;
-  return h->Wrow[i & 1];
-}
+// FP64 (G^<, G^>) copy of row i: the ring of the two newest rows (valid for
+// i = n-1, n)
+double2 *frow(kbe_handle *h, int i) { return h->Wrow[i & 1]; }
 
-// store row i into the history triangle in its storage format
+// store row i into the history triangle: (G^<, dG) in the storage format
 kbe_status publish(kbe_handle *h, int i) {
-  if (h->cfg.precision == KBE_PREC_FP64) return KBE_OK;
   char *dst = (char *)h->H + tri(i, 0) * 2 * h->blk * h->esz;
-  cudaError_t e = kbe::launch_pack(h->cfg.precision, frow(h, i), dst, (size_t)(i + 1) * 2 * h->blk, h->stream);
+  cudaError_t e = kbe::launch_pack(h->cfg.precision, frow(h, i), dst, (size_t)(i + 1), h->blk, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "publish row");
   if (h->prof) h->stats.launches += 1;
   return KBE_OK;
@@ -173,6 +177,7 @@ kbe_status evaluate_row(kbe_handle *h, int n) {
       cudaEventCreate(&b);
       h->ev.push_back({a, b});
       h->ev_flops.push_back(0);
+      h->ev_flops_x.push_back(0);
       h->ev_bytes.push_back(0);
     }
     cudaEventRecord(h->ev[h->ev_used].first, h->stream);
@@ -182,6 +187,7 @@ kbe_status evaluate_row(kbe_handle *h, int n) {
   if (timed) {
     cudaEventRecord(h->ev[h->ev_used].second, h->stream);
     h->ev_flops[h->ev_used] = sweep_flops(h, n);
+    h->ev_flops_x[h->ev_used] = sweep_flops_executed(h, n);
     h->ev_bytes[h->ev_used] = sweep_bytes(h, n);
     h->ev_used++;
     h->stats.launches += 5 + (kbe::sweep_splits(h->mesh, n) > 1 ? 1 : 0);
@@ -324,10 +330,8 @@ kbe_status kbe_create(const kbe_config *cfg, void *stream, kbe_handle **out) {
   h->esz = kbe::history_elem_bytes(cfg->precision);
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = dalloc(h, (char **)&h->H, ntri * 2 * h->blk * h->esz);
-  if (cfg->precision != KBE_PREC_FP64) {
-    if (e == cudaSuccess) e = dalloc(h, &h->Wrow[0], row);
-    if (e == cudaSuccess) e = dalloc(h, &h->Wrow[1], row);
-  }
+  if (e == cudaSuccess) e = dalloc(h, &h->Wrow[0], row);
+  if (e == cudaSuccess) e = dalloc(h, &h->Wrow[1], row);
   if (e == cudaSuccess) e = dalloc(h, (char **)&h->coef, kbe::sweep_workspace_bytes(h->mesh, (int)T, cfg->precision));
   if (e == cudaSuccess) e = dalloc(h, &h->Ip, row);
   if (e == cudaSuccess) e = dalloc(h, &h->Ic, row);
@@ -519,7 +523,7 @@ kbe_status kbe_get_row(kbe_handle *h, int i, int which, double *out) {
   const size_t cnt = nblk * 2 * h->blk;
   std::vector<double2> tmp(cnt);
   cudaError_t e;
-  if (h->cfg.precision == KBE_PREC_FP64 || i >= h->n - 1) {   // an FP64 copy exists
+  if (i >= h->n - 1) {                                        // an FP64 copy exists
     e = cudaMemcpyAsync(tmp.data(), frow(h, i), sizeof(double2) * cnt, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   } else {                                                    // unpack the stored row
@@ -528,14 +532,21 @@ kbe_status kbe_get_row(kbe_handle *h, int i, int which, double *out) {
                         cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e == cudaSuccess) {
-      if (h->cfg.precision == KBE_PREC_DF64) {
-        const float *f = (const float *)raw.data();
-        for (size_t q = 0; q < cnt; ++q)
+      const float *f = (const float *)raw.data();
+      const double2 *d = (const double2 *)raw.data();
+      for (size_t q = 0; q < cnt; ++q) {
+        if (h->cfg.precision == KBE_PREC_DF64)
           tmp[q] = make_double2((double)f[4 * q] + (double)f[4 * q + 1], (double)f[4 * q + 2] + (double)f[4 * q + 3]);
-      } else {
-        const float *f = (const float *)raw.data();
-        for (size_t q = 0; q < cnt; ++q) tmp[q] = make_double2((double)f[2 * q], (double)f[2 * q + 1]);
+        else if (h->cfg.precision == KBE_PREC_C64)
+          tmp[q] = make_double2((double)f[2 * q], (double)f[2 * q + 1]);
+        else
+          tmp[q] = d[q];
       }
+      for (size_t bq = 0; bq < nblk; ++bq)   // (G^<, dG) -> (G^<, G^> = G^< - dG)
+        for (size_t r = 0; r < h->blk; ++r) {
+          const double2 gl = tmp[(bq * 2) * h->blk + r], dg = tmp[(bq * 2 + 1) * h->blk + r];
+          tmp[(bq * 2 + 1) * h->blk + r] = make_double2(gl.x - dg.x, gl.y - dg.y);
+        }
     }
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "get_row copy");
@@ -566,12 +577,13 @@ kbe_status kbe_profile_read(kbe_handle *h, kbe_profile_stats *out) {
   if (e != cudaSuccess) return cuda_fail(h, e, "profile sync");
   kbe_profile_stats s = h->stats;
   s.sweep_launches = 0;
-  s.sweep_ms = s.sweep_flops = s.sweep_bytes = 0.0;
+  s.sweep_ms = s.sweep_flops = s.sweep_flops_executed = s.sweep_bytes = 0.0;
   for (size_t i = 0; i < h->ev_used; ++i) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, h->ev[i].first, h->ev[i].second) == cudaSuccess) {
       s.sweep_ms += ms;
       s.sweep_flops += h->ev_flops[i];
+      s.sweep_flops_executed += h->ev_flops_x[i];
       s.sweep_bytes += h->ev_bytes[i];
       s.sweep_launches++;
     }
@@ -610,10 +622,12 @@ size_t kbe_op_collision_row_workspace(const kbe_mesh *m, int n, int precision) {
   return kbe::sweep_workspace_bytes(to_mesh(m), n, precision);
 }
 
-kbe_status kbe_op_pack(int precision, const void *src_dev, void *dst_dev, size_t count, void *stream) {
-  if (!kbe::precision_supported(precision) || (count && (!src_dev || !dst_dev)))
+kbe_status kbe_op_pack(int precision, const void *src_dev, void *dst_dev, size_t nblocks,
+                       size_t block_elems, void *stream) {
+  if (!kbe::precision_supported(precision) || (nblocks && block_elems && (!src_dev || !dst_dev)))
     return fail(nullptr, KBE_ERR_ARG, "op_pack: bad arguments");
-  cudaError_t e = kbe::launch_pack(precision, (const double2 *)src_dev, dst_dev, count, (cudaStream_t)stream);
+  cudaError_t e = kbe::launch_pack(precision, (const double2 *)src_dev, dst_dev, nblocks, block_elems,
+                                   (cudaStream_t)stream);
   if (e != cudaSuccess) return fail(nullptr, KBE_ERR_CUDA, std::string("op_pack: ") + cudaGetErrorString(e));
   return KBE_OK;
 }

@@ -74,14 +74,16 @@ cudaError_t sigma_row(const Mesh &m, const double *v_host, int n, double Un, con
                       const double2 *Grow, double2 *Sig, double2 *work, cudaStream_t st);
 
 // a2 collision row. H is the history triangle in the precision's storage
-// (double2 / float4 hi-lo pairs / float2); work holds the coefficient rows
-// for DF64 and C64 (sweep_workspace_bytes).
+// (double2 / float4 hi-lo pairs / float2), each block holding G^< and
+// dG = G^< - G^>; work holds the coefficient rows and the l-split partial
+// sums (sweep_workspace_bytes).
 bool sweep_supported(int nb);
 bool precision_supported(int prec);
 size_t history_elem_bytes(int prec);
 size_t sweep_workspace_bytes(const Mesh &m, int n, int prec);
 int sweep_splits(const Mesh &m, int n);   // CTAs sharing one output's l range
-cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t count, cudaStream_t st);
+cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t nblocks, size_t blk,
+                        cudaStream_t st);
 cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const void *H,
                          const double2 *Sig, double2 *I, void *work, cudaStream_t st);
 

@@ -4,7 +4,13 @@
 //            + sum_{l=0}^{j} w^(j)_l  S^x(n,l) [G^<(l,j) - G^>(l,j)]
 // for j = 0..n and x in {<, >}. The history holds G only for l >= j; above
 // the diagonal G(l,j) = -G(j,l)^+ (the paper keeps G^> below and G^< above
-// the diagonal for the same reason).
+// the diagonal for the same reason). It stores, per block, G^< and
+// dG = G^< - G^> (so that G^> never has to be formed): with
+// C1 = w^(n)_l (S^> - S^<), C2^x = dt S^x and f = w^(j)_l / dt,
+//   I^<(n,j) = sum_l C1 G^<(l,j) + sum_{l<=j} f C2^< dG(l,j),
+//   I^>(n,j) = sum_l C1 G^<(l,j) + sum_{l<=j} (f C2^> - C1) dG(l,j)
+//                                - sum_{l>j}  C1 dG(l,j):
+// three complex multiply-adds per element and node for l <= j, two above.
 //
 // Work per evaluation: 3 N_b^3 complex multiply-adds per stored block and k,
 // i.e. 24 n^2 N_b^3 n_k flops for n^2 N_b^2 n_k complex numbers read: about
@@ -23,31 +29,37 @@
 //   C64  : complex64 history, FP32 partial products per l, partial sums
 //          added into a compensated (TwoSum) accumulator.
 // The Sigma row is first turned into three coefficient rows
-// C1 = w^(n)_l (S^> - S^<), C2^< = dt S^<, C2^> = dt S^> in the history's
-// storage; the term-2 weights w^(j)_l / dt are then exact powers of two.
+// C1 = w^(n)_l (S^> - S^<), C2^< = dt S^<, C3 = dt S^> - C1 in the history's
+// storage; the term-2 weights f = w^(j)_l / dt are then exact powers of two
+// (f = 1 inside, 1/2 at l = 0 and l = j, where f C2^> - C1 = (C3 - C1) / 2).
 #include "kbe_internal.cuh"
+
+#ifndef KBE_SWEEP_MINB_F64
+#define KBE_SWEEP_MINB_F64 2
+#endif
+#ifndef KBE_SWEEP_MINB_DF64
+#define KBE_SWEEP_MINB_DF64 3
+#endif
+#ifndef KBE_SWEEP_MINB_C64
+#define KBE_SWEEP_MINB_C64 2
+#endif
 
 namespace kbe {
 
 namespace {
 
-// term-2 weight w^(j)_l / dt: 0 above the diagonal or for j = 0, 1/2 at the
-// trapezoid ends, 1 inside
-__device__ __forceinline__ float term2_factor(int j, int l) {
-  if (j == 0 || l > j) return 0.f;
-  return (l == 0 || l == j) ? 0.5f : 1.f;
-}
-
 // ---------------------------------------------------------------- FP64 ----
 struct ArithF64 {
   using S = double2;   // stored complex
   using A = double2;   // accumulator
+  static constexpr int kMinBlocks = KBE_SWEEP_MINB_F64;   // CTAs of 256 per SM (register cap)
   static __device__ __forceinline__ void zero(A &a) { a = make_double2(0.0, 0.0); }
   static __device__ __forceinline__ void begin(A &) {}
   static __device__ __forceinline__ void end(A &) {}
   static __device__ __forceinline__ void mac(A &a, const S &x, const S &y) { a = c_fma(x, y, a); }
   static __device__ __forceinline__ S sub(const S &x, const S &y) { return c_sub(x, y); }
   static __device__ __forceinline__ S negconj(const S &x) { return make_double2(-x.x, x.y); }
+  static __device__ __forceinline__ S neg(const S &x) { return make_double2(-x.x, -x.y); }
   static __device__ __forceinline__ S scale(float f, const S &x) { return c_scale((double)f, x); }
   static __device__ __forceinline__ double2 result(const A &a) { return a; }
 };
@@ -93,6 +105,7 @@ __device__ __forceinline__ void df_renorm(float &h, float &l) {
 struct ArithDF64 {
   using S = float4;
   using A = float4;
+  static constexpr int kMinBlocks = KBE_SWEEP_MINB_DF64;
   static __device__ __forceinline__ void zero(A &a) { a = make_float4(0.f, 0.f, 0.f, 0.f); }
   static __device__ __forceinline__ void begin(A &) {}
   // after each memory-time node: keep the low word within a few ulps of the
@@ -114,6 +127,7 @@ struct ArithDF64 {
     return r;
   }
   static __device__ __forceinline__ S negconj(const S &X) { return make_float4(-X.x, -X.y, X.z, X.w); }
+  static __device__ __forceinline__ S neg(const S &X) { return make_float4(-X.x, -X.y, -X.z, -X.w); }
   static __device__ __forceinline__ S scale(float f, const S &X) {   // f a power of two: exact
     return make_float4(f * X.x, f * X.y, f * X.z, f * X.w);
   }
@@ -140,6 +154,7 @@ struct AccC64 {
 struct ArithC64 {
   using S = float2;
   using A = AccC64;
+  static constexpr int kMinBlocks = KBE_SWEEP_MINB_C64;
   static __device__ __forceinline__ void zero(A &a) { a.sum = make_float4(0.f, 0.f, 0.f, 0.f); }
   static __device__ __forceinline__ void begin(A &a) { a.part = make_float2(0.f, 0.f); }
   static __device__ __forceinline__ void end(A &a) {
@@ -152,6 +167,7 @@ struct ArithC64 {
   }
   static __device__ __forceinline__ S sub(const S &x, const S &y) { return make_float2(x.x - y.x, x.y - y.y); }
   static __device__ __forceinline__ S negconj(const S &x) { return make_float2(-x.x, x.y); }
+  static __device__ __forceinline__ S neg(const S &x) { return make_float2(-x.x, -x.y); }
   static __device__ __forceinline__ S scale(float f, const S &x) { return make_float2(f * x.x, f * x.y); }
   static __device__ __forceinline__ double2 result(const A &a) {
     return make_double2((double)a.sum.x + (double)a.sum.y, (double)a.sum.z + (double)a.sum.w);
@@ -159,13 +175,56 @@ struct ArithC64 {
 };
 
 // ------------------------------------------------------------ the sweep ----
+// One memory-time node l for this thread's element (k, a, b): MODE 0 is a
+// node above the output (l > j, or j = 0): only C1 G^< and -C1 dG; MODE 1 an
+// interior node of [0, t_j] (f = 1); MODE 2 an end node of [0, t_j] (l = 0
+// or l = j, f = 1/2). LOWER: the block (l, j) is stored (l >= j), else its
+// adjoint -X(j, l)^+ is read.
+template <class P, int NB, int MODE, bool LOWER>
+__device__ __forceinline__ void sweep_node(const typename P::S *__restrict__ c1,
+                                           const typename P::S *__restrict__ g, size_t blk, int nk,
+                                           int b, typename P::A &accP, typename P::A &accL,
+                                           typename P::A &accG) {
+  using S = typename P::S;
+  P::begin(accP);
+  P::begin(accL);
+  P::begin(accG);
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    const S A1 = c1[(size_t)c * nk];
+    S Gl, D;
+    if (LOWER) {   // G(l, j)_cb, dG(l, j)_cb stored directly
+      Gl = g[(size_t)(c * NB + b) * nk];
+      D = g[blk + (size_t)(c * NB + b) * nk];
+    } else {       // X(l, j)_cb = -conj(X(j, l)_bc)
+      Gl = P::negconj(g[(size_t)(b * NB + c) * nk]);
+      D = P::negconj(g[blk + (size_t)(b * NB + c) * nk]);
+    }
+    P::mac(accP, A1, Gl);
+    if (MODE == 0) {
+      P::mac(accG, P::neg(A1), D);
+    } else if (MODE == 1) {
+      P::mac(accL, c1[blk + (size_t)c * nk], D);
+      P::mac(accG, c1[2 * blk + (size_t)c * nk], D);
+    } else {   // (f C2^> - C1) = (C3 - C1) / 2 at the end nodes
+      P::mac(accL, P::scale(0.5f, c1[blk + (size_t)c * nk]), D);
+      P::mac(accG, P::scale(0.5f, P::sub(c1[2 * blk + (size_t)c * nk], A1)), D);
+    }
+  }
+  P::end(accP);
+  P::end(accL);
+  P::end(accG);
+}
+
 // grid: x = tiles of the N_b^2 n_k output elements, y = output column j
 // (0..n), z = split of the l range (lchunk values each). The tiles of one
 // column are adjacent in launch order, so they share its blocks through L2.
 // out is the I row when gridDim.z == 1, else the partial-sum scratch
-// [z][j][x][a][b][k].
+// [z][j][x][a][b][k]. The l range [l0, l1) is walked as three branch-free
+// runs: interior nodes 0 < l < j (adjoint blocks), nodes above l > j (stored
+// blocks), then the two end nodes l = 0 and l = j.
 template <class P, int NB>
-__global__ void __launch_bounds__(256) sweep_kernel(const typename P::S *__restrict__ H,
+__global__ void __launch_bounds__(256, P::kMinBlocks) sweep_kernel(const typename P::S *__restrict__ H,
                                                     const typename P::S *__restrict__ Cf,
                                                     double2 *__restrict__ out, int n, int nk,
                                                     int lchunk) {
@@ -179,48 +238,32 @@ __global__ void __launch_bounds__(256) sweep_kernel(const typename P::S *__restr
   const int l0 = blockIdx.z * lchunk;
   const int l1 = min(n + 1, l0 + lchunk);
   const size_t blk = (size_t)NB * NB * nk;
+  const S *cbase = Cf + (size_t)a * NB * nk + k;   // C1(l)_{a, .} at cbase + 3 l blk
+  const S *hbase = H + k;
 
-  typename P::A accL, accG;
+  typename P::A accP, accL, accG;   // sum C1 G^<, the dG terms of I^<, of I^>
+  P::zero(accP);
   P::zero(accL);
   P::zero(accG);
-  for (int l = l0; l < l1; ++l) {
-    const S *c1 = Cf + (size_t)l * 3 * blk + (size_t)a * NB * nk + k;   // C1(l)_{a, .}
-    const float f = term2_factor(j, l);
-    const bool lower = (l >= j);
-    const S *g = H + (lower ? tri(l, j) : tri(j, l)) * 2 * blk + k;
-    P::begin(accL);
-    P::begin(accG);
-#pragma unroll
-    for (int c = 0; c < NB; ++c) {
-      const S A1 = c1[(size_t)c * nk];
-      S Gl, Gg;
-      if (lower) {   // G(l, j)_cb stored directly
-        Gl = g[(size_t)(c * NB + b) * nk];
-        Gg = g[blk + (size_t)(c * NB + b) * nk];
-      } else {       // G(l, j)_cb = -conj(G(j, l)_bc)
-        Gl = P::negconj(g[(size_t)(b * NB + c) * nk]);
-        Gg = P::negconj(g[blk + (size_t)(b * NB + c) * nk]);
-      }
-      P::mac(accL, A1, Gl);
-      P::mac(accG, A1, Gg);
-      if (f != 0.f) {   // f is uniform over the CTA; only l = 0, j take the 1/2
-        S B2l = c1[blk + (size_t)c * nk];
-        S B2g = c1[2 * blk + (size_t)c * nk];
-        if (f != 1.f) {
-          B2l = P::scale(f, B2l);
-          B2g = P::scale(f, B2g);
-        }
-        const S D = P::sub(Gl, Gg);
-        P::mac(accL, B2l, D);
-        P::mac(accG, B2g, D);
-      }
-    }
-    P::end(accL);
-    P::end(accG);
+  if (j > 0) {
+    for (int l = max(l0, 1); l < min(l1, j); ++l)   // interior of [0, t_j]
+      sweep_node<P, NB, 1, false>(cbase + (size_t)l * 3 * blk, hbase + tri(j, l) * 2 * blk, blk, nk, b,
+                                  accP, accL, accG);
   }
+  for (int l = max(l0, j == 0 ? 0 : j + 1); l < l1; ++l)   // above the output
+    sweep_node<P, NB, 0, true>(cbase + (size_t)l * 3 * blk, hbase + tri(l, j) * 2 * blk, blk, nk, b,
+                               accP, accL, accG);
+  if (j > 0) {
+    if (l0 == 0)   // end node l = 0 (adjoint block, 0 < j)
+      sweep_node<P, NB, 2, false>(cbase, hbase + tri(j, 0) * 2 * blk, blk, nk, b, accP, accL, accG);
+    if (j >= l0 && j < l1)   // end node l = j (diagonal block)
+      sweep_node<P, NB, 2, true>(cbase + (size_t)j * 3 * blk, hbase + tri(j, j) * 2 * blk, blk, nk, b,
+                                 accP, accL, accG);
+  }
+  const double2 p = P::result(accP);
   double2 *o = out + ((size_t)blockIdx.z * (n + 1) + j) * 2 * blk + (size_t)ab * nk + k;
-  o[0] = P::result(accL);
-  o[blk] = P::result(accG);
+  o[0] = c_add(p, P::result(accL));
+  o[blk] = c_add(p, P::result(accG));
 }
 
 // I = sum over the z partial rows (FP64)
@@ -240,18 +283,31 @@ __device__ __forceinline__ float4 split_df(double2 x) {
   return make_float4(rh, __double2float_rn(x.x - (double)rh), ih, __double2float_rn(x.y - (double)ih));
 }
 
+// nblocks blocks [2][nb][nb][nk] of (G^<, G^>) in FP64 -> (G^<, dG = G^< - G^>)
+// in the history storage (dG formed in FP64 before rounding)
 __global__ void pack_kernel(int prec, const double2 *__restrict__ src, void *__restrict__ dst,
-                            size_t count) {
+                            size_t nblocks, size_t blk) {
+  const size_t count = nblocks * blk;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (size_t)gridDim.x * blockDim.x) {
-    const double2 x = src[i];
-    if (prec == KBE_PREC_DF64) ((float4 *)dst)[i] = split_df(x);
-    else if (prec == KBE_PREC_C64) ((float2 *)dst)[i] = make_float2((float)x.x, (float)x.y);
-    else ((double2 *)dst)[i] = x;
+    const size_t bq = i / blk, r = i - bq * blk;
+    const size_t o0 = bq * 2 * blk + r, o1 = o0 + blk;
+    const double2 gl = src[o0];
+    const double2 dg = c_sub(gl, src[o1]);
+    if (prec == KBE_PREC_DF64) {
+      ((float4 *)dst)[o0] = split_df(gl);
+      ((float4 *)dst)[o1] = split_df(dg);
+    } else if (prec == KBE_PREC_C64) {
+      ((float2 *)dst)[o0] = make_float2((float)gl.x, (float)gl.y);
+      ((float2 *)dst)[o1] = make_float2((float)dg.x, (float)dg.y);
+    } else {
+      ((double2 *)dst)[o0] = gl;
+      ((double2 *)dst)[o1] = dg;
+    }
   }
 }
 
-// coefficient rows [l][3][a][c][k]: C1 = w^(n)_l (S^> - S^<), C2^< = dt S^<, C2^> = dt S^>
+// coefficient rows [l][3][a][c][k]: C1 = w^(n)_l (S^> - S^<), C2^< = dt S^<, C3 = dt S^> - C1
 __global__ void coef_kernel(int prec, const double2 *__restrict__ Sig, void *__restrict__ Cf, int n,
                             int nk, int nb2, double dt) {
   const size_t blk = (size_t)nb2 * nk;
@@ -261,7 +317,8 @@ __global__ void coef_kernel(int prec, const double2 *__restrict__ Sig, void *__r
     const size_t l = i / blk, r = i - l * blk;
     const double2 sl = Sig[(l * 2) * blk + r], sg = Sig[(l * 2 + 1) * blk + r];
     const double w1 = trap_weight(n, (int)l, dt);
-    const double2 v[3] = {c_scale(w1, c_sub(sg, sl)), c_scale(dt, sl), c_scale(dt, sg)};
+    const double2 c1 = c_scale(w1, c_sub(sg, sl));
+    const double2 v[3] = {c1, c_scale(dt, sl), c_sub(c_scale(dt, sg), c1)};
     for (int q = 0; q < 3; ++q) {
       const size_t o = (l * 3 + q) * blk + r;
       if (prec == KBE_PREC_DF64) ((float4 *)Cf)[o] = split_df(v[q]);
@@ -357,9 +414,10 @@ size_t sweep_workspace_bytes(const Mesh &m, int n, int prec) {
 
 int sweep_splits(const Mesh &m, int n) { return sweep_shape(m, n).nz; }
 
-cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t count, cudaStream_t st) {
-  if (count == 0) return cudaSuccess;
-  pack_kernel<<<grid_for(count), 256, 0, st>>>(prec, src, dst, count);
+cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t nblocks, size_t blk,
+                        cudaStream_t st) {
+  if (nblocks == 0 || blk == 0) return cudaSuccess;
+  pack_kernel<<<grid_for(nblocks * blk), 256, 0, st>>>(prec, src, dst, nblocks, blk);
   return cudaGetLastError();
 }
 

@@ -63,7 +63,9 @@ def test_collision_row_matches_oracle(nb, L, n):
     Sl = ki.random_blocks(rng, (n + 1, nk, nb, nb))
     Sg = ki.random_blocks(rng, (n + 1, nk, nb, nb))
     Il, Ig = oracle.collision_row(nb, nk, n, dt, Hl, Hg, Sl, Sg)
-    H = dev(to_dev_blocks(Hl, Hg))
+    H64 = dev(to_dev_blocks(Hl, Hg))
+    H = torch.empty_like(H64)
+    kbe.pack(kbe.KBE_PREC_FP64, H64, H, ntri, nb * nb * nk)
     S = dev(to_dev_blocks(Sl, Sg))
     I = torch.full((n + 1, 2, nb, nb, nk), float("nan"), dtype=torch.complex128, device="cuda")
     work = torch.empty(kbe.collision_row_workspace(nb, L, n) // 4 + 1, dtype=torch.float32, device="cuda")

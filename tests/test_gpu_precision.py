@@ -27,10 +27,11 @@ def dev(a):
 
 
 def packed(prec, arr):
+    """[m, 2, nb, nb, nk] FP64 (G^<, G^>) blocks -> packed (G^<, dG) storage"""
     src = dev(arr)
     nbytes = 8 if prec == kbe.KBE_PREC_C64 else 16
     dst = torch.empty(src.numel() * nbytes // 4, dtype=torch.float32, device="cuda")
-    kbe.pack(prec, src.reshape(-1), dst)
+    kbe.pack(prec, src, dst, arr.shape[0], arr[0, 0].size)
     return dst
 
 

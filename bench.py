@@ -251,6 +251,11 @@ def run_ours(args, rank, world, local):
                        "max_rel_err_N": float(np.abs(sc_f[:, 0] - ref_obs[:, 0]).max() / abs(ref_obs[0, 0])),
                        "dtype": DTYPES[form], "roofline": roofline(pf, form, tf)}
 
+    # ---- batched form: uneven systems together vs one after another ----------
+    batched = None
+    if args.forms != "none":
+        batched = batched_form(kbe, stream, args)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "time-steps/s", "n_gpus": world,
@@ -268,12 +273,66 @@ def run_ours(args, rank, world, local):
             "gpu_launches": int(prof["launches"]),
             "clocks": clocks,
             "forms": forms,
+            "batched": batched,
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(s)
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+BATCH_N, BATCH_NT = 16, 64
+
+
+def batched_form(kbe, stream, args):
+    """The first 16 systems of the uneven 64-system draw (N_b 2..16, 4x4..12x12,
+    each truncated to 64 steps), advanced together (kbe_batch_*, one stream
+    per system) and one after another on one stream; FP64."""
+    import torch
+    systems = ki.batched(64)
+    full = sum(kbe.memory_bytes(kbe.system_config(x)) for x in systems)
+    sel = systems[:BATCH_N]
+    nts = [min(BATCH_NT, x.nt) for x in sel]
+    units = sum(nts)
+    b = kbe.KBEBatch(sel, nt_max=nts, stream=stream)
+    for _ in range(max(1, args.warmup)):
+        b.reset()
+        b.step(BATCH_NT)
+    b.synchronize()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b.reset()
+        b.step(BATCH_NT)
+    b.synchronize()
+    torch.cuda.synchronize()
+    t_batch = (time.perf_counter() - t0) / args.steps
+    b.close()
+    singles = [kbe.KBE.from_system(x, nt_max=nt, stream=stream) for x, nt in zip(sel, nts)]
+    for g, nt in zip(singles, nts):
+        g.reset()
+        g.step(nt)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for g, nt in zip(singles, nts):
+            g.reset()
+            g.step(nt)
+    for g in singles:
+        g.synchronize()
+    torch.cuda.synchronize()
+    t_seq = (time.perf_counter() - t0) / args.steps
+    for g in singles:
+        g.close()
+    free, tot = torch.cuda.mem_get_info()
+    return {"workload": f"first {BATCH_N} of the 64 uneven systems (seed 3), each truncated to "
+                        f"{BATCH_NT} steps; N_b {sorted(set(x.nb for x in sel))}",
+            "value": units / t_batch, "unit": "time-steps/s (summed over systems)",
+            "sequential_value": units / t_seq, "speedup_vs_sequential": t_seq / t_batch,
+            "full_64_system_fp64_bytes": int(full), "device_bytes": int(tot),
+            "note": "the full 64-system draw needs this many bytes in FP64 and does not fit; "
+                    "kbe_batch_create admits systems in order within the device budget"}
 
 
 def cpu_baseline(s, prefix=ORACLE_PREFIX):

@@ -153,6 +153,37 @@ kbe_status kbe_get_row(kbe_handle *h, int i, int which, double *out);
 kbe_status kbe_profile_enable(kbe_handle *h, int enable);
 kbe_status kbe_profile_read(kbe_handle *h, kbe_profile_stats *out);
 
+/* Device bytes kbe_create would allocate for cfg (0 if cfg is invalid). */
+size_t kbe_memory_bytes(const kbe_config *cfg);
+
+/* ---------------------------------------------------------------------- */
+/* batched systems (independent systems of uneven N_b, n_k, N_t)            */
+/* ---------------------------------------------------------------------- */
+
+typedef struct kbe_batch kbe_batch;
+
+/* Create nsys independent systems. Each admitted system gets its own handle
+ * on its own stream forked from `stream` (kernels of different systems run
+ * concurrently). Systems are admitted in order while their memory
+ * (kbe_memory_bytes) fits in budget_bytes (0: the device's free memory minus
+ * 2 GiB); admitted (host int[nsys], may be NULL) receives 1 / 0 per system.
+ * Systems that do not fit are not created: the caller may run them in a
+ * later batch or with a smaller nt_max (each reported, never silent). */
+kbe_status kbe_batch_create(int nsys, const kbe_config *cfgs, void *stream, size_t budget_bytes,
+                            kbe_batch **out, int *admitted);
+kbe_status kbe_batch_destroy(kbe_batch *b);
+/* The handle of system i (NULL if i is out of range or was not admitted):
+ * set its inputs and read its outputs with the handle API. */
+kbe_handle *kbe_batch_system(kbe_batch *b, int i);
+/* kbe_reset on every admitted system. */
+kbe_status kbe_batch_reset(kbe_batch *b);
+/* Advance every admitted system by nsteps rows (a system that reaches its
+ * nt_max stops there), one time step of all systems at a time; work is
+ * ordered after `stream`'s prior work and `stream` waits for all of it. */
+kbe_status kbe_batch_step(kbe_batch *b, int nsteps);
+/* Wait for all systems; the first failing system's status. */
+kbe_status kbe_batch_synchronize(kbe_batch *b);
+
 /* Message of the last error of this handle; with NULL, of the last failed
  * create or handle-free operation (kbe_op_*) on the calling thread. */
 const char *kbe_last_error(const kbe_handle *h);

@@ -32,7 +32,9 @@ EXPORTS = [
     "kbe_observables_all", "kbe_get_row", "kbe_profile_enable", "kbe_profile_read",
     "kbe_last_error", "kbe_op_sigma_row_workspace", "kbe_op_sigma_row", "kbe_op_collision_row",
     "kbe_op_propagators", "kbe_op_update_row", "kbe_op_sigma_row_noalloc",
-    "kbe_op_collision_row_workspace", "kbe_op_pack",
+    "kbe_op_collision_row_workspace", "kbe_op_pack", "kbe_memory_bytes", "kbe_batch_create",
+    "kbe_batch_destroy", "kbe_batch_system", "kbe_batch_reset", "kbe_batch_step",
+    "kbe_batch_synchronize",
 ]
 
 
@@ -98,6 +100,13 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "kbe_op_propagators": (I, [pmesh, D, P, P, P, P]),
         "kbe_op_update_row": (I, [pmesh, I, D, D, P, P, P, P, P, P, P, P]),
         "kbe_op_sigma_row_noalloc": (I, [pmesh, P, I, D, P, P, P, P]),
+        "kbe_memory_bytes": (S, [pcfg]),
+        "kbe_batch_create": (I, [I, pcfg, P, S, ctypes.POINTER(P), P]),
+        "kbe_batch_destroy": (I, [P]),
+        "kbe_batch_system": (P, [P, I]),
+        "kbe_batch_reset": (I, [P]),
+        "kbe_batch_step": (I, [P, I]),
+        "kbe_batch_synchronize": (I, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -136,19 +145,38 @@ def mesh(nb: int, L) -> kbe_mesh:
     return m
 
 
+def make_config(nb, dim, L, nt_max, dt, beta, mu, precision=KBE_PREC_FP64, n_corr=2, hf=1,
+                paper_shift=0) -> kbe_config:
+    cfg = kbe_config()
+    cfg.nb, cfg.dim = nb, dim
+    cfg.L[0], cfg.L[1] = int(L[0]), int(L[1])
+    cfg.nt_max, cfg.dt, cfg.beta, cfg.mu = nt_max, dt, beta, mu
+    cfg.precision, cfg.n_corr, cfg.hf, cfg.paper_shift = precision, n_corr, hf, paper_shift
+    return cfg
+
+
+def system_config(sys, nt_max=None, precision=KBE_PREC_FP64) -> kbe_config:
+    return make_config(sys.nb, sys.dim, sys.L, sys.nt if nt_max is None else nt_max, sys.dt, sys.beta,
+                       sys.mu, precision, sys.n_corr, sys.hf, sys.paper_shift)
+
+
+def memory_bytes(cfg: kbe_config) -> int:
+    return int(load().kbe_memory_bytes(ctypes.byref(cfg)))
+
+
 class KBE:
     """One Kadanoff-Baym system on the GPU (handle API of include/kbe.h)."""
 
     def __init__(self, nb: int, dim: int, L, nt_max: int, dt: float, beta: float, mu: float,
                  precision: int = KBE_PREC_FP64, n_corr: int = 2, hf: int = 1,
-                 paper_shift: int = 0, stream=None):
+                 paper_shift: int = 0, stream=None, _borrow=None):
         lib = load()
-        cfg = kbe_config()
-        cfg.nb, cfg.dim = nb, dim
-        cfg.L[0], cfg.L[1] = int(L[0]), int(L[1])
-        cfg.nt_max, cfg.dt, cfg.beta, cfg.mu = nt_max, dt, beta, mu
-        cfg.precision, cfg.n_corr, cfg.hf, cfg.paper_shift = precision, n_corr, hf, paper_shift
         self.nb, self.nk, self.nt_max = nb, int(L[0]) * int(L[1]), nt_max
+        self._owned = _borrow is None
+        if _borrow is not None:      # a handle owned by a batch
+            self._h = ctypes.c_void_p(_borrow)
+            return
+        cfg = make_config(nb, dim, L, nt_max, dt, beta, mu, precision, n_corr, hf, paper_shift)
         self._h = ctypes.c_void_p()
         self._stream = _stream_ptr(stream)
         _check(lib.kbe_create(ctypes.byref(cfg), self._stream, ctypes.byref(self._h)), None)
@@ -167,9 +195,15 @@ class KBE:
         return k
 
     def close(self):
-        if getattr(self, "_h", None) and self._h.value:
+        if getattr(self, "_h", None) and self._h.value and getattr(self, "_owned", True):
             load().kbe_destroy(self._h)
-            self._h = ctypes.c_void_p()
+        self._h = ctypes.c_void_p()
+
+    def load_inputs(self, sys, U=None):
+        """hoppings, interaction and drive of a kbe_inputs.System"""
+        self.set_hamiltonian(sys.hop_R, sys.hop_T)
+        self.set_interaction(np.array([sys.U]) if U is None else U, sys.v)
+        self.set_drive(sys.A, sys.direction)
 
     def __del__(self):
         try:
@@ -305,3 +339,50 @@ def sigma_row_noalloc(nb, L, v, n, Un, Grow, Sigma, Ul=None, stream=None):
 
 
 NOALLOC_SCRATCH_BYTES = 64 << 20   # KBE_NOALLOC_SCRATCH_BYTES in include/kbe.h
+
+
+class KBEBatch:
+    """Independent systems advanced together (kbe_batch_* of include/kbe.h)."""
+
+    def __init__(self, systems, precision=KBE_PREC_FP64, nt_max=None, budget_bytes=0, stream=None):
+        lib = load()
+        n = len(systems)
+        cfgs = (kbe_config * n)(*[system_config(s, None if nt_max is None else nt_max[i], precision)
+                                  for i, s in enumerate(systems)])
+        adm = (ctypes.c_int * n)()
+        self._b = ctypes.c_void_p()
+        _check(lib.kbe_batch_create(n, cfgs, _stream_ptr(stream), int(budget_bytes),
+                                    ctypes.byref(self._b), adm), None)
+        self.admitted = [bool(a) for a in adm]
+        self.systems = []
+        for i, s in enumerate(systems):
+            if not self.admitted[i]:
+                self.systems.append(None)
+                continue
+            h = lib.kbe_batch_system(self._b, i)
+            k = KBE(s.nb, s.dim, s.L, cfgs[i].nt_max, s.dt, s.beta, s.mu, _borrow=h)
+            k.load_inputs(s)
+            self.systems.append(k)
+
+    def reset(self):
+        _check(load().kbe_batch_reset(self._b))
+
+    def step(self, nsteps: int):
+        _check(load().kbe_batch_step(self._b, int(nsteps)))
+
+    def synchronize(self):
+        _check(load().kbe_batch_synchronize(self._b))
+
+    def close(self):
+        if getattr(self, "_b", None) and self._b.value:
+            for k in self.systems:
+                if k is not None:
+                    k._h = ctypes.c_void_p()
+            load().kbe_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

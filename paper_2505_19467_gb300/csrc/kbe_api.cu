@@ -297,6 +297,22 @@ Mesh to_mesh(const kbe_mesh *m) { return Mesh{m->nb, m->L[0], m->L[1], m->L[0] *
 
 void kbe::set_last_error(const std::string &msg) { g_create_err = msg; }
 
+// device bytes of one handle (the allocations of kbe_create)
+static size_t handle_bytes(const kbe_config *cfg) {
+  const Mesh m{cfg->nb, cfg->L[0], cfg->L[1], cfg->L[0] * cfg->L[1]};
+  const size_t T = (size_t)cfg->nt_max, nb2 = (size_t)cfg->nb * cfg->nb, blk = nb2 * m.nk;
+  const size_t ntri = tri((int)T, (int)T) + 1, row = (T + 1) * 2 * blk * sizeof(double2);
+  size_t b = ntri * 2 * blk * kbe::history_elem_bytes(cfg->precision);
+  b += 2 * row;                                                   // FP64 working rows
+  b += kbe::sweep_workspace_bytes(m, (int)T, cfg->precision);      // sweep coefficients, partials
+  b += 3 * row;                                                   // I rows, Sigma row
+  b += kbe::sigma_workspace_bytes(m, (int)T);                     // Sigma scratch
+  b += 3 * blk * sizeof(double2);                                 // U, V, h
+  b += (T + 2) * nb2 * sizeof(double2) + (T + 1) * (6 + (size_t)m.nk * cfg->nb) * sizeof(double);
+  b += (T + 1) * sizeof(double) + 64;
+  return b;
+}
+
 extern "C" {
 
 kbe_status kbe_create(const kbe_config *cfg, void *stream, kbe_handle **out) {
@@ -590,6 +606,13 @@ kbe_status kbe_profile_read(kbe_handle *h, kbe_profile_stats *out) {
   }
   *out = s;
   return KBE_OK;
+}
+
+size_t kbe_memory_bytes(const kbe_config *cfg) {
+  if (!cfg || !nb_ok(cfg->nb) || cfg->L[0] < 1 || cfg->L[1] < 1 || cfg->nt_max < 1 ||
+      (long)cfg->L[0] * cfg->L[1] > kbe::kMaxNk || !kbe::precision_supported(cfg->precision))
+    return 0;
+  return handle_bytes(cfg);
 }
 
 const char *kbe_last_error(const kbe_handle *h) {

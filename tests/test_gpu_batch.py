@@ -1,0 +1,58 @@
+"""Batched independent systems of uneven N_b, n_k and N_t (kbe_batch_*):
+every system of the batch must match its own oracle run entry by entry, each
+system stops at its own nt_max, and admission follows the memory budget."""
+import numpy as np
+import pytest
+
+import kbe_inputs as ki
+import oracle
+from layout import relerr
+
+torch = pytest.importorskip("torch")
+kbe = pytest.importorskip("paper_2505_19467_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+def uneven_batch():
+    specs = [(1, (5, 1), 5, 0.4), (2, (8, 1), 12, 0.0), (3, (3, 3), 8, 0.5), (4, (4, 3), 6, 0.3),
+             (8, (2, 2), 4, 0.2), (2, (1, 1), 9, 0.0)]
+    return [ki.small_system(nb, L, nt, 0.05, 0.9, seed=40 + i, drive_amp=amp)
+            for i, (nb, L, nt, amp) in enumerate(specs)]
+
+
+@pytest.mark.parametrize("prec,el_tol", [(0, 1e-10), (1, 5e-10)])
+def test_batch_matches_oracle_per_system(prec, el_tol):
+    systems = uneven_batch()
+    b = kbe.KBEBatch(systems, precision=prec)
+    assert all(b.admitted)
+    b.reset()
+    b.step(7)
+    b.step(10)            # systems with nt_max < 17 stop at their own end
+    b.synchronize()
+    for s, g in zip(systems, b.systems):
+        assert g.n == s.nt
+        o = oracle.Oracle(s)
+        o.step(s.nt)
+        for i in (1, s.nt // 2, s.nt):
+            ref = [o.row(i, 0), o.row(i, 1)]
+            scale = max(np.abs(ref[0]).max(), np.abs(ref[1]).max())
+            for x in (0, 1):
+                assert relerr(g.row(i, x), ref[x], scale=scale)[0] < el_tol, (s.name, i, x)
+        nkb, sc = g.observables_all()
+        assert np.abs(sc[s.nt] - o.observables(s.nt)[1]).max() < 1e-10
+    b.close()
+
+
+def test_batch_admission_by_memory_budget():
+    systems = uneven_batch()
+    need = [kbe.memory_bytes(kbe.system_config(s)) for s in systems]
+    budget = need[0] + need[1] + need[2] // 2          # the third does not fit
+    b = kbe.KBEBatch(systems, budget_bytes=budget)
+    assert b.admitted[:2] == [True, True] and not b.admitted[2]
+    assert b.systems[2] is None
+    b.reset()
+    b.step(3)
+    b.synchronize()
+    assert b.systems[0].n == 3 and b.systems[1].n == 3
+    b.close()

@@ -51,6 +51,12 @@ PEAKS = {
     "c64": (152 * 128 * 2 * 2.07, "GFLOP/s FP32",
             "FP32 FMA: 152 SM x 128 lanes x 2 flop x 2.07 GHz"),
 }
+# DRAM traffic of the sweep per launch as a multiple of its algorithmic bytes,
+# from ncu (dram__bytes_read.sum + dram__bytes_write.sum): fp64 at row 501 of
+# the full c2 run (8.29 GB vs 4.17 GB), df64 / c64 at row 247 of the c2 system
+# (profiles/sweep_c2_n247.md); traffic grows with the triangle like the
+# algorithmic bytes, so the average launch is scaled by the same factor.
+TRAFFIC_RATIO = {"fp64": 1.99, "df64": 1.57, "c64": 1.52}
 DTYPES = {"fp64": "f64", "df64": "df64 (f32 hi/lo pairs; everything but the sweep f64)",
           "c64": "c64/f32 history + sweep (everything else f64)"}
 ORACLE_PREFIX = 40
@@ -178,8 +184,12 @@ def roofline(prof, precision, t_dev):
     achieved = prof["sweep_flops"] / sweep_s / 1e9 if sweep_s > 0 else 0.0
     executed = prof["sweep_flops_executed"] / sweep_s / 1e9 if sweep_s > 0 else 0.0
     peak, punit, psrc = PEAKS[precision]
+    nl = max(1, prof["sweep_launches"])
+    alg_bytes = prof["sweep_bytes"] / nl
     return {"kernel": "collision sweep (a2)", "bound": "alu", "achieved": achieved, "peak": peak,
-            "unit": punit, "frac": achieved / peak, "traffic": None, "peak_source": psrc,
+            "unit": punit, "frac": achieved / peak,
+            "traffic": TRAFFIC_RATIO[precision] * alg_bytes, "traffic_unit": "bytes per launch",
+            "algorithmic_bytes_per_launch": alg_bytes, "peak_source": psrc,
             "achieved_executed": executed, "frac_executed": executed / peak,
             "launches": prof["sweep_launches"],
             "sweep_share_of_step": sweep_s / t_dev if t_dev > 0 else None,

@@ -262,9 +262,10 @@ def run_ours(args, rank, world, local):
                        "dtype": DTYPES[form], "roofline": roofline(pf, form, tf)}
 
     # ---- batched form: uneven systems together vs one after another ----------
-    batched = None
+    batched = paper = None
     if args.forms != "none":
         batched = batched_form(kbe, stream, args)
+        paper = paper_shape(kbe, stream)
 
     if rank == 0:
         line = {
@@ -284,12 +285,58 @@ def run_ours(args, rank, world, local):
             "clocks": clocks,
             "forms": forms,
             "batched": batched,
+            "paper_shape": paper,
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(s)
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def paper_shape(kbe, stream):
+    """The paper's model-problem shape (two bands, 1-D ring of n_k = 1024,
+    n = 500, Sec. 6 Tables I-II): one Sigma row and one collision row at
+    t_500 on a synthetic (random) history of that shape; their cost does not
+    depend on the values. Context for the paper's per-step times."""
+    import torch
+    nb, L, n = 2, (1024, 1), 500
+    nk, blk = 1024, 4 * 1024
+    ntri = (n + 1) * (n + 2) // 2
+    g = torch.Generator(device="cuda").manual_seed(5)
+    out = {"shape": "N_b=2, n_k=1024 (1-D), row n=500, one evaluation (P(EC)^2E does 3 per step)"}
+    row = torch.randn((n + 1, 2, nb, nb, nk), dtype=torch.complex128, device="cuda", generator=g)
+    sig = torch.empty_like(row)
+    work = torch.empty(kbe.sigma_row_workspace(nb, L, n) // 16 + 1, dtype=torch.complex128, device="cuda")
+    v = ki.pair_pattern(2)
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    with torch.cuda.stream(stream):
+        out["sigma_row_ms"] = timed(lambda: kbe.sigma_row(nb, L, v, n, 0.5, row, sig, work, stream=stream))
+        for name, prec in (("fp64", 0), ("df64", 1), ("c64", 2)):
+            H64 = torch.randn((ntri, 2, nb, nb, nk), dtype=torch.complex128, device="cuda", generator=g)
+            esz = 8 if prec == 2 else 16
+            H = torch.empty(H64.numel() * esz // 4, dtype=torch.float32, device="cuda")
+            kbe.pack(prec, H64, H, ntri, blk, stream=stream)
+            del H64
+            I = torch.empty_like(row)
+            w = torch.empty(kbe.collision_row_workspace(nb, L, n, prec) // 4 + 1, dtype=torch.float32,
+                            device="cuda")
+            out[f"collision_row_ms_{name}"] = timed(
+                lambda: kbe.collision_row(nb, L, n, 0.02, H, sig, I, precision=prec, work=w, stream=stream))
+            del H, I, w
+            torch.cuda.empty_cache()
+    return out
 
 
 BATCH_N, BATCH_NT = 16, 64

@@ -122,6 +122,14 @@ kbe_status kbe_set_interaction(kbe_handle *h, int len, const double *U, const do
  * A == NULL or len == 0 removes the drive. */
 kbe_status kbe_set_drive(kbe_handle *h, int len, const double *A, const double *dir);
 
+/* Dipole (length-gauge) drive of Eq. 4: during step t_i -> t_{i+1}, h(k) gains
+ * E_i M, with E_i (host double, len samples) the step-averaged field and M
+ * (host c128 [nb][nb], Hermitian, k-independent; the paper's two-band
+ * d_k = 1 coupling is M = [[0,1],[1,0]]). A pulse I delta(t - t_p) is the
+ * sample E_i = I / dt of the step that contains t_p. Steps beyond len use 0.
+ * E == NULL or len == 0 removes the drive. Combines with the Peierls drive. */
+kbe_status kbe_set_dipole(kbe_handle *h, int len, const double *E, const double *M);
+
 /* t = 0: G^<(k;0,0) = i f(h0(k)), G^>(0,0) = G^<(0,0) - i, I = 0 (no initial
  * correlations). Clears a sticky error. Requires kbe_set_hamiltonian. */
 kbe_status kbe_reset(kbe_handle *h);
@@ -152,6 +160,19 @@ kbe_status kbe_get_row(kbe_handle *h, int i, int which, double *out);
 /* Collision-integral sweep timing (CUDA events around each sweep launch). */
 kbe_status kbe_profile_enable(kbe_handle *h, int enable);
 kbe_status kbe_profile_read(kbe_handle *h, kbe_profile_stats *out);
+
+/* Checkpoint / resume. The state after row n is rows 0..n of the history,
+ * the two FP64 working rows, the last collision row and the densities and
+ * observables of rows 0..n; inputs (hoppings, interaction, drive) are not
+ * part of it. kbe_checkpoint_bytes: size of the current state (0 before
+ * kbe_reset). kbe_checkpoint_save copies it into caller-owned host memory of
+ * that size (synchronises). kbe_checkpoint_load restores it into a handle
+ * created with the same configuration (KBE_ERR_ARG otherwise); stepping then
+ * continues from row n exactly as the saving handle would have, given the
+ * same inputs. */
+size_t kbe_checkpoint_bytes(const kbe_handle *h);
+kbe_status kbe_checkpoint_save(kbe_handle *h, void *host, size_t bytes);
+kbe_status kbe_checkpoint_load(kbe_handle *h, const void *host, size_t bytes);
 
 /* Device bytes kbe_create would allocate for cfg (0 if cfg is invalid). */
 size_t kbe_memory_bytes(const kbe_config *cfg);

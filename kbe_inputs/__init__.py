@@ -21,6 +21,11 @@ Peierls drive):
           seed 2.
 * ``c4``  64 independent systems of uneven size (seed 3), see ``batched``.
 * ``c5``  c2's system with seeded target occupations (seed 4), see ``targets``.
+* ``paper`` the paper's own model problem shape (Sec. 2, Sec. 6): two bands on a
+          1-D ring of n_k = 1024, eps_v = -2(1 - cos k) - E_g/2,
+          eps_c = 2(1 - cos k) + E_g/2, E_g = 1, dipole kick E(t) = I delta(t - 0.5)
+          with d_k = 1, N_t = 500. The paper gives no U, I, dt or temperature;
+          this workload takes U = 0.5, I = 0.1, dt = 0.02, beta = 10, mu = 0.
 """
 from __future__ import annotations
 
@@ -53,6 +58,8 @@ class System:
     paper_shift: int = 0          # the -U n_c one-body term of Eq. 2 (N_b = 2)
     n_corr: int = 2               # corrector iterations, P(EC)^n_corr E
     seed: int = 0
+    dipole_E: Optional[np.ndarray] = None   # float64 [nt] dipole field samples (Eq. 4), or None
+    dipole_M: Optional[np.ndarray] = None   # complex128 [nb, nb] Hermitian dipole coupling
 
     @property
     def nk(self) -> int:
@@ -121,13 +128,40 @@ def config(name: str, nt: Optional[int] = None) -> System:
         R, T = square_hoppings(8, 0.25, 0.1, rng)
         s = System("c3", 8, 2, (16, 16), 512, 0.02, 1.5, 20.0, 0.0, R, T,
                    pair_pattern(8), pulse(512, 0.02, 0.5), (1.0, 0.0), seed=2)
+    elif name == "paper":
+        R, T = paper_hoppings(1.0)
+        dt, n_t = 0.02, 500
+        s = System("paper", 2, 1, (1024, 1), n_t, dt, 0.5, 10.0, 0.0, R, T, pair_pattern(2), None,
+                   (1.0, 0.0), hf=1, paper_shift=1, seed=5)
+        s.dipole_M = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+        s.dipole_E = kick(n_t, dt, 0.5, 0.1)
     else:
         raise KeyError(name)
     if nt is not None:
         s.nt = nt
         if s.A is not None:
             s.A = pulse(nt, s.dt, _pulse_amp(name))
+        if s.dipole_E is not None:
+            s.dipole_E = kick(nt, s.dt, 0.5, 0.1)
     return s
+
+
+def paper_hoppings(Eg: float = 1.0) -> Tuple[np.ndarray, np.ndarray]:
+    """eps_v(k) = -2(1 - cos k) - Eg/2, eps_c(k) = 2(1 - cos k) + Eg/2 as hoppings"""
+    R = np.array([[0, 0], [1, 0], [-1, 0]], dtype=np.int32)
+    T = np.zeros((3, 2, 2), dtype=np.complex128)
+    T[0, 0, 0], T[1, 0, 0], T[2, 0, 0] = -2 - Eg / 2, 1.0, 1.0
+    T[0, 1, 1], T[1, 1, 1], T[2, 1, 1] = 2 + Eg / 2, -1.0, -1.0
+    return R, T
+
+
+def kick(nt: int, dt: float, t_p: float, intensity: float) -> np.ndarray:
+    """I delta(t - t_p) as step-averaged samples: I / dt in the step containing t_p"""
+    E = np.zeros(nt)
+    i = int(np.floor(t_p / dt + 1e-9))
+    if 0 <= i < nt:
+        E[i] = intensity / dt
+    return E
 
 
 def _pulse_amp(name: str) -> float:

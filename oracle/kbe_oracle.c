@@ -499,6 +499,9 @@ typedef struct orc {
   int nA;
   double *Aseq;
   double dir[2];
+  int nE;    /* dipole field samples E_i (Eq. 4), coupling M [nb][nb] */
+  double *Eseq;
+  cplx dipM[MAXNB * MAXNB];
   int n; /* last completed row, -1 before reset */
   size_t blk;
   cplx *Hl, *Hg;
@@ -563,7 +566,7 @@ orc *orc_create(int nb, int dim, int L0, int L1, int nt_max, double dt, double b
 
 void orc_destroy(orc *s) {
   if (!s) return;
-  free(s->hopR); free(s->hopT); free(s->Useq); free(s->Aseq);
+  free(s->hopR); free(s->hopT); free(s->Useq); free(s->Aseq); free(s->Eseq);
   free(s->Hl); free(s->Hg); free(s->Ipl); free(s->Ipg); free(s->Icl); free(s->Icg);
   free(s->Sl); free(s->Sg); free(s->rho); free(s->h); free(s->Uk); free(s->Vk);
   free(s->Wk); free(s->lam); free(s->obs); free(s->nkb);
@@ -603,6 +606,20 @@ int orc_set_drive(orc *s, int len, const double *A, const double *dir) {
   if (dir) {
     s->dir[0] = dir[0];
     s->dir[1] = s->dim == 2 ? dir[1] : 0.0;
+  }
+  return 0;
+}
+
+/* dipole drive of Eq. 4 in the length gauge: h gains E_i M during step i */
+int orc_set_dipole(orc *s, int len, const double *E, const double *M) {
+  free(s->Eseq);
+  s->Eseq = NULL;
+  s->nE = 0;
+  if (E && len > 0) {
+    s->nE = len;
+    s->Eseq = malloc(sizeof(double) * len);
+    memcpy(s->Eseq, E, sizeof(double) * len);
+    memcpy(s->dipM, M, sizeof(cplx) * s->nb * s->nb);
   }
   return 0;
 }
@@ -666,6 +683,8 @@ static void build_h_and_props(orc *s, int n, const cplx *rho_mid) {
     h0_at(s, k, A_at(s, n - 1), hk);
     for (int e = 0; e < nb2; ++e) hk[e] += hf[e];
     if (s->paper_shift) hk[(nb - 1) * nb + (nb - 1)] -= Umid;
+    if (n - 1 < s->nE)
+      for (int e = 0; e < nb2; ++e) hk[e] += s->Eseq[n - 1] * s->dipM[e];
   }
   orc_propagators(nb, s->nk, s->dt, (const double *)s->h, (double *)s->Uk, (double *)s->Vk,
                   (double *)s->Wk, s->lam);

@@ -47,6 +47,7 @@ def _load():
             lib.orc_set_hamiltonian.argtypes = [P, i, P, P]
             lib.orc_set_interaction.argtypes = [P, i, P, P]
             lib.orc_set_drive.argtypes = [P, i, P, P]
+            lib.orc_set_dipole.argtypes = [P, i, P, P]
             lib.orc_reset.argtypes = [P]
             lib.orc_step.argtypes = [P, i]
             lib.orc_current.argtypes = [P]
@@ -166,6 +167,11 @@ class Oracle:
         else:
             lib.orc_set_drive(self._h, 0, None, _ptr(d))
         self._keep = (R, T, Us, v, d)
+        if getattr(sys, "dipole_E", None) is not None:
+            E = np.ascontiguousarray(sys.dipole_E, np.float64)
+            M = _c128(sys.dipole_M)
+            lib.orc_set_dipole(self._h, len(E), _ptr(E), _ptr(M))
+            self._keep = self._keep + (E, M)
         if lib.orc_reset(self._h) != 0:
             raise RuntimeError("oracle: reset failed")
 

@@ -34,7 +34,8 @@ EXPORTS = [
     "kbe_op_propagators", "kbe_op_update_row", "kbe_op_sigma_row_noalloc",
     "kbe_op_collision_row_workspace", "kbe_op_pack", "kbe_memory_bytes", "kbe_batch_create",
     "kbe_batch_destroy", "kbe_batch_system", "kbe_batch_reset", "kbe_batch_step",
-    "kbe_batch_synchronize",
+    "kbe_batch_synchronize", "kbe_checkpoint_bytes", "kbe_checkpoint_save", "kbe_checkpoint_load",
+    "kbe_set_dipole",
 ]
 
 
@@ -101,6 +102,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "kbe_op_update_row": (I, [pmesh, I, D, D, P, P, P, P, P, P, P, P]),
         "kbe_op_sigma_row_noalloc": (I, [pmesh, P, I, D, P, P, P, P]),
         "kbe_memory_bytes": (S, [pcfg]),
+        "kbe_checkpoint_bytes": (S, [P]),
+        "kbe_set_dipole": (I, [P, I, P, P]),
+        "kbe_checkpoint_save": (I, [P, P, S]),
+        "kbe_checkpoint_load": (I, [P, P, S]),
         "kbe_batch_create": (I, [I, pcfg, P, S, ctypes.POINTER(P), P]),
         "kbe_batch_destroy": (I, [P]),
         "kbe_batch_system": (P, [P, I]),
@@ -191,6 +196,8 @@ class KBE:
         k.set_hamiltonian(sys.hop_R, sys.hop_T)
         k.set_interaction(np.array([sys.U]) if U is None else U, sys.v)
         k.set_drive(sys.A, sys.direction)
+        if getattr(sys, "dipole_E", None) is not None:
+            k.set_dipole(sys.dipole_E, sys.dipole_M)
         k.reset()
         return k
 
@@ -204,6 +211,8 @@ class KBE:
         self.set_hamiltonian(sys.hop_R, sys.hop_T)
         self.set_interaction(np.array([sys.U]) if U is None else U, sys.v)
         self.set_drive(sys.A, sys.direction)
+        if getattr(sys, "dipole_E", None) is not None:
+            self.set_dipole(sys.dipole_E, sys.dipole_M)
 
     def __del__(self):
         try:
@@ -228,6 +237,15 @@ class KBE:
         else:
             A = np.ascontiguousarray(A, np.float64)
             _check(load().kbe_set_drive(self._h, len(A), _np_ptr(A), _np_ptr(d)), self._h)
+
+    def set_dipole(self, E, M=None):
+        """dipole drive E_i M (Eq. 4); E None removes it"""
+        if E is None:
+            _check(load().kbe_set_dipole(self._h, 0, None, None), self._h)
+            return
+        E = np.ascontiguousarray(E, np.float64)
+        M = np.ascontiguousarray(M, np.complex128)
+        _check(load().kbe_set_dipole(self._h, len(E), _np_ptr(E), _np_ptr(M)), self._h)
 
     def reset(self):
         _check(load().kbe_reset(self._h), self._h)
@@ -261,6 +279,17 @@ class KBE:
         out = np.empty((i + 1, self.nk, self.nb, self.nb), np.complex128)
         _check(load().kbe_get_row(self._h, int(i), int(which), _np_ptr(out)), self._h)
         return out
+
+    def checkpoint(self) -> bytes:
+        """The state after the current row, as bytes (history rows 0..n etc.)."""
+        nbytes = int(load().kbe_checkpoint_bytes(self._h))
+        buf = np.empty(nbytes, np.uint8)
+        _check(load().kbe_checkpoint_save(self._h, _np_ptr(buf), nbytes), self._h)
+        return buf.tobytes()
+
+    def restore(self, data: bytes):
+        buf = np.frombuffer(data, np.uint8)
+        _check(load().kbe_checkpoint_load(self._h, _np_ptr(np.ascontiguousarray(buf)), len(buf)), self._h)
 
     def profile(self, enable: bool = True):
         _check(load().kbe_profile_enable(self._h, int(enable)), self._h)

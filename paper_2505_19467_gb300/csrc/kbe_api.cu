@@ -37,6 +37,8 @@ struct kbe_handle {
   std::vector<double> v;
   std::vector<double> A;
   double dir[2] = {1.0, 0.0};
+  std::vector<double> dipE;    // dipole field samples
+  double2 *d_dipM = nullptr;   // dipole coupling (device)
 
   // device arena
   void *H = nullptr;           // history triangle (G^<, dG = G^< - G^>) in the precision's storage
@@ -119,7 +121,8 @@ cudaError_t dalloc(kbe_handle *h, T **p, size_t count) {
 
 void free_all(kbe_handle *h) {
   void *ptrs[] = {h->H, h->Wrow[0], h->Wrow[1], h->coef, h->Ip, h->Ic, h->Sig, h->work, h->U, h->V,
-                  h->hk, h->rho, h->obs, h->nkb, h->status, h->d_hopR, h->d_hopT, h->d_U};
+                  h->hk, h->rho, h->obs, h->nkb, h->status, h->d_hopR, h->d_hopT, h->d_U,
+                  h->d_dipM};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (auto &pr : h->ev) {
@@ -206,6 +209,8 @@ kbe_status build_props(kbe_handle *h, int n, const double2 *ra, const double2 *r
   p.hf = h->cfg.hf;
   p.paper_shift = h->cfg.paper_shift;
   for (int i = 0; i < h->nb2; ++i) p.v[i] = h->v[(size_t)i];
+  p.dipM = h->dipE.empty() ? nullptr : h->d_dipM;
+  p.dipE = (n - 1 < (int)h->dipE.size()) ? h->dipE[(size_t)(n - 1)] : 0.0;
   cudaError_t e = kbe::launch_build_props(h->mesh, hop_table(h), p, h->cfg.dt, nullptr, h->hk, h->U,
                                           h->V, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "build_props");
@@ -450,6 +455,26 @@ kbe_status kbe_set_drive(kbe_handle *h, int len, const double *A, const double *
   return KBE_OK;
 }
 
+kbe_status kbe_set_dipole(kbe_handle *h, int len, const double *E, const double *M) {
+  if (!h) return KBE_ERR_ARG;
+  if (len < 0 || (E && len > 0 && !M)) return fail(h, KBE_ERR_ARG, "set_dipole: bad arguments");
+  if (!E || len == 0) {
+    h->dipE.clear();
+    return KBE_OK;
+  }
+  for (int i = 0; i < len; ++i)
+    if (!std::isfinite(E[i])) return fail(h, KBE_ERR_NONFINITE, "set_dipole: non-finite field");
+  for (int i = 0; i < 2 * h->nb2; ++i)
+    if (!std::isfinite(M[i])) return fail(h, KBE_ERR_NONFINITE, "set_dipole: non-finite coupling");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess && !h->d_dipM) e = cudaMalloc((void **)&h->d_dipM, sizeof(double2) * h->nb2);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->d_dipM, M, sizeof(double2) * h->nb2, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_dipole");
+  h->dipE.assign(E, E + len);
+  return KBE_OK;
+}
+
 kbe_status kbe_reset(kbe_handle *h) {
   if (!h) return KBE_ERR_ARG;
   if (!h->ham_set) return fail(h, KBE_ERR_STATE, "reset: set_hamiltonian first");
@@ -605,6 +630,103 @@ kbe_status kbe_profile_read(kbe_handle *h, kbe_profile_stats *out) {
     }
   }
   *out = s;
+  return KBE_OK;
+}
+
+// ---- checkpoint / resume --------------------------------------------------
+
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int version, nb, dim, L0, L1, nt_max, precision, n;
+};
+
+// the device regions of the state after row n, in file order
+struct Region {
+  const void *dev;
+  void *dev_w;
+  size_t bytes;
+};
+
+std::vector<Region> state_regions(kbe_handle *h) {
+  const int n = h->n;
+  const size_t row = (size_t)(n + 1) * 2 * h->blk * sizeof(double2);
+  std::vector<Region> r;
+  r.push_back({h->H, h->H, (tri(n, n) + 1) * 2 * h->blk * h->esz});
+  r.push_back({frow(h, n), frow(h, n), row});
+  if (n >= 1) r.push_back({frow(h, n - 1), frow(h, n - 1), (size_t)n * 2 * h->blk * sizeof(double2)});
+  r.push_back({h->Ip, h->Ip, row});
+  r.push_back({h->rho, h->rho, (size_t)(n + 1) * h->nb2 * sizeof(double2)});
+  r.push_back({h->obs, h->obs, (size_t)(n + 1) * 6 * sizeof(double)});
+  r.push_back({h->nkb, h->nkb, (size_t)(n + 1) * h->mesh.nk * h->cfg.nb * sizeof(double)});
+  return r;
+}
+}  // namespace
+
+size_t kbe_checkpoint_bytes(const kbe_handle *h) {
+  if (!h || h->n < 0) return 0;
+  size_t b = sizeof(CkptHeader);
+  for (const Region &r : state_regions(const_cast<kbe_handle *>(h))) b += r.bytes;
+  return b;
+}
+
+kbe_status kbe_checkpoint_save(kbe_handle *h, void *host, size_t bytes) {
+  if (!h || !host) return KBE_ERR_ARG;
+  if (h->n < 0) return fail(h, KBE_ERR_STATE, "checkpoint_save: nothing to save before kbe_reset");
+  if (bytes < kbe_checkpoint_bytes(h)) return fail(h, KBE_ERR_ARG, "checkpoint_save: buffer too small");
+  kbe_status st = check_device_status(h);
+  if (st != KBE_OK) return st;
+  CkptHeader hd{};
+  memcpy(hd.magic, "KBECKPT", 8);
+  hd.version = 1;
+  hd.nb = h->cfg.nb;
+  hd.dim = h->cfg.dim;
+  hd.L0 = h->cfg.L[0];
+  hd.L1 = h->cfg.L[1];
+  hd.nt_max = h->cfg.nt_max;
+  hd.precision = h->cfg.precision;
+  hd.n = h->n;
+  char *p = (char *)host;
+  memcpy(p, &hd, sizeof hd);
+  p += sizeof hd;
+  for (const Region &r : state_regions(h)) {
+    cudaError_t e = cudaMemcpyAsync(p, r.dev, r.bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "checkpoint_save");
+    p += r.bytes;
+  }
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "checkpoint_save");
+  return KBE_OK;
+}
+
+kbe_status kbe_checkpoint_load(kbe_handle *h, const void *host, size_t bytes) {
+  if (!h || !host || bytes < sizeof(CkptHeader)) return KBE_ERR_ARG;
+  CkptHeader hd;
+  memcpy(&hd, host, sizeof hd);
+  if (memcmp(hd.magic, "KBECKPT", 8) != 0 || hd.version != 1 || hd.nb != h->cfg.nb ||
+      hd.dim != h->cfg.dim || hd.L0 != h->cfg.L[0] || hd.L1 != h->cfg.L[1] ||
+      hd.nt_max != h->cfg.nt_max || hd.precision != h->cfg.precision || hd.n < 0 || hd.n > h->cfg.nt_max)
+    return fail(h, KBE_ERR_ARG, "checkpoint_load: checkpoint does not match this handle's configuration");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "checkpoint_load");
+  const int keep = h->n;
+  h->n = hd.n;
+  size_t need = sizeof hd;
+  for (const Region &r : state_regions(h)) need += r.bytes;
+  if (bytes < need) {
+    h->n = keep;
+    return fail(h, KBE_ERR_ARG, "checkpoint_load: buffer too small");
+  }
+  const char *p = (const char *)host + sizeof hd;
+  for (const Region &r : state_regions(h)) {
+    e = cudaMemcpyAsync(r.dev_w, p, r.bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "checkpoint_load");
+    p += r.bytes;
+  }
+  cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
+  e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "checkpoint_load");
+  h->sticky = KBE_OK;
   return KBE_OK;
 }
 

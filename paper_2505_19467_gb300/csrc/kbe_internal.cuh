@@ -106,6 +106,8 @@ struct PropParams {
   double Umid;
   int hf, paper_shift;
   double v[kMaxNb * kMaxNb];
+  const double2 *dipM;          // device nb*nb dipole coupling (Eq. 4), or NULL
+  double dipE;                  // its field sample for the step
 };
 // h for the step (from the hopping table, mean field and shift; or h_in when
 // not NULL, then hop / p are unused), U = e^{-i dt h}, V = (U - 1) h^{-1};

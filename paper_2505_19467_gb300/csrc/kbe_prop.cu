@@ -255,6 +255,7 @@ __global__ void __launch_bounds__(256) build_props_kernel(Mesh m, HopTable hop, 
         hv = c_add(hv, c_scale(p.Umid, x));
       }
       if (p.paper_shift && g.a == NB - 1 && g.b == NB - 1) hv.x -= p.Umid;
+      if (p.dipM && p.dipE != 0.0) hv = c_add(hv, c_scale(p.dipE, p.dipM[g.e]));   // Eq. 4
     }
   }
   sh[0][o] = hv;

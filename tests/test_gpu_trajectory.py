@@ -132,3 +132,32 @@ def test_nonfinite_state_is_sticky_until_reset():
     g.reset()
     g.step(2)
     g.synchronize()
+
+
+def test_dipole_kick_paper_model_every_entry():
+    """The paper's two-band model (Sec. 2) with the dipole kick of Eq. 4, on a
+    16-site ring so that the oracle runs in seconds."""
+    s = ki.config("paper", nt=32)
+    s.L = (16, 1)
+    compare_trajectory(s, 32)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_checkpoint_resume_is_exact(prec):
+    s = ki.small_system(3, (3, 2), 14, 0.05, 0.8, seed=21, drive_amp=0.4)
+    a = kbe.KBE.from_system(s, precision=prec)
+    a.step(7)
+    ck = a.checkpoint()
+    a.step(7)
+    b = kbe.KBE.from_system(s, precision=prec)
+    b.step(2)                            # some other state, overwritten by the restore
+    b.restore(ck)
+    assert b.n == 7
+    b.step(7)
+    for i in (3, 7, 10, 14):
+        for x in (0, 1):
+            assert np.array_equal(a.row(i, x), b.row(i, x)), (i, x)
+    assert np.array_equal(a.observables_all()[1], b.observables_all()[1])
+    c = kbe.KBE(s.nb, s.dim, (2, 3), s.nt, s.dt, s.beta, s.mu, precision=prec)
+    with pytest.raises(kbe.KBEError):
+        c.restore(ck)                    # another mesh

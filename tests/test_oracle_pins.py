@@ -251,6 +251,29 @@ def test_noninteracting_closed_form(driven):
         assert np.abs(a - b).max() < 1e-13
 
 
+def test_noninteracting_closed_form_with_dipole_kick():
+    """U = 0 with the dipole drive of Eq. 4: G^<(t_n, t_j) = i Uc_n rho0 Uc_j^+
+    with Uc the product of exp(-i dt (h0(k) + E_i M)); the kick moves weight
+    from the valence to the conduction band."""
+    s = ki.config("paper", nt=40)
+    s.L = (16, 1)
+    s.U = 0.0
+    s.dipole_E = ki.kick(40, s.dt, 0.3, 0.4)
+    o = oracle.Oracle(s)
+    o.step(40)
+    nkb0 = o.observables(0)[0]
+    nkb1 = o.observables(40)[0]
+    assert np.abs(nkb1[:, 1] - nkb0[:, 1]).max() > 1e-3
+    for k in (0, 5, 11):
+        rho0 = fermi_matrix(h0_of(s, k), s.beta, s.mu)
+        Uc = [np.eye(2, dtype=complex)]
+        for i in range(40):
+            Uc.append(sla.expm(-1j * s.dt * (h0_of(s, k) + s.dipole_E[i] * s.dipole_M)) @ Uc[-1])
+        for (i, j) in [(10, 3), (20, 14), (40, 0), (40, 40), (7, 33)]:
+            want = 1j * Uc[i] @ rho0 @ Uc[j].conj().T
+            assert np.abs(o.block(i, j, 0)[k] - want).max() < 1e-13, (i, j)
+
+
 def test_particle_number_conserved_driven_interacting():
     s = ki.small_system(3, (3, 3), 40, 0.04, 1.2, seed=5, drive_amp=0.5)
     o = oracle.Oracle(s)

@@ -13,8 +13,9 @@
 //   1. forward DFT of every (l, x, a, b) array,
 //   2. band products per (l, j, R),
 //   3. inverse DFT into the Sigma row.
-// Cost per pair: O(N_b^2 n_k (L0 + L1)) for the DFTs and O(N_b^3 n_k) for the
-// products, against O(N_b^4 n_k^3) for Algorithm 2.
+// Cost per pair: O(N_b^2 n_k log n_k) for power-of-two meshes (FFT), else
+// O(N_b^2 n_k (L0 + L1)), and O(N_b^3 n_k) for the products, against
+// O(N_b^4 n_k^3) for Algorithm 2.
 #include "kbe_internal.cuh"
 
 namespace kbe {
@@ -23,8 +24,71 @@ namespace {
 
 // Separable 2-D DFT of length-n_k arrays (mesh L0 x L1, k = k0 * L1 + k1):
 //   out[R] = scale * sum_k exp(sign * i * 2 pi (k0 R0 / L0 + k1 R1 / L1)) in[k].
-// One CTA per array (grid-stride over arrays); the array and the half-way
-// result live in shared memory together with the twiddle tables.
+// One array at a time per CTA (grid-stride over arrays), in shared memory.
+// An axis whose length is a power of two is transformed in place by a
+// radix-2 FFT (bit reversal, then log2 L butterfly stages; O(L log L));
+// other lengths use the direct sum over that axis (O(L^2)). The twiddle
+// tables e^{sign 2 pi i m / L} are built once per CTA.
+
+__device__ __forceinline__ bool is_pow2(int L) { return L > 0 && (L & (L - 1)) == 0; }
+
+// in-place FFT of `count` sequences of length L, element i of sequence q at
+// x[q * qstride + i * stride]; tw[m] = e^{sign 2 pi i m / L}
+__device__ void fft_axis(double2 *x, int L, int stride, int count, int qstride, const double2 *tw) {
+  int logL = 0;
+  while ((1 << logL) < L) ++logL;
+  const int total = count * L;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {   // bit reversal
+    const int q = e / L, i = e - q * L;
+    const int r = __brev(i) >> (32 - logL);
+    if (logL > 0 && i < r) {
+      double2 *p = x + q * qstride;
+      const double2 t = p[i * stride];
+      p[i * stride] = p[r * stride];
+      p[r * stride] = t;
+    }
+  }
+  __syncthreads();
+  for (int len = 2; len <= L; len <<= 1) {
+    const int half = len >> 1, step = L / len, nbf = count * (L >> 1);
+    for (int e = threadIdx.x; e < nbf; e += blockDim.x) {
+      const int q = e / (L >> 1), bq = e - q * (L >> 1);
+      const int grp = bq / half, pos = bq - grp * half;
+      double2 *p = x + q * qstride;
+      const int i = grp * len + pos, j = i + half;
+      const double2 u = p[i * stride];
+      const double2 t = c_mul(tw[pos * step], p[j * stride]);
+      p[i * stride] = c_add(u, t);
+      p[j * stride] = c_sub(u, t);
+    }
+    __syncthreads();
+  }
+}
+
+// direct transform of `count` sequences of length L (x -> tmp -> x)
+__device__ void dft_axis(double2 *x, double2 *tmp, int L, int stride, int count, int qstride,
+                         const double2 *tw) {
+  const int total = count * L;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int q = e / L, R = e - q * L;
+    const double2 *p = x + q * qstride;
+    double2 acc = make_double2(0.0, 0.0);
+    int ph = 0;
+    for (int kk = 0; kk < L; ++kk) {
+      acc = c_fma(tw[ph], p[kk * stride], acc);
+      ph += R;
+      if (ph >= L) ph -= L;
+    }
+    tmp[e] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int q = e / L, R = e - q * L;
+    x[q * qstride + R * stride] = tmp[e];
+  }
+  __syncthreads();
+}
+
 __global__ void dft_rows_kernel(const double2 *__restrict__ in, double2 *__restrict__ out,
                                 long narr, int L0, int L1, int sign, double scale) {
   extern __shared__ double2 sm[];
@@ -48,30 +112,16 @@ __global__ void dft_rows_kernel(const double2 *__restrict__ in, double2 *__restr
     __syncthreads();
     for (int e = threadIdx.x; e < nk; e += blockDim.x) x[e] = src[e];
     __syncthreads();
-    for (int e = threadIdx.x; e < nk; e += blockDim.x) {
-      const int k0 = e / L1, R1 = e - (e / L1) * L1;
-      double2 acc = make_double2(0.0, 0.0);
-      int ph = 0;
-      for (int k1 = 0; k1 < L1; ++k1) {
-        acc = c_fma(tw1[ph], x[k0 * L1 + k1], acc);
-        ph += R1;
-        if (ph >= L1) ph -= L1;
-      }
-      t[e] = acc;
+    if (L1 > 1) {   // axis 1: L0 contiguous sequences of length L1
+      if (is_pow2(L1)) fft_axis(x, L1, 1, L0, L1, tw1);
+      else dft_axis(x, t, L1, 1, L0, L1, tw1);
     }
-    __syncthreads();
+    if (L0 > 1) {   // axis 0: L1 sequences of length L0, stride L1
+      if (is_pow2(L0)) fft_axis(x, L0, L1, L1, 1, tw0);
+      else dft_axis(x, t, L0, L1, L1, 1, tw0);
+    }
     double2 *dst = out + arr * nk;
-    for (int e = threadIdx.x; e < nk; e += blockDim.x) {
-      const int R0 = e / L1, R1 = e - (e / L1) * L1;
-      double2 acc = make_double2(0.0, 0.0);
-      int ph = 0;
-      for (int k0 = 0; k0 < L0; ++k0) {
-        acc = c_fma(tw0[ph], t[k0 * L1 + R1], acc);
-        ph += R0;
-        if (ph >= L0) ph -= L0;
-      }
-      dst[e] = c_scale(scale, acc);
-    }
+    for (int e = threadIdx.x; e < nk; e += blockDim.x) dst[e] = c_scale(scale, x[e]);
   }
 }
 
@@ -156,7 +206,7 @@ cudaError_t launch_dft_rows(const double2 *in, double2 *out, long narr, int L0, 
     attr_bytes = smem;
   }
   int threads = nk >= 256 ? 256 : ((nk + 31) / 32) * 32;
-  long blocks = narr < 152L * 32 ? narr : 152L * 32;
+  long blocks = narr < 152L * 8 ? narr : 152L * 8;
   dft_rows_kernel<<<(unsigned)blocks, threads, smem, st>>>(in, out, narr, L0, L1, sign, scale);
   return cudaGetLastError();
 }

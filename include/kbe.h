@@ -113,8 +113,11 @@ kbe_status kbe_destroy(kbe_handle *h);
 kbe_status kbe_set_hamiltonian(kbe_handle *h, int nhop, const int *R, const double *t);
 
 /* U(t_i) samples (len = nt_max + 1) or one constant (len = 1), the U(t) of
- * Eqs. 2 and 7; v: host double [nb][nb] pairing pattern v_ab (symmetric,
- * zero diagonal), NULL keeps the current one (default 1 - delta_ab). */
+ * Eqs. 2 and 7; v: host double [nb][nb] pairing pattern v_ab, NULL keeps
+ * the current one (default 1 - delta_ab, the paper's pair of bands). v must
+ * be symmetric (the interaction U sum_ab v_ab n_a n_b of Eq. 2 is; an
+ * asymmetric v would make the mean field non-Hermitian): KBE_ERR_ARG
+ * otherwise. */
 kbe_status kbe_set_interaction(kbe_handle *h, int len, const double *U, const double *v);
 
 /* Peierls vector potential samples A_i = A(t_{i+1/2}), i < len (len >= 1), the
@@ -176,6 +179,33 @@ kbe_status kbe_checkpoint_load(kbe_handle *h, const void *host, size_t bytes);
 
 /* Device bytes kbe_create would allocate for cfg (0 if cfg is invalid). */
 size_t kbe_memory_bytes(const kbe_config *cfg);
+
+/* ---------------------------------------------------------------------- */
+/* reverse mode                                                             */
+/* ---------------------------------------------------------------------- */
+
+/* Gradient of a loss of the current row's occupations. The paper has no
+ * counterpart: it only propagates (Algorithm 1). With N = the current step
+ * and n_kb = Im G^<_bb(k; t_N, t_N) (the occupations kbe_observables
+ * reports), given g = dL/dn_kb (host double [nk][nb]), returns
+ *   dL_dA[i] = dL/dA_i for i < N (host double [nt_max]; entries >= N are 0),
+ *              A_i being the Peierls sample the step to t_{i+1} used (the
+ *              i-th kbe_set_drive sample, or its last one when fewer were
+ *              given),
+ *   dL_dU    = dL/dU (host double [1]) for the constant U of kbe_set_interaction,
+ * the exact derivative of the computed trajectory (the discrete adjoint of
+ * Algorithm 1 as this library evaluates it: the trapezoid collision sums, the
+ * DFT form of Eq. 7, the series propagators, the mean field and the
+ * predictor-corrector schedule). Steps are recomputed one at a time from the
+ * stored history, so no per-step tape is kept; the history is left as it was
+ * and stepping may continue afterwards.
+ * Requires KBE_PREC_FP64, a constant U (len 1), at least one step, and
+ * dt ||h(k)||_rowsum <= 1/4 at every step (the propagators' unscaled
+ * series); KBE_ERR_UNSUPPORTED otherwise (the handle stays usable). The first
+ * call allocates kbe_backward_memory_bytes(cfg) of device memory, kept until
+ * kbe_destroy (KBE_ERR_OOM if it does not fit). Synchronises. */
+kbe_status kbe_backward(kbe_handle *h, const double *dL_dn, double *dL_dA, double *dL_dU);
+size_t kbe_backward_memory_bytes(const kbe_config *cfg);
 
 /* ---------------------------------------------------------------------- */
 /* batched systems (independent systems of uneven N_b, n_k, N_t)            */

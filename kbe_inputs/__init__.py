@@ -194,14 +194,21 @@ def targets(nk: int, nb: int, seed: int = 4) -> np.ndarray:
 def small_system(nb: int, L: Tuple[int, int], nt: int, dt: float, U: float,
                  seed: int, drive_amp: float = 0.0, beta: float = 10.0,
                  mu: float = 0.0, hf: int = 1, paper_shift: int = 0,
-                 n_corr: int = 2) -> System:
-    """A seeded test system of arbitrary size (square-lattice bands)."""
+                 n_corr: int = 2, band_velocity: float = 0.0) -> System:
+    """A seeded test system of arbitrary size (square-lattice bands).
+
+    band_velocity s scales the R != 0 hoppings of band b by (1 + s b), so that
+    the bands disperse differently and a Peierls drive changes occupations
+    even without interaction (equal dispersions only add a phase).
+    """
     rng = np.random.default_rng(seed)
     dim = 1 if L[1] == 1 else 2
     R, T = square_hoppings(nb, 0.3, 0.1, rng)
     if dim == 1:
         keep = [0, 1, 2]
         R, T = R[keep].copy(), T[keep].copy()
+    for b in range(nb):
+        T[1:, b, b] *= 1.0 + band_velocity * b
     A = pulse(nt, dt, drive_amp, t0=nt * dt / 3, sigma=nt * dt / 8, omega=2.0) if drive_amp else None
     return System(f"small{nb}x{L}", nb, dim, L, nt, dt, U, beta, mu, R, T,
                   pair_pattern(nb), A, (1.0, 0.0), hf=hf, paper_shift=paper_shift,

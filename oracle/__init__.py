@@ -10,6 +10,7 @@ checked by ``tests/test_oracle_pins.py``.
 """
 from .oracle import (Oracle, build, sigma_pair, sigma_pair_literal, collision_row,
                      propagators, update_row, library_path)
+from . import gradient
 
 PINS = {
     "sigma_pair": "literal Eq. 7 triple sum (N_b=2 bar form, general v); ED O(U^2)",
@@ -20,4 +21,6 @@ PINS = {
     "update_row": "U = 0 closed form (driven and undriven)",
     "Oracle.step": "U = 0 closed form; particle number; energy drift O(dt^2); "
                    "exact diagonalisation through O(U^2); time-step order 2",
+    "gradient.directional": "U = 0: Frechet derivative of the exact one-step propagators "
+                            "(drive samples and U through the mean field and shift)",
 }

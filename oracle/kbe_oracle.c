@@ -584,8 +584,17 @@ int orc_set_hamiltonian(orc *s, int nhop, const int *R, const double *t) {
   return 0;
 }
 
+/* v must be symmetric: the interaction U sum_ab v_ab n_a n_b of Eq. 2 is, and
+ * an asymmetric v would make the mean field non-Hermitian (the propagators
+ * below diagonalise h as a Hermitian matrix). */
 int orc_set_interaction(orc *s, int len, const double *U, const double *v) {
   if (len != 1 && len < s->nt_max + 1) return -1;
+  if (v)
+    for (int a = 0; a < s->nb; ++a)
+      for (int b = a + 1; b < s->nb; ++b) {
+        double x = v[a * s->nb + b], y = v[b * s->nb + a];
+        if (fabs(x - y) > 1e-12 * (fabs(x) + fabs(y))) return -2;
+      }
   free(s->Useq);
   s->nU = len;
   s->Useq = malloc(sizeof(double) * len);

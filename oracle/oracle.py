@@ -158,8 +158,9 @@ class Oracle:
         lib.orc_set_hamiltonian(self._h, R.shape[0], _ptr(R), _ptr(T))
         Us = np.array([sys.U], np.float64) if U is None else np.ascontiguousarray(U, np.float64)
         v = np.ascontiguousarray(sys.v, np.float64)
-        if lib.orc_set_interaction(self._h, len(Us), _ptr(Us), _ptr(v)) != 0:
-            raise ValueError("oracle: bad interaction samples")
+        rc = lib.orc_set_interaction(self._h, len(Us), _ptr(Us), _ptr(v))
+        if rc != 0:
+            raise ValueError("oracle: v must be symmetric" if rc == -2 else "oracle: bad interaction samples")
         d = np.array(sys.direction, np.float64)
         if sys.A is not None:
             A = np.ascontiguousarray(sys.A, np.float64)

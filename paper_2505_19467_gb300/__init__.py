@@ -6,10 +6,19 @@ C ABI in ``include/kbe.h``); this package is its thin Python binding.
 from ._binding import (KBE, KBEError, KBE_PREC_FP64, KBE_PREC_DF64, KBE_PREC_C64, PRECISIONS,
                        EXPORTS, collision_row_workspace, pack, LIB_PATH, load, collision_row,
                        propagators, sigma_row, sigma_row_noalloc, sigma_row_workspace, update_row,
-                       NOALLOC_SCRATCH_BYTES, KBEBatch, memory_bytes, system_config)
+                       NOALLOC_SCRATCH_BYTES, KBEBatch, memory_bytes, backward_memory_bytes,
+                       system_config)
 from .builder import build
 
 __all__ = ["KBE", "KBEError", "KBE_PREC_FP64", "KBE_PREC_DF64", "KBE_PREC_C64", "PRECISIONS",
            "collision_row_workspace", "pack", "EXPORTS", "LIB_PATH", "load", "build",
            "sigma_row", "sigma_row_noalloc", "sigma_row_workspace", "NOALLOC_SCRATCH_BYTES", "collision_row", "propagators", "update_row",
-           "KBEBatch", "memory_bytes", "system_config"]
+           "KBEBatch", "memory_bytes", "backward_memory_bytes", "system_config", "occupations",
+           "KBEFunction"]
+
+
+def __getattr__(name):   # the torch.autograd wrapper is imported on first use
+    if name in ("occupations", "KBEFunction"):
+        from . import autograd
+        return getattr(autograd, name)
+    raise AttributeError(name)

@@ -35,7 +35,7 @@ EXPORTS = [
     "kbe_op_collision_row_workspace", "kbe_op_pack", "kbe_memory_bytes", "kbe_batch_create",
     "kbe_batch_destroy", "kbe_batch_system", "kbe_batch_reset", "kbe_batch_step",
     "kbe_batch_synchronize", "kbe_checkpoint_bytes", "kbe_checkpoint_save", "kbe_checkpoint_load",
-    "kbe_set_dipole",
+    "kbe_set_dipole", "kbe_backward", "kbe_backward_memory_bytes",
 ]
 
 
@@ -112,6 +112,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "kbe_batch_reset": (I, [P]),
         "kbe_batch_step": (I, [P, I]),
         "kbe_batch_synchronize": (I, [P]),
+        "kbe_backward": (I, [P, P, P, P]),
+        "kbe_backward_memory_bytes": (S, [pcfg]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -167,6 +169,11 @@ def system_config(sys, nt_max=None, precision=KBE_PREC_FP64) -> kbe_config:
 
 def memory_bytes(cfg: kbe_config) -> int:
     return int(load().kbe_memory_bytes(ctypes.byref(cfg)))
+
+
+def backward_memory_bytes(cfg: kbe_config) -> int:
+    """device bytes the first KBE.backward of a handle with cfg allocates"""
+    return int(load().kbe_backward_memory_bytes(ctypes.byref(cfg)))
 
 
 class KBE:
@@ -290,6 +297,15 @@ class KBE:
     def restore(self, data: bytes):
         buf = np.frombuffer(data, np.uint8)
         _check(load().kbe_checkpoint_load(self._h, _np_ptr(np.ascontiguousarray(buf)), len(buf)), self._h)
+
+    def backward(self, dL_dn):
+        """(dL/dA [nt_max], dL/dU) for the cotangent dL_dn [nk][nb] of the
+        current row's occupations (kbe_backward)."""
+        g = np.ascontiguousarray(dL_dn, np.float64).reshape(self.nk, self.nb)
+        dA = np.empty(self.nt_max, np.float64)
+        dU = np.empty(1, np.float64)
+        _check(load().kbe_backward(self._h, _np_ptr(g), _np_ptr(dA), _np_ptr(dU)), self._h)
+        return dA, float(dU[0])
 
     def profile(self, enable: bool = True):
         _check(load().kbe_profile_enable(self._h, int(enable)), self._h)

@@ -1,0 +1,839 @@
+// Reverse mode (discrete adjoint) of one time step, FP64 history.
+//
+// kbe_backward differentiates a loss of the final-time occupations n_kb(t_N)
+// with respect to the Peierls samples A_i and the interaction U by walking
+// the steps n = N..1 backwards. Everything step n reads is the history
+// triangle (rows < n are final once written) and I_{n-1}, itself a function
+// of that history, so the step's intermediates (predictor and corrector
+// rows, h, U, V, the Sigma and collision rows of every stage) are recomputed
+// from the history, then the step's operations are transposed in reverse
+// order. The transposes are those of the kernels' own arithmetic (the
+// trapezoid sweep in the dG form, the DFT Sigma, the truncated power series
+// of the propagators), so the gradient is that of the computed trajectory.
+//
+// Convention: for a complex variable z the adjoint lam_z is defined by
+// dL = Re sum conj(lam_z) dz. A holomorphic use z = c w gives lam_w += conj(c)
+// lam_z, an anti-holomorphic one z = c conj(w) gives lam_w += conj(lam_z) c;
+// a matrix product Z = A B gives lam_A += lam_Z B^+ and lam_B += A^+ lam_Z.
+//
+// Pieces (forward operation -> kernel here):
+//   collision row (a2), coefficients  -> adj_coef_kernel: lam of the Sigma row
+//   collision row (a2), history       -> adj_hist_kernel: lam of every block
+//   Sigma row (a1)                    -> DFT, sigma_adj_products_kernel, DFT
+//   row / diagonal update (a4)        -> adj_rows_kernel, adj_uv_kernel,
+//                                        adj_diag_kernel (series reversed)
+//   h from A, mean field, shift (a3)  -> adj_hvec_kernel (dL/dA_i, dL/dU)
+#include "kbe_internal.cuh"
+#include "kbe_matgroup.cuh"
+
+namespace kbe {
+
+namespace {
+
+size_t blkof(const Mesh &m) { return (size_t)m.nb * m.nb * m.nk; }
+
+unsigned grid_for_count(size_t count) {
+  size_t b = (count + 255) / 256;
+  return (unsigned)(b < 152 * 64 ? (b ? b : 1) : 152 * 64);
+}
+
+// (G^<, dG) blocks of the FP64 history -> (G^<, G^> = G^< - dG)
+__global__ void unpack_fp64_kernel(const double2 *__restrict__ src, double2 *__restrict__ dst,
+                                   size_t nblocks, size_t blk) {
+  const size_t count = nblocks * blk;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t bq = i / blk, r = i - bq * blk;
+    const size_t o0 = bq * 2 * blk + r, o1 = o0 + blk;
+    const double2 gl = src[o0];
+    dst[o0] = gl;
+    dst[o1] = c_sub(gl, src[o1]);
+  }
+}
+
+// ------------------------------------------ collision row: coefficients ----
+// Forward (one output column j, l = 0..n, X = G(l, j) or -G(j, l)^+):
+//   I^<(j) = sum_l C1(l) X^<(l,j) + f(j,l) C2^<(l) D(l,j)
+//   I^>(j) = sum_l C1(l) X^>(l,j) + f(j,l) C2^>(l) D(l,j),  D = X^< - X^>
+// with C1 = w^(n)_l (S^> - S^<), C2^x = dt S^x, f = w^(j)_l / dt. Transposed,
+// for each l:
+//   lam_C1(l)  = sum_j lam^<_j X^<(l,j)^+ + lam^>_j X^>(l,j)^+
+//              = sum_j (lam^<_j + lam^>_j) X^<(l,j)^+ - lam^>_j D(l,j)^+
+//   lam_C2x(l) = sum_j f(j,l) lam^x_j D(l,j)^+
+//   lam_S^<(l) = -w^(n)_l lam_C1 + dt lam_C2^<,  lam_S^>(l) = w^(n)_l lam_C1 + dt lam_C2^>.
+// Stored block (l, j), j <= l: X^+_{cb} = conj(G(l,j)_bc); for j > l the
+// block (j, l) is read: X(l,j)^+_{cb} = -G(j,l)_cb.
+template <int NB, bool LOWER, bool F>
+__device__ __forceinline__ void coef_node(const double2 *__restrict__ lam, const double2 *__restrict__ g,
+                                          size_t blk, int nk, int b, double f, double2 &a1,
+                                          double2 &aL, double2 &aG) {
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    const double2 LL = lam[(size_t)c * nk], LG = lam[blk + (size_t)c * nk];
+    double2 cg, cd;
+    if (LOWER) {
+      cg = c_conj(g[(size_t)(b * NB + c) * nk]);
+      cd = c_conj(g[blk + (size_t)(b * NB + c) * nk]);
+    } else {
+      cg = c_neg(g[(size_t)(c * NB + b) * nk]);
+      cd = c_neg(g[blk + (size_t)(c * NB + b) * nk]);
+    }
+    a1 = c_fma(c_add(LL, LG), cg, a1);
+    a1 = c_fma(c_neg(LG), cd, a1);
+    if (F) {
+      aL = c_fma(c_scale(f, LL), cd, aL);
+      aG = c_fma(c_scale(f, LG), cd, aG);
+    }
+  }
+}
+
+// grid: x = tiles of the N_b^2 n_k elements (a, b, k) of one l, y = l (0..n),
+// z = split of the j range; out is lam_Sigma when gridDim.z == 1, else the
+// partial rows [z][l][x][a][b][k].
+template <int NB>
+__global__ void __launch_bounds__(256) adj_coef_kernel(const double2 *__restrict__ H,
+                                                       const double2 *__restrict__ lamI,
+                                                       double2 *__restrict__ out, int n, int nk,
+                                                       int jchunk, double dt) {
+  const int l = blockIdx.y;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= NB * NB * nk) return;
+  const int k = idx % nk;
+  const int ab = idx / nk;
+  const int a = ab / NB, b = ab - (ab / NB) * NB;
+  const int j0 = blockIdx.z * jchunk;
+  const int j1 = min(n + 1, j0 + jchunk);
+  const size_t blk = (size_t)NB * NB * nk;
+  const double2 *lbase = lamI + (size_t)a * NB * nk + k;   // lam_j(a, c) at + j 2 blk + c nk
+  const double2 *hbase = H + k;
+  double2 a1 = make_double2(0, 0), aL = make_double2(0, 0), aG = make_double2(0, 0);
+  for (int j = j0; j < min(j1, l); ++j)   // stored blocks below the diagonal, f = 0
+    coef_node<NB, true, false>(lbase + (size_t)j * 2 * blk, hbase + tri(l, j) * 2 * blk, blk, nk, b, 0.0,
+                               a1, aL, aG);
+  if (l >= j0 && l < j1) {                // the diagonal block, f = 1/2 (0 at l = 0)
+    if (l >= 1)
+      coef_node<NB, true, true>(lbase + (size_t)l * 2 * blk, hbase + tri(l, l) * 2 * blk, blk, nk, b, 0.5,
+                                a1, aL, aG);
+    else
+      coef_node<NB, true, false>(lbase, hbase, blk, nk, b, 0.0, a1, aL, aG);
+  }
+  const double fu = (l == 0) ? 0.5 : 1.0;   // j > l: l is an end node only at l = 0
+  for (int j = max(j0, l + 1); j < j1; ++j)
+    coef_node<NB, false, true>(lbase + (size_t)j * 2 * blk, hbase + tri(j, l) * 2 * blk, blk, nk, b, fu,
+                               a1, aL, aG);
+  const double w1 = trap_weight(n, l, dt);
+  double2 *o = out + ((size_t)blockIdx.z * (n + 1) + l) * 2 * blk + (size_t)ab * nk + k;
+  o[0] = c_add(c_scale(-w1, a1), c_scale(dt, aL));
+  o[blk] = c_add(c_scale(w1, a1), c_scale(dt, aG));
+}
+
+__global__ void sum_partials_kernel(const double2 *__restrict__ part, double2 *__restrict__ out,
+                                    size_t count, int nz) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x) {
+    double2 s = part[i];
+    for (int z = 1; z < nz; ++z) s = c_add(s, part[(size_t)z * count + i]);
+    out[i] = s;
+  }
+}
+
+// ----------------------------------------------- collision row: history ----
+// Every stored block (i, j'), i <= n, is used twice by the forward sweep:
+// as X(l = i, j = j') and, for j' < i, as X(l = j', j = i) = -G(i, j')^+.
+// In the (G^<, G^>) pair, I^< = C1 X^< + f C2^< (X^< - X^>) and
+// I^> = C1 X^> + f C2^> (X^< - X^>), so with c = f (C2^<^+ lam^< + C2^>^+ lam^>):
+//   use 1 (f = f(j', i)):  lam^<(i,j') += C1(i)^+ lam^<_j' + c,  lam^>(i,j') += C1(i)^+ lam^>_j' - c
+//   use 2 (f = f(i, j')):  lam^<(i,j') -= [C1(j')^+ lam^<_i + c]^+,  lam^>(i,j') -= [C1(j')^+ lam^>_i - c]^+
+// Row n of the triangle goes to lamRowN (the stage being differentiated).
+// grid: x = tiles of the N_b^2 n_k elements (p, q, k), y = row i, z = chunk
+// of j' (each block written by exactly one thread: no reduction).
+template <int NB>
+__global__ void __launch_bounds__(256) adj_hist_kernel(const double2 *__restrict__ Sig,
+                                                       const double2 *__restrict__ lamI,
+                                                       double2 *__restrict__ lamH,
+                                                       double2 *__restrict__ lamRowN, int n, int nk,
+                                                       int jchunk, double dt) {
+  const int i = blockIdx.y;
+  const int j0 = blockIdx.z * jchunk;
+  if (j0 > i) return;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= NB * NB * nk) return;
+  const int k = idx % nk;
+  const int pq = idx / nk;
+  const int p = pq / NB, q = pq - (pq / NB) * NB;
+  const int j1 = min(i + 1, j0 + jchunk);
+  const size_t blk = (size_t)NB * NB * nk;
+  const size_t cs = (size_t)NB * nk;                       // stride of the row index c
+  const double2 *si = Sig + (size_t)i * 2 * blk + (size_t)p * nk + k;    // S(i)_{cp}
+  const double2 *li = lamI + (size_t)i * 2 * blk + (size_t)p * nk + k;   // lam_i(c, p)
+  const double w1i = trap_weight(n, i, dt);
+  for (int jp = j0; jp < j1; ++jp) {
+    const double2 *sj = Sig + (size_t)jp * 2 * blk + (size_t)q * nk + k;   // S(j')_{cq}
+    const double2 *lj = lamI + (size_t)jp * 2 * blk + (size_t)q * nk + k;  // lam_j'(c, q)
+    double2 dl = make_double2(0, 0), dg = make_double2(0, 0);
+    const double fA = (jp == i && i >= 1) ? 0.5 * dt : 0.0;
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {   // use 1: C(i)^+ lam_j'
+      const double2 sl = si[c * cs], sg = si[blk + c * cs];
+      const double2 c1 = c_scale(w1i, c_sub(sg, sl));
+      const double2 LL = lj[c * cs], LG = lj[blk + c * cs];
+      dl = c_add(dl, c_mulc(LL, c1));
+      dg = c_add(dg, c_mulc(LG, c1));
+      if (fA != 0.0) {
+        const double2 t = c_scale(fA, c_add(c_mulc(LL, sl), c_mulc(LG, sg)));
+        dl = c_add(dl, t);
+        dg = c_sub(dg, t);
+      }
+    }
+    if (jp < i) {   // use 2: -[C(j')^+ lam_i]^+
+      const double fB = (jp == 0 ? 0.5 : 1.0) * dt;
+      const double w1j = trap_weight(n, jp, dt);
+#pragma unroll
+      for (int c = 0; c < NB; ++c) {
+        const double2 sl = sj[c * cs], sg = sj[blk + c * cs];
+        const double2 c1 = c_scale(w1j, c_sub(sg, sl));
+        const double2 Li = li[c * cs], Gi = li[blk + c * cs];
+        const double2 t = c_scale(fB, c_add(c_mulc(sl, Li), c_mulc(sg, Gi)));
+        dl = c_sub(dl, c_add(c_mulc(c1, Li), t));
+        dg = c_sub(dg, c_sub(c_mulc(c1, Gi), t));
+      }
+    }
+    double2 *dst = (i == n) ? lamRowN + (size_t)jp * 2 * blk : lamH + tri(i, jp) * 2 * blk;
+    double2 *e0 = dst + (size_t)pq * nk + k;
+    *e0 = c_add(*e0, dl);
+    e0[blk] = c_add(e0[blk], dg);
+  }
+}
+
+// ----------------------------------------------------------- Sigma row ----
+struct VMat {
+  double v[kMaxNb * kMaxNb];
+};
+
+// One real-space product z = fac (x_jm Q_jm - E_jm) with
+// Q_jm = sum_ab v_ja v_mb x_ab conj(y_ab), E_jm = sum_ab v_ja v_mb x_jb conj(y_ab) x_am
+// (the forward band products), transposed: adds lam_x(p, q) and lam_y(p, q)
+// for the output lam_z. With lam_Q = fac conj(x) lam_z, lam_E = -fac lam_z and
+// W_pq = sum_jm v_jp v_mq lam_Q_jm:
+//   lam_x_pq = fac conj(Q_pq) lam_z_pq + y_pq W_pq
+//            + sum_a v_pa y_aq sum_m v_mq conj(x_am) lam_E_pm
+//            + sum_j v_jp lam_E_jq sum_b v_qb conj(x_jb) y_pb
+//   lam_y_pq = x_pq conj(W_pq) + sum_j v_jp x_jq sum_m v_mq conj(lam_E_jm) x_pm
+template <int NB>
+__device__ __forceinline__ void prod_adj(const double2 *__restrict__ x, const double2 *__restrict__ y,
+                                         const double2 *__restrict__ lz, int p, int q, int nk, double fac,
+                                         const VMat &vm, double2 &lx, double2 &ly) {
+#define AT(M, r, c) M[(size_t)((r) * NB + (c)) * nk]
+  double2 Q = make_double2(0, 0), W = make_double2(0, 0);
+  double2 t3 = make_double2(0, 0), t4 = make_double2(0, 0), t6 = make_double2(0, 0);
+#pragma unroll 1
+  for (int a = 0; a < NB; ++a) {
+    const double va = vm.v[p * NB + a];   // v_pa (Q, t3)
+    const double vj = vm.v[a * NB + p];   // v_jp with j = a (W, t4, t6)
+    double2 sq = make_double2(0, 0), sw = make_double2(0, 0), s3 = make_double2(0, 0);
+    double2 s4 = make_double2(0, 0), s6 = make_double2(0, 0);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const double vb = vm.v[q * NB + b];   // v_qb
+      const double vm_ = vm.v[b * NB + q];  // v_mq with m = b
+      if (va != 0.0) {
+        if (vb != 0.0) sq = c_add(sq, c_scale(vb, c_mulc(AT(x, a, b), AT(y, a, b))));
+        if (vm_ != 0.0) s3 = c_add(s3, c_scale(vm_, c_mulc(AT(lz, p, b), AT(x, a, b))));
+      }
+      if (vj != 0.0) {
+        if (vm_ != 0.0) {
+          sw = c_add(sw, c_scale(vm_, c_mulc(AT(lz, a, b), AT(x, a, b))));
+          s6 = c_add(s6, c_scale(vm_, c_mulc(AT(x, p, b), AT(lz, a, b))));
+        }
+        if (vb != 0.0) s4 = c_add(s4, c_scale(vb, c_mulc(AT(y, p, b), AT(x, a, b))));
+      }
+    }
+    if (va != 0.0) {
+      Q = c_add(Q, c_scale(va, sq));
+      t3 = c_fma(c_scale(va, AT(y, a, q)), s3, t3);
+    }
+    if (vj != 0.0) {
+      W = c_add(W, c_scale(vj, sw));
+      t4 = c_fma(c_scale(vj, AT(lz, a, q)), s4, t4);
+      t6 = c_fma(c_scale(vj, AT(x, a, q)), s6, t6);
+    }
+  }
+  W = c_scale(fac, W);
+  lx = c_add(lx, c_mulc(c_scale(fac, AT(lz, p, q)), Q));
+  lx = c_fma(AT(y, p, q), W, lx);
+  lx = c_add(lx, c_scale(-fac, c_add(t3, t4)));
+  ly = c_add(ly, c_mulc(AT(x, p, q), W));
+  ly = c_add(ly, c_scale(-fac, t6));
+#undef AT
+}
+
+// one thread per (l, p, R): row p of lam_G^<(R) and lam_G^>(R) of pair l.
+// Sigma^< is the product with (x, y) = (G^<, G^>), Sigma^> with (G^>, G^<).
+template <int NB>
+__global__ void __launch_bounds__(128) sigma_adj_products_kernel(const double2 *__restrict__ GR,
+                                                                 const double2 *__restrict__ LR,
+                                                                 double2 *__restrict__ GLR, int n,
+                                                                 int nk, double fac, VMat vm) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long total = (long)(n + 1) * NB * nk;
+  if (idx >= total) return;
+  const int R = (int)(idx % nk);
+  const long t = idx / nk;
+  const int p = (int)(t % NB);
+  const int l = (int)(t / NB);
+  const size_t blk = (size_t)NB * NB * nk;
+  const double2 *gl = GR + (size_t)l * 2 * blk + R, *gg = gl + blk;
+  const double2 *ll = LR + (size_t)l * 2 * blk + R, *lg = ll + blk;
+  double2 *ol = GLR + (size_t)l * 2 * blk + (size_t)p * NB * nk + R, *og = ol + blk;
+#pragma unroll 1
+  for (int q = 0; q < NB; ++q) {
+    double2 aL = make_double2(0, 0), aG = make_double2(0, 0);
+    prod_adj<NB>(gl, gg, ll, p, q, nk, fac, vm, aL, aG);
+    prod_adj<NB>(gg, gl, lg, p, q, nk, fac, vm, aG, aL);
+    ol[(size_t)q * nk] = aL;
+    og[(size_t)q * nk] = aG;
+  }
+}
+
+// ------------------------------------------------------------- update ----
+// Forward rows j < n: G^x(n,j) = U G^x(n-1,j) + V Ibar^x(j),
+// Ibar = (1 - theta) Ip + theta Ic. Transposed per element:
+//   lam_Gprev += U^+ lam,  lam_Ip += (1 - theta) V^+ lam,  lam_Ic += theta V^+ lam.
+template <int NB>
+__global__ void adj_rows_kernel(int n, int nk, double theta, const double2 *__restrict__ U,
+                                const double2 *__restrict__ V, const double2 *__restrict__ lam,
+                                double2 *__restrict__ lamGprev, double2 *__restrict__ lamIp,
+                                double2 *__restrict__ lamIc) {
+  const size_t blk = (size_t)NB * NB * nk;
+  const size_t total = (size_t)n * 2 * blk;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int k = (int)(idx % nk);
+  size_t t = idx / nk;
+  const int q = (int)(t % NB);
+  t /= NB;
+  const int p = (int)(t % NB);
+  t /= NB;   // t = j * 2 + x
+  const size_t base = t * blk;
+  double2 gu = make_double2(0, 0), gv = make_double2(0, 0);
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    const double2 lo = lam[base + (size_t)(c * NB + q) * nk + k];
+    const size_t ocp = (size_t)(c * NB + p) * nk + k;
+    gu = c_add(gu, c_mulc(lo, U[ocp]));
+    gv = c_add(gv, c_mulc(lo, V[ocp]));
+  }
+  const size_t o = base + (size_t)(p * NB + q) * nk + k;
+  lamGprev[o] = c_add(lamGprev[o], gu);
+  lamIp[o] = c_add(lamIp[o], c_scale(1.0 - theta, gv));
+  if (theta != 0.0) lamIc[o] = c_add(lamIc[o], c_scale(theta, gv));
+}
+
+// lam_U = sum_{j<n, x} lam^x_j G^x(n-1,j)^+ and lam_V = sum lam^x_j Ibar^x_j^+,
+// per k, partial over a chunk of j (grid y); partial rows [z][2][p][q][k]
+template <int NB>
+__global__ void adj_uv_kernel(int n, int nk, double theta, const double2 *__restrict__ lam,
+                              const double2 *__restrict__ Gprev, const double2 *__restrict__ Ip,
+                              const double2 *__restrict__ Ic, double2 *__restrict__ part, int jchunk) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= NB * NB * nk) return;
+  const int k = idx % nk;
+  const int pq = idx / nk;
+  const int p = pq / NB, q = pq - (pq / NB) * NB;
+  const int z = blockIdx.y;
+  const int j0 = z * jchunk, j1 = min(n, j0 + jchunk);
+  const size_t blk = (size_t)NB * NB * nk;
+  double2 lu = make_double2(0, 0), lv = make_double2(0, 0);
+  for (int j = j0; j < j1; ++j)
+    for (int x = 0; x < 2; ++x) {
+      const size_t base = (size_t)(j * 2 + x) * blk + k;
+#pragma unroll
+      for (int c = 0; c < NB; ++c) {
+        const double2 lo = lam[base + (size_t)(p * NB + c) * nk];
+        const size_t oq = base + (size_t)(q * NB + c) * nk;
+        double2 ib = c_scale(1.0 - theta, Ip[oq]);
+        if (theta != 0.0) ib = c_add(ib, c_scale(theta, Ic[oq]));
+        lu = c_add(lu, c_mulc(lo, Gprev[oq]));
+        lv = c_add(lv, c_mulc(lo, ib));
+      }
+    }
+  part[(size_t)z * 2 * blk + (size_t)pq * nk + k] = lu;
+  part[((size_t)z * 2 + 1) * blk + (size_t)pq * nk + k] = lv;
+}
+
+// Time diagonal and propagators, per k (one matrix group per k-point):
+//   G^<(n,n) = U Gd U^+ - i X,  G^>(n,n) = G^<(n,n) - i,
+//   X = tau sum_{m=0}^{18} Q_m / (m+1),  Q_m = (-i tau / m)(h Q_{m-1} - Q_{m-1} h),  Q_0 = Sbar,
+//   U = sum_{m=0}^{14} P_m,  V = -i tau sum_m P_m / (m+1),  P_m = P_{m-1} (-i tau h) / m,
+// with tau = dt (no doubling; a step that needed one sets kDevAdjUnsupported).
+// Transposed, with ld = lam^<(n,n) + lam^>(n,n):
+//   lam_U += ld U Gd^+ + ld^+ U Gd,  lam_Gd += U^+ ld U,  lam_X = i ld,
+//   series reversed from the top: lam_Q_{m-1} = tau/m lam_X + conj(a_m) (h lam_Q_m - lam_Q_m h),
+//   lam_h += conj(a_m) (lam_Q_m Q_{m-1}^+ - Q_{m-1}^+ lam_Q_m),  a_m = -i tau / m;
+//   lam_P_{m-1} = lam_U + (i tau / m) lam_V + lam_P_m (-i tau h)^+ / m,
+//   lam_(-i tau h) += P_{m-1}^+ lam_P_m / m, lam_h += i tau lam_(-i tau h);
+//   lam_Sbar = lam_Q_0 -> lam_I^<(diag) += (1-theta or theta) (lam_Sbar + lam_Sbar^+).
+// The forward chains Q_0..Q_17 and P_0..P_13 are kept in `chain` (global,
+// [m][a][b][k]); each thread reads back only what it wrote itself.
+template <int NB>
+__global__ void __launch_bounds__(256) adj_diag_kernel(
+    int n, int nk, double dt, double theta, const double2 *__restrict__ h, const double2 *__restrict__ U,
+    const double2 *__restrict__ Gprev, const double2 *__restrict__ Ip, const double2 *__restrict__ Ic,
+    const double2 *__restrict__ lam, const double2 *__restrict__ part, int nz, double2 *lamGprev,
+    double2 *lamIp, double2 *lamIc, double2 *__restrict__ lamh, double2 *__restrict__ chain, int *status,
+    int kpc) {
+  using G = MatGroup<NB>;
+  const int span = kpc * G::E;
+  double2 *Hs = kbe_dsm, *Us = kbe_dsm + span, *LD = kbe_dsm + 2 * span, *A1 = kbe_dsm + 3 * span,
+          *A2 = kbe_dsm + 4 * span, *Qm = kbe_dsm + 5 * span;
+  double *red = (double *)(kbe_dsm + 6 * span);
+  const G g;
+  const int k = blockIdx.x * kpc + g.kk;
+  const bool active = k < nk;
+  const int nvalid = min(kpc, nk - (int)blockIdx.x * kpc);
+  const int o = g.kk * G::E + g.e;
+  const size_t blk = (size_t)G::E * nk;
+  const size_t oab = (size_t)g.e * nk + k, oba = (size_t)(g.b * NB + g.a) * nk + k;
+  const double2 zero = make_double2(0, 0);
+  double2 hv = zero, uv = zero, ld = zero, gd = zero, sv = zero, lu = zero, lv = zero;
+  if (active) {
+    hv = h[oab];
+    uv = U[oab];
+    const double2 *lr = lam + (size_t)n * 2 * blk;
+    ld = c_add(lr[oab], lr[blk + oab]);
+    gd = Gprev[(size_t)(n - 1) * 2 * blk + oab];
+    const double2 *ipd = Ip + (size_t)(n - 1) * 2 * blk;
+    sv = c_scale(1.0 - theta, c_add(ipd[oab], c_conj(ipd[oba])));
+    if (theta != 0.0) {
+      const double2 *icd = Ic + (size_t)n * 2 * blk;
+      sv = c_add(sv, c_scale(theta, c_add(icd[oab], c_conj(icd[oba]))));
+    }
+    for (int z = 0; z < nz; ++z) {
+      lu = c_add(lu, part[(size_t)z * 2 * blk + oab]);
+      lv = c_add(lv, part[((size_t)z * 2 + 1) * blk + oab]);
+    }
+  }
+  Hs[o] = hv;
+  __syncthreads();
+  const int s = doublings<NB>(g, Hs, kpc, nvalid, dt, red);
+  if (s != 0) {   // uniform over the CTA
+    if (threadIdx.x == 0) atomicOr(status, kDevAdjUnsupported);
+    return;
+  }
+  const double tau = dt;
+  Us[o] = uv;
+  LD[o] = ld;
+  A1[o] = gd;
+  __syncthreads();
+  A2[o] = g.mm_adj(Us, A1);   // U Gd^+
+  Qm[o] = g.mm(Us, A1);       // U Gd
+  __syncthreads();
+  lu = c_add(lu, c_add(g.mm(LD, A2), mm_hadj<NB>(g, LD, Qm)));
+  __syncthreads();
+  A2[o] = g.mm(LD, Us);       // ld U
+  __syncthreads();
+  const double2 gpd = mm_hadj<NB>(g, Us, A2);   // U^+ ld U
+  if (active) {
+    double2 *t = lamGprev + (size_t)(n - 1) * 2 * blk + oab;
+    *t = c_add(*t, gpd);
+  }
+  // X series: forward chain Q_0..Q_17
+  Qm[o] = sv;
+  if (active) chain[oab] = sv;
+  __syncthreads();
+  for (int m = 1; m <= 17; ++m) {
+    const double2 c = c_sub(g.mm(Hs, Qm), g.mm(Qm, Hs));
+    const double2 qv = make_double2(tau * c.y / m, -tau * c.x / m);
+    __syncthreads();
+    Qm[o] = qv;
+    if (active) chain[(size_t)m * blk + oab] = qv;
+    __syncthreads();
+  }
+  const double2 lX = c_i(ld);
+  double2 cur = c_scale(tau / 19.0, lX), lh = zero;
+  for (int m = 18; m >= 1; --m) {
+    A1[o] = cur;
+    Qm[o] = active ? chain[(size_t)(m - 1) * blk + oab] : zero;
+    __syncthreads();
+    const double2 ca = make_double2(0.0, tau / m);   // conj(-i tau / m)
+    lh = c_fma(ca, c_sub(g.mm_adj(A1, Qm), mm_hadj<NB>(g, Qm, A1)), lh);
+    const double2 t2 = c_sub(g.mm(Hs, A1), g.mm(A1, Hs));
+    __syncthreads();
+    cur = c_add(c_scale(tau / m, lX), c_mul(ca, t2));
+  }
+  A1[o] = cur;
+  __syncthreads();
+  const double2 lsh = c_add(cur, c_conj(A1[g.kk * G::E + g.b * NB + g.a]));   // lam_S + lam_S^+
+  if (active) {
+    double2 *t = lamIp + (size_t)(n - 1) * 2 * blk + oab;
+    *t = c_add(*t, c_scale(1.0 - theta, lsh));
+    if (theta != 0.0) {
+      double2 *u = lamIc + (size_t)n * 2 * blk + oab;
+      *u = c_add(*u, c_scale(theta, lsh));
+    }
+  }
+  __syncthreads();
+  // propagator series: forward chain P_0..P_13
+  const double2 one = make_double2(g.a == g.b ? 1.0 : 0.0, 0.0);
+  Qm[o] = one;
+  if (active) chain[oab] = one;
+  __syncthreads();
+  for (int m = 1; m <= 13; ++m) {
+    const double2 c = g.mm(Qm, Hs);
+    const double2 pv = make_double2(tau * c.y / m, -tau * c.x / m);
+    __syncthreads();
+    Qm[o] = pv;
+    if (active) chain[(size_t)m * blk + oab] = pv;
+    __syncthreads();
+  }
+  double2 lY = zero;
+  cur = c_add(lu, c_mul(make_double2(0.0, tau / 15.0), lv));
+  for (int m = 14; m >= 1; --m) {
+    A1[o] = cur;
+    Qm[o] = active ? chain[(size_t)(m - 1) * blk + oab] : zero;
+    __syncthreads();
+    lY = c_add(lY, c_scale(1.0 / m, mm_hadj<NB>(g, Qm, A1)));
+    const double2 t = g.mm(A1, Hs);   // lam_P h
+    __syncthreads();
+    const double2 im = make_double2(0.0, tau / m);
+    cur = c_add(lu, c_add(c_mul(im, lv), c_mul(im, t)));
+  }
+  lh = c_add(lh, c_mul(make_double2(0.0, tau), lY));
+  if (active) lamh[oab] = lh;
+}
+
+// -------------------------------------------------- h from A and the MF ----
+struct HvecAdj {
+  double A, U;
+  int hf, paper_shift;
+  double v[kMaxNb * kMaxNb];
+  const double2 *rho_a, *rho_b;   // mid density = ca rho_a + cb rho_b
+  double ca, cb;
+  double2 *lam_rho_a, *lam_rho_b; // receive ca lam_mid, cb lam_mid (NULL: skip)
+  double2 *lam_cur;               // G^<(n,n) block receiving i cur_scale lam_mid (NULL: skip)
+  double cur_scale;
+  double *gA, *gU;
+};
+
+// h_k = h0(k - A d) + U hf(mid) (- U on the last band, paper shift) (+ dipole).
+//   dL/dA += Re sum_k tr(lam_h^+ dh0/dA),  dh0/dA = sum_r t(R_r) e^{i theta_r} (-i d.R_r);
+//   Lam = sum_k lam_h; dL/dU += Re tr(Lam^+ hf(mid)) - Re Lam_{N_b N_b} (shift);
+//   lam_mid_jm = -U v_jm Lam_jm,  lam_mid_aa += U sum_j v_ja Lam_jj.
+// One CTA: a warp per element (a, b) reduces over k; thread 0 finishes.
+template <int NB>
+__global__ void adj_hvec_kernel(Mesh m, HopTable hop, HvecAdj p, const double2 *__restrict__ lamh) {
+  __shared__ double2 Lam[NB * NB];
+  __shared__ double2 lmid[NB * NB];
+  __shared__ double red[32];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  double ga = 0.0;
+  for (int e = warp; e < NB * NB; e += nw) {
+    double2 acc = make_double2(0, 0);
+    for (int k = lane; k < m.nk; k += 32) {
+      const double2 lh = lamh[(size_t)e * m.nk + k];
+      acc = c_add(acc, lh);
+      const int k0 = k / m.L1, k1 = k - (k / m.L1) * m.L1;
+      double2 dh = make_double2(0, 0);
+      for (int r = 0; r < hop.nhop; ++r) {
+        const int R0 = hop.R[2 * r], R1 = hop.R[2 * r + 1];
+        const double dR = hop.d0 * R0 + hop.d1 * R1;
+        if (dR == 0.0) continue;
+        const int m0 = ((k0 * R0) % m.L0 + m.L0) % m.L0, m1 = ((k1 * R1) % m.L1 + m.L1) % m.L1;
+        const double th = 2.0 * M_PI * ((double)m0 / m.L0 + (double)m1 / m.L1) - p.A * dR;
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        const double2 tv = c_mul(hop.T[(size_t)r * NB * NB + e], make_double2(cs, sn));
+        dh = c_add(dh, c_scale(dR, make_double2(tv.y, -tv.x)));   // (-i dR) t e^{i theta}
+      }
+      ga += lh.x * dh.x + lh.y * dh.y;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+    }
+    if (lane == 0) Lam[e] = acc;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, off);
+  if (lane == 0) red[warp] = ga;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double gsum = 0.0;
+    for (int w = 0; w < nw; ++w) gsum += red[w];
+    *p.gA += gsum;
+    double gu = 0.0;
+    for (int e = 0; e < NB * NB; ++e) lmid[e] = make_double2(0, 0);
+    if (p.hf) {
+      for (int j = 0; j < NB; ++j)
+        for (int mm = 0; mm < NB; ++mm) {
+          const int e = j * NB + mm;
+          const double2 mid = c_add(c_scale(p.ca, p.rho_a[e]), c_scale(p.cb, p.rho_b[e]));
+          double2 x = c_scale(-p.v[e], mid);
+          if (j == mm)
+            for (int a = 0; a < NB; ++a) {
+              const int ea = a * NB + a;
+              x = c_add(x, c_scale(p.v[j * NB + a], c_add(c_scale(p.ca, p.rho_a[ea]), c_scale(p.cb, p.rho_b[ea]))));
+            }
+          gu += Lam[e].x * x.x + Lam[e].y * x.y;
+          lmid[e] = c_add(lmid[e], c_scale(-p.U * p.v[e], Lam[e]));
+        }
+      for (int j = 0; j < NB; ++j)
+        for (int a = 0; a < NB; ++a)
+          lmid[a * NB + a] = c_add(lmid[a * NB + a], c_scale(p.U * p.v[j * NB + a], Lam[j * NB + j]));
+    }
+    if (p.paper_shift) gu -= Lam[NB * NB - 1].x;
+    *p.gU += gu;
+    for (int e = 0; e < NB * NB; ++e) {
+      if (p.lam_rho_a) p.lam_rho_a[e] = c_add(p.lam_rho_a[e], c_scale(p.ca, lmid[e]));
+      if (p.lam_rho_b) p.lam_rho_b[e] = c_add(p.lam_rho_b[e], c_scale(p.cb, lmid[e]));
+    }
+  }
+  __syncthreads();
+  if (p.lam_cur) {   // the current density is (1/n_k) sum_k (-i) G^<(k; n, n)
+    for (int i = threadIdx.x; i < NB * NB * m.nk; i += blockDim.x) {
+      const int e = i / m.nk;
+      p.lam_cur[i] = c_add(p.lam_cur[i], c_i(c_scale(p.cur_scale, lmid[e])));
+    }
+  }
+}
+
+// lamDiag[e][k] += i scale lamRho[e]  (transpose of rho = (1/n_k) sum_k -i G^<)
+__global__ void adj_density_kernel(int e_count, int nk, const double2 *__restrict__ lamRho, double scale,
+                                   double2 *__restrict__ lamDiag) {
+  const int total = e_count * nk;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x)
+    lamDiag[i] = c_add(lamDiag[i], c_i(c_scale(scale, lamRho[i / nk])));
+}
+
+// acc += scale * Re sum conj(a) b, in a fixed order (fixed grid, then one CTA)
+constexpr int kRedotBlocks = 304;
+__global__ void redot_kernel(const double2 *__restrict__ a, const double2 *__restrict__ b, size_t count,
+                             double *__restrict__ part) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const double2 x = a[i], y = b[i];
+    s += x.x * y.x + x.y * y.y;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (lane == 0) red[warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void redot_final_kernel(const double *__restrict__ part, int nparts, double scale,
+                                   double *__restrict__ acc) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < nparts; ++i) t += part[i];
+    *acc += scale * t;
+  }
+}
+
+// shapes ------------------------------------------------------------------
+struct CoefShape {
+  dim3 grid;
+  int threads, jchunk, nz;
+};
+
+CoefShape coef_shape(const Mesh &m, int n) {
+  CoefShape sh;
+  const long elems = (long)m.nb * m.nb * m.nk;
+  sh.threads = elems >= 256 ? 256 : (int)((elems + 31) / 32) * 32;
+  const long ty = (elems + sh.threads - 1) / sh.threads;
+  const long base = (long)(n + 1) * ty;
+  long nz = (152L * 8 + base - 1) / base;
+  if (nz > n + 1) nz = n + 1;
+  if (nz > 2 + 1024 / (n + 1)) nz = 2 + 1024 / (n + 1);
+  if (nz < 1) nz = 1;
+  sh.jchunk = (int)((n + 1 + nz - 1) / nz);
+  sh.nz = (int)((n + 1 + sh.jchunk - 1) / sh.jchunk);
+  sh.grid = dim3((unsigned)ty, n + 1, (unsigned)sh.nz);
+  return sh;
+}
+
+constexpr int kHistChunk = 32;
+constexpr int kUvMaxSplit = 64;
+
+int uv_splits(const Mesh &m, int n) {
+  const long elems = (long)m.nb * m.nb * m.nk;
+  const long tiles = (elems + 255) / 256;
+  long nz = (152L * 8 + tiles - 1) / tiles;
+  if (nz > n) nz = n;
+  if (nz > kUvMaxSplit) nz = kUvMaxSplit;
+  return nz < 1 ? 1 : (int)nz;
+}
+
+template <int NB>
+cudaError_t adj_sweep_nb(const Mesh &m, int n, double dt, const double2 *H, const double2 *Sig,
+                         const double2 *lamI, double2 *lamSig, double2 *lamH, double2 *lamRowN,
+                         double2 *coef_work, cudaStream_t st) {
+  const CoefShape sh = coef_shape(m, n);
+  double2 *out = sh.nz > 1 ? coef_work : lamSig;
+  adj_coef_kernel<NB><<<sh.grid, sh.threads, 0, st>>>(H, lamI, out, n, m.nk, sh.jchunk, dt);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int nch = n / kHistChunk + 1;   // chunks covering j' = 0..n
+  const long elems = (long)NB * NB * m.nk;
+  const dim3 hgrid((unsigned)((elems + 255) / 256), n + 1, (unsigned)nch);
+  adj_hist_kernel<NB><<<hgrid, 256, 0, st>>>(Sig, lamI, lamH, lamRowN, n, m.nk, kHistChunk, dt);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || sh.nz == 1) return e;
+  const size_t count = (size_t)(n + 1) * 2 * blkof(m);
+  sum_partials_kernel<<<grid_for_count(count), 256, 0, st>>>(coef_work, lamSig, count, sh.nz);
+  return cudaGetLastError();
+}
+
+template <int NB>
+cudaError_t adj_update_nb(const Mesh &m, int n, double dt, double theta, const double2 *h, const double2 *U,
+                          const double2 *V, const double2 *Gprev, const double2 *Ip, const double2 *Ic,
+                          const double2 *lam, double2 *lamGprev, double2 *lamIp, double2 *lamIc, double2 *lamh,
+                          double2 *work, int *status, cudaStream_t st) {
+  const size_t blk = (size_t)NB * NB * m.nk;
+  const size_t total = (size_t)n * 2 * blk;
+  const double2 *ic = theta != 0.0 ? Ic : Ip;
+  double2 *lic = theta != 0.0 ? lamIc : lamIp;
+  adj_rows_kernel<NB><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n, m.nk, theta, U, V, lam, lamGprev,
+                                                                        lamIp, lic);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int nz = uv_splits(m, n);
+  const int jchunk = (n + nz - 1) / nz;
+  const int nzr = (n + jchunk - 1) / jchunk;
+  double2 *part = work;
+  double2 *chain = work + (size_t)kUvMaxSplit * 2 * blk;
+  const long elems = (long)NB * NB * m.nk;
+  adj_uv_kernel<NB><<<dim3((unsigned)((elems + 255) / 256), (unsigned)nzr), 256, 0, st>>>(
+      n, m.nk, theta, lam, Gprev, Ip, ic, part, jchunk);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem = matgroup_smem<NB>(m.nk, 6);
+  adj_diag_kernel<NB><<<matgroup_blocks<NB>(m.nk), matgroup_threads<NB>(m.nk), smem, st>>>(
+      n, m.nk, dt, theta, h, U, Gprev, Ip, ic, lam, part, nzr, lamGprev, lamIp, lic, lamh, chain, status,
+      matgroup_kpc<NB>(m.nk));
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------- launchers ----
+
+cudaError_t launch_unpack_fp64(const double2 *packed, double2 *out, size_t nblocks, size_t blk,
+                               cudaStream_t st) {
+  if (nblocks == 0 || blk == 0) return cudaSuccess;
+  unpack_fp64_kernel<<<grid_for_count(nblocks * blk), 256, 0, st>>>(packed, out, nblocks, blk);
+  return cudaGetLastError();
+}
+
+size_t adj_coef_workspace_bytes(const Mesh &m, int nmax) {
+  const size_t blk = (size_t)m.nb * m.nb * m.nk;
+  size_t part = 0;
+  for (int r = 0; r <= nmax; ++r) {
+    const CoefShape sh = coef_shape(m, r);
+    if (sh.nz > 1) {
+      const size_t b = (size_t)sh.nz * (r + 1) * 2 * blk * sizeof(double2);
+      if (b > part) part = b;
+    }
+  }
+  return part ? part : 256;
+}
+
+cudaError_t launch_adj_sweep(const Mesh &m, int n, double dt, const double2 *H, const double2 *Sig,
+                             const double2 *lamI, double2 *lamSig, double2 *lamH, double2 *lamRowN,
+                             double2 *coef_work, cudaStream_t st) {
+  KBE_NB_SWITCH(m.nb, return adj_sweep_nb<NB>(m, n, dt, H, Sig, lamI, lamSig, lamH, lamRowN, coef_work, st));
+  return cudaErrorInvalidValue;
+}
+
+size_t adj_sigma_workspace_bytes(const Mesh &m, int n) {
+  const size_t blk = (size_t)m.nb * m.nb * m.nk;
+  return 3 * (size_t)(n + 1) * 2 * blk * sizeof(double2);
+}
+
+cudaError_t adj_sigma_row(const Mesh &m, const double *v_host, int n, double U, const double2 *Grow,
+                          const double2 *lamSig, double2 *lamRow, double2 *work, cudaStream_t st) {
+  const size_t blk = (size_t)m.nb * m.nb * m.nk;
+  const size_t row = (size_t)(n + 1) * 2 * blk;
+  const long narr = (long)(n + 1) * 2 * m.nb * m.nb;
+  double2 *GR = work, *LR = work + row, *GLR = work + 2 * row;
+  // forward: G(R) = DFT_+(G(k)) / n_k; Sigma(k) = DFT_-(products(G(R)))
+  cudaError_t e = launch_dft_rows(Grow, GR, narr, m.L0, m.L1, +1, 1.0 / m.nk, st);
+  if (e != cudaSuccess) return e;
+  // transpose of DFT_- is DFT_+, of DFT_+ / n_k is DFT_- / n_k
+  e = launch_dft_rows(lamSig, LR, narr, m.L0, m.L1, +1, 1.0, st);
+  if (e != cudaSuccess) return e;
+  VMat vm;
+  for (int i = 0; i < kMaxNb * kMaxNb; ++i) vm.v[i] = 0.0;
+  for (int i = 0; i < m.nb * m.nb; ++i) vm.v[i] = v_host[i];
+  const double fac = -U * U;
+  const long total = (long)(n + 1) * m.nb * m.nk;
+  const unsigned blocks = (unsigned)((total + 127) / 128);
+  KBE_NB_SWITCH(m.nb, (sigma_adj_products_kernel<NB><<<blocks, 128, 0, st>>>(GR, LR, GLR, n, m.nk, fac, vm)));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_dft_rows(GLR, lamRow, narr, m.L0, m.L1, -1, 1.0 / m.nk, st, true);
+}
+
+size_t adj_update_workspace_bytes(const Mesh &m) {
+  const size_t blk = (size_t)m.nb * m.nb * m.nk;
+  return ((size_t)kUvMaxSplit * 2 + 18) * blk * sizeof(double2);
+}
+
+cudaError_t launch_adj_update(const Mesh &m, int n, double dt, double theta, const double2 *h,
+                              const double2 *U, const double2 *V, const double2 *Gprev, const double2 *Ip,
+                              const double2 *Ic, const double2 *lam, double2 *lamGprev, double2 *lamIp,
+                              double2 *lamIc, double2 *lamh, double2 *work, int *status, cudaStream_t st) {
+  KBE_NB_SWITCH(m.nb, return adj_update_nb<NB>(m, n, dt, theta, h, U, V, Gprev, Ip, Ic, lam, lamGprev, lamIp,
+                                                lamIc, lamh, work, status, st));
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_adj_hvec(const Mesh &m, const HopTable &hop, const AdjHvecArgs &a, const double *v_host,
+                            const double2 *lamh, cudaStream_t st) {
+  HvecAdj p{};
+  p.A = a.A;
+  p.U = a.U;
+  p.hf = a.hf;
+  p.paper_shift = a.paper_shift;
+  for (int i = 0; i < m.nb * m.nb; ++i) p.v[i] = v_host[i];
+  p.rho_a = a.rho_a;
+  p.rho_b = a.rho_b;
+  p.ca = a.ca;
+  p.cb = a.cb;
+  p.lam_rho_a = a.lam_rho_a;
+  p.lam_rho_b = a.lam_rho_b;
+  p.lam_cur = a.lam_cur;
+  p.cur_scale = a.cur_scale;
+  p.gA = a.gA;
+  p.gU = a.gU;
+  KBE_NB_SWITCH(m.nb, (adj_hvec_kernel<NB><<<1, 256, 0, st>>>(m, hop, p, lamh)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_density(const Mesh &m, const double2 *lamRho, double scale, double2 *lamDiag,
+                               cudaStream_t st) {
+  const int total = m.nb * m.nb * m.nk;
+  adj_density_kernel<<<(total + 255) / 256, 256, 0, st>>>(m.nb * m.nb, m.nk, lamRho, scale, lamDiag);
+  return cudaGetLastError();
+}
+
+size_t redot_workspace_bytes() { return kRedotBlocks * sizeof(double); }
+
+cudaError_t launch_redot(const double2 *a, const double2 *b, size_t count, double scale, double *acc,
+                         double *part, cudaStream_t st) {
+  redot_kernel<<<kRedotBlocks, 256, 0, st>>>(a, b, count, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  redot_final_kernel<<<1, 32, 0, st>>>(part, kRedotBlocks, scale, acc);
+  return cudaGetLastError();
+}
+
+}  // namespace kbe

@@ -64,6 +64,10 @@ struct kbe_handle {
   kbe_status sticky = KBE_OK;
   std::string err;
 
+  // reverse mode: one device arena, allocated by the first kbe_backward
+  void *adj = nullptr;
+  size_t adj_bytes = 0;
+
   // profiling
   bool prof = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
@@ -122,7 +126,7 @@ cudaError_t dalloc(kbe_handle *h, T **p, size_t count) {
 void free_all(kbe_handle *h) {
   void *ptrs[] = {h->H, h->Wrow[0], h->Wrow[1], h->coef, h->Ip, h->Ic, h->Sig, h->work, h->U, h->V,
                   h->hk, h->rho, h->obs, h->nkb, h->status, h->d_hopR, h->d_hopT, h->d_U,
-                  h->d_dipM};
+                  h->d_dipM, h->adj};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (auto &pr : h->ev) {
@@ -198,7 +202,8 @@ kbe_status evaluate_row(kbe_handle *h, int n) {
   return KBE_OK;
 }
 
-kbe_status build_props(kbe_handle *h, int n, const double2 *ra, const double2 *rb, double ca, double cb) {
+kbe_status build_props(kbe_handle *h, int n, const double2 *ra, const double2 *rb, double ca, double cb,
+                       double2 *hk = nullptr, double2 *Uk = nullptr, double2 *Vk = nullptr) {
   kbe::PropParams p{};
   p.A = A_at(h, n - 1);
   p.rho_a = ra;
@@ -211,8 +216,8 @@ kbe_status build_props(kbe_handle *h, int n, const double2 *ra, const double2 *r
   for (int i = 0; i < h->nb2; ++i) p.v[i] = h->v[(size_t)i];
   p.dipM = h->dipE.empty() ? nullptr : h->d_dipM;
   p.dipE = (n - 1 < (int)h->dipE.size()) ? h->dipE[(size_t)(n - 1)] : 0.0;
-  cudaError_t e = kbe::launch_build_props(h->mesh, hop_table(h), p, h->cfg.dt, nullptr, h->hk, h->U,
-                                          h->V, h->stream);
+  cudaError_t e = kbe::launch_build_props(h->mesh, hop_table(h), p, h->cfg.dt, nullptr, hk ? hk : h->hk,
+                                          Uk ? Uk : h->U, Vk ? Vk : h->V, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "build_props");
   if (h->prof) h->stats.launches += 1;
   return KBE_OK;
@@ -274,6 +279,178 @@ kbe_status one_step(kbe_handle *h) {
   h->n = n;
   return KBE_OK;
 }
+
+// ---- reverse mode ----------------------------------------------------------
+// Pointers into the reverse-mode arena. Row slots hold (nt_max+1) blocks of
+// (x, a, b, k) pairs; per-stage arrays are indexed by the stage c (0 =
+// predictor, 1..n_corr = correctors, n_corr + 1 = the final evaluation).
+struct AdjPtrs {
+  double2 *lamH;          // adjoint of the history triangle, (G^<, G^>) per block
+  double2 *rowp, *Ip, *sigp;   // recomputed row n-1 (G^<, G^>), I_{n-1}, Sigma_{n-1}
+  double2 *rows;          // stage rows c = 0..n_corr
+  double2 *sigs;          // Sigma rows of stages 1..n_corr and the final one
+  double2 *Is;            // collision rows of stages 1..n_corr
+  double2 *lst;           // adjoints of stage rows 0..n_corr-1
+  double2 *hUV;           // (h, U, V) per k of every stage
+  double2 *cur;           // current density of stages 1..n_corr
+  double2 *lamIa, *lamIb, *lamIc, *lamSig;
+  double2 *save;          // the stored row n while its stages are republished
+  double2 *sigw, *coefw, *updw, *lamh, *lamRho;
+  double *gA, *gU, *red;
+  size_t row;             // complex numbers per row slot
+};
+
+size_t adj_carve(const kbe_config *cfg, const Mesh &m, char *base, AdjPtrs *p) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char * {
+    char *r = base ? base + off : nullptr;
+    off += (bytes + 255) / 256 * 256;
+    return r;
+  };
+  const size_t T = (size_t)cfg->nt_max, nb2 = (size_t)cfg->nb * cfg->nb, blk = nb2 * m.nk;
+  const size_t nc = (size_t)cfg->n_corr, c16 = sizeof(double2);
+  p->row = (T + 1) * 2 * blk;
+  const size_t R = p->row * c16;
+  p->lamH = (double2 *)take((tri((int)T, (int)T) + 1) * 2 * blk * c16);
+  p->rowp = (double2 *)take(R);
+  p->Ip = (double2 *)take(R);
+  p->sigp = (double2 *)take(R);
+  p->rows = (double2 *)take((nc + 1) * R);
+  p->sigs = (double2 *)take((nc + 1) * R);
+  p->Is = (double2 *)take(nc * R);
+  p->lst = (double2 *)take(nc * R);
+  p->hUV = (double2 *)take((nc + 1) * 3 * blk * c16);
+  p->cur = (double2 *)take((nc + 1) * nb2 * c16);
+  p->lamIa = (double2 *)take(R);
+  p->lamIb = (double2 *)take(R);
+  p->lamIc = (double2 *)take(R);
+  p->lamSig = (double2 *)take(R);
+  p->save = (double2 *)take(R);
+  p->sigw = (double2 *)take(kbe::adj_sigma_workspace_bytes(m, (int)T));
+  p->coefw = (double2 *)take(kbe::adj_coef_workspace_bytes(m, (int)T));
+  p->updw = (double2 *)take(kbe::adj_update_workspace_bytes(m));
+  p->lamh = (double2 *)take(blk * c16);
+  p->lamRho = (double2 *)take((T + 1) * nb2 * c16);
+  p->gA = (double *)take(T * sizeof(double));
+  p->gU = (double *)take(sizeof(double));
+  p->red = (double *)take(kbe::redot_workspace_bytes());
+  return off;
+}
+
+#define KBE_TRY(expr, where)                          \
+  do {                                                \
+    cudaError_t e_ = (expr);                          \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
+  } while (0)
+
+// Step n in reverse: recompute the step from the history (rows < n) and
+// I_{n-1}, then transpose its operations, last first. lamIcur is the adjoint
+// of I_n (complete), lamIprev accumulates that of I_{n-1}.
+kbe_status backward_step(kbe_handle *h, const AdjPtrs &P, int n, double2 *lamIcur, double2 *lamIprev) {
+  const Mesh &m = h->mesh;
+  const size_t blk = h->blk, nb2 = (size_t)h->nb2;
+  const double dt = h->cfg.dt, Uc = h->Useq[0];
+  const int nc = h->cfg.n_corr;
+  cudaStream_t st = h->stream;
+  const double *v = h->v.data();
+  double2 *Hd = (double2 *)h->H;
+  double2 *histN = Hd + tri(n, 0) * 2 * blk;
+  const size_t rowc = (size_t)(n + 1) * 2 * blk;
+  auto row = [&](int c) { return P.rows + (size_t)c * P.row; };
+  auto sig = [&](int c) { return P.sigs + (size_t)(c - 1) * P.row; };
+  auto Ist = [&](int c) { return P.Is + (size_t)(c - 1) * P.row; };
+  auto lst = [&](int c) { return P.lst + (size_t)c * P.row; };
+  auto hk = [&](int c) { return P.hUV + (size_t)c * 3 * blk; };
+  auto Uk = [&](int c) { return P.hUV + ((size_t)c * 3 + 1) * blk; };
+  auto Vk = [&](int c) { return P.hUV + ((size_t)c * 3 + 2) * blk; };
+  auto cur = [&](int c) { return P.cur + (size_t)c * nb2; };
+  auto rho = [&](int i) { return h->rho + (size_t)i * nb2; };
+  auto lrho = [&](int i) { return P.lamRho + (size_t)i * nb2; };
+  const int n2 = n >= 2 ? n - 2 : 0;
+  const double ca0 = n >= 2 ? 1.5 : 1.0, cb0 = n >= 2 ? -0.5 : 0.0;
+
+  // ---- recompute step n (the forward's order and kernels) ----
+  KBE_TRY(cudaMemcpyAsync(P.save, histN, rowc * sizeof(double2), cudaMemcpyDeviceToDevice, st), "backward save");
+  KBE_TRY(kbe::launch_unpack_fp64(Hd + tri(n - 1, 0) * 2 * blk, P.rowp, (size_t)n, blk, st), "backward unpack");
+  KBE_TRY(kbe::sigma_row(m, v, n - 1, Uc, nullptr, P.rowp, P.sigp, h->work, st), "backward sigma");
+  KBE_TRY(kbe::launch_sweep(m, n - 1, dt, KBE_PREC_FP64, h->H, P.sigp, P.Ip, h->coef, st), "backward sweep");
+  kbe_status s = build_props(h, n, rho(n - 1), rho(n2), ca0, cb0, hk(0), Uk(0), Vk(0));
+  if (s != KBE_OK) return s;
+  KBE_TRY(kbe::launch_update_row(m, n, dt, 0.0, hk(0), Uk(0), Vk(0), P.rowp, P.Ip, nullptr, row(0), st),
+          "backward update");
+  KBE_TRY(kbe::launch_pack(KBE_PREC_FP64, row(0), histN, (size_t)(n + 1), blk, st), "backward pack");
+  for (int c = 1; c <= nc; ++c) {
+    KBE_TRY(kbe::launch_local_density(m, row(c - 1) + (size_t)n * 2 * blk, cur(c), st), "backward density");
+    if ((s = build_props(h, n, rho(n - 1), cur(c), 0.5, 0.5, hk(c), Uk(c), Vk(c))) != KBE_OK) return s;
+    KBE_TRY(kbe::sigma_row(m, v, n, Uc, nullptr, row(c - 1), sig(c), h->work, st), "backward sigma");
+    KBE_TRY(kbe::launch_sweep(m, n, dt, KBE_PREC_FP64, h->H, sig(c), Ist(c), h->coef, st), "backward sweep");
+    KBE_TRY(kbe::launch_update_row(m, n, dt, 0.5, hk(c), Uk(c), Vk(c), P.rowp, P.Ip, Ist(c), row(c), st),
+            "backward update");
+    KBE_TRY(kbe::launch_pack(KBE_PREC_FP64, row(c), histN, (size_t)(n + 1), blk, st), "backward pack");
+  }
+  KBE_TRY(kbe::sigma_row(m, v, n, Uc, nullptr, row(nc), sig(nc + 1), h->work, st), "backward sigma");
+
+  // ---- transpose ----
+  double2 *lamN = P.lamH + tri(n, 0) * 2 * blk;       // row n (the final row's adjoint)
+  double2 *lamP = P.lamH + tri(n - 1, 0) * 2 * blk;   // row n-1
+  const kbe::HopTable hop = hop_table(h);
+  // density rho_n of the final row, used by later steps
+  KBE_TRY(kbe::launch_adj_density(m, lrho(n), 1.0 / m.nk, lamN + (size_t)n * 2 * blk, st), "backward density");
+  // final evaluation: I_n = sweep(Sigma(row), history with row n)
+  KBE_TRY(kbe::launch_adj_sweep(m, n, dt, Hd, sig(nc + 1), lamIcur, P.lamSig, P.lamH, lamN, P.coefw, st),
+          "backward adj sweep");
+  KBE_TRY(kbe::adj_sigma_row(m, v, n, Uc, row(nc), P.lamSig, lamN, P.sigw, st), "backward adj sigma");
+  if (Uc != 0.0)   // Sigma is -U^2 times U-free products: dL/dU += (2/U) Re <lam_Sigma, Sigma>
+    KBE_TRY(kbe::launch_redot(P.lamSig, sig(nc + 1), rowc, 2.0 / Uc, P.gU, P.red, st), "backward redot");
+  kbe::AdjHvecArgs a{};
+  a.U = Uc;
+  a.hf = h->cfg.hf;
+  a.paper_shift = h->cfg.paper_shift;
+  a.A = A_at(h, n - 1);
+  a.gA = P.gA + (n - 1);
+  a.gU = P.gU;
+  for (int c = nc; c >= 1; --c) {
+    double2 *lamS = (c == nc) ? lamN : lst(c);
+    double2 *lamPS = lst(c - 1);
+    KBE_TRY(cudaMemsetAsync(lamPS, 0, rowc * sizeof(double2), st), "backward memset");
+    KBE_TRY(cudaMemsetAsync(P.lamIc, 0, rowc * sizeof(double2), st), "backward memset");
+    KBE_TRY(kbe::launch_adj_update(m, n, dt, 0.5, hk(c), Uk(c), Vk(c), P.rowp, P.Ip, Ist(c), lamS, lamP,
+                                   lamIprev, P.lamIc, P.lamh, P.updw, h->status, st),
+            "backward adj update");
+    a.rho_a = rho(n - 1);
+    a.rho_b = cur(c);
+    a.ca = a.cb = 0.5;
+    a.lam_rho_a = lrho(n - 1);
+    a.lam_rho_b = nullptr;
+    a.lam_cur = lamPS + (size_t)n * 2 * blk;
+    a.cur_scale = 0.5 / m.nk;
+    KBE_TRY(kbe::launch_adj_hvec(m, hop, a, v, P.lamh, st), "backward adj h");
+    // the stage's collision row saw the previous stage's row as row n
+    KBE_TRY(kbe::launch_pack(KBE_PREC_FP64, row(c - 1), histN, (size_t)(n + 1), blk, st), "backward pack");
+    KBE_TRY(kbe::launch_adj_sweep(m, n, dt, Hd, sig(c), P.lamIc, P.lamSig, P.lamH, lamPS, P.coefw, st),
+            "backward adj sweep");
+    KBE_TRY(kbe::adj_sigma_row(m, v, n, Uc, row(c - 1), P.lamSig, lamPS, P.sigw, st), "backward adj sigma");
+    if (Uc != 0.0)
+      KBE_TRY(kbe::launch_redot(P.lamSig, sig(c), rowc, 2.0 / Uc, P.gU, P.red, st), "backward redot");
+  }
+  double2 *lam0 = nc == 0 ? lamN : lst(0);
+  KBE_TRY(kbe::launch_adj_update(m, n, dt, 0.0, hk(0), Uk(0), Vk(0), P.rowp, P.Ip, nullptr, lam0, lamP,
+                                 lamIprev, nullptr, P.lamh, P.updw, h->status, st),
+          "backward adj update");
+  a.rho_a = rho(n - 1);
+  a.rho_b = rho(n2);
+  a.ca = ca0;
+  a.cb = cb0;
+  a.lam_rho_a = lrho(n - 1);
+  a.lam_rho_b = lrho(n2);
+  a.lam_cur = nullptr;
+  KBE_TRY(kbe::launch_adj_hvec(m, hop, a, v, P.lamh, st), "backward adj h");
+  KBE_TRY(cudaMemcpyAsync(histN, P.save, rowc * sizeof(double2), cudaMemcpyDeviceToDevice, st),
+          "backward restore");
+  return KBE_OK;
+}
+
+#undef KBE_TRY
 
 kbe_status check_device_status(kbe_handle *h) {
   int st = 0;
@@ -424,6 +601,13 @@ kbe_status kbe_set_interaction(kbe_handle *h, int len, const double *U, const do
   if (v) {
     for (int i = 0; i < h->nb2; ++i)
       if (!std::isfinite(v[i])) return fail(h, KBE_ERR_NONFINITE, "set_interaction: non-finite v");
+    const int nb = h->cfg.nb;
+    for (int a = 0; a < nb; ++a)
+      for (int b = a + 1; b < nb; ++b) {
+        const double x = v[a * nb + b], y = v[b * nb + a];
+        if (std::fabs(x - y) > 1e-12 * (std::fabs(x) + std::fabs(y)))
+          return fail(h, KBE_ERR_ARG, "set_interaction: v must be symmetric (v_ab = v_ba)");
+      }
     h->v.assign(v, v + h->nb2);
   }
   h->Useq.assign(U, U + (len == 1 ? 1 : h->cfg.nt_max + 1));
@@ -735,6 +919,94 @@ size_t kbe_memory_bytes(const kbe_config *cfg) {
       (long)cfg->L[0] * cfg->L[1] > kbe::kMaxNk || !kbe::precision_supported(cfg->precision))
     return 0;
   return handle_bytes(cfg);
+}
+
+// ---- reverse mode ----------------------------------------------------------
+
+size_t kbe_backward_memory_bytes(const kbe_config *cfg) {
+  if (!cfg || !nb_ok(cfg->nb) || cfg->L[0] < 1 || cfg->L[1] < 1 || cfg->nt_max < 1 ||
+      (long)cfg->L[0] * cfg->L[1] > kbe::kMaxNk || cfg->n_corr < 0 || cfg->n_corr > 64)
+    return 0;
+  AdjPtrs p{};
+  const Mesh m{cfg->nb, cfg->L[0], cfg->L[1], cfg->L[0] * cfg->L[1]};
+  return adj_carve(cfg, m, nullptr, &p);
+}
+
+kbe_status kbe_backward(kbe_handle *h, const double *dL_dn, double *dL_dA, double *dL_dU) {
+  if (!h) return KBE_ERR_ARG;
+  if (!dL_dn || !dL_dA || !dL_dU) return fail(h, KBE_ERR_ARG, "backward: null argument");
+  if (h->sticky != KBE_OK) return fail(h, h->sticky, "backward: handle has a sticky error; reset it");
+  if (h->n < 1) return fail(h, KBE_ERR_STATE, "backward: no step to differentiate (call kbe_step first)");
+  if (h->cfg.precision != KBE_PREC_FP64)
+    return fail(h, KBE_ERR_UNSUPPORTED, "backward: needs the FP64 history (KBE_PREC_FP64)");
+  if (h->Useq.size() != 1)
+    return fail(h, KBE_ERR_UNSUPPORTED, "backward: needs a constant U (set_interaction with len 1)");
+  const int nk = h->mesh.nk, nb = h->cfg.nb;
+  for (int i = 0; i < nk * nb; ++i)
+    if (!std::isfinite(dL_dn[i])) return fail(h, KBE_ERR_NONFINITE, "backward: non-finite dL/dn");
+  kbe_status s = check_device_status(h);
+  if (s != KBE_OK) return s;
+  AdjPtrs P{};
+  if (!h->adj) {
+    const size_t bytes = adj_carve(&h->cfg, h->mesh, nullptr, &P);
+    cudaError_t e = cudaMalloc(&h->adj, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      h->adj = nullptr;
+      return fail(h, e == cudaErrorMemoryAllocation ? KBE_ERR_OOM : KBE_ERR_CUDA,
+                  std::string("backward: device allocation failed (") + cudaGetErrorString(e) + ")");
+    }
+    h->adj_bytes = bytes;
+  }
+  adj_carve(&h->cfg, h->mesh, (char *)h->adj, &P);
+  const int N = h->n;
+  const size_t blk = h->blk, nb2 = (size_t)h->nb2;
+  cudaStream_t st = h->stream;
+  cudaError_t e = cudaMemsetAsync(P.lamH, 0, (tri(N, N) + 1) * 2 * blk * sizeof(double2), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.lamRho, 0, (size_t)(N + 1) * nb2 * sizeof(double2), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.gA, 0, (size_t)h->cfg.nt_max * sizeof(double), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.gU, 0, sizeof(double), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.lamIa, 0, (size_t)(N + 1) * 2 * blk * sizeof(double2), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.lamIb, 0, (size_t)(N + 1) * 2 * blk * sizeof(double2), st);
+  // n_kb = Im G^<_bb(k; N, N): dL = Re conj(i g) dG^<_bb for g = dL/dn_kb
+  std::vector<double2> seed(blk, make_double2(0.0, 0.0));
+  for (int k = 0; k < nk; ++k)
+    for (int b = 0; b < nb; ++b) seed[(size_t)(b * nb + b) * nk + k] = make_double2(0.0, dL_dn[(size_t)k * nb + b]);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(P.lamH + tri(N, N) * 2 * blk, seed.data(), blk * sizeof(double2), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "backward setup");
+  double2 *lamIcur = P.lamIa, *lamIprev = P.lamIb;
+  for (int n = N; n >= 1; --n) {
+    s = backward_step(h, P, n, lamIcur, lamIprev);
+    if (s != KBE_OK) return s;
+    std::swap(lamIcur, lamIprev);
+    e = cudaMemsetAsync(lamIprev, 0, (size_t)n * 2 * blk * sizeof(double2), st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "backward memset");
+  }
+  std::vector<double> gA((size_t)N);
+  double gU = 0.0;
+  int stat = 0;
+  e = cudaMemcpyAsync(gA.data(), P.gA, sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&gU, P.gU, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&stat, h->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "backward result copy");
+  if (stat & kbe::kDevAdjUnsupported) {   // the forward state is intact: clear the flag, keep the handle usable
+    const int keep = stat & ~kbe::kDevAdjUnsupported;
+    e = cudaMemcpyAsync(h->status, &keep, sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "backward status");
+    return fail(h, KBE_ERR_UNSUPPORTED,
+                "backward: a step needed the scaled-and-squared propagators (dt ||h|| > 1/4), which have no adjoint");
+  }
+  s = check_device_status(h);
+  if (s != KBE_OK) return s;
+  for (int i = 0; i < h->cfg.nt_max; ++i) dL_dA[i] = i < N ? gA[(size_t)i] : 0.0;
+  *dL_dU = gU;
+  for (int i = 0; i < N; ++i)
+    if (!std::isfinite(gA[(size_t)i])) return fail(h, KBE_ERR_NONFINITE, "backward: non-finite gradient");
+  if (!std::isfinite(gU)) return fail(h, KBE_ERR_NONFINITE, "backward: non-finite gradient");
+  return KBE_OK;
 }
 
 const char *kbe_last_error(const kbe_handle *h) {

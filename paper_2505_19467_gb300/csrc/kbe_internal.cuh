@@ -60,12 +60,14 @@ __device__ __forceinline__ double2 c_fma(double2 a, double2 b, double2 acc) {
 __device__ __forceinline__ double2 c_i(double2 a) { return make_double2(-a.y, a.x); }
 
 // ---- status word written by kernels (sticky, read by the host) -----------
-enum : int { kDevOk = 0, kDevNonFinite = 1, kDevEigNoConv = 2 };
+enum : int { kDevOk = 0, kDevNonFinite = 1, kDevEigNoConv = 2, kDevAdjUnsupported = 4 };
 
 // ---- kernels launch wrappers (return cudaGetLastError()) ------------------
 // a1 self-energy row
+// out[arr] = scale * DFT_sign(in[arr]) for narr arrays of n_k points (added
+// to out when accumulate)
 cudaError_t launch_dft_rows(const double2 *in, double2 *out, long narr, int L0, int L1, int sign,
-                            double scale, cudaStream_t st);
+                            double scale, cudaStream_t st, bool accumulate = false);
 cudaError_t launch_sigma_products(const Mesh &m, const double *v, int n, double Un,
                                   const double *Ul_dev, const double2 *GR, double2 *SR,
                                   cudaStream_t st);
@@ -131,6 +133,50 @@ struct ObsParams {
 cudaError_t launch_observables(const Mesh &m, const HopTable &hop, const ObsParams &p,
                                const double2 *Gdiag, const double2 *Idiag, const double2 *rho_n,
                                double *obs_out, double *nkb_out, int *status, cudaStream_t st);
+
+// reverse mode (FP64 history; see kbe_adjoint.cu). Rows are [l][x][a][b][k]
+// with x = (G^<, G^>) or their adjoints.
+// (G^<, dG) history blocks -> (G^<, G^>)
+cudaError_t launch_unpack_fp64(const double2 *packed, double2 *out, size_t nblocks, size_t blk,
+                               cudaStream_t st);
+// transpose of the collision row at n: lamSig = lambda of the Sigma row;
+// lamH (blocks of rows < n) and lamRowN (row n) += lambda of the history
+// blocks the sweep read (H holds row n as that sweep saw it)
+size_t adj_coef_workspace_bytes(const Mesh &m, int nmax);
+cudaError_t launch_adj_sweep(const Mesh &m, int n, double dt, const double2 *H, const double2 *Sig,
+                             const double2 *lamI, double2 *lamSig, double2 *lamH, double2 *lamRowN,
+                             double2 *coef_work, cudaStream_t st);
+// transpose of the Sigma row: lamRow += lambda of the G row (constant U)
+size_t adj_sigma_workspace_bytes(const Mesh &m, int n);
+cudaError_t adj_sigma_row(const Mesh &m, const double *v_host, int n, double U, const double2 *Grow,
+                          const double2 *lamSig, double2 *lamRow, double2 *work, cudaStream_t st);
+// transpose of the row and diagonal update: lamGprev, lamIp, lamIc +=;
+// lamh (per k) = lambda of the step's h through U, V and the diagonal
+size_t adj_update_workspace_bytes(const Mesh &m);
+cudaError_t launch_adj_update(const Mesh &m, int n, double dt, double theta, const double2 *h,
+                              const double2 *U, const double2 *V, const double2 *Gprev, const double2 *Ip,
+                              const double2 *Ic, const double2 *lam, double2 *lamGprev, double2 *lamIp,
+                              double2 *lamIc, double2 *lamh, double2 *work, int *status, cudaStream_t st);
+// transpose of h = h0(k - A d) + U hf(mid) + shift: dL/dA, dL/dU and the
+// lambda of the mid density (to rho_a, rho_b or a G^<(n,n) block)
+struct AdjHvecArgs {
+  double A, U;
+  int hf, paper_shift;
+  const double2 *rho_a, *rho_b;
+  double ca, cb;
+  double2 *lam_rho_a, *lam_rho_b, *lam_cur;
+  double cur_scale;
+  double *gA, *gU;
+};
+cudaError_t launch_adj_hvec(const Mesh &m, const HopTable &hop, const AdjHvecArgs &a, const double *v_host,
+                            const double2 *lamh, cudaStream_t st);
+// lamDiag[e][k] += i scale lamRho[e]
+cudaError_t launch_adj_density(const Mesh &m, const double2 *lamRho, double scale, double2 *lamDiag,
+                               cudaStream_t st);
+// acc += scale Re sum conj(a) b (deterministic order; part: redot_workspace_bytes)
+size_t redot_workspace_bytes();
+cudaError_t launch_redot(const double2 *a, const double2 *b, size_t count, double scale, double *acc,
+                         double *part, cudaStream_t st);
 
 // message returned by kbe_last_error(NULL) on this thread
 void set_last_error(const std::string &msg);

@@ -23,7 +23,8 @@ namespace kbe {
 namespace {
 
 // Separable 2-D DFT of length-n_k arrays (mesh L0 x L1, k = k0 * L1 + k1):
-//   out[R] = scale * sum_k exp(sign * i * 2 pi (k0 R0 / L0 + k1 R1 / L1)) in[k].
+//   out[R] (+)= scale * sum_k exp(sign * i * 2 pi (k0 R0 / L0 + k1 R1 / L1)) in[k]
+// (added to out when accumulating).
 // One array at a time per CTA (grid-stride over arrays), in shared memory.
 // An axis whose length is a power of two is transformed in place by a
 // radix-2 FFT (bit reversal, then log2 L butterfly stages; O(L log L));
@@ -90,7 +91,7 @@ __device__ void dft_axis(double2 *x, double2 *tmp, int L, int stride, int count,
 }
 
 __global__ void dft_rows_kernel(const double2 *__restrict__ in, double2 *__restrict__ out,
-                                long narr, int L0, int L1, int sign, double scale) {
+                                long narr, int L0, int L1, int sign, double scale, int accumulate) {
   extern __shared__ double2 sm[];
   const int nk = L0 * L1;
   double2 *x = sm;
@@ -121,7 +122,10 @@ __global__ void dft_rows_kernel(const double2 *__restrict__ in, double2 *__restr
       else dft_axis(x, t, L0, L1, L1, 1, tw0);
     }
     double2 *dst = out + arr * nk;
-    for (int e = threadIdx.x; e < nk; e += blockDim.x) dst[e] = c_scale(scale, x[e]);
+    if (accumulate)
+      for (int e = threadIdx.x; e < nk; e += blockDim.x) dst[e] = c_add(dst[e], c_scale(scale, x[e]));
+    else
+      for (int e = threadIdx.x; e < nk; e += blockDim.x) dst[e] = c_scale(scale, x[e]);
   }
 }
 
@@ -194,7 +198,7 @@ cudaError_t products_nb(const Mesh &m, const VMat &vm, int n, double Un, const d
 }  // namespace
 
 cudaError_t launch_dft_rows(const double2 *in, double2 *out, long narr, int L0, int L1, int sign,
-                            double scale, cudaStream_t st) {
+                            double scale, cudaStream_t st, bool accumulate) {
   if (narr <= 0) return cudaSuccess;
   const int nk = L0 * L1;
   const size_t smem = sizeof(double2) * (2 * (size_t)nk + L0 + L1);
@@ -207,7 +211,8 @@ cudaError_t launch_dft_rows(const double2 *in, double2 *out, long narr, int L0, 
   }
   int threads = nk >= 256 ? 256 : ((nk + 31) / 32) * 32;
   long blocks = narr < 152L * 8 ? narr : 152L * 8;
-  dft_rows_kernel<<<(unsigned)blocks, threads, smem, st>>>(in, out, narr, L0, L1, sign, scale);
+  dft_rows_kernel<<<(unsigned)blocks, threads, smem, st>>>(in, out, narr, L0, L1, sign, scale,
+                                                            accumulate ? 1 : 0);
   return cudaGetLastError();
 }
 

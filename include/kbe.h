@@ -95,6 +95,12 @@ typedef struct kbe_profile_stats {
   double sweep_flops_executed; /* flops the dG form executes (~20 n^2 N_b^3 n_k)     */
   double sweep_bytes;       /* algorithmic bytes (stored history read once + I row) */
   int launches;             /* all kernels launched while enabled                 */
+  /* kbe_backward while enabled (CUDA events around each phase): the steps'
+   * recomputation, the collision-row transposes, the Sigma-row transposes,
+   * and the update / h transposes, in ms; and the flops of the collision-row
+   * transposes (algorithmic count, 8 per complex multiply-add). */
+  double backward_ms[4];
+  double backward_sweep_flops;
 } kbe_profile_stats;
 
 /* ---------------------------------------------------------------------- */

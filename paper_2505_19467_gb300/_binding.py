@@ -60,7 +60,8 @@ class kbe_profile_stats(ctypes.Structure):
     _fields_ = [("sweep_launches", ctypes.c_int), ("sweep_ms", ctypes.c_double),
                 ("sweep_flops", ctypes.c_double), ("sweep_flops_executed", ctypes.c_double),
                 ("sweep_bytes", ctypes.c_double),
-                ("launches", ctypes.c_int)]
+                ("launches", ctypes.c_int), ("backward_ms", ctypes.c_double * 4),
+                ("backward_sweep_flops", ctypes.c_double)]
 
 
 _lib = None
@@ -315,7 +316,8 @@ class KBE:
         _check(load().kbe_profile_read(self._h, ctypes.byref(s)), self._h)
         return dict(sweep_launches=s.sweep_launches, sweep_ms=s.sweep_ms, sweep_flops=s.sweep_flops,
                     sweep_flops_executed=s.sweep_flops_executed, sweep_bytes=s.sweep_bytes,
-                    launches=s.launches)
+                    launches=s.launches, backward_ms=list(s.backward_ms),
+                    backward_sweep_flops=s.backward_sweep_flops)
 
 
 # ---- stateless ops on torch device tensors (GPU layout, see include/kbe.h) ----

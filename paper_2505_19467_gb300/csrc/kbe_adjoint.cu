@@ -63,26 +63,34 @@ __global__ void unpack_fp64_kernel(const double2 *__restrict__ src, double2 *__r
 //   lam_S^<(l) = -w^(n)_l lam_C1 + dt lam_C2^<,  lam_S^>(l) = w^(n)_l lam_C1 + dt lam_C2^>.
 // Stored block (l, j), j <= l: X^+_{cb} = conj(G(l,j)_bc); for j > l the
 // block (j, l) is read: X(l,j)^+_{cb} = -G(j,l)_cb.
+// One node j for the output (l; a, b) in fused form: with lam^P = lam^< + lam^>,
+//   LOWER (block (l, j)):  a1 += lam^P conj(G^<)_bc - lam^> conj(dG)_bc,  aL/aG += lam^x conj(dG)_bc
+//   upper (block (j, l)):  a1 += -lam^P G^<_cb + lam^> dG_cb,            aL/aG += -lam^x dG_cb
+// (f is applied by the caller: it is uniform over each run of nodes).
 template <int NB, bool LOWER, bool F>
 __device__ __forceinline__ void coef_node(const double2 *__restrict__ lam, const double2 *__restrict__ g,
-                                          size_t blk, int nk, int b, double f, double2 &a1,
-                                          double2 &aL, double2 &aG) {
+                                          size_t blk, int nk, int b, double2 &a1, double2 &aL,
+                                          double2 &aG) {
 #pragma unroll
   for (int c = 0; c < NB; ++c) {
     const double2 LL = lam[(size_t)c * nk], LG = lam[blk + (size_t)c * nk];
-    double2 cg, cd;
+    const double2 LP = c_add(LL, LG);
     if (LOWER) {
-      cg = c_conj(g[(size_t)(b * NB + c) * nk]);
-      cd = c_conj(g[blk + (size_t)(b * NB + c) * nk]);
+      const double2 gl = g[(size_t)(b * NB + c) * nk], dg = g[blk + (size_t)(b * NB + c) * nk];
+      a1 = c_fmac(LP, gl, a1);
+      a1 = c_fnmac(LG, dg, a1);
+      if (F) {
+        aL = c_fmac(LL, dg, aL);
+        aG = c_fmac(LG, dg, aG);
+      }
     } else {
-      cg = c_neg(g[(size_t)(c * NB + b) * nk]);
-      cd = c_neg(g[blk + (size_t)(c * NB + b) * nk]);
-    }
-    a1 = c_fma(c_add(LL, LG), cg, a1);
-    a1 = c_fma(c_neg(LG), cd, a1);
-    if (F) {
-      aL = c_fma(c_scale(f, LL), cd, aL);
-      aG = c_fma(c_scale(f, LG), cd, aG);
+      const double2 gl = g[(size_t)(c * NB + b) * nk], dg = g[blk + (size_t)(c * NB + b) * nk];
+      a1 = c_fnma(LP, gl, a1);
+      a1 = c_fma(LG, dg, a1);
+      if (F) {
+        aL = c_fnma(LL, dg, aL);
+        aG = c_fnma(LG, dg, aG);
+      }
     }
   }
 }
@@ -91,10 +99,10 @@ __device__ __forceinline__ void coef_node(const double2 *__restrict__ lam, const
 // z = split of the j range; out is lam_Sigma when gridDim.z == 1, else the
 // partial rows [z][l][x][a][b][k].
 template <int NB>
-__global__ void __launch_bounds__(256) adj_coef_kernel(const double2 *__restrict__ H,
-                                                       const double2 *__restrict__ lamI,
-                                                       double2 *__restrict__ out, int n, int nk,
-                                                       int jchunk, double dt) {
+__global__ void __launch_bounds__(256, 2) adj_coef_kernel(const double2 *__restrict__ H,
+                                                          const double2 *__restrict__ lamI,
+                                                          double2 *__restrict__ out, int n, int nk,
+                                                          int jchunk, double dt) {
   const int l = blockIdx.y;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= NB * NB * nk) return;
@@ -106,25 +114,35 @@ __global__ void __launch_bounds__(256) adj_coef_kernel(const double2 *__restrict
   const size_t blk = (size_t)NB * NB * nk;
   const double2 *lbase = lamI + (size_t)a * NB * nk + k;   // lam_j(a, c) at + j 2 blk + c nk
   const double2 *hbase = H + k;
-  double2 a1 = make_double2(0, 0), aL = make_double2(0, 0), aG = make_double2(0, 0);
+  const double2 z = make_double2(0, 0);
+  double2 a1 = z, aL = z, aG = z, dL = z, dG = z;
   for (int j = j0; j < min(j1, l); ++j)   // stored blocks below the diagonal, f = 0
-    coef_node<NB, true, false>(lbase + (size_t)j * 2 * blk, hbase + tri(l, j) * 2 * blk, blk, nk, b, 0.0,
-                               a1, aL, aG);
+    coef_node<NB, true, false>(lbase + (size_t)j * 2 * blk, hbase + tri(l, j) * 2 * blk, blk, nk, b, a1, aL, aG);
   if (l >= j0 && l < j1) {                // the diagonal block, f = 1/2 (0 at l = 0)
     if (l >= 1)
-      coef_node<NB, true, true>(lbase + (size_t)l * 2 * blk, hbase + tri(l, l) * 2 * blk, blk, nk, b, 0.5,
-                                a1, aL, aG);
+      coef_node<NB, true, true>(lbase + (size_t)l * 2 * blk, hbase + tri(l, l) * 2 * blk, blk, nk, b, a1, dL, dG);
     else
-      coef_node<NB, true, false>(lbase, hbase, blk, nk, b, 0.0, a1, aL, aG);
+      coef_node<NB, true, false>(lbase, hbase, blk, nk, b, a1, dL, dG);
   }
-  const double fu = (l == 0) ? 0.5 : 1.0;   // j > l: l is an end node only at l = 0
-  for (int j = max(j0, l + 1); j < j1; ++j)
-    coef_node<NB, false, true>(lbase + (size_t)j * 2 * blk, hbase + tri(j, l) * 2 * blk, blk, nk, b, fu,
-                               a1, aL, aG);
+  for (int j = max(j0, l + 1); j < j1; ++j)   // j > l: f = 1, or 1/2 when l = 0 is the end node
+    coef_node<NB, false, true>(lbase + (size_t)j * 2 * blk, hbase + tri(j, l) * 2 * blk, blk, nk, b, a1, aL, aG);
+  const double fu = (l == 0) ? 0.5 : 1.0;
+  aL = c_add(c_scale(fu, aL), c_scale(0.5, dL));
+  aG = c_add(c_scale(fu, aG), c_scale(0.5, dG));
   const double w1 = trap_weight(n, l, dt);
   double2 *o = out + ((size_t)blockIdx.z * (n + 1) + l) * 2 * blk + (size_t)ab * nk + k;
   o[0] = c_add(c_scale(-w1, a1), c_scale(dt, aL));
   o[blk] = c_add(c_scale(w1, a1), c_scale(dt, aG));
+}
+
+// C1(l) = w^(n)_l (S^>(l) - S^<(l)), l = 0..n, one block per l
+__global__ void adj_c1_kernel(const double2 *__restrict__ Sig, double2 *__restrict__ C1, int n, size_t blk,
+                              double dt) {
+  const size_t total = (size_t)(n + 1) * blk;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t l = i / blk, r = i - l * blk;
+    C1[i] = c_scale(trap_weight(n, (int)l, dt), c_sub(Sig[(l * 2 + 1) * blk + r], Sig[l * 2 * blk + r]));
+  }
 }
 
 __global__ void sum_partials_kernel(const double2 *__restrict__ part, double2 *__restrict__ out,
@@ -145,14 +163,16 @@ __global__ void sum_partials_kernel(const double2 *__restrict__ part, double2 *_
 //   use 1 (f = f(j', i)):  lam^<(i,j') += C1(i)^+ lam^<_j' + c,  lam^>(i,j') += C1(i)^+ lam^>_j' - c
 //   use 2 (f = f(i, j')):  lam^<(i,j') -= [C1(j')^+ lam^<_i + c]^+,  lam^>(i,j') -= [C1(j')^+ lam^>_i - c]^+
 // Row n of the triangle goes to lamRowN (the stage being differentiated).
+// C1 is precomputed per launch (adj_c1_kernel); each thread keeps its
+// column p of C1(i) and lam_i in registers.
 // grid: x = tiles of the N_b^2 n_k elements (p, q, k), y = row i, z = chunk
 // of j' (each block written by exactly one thread: no reduction).
 template <int NB>
-__global__ void __launch_bounds__(256) adj_hist_kernel(const double2 *__restrict__ Sig,
-                                                       const double2 *__restrict__ lamI,
-                                                       double2 *__restrict__ lamH,
-                                                       double2 *__restrict__ lamRowN, int n, int nk,
-                                                       int jchunk, double dt) {
+__global__ void __launch_bounds__(256, 2) adj_hist_kernel(const double2 *__restrict__ Sig,
+                                                          const double2 *__restrict__ C1,
+                                                          const double2 *__restrict__ lamI,
+                                                          double2 *lamH, double2 *lamRowN, int n, int nk,
+                                                          int jchunk, double dt) {
   const int i = blockIdx.y;
   const int j0 = blockIdx.z * jchunk;
   if (j0 > i) return;
@@ -163,40 +183,54 @@ __global__ void __launch_bounds__(256) adj_hist_kernel(const double2 *__restrict
   const int p = pq / NB, q = pq - (pq / NB) * NB;
   const int j1 = min(i + 1, j0 + jchunk);
   const size_t blk = (size_t)NB * NB * nk;
-  const size_t cs = (size_t)NB * nk;                       // stride of the row index c
-  const double2 *si = Sig + (size_t)i * 2 * blk + (size_t)p * nk + k;    // S(i)_{cp}
-  const double2 *li = lamI + (size_t)i * 2 * blk + (size_t)p * nk + k;   // lam_i(c, p)
-  const double w1i = trap_weight(n, i, dt);
-  for (int jp = j0; jp < j1; ++jp) {
-    const double2 *sj = Sig + (size_t)jp * 2 * blk + (size_t)q * nk + k;   // S(j')_{cq}
-    const double2 *lj = lamI + (size_t)jp * 2 * blk + (size_t)q * nk + k;  // lam_j'(c, q)
-    double2 dl = make_double2(0, 0), dg = make_double2(0, 0);
-    const double fA = (jp == i && i >= 1) ? 0.5 * dt : 0.0;
+  const size_t cs = (size_t)NB * nk;   // stride of the row index c
+  // this thread's column p of C1(i) and of lam_i, elements (c, p)
+  double2 c1i[NB], Li[NB], Gi[NB];
+  {
+    const double2 *ci = C1 + (size_t)i * blk + (size_t)p * nk + k;
+    const double2 *li = lamI + (size_t)i * 2 * blk + (size_t)p * nk + k;
 #pragma unroll
-    for (int c = 0; c < NB; ++c) {   // use 1: C(i)^+ lam_j'
-      const double2 sl = si[c * cs], sg = si[blk + c * cs];
-      const double2 c1 = c_scale(w1i, c_sub(sg, sl));
-      const double2 LL = lj[c * cs], LG = lj[blk + c * cs];
-      dl = c_add(dl, c_mulc(LL, c1));
-      dg = c_add(dg, c_mulc(LG, c1));
-      if (fA != 0.0) {
-        const double2 t = c_scale(fA, c_add(c_mulc(LL, sl), c_mulc(LG, sg)));
-        dl = c_add(dl, t);
-        dg = c_sub(dg, t);
-      }
+    for (int c = 0; c < NB; ++c) {
+      c1i[c] = ci[c * cs];
+      Li[c] = li[c * cs];
+      Gi[c] = li[blk + c * cs];
     }
-    if (jp < i) {   // use 2: -[C(j')^+ lam_i]^+
-      const double fB = (jp == 0 ? 0.5 : 1.0) * dt;
-      const double w1j = trap_weight(n, jp, dt);
+  }
+  const double2 z = make_double2(0, 0);
+  for (int jp = j0; jp < j1; ++jp) {
+    const double2 *lj = lamI + (size_t)jp * 2 * blk + (size_t)q * nk + k;   // lam_j'(c, q)
+    double2 dl = z, dg = z;
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {   // use 1: C1(i)^+ lam_j'
+      dl = c_fmac(lj[c * cs], c1i[c], dl);
+      dg = c_fmac(lj[blk + c * cs], c1i[c], dg);
+    }
+    if (jp < i) {   // use 2: -[C1(j')^+ lam_i + c]^+ with c = f dt (S^<^+ lam^<_i + S^>^+ lam^>_i)
+      const double2 *cj = C1 + (size_t)jp * blk + (size_t)q * nk + k;     // C1(j')_{cq}
+      const double2 *sj = Sig + (size_t)jp * 2 * blk + (size_t)q * nk + k; // S(j')_{cq}
+      double2 t = z;
 #pragma unroll
       for (int c = 0; c < NB; ++c) {
-        const double2 sl = sj[c * cs], sg = sj[blk + c * cs];
-        const double2 c1 = c_scale(w1j, c_sub(sg, sl));
-        const double2 Li = li[c * cs], Gi = li[blk + c * cs];
-        const double2 t = c_scale(fB, c_add(c_mulc(sl, Li), c_mulc(sg, Gi)));
-        dl = c_sub(dl, c_add(c_mulc(c1, Li), t));
-        dg = c_sub(dg, c_sub(c_mulc(c1, Gi), t));
+        const double2 cc = cj[c * cs];
+        dl = c_fnmac(cc, Li[c], dl);
+        dg = c_fnmac(cc, Gi[c], dg);
+        t = c_fmac(sj[c * cs], Li[c], t);
+        t = c_fmac(sj[blk + c * cs], Gi[c], t);
       }
+      const double fB = (jp == 0 ? 0.5 : 1.0) * dt;
+      dl = make_double2(fma(-fB, t.x, dl.x), fma(-fB, t.y, dl.y));
+      dg = make_double2(fma(fB, t.x, dg.x), fma(fB, t.y, dg.y));
+    } else if (i >= 1) {   // the diagonal block, use 1 with f = 1/2: + c, - c
+      const double2 *si = Sig + (size_t)i * 2 * blk + (size_t)p * nk + k;   // S(i)_{cp}
+      double2 t = z;
+#pragma unroll
+      for (int c = 0; c < NB; ++c) {
+        t = c_fmac(lj[c * cs], si[c * cs], t);
+        t = c_fmac(lj[blk + c * cs], si[blk + c * cs], t);
+      }
+      const double fA = 0.5 * dt;
+      dl = make_double2(fma(fA, t.x, dl.x), fma(fA, t.y, dl.y));
+      dg = make_double2(fma(-fA, t.x, dg.x), fma(-fA, t.y, dg.y));
     }
     double2 *dst = (i == n) ? lamRowN + (size_t)jp * 2 * blk : lamH + tri(i, jp) * 2 * blk;
     double2 *e0 = dst + (size_t)pq * nk + k;
@@ -675,16 +709,19 @@ int uv_splits(const Mesh &m, int n) {
 template <int NB>
 cudaError_t adj_sweep_nb(const Mesh &m, int n, double dt, const double2 *H, const double2 *Sig,
                          const double2 *lamI, double2 *lamSig, double2 *lamH, double2 *lamRowN,
-                         double2 *coef_work, cudaStream_t st) {
+                         double2 *coef_work, double2 *c1_work, cudaStream_t st) {
   const CoefShape sh = coef_shape(m, n);
   double2 *out = sh.nz > 1 ? coef_work : lamSig;
   adj_coef_kernel<NB><<<sh.grid, sh.threads, 0, st>>>(H, lamI, out, n, m.nk, sh.jchunk, dt);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  adj_c1_kernel<<<grid_for_count((size_t)(n + 1) * blkof(m)), 256, 0, st>>>(Sig, c1_work, n, blkof(m), dt);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   const int nch = n / kHistChunk + 1;   // chunks covering j' = 0..n
   const long elems = (long)NB * NB * m.nk;
   const dim3 hgrid((unsigned)((elems + 255) / 256), n + 1, (unsigned)nch);
-  adj_hist_kernel<NB><<<hgrid, 256, 0, st>>>(Sig, lamI, lamH, lamRowN, n, m.nk, kHistChunk, dt);
+  adj_hist_kernel<NB><<<hgrid, 256, 0, st>>>(Sig, c1_work, lamI, lamH, lamRowN, n, m.nk, kHistChunk, dt);
   e = cudaGetLastError();
   if (e != cudaSuccess || sh.nz == 1) return e;
   const size_t count = (size_t)(n + 1) * 2 * blkof(m);
@@ -748,8 +785,9 @@ size_t adj_coef_workspace_bytes(const Mesh &m, int nmax) {
 
 cudaError_t launch_adj_sweep(const Mesh &m, int n, double dt, const double2 *H, const double2 *Sig,
                              const double2 *lamI, double2 *lamSig, double2 *lamH, double2 *lamRowN,
-                             double2 *coef_work, cudaStream_t st) {
-  KBE_NB_SWITCH(m.nb, return adj_sweep_nb<NB>(m, n, dt, H, Sig, lamI, lamSig, lamH, lamRowN, coef_work, st));
+                             double2 *coef_work, double2 *c1_work, cudaStream_t st) {
+  KBE_NB_SWITCH(m.nb, return adj_sweep_nb<NB>(m, n, dt, H, Sig, lamI, lamSig, lamH, lamRowN, coef_work,
+                                               c1_work, st));
   return cudaErrorInvalidValue;
 }
 

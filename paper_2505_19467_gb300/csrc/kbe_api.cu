@@ -73,6 +73,13 @@ struct kbe_handle {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
   std::vector<double> ev_flops, ev_flops_x, ev_bytes;
   size_t ev_used = 0;
+  struct PhaseEv {
+    cudaEvent_t a, b;
+    int phase;
+    double flops;
+  };
+  std::vector<PhaseEv> bev;    // backward phases
+  size_t bev_used = 0;
   kbe_profile_stats stats{};
 };
 
@@ -134,6 +141,11 @@ void free_all(kbe_handle *h) {
     cudaEventDestroy(pr.second);
   }
   h->ev.clear();
+  for (auto &pe : h->bev) {
+    cudaEventDestroy(pe.a);
+    cudaEventDestroy(pe.b);
+  }
+  h->bev.clear();
 }
 
 // collision sweep flops of one launch at row n: the method's count with the
@@ -295,7 +307,7 @@ struct AdjPtrs {
   double2 *cur;           // current density of stages 1..n_corr
   double2 *lamIa, *lamIb, *lamIc, *lamSig;
   double2 *save;          // the stored row n while its stages are republished
-  double2 *sigw, *coefw, *updw, *lamh, *lamRho;
+  double2 *sigw, *coefw, *updw, *lamh, *lamRho, *c1w;
   double *gA, *gU, *red;
   size_t row;             // complex numbers per row slot
 };
@@ -331,10 +343,47 @@ size_t adj_carve(const kbe_config *cfg, const Mesh &m, char *base, AdjPtrs *p) {
   p->updw = (double2 *)take(kbe::adj_update_workspace_bytes(m));
   p->lamh = (double2 *)take(blk * c16);
   p->lamRho = (double2 *)take((T + 1) * nb2 * c16);
+  p->c1w = (double2 *)take((T + 1) * blk * c16);
   p->gA = (double *)take(T * sizeof(double));
   p->gU = (double *)take(sizeof(double));
   p->red = (double *)take(kbe::redot_workspace_bytes());
   return off;
+}
+
+// backward phase timing (profiling only): open() records the start event of
+// a phase, close() its end
+struct PhaseTimer {
+  kbe_handle *h;
+  size_t cur = (size_t)-1;
+  void open(int phase, double flops = 0.0) {
+    if (!h->prof) return;
+    if (h->bev_used == h->bev.size()) {
+      kbe_handle::PhaseEv pe{};
+      cudaEventCreate(&pe.a);
+      cudaEventCreate(&pe.b);
+      h->bev.push_back(pe);
+    }
+    cur = h->bev_used++;
+    h->bev[cur].phase = phase;
+    h->bev[cur].flops = flops;
+    cudaEventRecord(h->bev[cur].a, h->stream);
+  }
+  void close() {
+    if (!h->prof || cur == (size_t)-1) return;
+    cudaEventRecord(h->bev[cur].b, h->stream);
+    cur = (size_t)-1;
+  }
+};
+
+// flops of the collision-row transposes at row n (8 per complex multiply-add):
+// the coefficient transpose takes 2 per pair (l, j) below the diagonal and 4
+// on and above it; the history transpose 2 per block for the first use (4 on
+// the diagonal) and 4 for the second, per N_b^3 n_k
+double adj_sweep_flops(const kbe_handle *h, int n) {
+  const double nb3 = (double)h->cfg.nb * h->cfg.nb * h->cfg.nb, N = n;
+  const double coef = 2.0 * N * (N + 1) / 2 + 4.0 * (N + 1) + 4.0 * N * (N + 1) / 2;
+  const double hist = 6.0 * N * (N + 1) / 2 + 4.0 * (N + 1);
+  return 8.0 * (coef + hist) * nb3 * h->mesh.nk;
 }
 
 #define KBE_TRY(expr, where)                          \
@@ -369,7 +418,9 @@ kbe_status backward_step(kbe_handle *h, const AdjPtrs &P, int n, double2 *lamIcu
   const int n2 = n >= 2 ? n - 2 : 0;
   const double ca0 = n >= 2 ? 1.5 : 1.0, cb0 = n >= 2 ? -0.5 : 0.0;
 
+  PhaseTimer tm{h};
   // ---- recompute step n (the forward's order and kernels) ----
+  tm.open(0);
   KBE_TRY(cudaMemcpyAsync(P.save, histN, rowc * sizeof(double2), cudaMemcpyDeviceToDevice, st), "backward save");
   KBE_TRY(kbe::launch_unpack_fp64(Hd + tri(n - 1, 0) * 2 * blk, P.rowp, (size_t)n, blk, st), "backward unpack");
   KBE_TRY(kbe::sigma_row(m, v, n - 1, Uc, nullptr, P.rowp, P.sigp, h->work, st), "backward sigma");
@@ -389,6 +440,7 @@ kbe_status backward_step(kbe_handle *h, const AdjPtrs &P, int n, double2 *lamIcu
     KBE_TRY(kbe::launch_pack(KBE_PREC_FP64, row(c), histN, (size_t)(n + 1), blk, st), "backward pack");
   }
   KBE_TRY(kbe::sigma_row(m, v, n, Uc, nullptr, row(nc), sig(nc + 1), h->work, st), "backward sigma");
+  tm.close();
 
   // ---- transpose ----
   double2 *lamN = P.lamH + tri(n, 0) * 2 * blk;       // row n (the final row's adjoint)
@@ -397,11 +449,15 @@ kbe_status backward_step(kbe_handle *h, const AdjPtrs &P, int n, double2 *lamIcu
   // density rho_n of the final row, used by later steps
   KBE_TRY(kbe::launch_adj_density(m, lrho(n), 1.0 / m.nk, lamN + (size_t)n * 2 * blk, st), "backward density");
   // final evaluation: I_n = sweep(Sigma(row), history with row n)
-  KBE_TRY(kbe::launch_adj_sweep(m, n, dt, Hd, sig(nc + 1), lamIcur, P.lamSig, P.lamH, lamN, P.coefw, st),
+  tm.open(1, adj_sweep_flops(h, n));
+  KBE_TRY(kbe::launch_adj_sweep(m, n, dt, Hd, sig(nc + 1), lamIcur, P.lamSig, P.lamH, lamN, P.coefw, P.c1w, st),
           "backward adj sweep");
+  tm.close();
+  tm.open(2);
   KBE_TRY(kbe::adj_sigma_row(m, v, n, Uc, row(nc), P.lamSig, lamN, P.sigw, st), "backward adj sigma");
   if (Uc != 0.0)   // Sigma is -U^2 times U-free products: dL/dU += (2/U) Re <lam_Sigma, Sigma>
     KBE_TRY(kbe::launch_redot(P.lamSig, sig(nc + 1), rowc, 2.0 / Uc, P.gU, P.red, st), "backward redot");
+  tm.close();
   kbe::AdjHvecArgs a{};
   a.U = Uc;
   a.hf = h->cfg.hf;
@@ -412,6 +468,7 @@ kbe_status backward_step(kbe_handle *h, const AdjPtrs &P, int n, double2 *lamIcu
   for (int c = nc; c >= 1; --c) {
     double2 *lamS = (c == nc) ? lamN : lst(c);
     double2 *lamPS = lst(c - 1);
+    tm.open(3);
     KBE_TRY(cudaMemsetAsync(lamPS, 0, rowc * sizeof(double2), st), "backward memset");
     KBE_TRY(cudaMemsetAsync(P.lamIc, 0, rowc * sizeof(double2), st), "backward memset");
     KBE_TRY(kbe::launch_adj_update(m, n, dt, 0.5, hk(c), Uk(c), Vk(c), P.rowp, P.Ip, Ist(c), lamS, lamP,
@@ -427,13 +484,19 @@ kbe_status backward_step(kbe_handle *h, const AdjPtrs &P, int n, double2 *lamIcu
     KBE_TRY(kbe::launch_adj_hvec(m, hop, a, v, P.lamh, st), "backward adj h");
     // the stage's collision row saw the previous stage's row as row n
     KBE_TRY(kbe::launch_pack(KBE_PREC_FP64, row(c - 1), histN, (size_t)(n + 1), blk, st), "backward pack");
-    KBE_TRY(kbe::launch_adj_sweep(m, n, dt, Hd, sig(c), P.lamIc, P.lamSig, P.lamH, lamPS, P.coefw, st),
+    tm.close();
+    tm.open(1, adj_sweep_flops(h, n));
+    KBE_TRY(kbe::launch_adj_sweep(m, n, dt, Hd, sig(c), P.lamIc, P.lamSig, P.lamH, lamPS, P.coefw, P.c1w, st),
             "backward adj sweep");
+    tm.close();
+    tm.open(2);
     KBE_TRY(kbe::adj_sigma_row(m, v, n, Uc, row(c - 1), P.lamSig, lamPS, P.sigw, st), "backward adj sigma");
     if (Uc != 0.0)
       KBE_TRY(kbe::launch_redot(P.lamSig, sig(c), rowc, 2.0 / Uc, P.gU, P.red, st), "backward redot");
+    tm.close();
   }
   double2 *lam0 = nc == 0 ? lamN : lst(0);
+  tm.open(3);
   KBE_TRY(kbe::launch_adj_update(m, n, dt, 0.0, hk(0), Uk(0), Vk(0), P.rowp, P.Ip, nullptr, lam0, lamP,
                                  lamIprev, nullptr, P.lamh, P.updw, h->status, st),
           "backward adj update");
@@ -447,6 +510,7 @@ kbe_status backward_step(kbe_handle *h, const AdjPtrs &P, int n, double2 *lamIcu
   KBE_TRY(kbe::launch_adj_hvec(m, hop, a, v, P.lamh, st), "backward adj h");
   KBE_TRY(cudaMemcpyAsync(histN, P.save, rowc * sizeof(double2), cudaMemcpyDeviceToDevice, st),
           "backward restore");
+  tm.close();
   return KBE_OK;
 }
 
@@ -792,6 +856,7 @@ kbe_status kbe_profile_enable(kbe_handle *h, int enable) {
   cudaStreamSynchronize(h->stream);
   h->prof = enable != 0;
   h->ev_used = 0;
+  h->bev_used = 0;
   h->stats = kbe_profile_stats{};
   return KBE_OK;
 }
@@ -811,6 +876,15 @@ kbe_status kbe_profile_read(kbe_handle *h, kbe_profile_stats *out) {
       s.sweep_flops_executed += h->ev_flops_x[i];
       s.sweep_bytes += h->ev_bytes[i];
       s.sweep_launches++;
+    }
+  }
+  for (int q = 0; q < 4; ++q) s.backward_ms[q] = 0.0;
+  s.backward_sweep_flops = 0.0;
+  for (size_t i = 0; i < h->bev_used; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->bev[i].a, h->bev[i].b) == cudaSuccess) {
+      s.backward_ms[h->bev[i].phase] += ms;
+      s.backward_sweep_flops += h->bev[i].flops;
     }
   }
   *out = s;

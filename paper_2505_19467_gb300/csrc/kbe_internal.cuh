@@ -58,6 +58,19 @@ __device__ __forceinline__ double2 c_fma(double2 a, double2 b, double2 acc) {
 }
 // i * a
 __device__ __forceinline__ double2 c_i(double2 a) { return make_double2(-a.y, a.x); }
+// fused forms, four FMAs each (signs and conjugates folded into the FMAs):
+// acc + a * conj(b)
+__device__ __forceinline__ double2 c_fmac(double2 a, double2 b, double2 acc) {
+  return make_double2(fma(a.x, b.x, fma(a.y, b.y, acc.x)), fma(a.y, b.x, fma(-a.x, b.y, acc.y)));
+}
+// acc - a * b
+__device__ __forceinline__ double2 c_fnma(double2 a, double2 b, double2 acc) {
+  return make_double2(fma(-a.x, b.x, fma(a.y, b.y, acc.x)), fma(-a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
+// acc - a * conj(b)
+__device__ __forceinline__ double2 c_fnmac(double2 a, double2 b, double2 acc) {
+  return make_double2(fma(-a.x, b.x, fma(-a.y, b.y, acc.x)), fma(-a.y, b.x, fma(a.x, b.y, acc.y)));
+}
 
 // ---- status word written by kernels (sticky, read by the host) -----------
 enum : int { kDevOk = 0, kDevNonFinite = 1, kDevEigNoConv = 2, kDevAdjUnsupported = 4 };
@@ -141,11 +154,12 @@ cudaError_t launch_unpack_fp64(const double2 *packed, double2 *out, size_t nbloc
                                cudaStream_t st);
 // transpose of the collision row at n: lamSig = lambda of the Sigma row;
 // lamH (blocks of rows < n) and lamRowN (row n) += lambda of the history
-// blocks the sweep read (H holds row n as that sweep saw it)
+// blocks the sweep read (H holds row n as that sweep saw it). c1_work holds
+// (n+1) blocks (the C1 coefficients).
 size_t adj_coef_workspace_bytes(const Mesh &m, int nmax);
 cudaError_t launch_adj_sweep(const Mesh &m, int n, double dt, const double2 *H, const double2 *Sig,
                              const double2 *lamI, double2 *lamSig, double2 *lamH, double2 *lamRowN,
-                             double2 *coef_work, cudaStream_t st);
+                             double2 *coef_work, double2 *c1_work, cudaStream_t st);
 // transpose of the Sigma row: lamRow += lambda of the G row (constant U)
 size_t adj_sigma_workspace_bytes(const Mesh &m, int n);
 cudaError_t adj_sigma_row(const Mesh &m, const double *v_host, int n, double U, const double2 *Grow,

@@ -14,7 +14,9 @@ error against the FP64 trajectory. With N > 1 (torchrun, one process per GPU)
 every rank advances its own independent c2 system (weak scaling, no
 data-path collective).
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
-prefix of the same workload.
+prefix of the same workload. The line also carries the reverse mode on the
+same system ("gradient": forward + kbe_backward for dL/dA_i, dL/dU);
+--gradient-fd checks that gradient by central differences instead.
 """
 from __future__ import annotations
 
@@ -72,9 +74,12 @@ def parse():
     p.add_argument("--precision", default="fp64", choices=["fp64", "df64", "c64"],
                    help="history storage / sweep arithmetic of the headline value (fp64 meets "
                         "the 1e-10 bar; df64 / c64 are the reduced-storage forms)")
-    p.add_argument("--forms", default="all", choices=["all", "none"],
-                   help="also time the other storage forms (speedup and error vs the headline)")
+    p.add_argument("--forms", default="all", choices=["all", "none", "gradient"],
+                   help="also time the other storage forms (speedup and error vs the headline), "
+                        "the batched and paper-shaped forms and the gradient; 'gradient': only the last")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--gradient-fd", action="store_true",
+                   help="check the c5 gradient (512 steps) by central differences on 16 A_i and U, then exit")
     return p.parse_args()
 
 
@@ -249,7 +254,7 @@ def run_ours(args, rank, world, local):
 
     # ---- the reduced-storage forms on the same workload (speedup, error) ----
     forms = {}
-    for form in ([] if args.forms == "none" else [f for f in ("fp64", "df64", "c64") if f != args.precision]):
+    for form in ([] if args.forms != "all" else [f for f in ("fp64", "df64", "c64") if f != args.precision]):
         gf = kbe.KBE.from_system(s, stream=stream, precision=kbe.PRECISIONS[form])
         tf, pf, _ = time_trajectories(gf, nt, args.steps, args.warmup, stream, None, dist)
         nkb_f, sc_f = gf.observables_all()
@@ -262,10 +267,12 @@ def run_ours(args, rank, world, local):
                        "dtype": DTYPES[form], "roofline": roofline(pf, form, tf)}
 
     # ---- batched form: uneven systems together vs one after another ----------
-    batched = paper = None
-    if args.forms != "none":
+    batched = paper = gradient = None
+    if args.forms == "all":
         batched = batched_form(kbe, stream, args)
         paper = paper_shape(kbe, stream)
+    if args.forms in ("all", "gradient"):
+        gradient = gradient_form(kbe, stream, args)
 
     if rank == 0:
         line = {
@@ -286,6 +293,7 @@ def run_ours(args, rank, world, local):
             "forms": forms,
             "batched": batched,
             "paper_shape": paper,
+            "gradient": gradient,
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(s)
@@ -337,6 +345,84 @@ def paper_shape(kbe, stream):
             del H, I, w
             torch.cuda.empty_cache()
     return out
+
+
+def gradient_form(kbe, stream, args):
+    """c5: the gradient of L = sum_kb (n_kb(t_N) - n*_kb)^2 (n* ~ U(0,1), seed 4)
+    with respect to the 512 Peierls samples A_i and U on c2's system: one
+    forward trajectory, then kbe_backward, each timed with CUDA events on the
+    handle's stream. The collision-row transposes are set against the FP64
+    pipe (their flops: kbe_profile_stats.backward_sweep_flops)."""
+    import torch
+    s = ki.config("c2", nt=args.nt)
+    nt = s.nt
+    tgt = ki.targets(s.nk, s.nb, seed=4)
+    g = kbe.KBE.from_system(s, stream=stream)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    g.step(nt)
+    e[1].record(stream)
+    nkb, _ = g.observables(nt)
+    g.profile(True)
+    dA, dU = g.backward(2.0 * (nkb - tgt))
+    e[2].record(stream)
+    e[2].synchronize()
+    pb = g.profile_read()
+    g.close()
+    fwd, bwd = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    bm = pb["backward_ms"]
+    achieved = pb["backward_sweep_flops"] / (bm[1] * 1e-3) / 1e9
+    peak = PEAKS["fp64"][0]
+    return {"workload": f"c5: c2's system, {nt} steps, loss sum (n_kb(t_N) - n*)^2, n* ~ U(0,1) seed 4; "
+                        f"gradient w.r.t. {nt} A_i and U",
+            "forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd,
+            "phases_ms": {"recompute": bm[0], "collision_transposes": bm[1], "sigma_transposes": bm[2],
+                          "update_and_h_transposes": bm[3]},
+            "collision_transposes_roofline": {"bound": "fp64", "achieved": achieved, "peak": peak,
+                                              "unit": "GFLOP/s FP64", "frac": achieved / peak},
+            "dL_dU": dU, "max_abs_dL_dA": float(np.abs(dA).max())}
+
+
+def gradient_fd_check(args):
+    """c5 gradient against central differences of the library's own forward
+    (h = 1e-6) on U and 16 seeded A_i; prints one JSON line."""
+    import dataclasses
+    import torch
+    import paper_2505_19467_gb300 as kbe
+    torch.cuda.set_device(0)
+    s = ki.config("c2", nt=args.nt)
+    nt = s.nt
+    tgt = ki.targets(s.nk, s.nb, seed=4)
+
+    def loss(A=None, U=None):
+        ss = dataclasses.replace(s, A=s.A if A is None else A, U=s.U if U is None else U)
+        g = kbe.KBE.from_system(ss)
+        g.step(nt)
+        n_, _ = g.observables(nt)
+        g.close()
+        return float(((n_ - tgt) ** 2).sum())
+
+    g = kbe.KBE.from_system(s)
+    g.step(nt)
+    nkb, _ = g.observables(nt)
+    dA, dU = g.backward(2.0 * (nkb - tgt))
+    g.close()
+    h = 1e-6
+    idx = [int(i) for i in np.sort(np.random.default_rng(4).choice(nt, 16, replace=False))]
+    fd, ad = [], []
+    for i in idx:
+        e = np.zeros(nt)
+        e[i] = h
+        fd.append((loss(A=s.A + e) - loss(A=s.A - e)) / (2 * h))
+        ad.append(float(dA[i]))
+    fd.append((loss(U=s.U + h) - loss(U=s.U - h)) / (2 * h))
+    ad.append(dU)
+    fd, ad = np.array(fd), np.array(ad)
+    print(json.dumps({"check": "c5 gradient vs central differences (h = 1e-6)", "steps": nt,
+                      "A_indices": idx, "adjoint": ad.tolist(), "fd": fd.tolist(),
+                      "normwise_rel_err": float(np.linalg.norm(ad - fd) / np.linalg.norm(fd)),
+                      "max_rel_err": float(np.max(np.abs(ad - fd)) / np.max(np.abs(fd)))}), flush=True)
 
 
 BATCH_N, BATCH_NT = 16, 64
@@ -441,6 +527,10 @@ def main():
     rank, world, local = dist_env()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.gradient_fd:
+        if rank == 0:
+            gradient_fd_check(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

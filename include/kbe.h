@@ -198,18 +198,21 @@ size_t kbe_memory_bytes(const kbe_config *cfg);
  *              A_i being the Peierls sample the step to t_{i+1} used (the
  *              i-th kbe_set_drive sample, or its last one when fewer were
  *              given),
- *   dL_dU    = dL/dU (host double [1]) for the constant U of kbe_set_interaction,
+ *   dL_dU    = dL/dU: host double [1] for the constant U of
+ *              kbe_set_interaction (len 1), or host double [nt_max + 1] with
+ *              dL/dU(t_i) per sample when it was given U(t) samples (entries
+ *              beyond t_N are 0),
  * the exact derivative of the computed trajectory (the discrete adjoint of
  * Algorithm 1 as this library evaluates it: the trapezoid collision sums, the
  * DFT form of Eq. 7, the series propagators, the mean field and the
  * predictor-corrector schedule). Steps are recomputed one at a time from the
  * stored history, so no per-step tape is kept; the history is left as it was
  * and stepping may continue afterwards.
- * Requires KBE_PREC_FP64, a constant U (len 1), at least one step, and
- * dt ||h(k)||_rowsum <= 1/4 at every step (the propagators' unscaled
- * series); KBE_ERR_UNSUPPORTED otherwise (the handle stays usable). The first
- * call allocates kbe_backward_memory_bytes(cfg) of device memory, kept until
- * kbe_destroy (KBE_ERR_OOM if it does not fit). Synchronises. */
+ * Requires KBE_PREC_FP64, at least one step, and dt ||h(k)||_rowsum <= 1/4
+ * at every step (the propagators' unscaled series); KBE_ERR_UNSUPPORTED
+ * otherwise (the handle stays usable). The first call allocates
+ * kbe_backward_memory_bytes(cfg) of device memory, kept until kbe_destroy
+ * (KBE_ERR_OOM if it does not fit). Synchronises. */
 kbe_status kbe_backward(kbe_handle *h, const double *dL_dn, double *dL_dA, double *dL_dU);
 size_t kbe_backward_memory_bytes(const kbe_config *cfg);
 

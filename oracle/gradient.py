@@ -30,11 +30,14 @@ import numpy as np
 from .oracle import Oracle
 
 
-def occupations(sys, N: int, A: Optional[np.ndarray] = None, U: Optional[float] = None) -> np.ndarray:
-    """n_kb(t_N) [nk][nb] of the oracle's trajectory with drive A and constant U."""
+def occupations(sys, N: int, A: Optional[np.ndarray] = None, U=None) -> np.ndarray:
+    """n_kb(t_N) [nk][nb] of the oracle's trajectory with drive A and U: a
+    constant, or samples U(t_i) (len >= max(N, sys.nt) + 1)."""
+    samples = U is not None and np.ndim(U) > 0
     s = dataclasses.replace(sys, A=sys.A if A is None else np.asarray(A, np.float64).copy(),
-                            U=sys.U if U is None else float(U))
-    o = Oracle(s, nt_max=max(N, s.nt))
+                            U=sys.U if (U is None or samples) else float(U))
+    nt_max = max(N, s.nt)
+    o = Oracle(s, nt_max=nt_max, U=np.asarray(U, np.float64)[: nt_max + 1] if samples else None)
     o.step(N)
     nkb, _ = o.observables(N)
     o.close()
@@ -57,6 +60,19 @@ def directional(sys, N: int, target: np.ndarray, dA: Optional[np.ndarray] = None
         return (lp - lm) / (2 * step)
 
     return (4.0 * D(h / 2) - D(h)) / 3.0
+
+
+def gradient_samples(sys, N: int, target: np.ndarray, U: np.ndarray, which=None, h: float = 1e-3):
+    """dL/dU_i for samples U(t_i) (i in which, default 0..N), at the drive sys.A"""
+    U = np.asarray(U, np.float64)
+
+    def D(i, step):
+        e = np.zeros_like(U)
+        e[i] = step
+        return (loss(sys, N, target, U=U + e) - loss(sys, N, target, U=U - e)) / (2 * step)
+
+    idx = range(N + 1) if which is None else which
+    return np.array([(4.0 * D(i, h / 2) - D(i, h)) / 3.0 for i in idx])
 
 
 def gradient(sys, N: int, target: np.ndarray, which_A=None, with_U: bool = True, h: float = 1e-3):

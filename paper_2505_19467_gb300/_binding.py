@@ -185,6 +185,7 @@ class KBE:
                  paper_shift: int = 0, stream=None, _borrow=None):
         lib = load()
         self.nb, self.nk, self.nt_max = nb, int(L[0]) * int(L[1]), nt_max
+        self._u_len = 1
         self._owned = _borrow is None
         if _borrow is not None:      # a handle owned by a batch
             self._h = ctypes.c_void_p(_borrow)
@@ -235,6 +236,7 @@ class KBE:
 
     def set_interaction(self, U, v=None):
         U = np.ascontiguousarray(np.atleast_1d(U), np.float64)
+        self._u_len = len(U)
         v = None if v is None else np.ascontiguousarray(v, np.float64)
         _check(load().kbe_set_interaction(self._h, len(U), _np_ptr(U), _np_ptr(v)), self._h)
 
@@ -301,12 +303,13 @@ class KBE:
 
     def backward(self, dL_dn):
         """(dL/dA [nt_max], dL/dU) for the cotangent dL_dn [nk][nb] of the
-        current row's occupations (kbe_backward)."""
+        current row's occupations (kbe_backward). dL/dU is a float for a
+        constant U, an array [nt_max + 1] (per sample) for U(t) samples."""
         g = np.ascontiguousarray(dL_dn, np.float64).reshape(self.nk, self.nb)
         dA = np.empty(self.nt_max, np.float64)
-        dU = np.empty(1, np.float64)
+        dU = np.empty(self.nt_max + 1, np.float64)
         _check(load().kbe_backward(self._h, _np_ptr(g), _np_ptr(dA), _np_ptr(dU)), self._h)
-        return dA, float(dU[0])
+        return dA, (float(dU[0]) if self._u_len == 1 else dU)
 
     def profile(self, enable: bool = True):
         _check(load().kbe_profile_enable(self._h, int(enable)), self._h)

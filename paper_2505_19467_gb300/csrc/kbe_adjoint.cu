@@ -253,25 +253,29 @@ struct VMat {
 //            + sum_a v_pa y_aq sum_m v_mq conj(x_am) lam_E_pm
 //            + sum_j v_jp lam_E_jq sum_b v_qb conj(x_jb) y_pb
 //   lam_y_pq = x_pq conj(W_pq) + sum_j v_jp x_jq sum_m v_mq conj(lam_E_jm) x_pm
+//   and returns Re conj(lam_z_pq) (x_pq Q_pq - E_pq), the U-free product's share of dL/dfac.
 template <int NB>
-__device__ __forceinline__ void prod_adj(const double2 *__restrict__ x, const double2 *__restrict__ y,
-                                         const double2 *__restrict__ lz, int p, int q, int nk, double fac,
-                                         const VMat &vm, double2 &lx, double2 &ly) {
+__device__ __forceinline__ double prod_adj(const double2 *__restrict__ x, const double2 *__restrict__ y,
+                                           const double2 *__restrict__ lz, int p, int q, int nk, double fac,
+                                           const VMat &vm, double2 &lx, double2 &ly) {
 #define AT(M, r, c) M[(size_t)((r) * NB + (c)) * nk]
-  double2 Q = make_double2(0, 0), W = make_double2(0, 0);
+  double2 Q = make_double2(0, 0), W = make_double2(0, 0), E = make_double2(0, 0);
   double2 t3 = make_double2(0, 0), t4 = make_double2(0, 0), t6 = make_double2(0, 0);
 #pragma unroll 1
   for (int a = 0; a < NB; ++a) {
     const double va = vm.v[p * NB + a];   // v_pa (Q, t3)
     const double vj = vm.v[a * NB + p];   // v_jp with j = a (W, t4, t6)
     double2 sq = make_double2(0, 0), sw = make_double2(0, 0), s3 = make_double2(0, 0);
-    double2 s4 = make_double2(0, 0), s6 = make_double2(0, 0);
+    double2 s4 = make_double2(0, 0), s6 = make_double2(0, 0), se = make_double2(0, 0);
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const double vb = vm.v[q * NB + b];   // v_qb
       const double vm_ = vm.v[b * NB + q];  // v_mq with m = b
       if (va != 0.0) {
-        if (vb != 0.0) sq = c_add(sq, c_scale(vb, c_mulc(AT(x, a, b), AT(y, a, b))));
+        if (vb != 0.0) {
+          sq = c_add(sq, c_scale(vb, c_mulc(AT(x, a, b), AT(y, a, b))));
+          se = c_add(se, c_scale(vb, c_mulc(AT(x, p, b), AT(y, a, b))));   // x_pb conj(y_ab)
+        }
         if (vm_ != 0.0) s3 = c_add(s3, c_scale(vm_, c_mulc(AT(lz, p, b), AT(x, a, b))));
       }
       if (vj != 0.0) {
@@ -284,6 +288,7 @@ __device__ __forceinline__ void prod_adj(const double2 *__restrict__ x, const do
     }
     if (va != 0.0) {
       Q = c_add(Q, c_scale(va, sq));
+      E = c_fma(c_scale(va, AT(x, a, q)), se, E);
       t3 = c_fma(c_scale(va, AT(y, a, q)), s3, t3);
     }
     if (vj != 0.0) {
@@ -298,16 +303,24 @@ __device__ __forceinline__ void prod_adj(const double2 *__restrict__ x, const do
   lx = c_add(lx, c_scale(-fac, c_add(t3, t4)));
   ly = c_add(ly, c_mulc(AT(x, p, q), W));
   ly = c_add(ly, c_scale(-fac, t6));
+  const double2 z = c_sub(c_mul(AT(x, p, q), Q), E);
+  const double2 l = AT(lz, p, q);
+  return l.x * z.x + l.y * z.y;
 #undef AT
 }
 
 // one thread per (l, p, R): row p of lam_G^<(R) and lam_G^>(R) of pair l.
-// Sigma^< is the product with (x, y) = (G^<, G^>), Sigma^> with (G^>, G^<).
+// Sigma^< is the product with (x, y) = (G^<, G^>), Sigma^> with (G^>, G^<);
+// fac = -U_n U_l. gpart[l][p][R] receives this thread's share of
+// g_l = Re <lam_Sigma(n,l), Sigma(n,l) / fac>, evaluated in real space (the
+// DFT pair makes the k-space and real-space inner products equal).
 template <int NB>
 __global__ void __launch_bounds__(128) sigma_adj_products_kernel(const double2 *__restrict__ GR,
                                                                  const double2 *__restrict__ LR,
                                                                  double2 *__restrict__ GLR, int n,
-                                                                 int nk, double fac, VMat vm) {
+                                                                 int nk, double Un,
+                                                                 const double *__restrict__ Ul, VMat vm,
+                                                                 double *__restrict__ gpart) {
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long total = (long)(n + 1) * NB * nk;
   if (idx >= total) return;
@@ -319,14 +332,46 @@ __global__ void __launch_bounds__(128) sigma_adj_products_kernel(const double2 *
   const double2 *gl = GR + (size_t)l * 2 * blk + R, *gg = gl + blk;
   const double2 *ll = LR + (size_t)l * 2 * blk + R, *lg = ll + blk;
   double2 *ol = GLR + (size_t)l * 2 * blk + (size_t)p * NB * nk + R, *og = ol + blk;
+  const double fac = -Un * (Ul ? Ul[l] : Un);
+  double g = 0.0;
 #pragma unroll 1
   for (int q = 0; q < NB; ++q) {
     double2 aL = make_double2(0, 0), aG = make_double2(0, 0);
-    prod_adj<NB>(gl, gg, ll, p, q, nk, fac, vm, aL, aG);
-    prod_adj<NB>(gg, gl, lg, p, q, nk, fac, vm, aG, aL);
+    g += prod_adj<NB>(gl, gg, ll, p, q, nk, fac, vm, aL, aG);
+    g += prod_adj<NB>(gg, gl, lg, p, q, nk, fac, vm, aG, aL);
     ol[(size_t)q * nk] = aL;
     og[(size_t)q * nk] = aG;
   }
+  gpart[idx] = g;
+}
+
+// dL/dU from the Sigma row n: fac_l = -U_n U_l, so with g_l = sum_{p,R} gpart,
+//   dL/dU_l += -U_n g_l (every l),  dL/dU_n += -sum_l U_l g_l.
+// One CTA, l in a fixed order (deterministic).
+__global__ void adj_sigma_u_kernel(const double *__restrict__ gpart, int n, int per_l, double Un,
+                                   const double *__restrict__ Ul, double *__restrict__ gU) {
+  __shared__ double red[32];
+  __shared__ double acc;
+  if (threadIdx.x == 0) acc = 0.0;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  for (int l = 0; l <= n; ++l) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < per_l; i += blockDim.x) s += gpart[(size_t)l * per_l + i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double g = 0.0;
+      for (int w = 0; w < nw; ++w) g += red[w];
+      const double ul = Ul ? Ul[l] : Un;
+      if (Ul) gU[l] += -Un * g;
+      else gU[n] += -Un * g;
+      acc += ul * g;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) gU[n] += -acc;
 }
 
 // ------------------------------------------------------------- update ----
@@ -546,12 +591,13 @@ struct HvecAdj {
   double2 *lam_rho_a, *lam_rho_b; // receive ca lam_mid, cb lam_mid (NULL: skip)
   double2 *lam_cur;               // G^<(n,n) block receiving i cur_scale lam_mid (NULL: skip)
   double cur_scale;
-  double *gA, *gU;
+  double *gA, *gU_a, *gU_b;       // dL/dU_mid goes half to each (U_mid = (U_{n-1} + U_n) / 2)
 };
 
-// h_k = h0(k - A d) + U hf(mid) (- U on the last band, paper shift) (+ dipole).
+// h_k = h0(k - A d) + U hf(mid) (- U on the last band, paper shift) (+ dipole),
+// U = U_mid of the step.
 //   dL/dA += Re sum_k tr(lam_h^+ dh0/dA),  dh0/dA = sum_r t(R_r) e^{i theta_r} (-i d.R_r);
-//   Lam = sum_k lam_h; dL/dU += Re tr(Lam^+ hf(mid)) - Re Lam_{N_b N_b} (shift);
+//   Lam = sum_k lam_h; dL/dU_mid = Re tr(Lam^+ hf(mid)) - Re Lam_{N_b N_b} (shift);
 //   lam_mid_jm = -U v_jm Lam_jm,  lam_mid_aa += U sum_j v_ja Lam_jj.
 // One CTA: a warp per element (a, b) reduces over k; thread 0 finishes.
 template <int NB>
@@ -617,7 +663,8 @@ __global__ void adj_hvec_kernel(Mesh m, HopTable hop, HvecAdj p, const double2 *
           lmid[a * NB + a] = c_add(lmid[a * NB + a], c_scale(p.U * p.v[j * NB + a], Lam[j * NB + j]));
     }
     if (p.paper_shift) gu -= Lam[NB * NB - 1].x;
-    *p.gU += gu;
+    *p.gU_a += 0.5 * gu;
+    *p.gU_b += 0.5 * gu;
     for (int e = 0; e < NB * NB; ++e) {
       if (p.lam_rho_a) p.lam_rho_a[e] = c_add(p.lam_rho_a[e], c_scale(p.ca, lmid[e]));
       if (p.lam_rho_b) p.lam_rho_b[e] = c_add(p.lam_rho_b[e], c_scale(p.cb, lmid[e]));
@@ -638,38 +685,6 @@ __global__ void adj_density_kernel(int e_count, int nk, const double2 *__restric
   const int total = e_count * nk;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x)
     lamDiag[i] = c_add(lamDiag[i], c_i(c_scale(scale, lamRho[i / nk])));
-}
-
-// acc += scale * Re sum conj(a) b, in a fixed order (fixed grid, then one CTA)
-constexpr int kRedotBlocks = 304;
-__global__ void redot_kernel(const double2 *__restrict__ a, const double2 *__restrict__ b, size_t count,
-                             double *__restrict__ part) {
-  __shared__ double red[32];
-  double s = 0.0;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const double2 x = a[i], y = b[i];
-    s += x.x * y.x + x.y * y.y;
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  if (lane == 0) red[warp] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
-    part[blockIdx.x] = t;
-  }
-}
-
-__global__ void redot_final_kernel(const double *__restrict__ part, int nparts, double scale,
-                                   double *__restrict__ acc) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < nparts; ++i) t += part[i];
-    *acc += scale * t;
-  }
 }
 
 // shapes ------------------------------------------------------------------
@@ -793,11 +808,12 @@ cudaError_t launch_adj_sweep(const Mesh &m, int n, double dt, const double2 *H, 
 
 size_t adj_sigma_workspace_bytes(const Mesh &m, int n) {
   const size_t blk = (size_t)m.nb * m.nb * m.nk;
-  return 3 * (size_t)(n + 1) * 2 * blk * sizeof(double2);
+  return 3 * (size_t)(n + 1) * 2 * blk * sizeof(double2) + (size_t)(n + 1) * m.nb * m.nk * sizeof(double);
 }
 
-cudaError_t adj_sigma_row(const Mesh &m, const double *v_host, int n, double U, const double2 *Grow,
-                          const double2 *lamSig, double2 *lamRow, double2 *work, cudaStream_t st) {
+cudaError_t adj_sigma_row(const Mesh &m, const double *v_host, int n, double Un, const double *Ul_dev,
+                          const double2 *Grow, const double2 *lamSig, double2 *lamRow, double *gU,
+                          double2 *work, cudaStream_t st) {
   const size_t blk = (size_t)m.nb * m.nb * m.nk;
   const size_t row = (size_t)(n + 1) * 2 * blk;
   const long narr = (long)(n + 1) * 2 * m.nb * m.nb;
@@ -811,10 +827,14 @@ cudaError_t adj_sigma_row(const Mesh &m, const double *v_host, int n, double U, 
   VMat vm;
   for (int i = 0; i < kMaxNb * kMaxNb; ++i) vm.v[i] = 0.0;
   for (int i = 0; i < m.nb * m.nb; ++i) vm.v[i] = v_host[i];
-  const double fac = -U * U;
   const long total = (long)(n + 1) * m.nb * m.nk;
   const unsigned blocks = (unsigned)((total + 127) / 128);
-  KBE_NB_SWITCH(m.nb, (sigma_adj_products_kernel<NB><<<blocks, 128, 0, st>>>(GR, LR, GLR, n, m.nk, fac, vm)));
+  double *gpart = (double *)(work + 3 * row);
+  KBE_NB_SWITCH(m.nb, (sigma_adj_products_kernel<NB><<<blocks, 128, 0, st>>>(GR, LR, GLR, n, m.nk, Un, Ul_dev, vm,
+                                                                               gpart)));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  adj_sigma_u_kernel<<<1, 256, 0, st>>>(gpart, n, m.nb * m.nk, Un, Ul_dev, gU);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_dft_rows(GLR, lamRow, narr, m.L0, m.L1, -1, 1.0 / m.nk, st, true);
@@ -851,7 +871,8 @@ cudaError_t launch_adj_hvec(const Mesh &m, const HopTable &hop, const AdjHvecArg
   p.lam_cur = a.lam_cur;
   p.cur_scale = a.cur_scale;
   p.gA = a.gA;
-  p.gU = a.gU;
+  p.gU_a = a.gU_a;
+  p.gU_b = a.gU_b;
   KBE_NB_SWITCH(m.nb, (adj_hvec_kernel<NB><<<1, 256, 0, st>>>(m, hop, p, lamh)));
   return cudaGetLastError();
 }
@@ -860,17 +881,6 @@ cudaError_t launch_adj_density(const Mesh &m, const double2 *lamRho, double scal
                                cudaStream_t st) {
   const int total = m.nb * m.nb * m.nk;
   adj_density_kernel<<<(total + 255) / 256, 256, 0, st>>>(m.nb * m.nb, m.nk, lamRho, scale, lamDiag);
-  return cudaGetLastError();
-}
-
-size_t redot_workspace_bytes() { return kRedotBlocks * sizeof(double); }
-
-cudaError_t launch_redot(const double2 *a, const double2 *b, size_t count, double scale, double *acc,
-                         double *part, cudaStream_t st) {
-  redot_kernel<<<kRedotBlocks, 256, 0, st>>>(a, b, count, part);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  redot_final_kernel<<<1, 32, 0, st>>>(part, kRedotBlocks, scale, acc);
   return cudaGetLastError();
 }
 

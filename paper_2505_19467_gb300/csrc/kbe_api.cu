@@ -308,7 +308,7 @@ struct AdjPtrs {
   double2 *lamIa, *lamIb, *lamIc, *lamSig;
   double2 *save;          // the stored row n while its stages are republished
   double2 *sigw, *coefw, *updw, *lamh, *lamRho, *c1w;
-  double *gA, *gU, *red;
+  double *gA, *gU;        // dL/dA_i; dL/dU_i per U sample (summed for a constant U)
   size_t row;             // complex numbers per row slot
 };
 
@@ -345,8 +345,7 @@ size_t adj_carve(const kbe_config *cfg, const Mesh &m, char *base, AdjPtrs *p) {
   p->lamRho = (double2 *)take((T + 1) * nb2 * c16);
   p->c1w = (double2 *)take((T + 1) * blk * c16);
   p->gA = (double *)take(T * sizeof(double));
-  p->gU = (double *)take(sizeof(double));
-  p->red = (double *)take(kbe::redot_workspace_bytes());
+  p->gU = (double *)take((T + 1) * sizeof(double));
   return off;
 }
 
@@ -398,7 +397,9 @@ double adj_sweep_flops(const kbe_handle *h, int n) {
 kbe_status backward_step(kbe_handle *h, const AdjPtrs &P, int n, double2 *lamIcur, double2 *lamIprev) {
   const Mesh &m = h->mesh;
   const size_t blk = h->blk, nb2 = (size_t)h->nb2;
-  const double dt = h->cfg.dt, Uc = h->Useq[0];
+  const double dt = h->cfg.dt;
+  const double *Ul = h->Useq.size() == 1 ? nullptr : h->d_U;   // as the forward's Sigma rows
+  const double Un = U_at(h, n), Up = U_at(h, n - 1);
   const int nc = h->cfg.n_corr;
   cudaStream_t st = h->stream;
   const double *v = h->v.data();
@@ -423,7 +424,7 @@ kbe_status backward_step(kbe_handle *h, const AdjPtrs &P, int n, double2 *lamIcu
   tm.open(0);
   KBE_TRY(cudaMemcpyAsync(P.save, histN, rowc * sizeof(double2), cudaMemcpyDeviceToDevice, st), "backward save");
   KBE_TRY(kbe::launch_unpack_fp64(Hd + tri(n - 1, 0) * 2 * blk, P.rowp, (size_t)n, blk, st), "backward unpack");
-  KBE_TRY(kbe::sigma_row(m, v, n - 1, Uc, nullptr, P.rowp, P.sigp, h->work, st), "backward sigma");
+  KBE_TRY(kbe::sigma_row(m, v, n - 1, Up, Ul, P.rowp, P.sigp, h->work, st), "backward sigma");
   KBE_TRY(kbe::launch_sweep(m, n - 1, dt, KBE_PREC_FP64, h->H, P.sigp, P.Ip, h->coef, st), "backward sweep");
   kbe_status s = build_props(h, n, rho(n - 1), rho(n2), ca0, cb0, hk(0), Uk(0), Vk(0));
   if (s != KBE_OK) return s;
@@ -433,13 +434,13 @@ kbe_status backward_step(kbe_handle *h, const AdjPtrs &P, int n, double2 *lamIcu
   for (int c = 1; c <= nc; ++c) {
     KBE_TRY(kbe::launch_local_density(m, row(c - 1) + (size_t)n * 2 * blk, cur(c), st), "backward density");
     if ((s = build_props(h, n, rho(n - 1), cur(c), 0.5, 0.5, hk(c), Uk(c), Vk(c))) != KBE_OK) return s;
-    KBE_TRY(kbe::sigma_row(m, v, n, Uc, nullptr, row(c - 1), sig(c), h->work, st), "backward sigma");
+    KBE_TRY(kbe::sigma_row(m, v, n, Un, Ul, row(c - 1), sig(c), h->work, st), "backward sigma");
     KBE_TRY(kbe::launch_sweep(m, n, dt, KBE_PREC_FP64, h->H, sig(c), Ist(c), h->coef, st), "backward sweep");
     KBE_TRY(kbe::launch_update_row(m, n, dt, 0.5, hk(c), Uk(c), Vk(c), P.rowp, P.Ip, Ist(c), row(c), st),
             "backward update");
     KBE_TRY(kbe::launch_pack(KBE_PREC_FP64, row(c), histN, (size_t)(n + 1), blk, st), "backward pack");
   }
-  KBE_TRY(kbe::sigma_row(m, v, n, Uc, nullptr, row(nc), sig(nc + 1), h->work, st), "backward sigma");
+  KBE_TRY(kbe::sigma_row(m, v, n, Un, Ul, row(nc), sig(nc + 1), h->work, st), "backward sigma");
   tm.close();
 
   // ---- transpose ----
@@ -454,17 +455,16 @@ kbe_status backward_step(kbe_handle *h, const AdjPtrs &P, int n, double2 *lamIcu
           "backward adj sweep");
   tm.close();
   tm.open(2);
-  KBE_TRY(kbe::adj_sigma_row(m, v, n, Uc, row(nc), P.lamSig, lamN, P.sigw, st), "backward adj sigma");
-  if (Uc != 0.0)   // Sigma is -U^2 times U-free products: dL/dU += (2/U) Re <lam_Sigma, Sigma>
-    KBE_TRY(kbe::launch_redot(P.lamSig, sig(nc + 1), rowc, 2.0 / Uc, P.gU, P.red, st), "backward redot");
+  KBE_TRY(kbe::adj_sigma_row(m, v, n, Un, Ul, row(nc), P.lamSig, lamN, P.gU, P.sigw, st), "backward adj sigma");
   tm.close();
   kbe::AdjHvecArgs a{};
-  a.U = Uc;
+  a.U = 0.5 * (Up + Un);   // U_mid of the step
   a.hf = h->cfg.hf;
   a.paper_shift = h->cfg.paper_shift;
   a.A = A_at(h, n - 1);
   a.gA = P.gA + (n - 1);
-  a.gU = P.gU;
+  a.gU_a = P.gU + (n - 1);
+  a.gU_b = P.gU + n;
   for (int c = nc; c >= 1; --c) {
     double2 *lamS = (c == nc) ? lamN : lst(c);
     double2 *lamPS = lst(c - 1);
@@ -490,9 +490,8 @@ kbe_status backward_step(kbe_handle *h, const AdjPtrs &P, int n, double2 *lamIcu
             "backward adj sweep");
     tm.close();
     tm.open(2);
-    KBE_TRY(kbe::adj_sigma_row(m, v, n, Uc, row(c - 1), P.lamSig, lamPS, P.sigw, st), "backward adj sigma");
-    if (Uc != 0.0)
-      KBE_TRY(kbe::launch_redot(P.lamSig, sig(c), rowc, 2.0 / Uc, P.gU, P.red, st), "backward redot");
+    KBE_TRY(kbe::adj_sigma_row(m, v, n, Un, Ul, row(c - 1), P.lamSig, lamPS, P.gU, P.sigw, st),
+            "backward adj sigma");
     tm.close();
   }
   double2 *lam0 = nc == 0 ? lamN : lst(0);
@@ -1013,8 +1012,6 @@ kbe_status kbe_backward(kbe_handle *h, const double *dL_dn, double *dL_dA, doubl
   if (h->n < 1) return fail(h, KBE_ERR_STATE, "backward: no step to differentiate (call kbe_step first)");
   if (h->cfg.precision != KBE_PREC_FP64)
     return fail(h, KBE_ERR_UNSUPPORTED, "backward: needs the FP64 history (KBE_PREC_FP64)");
-  if (h->Useq.size() != 1)
-    return fail(h, KBE_ERR_UNSUPPORTED, "backward: needs a constant U (set_interaction with len 1)");
   const int nk = h->mesh.nk, nb = h->cfg.nb;
   for (int i = 0; i < nk * nb; ++i)
     if (!std::isfinite(dL_dn[i])) return fail(h, KBE_ERR_NONFINITE, "backward: non-finite dL/dn");
@@ -1039,7 +1036,7 @@ kbe_status kbe_backward(kbe_handle *h, const double *dL_dn, double *dL_dA, doubl
   cudaError_t e = cudaMemsetAsync(P.lamH, 0, (tri(N, N) + 1) * 2 * blk * sizeof(double2), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(P.lamRho, 0, (size_t)(N + 1) * nb2 * sizeof(double2), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(P.gA, 0, (size_t)h->cfg.nt_max * sizeof(double), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(P.gU, 0, sizeof(double), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.gU, 0, (size_t)(h->cfg.nt_max + 1) * sizeof(double), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(P.lamIa, 0, (size_t)(N + 1) * 2 * blk * sizeof(double2), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(P.lamIb, 0, (size_t)(N + 1) * 2 * blk * sizeof(double2), st);
   // n_kb = Im G^<_bb(k; N, N): dL = Re conj(i g) dG^<_bb for g = dL/dn_kb
@@ -1057,11 +1054,11 @@ kbe_status kbe_backward(kbe_handle *h, const double *dL_dn, double *dL_dA, doubl
     e = cudaMemsetAsync(lamIprev, 0, (size_t)n * 2 * blk * sizeof(double2), st);
     if (e != cudaSuccess) return cuda_fail(h, e, "backward memset");
   }
-  std::vector<double> gA((size_t)N);
-  double gU = 0.0;
+  std::vector<double> gA((size_t)N), gUs((size_t)h->cfg.nt_max + 1);
   int stat = 0;
   e = cudaMemcpyAsync(gA.data(), P.gA, sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&gU, P.gU, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(gUs.data(), P.gU, sizeof(double) * gUs.size(), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&stat, h->status, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(h, e, "backward result copy");
@@ -1076,10 +1073,17 @@ kbe_status kbe_backward(kbe_handle *h, const double *dL_dn, double *dL_dA, doubl
   s = check_device_status(h);
   if (s != KBE_OK) return s;
   for (int i = 0; i < h->cfg.nt_max; ++i) dL_dA[i] = i < N ? gA[(size_t)i] : 0.0;
-  *dL_dU = gU;
+  if (h->Useq.size() == 1) {   // one parameter: the sum over the samples it stands for
+    double t = 0.0;
+    for (double x : gUs) t += x;
+    dL_dU[0] = t;
+  } else {
+    for (size_t i = 0; i < gUs.size(); ++i) dL_dU[i] = gUs[i];
+  }
   for (int i = 0; i < N; ++i)
     if (!std::isfinite(gA[(size_t)i])) return fail(h, KBE_ERR_NONFINITE, "backward: non-finite gradient");
-  if (!std::isfinite(gU)) return fail(h, KBE_ERR_NONFINITE, "backward: non-finite gradient");
+  for (double x : gUs)
+    if (!std::isfinite(x)) return fail(h, KBE_ERR_NONFINITE, "backward: non-finite gradient");
   return KBE_OK;
 }
 

@@ -160,10 +160,12 @@ size_t adj_coef_workspace_bytes(const Mesh &m, int nmax);
 cudaError_t launch_adj_sweep(const Mesh &m, int n, double dt, const double2 *H, const double2 *Sig,
                              const double2 *lamI, double2 *lamSig, double2 *lamH, double2 *lamRowN,
                              double2 *coef_work, double2 *c1_work, cudaStream_t st);
-// transpose of the Sigma row: lamRow += lambda of the G row (constant U)
+// transpose of the Sigma row (factor -U_n U_l, Ul_dev NULL: U_l = U_n): lamRow
+// += lambda of the G row; gU[i] += dL/dU_i (gU[n] only when Ul_dev is NULL)
 size_t adj_sigma_workspace_bytes(const Mesh &m, int n);
-cudaError_t adj_sigma_row(const Mesh &m, const double *v_host, int n, double U, const double2 *Grow,
-                          const double2 *lamSig, double2 *lamRow, double2 *work, cudaStream_t st);
+cudaError_t adj_sigma_row(const Mesh &m, const double *v_host, int n, double Un, const double *Ul_dev,
+                          const double2 *Grow, const double2 *lamSig, double2 *lamRow, double *gU,
+                          double2 *work, cudaStream_t st);
 // transpose of the row and diagonal update: lamGprev, lamIp, lamIc +=;
 // lamh (per k) = lambda of the step's h through U, V and the diagonal
 size_t adj_update_workspace_bytes(const Mesh &m);
@@ -180,18 +182,13 @@ struct AdjHvecArgs {
   double ca, cb;
   double2 *lam_rho_a, *lam_rho_b, *lam_cur;
   double cur_scale;
-  double *gA, *gU;
+  double *gA, *gU_a, *gU_b;   // dL/dU_mid is split evenly between U_{n-1} and U_n
 };
 cudaError_t launch_adj_hvec(const Mesh &m, const HopTable &hop, const AdjHvecArgs &a, const double *v_host,
                             const double2 *lamh, cudaStream_t st);
 // lamDiag[e][k] += i scale lamRho[e]
 cudaError_t launch_adj_density(const Mesh &m, const double2 *lamRho, double scale, double2 *lamDiag,
                                cudaStream_t st);
-// acc += scale Re sum conj(a) b (deterministic order; part: redot_workspace_bytes)
-size_t redot_workspace_bytes();
-cudaError_t launch_redot(const double2 *a, const double2 *b, size_t count, double scale, double *acc,
-                         double *part, cudaStream_t st);
-
 // message returned by kbe_last_error(NULL) on this thread
 void set_last_error(const std::string &msg);
 

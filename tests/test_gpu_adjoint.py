@@ -5,7 +5,8 @@ library returns dL/dA_i for every Peierls sample and dL/dU.
 
 * Against the oracle: its Richardson-extrapolated central differences
   (oracle/gradient.py, pinned by tests/test_oracle_gradient.py) on small
-  systems, every A_i and U, bar 1e-7 of the largest component. The oracle's
+  systems, every A_i and U (or every U(t_i) sample), bar 1e-7 of the
+  largest component. The oracle's
   forward is the same discrete map up to rounding (exact exponentials in
   place of the converged series), so the two derivatives agree to the
   differences' accuracy.
@@ -131,6 +132,34 @@ def test_gradient_c2_system():
     assert np.all(np.isfinite(dA)) and np.abs(dA).max() > 0
 
 
+def test_gradient_per_u_sample():
+    """U(t) samples: dL/dU_i for every sample through Sigma (-U_n U_l) and the mean
+    field (U_mid), against the oracle's reference; and a constant U equals the
+    sum of the per-sample gradient at constant samples"""
+    sys = ki.small_system(2, (4, 1), 6, 0.05, 0.8, seed=9, drive_amp=0.5, paper_shift=1, band_velocity=0.5)
+    N = 6
+    tgt = ki.targets(sys.nk, sys.nb, seed=4)
+    Us = 0.8 * (1.0 + 0.3 * np.sin(np.arange(N + 1) * 0.9))
+    g = kbe.KBE.from_system(sys, U=Us)
+    g.step(N)
+    nkb, _ = g.observables(N)
+    dA, dU = g.backward(2.0 * (nkb - tgt))
+    g.close()
+    assert dU.shape == (N + 1,)
+    rU = og.gradient_samples(sys, N, tgt, Us)
+    scale = np.abs(rU).max()
+    assert np.abs(dU[: N + 1] - rU).max() < 1e-7 * scale, (dU, rU)
+    # constant samples: per-sample gradient sums to the scalar one
+    c = kbe.KBE.from_system(sys, U=np.full(N + 1, sys.U))
+    c.step(N)
+    nkb, _ = c.observables(N)
+    dA_s, dU_s = c.backward(2.0 * (nkb - tgt))
+    c.close()
+    dA_c, dU_c = gpu_grad(sys, N, tgt)
+    assert abs(dU_s.sum() - dU_c) < 1e-12 * abs(dU_c)
+    assert np.allclose(dA_s, dA_c, rtol=1e-12, atol=1e-16)
+
+
 def test_backward_leaves_state_and_is_deterministic():
     sys = ki.small_system(3, (4, 4), 12, 0.025, 1.0, seed=2, drive_amp=0.5, band_velocity=0.4)
     tgt = ki.targets(sys.nk, sys.nb, seed=4)
@@ -164,12 +193,6 @@ def test_backward_refusals():
         d.backward(z)
     assert ex.value.status == -7
     d.close()
-    u = kbe.KBE.from_system(sys, U=np.full(sys.nt + 1, 0.5))
-    u.step(2)
-    with pytest.raises(kbe.KBEError) as ex:
-        u.backward(z)
-    assert ex.value.status == -7
-    u.close()
     # dt ||h|| > 1/4 needs the scaled-and-squared propagators: refused, handle still steps
     big = ki.small_system(2, (4, 1), 6, 0.3, 0.5, seed=1, drive_amp=0.3)
     b = kbe.KBE.from_system(big)

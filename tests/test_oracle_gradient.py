@@ -45,8 +45,10 @@ def hf_matrix(sys, rho):
     return x
 
 
-def closed_form(sys, N, target):
-    """(L, dL/dA [N], dL/dU) at U = 0 by exact propagators"""
+def closed_form(sys, N, target, per_step_u=False):
+    """(L, dL/dA [N], dL/dU) at U = 0 by exact propagators; with per_step_u,
+    dL/dU is the list of each step's share (the derivative along U_mid of that
+    step)"""
     expm, frechet = scipy_linalg.expm, scipy_linalg.expm_frechet
     h0, _ = bare_h(sys, 0.0)
     G = []
@@ -87,13 +89,13 @@ def closed_form(sys, N, target):
                 + np.einsum('kab,kbc,kdc->kad', P, Gp, dP.conj()))
 
     gA = np.array([dL_from(propagate(i + 1, step_variation(i + 1, dPs[i][1]))) for i in range(N)])
-    gU = 0.0
+    gU = []
     for n in range(1, N + 1):
         mid = 0.5 * (rho[n - 1] + rho[n])
         E = np.repeat(hf_matrix(sys, mid)[None], sys.nk, axis=0) if sys.hf else \
             np.repeat(np.diag([0.0] * (sys.nb - 1) + [-float(sys.paper_shift)])[None], sys.nk, axis=0)
-        gU += dL_from(propagate(n, step_variation(n, E)))
-    return L, gA, gU
+        gU.append(dL_from(propagate(n, step_variation(n, E))))
+    return L, gA, (gU if per_step_u else sum(gU))
 
 
 @pytest.mark.parametrize("nb,L,shift", [(2, (4, 1), 1), (3, (2, 2), 0)])
@@ -118,3 +120,20 @@ def test_reference_gradient_detects_a_dropped_drive_derivative():
     _, gA_c, _ = closed_form(sys, 4, tgt)
     gA, _ = og.gradient(sys, 4, tgt, with_U=False)
     assert np.abs(gA - 0.5 * gA_c).max() > 1e-3 * np.abs(gA_c).max()
+
+
+def test_reference_gradient_per_u_sample_at_u0():
+    """U(t) samples, all zero: step n uses U_mid = (U_{n-1} + U_n) / 2 in its mean
+    field and shift, and Sigma (U_n U_l) has no first-order term, so
+    dL/dU_i = (g_i + g_{i+1}) / 2 with g_n the step-n share of the closed form"""
+    sys = ki.small_system(2, (4, 1), 5, 0.05, 0.0, seed=11, drive_amp=0.6, paper_shift=1,
+                          band_velocity=0.5)
+    N = 5
+    tgt = ki.targets(sys.nk, sys.nb, seed=4)
+    _, _, g = closed_form(sys, N, tgt, per_step_u=True)
+    ref = np.zeros(N + 1)
+    for n in range(1, N + 1):
+        ref[n - 1] += 0.5 * g[n - 1]
+        ref[n] += 0.5 * g[n - 1]
+    got = og.gradient_samples(sys, N, tgt, np.zeros(sys.nt + 1))
+    assert np.abs(got - ref).max() < 1e-8 * np.abs(ref).max(), (got, ref)

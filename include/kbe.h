@@ -79,9 +79,13 @@ typedef struct kbe_config {
   double dt;       /* time step (> 0)                                            */
   double beta, mu; /* Fermi initial state f(h0(k)) at inverse temperature beta  */
   int precision;   /* KBE_PREC_*                                                 */
-  int n_corr;      /* corrector passes of Algorithm 1 (fixed count, >= 0)        */
+  int n_corr;      /* corrector passes of Algorithm 1 (its "max", >= 0)          */
   int hf;          /* 1: Hartree-Fock mean field in h                            */
   int paper_shift; /* 1: the -U(t) n_c one-body term of Eq. 2 on band N_b - 1    */
+  double corr_tol; /* Algorithm 1's epsilon: > 0 stops the correctors of a step   *
+                    * once max_{j,k,a,b} |G^<(t_n,t_j) - previous pass| <=        *
+                    * corr_tol (decided on the device, no host round trip);       *
+                    * 0: always n_corr passes                                     */
 } kbe_config;
 
 typedef struct kbe_handle kbe_handle;
@@ -142,6 +146,10 @@ kbe_status kbe_set_dipole(kbe_handle *h, int len, const double *E, const double 
 /* t = 0: G^<(k;0,0) = i f(h0(k)), G^>(0,0) = G^<(0,0) - i, I = 0 (no initial
  * correlations). Clears a sticky error. Requires kbe_set_hamiltonian. */
 kbe_status kbe_reset(kbe_handle *h);
+
+/* Corrector passes run at each step 0..current (host int [n+1]; entry 0 is 0):
+ * n_corr everywhere when corr_tol = 0. Synchronises. */
+kbe_status kbe_corrector_iterations(kbe_handle *h, int *out);
 
 /* Advance nsteps rows with P(EC)^n_corr E (Algorithm 1). Asynchronous on the
  * handle's stream. KBE_ERR_STATE past nt_max or before kbe_reset. */

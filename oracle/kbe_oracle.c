@@ -489,6 +489,8 @@ void orc_update_row(int nb, int nk, int n, double dt, double theta, const double
 
 typedef struct orc {
   int nb, dim, L0, L1, nk, nt_max, n_corr, hf, paper_shift;
+  double corr_tol; /* Algorithm 1's epsilon (0: always n_corr passes) */
+  int *iters;      /* corrector passes run at each step */
   double dt, beta, mu;
   int nhop;
   int *hopR;
@@ -550,6 +552,7 @@ orc *orc_create(int nb, int dim, int L0, int L1, int nt_max, double dt, double b
   s->lam = malloc(sizeof(double) * s->nk * nb);
   s->obs = calloc((size_t)(nt_max + 1) * 6, sizeof(double));
   s->nkb = calloc((size_t)(nt_max + 1) * s->nk * nb, sizeof(double));
+  s->iters = calloc((size_t)(nt_max + 1), sizeof(int));
   if (!s->Hl || !s->Hg || !s->Ipl || !s->Ipg || !s->Icl || !s->Icg || !s->Sl || !s->Sg) {
     free(s->Hl); free(s->Hg); free(s->Ipl); free(s->Ipg); free(s->Icl); free(s->Icg);
     free(s->Sl); free(s->Sg); free(s->rho); free(s->h); free(s->Uk); free(s->Vk);
@@ -569,7 +572,7 @@ void orc_destroy(orc *s) {
   free(s->hopR); free(s->hopT); free(s->Useq); free(s->Aseq); free(s->Eseq);
   free(s->Hl); free(s->Hg); free(s->Ipl); free(s->Ipg); free(s->Icl); free(s->Icg);
   free(s->Sl); free(s->Sg); free(s->rho); free(s->h); free(s->Uk); free(s->Vk);
-  free(s->Wk); free(s->lam); free(s->obs); free(s->nkb);
+  free(s->Wk); free(s->lam); free(s->obs); free(s->nkb); free(s->iters);
   free(s);
 }
 
@@ -800,13 +803,32 @@ int orc_step(orc *s, int nsteps) {
     for (int e = 0; e < nb2; ++e) mid[e] = n >= 2 ? 1.5 * r1[e] - 0.5 * r2[e] : r1[e];
     build_h_and_props(s, n, mid);
     update(s, n, 0.0); /* predictor: Ibar = I_{n-1} */
+    /* the corrector loop of Algorithm 1: at most n_corr passes; with
+     * corr_tol > 0 it ends once the largest change of the new G^< row,
+     * max_{j,k,a,b} |G^< - G_0^<| (the reading of the algorithm's norm), is
+     * <= corr_tol */
+    const size_t rowlen = (size_t)(n + 1) * s->blk;
+    cplx *G0 = s->corr_tol > 0.0 ? malloc(sizeof(cplx) * rowlen) : NULL;
+    s->iters[n] = 0;
     for (int c = 0; c < s->n_corr; ++c) {
+      if (G0) memcpy(G0, s->Hl + tri(n, 0) * s->blk, sizeof(cplx) * rowlen);
       local_density(s, n, cur);
       for (int e = 0; e < nb2; ++e) mid[e] = 0.5 * (r1[e] + cur[e]);
       build_h_and_props(s, n, mid);
       evaluate_row(s, n);
       update(s, n, 0.5);
+      s->iters[n] += 1;
+      if (G0) {
+        double d = 0.0;
+        const cplx *G = s->Hl + tri(n, 0) * s->blk;
+        for (size_t q = 0; q < rowlen; ++q) {
+          double a = cabs(G[q] - G0[q]);
+          if (a > d) d = a;
+        }
+        if (d <= s->corr_tol) break;
+      }
     }
+    free(G0);
     evaluate_row(s, n); /* final evaluation: I_n for the next predictor */
     local_density(s, n, s->rho + (size_t)n * nb2);
     s->n = n;
@@ -819,6 +841,15 @@ int orc_step(orc *s, int nsteps) {
 }
 
 int orc_current(const orc *s) { return s->n; }
+
+void orc_set_corr_tol(orc *s, double tol) { s->corr_tol = tol > 0.0 ? tol : 0.0; }
+
+/* corrector passes run at steps 0..n */
+int orc_get_iters(const orc *s, int *out) {
+  if (s->n < 0) return -1;
+  memcpy(out, s->iters, sizeof(int) * (size_t)(s->n + 1));
+  return 0;
+}
 
 /* G^x(i, j) for any i, j <= n (x = 0: lesser, 1: greater), [k][a][b] */
 int orc_get_block(const orc *s, int i, int j, int which, double *out) {

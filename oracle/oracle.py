@@ -59,6 +59,8 @@ def _load():
             lib.orc_collision_row.argtypes = [i, i, i, d, P, P, P, P, P, P]
             lib.orc_propagators.argtypes = [i, i, d, P, P, P, P, P]
             lib.orc_update_row.argtypes = [i, i, i, d, d, P, P, P, P, P, P, P, P, P, P, P, P]
+            lib.orc_set_corr_tol.argtypes = [P, d]
+            lib.orc_get_iters.argtypes = [P, P]
             lib.orc_set_threads.argtypes = [i]
             lib.orc_threads.restype = i
             _lib = lib
@@ -173,6 +175,7 @@ class Oracle:
             M = _c128(sys.dipole_M)
             lib.orc_set_dipole(self._h, len(E), _ptr(E), _ptr(M))
             self._keep = self._keep + (E, M)
+        lib.orc_set_corr_tol(self._h, float(getattr(sys, "corr_tol", 0.0)))
         if lib.orc_reset(self._h) != 0:
             raise RuntimeError("oracle: reset failed")
 
@@ -204,6 +207,12 @@ class Oracle:
 
     def row(self, i: int, which: int = 0) -> np.ndarray:
         return np.stack([self.block(i, j, which) for j in range(i + 1)])
+
+    def iterations(self) -> np.ndarray:
+        """corrector passes run at steps 0..n"""
+        out = np.empty(self.n + 1, np.int32)
+        _load().orc_get_iters(self._h, _ptr(out))
+        return out
 
     def irow(self, which: int = 0) -> np.ndarray:
         out = np.empty((self.n + 1, self.nk, self.nb, self.nb), np.complex128)

@@ -54,6 +54,9 @@ struct kbe_handle {
   double *obs = nullptr;       // [(nt_max+1)][6]
   double *nkb = nullptr;       // [(nt_max+1)][nk][nb]
   int *status = nullptr;
+  int *d_skip = nullptr;                 // corrector passes skipped once converged (corr_tol > 0)
+  unsigned long long *d_maxdiff = nullptr;   // max |G^< change| of the last corrector pass (bits)
+  int *d_iters = nullptr;                // corrector passes run at each step [(nt_max+1)]
   int *d_hopR = nullptr;
   double2 *d_hopT = nullptr;
   double *d_U = nullptr;       // U(t_l) samples, nt_max+1
@@ -133,7 +136,7 @@ cudaError_t dalloc(kbe_handle *h, T **p, size_t count) {
 void free_all(kbe_handle *h) {
   void *ptrs[] = {h->H, h->Wrow[0], h->Wrow[1], h->coef, h->Ip, h->Ic, h->Sig, h->work, h->U, h->V,
                   h->hk, h->rho, h->obs, h->nkb, h->status, h->d_hopR, h->d_hopT, h->d_U,
-                  h->d_dipM, h->adj};
+                  h->d_dipM, h->adj, h->d_skip, h->d_maxdiff, h->d_iters};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (auto &pr : h->ev) {
@@ -174,19 +177,19 @@ double sweep_bytes(const kbe_handle *h, int n) {
 double2 *frow(kbe_handle *h, int i) { return h->Wrow[i & 1]; }
 
 // store row i into the history triangle: (G^<, dG) in the storage format
-kbe_status publish(kbe_handle *h, int i) {
+kbe_status publish(kbe_handle *h, int i, const int *skip = nullptr) {
   char *dst = (char *)h->H + tri(i, 0) * 2 * h->blk * h->esz;
-  cudaError_t e = kbe::launch_pack(h->cfg.precision, frow(h, i), dst, (size_t)(i + 1), h->blk, h->stream);
+  cudaError_t e = kbe::launch_pack(h->cfg.precision, frow(h, i), dst, (size_t)(i + 1), h->blk, h->stream, skip);
   if (e != cudaSuccess) return cuda_fail(h, e, "publish row");
   if (h->prof) h->stats.launches += 1;
   return KBE_OK;
 }
 
-kbe_status evaluate_row(kbe_handle *h, int n) {
+kbe_status evaluate_row(kbe_handle *h, int n, const int *skip = nullptr) {
   const Mesh &m = h->mesh;
   double2 *Hrow = frow(h, n);
   const double *Ul = h->Useq.size() == 1 ? nullptr : h->d_U;
-  cudaError_t e = kbe::sigma_row(m, h->v.data(), n, U_at(h, n), Ul, Hrow, h->Sig, h->work, h->stream);
+  cudaError_t e = kbe::sigma_row(m, h->v.data(), n, U_at(h, n), Ul, Hrow, h->Sig, h->work, h->stream, skip);
   if (e != cudaSuccess) return cuda_fail(h, e, "sigma_row");
   const bool timed = h->prof;
   if (timed) {
@@ -201,7 +204,7 @@ kbe_status evaluate_row(kbe_handle *h, int n) {
     }
     cudaEventRecord(h->ev[h->ev_used].first, h->stream);
   }
-  e = kbe::launch_sweep(m, n, h->cfg.dt, h->cfg.precision, h->H, h->Sig, h->Ic, h->coef, h->stream);
+  e = kbe::launch_sweep(m, n, h->cfg.dt, h->cfg.precision, h->H, h->Sig, h->Ic, h->coef, h->stream, skip);
   if (e != cudaSuccess) return cuda_fail(h, e, "collision sweep");
   if (timed) {
     cudaEventRecord(h->ev[h->ev_used].second, h->stream);
@@ -215,7 +218,8 @@ kbe_status evaluate_row(kbe_handle *h, int n) {
 }
 
 kbe_status build_props(kbe_handle *h, int n, const double2 *ra, const double2 *rb, double ca, double cb,
-                       double2 *hk = nullptr, double2 *Uk = nullptr, double2 *Vk = nullptr) {
+                       double2 *hk = nullptr, double2 *Uk = nullptr, double2 *Vk = nullptr,
+                       const int *skip = nullptr) {
   kbe::PropParams p{};
   p.A = A_at(h, n - 1);
   p.rho_a = ra;
@@ -229,24 +233,25 @@ kbe_status build_props(kbe_handle *h, int n, const double2 *ra, const double2 *r
   p.dipM = h->dipE.empty() ? nullptr : h->d_dipM;
   p.dipE = (n - 1 < (int)h->dipE.size()) ? h->dipE[(size_t)(n - 1)] : 0.0;
   cudaError_t e = kbe::launch_build_props(h->mesh, hop_table(h), p, h->cfg.dt, nullptr, hk ? hk : h->hk,
-                                          Uk ? Uk : h->U, Vk ? Vk : h->V, h->stream);
+                                          Uk ? Uk : h->U, Vk ? Vk : h->V, h->stream, skip);
   if (e != cudaSuccess) return cuda_fail(h, e, "build_props");
   if (h->prof) h->stats.launches += 1;
   return KBE_OK;
 }
 
-kbe_status update(kbe_handle *h, int n, double theta) {
+kbe_status update(kbe_handle *h, int n, double theta, const int *skip = nullptr,
+                  unsigned long long *maxdiff = nullptr) {
   double2 *prev = frow(h, n - 1);
   double2 *row = frow(h, n);
   cudaError_t e = kbe::launch_update_row(h->mesh, n, h->cfg.dt, theta, h->hk, h->U, h->V, prev, h->Ip,
-                                         h->Ic, row, h->stream);
+                                         h->Ic, row, h->stream, skip, maxdiff);
   if (e != cudaSuccess) return cuda_fail(h, e, "update_row");
   if (h->prof) h->stats.launches += 2;
-  return publish(h, n);
+  return publish(h, n, skip);
 }
 
-kbe_status density(kbe_handle *h, int n, double2 *out) {
-  cudaError_t e = kbe::launch_local_density(h->mesh, frow(h, n) + (size_t)n * 2 * h->blk, out, h->stream);
+kbe_status density(kbe_handle *h, int n, double2 *out, const int *skip = nullptr) {
+  cudaError_t e = kbe::launch_local_density(h->mesh, frow(h, n) + (size_t)n * 2 * h->blk, out, h->stream, skip);
   if (e != cudaSuccess) return cuda_fail(h, e, "local_density");
   if (h->prof) h->stats.launches += 1;
   return KBE_OK;
@@ -278,11 +283,27 @@ kbe_status one_step(kbe_handle *h) {
   // predictor: density extrapolated to the midpoint, Ibar = I_{n-1}
   if ((s = build_props(h, n, r1, r2, n >= 2 ? 1.5 : 1.0, n >= 2 ? -0.5 : 0.0)) != KBE_OK) return s;
   if ((s = update(h, n, 0.0)) != KBE_OK) return s;
+  // correctors: a fixed count, or (corr_tol > 0) up to n_corr passes until the
+  // largest change of the G^< row is <= corr_tol (Algorithm 1's break), decided
+  // on the device: once converged, the remaining passes' kernels return at once
+  const bool tol = h->cfg.corr_tol > 0.0;
+  const int *skip = tol ? h->d_skip : nullptr;
+  unsigned long long *md = tol ? h->d_maxdiff : nullptr;
+  if (tol) {
+    cudaError_t e = cudaMemsetAsync(h->d_skip, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_maxdiff, 0, sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_iters + n, 0, sizeof(int), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "corrector flags");
+  }
   for (int c = 0; c < h->cfg.n_corr; ++c) {
-    if ((s = density(h, n, rcur)) != KBE_OK) return s;
-    if ((s = build_props(h, n, r1, rcur, 0.5, 0.5)) != KBE_OK) return s;
-    if ((s = evaluate_row(h, n)) != KBE_OK) return s;
-    if ((s = update(h, n, 0.5)) != KBE_OK) return s;
+    if ((s = density(h, n, rcur, skip)) != KBE_OK) return s;
+    if ((s = build_props(h, n, r1, rcur, 0.5, 0.5, nullptr, nullptr, nullptr, skip)) != KBE_OK) return s;
+    if ((s = evaluate_row(h, n, skip)) != KBE_OK) return s;
+    if ((s = update(h, n, 0.5, skip, md)) != KBE_OK) return s;
+    if (tol) {
+      cudaError_t e = kbe::launch_corr_check(h->d_maxdiff, h->cfg.corr_tol, h->d_skip, h->d_iters + n, h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e, "corrector check");
+    }
   }
   if ((s = evaluate_row(h, n)) != KBE_OK) return s;
   if ((s = density(h, n, h->rho + (size_t)n * nb2)) != KBE_OK) return s;
@@ -394,14 +415,13 @@ double adj_sweep_flops(const kbe_handle *h, int n) {
 // Step n in reverse: recompute the step from the history (rows < n) and
 // I_{n-1}, then transpose its operations, last first. lamIcur is the adjoint
 // of I_n (complete), lamIprev accumulates that of I_{n-1}.
-kbe_status backward_step(kbe_handle *h, const AdjPtrs &P, int n, double2 *lamIcur, double2 *lamIprev) {
+kbe_status backward_step(kbe_handle *h, const AdjPtrs &P, int n, int nc, double2 *lamIcur, double2 *lamIprev) {
   const Mesh &m = h->mesh;
   const size_t blk = h->blk, nb2 = (size_t)h->nb2;
   const double dt = h->cfg.dt;
   const double *Ul = h->Useq.size() == 1 ? nullptr : h->d_U;   // as the forward's Sigma rows
   const double Un = U_at(h, n), Up = U_at(h, n - 1);
-  const int nc = h->cfg.n_corr;
-  cudaStream_t st = h->stream;
+  cudaStream_t st = h->stream;   // nc: the corrector passes the forward ran at step n
   const double *v = h->v.data();
   double2 *Hd = (double2 *)h->H;
   double2 *histN = Hd + tri(n, 0) * 2 * blk;
@@ -555,6 +575,7 @@ static size_t handle_bytes(const kbe_config *cfg) {
   b += 3 * blk * sizeof(double2);                                 // U, V, h
   b += (T + 2) * nb2 * sizeof(double2) + (T + 1) * (6 + (size_t)m.nk * cfg->nb) * sizeof(double);
   b += (T + 1) * sizeof(double) + 64;
+  b += (T + 1) * sizeof(int) + 16;                                // corrector counts and flags
   return b;
 }
 
@@ -573,6 +594,8 @@ kbe_status kbe_create(const kbe_config *cfg, void *stream, kbe_handle **out) {
   if (!std::isfinite(cfg->beta) || !std::isfinite(cfg->mu)) return fail(nullptr, KBE_ERR_ARG, "kbe_create: beta/mu not finite");
   if (!kbe::precision_supported(cfg->precision)) return fail(nullptr, KBE_ERR_UNSUPPORTED, "kbe_create: unknown precision");
   if (cfg->n_corr < 0 || cfg->n_corr > 64) return fail(nullptr, KBE_ERR_ARG, "kbe_create: n_corr out of range");
+  if (!std::isfinite(cfg->corr_tol) || cfg->corr_tol < 0.0)
+    return fail(nullptr, KBE_ERR_ARG, "kbe_create: corr_tol must be finite and >= 0");
 
   kbe_handle *h = new kbe_handle();
   h->cfg = *cfg;
@@ -606,6 +629,9 @@ kbe_status kbe_create(const kbe_config *cfg, void *stream, kbe_handle **out) {
   if (e == cudaSuccess) e = dalloc(h, &h->nkb, (T + 1) * h->mesh.nk * cfg->nb);
   if (e == cudaSuccess) e = dalloc(h, &h->status, 1);
   if (e == cudaSuccess) e = dalloc(h, &h->d_U, T + 1);
+  if (e == cudaSuccess) e = dalloc(h, &h->d_skip, 1);
+  if (e == cudaSuccess) e = dalloc(h, &h->d_maxdiff, 1);
+  if (e == cudaSuccess) e = dalloc(h, &h->d_iters, T + 1);
   if (e != cudaSuccess) {
     std::string msg = std::string("kbe_create: device allocation failed (") + cudaGetErrorString(e) + ")";
     cudaGetLastError();
@@ -615,6 +641,7 @@ kbe_status kbe_create(const kbe_config *cfg, void *stream, kbe_handle **out) {
   }
   cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
   cudaMemsetAsync(h->rho, 0, sizeof(double2) * (T + 2) * h->nb2, h->stream);
+  cudaMemsetAsync(h->d_iters, 0, sizeof(int) * (T + 1), h->stream);
   *out = h;
   return KBE_OK;
 }
@@ -850,6 +877,21 @@ kbe_status kbe_get_row(kbe_handle *h, int i, int which, double *out) {
   return KBE_OK;
 }
 
+kbe_status kbe_corrector_iterations(kbe_handle *h, int *out) {
+  if (!h || !out) return KBE_ERR_ARG;
+  if (h->n < 0) return fail(h, KBE_ERR_STATE, "corrector_iterations: call kbe_reset first");
+  const size_t rows = (size_t)h->n + 1;
+  if (h->cfg.corr_tol > 0.0) {
+    cudaError_t e = cudaMemcpyAsync(out, h->d_iters, sizeof(int) * rows, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "corrector_iterations copy");
+  } else {
+    for (size_t i = 0; i < rows; ++i) out[i] = i == 0 ? 0 : h->cfg.n_corr;
+  }
+  out[0] = 0;
+  return KBE_OK;
+}
+
 kbe_status kbe_profile_enable(kbe_handle *h, int enable) {
   if (!h) return KBE_ERR_ARG;
   cudaStreamSynchronize(h->stream);
@@ -916,6 +958,7 @@ std::vector<Region> state_regions(kbe_handle *h) {
   r.push_back({h->rho, h->rho, (size_t)(n + 1) * h->nb2 * sizeof(double2)});
   r.push_back({h->obs, h->obs, (size_t)(n + 1) * 6 * sizeof(double)});
   r.push_back({h->nkb, h->nkb, (size_t)(n + 1) * h->mesh.nk * h->cfg.nb * sizeof(double)});
+  r.push_back({h->d_iters, h->d_iters, (size_t)(n + 1) * sizeof(int)});
   return r;
 }
 }  // namespace
@@ -935,7 +978,7 @@ kbe_status kbe_checkpoint_save(kbe_handle *h, void *host, size_t bytes) {
   if (st != KBE_OK) return st;
   CkptHeader hd{};
   memcpy(hd.magic, "KBECKPT", 8);
-  hd.version = 1;
+  hd.version = 2;
   hd.nb = h->cfg.nb;
   hd.dim = h->cfg.dim;
   hd.L0 = h->cfg.L[0];
@@ -960,7 +1003,7 @@ kbe_status kbe_checkpoint_load(kbe_handle *h, const void *host, size_t bytes) {
   if (!h || !host || bytes < sizeof(CkptHeader)) return KBE_ERR_ARG;
   CkptHeader hd;
   memcpy(&hd, host, sizeof hd);
-  if (memcmp(hd.magic, "KBECKPT", 8) != 0 || hd.version != 1 || hd.nb != h->cfg.nb ||
+  if (memcmp(hd.magic, "KBECKPT", 8) != 0 || hd.version != 2 || hd.nb != h->cfg.nb ||
       hd.dim != h->cfg.dim || hd.L0 != h->cfg.L[0] || hd.L1 != h->cfg.L[1] ||
       hd.nt_max != h->cfg.nt_max || hd.precision != h->cfg.precision || hd.n < 0 || hd.n > h->cfg.nt_max)
     return fail(h, KBE_ERR_ARG, "checkpoint_load: checkpoint does not match this handle's configuration");
@@ -1046,9 +1089,15 @@ kbe_status kbe_backward(kbe_handle *h, const double *dL_dn, double *dL_dA, doubl
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(P.lamH + tri(N, N) * 2 * blk, seed.data(), blk * sizeof(double2), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "backward setup");
+  std::vector<int> iters((size_t)N + 1, h->cfg.n_corr);
+  if (h->cfg.corr_tol > 0.0) {   // replay the passes each step ran
+    e = cudaMemcpyAsync(iters.data(), h->d_iters, sizeof(int) * iters.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "backward corrector counts");
+  }
   double2 *lamIcur = P.lamIa, *lamIprev = P.lamIb;
   for (int n = N; n >= 1; --n) {
-    s = backward_step(h, P, n, lamIcur, lamIprev);
+    s = backward_step(h, P, n, iters[(size_t)n], lamIcur, lamIprev);
     if (s != KBE_OK) return s;
     std::swap(lamIcur, lamIprev);
     e = cudaMemsetAsync(lamIprev, 0, (size_t)n * 2 * blk * sizeof(double2), st);

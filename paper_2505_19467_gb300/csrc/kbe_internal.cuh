@@ -80,13 +80,17 @@ enum : int { kDevOk = 0, kDevNonFinite = 1, kDevEigNoConv = 2, kDevAdjUnsupporte
 // out[arr] = scale * DFT_sign(in[arr]) for narr arrays of n_k points (added
 // to out when accumulate)
 cudaError_t launch_dft_rows(const double2 *in, double2 *out, long narr, int L0, int L1, int sign,
-                            double scale, cudaStream_t st, bool accumulate = false);
+                            double scale, cudaStream_t st, bool accumulate = false,
+                            const int *skip = nullptr);
+// skip (device int, may be NULL): when it holds non-zero the launch does
+// nothing (the corrector passes of a converged step, Algorithm 1's break).
 cudaError_t launch_sigma_products(const Mesh &m, const double *v, int n, double Un,
                                   const double *Ul_dev, const double2 *GR, double2 *SR,
-                                  cudaStream_t st);
+                                  cudaStream_t st, const int *skip = nullptr);
 size_t sigma_workspace_bytes(const Mesh &m, int n);
 cudaError_t sigma_row(const Mesh &m, const double *v_host, int n, double Un, const double *Ul_dev,
-                      const double2 *Grow, double2 *Sig, double2 *work, cudaStream_t st);
+                      const double2 *Grow, double2 *Sig, double2 *work, cudaStream_t st,
+                      const int *skip = nullptr);
 
 // a2 collision row. H is the history triangle in the precision's storage
 // (double2 / float4 hi-lo pairs / float2), each block holding G^< and
@@ -98,9 +102,10 @@ size_t history_elem_bytes(int prec);
 size_t sweep_workspace_bytes(const Mesh &m, int n, int prec);
 int sweep_splits(const Mesh &m, int n);   // CTAs sharing one output's l range
 cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t nblocks, size_t blk,
-                        cudaStream_t st);
+                        cudaStream_t st, const int *skip = nullptr);
 cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const void *H,
-                         const double2 *Sig, double2 *I, void *work, cudaStream_t st);
+                         const double2 *Sig, double2 *I, void *work, cudaStream_t st,
+                         const int *skip = nullptr);
 
 // a3 propagators / initial state / density
 struct HopTable {
@@ -112,7 +117,7 @@ struct HopTable {
 cudaError_t launch_init_state(const Mesh &m, const HopTable &hop, double beta, double mu,
                               double2 *H00, int *status, cudaStream_t st);
 cudaError_t launch_local_density(const Mesh &m, const double2 *Gdiag, double2 *rho_out,
-                                 cudaStream_t st);
+                                 cudaStream_t st, const int *skip = nullptr);
 struct PropParams {
   double A;                     // Peierls sample for this step
   const double2 *rho_a;         // device nb*nb, mid density = ca*rho_a + cb*rho_b
@@ -129,12 +134,20 @@ struct PropParams {
 // h_out (may be NULL) receives h. All per-k [a][b][k].
 cudaError_t launch_build_props(const Mesh &m, const HopTable &hop, const PropParams &p, double dt,
                                const double2 *h_in, double2 *h_out, double2 *U, double2 *V,
-                               cudaStream_t st);
+                               cudaStream_t st, const int *skip = nullptr);
 
-// a4 update: rows j < n and the time diagonal (h, U, V of the step)
+// a4 update: rows j < n and the time diagonal (h, U, V of the step).
+// maxdiff (may be NULL): max over the new row of |G^< - its previous value in
+// out| is folded in (atomicMax on the bits of a non-negative double).
 cudaError_t launch_update_row(const Mesh &m, int n, double dt, double theta, const double2 *h,
                               const double2 *U, const double2 *V, const double2 *Gprev,
                               const double2 *Iprev, const double2 *Icur, double2 *out,
+                              cudaStream_t st, const int *skip = nullptr,
+                              unsigned long long *maxdiff = nullptr);
+// Algorithm 1's convergence test after a corrector pass (one thread): unless
+// skip is set, count the pass in *iters, set skip when *maxdiff <= tol, and
+// clear *maxdiff for the next pass.
+cudaError_t launch_corr_check(unsigned long long *maxdiff, double tol, int *skip, int *iters,
                               cudaStream_t st);
 
 // a5 observables

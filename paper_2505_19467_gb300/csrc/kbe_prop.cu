@@ -122,7 +122,9 @@ __global__ void __launch_bounds__(256) build_props_kernel(Mesh m, HopTable hop, 
                                                           const double2 *__restrict__ hin, double dt,
                                                           double2 *__restrict__ hout,
                                                           double2 *__restrict__ U,
-                                                          double2 *__restrict__ V, int kpc) {
+                                                          double2 *__restrict__ V, int kpc,
+                                                          const int *__restrict__ skip) {
+  if (skip && *skip) return;
   using G = MatGroup<NB>;
   const int span = kpc * G::E;
   double2 *sh[4] = {kbe_dsm, kbe_dsm + span, kbe_dsm + 2 * span, kbe_dsm + 3 * span};
@@ -182,7 +184,10 @@ __global__ void __launch_bounds__(256) update_diag_kernel(int n, int nk, double 
                                                           const double2 *__restrict__ Gprev,
                                                           const double2 *__restrict__ Ip,
                                                           const double2 *__restrict__ Ic,
-                                                          double2 *__restrict__ out, int kpc) {
+                                                          double2 *__restrict__ out, int kpc,
+                                                          const int *__restrict__ skip,
+                                                          unsigned long long *maxdiff) {
+  if (skip && *skip) return;
   using G = MatGroup<NB>;
   const int span = kpc * G::E;
   double2 *H = kbe_dsm, *Qs = kbe_dsm + span, *T = kbe_dsm + 2 * span, *P = kbe_dsm + 3 * span,
@@ -244,6 +249,10 @@ __global__ void __launch_bounds__(256) update_diag_kernel(int n, int nk, double 
   const double2 gg = c_sub(g.mm(P, T), c_i(x));
   if (active) {
     double2 *ol = out + (size_t)n * 2 * blk + (size_t)g.e * nk + k;
+    if (maxdiff) {
+      const double2 d = c_sub(gg, ol[0]);
+      atomicMax(maxdiff, (unsigned long long)__double_as_longlong(sqrt(d.x * d.x + d.y * d.y)));
+    }
     ol[0] = gg;
     ol[blk] = (g.a == g.b) ? make_double2(gg.x, gg.y - 1.0) : gg;
   }
@@ -285,7 +294,9 @@ __global__ void init_state_kernel(Mesh m, HopTable hop, double beta, double mu, 
 }
 
 // rho_loc_ab = (1/n_k) sum_k (-i) G^<_ab(k; n, n); one CTA, a warp per element
-__global__ void local_density_kernel(int nb, int nk, const double2 *__restrict__ G, double2 *out) {
+__global__ void local_density_kernel(int nb, int nk, const double2 *__restrict__ G, double2 *out,
+                                     const int *__restrict__ skip) {
+  if (skip && *skip) return;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
   for (int e = warp; e < nb * nb; e += nw) {
     double sr = 0.0, si = 0.0;
@@ -308,29 +319,51 @@ template <int NB>
 __global__ void update_rows_kernel(int n, int nk, double theta, const double2 *__restrict__ U,
                                    const double2 *__restrict__ V, const double2 *__restrict__ Gprev,
                                    const double2 *__restrict__ Ip, const double2 *__restrict__ Ic,
-                                   double2 *__restrict__ out) {
+                                   double2 *__restrict__ out, const int *__restrict__ skip,
+                                   unsigned long long *maxdiff) {
+  if (skip && *skip) return;
   const size_t blk = (size_t)NB * NB * nk;
   const size_t total = (size_t)n * 2 * blk;
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  const int k = (int)(idx % nk);
-  size_t t = idx / nk;
-  const int b = (int)(t % NB);
-  t /= NB;
-  const int a = (int)(t % NB);
-  t /= NB;   // t = j * 2 + x
-  const size_t base = t * blk;
-  double2 acc = make_double2(0, 0);
+  double dmax = 0.0;
+  if (idx < total) {
+    const int k = (int)(idx % nk);
+    size_t t = idx / nk;
+    const int b = (int)(t % NB);
+    t /= NB;
+    const int a = (int)(t % NB);
+    t /= NB;   // t = j * 2 + x
+    const size_t base = t * blk;
+    double2 acc = make_double2(0, 0);
 #pragma unroll
-  for (int c = 0; c < NB; ++c) {
-    const size_t oc = (size_t)(c * NB + b) * nk + k;
-    const size_t ou = (size_t)(a * NB + c) * nk + k;
-    double2 ib = c_scale(1.0 - theta, Ip[base + oc]);
-    if (theta != 0.0) ib = c_fma(make_double2(theta, 0.0), Ic[base + oc], ib);
-    acc = c_fma(U[ou], Gprev[base + oc], acc);
-    acc = c_fma(V[ou], ib, acc);
+    for (int c = 0; c < NB; ++c) {
+      const size_t oc = (size_t)(c * NB + b) * nk + k;
+      const size_t ou = (size_t)(a * NB + c) * nk + k;
+      double2 ib = c_scale(1.0 - theta, Ip[base + oc]);
+      if (theta != 0.0) ib = c_fma(make_double2(theta, 0.0), Ic[base + oc], ib);
+      acc = c_fma(U[ou], Gprev[base + oc], acc);
+      acc = c_fma(V[ou], ib, acc);
+    }
+    double2 *o = out + base + (size_t)(a * NB + b) * nk + k;
+    if (maxdiff && (t & 1) == 0) {   // G^< entries
+      const double2 d = c_sub(acc, *o);
+      dmax = sqrt(d.x * d.x + d.y * d.y);
+    }
+    *o = acc;
   }
-  out[base + (size_t)(a * NB + b) * nk + k] = acc;
+  if (maxdiff) {   // every lane reaches here (blockDim is a multiple of 32)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
+    if ((threadIdx.x & 31) == 0 && dmax > 0.0)
+      atomicMax(maxdiff, (unsigned long long)__double_as_longlong(dmax));
+  }
+}
+
+__global__ void corr_check_kernel(unsigned long long *maxdiff, double tol, int *skip, int *iters) {
+  if (*skip) return;
+  *iters += 1;
+  if (__longlong_as_double((long long)*maxdiff) <= tol) *skip = 1;
+  *maxdiff = 0ull;
 }
 
 // equal-time observables of row n; one CTA
@@ -408,35 +441,43 @@ cudaError_t launch_init_state(const Mesh &m, const HopTable &hop, double beta, d
 }
 
 cudaError_t launch_local_density(const Mesh &m, const double2 *Gdiag, double2 *rho_out,
-                                 cudaStream_t st) {
-  local_density_kernel<<<1, 256, 0, st>>>(m.nb, m.nk, Gdiag, rho_out);
+                                 cudaStream_t st, const int *skip) {
+  local_density_kernel<<<1, 256, 0, st>>>(m.nb, m.nk, Gdiag, rho_out, skip);
   return cudaGetLastError();
 }
 
 cudaError_t launch_build_props(const Mesh &m, const HopTable &hop, const PropParams &p, double dt,
                                const double2 *h_in, double2 *h_out, double2 *U, double2 *V,
-                               cudaStream_t st) {
+                               cudaStream_t st, const int *skip) {
   KBE_NB_SWITCH(m.nb, (build_props_kernel<NB><<<matgroup_blocks<NB>(m.nk), matgroup_threads<NB>(m.nk),
                                                  matgroup_smem<NB>(m.nk, 4), st>>>(
-                          m, hop, p, h_in, dt, h_out, U, V, matgroup_kpc<NB>(m.nk))));
+                          m, hop, p, h_in, dt, h_out, U, V, matgroup_kpc<NB>(m.nk), skip)));
   return cudaGetLastError();
 }
 
 cudaError_t launch_update_row(const Mesh &m, int n, double dt, double theta, const double2 *h,
                               const double2 *U, const double2 *V, const double2 *Gprev,
                               const double2 *Iprev, const double2 *Icur, double2 *out,
-                              cudaStream_t st) {
+                              cudaStream_t st, const int *skip, unsigned long long *maxdiff) {
   const size_t blk = (size_t)m.nb * m.nb * m.nk;
   const size_t total = (size_t)n * 2 * blk;
   const int threads = 256;
   const unsigned blocks = (unsigned)((total + threads - 1) / threads);
   const double2 *ic = (theta != 0.0) ? Icur : Iprev;
-  KBE_NB_SWITCH(m.nb, (update_rows_kernel<NB><<<blocks, threads, 0, st>>>(n, m.nk, theta, U, V, Gprev, Iprev, ic, out)));
+  KBE_NB_SWITCH(m.nb, (update_rows_kernel<NB><<<blocks, threads, 0, st>>>(n, m.nk, theta, U, V, Gprev, Iprev, ic, out,
+                                                                           skip, maxdiff)));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   KBE_NB_SWITCH(m.nb, (update_diag_kernel<NB><<<matgroup_blocks<NB>(m.nk), matgroup_threads<NB>(m.nk),
                                                  matgroup_smem<NB>(m.nk, 5), st>>>(
-                          n, m.nk, dt, theta, h, Gprev, Iprev, ic, out, matgroup_kpc<NB>(m.nk))));
+                          n, m.nk, dt, theta, h, Gprev, Iprev, ic, out, matgroup_kpc<NB>(m.nk), skip,
+                          maxdiff)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_corr_check(unsigned long long *maxdiff, double tol, int *skip, int *iters,
+                              cudaStream_t st) {
+  corr_check_kernel<<<1, 1, 0, st>>>(maxdiff, tol, skip, iters);
   return cudaGetLastError();
 }
 

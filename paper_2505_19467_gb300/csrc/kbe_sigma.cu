@@ -91,7 +91,9 @@ __device__ void dft_axis(double2 *x, double2 *tmp, int L, int stride, int count,
 }
 
 __global__ void dft_rows_kernel(const double2 *__restrict__ in, double2 *__restrict__ out,
-                                long narr, int L0, int L1, int sign, double scale, int accumulate) {
+                                long narr, int L0, int L1, int sign, double scale, int accumulate,
+                                const int *__restrict__ skip) {
+  if (skip && *skip) return;
   extern __shared__ double2 sm[];
   const int nk = L0 * L1;
   double2 *x = sm;
@@ -138,7 +140,8 @@ template <int NB>
 __global__ void __launch_bounds__(128) sigma_products_kernel(const double2 *__restrict__ GR,
                                                              double2 *__restrict__ SR, int n, int nk,
                                                              double Un, const double *__restrict__ Ul,
-                                                             VMat vm) {
+                                                             VMat vm, const int *__restrict__ skip) {
+  if (skip && *skip) return;
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long total = (long)(n + 1) * NB * nk;
   if (idx >= total) return;
@@ -187,18 +190,18 @@ __global__ void __launch_bounds__(128) sigma_products_kernel(const double2 *__re
 
 template <int NB>
 cudaError_t products_nb(const Mesh &m, const VMat &vm, int n, double Un, const double *Ul,
-                        const double2 *GR, double2 *SR, cudaStream_t st) {
+                        const double2 *GR, double2 *SR, cudaStream_t st, const int *skip) {
   const long total = (long)(n + 1) * NB * m.nk;
   const int threads = 128;
   const long blocks = (total + threads - 1) / threads;
-  sigma_products_kernel<NB><<<(unsigned)blocks, threads, 0, st>>>(GR, SR, n, m.nk, Un, Ul, vm);
+  sigma_products_kernel<NB><<<(unsigned)blocks, threads, 0, st>>>(GR, SR, n, m.nk, Un, Ul, vm, skip);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_dft_rows(const double2 *in, double2 *out, long narr, int L0, int L1, int sign,
-                            double scale, cudaStream_t st, bool accumulate) {
+                            double scale, cudaStream_t st, bool accumulate, const int *skip) {
   if (narr <= 0) return cudaSuccess;
   const int nk = L0 * L1;
   const size_t smem = sizeof(double2) * (2 * (size_t)nk + L0 + L1);
@@ -212,25 +215,25 @@ cudaError_t launch_dft_rows(const double2 *in, double2 *out, long narr, int L0, 
   int threads = nk >= 256 ? 256 : ((nk + 31) / 32) * 32;
   long blocks = narr < 152L * 8 ? narr : 152L * 8;
   dft_rows_kernel<<<(unsigned)blocks, threads, smem, st>>>(in, out, narr, L0, L1, sign, scale,
-                                                            accumulate ? 1 : 0);
+                                                            accumulate ? 1 : 0, skip);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sigma_products(const Mesh &m, const double *v, int n, double Un,
                                   const double *Ul_dev, const double2 *GR, double2 *SR,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, const int *skip) {
   VMat vm;
   for (int i = 0; i < kMaxNb * kMaxNb; ++i) vm.v[i] = 0.0;
   for (int i = 0; i < m.nb * m.nb; ++i) vm.v[i] = v[i];
   switch (m.nb) {
-    case 1: return products_nb<1>(m, vm, n, Un, Ul_dev, GR, SR, st);
-    case 2: return products_nb<2>(m, vm, n, Un, Ul_dev, GR, SR, st);
-    case 3: return products_nb<3>(m, vm, n, Un, Ul_dev, GR, SR, st);
-    case 4: return products_nb<4>(m, vm, n, Un, Ul_dev, GR, SR, st);
-    case 6: return products_nb<6>(m, vm, n, Un, Ul_dev, GR, SR, st);
-    case 8: return products_nb<8>(m, vm, n, Un, Ul_dev, GR, SR, st);
-    case 12: return products_nb<12>(m, vm, n, Un, Ul_dev, GR, SR, st);
-    case 16: return products_nb<16>(m, vm, n, Un, Ul_dev, GR, SR, st);
+    case 1: return products_nb<1>(m, vm, n, Un, Ul_dev, GR, SR, st, skip);
+    case 2: return products_nb<2>(m, vm, n, Un, Ul_dev, GR, SR, st, skip);
+    case 3: return products_nb<3>(m, vm, n, Un, Ul_dev, GR, SR, st, skip);
+    case 4: return products_nb<4>(m, vm, n, Un, Ul_dev, GR, SR, st, skip);
+    case 6: return products_nb<6>(m, vm, n, Un, Ul_dev, GR, SR, st, skip);
+    case 8: return products_nb<8>(m, vm, n, Un, Ul_dev, GR, SR, st, skip);
+    case 12: return products_nb<12>(m, vm, n, Un, Ul_dev, GR, SR, st, skip);
+    case 16: return products_nb<16>(m, vm, n, Un, Ul_dev, GR, SR, st, skip);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -241,16 +244,16 @@ size_t sigma_workspace_bytes(const Mesh &m, int n) {
 }
 
 cudaError_t sigma_row(const Mesh &m, const double *v_host, int n, double Un, const double *Ul_dev,
-                      const double2 *Grow, double2 *Sig, double2 *work, cudaStream_t st) {
+                      const double2 *Grow, double2 *Sig, double2 *work, cudaStream_t st, const int *skip) {
   const size_t blk = (size_t)m.nb * m.nb * m.nk;
   const long narr = (long)(n + 1) * 2 * m.nb * m.nb;
   double2 *GR = work;
   double2 *SR = work + (size_t)(n + 1) * 2 * blk;
-  cudaError_t e = launch_dft_rows(Grow, GR, narr, m.L0, m.L1, +1, 1.0 / m.nk, st);
+  cudaError_t e = launch_dft_rows(Grow, GR, narr, m.L0, m.L1, +1, 1.0 / m.nk, st, false, skip);
   if (e != cudaSuccess) return e;
-  e = launch_sigma_products(m, v_host, n, Un, Ul_dev, GR, SR, st);
+  e = launch_sigma_products(m, v_host, n, Un, Ul_dev, GR, SR, st, skip);
   if (e != cudaSuccess) return e;
-  return launch_dft_rows(SR, Sig, narr, m.L0, m.L1, -1, 1.0, st);
+  return launch_dft_rows(SR, Sig, narr, m.L0, m.L1, -1, 1.0, st, false, skip);
 }
 
 }  // namespace kbe

@@ -227,7 +227,8 @@ template <class P, int NB>
 __global__ void __launch_bounds__(256, P::kMinBlocks) sweep_kernel(const typename P::S *__restrict__ H,
                                                     const typename P::S *__restrict__ Cf,
                                                     double2 *__restrict__ out, int n, int nk,
-                                                    int lchunk) {
+                                                    int lchunk, const int *__restrict__ skip) {
+  if (skip && *skip) return;
   using S = typename P::S;
   const int j = blockIdx.y;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -268,7 +269,8 @@ __global__ void __launch_bounds__(256, P::kMinBlocks) sweep_kernel(const typenam
 
 // I = sum over the z partial rows (FP64)
 __global__ void reduce_partials_kernel(const double2 *__restrict__ part, double2 *__restrict__ I,
-                                       size_t count, int nz) {
+                                       size_t count, int nz, const int *__restrict__ skip) {
+  if (skip && *skip) return;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (size_t)gridDim.x * blockDim.x) {
     double2 s = part[i];
@@ -286,7 +288,8 @@ __device__ __forceinline__ float4 split_df(double2 x) {
 // nblocks blocks [2][nb][nb][nk] of (G^<, G^>) in FP64 -> (G^<, dG = G^< - G^>)
 // in the history storage (dG formed in FP64 before rounding)
 __global__ void pack_kernel(int prec, const double2 *__restrict__ src, void *__restrict__ dst,
-                            size_t nblocks, size_t blk) {
+                            size_t nblocks, size_t blk, const int *__restrict__ skip) {
+  if (skip && *skip) return;
   const size_t count = nblocks * blk;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (size_t)gridDim.x * blockDim.x) {
@@ -309,7 +312,8 @@ __global__ void pack_kernel(int prec, const double2 *__restrict__ src, void *__r
 
 // coefficient rows [l][3][a][c][k]: C1 = w^(n)_l (S^> - S^<), C2^< = dt S^<, C3 = dt S^> - C1
 __global__ void coef_kernel(int prec, const double2 *__restrict__ Sig, void *__restrict__ Cf, int n,
-                            int nk, int nb2, double dt) {
+                            int nk, int nb2, double dt, const int *__restrict__ skip) {
+  if (skip && *skip) return;
   const size_t blk = (size_t)nb2 * nk;
   const size_t total = (size_t)(n + 1) * blk;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -360,24 +364,24 @@ SweepShape sweep_shape(const Mesh &m, int n) {
 
 template <class P, int NB>
 cudaError_t sweep_nb(const Mesh &m, int n, const void *H, const void *Cf, double2 *I, double2 *part,
-                     cudaStream_t st) {
+                     cudaStream_t st, const int *skip) {
   const SweepShape sh = sweep_shape(m, n);
   double2 *out = sh.nz > 1 ? part : I;
   sweep_kernel<P, NB><<<sh.grid, sh.threads, 0, st>>>((const typename P::S *)H,
-                                                      (const typename P::S *)Cf, out, n, m.nk, sh.lchunk);
+                                                      (const typename P::S *)Cf, out, n, m.nk, sh.lchunk, skip);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || sh.nz == 1) return e;
   const size_t count = (size_t)(n + 1) * 2 * m.nb * m.nb * m.nk;
-  reduce_partials_kernel<<<grid_for(count), 256, 0, st>>>(part, I, count, sh.nz);
+  reduce_partials_kernel<<<grid_for(count), 256, 0, st>>>(part, I, count, sh.nz, skip);
   return cudaGetLastError();
 }
 
 template <int NB>
 cudaError_t sweep_prec(const Mesh &m, int n, int prec, const void *H, const void *Cf, double2 *I,
-                       double2 *part, cudaStream_t st) {
-  if (prec == KBE_PREC_FP64) return sweep_nb<ArithF64, NB>(m, n, H, Cf, I, part, st);
-  if (prec == KBE_PREC_DF64) return sweep_nb<ArithDF64, NB>(m, n, H, Cf, I, part, st);
-  return sweep_nb<ArithC64, NB>(m, n, H, Cf, I, part, st);
+                       double2 *part, cudaStream_t st, const int *skip) {
+  if (prec == KBE_PREC_FP64) return sweep_nb<ArithF64, NB>(m, n, H, Cf, I, part, st, skip);
+  if (prec == KBE_PREC_DF64) return sweep_nb<ArithDF64, NB>(m, n, H, Cf, I, part, st, skip);
+  return sweep_nb<ArithC64, NB>(m, n, H, Cf, I, part, st, skip);
 }
 
 }  // namespace
@@ -415,32 +419,32 @@ size_t sweep_workspace_bytes(const Mesh &m, int n, int prec) {
 int sweep_splits(const Mesh &m, int n) { return sweep_shape(m, n).nz; }
 
 cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t nblocks, size_t blk,
-                        cudaStream_t st) {
+                        cudaStream_t st, const int *skip) {
   if (nblocks == 0 || blk == 0) return cudaSuccess;
-  pack_kernel<<<grid_for(nblocks * blk), 256, 0, st>>>(prec, src, dst, nblocks, blk);
+  pack_kernel<<<grid_for(nblocks * blk), 256, 0, st>>>(prec, src, dst, nblocks, blk, skip);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const void *H,
-                         const double2 *Sig, double2 *I, void *work, cudaStream_t st) {
+                         const double2 *Sig, double2 *I, void *work, cudaStream_t st, const int *skip) {
   if (!precision_supported(precision)) return cudaErrorInvalidValue;
   const size_t blk = (size_t)m.nb * m.nb * m.nk;
   const size_t total = (size_t)(n + 1) * blk;
-  coef_kernel<<<grid_for(total), 256, 0, st>>>(precision, Sig, work, n, m.nk, m.nb * m.nb, dt);
+  coef_kernel<<<grid_for(total), 256, 0, st>>>(precision, Sig, work, n, m.nk, m.nb * m.nb, dt, skip);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   size_t coef = (size_t)(n + 1) * 3 * blk * history_elem_bytes(precision);
   coef = (coef + 255) / 256 * 256;
   double2 *part = (double2 *)((char *)work + coef);
   switch (m.nb) {
-    case 1: return sweep_prec<1>(m, n, precision, H, work, I, part, st);
-    case 2: return sweep_prec<2>(m, n, precision, H, work, I, part, st);
-    case 3: return sweep_prec<3>(m, n, precision, H, work, I, part, st);
-    case 4: return sweep_prec<4>(m, n, precision, H, work, I, part, st);
-    case 6: return sweep_prec<6>(m, n, precision, H, work, I, part, st);
-    case 8: return sweep_prec<8>(m, n, precision, H, work, I, part, st);
-    case 12: return sweep_prec<12>(m, n, precision, H, work, I, part, st);
-    case 16: return sweep_prec<16>(m, n, precision, H, work, I, part, st);
+    case 1: return sweep_prec<1>(m, n, precision, H, work, I, part, st, skip);
+    case 2: return sweep_prec<2>(m, n, precision, H, work, I, part, st, skip);
+    case 3: return sweep_prec<3>(m, n, precision, H, work, I, part, st, skip);
+    case 4: return sweep_prec<4>(m, n, precision, H, work, I, part, st, skip);
+    case 6: return sweep_prec<6>(m, n, precision, H, work, I, part, st, skip);
+    case 8: return sweep_prec<8>(m, n, precision, H, work, I, part, st, skip);
+    case 12: return sweep_prec<12>(m, n, precision, H, work, I, part, st, skip);
+    case 16: return sweep_prec<16>(m, n, precision, H, work, I, part, st, skip);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -405,3 +405,39 @@ def test_exact_diagonalisation_error_scales_as_U_cubed():
         assert np.abs(ed - ed[0]).max() > 20 * errs[-1]    # the dynamics is resolved
     r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
     assert 7.0 < r1 < 9.5 and 7.0 < r2 < 9.5, errs
+
+
+def test_corrector_tolerance_limits_of_algorithm_1():
+    """Algorithm 1's corrector loop with its epsilon: a tolerance no pass can meet
+    runs all n_corr passes and reproduces the fixed-count run exactly; one every
+    pass meets stops after the first and reproduces n_corr = 1 exactly."""
+    import dataclasses
+    s = ki.config("c1", nt=8)
+    fixed = oracle.Oracle(dataclasses.replace(s, n_corr=3))
+    fixed.step(8)
+    tiny = oracle.Oracle(dataclasses.replace(s, n_corr=3, corr_tol=1e-300))
+    tiny.step(8)
+    assert tiny.iterations().tolist() == [0] + [3] * 8
+    one = oracle.Oracle(dataclasses.replace(s, n_corr=1))
+    one.step(8)
+    huge = oracle.Oracle(dataclasses.replace(s, n_corr=3, corr_tol=1e30))
+    huge.step(8)
+    assert huge.iterations().tolist() == [0] + [1] * 8
+    for i in (1, 4, 8):
+        for x in (0, 1):
+            assert np.array_equal(tiny.row(i, x), fixed.row(i, x))
+            assert np.array_equal(huge.row(i, x), one.row(i, x))
+
+
+def test_corrector_tolerance_counts_follow_the_change():
+    """with a moderate epsilon the number of passes varies from step to step, and
+    tightening epsilon never removes a pass"""
+    import dataclasses
+    s = ki.config("c1", nt=24)
+    runs = []
+    for tol in (2e-10, 1.19e-10, 1e-12):
+        o = oracle.Oracle(dataclasses.replace(s, n_corr=4, corr_tol=tol))
+        o.step(24)
+        runs.append(o.iterations())
+    assert set(runs[1][1:].tolist()) == {3, 4}
+    assert np.all(runs[0] <= runs[1]) and np.all(runs[1] <= runs[2])

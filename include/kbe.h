@@ -86,7 +86,18 @@ typedef struct kbe_config {
                     * once max_{j,k,a,b} |G^<(t_n,t_j) - previous pass| <=        *
                     * corr_tol (decided on the device, no host round trip);       *
                     * 0: always n_corr passes                                     */
+  int quadrature;  /* memory-integral weights of Eq. 6: KBE_QUAD_TRAPEZOID (the     *
+                    * paper's second-order rule) or KBE_QUAD_GREGORY                */
 } kbe_config;
+
+/* Quadrature of the collision integrals over [0, t_m] (Eq. 6). Gregory: the
+ * fourth-order rule with end weights 3/8, 7/6, 23/24 (in units of dt) at both
+ * ends for m >= 5, and for m <= 4 the closed Newton-Cotes rule of the whole
+ * interval (trapezoid, Simpson, Simpson 3/8, Boole). */
+enum {
+  KBE_QUAD_TRAPEZOID = 0,
+  KBE_QUAD_GREGORY = 1
+};
 
 typedef struct kbe_handle kbe_handle;
 
@@ -306,6 +317,11 @@ size_t kbe_op_collision_row_workspace(const kbe_mesh *m, int n, int precision);
 kbe_status kbe_op_collision_row(const kbe_mesh *m, int n, double dt, int precision,
                                 const void *H_dev, const void *Sigma_dev, void *I_dev,
                                 void *work_dev, size_t work_bytes, void *stream);
+
+/* kbe_op_collision_row with the weights of `quadrature` (KBE_QUAD_*). */
+kbe_status kbe_op_collision_row_quad(const kbe_mesh *m, int n, double dt, int precision, int quadrature,
+                                     const void *H_dev, const void *Sigma_dev, void *I_dev,
+                                     void *work_dev, size_t work_bytes, void *stream);
 
 /* (a3) Step propagators of a Hermitian h(k) (device [nb][nb][nk] c128):
  * U = e^{-i dt h}, V = (U - 1) h^{-1} (= -i dt on the null space of h), each

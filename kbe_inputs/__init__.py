@@ -61,6 +61,7 @@ class System:
     dipole_E: Optional[np.ndarray] = None   # float64 [nt] dipole field samples (Eq. 4), or None
     dipole_M: Optional[np.ndarray] = None   # complex128 [nb, nb] Hermitian dipole coupling
     corr_tol: float = 0.0         # Algorithm 1's epsilon (0: always n_corr corrector passes)
+    quadrature: int = 0           # collision-integral weights: 0 trapezoid, 1 Gregory
 
     @property
     def nk(self) -> int:

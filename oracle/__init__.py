@@ -15,8 +15,8 @@ from . import gradient
 PINS = {
     "sigma_pair": "literal Eq. 7 triple sum (N_b=2 bar form, general v); ED O(U^2)",
     "sigma_pair_literal": "Eq. 7 as printed (bar convention) on random G",
-    "collision_row": "analytic integrals of exponentials (trapezoid error O(dt^2)); "
-                     "I^>(n,n) = I^<(n,n); number conservation",
+    "collision_row": "analytic integrals of exponentials (trapezoid error O(dt^2); Gregory "
+                     "O(dt^4), exact for cubics); I^>(n,n) = I^<(n,n); number conservation",
     "propagators": "unitarity, closed form at U = 0, h V = U - 1",
     "update_row": "U = 0 closed form (driven and undriven)",
     "Oracle.step": "U = 0 closed form; particle number; energy drift O(dt^2); "

@@ -307,6 +307,25 @@ static double trap_w(int m, int l, double dt) {
   return w;
 }
 
+/* Weight of node l for the integral over [0, t_m] with quadrature quad:
+ * 0 the composite trapezoid rule; 1 the fourth-order Gregory rule (end
+ * corrections 3/8, 7/6, 23/24 of the trapezoid's unit interior weight) when
+ * m >= 5, and for 1 <= m <= 4 the closed Newton-Cotes rule over all m + 1
+ * nodes (trapezoid, Simpson 1/3, Simpson 3/8, Boole). Zero for m = 0. */
+static double quad_w(int quad, int m, int l, double dt) {
+  static const double newton_cotes[5][5] = {
+      {0.0},
+      {1.0 / 2, 1.0 / 2},
+      {1.0 / 3, 4.0 / 3, 1.0 / 3},
+      {3.0 / 8, 9.0 / 8, 9.0 / 8, 3.0 / 8},
+      {14.0 / 45, 64.0 / 45, 24.0 / 45, 64.0 / 45, 14.0 / 45}};
+  static const double gregory_end[3] = {3.0 / 8, 7.0 / 6, 23.0 / 24};
+  if (quad == 0) return trap_w(m, l, dt);
+  if (m <= 4) return dt * newton_cotes[m][l];
+  int d = l <= m - l ? l : m - l; /* distance to the nearer end */
+  return dt * (d < 3 ? gregory_end[d] : 1.0);
+}
+
 /* block G^x(l, j) at one k for any l, j, from the lower triangle H */
 static void fetch(int nb, int nk, const cplx *H, int l, int j, int k, cplx *out) {
   size_t blk = (size_t)nk * nb * nb;
@@ -325,8 +344,8 @@ static void fetch(int nb, int nk, const cplx *H, int l, int j, int k, cplx *out)
  * + sum_{l=0}^{j} w^(j)_l S^x(n,l) [G^<(l,j) - G^>(l,j)].
  * H*: triangle with rows 0..n; S*: [l][k][a][b], l <= n; I*: [j][k][a][b].
  */
-void orc_collision_row(int nb, int nk, int n, double dt, const double *Hl_, const double *Hg_,
-                       const double *Sl_, const double *Sg_, double *Il_, double *Ig_) {
+void orc_collision_row_q(int nb, int nk, int n, double dt, int quad, const double *Hl_, const double *Hg_,
+                         const double *Sl_, const double *Sg_, double *Il_, double *Ig_) {
   const cplx *Hl = (const cplx *)Hl_, *Hg = (const cplx *)Hg_;
   const cplx *Sl = (const cplx *)Sl_, *Sg = (const cplx *)Sg_;
   cplx *Il = (cplx *)Il_, *Ig = (cplx *)Ig_;
@@ -342,7 +361,7 @@ void orc_collision_row(int nb, int nk, int n, double dt, const double *Hl_, cons
         const cplx *sl = Sl + l * blk + (size_t)k * nb2, *sg = Sg + l * blk + (size_t)k * nb2;
         fetch(nb, nk, Hl, l, j, k, gl);
         fetch(nb, nk, Hg, l, j, k, gg);
-        double w1 = trap_w(n, l, dt);
+        double w1 = quad_w(quad, n, l, dt);
         for (int e = 0; e < nb2; ++e) sr[e] = w1 * (sg[e] - sl[e]);
         mat_mul(nb, sr, gl, tl);
         mat_mul(nb, sr, gg, tg);
@@ -351,7 +370,7 @@ void orc_collision_row(int nb, int nk, int n, double dt, const double *Hl_, cons
           accg[e] += tg[e];
         }
         if (l <= j) {
-          double w2 = trap_w(j, l, dt);
+          double w2 = quad_w(quad, j, l, dt);
           for (int e = 0; e < nb2; ++e) dg[e] = gl[e] - gg[e];
           mat_mul(nb, sl, dg, tl);
           mat_mul(nb, sg, dg, tg);
@@ -364,6 +383,11 @@ void orc_collision_row(int nb, int nk, int n, double dt, const double *Hl_, cons
       memcpy(Il + j * blk + (size_t)k * nb2, accl, sizeof(cplx) * nb2);
       memcpy(Ig + j * blk + (size_t)k * nb2, accg, sizeof(cplx) * nb2);
     }
+}
+
+void orc_collision_row(int nb, int nk, int n, double dt, const double *Hl, const double *Hg,
+                       const double *Sl, const double *Sg, double *Il, double *Ig) {
+  orc_collision_row_q(nb, nk, n, dt, 0, Hl, Hg, Sl, Sg, Il, Ig);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -490,6 +514,7 @@ void orc_update_row(int nb, int nk, int n, double dt, double theta, const double
 typedef struct orc {
   int nb, dim, L0, L1, nk, nt_max, n_corr, hf, paper_shift;
   double corr_tol; /* Algorithm 1's epsilon (0: always n_corr passes) */
+  int quad;        /* collision-integral quadrature: 0 trapezoid, 1 Gregory */
   int *iters;      /* corrector passes run at each step */
   double dt, beta, mu;
   int nhop;
@@ -712,9 +737,9 @@ static void evaluate_row(orc *s, int n) {
                    (const double *)(s->Hg + tri(n, l) * blk), (double *)(s->Sl + l * blk),
                    (double *)(s->Sg + l * blk));
   }
-  orc_collision_row(s->nb, s->nk, n, s->dt, (const double *)s->Hl, (const double *)s->Hg,
-                    (const double *)s->Sl, (const double *)s->Sg, (double *)s->Icl,
-                    (double *)s->Icg);
+  orc_collision_row_q(s->nb, s->nk, n, s->dt, s->quad, (const double *)s->Hl, (const double *)s->Hg,
+                      (const double *)s->Sl, (const double *)s->Sg, (double *)s->Icl,
+                      (double *)s->Icg);
 }
 
 static void update(orc *s, int n, double theta) {
@@ -843,6 +868,8 @@ int orc_step(orc *s, int nsteps) {
 int orc_current(const orc *s) { return s->n; }
 
 void orc_set_corr_tol(orc *s, double tol) { s->corr_tol = tol > 0.0 ? tol : 0.0; }
+
+void orc_set_quadrature(orc *s, int quad) { s->quad = quad == 1 ? 1 : 0; }
 
 /* corrector passes run at steps 0..n */
 int orc_get_iters(const orc *s, int *out) {

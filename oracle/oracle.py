@@ -60,6 +60,8 @@ def _load():
             lib.orc_propagators.argtypes = [i, i, d, P, P, P, P, P]
             lib.orc_update_row.argtypes = [i, i, i, d, d, P, P, P, P, P, P, P, P, P, P, P, P]
             lib.orc_set_corr_tol.argtypes = [P, d]
+            lib.orc_set_quadrature.argtypes = [P, i]
+            lib.orc_collision_row_q.argtypes = [i, i, i, d, i, P, P, P, P, P, P]
             lib.orc_get_iters.argtypes = [P, P]
             lib.orc_set_threads.argtypes = [i]
             lib.orc_threads.restype = i
@@ -103,14 +105,16 @@ def sigma_pair_literal(nb, L, v, UnUl, Gl, Gg):
     return Sl, Sg
 
 
-def collision_row(nb, nk, n, dt, Hl, Hg, Sl, Sg):
+def collision_row(nb, nk, n, dt, Hl, Hg, Sl, Sg, quadrature=0):
     """I^<, I^> (n, j), j=0..n. H*: triangle [(n+1)(n+2)/2, nk, nb, nb];
-    S*: [n+1, nk, nb, nb]. Returns two [n+1, nk, nb, nb] arrays."""
+    S*: [n+1, nk, nb, nb]. Returns two [n+1, nk, nb, nb] arrays. quadrature:
+    0 trapezoid (the paper's rule), 1 fourth-order Gregory."""
     lib = _load()
     Hl, Hg, Sl, Sg = map(_c128, (Hl, Hg, Sl, Sg))
     Il = np.empty((n + 1, nk, nb, nb), np.complex128)
     Ig = np.empty_like(Il)
-    lib.orc_collision_row(nb, nk, n, float(dt), _ptr(Hl), _ptr(Hg), _ptr(Sl), _ptr(Sg), _ptr(Il), _ptr(Ig))
+    lib.orc_collision_row_q(nb, nk, n, float(dt), int(quadrature), _ptr(Hl), _ptr(Hg), _ptr(Sl), _ptr(Sg),
+                            _ptr(Il), _ptr(Ig))
     return Il, Ig
 
 
@@ -176,6 +180,7 @@ class Oracle:
             lib.orc_set_dipole(self._h, len(E), _ptr(E), _ptr(M))
             self._keep = self._keep + (E, M)
         lib.orc_set_corr_tol(self._h, float(getattr(sys, "corr_tol", 0.0)))
+        lib.orc_set_quadrature(self._h, int(getattr(sys, "quadrature", 0)))
         if lib.orc_reset(self._h) != 0:
             raise RuntimeError("oracle: reset failed")
 

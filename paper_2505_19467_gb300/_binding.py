@@ -36,6 +36,7 @@ EXPORTS = [
     "kbe_batch_destroy", "kbe_batch_system", "kbe_batch_reset", "kbe_batch_step",
     "kbe_batch_synchronize", "kbe_checkpoint_bytes", "kbe_checkpoint_save", "kbe_checkpoint_load",
     "kbe_set_dipole", "kbe_backward", "kbe_backward_memory_bytes", "kbe_corrector_iterations",
+    "kbe_op_collision_row_quad",
 ]
 
 
@@ -49,7 +50,8 @@ class kbe_config(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int), ("dim", ctypes.c_int), ("L", ctypes.c_int * 2),
                 ("nt_max", ctypes.c_int), ("dt", ctypes.c_double), ("beta", ctypes.c_double),
                 ("mu", ctypes.c_double), ("precision", ctypes.c_int), ("n_corr", ctypes.c_int),
-                ("hf", ctypes.c_int), ("paper_shift", ctypes.c_int), ("corr_tol", ctypes.c_double)]
+                ("hf", ctypes.c_int), ("paper_shift", ctypes.c_int), ("corr_tol", ctypes.c_double),
+                ("quadrature", ctypes.c_int)]
 
 
 class kbe_mesh(ctypes.Structure):
@@ -116,6 +118,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "kbe_backward": (I, [P, P, P, P]),
         "kbe_backward_memory_bytes": (S, [pcfg]),
         "kbe_corrector_iterations": (I, [P, P]),
+        "kbe_op_collision_row_quad": (I, [pmesh, I, D, I, I, P, P, P, P, S, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -155,19 +158,20 @@ def mesh(nb: int, L) -> kbe_mesh:
 
 
 def make_config(nb, dim, L, nt_max, dt, beta, mu, precision=KBE_PREC_FP64, n_corr=2, hf=1,
-                paper_shift=0, corr_tol=0.0) -> kbe_config:
+                paper_shift=0, corr_tol=0.0, quadrature=0) -> kbe_config:
     cfg = kbe_config()
     cfg.nb, cfg.dim = nb, dim
     cfg.L[0], cfg.L[1] = int(L[0]), int(L[1])
     cfg.nt_max, cfg.dt, cfg.beta, cfg.mu = nt_max, dt, beta, mu
     cfg.precision, cfg.n_corr, cfg.hf, cfg.paper_shift = precision, n_corr, hf, paper_shift
     cfg.corr_tol = corr_tol
+    cfg.quadrature = quadrature
     return cfg
 
 
 def system_config(sys, nt_max=None, precision=KBE_PREC_FP64) -> kbe_config:
     return make_config(sys.nb, sys.dim, sys.L, sys.nt if nt_max is None else nt_max, sys.dt, sys.beta,
-                       sys.mu, precision, sys.n_corr, sys.hf, sys.paper_shift, sys.corr_tol)
+                       sys.mu, precision, sys.n_corr, sys.hf, sys.paper_shift, sys.corr_tol, sys.quadrature)
 
 
 def memory_bytes(cfg: kbe_config) -> int:
@@ -184,7 +188,8 @@ class KBE:
 
     def __init__(self, nb: int, dim: int, L, nt_max: int, dt: float, beta: float, mu: float,
                  precision: int = KBE_PREC_FP64, n_corr: int = 2, hf: int = 1,
-                 paper_shift: int = 0, stream=None, _borrow=None, corr_tol: float = 0.0):
+                 paper_shift: int = 0, stream=None, _borrow=None, corr_tol: float = 0.0,
+                 quadrature: int = 0):
         lib = load()
         self.nb, self.nk, self.nt_max = nb, int(L[0]) * int(L[1]), nt_max
         self._u_len = 1
@@ -192,7 +197,8 @@ class KBE:
         if _borrow is not None:      # a handle owned by a batch
             self._h = ctypes.c_void_p(_borrow)
             return
-        cfg = make_config(nb, dim, L, nt_max, dt, beta, mu, precision, n_corr, hf, paper_shift, corr_tol)
+        cfg = make_config(nb, dim, L, nt_max, dt, beta, mu, precision, n_corr, hf, paper_shift, corr_tol,
+                          quadrature)
         self._h = ctypes.c_void_p()
         self._stream = _stream_ptr(stream)
         _check(lib.kbe_create(ctypes.byref(cfg), self._stream, ctypes.byref(self._h)), None)
@@ -200,7 +206,8 @@ class KBE:
     @classmethod
     def from_system(cls, sys, nt_max=None, precision=KBE_PREC_FP64, stream=None, U=None, **over):
         """Build and initialise from a kbe_inputs.System (reset included)."""
-        kw = dict(n_corr=sys.n_corr, hf=sys.hf, paper_shift=sys.paper_shift, corr_tol=sys.corr_tol)
+        kw = dict(n_corr=sys.n_corr, hf=sys.hf, paper_shift=sys.paper_shift, corr_tol=sys.corr_tol,
+                  quadrature=sys.quadrature)
         kw.update(over)
         k = cls(sys.nb, sys.dim, sys.L, sys.nt if nt_max is None else nt_max, sys.dt, sys.beta,
                 sys.mu, precision=precision, stream=stream, **kw)
@@ -356,13 +363,20 @@ def collision_row_workspace(nb, L, n, precision=KBE_PREC_FP64) -> int:
     return int(load().kbe_op_collision_row_workspace(ctypes.byref(m), int(n), int(precision)))
 
 
-def collision_row(nb, L, n, dt, H, Sigma, I, precision=KBE_PREC_FP64, work=None, stream=None):
-    """H: history triangle in the precision's storage (see pack)."""
+def collision_row(nb, L, n, dt, H, Sigma, I, precision=KBE_PREC_FP64, work=None, stream=None,
+                  quadrature=0):
+    """H: history triangle in the precision's storage (see pack); quadrature
+    0 trapezoid, 1 Gregory (kbe_op_collision_row_quad)."""
     m = mesh(nb, L)
     wb = 0 if work is None else work.numel() * work.element_size()
-    _check(load().kbe_op_collision_row(ctypes.byref(m), int(n), float(dt), int(precision), _c(H),
-                                       _c(Sigma), _c(I), None if work is None else _c(work), wb,
-                                       _stream_ptr(stream)))
+    if quadrature == 0:
+        _check(load().kbe_op_collision_row(ctypes.byref(m), int(n), float(dt), int(precision), _c(H),
+                                           _c(Sigma), _c(I), None if work is None else _c(work), wb,
+                                           _stream_ptr(stream)))
+    else:
+        _check(load().kbe_op_collision_row_quad(ctypes.byref(m), int(n), float(dt), int(precision),
+                                                int(quadrature), _c(H), _c(Sigma), _c(I),
+                                                None if work is None else _c(work), wb, _stream_ptr(stream)))
 
 
 def pack(precision, src, dst, nblocks, block_elems, stream=None):

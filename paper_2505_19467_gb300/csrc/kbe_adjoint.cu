@@ -55,7 +55,8 @@ __global__ void unpack_fp64_kernel(const double2 *__restrict__ src, double2 *__r
 // Forward (one output column j, l = 0..n, X = G(l, j) or -G(j, l)^+):
 //   I^<(j) = sum_l C1(l) X^<(l,j) + f(j,l) C2^<(l) D(l,j)
 //   I^>(j) = sum_l C1(l) X^>(l,j) + f(j,l) C2^>(l) D(l,j),  D = X^< - X^>
-// with C1 = w^(n)_l (S^> - S^<), C2^x = dt S^x, f = w^(j)_l / dt. Transposed,
+// with C1 = w^(n)_l (S^> - S^<), C2^x = dt S^x, f = w^(j)_l / dt (trapezoid or
+// Gregory weights, quad_omega). Transposed,
 // for each l:
 //   lam_C1(l)  = sum_j lam^<_j X^<(l,j)^+ + lam^>_j X^>(l,j)^+
 //              = sum_j (lam^<_j + lam^>_j) X^<(l,j)^+ - lam^>_j D(l,j)^+
@@ -98,7 +99,7 @@ __device__ __forceinline__ void coef_node(const double2 *__restrict__ lam, const
 // grid: x = tiles of the N_b^2 n_k elements (a, b, k) of one l, y = l (0..n),
 // z = split of the j range; out is lam_Sigma when gridDim.z == 1, else the
 // partial rows [z][l][x][a][b][k].
-template <int NB>
+template <int NB, int QUAD>
 __global__ void __launch_bounds__(256, 2) adj_coef_kernel(const double2 *__restrict__ H,
                                                           const double2 *__restrict__ lamI,
                                                           double2 *__restrict__ out, int n, int nk,
@@ -124,12 +125,23 @@ __global__ void __launch_bounds__(256, 2) adj_coef_kernel(const double2 *__restr
     else
       coef_node<NB, true, false>(lbase, hbase, blk, nk, b, a1, dL, dG);
   }
-  for (int j = max(j0, l + 1); j < j1; ++j)   // j > l: f = 1, or 1/2 when l = 0 is the end node
-    coef_node<NB, false, true>(lbase + (size_t)j * 2 * blk, hbase + tri(j, l) * 2 * blk, blk, nk, b, a1, aL, aG);
-  const double fu = (l == 0) ? 0.5 : 1.0;
-  aL = c_add(c_scale(fu, aL), c_scale(0.5, dL));
-  aG = c_add(c_scale(fu, aG), c_scale(0.5, dG));
-  const double w1 = trap_weight(n, l, dt);
+  if (QUAD == kQuadTrapezoid) {   // j > l: f = 1, or 1/2 when l = 0 is the end node
+    for (int j = max(j0, l + 1); j < j1; ++j)
+      coef_node<NB, false, true>(lbase + (size_t)j * 2 * blk, hbase + tri(j, l) * 2 * blk, blk, nk, b, a1, aL, aG);
+  } else {   // Gregory: f = w^(j)_l / dt per node
+    for (int j = max(j0, l + 1); j < j1; ++j) {
+      double2 tL = z, tG = z;
+      coef_node<NB, false, true>(lbase + (size_t)j * 2 * blk, hbase + tri(j, l) * 2 * blk, blk, nk, b, a1, tL, tG);
+      const double f = quad_omega(QUAD, j, l);
+      aL = make_double2(fma(f, tL.x, aL.x), fma(f, tL.y, aL.y));
+      aG = make_double2(fma(f, tG.x, aG.x), fma(f, tG.y, aG.y));
+    }
+  }
+  const double fu = (QUAD == kQuadTrapezoid && l == 0) ? 0.5 : 1.0;
+  const double fd = quad_omega(QUAD, l, l);   // the diagonal node's weight (0 at l = 0)
+  aL = c_add(c_scale(fu, aL), c_scale(fd, dL));
+  aG = c_add(c_scale(fu, aG), c_scale(fd, dG));
+  const double w1 = dt * quad_omega(QUAD, n, l);
   double2 *o = out + ((size_t)blockIdx.z * (n + 1) + l) * 2 * blk + (size_t)ab * nk + k;
   o[0] = c_add(c_scale(-w1, a1), c_scale(dt, aL));
   o[blk] = c_add(c_scale(w1, a1), c_scale(dt, aG));
@@ -137,11 +149,11 @@ __global__ void __launch_bounds__(256, 2) adj_coef_kernel(const double2 *__restr
 
 // C1(l) = w^(n)_l (S^>(l) - S^<(l)), l = 0..n, one block per l
 __global__ void adj_c1_kernel(const double2 *__restrict__ Sig, double2 *__restrict__ C1, int n, size_t blk,
-                              double dt) {
+                              double dt, int quad) {
   const size_t total = (size_t)(n + 1) * blk;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
     const size_t l = i / blk, r = i - l * blk;
-    C1[i] = c_scale(trap_weight(n, (int)l, dt), c_sub(Sig[(l * 2 + 1) * blk + r], Sig[l * 2 * blk + r]));
+    C1[i] = c_scale(dt * quad_omega(quad, n, (int)l), c_sub(Sig[(l * 2 + 1) * blk + r], Sig[l * 2 * blk + r]));
   }
 }
 
@@ -172,7 +184,7 @@ __global__ void __launch_bounds__(256, 2) adj_hist_kernel(const double2 *__restr
                                                           const double2 *__restrict__ C1,
                                                           const double2 *__restrict__ lamI,
                                                           double2 *lamH, double2 *lamRowN, int n, int nk,
-                                                          int jchunk, double dt) {
+                                                          int jchunk, double dt, int quad) {
   const int i = blockIdx.y;
   const int j0 = blockIdx.z * jchunk;
   if (j0 > i) return;
@@ -217,7 +229,7 @@ __global__ void __launch_bounds__(256, 2) adj_hist_kernel(const double2 *__restr
         t = c_fmac(sj[c * cs], Li[c], t);
         t = c_fmac(sj[blk + c * cs], Gi[c], t);
       }
-      const double fB = (jp == 0 ? 0.5 : 1.0) * dt;
+      const double fB = quad_omega(quad, i, jp) * dt;
       dl = make_double2(fma(-fB, t.x, dl.x), fma(-fB, t.y, dl.y));
       dg = make_double2(fma(fB, t.x, dg.x), fma(fB, t.y, dg.y));
     } else if (i >= 1) {   // the diagonal block, use 1 with f = 1/2: + c, - c
@@ -228,7 +240,7 @@ __global__ void __launch_bounds__(256, 2) adj_hist_kernel(const double2 *__restr
         t = c_fmac(lj[c * cs], si[c * cs], t);
         t = c_fmac(lj[blk + c * cs], si[blk + c * cs], t);
       }
-      const double fA = 0.5 * dt;
+      const double fA = quad_omega(quad, i, i) * dt;
       dl = make_double2(fma(fA, t.x, dl.x), fma(fA, t.y, dl.y));
       dg = make_double2(fma(-fA, t.x, dg.x), fma(-fA, t.y, dg.y));
     }
@@ -724,19 +736,22 @@ int uv_splits(const Mesh &m, int n) {
 template <int NB>
 cudaError_t adj_sweep_nb(const Mesh &m, int n, double dt, const double2 *H, const double2 *Sig,
                          const double2 *lamI, double2 *lamSig, double2 *lamH, double2 *lamRowN,
-                         double2 *coef_work, double2 *c1_work, cudaStream_t st) {
+                         double2 *coef_work, double2 *c1_work, cudaStream_t st, int quad) {
   const CoefShape sh = coef_shape(m, n);
   double2 *out = sh.nz > 1 ? coef_work : lamSig;
-  adj_coef_kernel<NB><<<sh.grid, sh.threads, 0, st>>>(H, lamI, out, n, m.nk, sh.jchunk, dt);
+  if (quad == kQuadGregory)
+    adj_coef_kernel<NB, kQuadGregory><<<sh.grid, sh.threads, 0, st>>>(H, lamI, out, n, m.nk, sh.jchunk, dt);
+  else
+    adj_coef_kernel<NB, kQuadTrapezoid><<<sh.grid, sh.threads, 0, st>>>(H, lamI, out, n, m.nk, sh.jchunk, dt);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  adj_c1_kernel<<<grid_for_count((size_t)(n + 1) * blkof(m)), 256, 0, st>>>(Sig, c1_work, n, blkof(m), dt);
+  adj_c1_kernel<<<grid_for_count((size_t)(n + 1) * blkof(m)), 256, 0, st>>>(Sig, c1_work, n, blkof(m), dt, quad);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int nch = n / kHistChunk + 1;   // chunks covering j' = 0..n
   const long elems = (long)NB * NB * m.nk;
   const dim3 hgrid((unsigned)((elems + 255) / 256), n + 1, (unsigned)nch);
-  adj_hist_kernel<NB><<<hgrid, 256, 0, st>>>(Sig, c1_work, lamI, lamH, lamRowN, n, m.nk, kHistChunk, dt);
+  adj_hist_kernel<NB><<<hgrid, 256, 0, st>>>(Sig, c1_work, lamI, lamH, lamRowN, n, m.nk, kHistChunk, dt, quad);
   e = cudaGetLastError();
   if (e != cudaSuccess || sh.nz == 1) return e;
   const size_t count = (size_t)(n + 1) * 2 * blkof(m);
@@ -800,9 +815,9 @@ size_t adj_coef_workspace_bytes(const Mesh &m, int nmax) {
 
 cudaError_t launch_adj_sweep(const Mesh &m, int n, double dt, const double2 *H, const double2 *Sig,
                              const double2 *lamI, double2 *lamSig, double2 *lamH, double2 *lamRowN,
-                             double2 *coef_work, double2 *c1_work, cudaStream_t st) {
+                             double2 *coef_work, double2 *c1_work, cudaStream_t st, int quad) {
   KBE_NB_SWITCH(m.nb, return adj_sweep_nb<NB>(m, n, dt, H, Sig, lamI, lamSig, lamH, lamRowN, coef_work,
-                                               c1_work, st));
+                                               c1_work, st, quad));
   return cudaErrorInvalidValue;
 }
 

@@ -204,7 +204,8 @@ kbe_status evaluate_row(kbe_handle *h, int n, const int *skip = nullptr) {
     }
     cudaEventRecord(h->ev[h->ev_used].first, h->stream);
   }
-  e = kbe::launch_sweep(m, n, h->cfg.dt, h->cfg.precision, h->H, h->Sig, h->Ic, h->coef, h->stream, skip);
+  e = kbe::launch_sweep(m, n, h->cfg.dt, h->cfg.precision, h->H, h->Sig, h->Ic, h->coef, h->stream, skip,
+                        h->cfg.quadrature);
   if (e != cudaSuccess) return cuda_fail(h, e, "collision sweep");
   if (timed) {
     cudaEventRecord(h->ev[h->ev_used].second, h->stream);
@@ -445,7 +446,9 @@ kbe_status backward_step(kbe_handle *h, const AdjPtrs &P, int n, int nc, double2
   KBE_TRY(cudaMemcpyAsync(P.save, histN, rowc * sizeof(double2), cudaMemcpyDeviceToDevice, st), "backward save");
   KBE_TRY(kbe::launch_unpack_fp64(Hd + tri(n - 1, 0) * 2 * blk, P.rowp, (size_t)n, blk, st), "backward unpack");
   KBE_TRY(kbe::sigma_row(m, v, n - 1, Up, Ul, P.rowp, P.sigp, h->work, st), "backward sigma");
-  KBE_TRY(kbe::launch_sweep(m, n - 1, dt, KBE_PREC_FP64, h->H, P.sigp, P.Ip, h->coef, st), "backward sweep");
+  const int quad = h->cfg.quadrature;
+  KBE_TRY(kbe::launch_sweep(m, n - 1, dt, KBE_PREC_FP64, h->H, P.sigp, P.Ip, h->coef, st, nullptr, quad),
+          "backward sweep");
   kbe_status s = build_props(h, n, rho(n - 1), rho(n2), ca0, cb0, hk(0), Uk(0), Vk(0));
   if (s != KBE_OK) return s;
   KBE_TRY(kbe::launch_update_row(m, n, dt, 0.0, hk(0), Uk(0), Vk(0), P.rowp, P.Ip, nullptr, row(0), st),
@@ -455,7 +458,8 @@ kbe_status backward_step(kbe_handle *h, const AdjPtrs &P, int n, int nc, double2
     KBE_TRY(kbe::launch_local_density(m, row(c - 1) + (size_t)n * 2 * blk, cur(c), st), "backward density");
     if ((s = build_props(h, n, rho(n - 1), cur(c), 0.5, 0.5, hk(c), Uk(c), Vk(c))) != KBE_OK) return s;
     KBE_TRY(kbe::sigma_row(m, v, n, Un, Ul, row(c - 1), sig(c), h->work, st), "backward sigma");
-    KBE_TRY(kbe::launch_sweep(m, n, dt, KBE_PREC_FP64, h->H, sig(c), Ist(c), h->coef, st), "backward sweep");
+    KBE_TRY(kbe::launch_sweep(m, n, dt, KBE_PREC_FP64, h->H, sig(c), Ist(c), h->coef, st, nullptr, quad),
+            "backward sweep");
     KBE_TRY(kbe::launch_update_row(m, n, dt, 0.5, hk(c), Uk(c), Vk(c), P.rowp, P.Ip, Ist(c), row(c), st),
             "backward update");
     KBE_TRY(kbe::launch_pack(KBE_PREC_FP64, row(c), histN, (size_t)(n + 1), blk, st), "backward pack");
@@ -471,7 +475,7 @@ kbe_status backward_step(kbe_handle *h, const AdjPtrs &P, int n, int nc, double2
   KBE_TRY(kbe::launch_adj_density(m, lrho(n), 1.0 / m.nk, lamN + (size_t)n * 2 * blk, st), "backward density");
   // final evaluation: I_n = sweep(Sigma(row), history with row n)
   tm.open(1, adj_sweep_flops(h, n));
-  KBE_TRY(kbe::launch_adj_sweep(m, n, dt, Hd, sig(nc + 1), lamIcur, P.lamSig, P.lamH, lamN, P.coefw, P.c1w, st),
+  KBE_TRY(kbe::launch_adj_sweep(m, n, dt, Hd, sig(nc + 1), lamIcur, P.lamSig, P.lamH, lamN, P.coefw, P.c1w, st, quad),
           "backward adj sweep");
   tm.close();
   tm.open(2);
@@ -506,7 +510,7 @@ kbe_status backward_step(kbe_handle *h, const AdjPtrs &P, int n, int nc, double2
     KBE_TRY(kbe::launch_pack(KBE_PREC_FP64, row(c - 1), histN, (size_t)(n + 1), blk, st), "backward pack");
     tm.close();
     tm.open(1, adj_sweep_flops(h, n));
-    KBE_TRY(kbe::launch_adj_sweep(m, n, dt, Hd, sig(c), P.lamIc, P.lamSig, P.lamH, lamPS, P.coefw, P.c1w, st),
+    KBE_TRY(kbe::launch_adj_sweep(m, n, dt, Hd, sig(c), P.lamIc, P.lamSig, P.lamH, lamPS, P.coefw, P.c1w, st, quad),
             "backward adj sweep");
     tm.close();
     tm.open(2);
@@ -596,6 +600,8 @@ kbe_status kbe_create(const kbe_config *cfg, void *stream, kbe_handle **out) {
   if (cfg->n_corr < 0 || cfg->n_corr > 64) return fail(nullptr, KBE_ERR_ARG, "kbe_create: n_corr out of range");
   if (!std::isfinite(cfg->corr_tol) || cfg->corr_tol < 0.0)
     return fail(nullptr, KBE_ERR_ARG, "kbe_create: corr_tol must be finite and >= 0");
+  if (cfg->quadrature != KBE_QUAD_TRAPEZOID && cfg->quadrature != KBE_QUAD_GREGORY)
+    return fail(nullptr, KBE_ERR_ARG, "kbe_create: unknown quadrature");
 
   kbe_handle *h = new kbe_handle();
   h->cfg = *cfg;
@@ -1187,6 +1193,22 @@ kbe_status kbe_op_collision_row(const kbe_mesh *m, int n, double dt, int precisi
     return fail(nullptr, KBE_ERR_ARG, "op_collision_row: workspace too small");
   cudaError_t e = kbe::launch_sweep(to_mesh(m), n, dt, precision, H_dev, (const double2 *)Sigma_dev,
                                     (double2 *)I_dev, work_dev, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(nullptr, KBE_ERR_CUDA, std::string("op_collision_row: ") + cudaGetErrorString(e));
+  return KBE_OK;
+}
+
+kbe_status kbe_op_collision_row_quad(const kbe_mesh *m, int n, double dt, int precision, int quadrature,
+                                     const void *H_dev, const void *Sigma_dev, void *I_dev,
+                                     void *work_dev, size_t work_bytes, void *stream) {
+  if (!mesh_ok(m) || n < 0 || !H_dev || !Sigma_dev || !I_dev || !(dt > 0.0) ||
+      (quadrature != KBE_QUAD_TRAPEZOID && quadrature != KBE_QUAD_GREGORY))
+    return fail(nullptr, KBE_ERR_ARG, "op_collision_row: bad arguments");
+  if (!kbe::precision_supported(precision)) return fail(nullptr, KBE_ERR_UNSUPPORTED, "op_collision_row: precision");
+  const size_t need = kbe::sweep_workspace_bytes(to_mesh(m), n, precision);
+  if (!work_dev || work_bytes < need)
+    return fail(nullptr, KBE_ERR_ARG, "op_collision_row: workspace too small");
+  cudaError_t e = kbe::launch_sweep(to_mesh(m), n, dt, precision, H_dev, (const double2 *)Sigma_dev,
+                                    (double2 *)I_dev, work_dev, (cudaStream_t)stream, nullptr, quadrature);
   if (e != cudaSuccess) return fail(nullptr, KBE_ERR_CUDA, std::string("op_collision_row: ") + cudaGetErrorString(e));
   return KBE_OK;
 }

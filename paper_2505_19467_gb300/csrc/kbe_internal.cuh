@@ -38,6 +38,23 @@ __host__ __device__ __forceinline__ double trap_weight(int m, int l, double dt) 
   return w;
 }
 
+enum : int { kQuadTrapezoid = 0, kQuadGregory = 1 };
+
+// quadrature weight of node l on [0, t_m] in units of dt (zero for m = 0):
+// trapezoid (the paper's second-order rule), or fourth-order Gregory: end
+// corrections 3/8, 7/6, 23/24 at both ends for m >= 5, and for m <= 4 the
+// closed Newton-Cotes rule of the whole interval (m = 1 trapezoid, 2 Simpson,
+// 3 Simpson 3/8, 4 Boole); every m >= 2 integrates cubics exactly
+__host__ __device__ __forceinline__ double quad_omega(int quad, int m, int l) {
+  if (m <= 0) return 0.0;
+  if (quad == kQuadTrapezoid || m == 1) return (l == 0 || l == m) ? 0.5 : 1.0;
+  if (m == 2) return l == 1 ? 4.0 / 3.0 : 1.0 / 3.0;
+  if (m == 3) return (l == 0 || l == 3) ? 0.375 : 1.125;
+  if (m == 4) return (l == 0 || l == 4) ? 14.0 / 45.0 : (l == 2 ? 24.0 / 45.0 : 64.0 / 45.0);
+  const int e = l < m - l ? l : m - l;
+  return e == 0 ? 0.375 : (e == 1 ? 7.0 / 6.0 : (e == 2 ? 23.0 / 24.0 : 1.0));
+}
+
 // ---- double2 complex helpers -------------------------------------------
 __device__ __forceinline__ double2 c_make(double r, double i) { return make_double2(r, i); }
 __device__ __forceinline__ double2 c_add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -105,7 +122,7 @@ cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t nblocks,
                         cudaStream_t st, const int *skip = nullptr);
 cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const void *H,
                          const double2 *Sig, double2 *I, void *work, cudaStream_t st,
-                         const int *skip = nullptr);
+                         const int *skip = nullptr, int quad = kQuadTrapezoid);
 
 // a3 propagators / initial state / density
 struct HopTable {
@@ -172,7 +189,8 @@ cudaError_t launch_unpack_fp64(const double2 *packed, double2 *out, size_t nbloc
 size_t adj_coef_workspace_bytes(const Mesh &m, int nmax);
 cudaError_t launch_adj_sweep(const Mesh &m, int n, double dt, const double2 *H, const double2 *Sig,
                              const double2 *lamI, double2 *lamSig, double2 *lamH, double2 *lamRowN,
-                             double2 *coef_work, double2 *c1_work, cudaStream_t st);
+                             double2 *coef_work, double2 *c1_work, cudaStream_t st,
+                             int quad = kQuadTrapezoid);
 // transpose of the Sigma row (factor -U_n U_l, Ul_dev NULL: U_l = U_n): lamRow
 // += lambda of the G row; gU[i] += dL/dU_i (gU[n] only when Ul_dev is NULL)
 size_t adj_sigma_workspace_bytes(const Mesh &m, int n);

@@ -61,6 +61,8 @@ struct ArithF64 {
   static __device__ __forceinline__ S negconj(const S &x) { return make_double2(-x.x, x.y); }
   static __device__ __forceinline__ S neg(const S &x) { return make_double2(-x.x, -x.y); }
   static __device__ __forceinline__ S scale(float f, const S &x) { return c_scale((double)f, x); }
+  static __device__ __forceinline__ S scale_w(double f, const S &x) { return c_scale(f, x); }
+  static __device__ __forceinline__ S add(const S &x, const S &y) { return c_add(x, y); }
   static __device__ __forceinline__ double2 result(const A &a) { return a; }
 };
 
@@ -92,6 +94,19 @@ __device__ __forceinline__ void df_sub(float &sh, float &sl, float ah, float al,
   const float tb = __fsub_rn(t, s);
   sl = __fadd_rn(__fsub_rn(s, __fsub_rn(t, tb)), __fsub_rn(e, tb));
   sh = t;
+}
+
+// (rh, rl) = (xh + xl) * f for a double weight f (split into two floats):
+// the exact product of the high parts plus the cross terms, renormalised
+__device__ __forceinline__ void df_mul_w(float &rh, float &rl, float xh, float xl, double f) {
+  const float fh = __double2float_rn(f), fl = __double2float_rn(f - (double)fh);
+  const float p = __fmul_rn(xh, fh);
+  float e = __fmaf_rn(xh, fh, -p);
+  e = __fmaf_rn(xh, fl, e);
+  e = __fmaf_rn(xl, fh, e);
+  const float s = __fadd_rn(p, e);
+  rl = __fsub_rn(e, __fsub_rn(s, p));
+  rh = s;
 }
 
 // (h, l) <- TwoSum(h, l): renormalise so that |l| <= ulp(h) / 2
@@ -131,6 +146,18 @@ struct ArithDF64 {
   static __device__ __forceinline__ S scale(float f, const S &X) {   // f a power of two: exact
     return make_float4(f * X.x, f * X.y, f * X.z, f * X.w);
   }
+  static __device__ __forceinline__ S scale_w(double f, const S &X) {   // any weight, 2^-48 relative
+    float4 r;
+    df_mul_w(r.x, r.y, X.x, X.y, f);
+    df_mul_w(r.z, r.w, X.z, X.w, f);
+    return r;
+  }
+  static __device__ __forceinline__ S add(const S &X, const S &Y) {
+    float4 r;
+    df_sub(r.x, r.y, X.x, X.y, -Y.x, -Y.y);
+    df_sub(r.z, r.w, X.z, X.w, -Y.z, -Y.w);
+    return r;
+  }
   static __device__ __forceinline__ double2 result(const A &a) {
     return make_double2((double)a.x + (double)a.y, (double)a.z + (double)a.w);
   }
@@ -169,6 +196,11 @@ struct ArithC64 {
   static __device__ __forceinline__ S negconj(const S &x) { return make_float2(-x.x, x.y); }
   static __device__ __forceinline__ S neg(const S &x) { return make_float2(-x.x, -x.y); }
   static __device__ __forceinline__ S scale(float f, const S &x) { return make_float2(f * x.x, f * x.y); }
+  static __device__ __forceinline__ S scale_w(double f, const S &x) {
+    const float g = (float)f;
+    return make_float2(g * x.x, g * x.y);
+  }
+  static __device__ __forceinline__ S add(const S &x, const S &y) { return make_float2(x.x + y.x, x.y + y.y); }
   static __device__ __forceinline__ double2 result(const A &a) {
     return make_double2((double)a.sum.x + (double)a.sum.y, (double)a.sum.z + (double)a.sum.w);
   }
@@ -216,6 +248,37 @@ __device__ __forceinline__ void sweep_node(const typename P::S *__restrict__ c1,
   P::end(accG);
 }
 
+// One node of [0, t_j] with a general weight f = w^(j)_l / dt (the Gregory end
+// nodes): f C2^< dG for I^<, and (f C2^> - C1) dG = (f C3 + (f - 1) C1) dG for I^>.
+template <class P, int NB, bool LOWER>
+__device__ __forceinline__ void sweep_wnode(const typename P::S *__restrict__ c1,
+                                            const typename P::S *__restrict__ g, size_t blk, int nk,
+                                            int b, double f, typename P::A &accP, typename P::A &accL,
+                                            typename P::A &accG) {
+  using S = typename P::S;
+  P::begin(accP);
+  P::begin(accL);
+  P::begin(accG);
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    const S A1 = c1[(size_t)c * nk];
+    S Gl, D;
+    if (LOWER) {
+      Gl = g[(size_t)(c * NB + b) * nk];
+      D = g[blk + (size_t)(c * NB + b) * nk];
+    } else {
+      Gl = P::negconj(g[(size_t)(b * NB + c) * nk]);
+      D = P::negconj(g[blk + (size_t)(b * NB + c) * nk]);
+    }
+    P::mac(accP, A1, Gl);
+    P::mac(accL, P::scale_w(f, c1[blk + (size_t)c * nk]), D);
+    P::mac(accG, P::add(P::scale_w(f, c1[2 * blk + (size_t)c * nk]), P::scale_w(f - 1.0, A1)), D);
+  }
+  P::end(accP);
+  P::end(accL);
+  P::end(accG);
+}
+
 // grid: x = tiles of the N_b^2 n_k output elements, y = output column j
 // (0..n), z = split of the l range (lchunk values each). The tiles of one
 // column are adjacent in launch order, so they share its blocks through L2.
@@ -223,7 +286,7 @@ __device__ __forceinline__ void sweep_node(const typename P::S *__restrict__ c1,
 // [z][j][x][a][b][k]. The l range [l0, l1) is walked as three branch-free
 // runs: interior nodes 0 < l < j (adjoint blocks), nodes above l > j (stored
 // blocks), then the two end nodes l = 0 and l = j.
-template <class P, int NB>
+template <class P, int NB, int QUAD>
 __global__ void __launch_bounds__(256, P::kMinBlocks) sweep_kernel(const typename P::S *__restrict__ H,
                                                     const typename P::S *__restrict__ Cf,
                                                     double2 *__restrict__ out, int n, int nk,
@@ -246,20 +309,35 @@ __global__ void __launch_bounds__(256, P::kMinBlocks) sweep_kernel(const typenam
   P::zero(accP);
   P::zero(accL);
   P::zero(accG);
+  // interior of [0, t_j] with weight 1: 0 < l < j (trapezoid), 3 <= l <= j - 3 (Gregory)
+  const int ia = QUAD == kQuadTrapezoid ? 1 : 3, ib = QUAD == kQuadTrapezoid ? j : j - 2;
   if (j > 0) {
-    for (int l = max(l0, 1); l < min(l1, j); ++l)   // interior of [0, t_j]
+    for (int l = max(l0, ia); l < min(l1, ib); ++l)
       sweep_node<P, NB, 1, false>(cbase + (size_t)l * 3 * blk, hbase + tri(j, l) * 2 * blk, blk, nk, b,
                                   accP, accL, accG);
   }
   for (int l = max(l0, j == 0 ? 0 : j + 1); l < l1; ++l)   // above the output
     sweep_node<P, NB, 0, true>(cbase + (size_t)l * 3 * blk, hbase + tri(l, j) * 2 * blk, blk, nk, b,
                                accP, accL, accG);
-  if (j > 0) {
+  if (j > 0 && QUAD == kQuadTrapezoid) {
     if (l0 == 0)   // end node l = 0 (adjoint block, 0 < j)
       sweep_node<P, NB, 2, false>(cbase, hbase + tri(j, 0) * 2 * blk, blk, nk, b, accP, accL, accG);
     if (j >= l0 && j < l1)   // end node l = j (diagonal block)
       sweep_node<P, NB, 2, true>(cbase + (size_t)j * 3 * blk, hbase + tri(j, j) * 2 * blk, blk, nk, b,
                                  accP, accL, accG);
+  } else if (j > 0) {   // Gregory: the three nodes at each end (every node for j <= 4)
+    const int ns = j >= 5 ? 6 : j + 1;
+    for (int s = 0; s < ns; ++s) {
+      const int l = (j >= 5 && s >= 3) ? j - 5 + s : s;
+      if (l < l0 || l >= l1) continue;
+      const double f = quad_omega(kQuadGregory, j, l);
+      if (l == j)
+        sweep_wnode<P, NB, true>(cbase + (size_t)l * 3 * blk, hbase + tri(j, j) * 2 * blk, blk, nk, b, f,
+                                 accP, accL, accG);
+      else
+        sweep_wnode<P, NB, false>(cbase + (size_t)l * 3 * blk, hbase + tri(j, l) * 2 * blk, blk, nk, b, f,
+                                  accP, accL, accG);
+    }
   }
   const double2 p = P::result(accP);
   double2 *o = out + ((size_t)blockIdx.z * (n + 1) + j) * 2 * blk + (size_t)ab * nk + k;
@@ -312,7 +390,7 @@ __global__ void pack_kernel(int prec, const double2 *__restrict__ src, void *__r
 
 // coefficient rows [l][3][a][c][k]: C1 = w^(n)_l (S^> - S^<), C2^< = dt S^<, C3 = dt S^> - C1
 __global__ void coef_kernel(int prec, const double2 *__restrict__ Sig, void *__restrict__ Cf, int n,
-                            int nk, int nb2, double dt, const int *__restrict__ skip) {
+                            int nk, int nb2, double dt, const int *__restrict__ skip, int quad) {
   if (skip && *skip) return;
   const size_t blk = (size_t)nb2 * nk;
   const size_t total = (size_t)(n + 1) * blk;
@@ -320,7 +398,7 @@ __global__ void coef_kernel(int prec, const double2 *__restrict__ Sig, void *__r
        i += (size_t)gridDim.x * blockDim.x) {
     const size_t l = i / blk, r = i - l * blk;
     const double2 sl = Sig[(l * 2) * blk + r], sg = Sig[(l * 2 + 1) * blk + r];
-    const double w1 = trap_weight(n, (int)l, dt);
+    const double w1 = dt * quad_omega(quad, n, (int)l);
     const double2 c1 = c_scale(w1, c_sub(sg, sl));
     const double2 v[3] = {c1, c_scale(dt, sl), c_sub(c_scale(dt, sg), c1)};
     for (int q = 0; q < 3; ++q) {
@@ -364,11 +442,15 @@ SweepShape sweep_shape(const Mesh &m, int n) {
 
 template <class P, int NB>
 cudaError_t sweep_nb(const Mesh &m, int n, const void *H, const void *Cf, double2 *I, double2 *part,
-                     cudaStream_t st, const int *skip) {
+                     cudaStream_t st, const int *skip, int quad) {
   const SweepShape sh = sweep_shape(m, n);
   double2 *out = sh.nz > 1 ? part : I;
-  sweep_kernel<P, NB><<<sh.grid, sh.threads, 0, st>>>((const typename P::S *)H,
-                                                      (const typename P::S *)Cf, out, n, m.nk, sh.lchunk, skip);
+  if (quad == kQuadGregory)
+    sweep_kernel<P, NB, kQuadGregory><<<sh.grid, sh.threads, 0, st>>>(
+        (const typename P::S *)H, (const typename P::S *)Cf, out, n, m.nk, sh.lchunk, skip);
+  else
+    sweep_kernel<P, NB, kQuadTrapezoid><<<sh.grid, sh.threads, 0, st>>>(
+        (const typename P::S *)H, (const typename P::S *)Cf, out, n, m.nk, sh.lchunk, skip);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || sh.nz == 1) return e;
   const size_t count = (size_t)(n + 1) * 2 * m.nb * m.nb * m.nk;
@@ -378,10 +460,10 @@ cudaError_t sweep_nb(const Mesh &m, int n, const void *H, const void *Cf, double
 
 template <int NB>
 cudaError_t sweep_prec(const Mesh &m, int n, int prec, const void *H, const void *Cf, double2 *I,
-                       double2 *part, cudaStream_t st, const int *skip) {
-  if (prec == KBE_PREC_FP64) return sweep_nb<ArithF64, NB>(m, n, H, Cf, I, part, st, skip);
-  if (prec == KBE_PREC_DF64) return sweep_nb<ArithDF64, NB>(m, n, H, Cf, I, part, st, skip);
-  return sweep_nb<ArithC64, NB>(m, n, H, Cf, I, part, st, skip);
+                       double2 *part, cudaStream_t st, const int *skip, int quad) {
+  if (prec == KBE_PREC_FP64) return sweep_nb<ArithF64, NB>(m, n, H, Cf, I, part, st, skip, quad);
+  if (prec == KBE_PREC_DF64) return sweep_nb<ArithDF64, NB>(m, n, H, Cf, I, part, st, skip, quad);
+  return sweep_nb<ArithC64, NB>(m, n, H, Cf, I, part, st, skip, quad);
 }
 
 }  // namespace
@@ -426,25 +508,26 @@ cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t nblocks,
 }
 
 cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const void *H,
-                         const double2 *Sig, double2 *I, void *work, cudaStream_t st, const int *skip) {
+                         const double2 *Sig, double2 *I, void *work, cudaStream_t st, const int *skip,
+                         int quad) {
   if (!precision_supported(precision)) return cudaErrorInvalidValue;
   const size_t blk = (size_t)m.nb * m.nb * m.nk;
   const size_t total = (size_t)(n + 1) * blk;
-  coef_kernel<<<grid_for(total), 256, 0, st>>>(precision, Sig, work, n, m.nk, m.nb * m.nb, dt, skip);
+  coef_kernel<<<grid_for(total), 256, 0, st>>>(precision, Sig, work, n, m.nk, m.nb * m.nb, dt, skip, quad);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   size_t coef = (size_t)(n + 1) * 3 * blk * history_elem_bytes(precision);
   coef = (coef + 255) / 256 * 256;
   double2 *part = (double2 *)((char *)work + coef);
   switch (m.nb) {
-    case 1: return sweep_prec<1>(m, n, precision, H, work, I, part, st, skip);
-    case 2: return sweep_prec<2>(m, n, precision, H, work, I, part, st, skip);
-    case 3: return sweep_prec<3>(m, n, precision, H, work, I, part, st, skip);
-    case 4: return sweep_prec<4>(m, n, precision, H, work, I, part, st, skip);
-    case 6: return sweep_prec<6>(m, n, precision, H, work, I, part, st, skip);
-    case 8: return sweep_prec<8>(m, n, precision, H, work, I, part, st, skip);
-    case 12: return sweep_prec<12>(m, n, precision, H, work, I, part, st, skip);
-    case 16: return sweep_prec<16>(m, n, precision, H, work, I, part, st, skip);
+    case 1: return sweep_prec<1>(m, n, precision, H, work, I, part, st, skip, quad);
+    case 2: return sweep_prec<2>(m, n, precision, H, work, I, part, st, skip, quad);
+    case 3: return sweep_prec<3>(m, n, precision, H, work, I, part, st, skip, quad);
+    case 4: return sweep_prec<4>(m, n, precision, H, work, I, part, st, skip, quad);
+    case 6: return sweep_prec<6>(m, n, precision, H, work, I, part, st, skip, quad);
+    case 8: return sweep_prec<8>(m, n, precision, H, work, I, part, st, skip, quad);
+    case 12: return sweep_prec<12>(m, n, precision, H, work, I, part, st, skip, quad);
+    case 16: return sweep_prec<16>(m, n, precision, H, work, I, part, st, skip, quad);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -75,6 +75,36 @@ def test_collision_row_matches_oracle(nb, L, n):
     assert relerr(gl, Il)[1] < TOL and relerr(gg, Ig)[1] < TOL
 
 
+@pytest.mark.parametrize("prec", ["fp64", "df64", "c64"])
+@pytest.mark.parametrize("nb,L,n", [(2, (8, 1), 1), (2, (8, 1), 2), (3, (3, 3), 4), (4, (8, 8), 5),
+                                    (4, (7, 5), 23), (2, (8, 1), 40)])
+def test_gregory_collision_row_matches_oracle(nb, L, n, prec):
+    """the Gregory weights (start rules for n <= 4, end corrections beyond) in all
+    three arithmetic forms; the l range is split over CTAs at the larger n"""
+    rng = np.random.default_rng(300 + nb * 13 + n)
+    nk = L[0] * L[1]
+    dt = 0.03
+    ntri = tri(n, n) + 1
+    Hl = ki.random_blocks(rng, (ntri, nk, nb, nb))
+    Hg = ki.random_blocks(rng, (ntri, nk, nb, nb))
+    Sl = ki.random_blocks(rng, (n + 1, nk, nb, nb))
+    Sg = ki.random_blocks(rng, (n + 1, nk, nb, nb))
+    Il, Ig = oracle.collision_row(nb, nk, n, dt, Hl, Hg, Sl, Sg, quadrature=1)
+    p = kbe.PRECISIONS[prec]
+    H64 = dev(to_dev_blocks(Hl, Hg))
+    esz = 8 if prec == "c64" else 16
+    H = torch.empty(H64.numel() * esz // 4, dtype=torch.float32, device="cuda")
+    kbe.pack(p, H64, H, ntri, nb * nb * nk)
+    S = dev(to_dev_blocks(Sl, Sg))
+    I = torch.full((n + 1, 2, nb, nb, nk), float("nan"), dtype=torch.complex128, device="cuda")
+    work = torch.empty(kbe.collision_row_workspace(nb, L, n, p) // 4 + 1, dtype=torch.float32, device="cuda")
+    kbe.collision_row(nb, L, n, dt, H, S, I, precision=p, work=work, quadrature=1)
+    torch.cuda.synchronize()
+    gl, gg = from_dev_blocks(I.cpu().numpy())
+    bar = {"fp64": TOL, "df64": 1e-12, "c64": 1e-5}[prec]
+    assert relerr(gl, Il)[1] < bar and relerr(gg, Ig)[1] < bar
+
+
 def _herm_batch(rng, nk, nb, scale=1.5):
     a = ki.random_blocks(rng, (nk, nb, nb), scale)
     return 0.5 * (a + np.conj(np.swapaxes(a, 1, 2)))

@@ -441,3 +441,65 @@ def test_corrector_tolerance_counts_follow_the_change():
         runs.append(o.iterations())
     assert set(runs[1][1:].tolist()) == {3, 4}
     assert np.all(runs[0] <= runs[1]) and np.all(runs[1] <= runs[2])
+
+
+@pytest.mark.parametrize("nb,nk", [(2, 3), (3, 2)])
+def test_gregory_collision_integral_converges_at_fourth_order(nb, nk):
+    """The Gregory weights against exact integrals of the same exponential
+    histories as the trapezoid pin: columns j >= 2 and the first integral use
+    rules exact for cubics, so their error falls ~16x per halving of dt; the
+    column j = 1 (a single trapezoid panel) falls ~8x."""
+    rng = np.random.default_rng(nb * 10 + nk + 7)
+    gl = np.stack([_antiherm(rng, nb) for _ in range(nk)])
+    gg = np.stack([_antiherm(rng, nb) for _ in range(nk)])
+    sl = ki.random_blocks(rng, (nk, nb, nb))
+    sg = ki.random_blocks(rng, (nk, nb, nb))
+    alpha, beta, T = 1.7, -0.6, 2.0
+    kappa = alpha - beta
+
+    def F(t):
+        return (np.exp(1j * kappa * t) - 1) / (1j * kappa)
+
+    errs_hi, errs_1 = [], []
+    for n in (20, 40):
+        dt = T / n
+        tri = [(i, j) for i in range(n + 1) for j in range(i + 1)]
+        Hl = np.stack([gl * np.exp(-1j * beta * (i - j) * dt) for i, j in tri])
+        Hg = np.stack([gg * np.exp(-1j * beta * (i - j) * dt) for i, j in tri])
+        Sl = np.stack([sl * np.exp(-1j * alpha * (n - l) * dt) for l in range(n + 1)])
+        Sg = np.stack([sg * np.exp(-1j * alpha * (n - l) * dt) for l in range(n + 1)])
+        Il, Ig = oracle.collision_row(nb, nk, n, dt, Hl, Hg, Sl, Sg, quadrature=1)
+        t = n * dt
+        e_hi = e_1 = 0.0
+        for j in range(n + 1):
+            tp = j * dt
+            ph = np.exp(-1j * alpha * t + 1j * beta * tp)
+            for I, g, s in ((Il, gl, sl), (Ig, gg, sg)):
+                err = np.abs(I[j] - ph * ((sg - sl) @ g * F(t) + s @ (gl - gg) * F(tp))).max()
+                if j == 1:
+                    e_1 = max(e_1, err)
+                elif j != 1:
+                    e_hi = max(e_hi, err)
+        errs_hi.append(e_hi)
+        errs_1.append(e_1)
+    assert 13 < errs_hi[0] / errs_hi[1] < 19, errs_hi
+    assert 6.5 < errs_1[0] / errs_1[1] < 9.5, errs_1
+
+
+def test_gregory_weights_integrate_cubics_exactly():
+    """I^< of a history whose integrands are cubic in the memory time: every rule
+    with m >= 2 nodes-1 is exact (Gregory, Simpson, Simpson 3/8, Boole)."""
+    nb, nk, dt = 1, 1, 0.3
+    for n in range(2, 9):
+        c3 = lambda t: 0.5 - 1.1 * t + 0.7 * t ** 2 + 0.2 * t ** 3
+        tri = [(i, j) for i in range(n + 1) for j in range(i + 1)]
+        # G^<(l, j) = i (for every l, j: its adjoint image is also i), G^> = 0
+        Hl = np.full((len(tri), nk, nb, nb), 1j)
+        Hg = np.zeros_like(Hl)
+        Sl = np.zeros((n + 1, nk, nb, nb), complex)
+        Sg = np.stack([np.full((nk, nb, nb), c3(l * dt)) for l in range(n + 1)])
+        Il, _ = oracle.collision_row(nb, nk, n, dt, Hl, Hg, Sl, Sg, quadrature=1)
+        T = n * dt
+        exact = 1j * (0.5 * T - 1.1 * T ** 2 / 2 + 0.7 * T ** 3 / 3 + 0.2 * T ** 4 / 4)
+        # j = 0: only the first integral; I^<(n, 0) = int_0^T (S^> - S^<) G^< = i int c3
+        assert abs(Il[0][0, 0, 0] - exact) < 1e-13, (n, Il[0][0, 0, 0], exact)

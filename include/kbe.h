@@ -158,6 +158,16 @@ kbe_status kbe_set_dipole(kbe_handle *h, int len, const double *E, const double 
  * correlations). Clears a sticky error. Requires kbe_set_hamiltonian. */
 kbe_status kbe_reset(kbe_handle *h);
 
+/* Graph replay of kbe_step (enable != 0; off by default): the first
+ * kbe_step(h, k) from a given row captures the kernels of those k steps into a
+ * CUDA graph on the handle's stream, instantiates it and launches it; a later
+ * call from the same row with the same k (e.g. after kbe_reset) launches the
+ * instantiated graph, with no per-kernel launch cost. Results are identical to
+ * the ordinary path. Any kbe_set_* call drops the cached graphs (captured
+ * kernels carry the inputs by value). Needs a stream other than the legacy
+ * default stream (otherwise steps run ungraphed); profiled steps run ungraphed. */
+kbe_status kbe_set_graphs(kbe_handle *h, int enable);
+
 /* Corrector passes run at each step 0..current (host int [n+1]; entry 0 is 0):
  * n_corr everywhere when corr_tol = 0. Synchronises. */
 kbe_status kbe_corrector_iterations(kbe_handle *h, int *out);

@@ -12,7 +12,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -47,6 +49,7 @@ struct kbe_handle {
   void *coef = nullptr;        // sweep workspace: coefficient rows + l-split partial sums
   double2 *Ip = nullptr;       // I row n-1
   double2 *Ic = nullptr;       // I row n
+  double2 *Ip0 = nullptr, *Ic0 = nullptr;   // their order after kbe_reset
   double2 *Sig = nullptr;      // Sigma row
   double2 *work = nullptr;     // Sigma scratch
   double2 *U = nullptr, *V = nullptr, *hk = nullptr;   // step propagators and h, per k
@@ -66,6 +69,11 @@ struct kbe_handle {
   bool ham_set = false;
   kbe_status sticky = KBE_OK;
   std::string err;
+
+  // graph replay of kbe_step (kbe_set_graphs): one instantiated graph per
+  // (first row, step count, order of the I ring), valid for the current inputs
+  bool graphs = false;
+  std::map<std::tuple<int, int, int>, cudaGraphExec_t> gcache;
 
   // reverse mode: one device arena, allocated by the first kbe_backward
   void *adj = nullptr;
@@ -133,7 +141,13 @@ cudaError_t dalloc(kbe_handle *h, T **p, size_t count) {
   return e;
 }
 
+void drop_graphs(kbe_handle *h) {
+  for (auto &kv : h->gcache) cudaGraphExecDestroy(kv.second);
+  h->gcache.clear();
+}
+
 void free_all(kbe_handle *h) {
+  drop_graphs(h);
   void *ptrs[] = {h->H, h->Wrow[0], h->Wrow[1], h->coef, h->Ip, h->Ic, h->Sig, h->work, h->U, h->V,
                   h->hk, h->rho, h->obs, h->nkb, h->status, h->d_hopR, h->d_hopT, h->d_U,
                   h->d_dipM, h->adj, h->d_skip, h->d_maxdiff, h->d_iters};
@@ -539,6 +553,49 @@ kbe_status backward_step(kbe_handle *h, const AdjPtrs &P, int n, int nc, double2
 
 #undef KBE_TRY
 
+// kbe_step through an instantiated graph: the first call for a given (row,
+// count, I-ring order) captures the ordinary enqueue path on the handle's
+// stream (nothing runs while capturing) and instantiates it; later calls with
+// the same key replay it and only advance the host-side state.
+kbe_status step_graph(kbe_handle *h, int nsteps) {
+  const auto key = std::make_tuple(h->n, nsteps, h->Ip == h->Ip0 ? 0 : 1);
+  auto it = h->gcache.find(key);
+  if (it == h->gcache.end()) {
+    cudaError_t e = kbe::dft_prepare(h->mesh.L0, h->mesh.L1);
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph prepare");
+    const int n0 = h->n;
+    double2 *ip = h->Ip, *ic = h->Ic;
+    e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph capture");
+    kbe_status s = KBE_OK;
+    for (int i = 0; i < nsteps && s == KBE_OK; ++i) s = one_step(h);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(h->stream, &graph);
+    // the capture only recorded: roll the host state back, then replay below
+    h->n = n0;
+    h->Ip = ip;
+    h->Ic = ic;
+    if (s != KBE_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      h->sticky = KBE_OK;
+      return s != KBE_OK ? s : cuda_fail(h, e, "graph capture");
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
+    it = h->gcache.emplace(key, exec).first;
+  }
+  cudaError_t e = cudaGraphLaunch(it->second, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+  for (int i = 0; i < nsteps; ++i) {   // the host-side state one_step keeps
+    std::swap(h->Ip, h->Ic);
+    h->n += 1;
+  }
+  return KBE_OK;
+}
+
 kbe_status check_device_status(kbe_handle *h) {
   int st = 0;
   cudaError_t e = cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
@@ -648,6 +705,8 @@ kbe_status kbe_create(const kbe_config *cfg, void *stream, kbe_handle **out) {
   cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
   cudaMemsetAsync(h->rho, 0, sizeof(double2) * (T + 2) * h->nb2, h->stream);
   cudaMemsetAsync(h->d_iters, 0, sizeof(int) * (T + 1), h->stream);
+  h->Ip0 = h->Ip;
+  h->Ic0 = h->Ic;
   *out = h;
   return KBE_OK;
 }
@@ -662,6 +721,8 @@ kbe_status kbe_destroy(kbe_handle *h) {
 
 kbe_status kbe_set_hamiltonian(kbe_handle *h, int nhop, const int *R, const double *t) {
   if (!h) return KBE_ERR_ARG;
+  cudaStreamSynchronize(h->stream);
+  drop_graphs(h);   // captured kernels carry the old inputs
   if (nhop < 1 || nhop > 4096 || !R || !t) return fail(h, KBE_ERR_ARG, "set_hamiltonian: bad arguments");
   for (size_t i = 0; i < (size_t)nhop * h->nb2 * 2; ++i)
     if (!std::isfinite(t[i])) return fail(h, KBE_ERR_NONFINITE, "set_hamiltonian: non-finite hopping");
@@ -690,6 +751,8 @@ kbe_status kbe_set_hamiltonian(kbe_handle *h, int nhop, const int *R, const doub
 
 kbe_status kbe_set_interaction(kbe_handle *h, int len, const double *U, const double *v) {
   if (!h) return KBE_ERR_ARG;
+  cudaStreamSynchronize(h->stream);
+  drop_graphs(h);   // captured kernels carry the old inputs
   if (!U || (len != 1 && len < h->cfg.nt_max + 1))
     return fail(h, KBE_ERR_ARG, "set_interaction: need 1 or nt_max+1 samples of U");
   for (int i = 0; i < len; ++i)
@@ -718,6 +781,8 @@ kbe_status kbe_set_interaction(kbe_handle *h, int len, const double *U, const do
 
 kbe_status kbe_set_drive(kbe_handle *h, int len, const double *A, const double *dir) {
   if (!h) return KBE_ERR_ARG;
+  cudaStreamSynchronize(h->stream);
+  drop_graphs(h);   // captured kernels carry the old inputs
   if (len < 0) return fail(h, KBE_ERR_ARG, "set_drive: negative length");
   if (A && len > 0) {
     for (int i = 0; i < len; ++i)
@@ -737,6 +802,8 @@ kbe_status kbe_set_drive(kbe_handle *h, int len, const double *A, const double *
 
 kbe_status kbe_set_dipole(kbe_handle *h, int len, const double *E, const double *M) {
   if (!h) return KBE_ERR_ARG;
+  cudaStreamSynchronize(h->stream);
+  drop_graphs(h);   // captured kernels carry the old inputs
   if (len < 0 || (E && len > 0 && !M)) return fail(h, KBE_ERR_ARG, "set_dipole: bad arguments");
   if (!E || len == 0) {
     h->dipE.clear();
@@ -762,6 +829,8 @@ kbe_status kbe_reset(kbe_handle *h) {
   if (e != cudaSuccess) return cuda_fail(h, e, "reset sync");
   h->sticky = KBE_OK;
   cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
+  h->Ip = h->Ip0;   // a fixed order, so that a replayed graph sees the pointers it captured
+  h->Ic = h->Ic0;
   cudaMemsetAsync(h->Ip, 0, sizeof(double2) * 2 * h->blk, h->stream);
   cudaMemsetAsync(h->Ic, 0, sizeof(double2) * 2 * h->blk, h->stream);
   e = kbe::launch_init_state(h->mesh, hop_table(h), h->cfg.beta, h->cfg.mu, frow(h, 0), h->status, h->stream);
@@ -785,10 +854,20 @@ kbe_status kbe_step(kbe_handle *h, int nsteps) {
   if (h->n < 0) return fail(h, KBE_ERR_STATE, "step: call kbe_reset first");
   if (nsteps < 0) return fail(h, KBE_ERR_ARG, "step: negative count");
   if (h->n + nsteps > h->cfg.nt_max) return fail(h, KBE_ERR_STATE, "step: past nt_max");
+  if (h->graphs && !h->prof && h->stream != nullptr && nsteps > 0) return step_graph(h, nsteps);
   for (int i = 0; i < nsteps; ++i) {
     kbe_status s = one_step(h);
     if (s != KBE_OK) return s;
   }
+  return KBE_OK;
+}
+
+kbe_status kbe_set_graphs(kbe_handle *h, int enable) {
+  if (!h) return KBE_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_graphs");
+  drop_graphs(h);
+  h->graphs = enable != 0;
   return KBE_OK;
 }
 
@@ -900,7 +979,7 @@ kbe_status kbe_corrector_iterations(kbe_handle *h, int *out) {
 
 kbe_status kbe_profile_enable(kbe_handle *h, int enable) {
   if (!h) return KBE_ERR_ARG;
-  cudaStreamSynchronize(h->stream);
+  cudaStreamSynchronize(h->stream);   // (profiled steps run without graphs)
   h->prof = enable != 0;
   h->ev_used = 0;
   h->bev_used = 0;

@@ -94,6 +94,8 @@ enum : int { kDevOk = 0, kDevNonFinite = 1, kDevEigNoConv = 2, kDevAdjUnsupporte
 
 // ---- kernels launch wrappers (return cudaGetLastError()) ------------------
 // a1 self-energy row
+// raises the DFT kernel's shared-memory limit for an L0 x L1 mesh (host side)
+cudaError_t dft_prepare(int L0, int L1);
 // out[arr] = scale * DFT_sign(in[arr]) for narr arrays of n_k points (added
 // to out when accumulate)
 cudaError_t launch_dft_rows(const double2 *in, double2 *out, long narr, int L0, int L1, int sign,

@@ -200,18 +200,33 @@ cudaError_t products_nb(const Mesh &m, const VMat &vm, int n, double Un, const d
 
 }  // namespace
 
-cudaError_t launch_dft_rows(const double2 *in, double2 *out, long narr, int L0, int L1, int sign,
-                            double scale, cudaStream_t st, bool accumulate, const int *skip) {
-  if (narr <= 0) return cudaSuccess;
-  const int nk = L0 * L1;
-  const size_t smem = sizeof(double2) * (2 * (size_t)nk + L0 + L1);
+namespace {
+size_t dft_smem_bytes(int L0, int L1) {
+  return sizeof(double2) * (2 * (size_t)L0 * L1 + L0 + L1);
+}
+}  // namespace
+
+// raise the DFT kernel's dynamic shared-memory limit for this mesh (a host-side
+// attribute, done before any stream capture that launches it)
+cudaError_t dft_prepare(int L0, int L1) {
   static size_t attr_bytes = 48 * 1024;  // default opt-in limit
+  const size_t smem = dft_smem_bytes(L0, L1);
   if (smem > attr_bytes) {
     cudaError_t e = cudaFuncSetAttribute(dft_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     attr_bytes = smem;
   }
+  return cudaSuccess;
+}
+
+cudaError_t launch_dft_rows(const double2 *in, double2 *out, long narr, int L0, int L1, int sign,
+                            double scale, cudaStream_t st, bool accumulate, const int *skip) {
+  if (narr <= 0) return cudaSuccess;
+  const int nk = L0 * L1;
+  const size_t smem = dft_smem_bytes(L0, L1);
+  cudaError_t pe = dft_prepare(L0, L1);
+  if (pe != cudaSuccess) return pe;
   int threads = nk >= 256 ? 256 : ((nk + 31) / 32) * 32;
   long blocks = narr < 152L * 8 ? narr : 152L * 8;
   dft_rows_kernel<<<(unsigned)blocks, threads, smem, st>>>(in, out, narr, L0, L1, sign, scale,

@@ -227,7 +227,7 @@ kbe_status evaluate_row(kbe_handle *h, int n, const int *skip = nullptr) {
     h->ev_flops_x[h->ev_used] = sweep_flops_executed(h, n);
     h->ev_bytes[h->ev_used] = sweep_bytes(h, n);
     h->ev_used++;
-    h->stats.launches += 5 + (kbe::sweep_splits(h->mesh, n) > 1 ? 1 : 0);
+    h->stats.launches += 5 + (kbe::sweep_splits(h->mesh, n, h->cfg.precision) > 1 ? 1 : 0);
   }
   return KBE_OK;
 }

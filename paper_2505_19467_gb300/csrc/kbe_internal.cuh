@@ -119,7 +119,7 @@ bool sweep_supported(int nb);
 bool precision_supported(int prec);
 size_t history_elem_bytes(int prec);
 size_t sweep_workspace_bytes(const Mesh &m, int n, int prec);
-int sweep_splits(const Mesh &m, int n);   // CTAs sharing one output's l range
+int sweep_splits(const Mesh &m, int n, int prec);   // CTAs sharing one output's l range
 cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t nblocks, size_t blk,
                         cudaStream_t st, const int *skip = nullptr);
 cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const void *H,

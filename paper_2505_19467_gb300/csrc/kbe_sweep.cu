@@ -43,15 +43,26 @@
 #ifndef KBE_SWEEP_MINB_C64
 #define KBE_SWEEP_MINB_C64 2
 #endif
+#ifndef KBE_SWEEP_MINB_C64X2
+#define KBE_SWEEP_MINB_C64X2 3   // picked by timing (pairs at 2 / 3 CTAs, single k at 2 / 4)
+#endif
+#ifndef KBE_SWEEP_C64_PAIRS
+#define KBE_SWEEP_C64_PAIRS 1   // C64: two consecutive k per thread when n_k is even
+#endif
 
 namespace kbe {
 
 namespace {
 
 // ---------------------------------------------------------------- FP64 ----
+// Every arithmetic form below provides, besides the complex operations, V (the
+// complex values of consecutive k one stored element S carries) and store()
+// (the I^< and I^> outputs of this thread; blkc = the component stride in
+// complex numbers).
 struct ArithF64 {
   using S = double2;   // stored complex
   using A = double2;   // accumulator
+  static constexpr int V = 1;
   static constexpr int kMinBlocks = KBE_SWEEP_MINB_F64;   // CTAs of 256 per SM (register cap)
   static __device__ __forceinline__ void zero(A &a) { a = make_double2(0.0, 0.0); }
   static __device__ __forceinline__ void begin(A &) {}
@@ -64,6 +75,10 @@ struct ArithF64 {
   static __device__ __forceinline__ S scale_w(double f, const S &x) { return c_scale(f, x); }
   static __device__ __forceinline__ S add(const S &x, const S &y) { return c_add(x, y); }
   static __device__ __forceinline__ double2 result(const A &a) { return a; }
+  static __device__ __forceinline__ void store(double2 *o, size_t blkc, const A &p, const A &l, const A &g) {
+    o[0] = c_add(p, l);
+    o[blkc] = c_add(p, g);
+  }
 };
 
 // ---------------------------------------------------------------- DF64 ----
@@ -120,6 +135,7 @@ __device__ __forceinline__ void df_renorm(float &h, float &l) {
 struct ArithDF64 {
   using S = float4;
   using A = float4;
+  static constexpr int V = 1;
   static constexpr int kMinBlocks = KBE_SWEEP_MINB_DF64;
   static __device__ __forceinline__ void zero(A &a) { a = make_float4(0.f, 0.f, 0.f, 0.f); }
   static __device__ __forceinline__ void begin(A &) {}
@@ -161,6 +177,11 @@ struct ArithDF64 {
   static __device__ __forceinline__ double2 result(const A &a) {
     return make_double2((double)a.x + (double)a.y, (double)a.z + (double)a.w);
   }
+  static __device__ __forceinline__ void store(double2 *o, size_t blkc, const A &p, const A &l, const A &g) {
+    const double2 pr = result(p);
+    o[0] = c_add(pr, result(l));
+    o[blkc] = c_add(pr, result(g));
+  }
 };
 
 // ----------------------------------------------------------------- C64 ----
@@ -181,6 +202,7 @@ struct AccC64 {
 struct ArithC64 {
   using S = float2;
   using A = AccC64;
+  static constexpr int V = 1;
   static constexpr int kMinBlocks = KBE_SWEEP_MINB_C64;
   static __device__ __forceinline__ void zero(A &a) { a.sum = make_float4(0.f, 0.f, 0.f, 0.f); }
   static __device__ __forceinline__ void begin(A &a) { a.part = make_float2(0.f, 0.f); }
@@ -203,6 +225,48 @@ struct ArithC64 {
   static __device__ __forceinline__ S add(const S &x, const S &y) { return make_float2(x.x + y.x, x.y + y.y); }
   static __device__ __forceinline__ double2 result(const A &a) {
     return make_double2((double)a.sum.x + (double)a.sum.y, (double)a.sum.z + (double)a.sum.w);
+  }
+  static __device__ __forceinline__ void store(double2 *o, size_t blkc, const A &p, const A &l, const A &g) {
+    const double2 pr = result(p);
+    o[0] = c_add(pr, result(l));
+    o[blkc] = c_add(pr, result(g));
+  }
+};
+
+// C64 with two consecutive k per thread: one 16-byte load carries both
+// complex64 values, halving the load instructions per multiply-add (the C64
+// sweep is bound by load issue, not by the FP32 pipe); same arithmetic as
+// ArithC64 on each half.
+struct AccC64x2 {
+  AccC64 h[2];
+};
+
+struct ArithC64x2 {
+  using S = float4;
+  using A = AccC64x2;
+  static constexpr int V = 2;
+  static constexpr int kMinBlocks = KBE_SWEEP_MINB_C64X2;
+  static __device__ __forceinline__ float2 lo(const S &x) { return make_float2(x.x, x.y); }
+  static __device__ __forceinline__ float2 hi(const S &x) { return make_float2(x.z, x.w); }
+  static __device__ __forceinline__ S join(const float2 &a, const float2 &b) { return make_float4(a.x, a.y, b.x, b.y); }
+  static __device__ __forceinline__ void zero(A &a) { ArithC64::zero(a.h[0]); ArithC64::zero(a.h[1]); }
+  static __device__ __forceinline__ void begin(A &a) { ArithC64::begin(a.h[0]); ArithC64::begin(a.h[1]); }
+  static __device__ __forceinline__ void end(A &a) { ArithC64::end(a.h[0]); ArithC64::end(a.h[1]); }
+  static __device__ __forceinline__ void mac(A &a, const S &x, const S &y) {
+    ArithC64::mac(a.h[0], lo(x), lo(y));
+    ArithC64::mac(a.h[1], hi(x), hi(y));
+  }
+  static __device__ __forceinline__ S sub(const S &x, const S &y) { return join(ArithC64::sub(lo(x), lo(y)), ArithC64::sub(hi(x), hi(y))); }
+  static __device__ __forceinline__ S negconj(const S &x) { return make_float4(-x.x, x.y, -x.z, x.w); }
+  static __device__ __forceinline__ S neg(const S &x) { return make_float4(-x.x, -x.y, -x.z, -x.w); }
+  static __device__ __forceinline__ S scale(float f, const S &x) { return make_float4(f * x.x, f * x.y, f * x.z, f * x.w); }
+  static __device__ __forceinline__ S scale_w(double f, const S &x) { return scale((float)f, x); }
+  static __device__ __forceinline__ S add(const S &x, const S &y) {
+    return make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
+  }
+  static __device__ __forceinline__ void store(double2 *o, size_t blkc, const A &p, const A &l, const A &g) {
+    ArithC64::store(o, blkc, p.h[0], l.h[0], g.h[0]);
+    ArithC64::store(o + 1, blkc, p.h[1], l.h[1], g.h[1]);
   }
 };
 
@@ -339,10 +403,10 @@ __global__ void __launch_bounds__(256, P::kMinBlocks) sweep_kernel(const typenam
                                   accP, accL, accG);
     }
   }
-  const double2 p = P::result(accP);
-  double2 *o = out + ((size_t)blockIdx.z * (n + 1) + j) * 2 * blk + (size_t)ab * nk + k;
-  o[0] = c_add(p, P::result(accL));
-  o[blk] = c_add(p, P::result(accG));
+  // outputs in complex numbers: nk, blk and k above count stored elements S
+  const size_t blkc = blk * P::V;
+  double2 *o = out + ((size_t)blockIdx.z * (n + 1) + j) * 2 * blkc + (size_t)ab * nk * P::V + (size_t)k * P::V;
+  P::store(o, blkc, accP, accL, accG);
 }
 
 // I = sum over the z partial rows (FP64)
@@ -424,9 +488,14 @@ struct SweepShape {
   int threads, lchunk, nz;
 };
 
-SweepShape sweep_shape(const Mesh &m, int n) {
+// V: complex values of consecutive k per thread (the C64 pair form)
+int sweep_width(const Mesh &m, int prec) {
+  return (KBE_SWEEP_C64_PAIRS && prec == KBE_PREC_C64 && m.nk % 2 == 0) ? 2 : 1;
+}
+
+SweepShape sweep_shape(const Mesh &m, int n, int V = 1) {
   SweepShape sh;
-  const long elems = (long)m.nb * m.nb * m.nk;
+  const long elems = (long)m.nb * m.nb * (m.nk / V);
   sh.threads = elems >= 256 ? 256 : (int)((elems + 31) / 32) * 32;
   const long ty = (elems + sh.threads - 1) / sh.threads;
   const long base = (long)(n + 1) * ty;
@@ -443,14 +512,15 @@ SweepShape sweep_shape(const Mesh &m, int n) {
 template <class P, int NB>
 cudaError_t sweep_nb(const Mesh &m, int n, const void *H, const void *Cf, double2 *I, double2 *part,
                      cudaStream_t st, const int *skip, int quad) {
-  const SweepShape sh = sweep_shape(m, n);
+  const SweepShape sh = sweep_shape(m, n, P::V);
   double2 *out = sh.nz > 1 ? part : I;
+  const int nkS = m.nk / P::V;   // stored elements per (a, b) array
   if (quad == kQuadGregory)
     sweep_kernel<P, NB, kQuadGregory><<<sh.grid, sh.threads, 0, st>>>(
-        (const typename P::S *)H, (const typename P::S *)Cf, out, n, m.nk, sh.lchunk, skip);
+        (const typename P::S *)H, (const typename P::S *)Cf, out, n, nkS, sh.lchunk, skip);
   else
     sweep_kernel<P, NB, kQuadTrapezoid><<<sh.grid, sh.threads, 0, st>>>(
-        (const typename P::S *)H, (const typename P::S *)Cf, out, n, m.nk, sh.lchunk, skip);
+        (const typename P::S *)H, (const typename P::S *)Cf, out, n, nkS, sh.lchunk, skip);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || sh.nz == 1) return e;
   const size_t count = (size_t)(n + 1) * 2 * m.nb * m.nb * m.nk;
@@ -463,6 +533,7 @@ cudaError_t sweep_prec(const Mesh &m, int n, int prec, const void *H, const void
                        double2 *part, cudaStream_t st, const int *skip, int quad) {
   if (prec == KBE_PREC_FP64) return sweep_nb<ArithF64, NB>(m, n, H, Cf, I, part, st, skip, quad);
   if (prec == KBE_PREC_DF64) return sweep_nb<ArithDF64, NB>(m, n, H, Cf, I, part, st, skip, quad);
+  if (sweep_width(m, prec) == 2) return sweep_nb<ArithC64x2, NB>(m, n, H, Cf, I, part, st, skip, quad);
   return sweep_nb<ArithC64, NB>(m, n, H, Cf, I, part, st, skip, quad);
 }
 
@@ -489,7 +560,7 @@ size_t sweep_workspace_bytes(const Mesh &m, int n, int prec) {
   coef = (coef + 255) / 256 * 256;
   size_t part = 0;
   for (int r = 0; r <= n; ++r) {   // the largest partial buffer over rows 0..n
-    const SweepShape sh = sweep_shape(m, r);
+    const SweepShape sh = sweep_shape(m, r, sweep_width(m, prec));
     if (sh.nz > 1) {
       const size_t b = (size_t)sh.nz * (r + 1) * 2 * blk * sizeof(double2);
       if (b > part) part = b;
@@ -498,7 +569,7 @@ size_t sweep_workspace_bytes(const Mesh &m, int n, int prec) {
   return coef + part;
 }
 
-int sweep_splits(const Mesh &m, int n) { return sweep_shape(m, n).nz; }
+int sweep_splits(const Mesh &m, int n, int prec) { return sweep_shape(m, n, sweep_width(m, prec)).nz; }
 
 cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t nblocks, size_t blk,
                         cudaStream_t st, const int *skip) {

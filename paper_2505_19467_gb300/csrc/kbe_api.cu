@@ -562,6 +562,7 @@ kbe_status step_graph(kbe_handle *h, int nsteps) {
   auto it = h->gcache.find(key);
   if (it == h->gcache.end()) {
     cudaError_t e = kbe::dft_prepare(h->mesh.L0, h->mesh.L1);
+    if (e == cudaSuccess) e = kbe::sweep_prepare(h->cfg.nb);
     if (e != cudaSuccess) return cuda_fail(h, e, "graph prepare");
     const int n0 = h->n;
     double2 *ip = h->Ip, *ic = h->Ic;

@@ -120,6 +120,7 @@ bool precision_supported(int prec);
 size_t history_elem_bytes(int prec);
 size_t sweep_workspace_bytes(const Mesh &m, int n, int prec);
 int sweep_splits(const Mesh &m, int n, int prec);   // CTAs sharing one output's l range
+cudaError_t sweep_prepare(int nb);   // kernel attributes, host side (before stream capture)
 cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t nblocks, size_t blk,
                         cudaStream_t st, const int *skip = nullptr);
 cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const void *H,

@@ -481,6 +481,200 @@ __global__ void coef_kernel(int prec, const double2 *__restrict__ Sig, void *__r
   }
 }
 
+
+// ------------------------------------------------ C64, staged through smem --
+// The C64 sweep is bound by load latency, not by the FP32 pipe. This form
+// stages every memory-time node's operands in shared memory ahead of use: a
+// CTA of 128 threads owns KT consecutive k for all outputs (a, b) of one
+// column j, and for each node l copies the three coefficient rows (C1, C2^<,
+// C3 for all (a, c)) and the block X(l, j) (G^< and dG, both orientations
+// come from the same stored block) for its k range into a ring of kStages
+// buffers with 16-byte cp.async copies, kStages - 1 nodes ahead of the
+// arithmetic (zero-filled past n_k). Each thread keeps NBB <= 4 outputs
+// (a, b..b+NBB) of both components in registers, so one shared-memory load
+// of a coefficient feeds NBB multiply-adds. The waits are cp.async group
+// waits and barriers only. Same C64 arithmetic as ArithC64 (FP32 products,
+// TwoSum-compensated sum over the nodes).
+#ifndef KBE_STAGED_STAGES
+#define KBE_STAGED_STAGES 3   // timed: 4 stages (2 CTAs/SM) 9 % slower, 2 stages no better
+#endif
+#ifndef KBE_STAGED_MINB
+#define KBE_STAGED_MINB 3
+#endif
+#ifndef KBE_STAGED_TARGET
+#define KBE_STAGED_TARGET 12  // CTAs per SM the l-split aims for (timed: 3, 6, 12 within 3 %)
+#endif
+constexpr int kStagedThreads = 128;
+constexpr int kStages = KBE_STAGED_STAGES;
+
+__host__ __device__ constexpr int staged_nbb(int NB) { return NB < 4 ? NB : 4; }
+__host__ __device__ constexpr int staged_kt(int NB) { return kStagedThreads / (NB * (NB / staged_nbb(NB))); }
+__host__ __device__ constexpr size_t staged_stage_elems(int NB) { return (size_t)5 * NB * NB * staged_kt(NB); }
+
+bool staged_supported(int nb) { return nb == 1 || nb == 2 || nb == 4 || nb == 8 || nb == 16; }
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? 16 : 0;   // 0: zero-fill, nothing read
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// copy node l's operands for k in [k0, k0 + KT) into one stage buffer:
+// [q][a][c][kk] coefficient rows (q = C1, C2^<, C3), then [x][r][s][kk] of the
+// stored block (x = G^<, dG), as float2 pairs (16 bytes)
+template <int NB>
+__device__ __forceinline__ void staged_issue(float2 *st, const float2 *__restrict__ Cf,
+                                             const float2 *__restrict__ H, int l, size_t tblk, int k0,
+                                             int nk) {
+  constexpr int KT = staged_kt(NB), NB2 = NB * NB, CH = KT / 2;   // 16-byte chunks per row
+  const size_t blk = (size_t)NB2 * nk;
+  const float2 *csrc = Cf + (size_t)l * 3 * blk;
+  const float2 *hsrc = H + tblk * 2 * blk;
+  constexpr int nrow = 5 * NB2;                                     // 3 NB^2 + 2 NB^2 rows
+  for (int e = threadIdx.x; e < nrow * CH; e += kStagedThreads) {
+    const int row = e / CH, ch = e - row * CH;
+    const int kk = 2 * ch, kg = k0 + kk;
+    const bool valid = kg < nk;   // n_k even: a chunk is wholly inside or wholly past the end
+    const float2 *src = row < 3 * NB2 ? csrc + (size_t)row * nk : hsrc + (size_t)(row - 3 * NB2) * nk;
+    cp_async16(st + (size_t)row * KT + kk, valid ? src + kg : src, valid);
+  }
+}
+
+// one node on the staged operands; KIND 0: above the output (stored block,
+// C1 G^< and -C1 dG); 1: stored diagonal block; 2: adjoint block (-X(j, l)^+);
+// kinds 1 and 2 take the node weight f (1: the plain form, else f C2^< and
+// f C3 + (f - 1) C1)
+template <int NB, int KIND>
+__device__ __forceinline__ void staged_node(const float2 *st, int kk, int a, int b0, float f, AccC64 *accP,
+                                            AccC64 *accL, AccC64 *accG) {
+  constexpr int KT = staged_kt(NB), NBB = staged_nbb(NB), NB2 = NB * NB;
+  const float2 *c1 = st + (size_t)(0 * NB2 + a * NB) * KT + kk;
+  const float2 *c2 = st + (size_t)(1 * NB2 + a * NB) * KT + kk;
+  const float2 *c3 = st + (size_t)(2 * NB2 + a * NB) * KT + kk;
+  const float2 *gl = st + (size_t)(3 * NB2) * KT + kk;
+  const float2 *dg = st + (size_t)(4 * NB2) * KT + kk;
+#pragma unroll
+  for (int q = 0; q < NBB; ++q) {
+    ArithC64::begin(accP[q]);
+    ArithC64::begin(accL[q]);
+    ArithC64::begin(accG[q]);
+  }
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    const float2 A1 = c1[(size_t)c * KT];
+    float2 K2 = make_float2(0.f, 0.f), K3 = make_float2(0.f, 0.f);
+    if (KIND != 0) {
+      K2 = c2[(size_t)c * KT];
+      K3 = c3[(size_t)c * KT];
+      if (f != 1.0f) {
+        K3 = make_float2(f * K3.x + (f - 1.0f) * A1.x, f * K3.y + (f - 1.0f) * A1.y);
+        K2 = make_float2(f * K2.x, f * K2.y);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NBB; ++q) {
+      const int b = b0 + q;
+      float2 G, D;
+      if (KIND == 2) {   // X(l, j)_cb = -conj(G(j, l)_bc)
+        const float2 g = gl[(size_t)(b * NB + c) * KT], d = dg[(size_t)(b * NB + c) * KT];
+        G = make_float2(-g.x, g.y);
+        D = make_float2(-d.x, d.y);
+      } else {
+        G = gl[(size_t)(c * NB + b) * KT];
+        D = dg[(size_t)(c * NB + b) * KT];
+      }
+      ArithC64::mac(accP[q], A1, G);
+      if (KIND == 0) {
+        ArithC64::mac(accG[q], make_float2(-A1.x, -A1.y), D);
+      } else {
+        ArithC64::mac(accL[q], K2, D);
+        ArithC64::mac(accG[q], K3, D);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NBB; ++q) {
+    ArithC64::end(accP[q]);
+    ArithC64::end(accL[q]);
+    ArithC64::end(accG[q]);
+  }
+}
+
+// grid: x = k tiles of KT, y = output column j (0..n), z = split of the l range
+template <int NB, int QUAD>
+__global__ void __launch_bounds__(kStagedThreads, KBE_STAGED_MINB)
+    sweep_c64_staged_kernel(const float2 *__restrict__ H, const float2 *__restrict__ Cf, double2 *__restrict__ out,
+                            int n, int nk, int lchunk, const int *__restrict__ skip) {
+  if (skip && *skip) return;
+  extern __shared__ float4 staged_smem4[];
+  float2 *smem = reinterpret_cast<float2 *>(staged_smem4);
+  constexpr int KT = staged_kt(NB), NBB = staged_nbb(NB);
+  const int tid = threadIdx.x;
+  const int kk = tid % KT, rest = tid / KT;
+  const int a = rest % NB, b0 = (rest / NB) * NBB;
+  const int k0 = blockIdx.x * KT;
+  const int j = blockIdx.y;
+  const int l0 = blockIdx.z * lchunk;
+  const int l1 = min(n + 1, l0 + lchunk);
+  const int nodes = max(l1 - l0, 0);
+  AccC64 accP[NBB], accL[NBB], accG[NBB];
+#pragma unroll
+  for (int q = 0; q < NBB; ++q) {
+    ArithC64::zero(accP[q]);
+    ArithC64::zero(accL[q]);
+    ArithC64::zero(accG[q]);
+  }
+  // node i is l = l0 + i; its block is stored at (l, j) when l >= j, else (j, l)
+  auto tblk = [&](int l) -> size_t { return l >= j ? tri(l, j) : tri(j, l); };
+#pragma unroll
+  for (int s = 0; s < kStages - 1; ++s) {
+    if (s < nodes) staged_issue<NB>(smem + (size_t)s * staged_stage_elems(NB), Cf, H, l0 + s, tblk(l0 + s), k0, nk);
+    cp_async_commit();
+  }
+  for (int i = 0; i < nodes; ++i) {
+    const int ahead = i + kStages - 1;
+    if (ahead < nodes)
+      staged_issue<NB>(smem + (size_t)(ahead % kStages) * staged_stage_elems(NB), Cf, H, l0 + ahead, tblk(l0 + ahead),
+                       k0, nk);
+    cp_async_commit();
+    cp_async_wait<kStages - 1>();   // this thread's copies of node i have landed
+    __syncthreads();                // and everybody else's
+    const float2 *st = smem + (size_t)(i % kStages) * staged_stage_elems(NB);
+    const int l = l0 + i;
+    if (l > j || j == 0) {
+      staged_node<NB, 0>(st, kk, a, b0, 1.0f, accP, accL, accG);
+    } else {
+      const float f = (float)quad_omega(QUAD, j, l);
+      if (l == j) staged_node<NB, 1>(st, kk, a, b0, f, accP, accL, accG);
+      else staged_node<NB, 2>(st, kk, a, b0, f, accP, accL, accG);
+    }
+    __syncthreads();                // the stage may be refilled next iteration
+  }
+  const int k = k0 + kk;
+  if (k >= nk) return;
+  const size_t blk = (size_t)NB * NB * nk;
+  double2 *o = out + ((size_t)blockIdx.z * (n + 1) + j) * 2 * blk + k;
+#pragma unroll
+  for (int q = 0; q < NBB; ++q) ArithC64::store(o + (size_t)(a * NB + b0 + q) * nk, blk, accP[q], accL[q], accG[q]);
+}
+
+template <int NB>
+cudaError_t staged_prepare() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  const int bytes = (int)(kStages * staged_stage_elems(NB) * sizeof(float2));
+  cudaError_t e = cudaFuncSetAttribute(sweep_c64_staged_kernel<NB, kQuadTrapezoid>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sweep_c64_staged_kernel<NB, kQuadGregory>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             bytes);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
 unsigned grid_for(size_t count) {
   size_t b = (count + 255) / 256;
   return (unsigned)(b < 152 * 64 ? (b ? b : 1) : 152 * 64);
@@ -495,9 +689,48 @@ struct SweepShape {
   int threads, lchunk, nz;
 };
 
+#ifndef KBE_SWEEP_C64_STAGED
+#define KBE_SWEEP_C64_STAGED 1   // C64: the shared-memory staged sweep where it applies
+#endif
+
+// the C64 staged form: N_b in {4, 8, 16} and n_k even (16-byte copies); at
+// N_b <= 2 a node is too little arithmetic for two barriers (timed: the
+// paper's two-band shape 5.56 ms staged against 5.23 ms for the pair form)
+bool use_staged(const Mesh &m, int prec) {
+  return KBE_SWEEP_C64_STAGED && prec == KBE_PREC_C64 && staged_supported(m.nb) && m.nb >= 4 &&
+         m.nk % 2 == 0;
+}
+
 // V: complex values of consecutive k per thread (the C64 pair form)
 int sweep_width(const Mesh &m, int prec) {
   return (KBE_SWEEP_C64_PAIRS && prec == KBE_PREC_C64 && m.nk % 2 == 0) ? 2 : 1;
+}
+
+int staged_kt_of(int nb) {
+  switch (nb) {
+    case 1: return staged_kt(1);
+    case 2: return staged_kt(2);
+    case 4: return staged_kt(4);
+    case 8: return staged_kt(8);
+    default: return staged_kt(16);
+  }
+}
+
+// l-split of the staged form: enough CTAs for ~3 resident per SM, twice over
+SweepShape staged_shape(const Mesh &m, int n) {
+  SweepShape sh;
+  sh.threads = kStagedThreads;
+  const int kt = staged_kt_of(m.nb);
+  const long tx = (m.nk + kt - 1) / kt;
+  const long base = (long)(n + 1) * tx;
+  long nz = (152L * KBE_STAGED_TARGET + base - 1) / base;
+  if (nz > n + 1) nz = n + 1;
+  if (nz > 2 + 1024 / (n + 1)) nz = 2 + 1024 / (n + 1);
+  if (nz < 1) nz = 1;
+  sh.lchunk = (int)((n + 1 + nz - 1) / nz);
+  sh.nz = (int)((n + 1 + sh.lchunk - 1) / sh.lchunk);
+  sh.grid = dim3((unsigned)tx, n + 1, (unsigned)sh.nz);
+  return sh;
 }
 
 SweepShape sweep_shape(const Mesh &m, int n, int V = 1) {
@@ -536,8 +769,32 @@ cudaError_t sweep_nb(const Mesh &m, int n, const void *H, const void *Cf, double
 }
 
 template <int NB>
+cudaError_t sweep_staged(const Mesh &m, int n, const void *H, const void *Cf, double2 *I, double2 *part,
+                         cudaStream_t st, const int *skip, int quad) {
+  cudaError_t e = staged_prepare<NB>();
+  if (e != cudaSuccess) return e;
+  const SweepShape sh = staged_shape(m, n);
+  double2 *out = sh.nz > 1 ? part : I;
+  const size_t smem = kStages * staged_stage_elems(NB) * sizeof(float2);
+  if (quad == kQuadGregory)
+    sweep_c64_staged_kernel<NB, kQuadGregory><<<sh.grid, sh.threads, smem, st>>>(
+        (const float2 *)H, (const float2 *)Cf, out, n, m.nk, sh.lchunk, skip);
+  else
+    sweep_c64_staged_kernel<NB, kQuadTrapezoid><<<sh.grid, sh.threads, smem, st>>>(
+        (const float2 *)H, (const float2 *)Cf, out, n, m.nk, sh.lchunk, skip);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || sh.nz == 1) return e;
+  const size_t count = (size_t)(n + 1) * 2 * m.nb * m.nb * m.nk;
+  reduce_partials_kernel<<<grid_for(count), 256, 0, st>>>(part, I, count, sh.nz, skip);
+  return cudaGetLastError();
+}
+
+template <int NB>
 cudaError_t sweep_prec(const Mesh &m, int n, int prec, const void *H, const void *Cf, double2 *I,
                        double2 *part, cudaStream_t st, const int *skip, int quad) {
+  if constexpr (NB == 1 || NB == 2 || NB == 4 || NB == 8 || NB == 16) {
+    if (use_staged(m, prec)) return sweep_staged<NB>(m, n, H, Cf, I, part, st, skip, quad);
+  }
   if (prec == KBE_PREC_FP64) return sweep_nb<ArithF64, NB>(m, n, H, Cf, I, part, st, skip, quad);
   if (prec == KBE_PREC_DF64) return sweep_nb<ArithDF64, NB>(m, n, H, Cf, I, part, st, skip, quad);
   if (sweep_width(m, prec) == 2) return sweep_nb<ArithC64x2, NB>(m, n, H, Cf, I, part, st, skip, quad);
@@ -567,7 +824,7 @@ size_t sweep_workspace_bytes(const Mesh &m, int n, int prec) {
   coef = (coef + 255) / 256 * 256;
   size_t part = 0;
   for (int r = 0; r <= n; ++r) {   // the largest partial buffer over rows 0..n
-    const SweepShape sh = sweep_shape(m, r, sweep_width(m, prec));
+    const SweepShape sh = use_staged(m, prec) ? staged_shape(m, r) : sweep_shape(m, r, sweep_width(m, prec));
     if (sh.nz > 1) {
       const size_t b = (size_t)sh.nz * (r + 1) * 2 * blk * sizeof(double2);
       if (b > part) part = b;
@@ -576,7 +833,21 @@ size_t sweep_workspace_bytes(const Mesh &m, int n, int prec) {
   return coef + part;
 }
 
-int sweep_splits(const Mesh &m, int n, int prec) { return sweep_shape(m, n, sweep_width(m, prec)).nz; }
+int sweep_splits(const Mesh &m, int n, int prec) {
+  return use_staged(m, prec) ? staged_shape(m, n).nz : sweep_shape(m, n, sweep_width(m, prec)).nz;
+}
+
+// shared-memory limits of the staged kernels (host side, before any capture)
+cudaError_t sweep_prepare(int nb) {
+  switch (nb) {
+    case 1: return staged_prepare<1>();
+    case 2: return staged_prepare<2>();
+    case 4: return staged_prepare<4>();
+    case 8: return staged_prepare<8>();
+    case 16: return staged_prepare<16>();
+    default: return cudaSuccess;
+  }
+}
 
 cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t nblocks, size_t blk,
                         cudaStream_t st, const int *skip) {

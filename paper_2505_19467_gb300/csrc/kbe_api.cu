@@ -219,7 +219,7 @@ kbe_status evaluate_row(kbe_handle *h, int n, const int *skip = nullptr) {
     cudaEventRecord(h->ev[h->ev_used].first, h->stream);
   }
   e = kbe::launch_sweep(m, n, h->cfg.dt, h->cfg.precision, h->H, h->Sig, h->Ic, h->coef, h->stream, skip,
-                        h->cfg.quadrature);
+                        h->cfg.quadrature, h->status);
   if (e != cudaSuccess) return cuda_fail(h, e, "collision sweep");
   if (timed) {
     cudaEventRecord(h->ev[h->ev_used].second, h->stream);
@@ -609,6 +609,10 @@ kbe_status check_device_status(kbe_handle *h) {
   if (st & kbe::kDevEigNoConv) {
     h->sticky = KBE_ERR_NONFINITE;
     return fail(h, KBE_ERR_NONFINITE, "eigen-solver did not converge (non-finite or huge h)");
+  }
+  if (st & kbe::kDevTimeout) {
+    h->sticky = KBE_ERR_TIMEOUT;
+    return fail(h, KBE_ERR_TIMEOUT, "a staged copy of the collision sweep did not complete (bounded wait)");
   }
   return h->sticky;
 }

@@ -90,7 +90,7 @@ __device__ __forceinline__ double2 c_fnmac(double2 a, double2 b, double2 acc) {
 }
 
 // ---- status word written by kernels (sticky, read by the host) -----------
-enum : int { kDevOk = 0, kDevNonFinite = 1, kDevEigNoConv = 2, kDevAdjUnsupported = 4 };
+enum : int { kDevOk = 0, kDevNonFinite = 1, kDevEigNoConv = 2, kDevAdjUnsupported = 4, kDevTimeout = 8 };
 
 // ---- kernels launch wrappers (return cudaGetLastError()) ------------------
 // a1 self-energy row
@@ -123,9 +123,11 @@ int sweep_splits(const Mesh &m, int n, int prec);   // CTAs sharing one output's
 cudaError_t sweep_prepare(int nb);   // kernel attributes, host side (before stream capture)
 cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t nblocks, size_t blk,
                         cudaStream_t st, const int *skip = nullptr);
+// status (may be NULL): device word that receives kDevTimeout if a staged
+// copy never completes (bounded waits)
 cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const void *H,
                          const double2 *Sig, double2 *I, void *work, cudaStream_t st,
-                         const int *skip = nullptr, int quad = kQuadTrapezoid);
+                         const int *skip = nullptr, int quad = kQuadTrapezoid, int *status = nullptr);
 
 // a3 propagators / initial state / density
 struct HopTable {

@@ -32,6 +32,9 @@
 // C1 = w^(n)_l (S^> - S^<), C2^< = dt S^<, C3 = dt S^> - C1 in the history's
 // storage; the term-2 weights f = w^(j)_l / dt are then exact powers of two
 // (f = 1 inside, 1/2 at l = 0 and l = j, where f C2^> - C1 = (C3 - C1) / 2).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "kbe_internal.cuh"
 
 #ifndef KBE_SWEEP_MINB_F64
@@ -661,6 +664,184 @@ __global__ void __launch_bounds__(kStagedThreads, KBE_STAGED_MINB)
   for (int q = 0; q < NBB; ++q) ArithC64::store(o + (size_t)(a * NB + b0 + q) * nk, blk, accP[q], accL[q], accG[q]);
 }
 
+
+// The same staged sweep with TMA copies: one thread issues, per node, a 3-D
+// tensor copy of the coefficient rows (box 2KT floats x N_b^2 x 3 rows of
+// [l][q][a][c][k]) and a 4-D one of the stored block (box 2KT x N_b^2 x 2
+// components x 1 block of [tri][x][r][s][k]) into the stage, completing on
+// that stage's mbarrier; the hardware zero-fills past n_k. The shared-memory
+// layout is the cp.async form's, so the arithmetic is shared. Every wait on
+// an mbarrier is bounded: past the limit the kernel marks kDevTimeout in the
+// status word and stops after waiting (bounded) for its copies in flight.
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+// true when the phase with this parity has completed; false after the limit
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, int limit) {
+  const unsigned a = smem_addr(bar);
+  for (int it = 0; it < limit; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *tm, int x, int y, int z, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];\n" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *tm, int x, int y, int z, int w,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];\n" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_addr(bar))
+      : "memory");
+}
+
+constexpr int kMbarWaitLimit = 1 << 22;   // try_wait rounds before giving up (far beyond any copy)
+
+template <int NB, int QUAD>
+__global__ void __launch_bounds__(kStagedThreads, KBE_STAGED_MINB)
+    sweep_c64_tma_kernel(const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmH,
+                         double2 *__restrict__ out, int n, int nk, int lchunk, const int *__restrict__ skip,
+                         int *status) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(128) float4 tma_smem4[];
+  __shared__ __align__(8) uint64_t bar[kStages];
+  __shared__ int failed;
+  float2 *smem = reinterpret_cast<float2 *>(tma_smem4);
+  constexpr int KT = staged_kt(NB), NBB = staged_nbb(NB), NB2 = NB * NB;
+  constexpr unsigned kBytesC = 3u * NB2 * KT * sizeof(float2), kBytesH = 2u * NB2 * KT * sizeof(float2);
+  const int tid = threadIdx.x;
+  const int kk = tid % KT, rest = tid / KT;
+  const int a = rest % NB, b0 = (rest / NB) * NBB;
+  const int k0 = blockIdx.x * KT;
+  const int j = blockIdx.y;
+  const int l0 = blockIdx.z * lchunk;
+  const int l1 = min(n + 1, l0 + lchunk);
+  const int nodes = max(l1 - l0, 0);
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+    failed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int i) {   // node i into stage i % kStages (thread 0)
+    const int l = l0 + i, s = i % kStages;
+    const int tb = (int)(l >= j ? tri(l, j) : tri(j, l));
+    float2 *st = smem + (size_t)s * staged_stage_elems(NB);
+    mbar_expect_tx(&bar[s], kBytesC + kBytesH);
+    tma_load_3d(st, &tmC, 2 * k0, 0, 3 * l, &bar[s]);
+    tma_load_4d(st + (size_t)3 * NB2 * KT, &tmH, 2 * k0, 0, 0, tb, &bar[s]);
+  };
+  AccC64 accP[NBB], accL[NBB], accG[NBB];
+#pragma unroll
+  for (int q = 0; q < NBB; ++q) {
+    ArithC64::zero(accP[q]);
+    ArithC64::zero(accL[q]);
+    ArithC64::zero(accG[q]);
+  }
+  if (tid == 0)
+    for (int i = 0; i < kStages - 1 && i < nodes; ++i) issue(i);
+  int issued = min(kStages - 1, nodes);
+  for (int i = 0; i < nodes; ++i) {
+    if (tid == 0 && issued < nodes && issued == i + kStages - 1) {
+      issue(issued);
+    }
+    issued = min(i + kStages, nodes);
+    const int s = i % kStages;
+    if (!mbar_wait(&bar[s], (unsigned)((i / kStages) & 1), kMbarWaitLimit)) failed = 1;
+    __syncthreads();
+    if (failed) {   // a copy did not arrive: flag it, let the in-flight ones land, stop
+      if (tid == 0) {
+        if (status) atomicOr(status, kDevTimeout);
+        for (int q = i; q < issued; ++q)
+          mbar_wait(&bar[q % kStages], (unsigned)((q / kStages) & 1), kMbarWaitLimit);
+      }
+      __syncthreads();
+      return;
+    }
+    const float2 *st = smem + (size_t)s * staged_stage_elems(NB);
+    const int l = l0 + i;
+    if (l > j || j == 0) {
+      staged_node<NB, 0>(st, kk, a, b0, 1.0f, accP, accL, accG);
+    } else {
+      const float f = (float)quad_omega(QUAD, j, l);
+      if (l == j) staged_node<NB, 1>(st, kk, a, b0, f, accP, accL, accG);
+      else staged_node<NB, 2>(st, kk, a, b0, f, accP, accL, accG);
+    }
+    __syncthreads();   // stage s is free for the copy issued next iteration
+  }
+  const int k = k0 + kk;
+  if (k >= nk) return;
+  const size_t blk = (size_t)NB2 * nk;
+  double2 *o = out + ((size_t)blockIdx.z * (n + 1) + j) * 2 * blk + k;
+#pragma unroll
+  for (int q = 0; q < NBB; ++q) ArithC64::store(o + (size_t)(a * NB + b0 + q) * nk, blk, accP[q], accL[q], accG[q]);
+}
+
+// cuTensorMapEncodeTiled from the driver (no link against libcuda)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// tensor maps of the coefficient rows (rows 0..n) and the stored triangle (rows
+// 0..n) of a C64 sweep; false when the driver cannot encode them
+template <int NB>
+bool staged_tensor_maps(const void *Cf, const void *H, int n, int nk, CUtensorMap *tmC, CUtensorMap *tmH) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  constexpr int KT = staged_kt(NB), NB2 = NB * NB;
+  const cuuint64_t row = (cuuint64_t)2 * nk * sizeof(float);   // one (a, c) row of k, bytes
+  {
+    const cuuint64_t dim[3] = {(cuuint64_t)2 * nk, (cuuint64_t)NB2, (cuuint64_t)3 * (n + 1)};
+    const cuuint64_t stride[2] = {row, row * NB2};
+    const cuuint32_t box[3] = {(cuuint32_t)(2 * KT), (cuuint32_t)NB2, 3};
+    const cuuint32_t es[3] = {1, 1, 1};
+    if (enc(tmC, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(Cf), dim, stride, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  {
+    const cuuint64_t ntri = (cuuint64_t)tri(n, n) + 1;
+    const cuuint64_t dim[4] = {(cuuint64_t)2 * nk, (cuuint64_t)NB2, 2, ntri};
+    const cuuint64_t stride[3] = {row, row * NB2, row * NB2 * 2};
+    const cuuint32_t box[4] = {(cuuint32_t)(2 * KT), (cuuint32_t)NB2, 2, 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    if (enc(tmH, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(H), dim, stride, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
+}
+
 template <int NB>
 cudaError_t staged_prepare() {
   static bool done = false;
@@ -671,7 +852,14 @@ cudaError_t staged_prepare() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(sweep_c64_staged_kernel<NB, kQuadGregory>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sweep_c64_tma_kernel<NB, kQuadTrapezoid>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sweep_c64_tma_kernel<NB, kQuadGregory>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             bytes);
   if (e == cudaSuccess) done = true;
+  tensor_map_encoder();   // resolve the driver entry point outside any stream capture
   return e;
 }
 
@@ -689,6 +877,9 @@ struct SweepShape {
   int threads, lchunk, nz;
 };
 
+#ifndef KBE_SWEEP_C64_TMA
+#define KBE_SWEEP_C64_TMA 1      // the staged sweep's copies by TMA (else per-thread cp.async)
+#endif
 #ifndef KBE_SWEEP_C64_STAGED
 #define KBE_SWEEP_C64_STAGED 1   // C64: the shared-memory staged sweep where it applies
 #endif
@@ -770,13 +961,21 @@ cudaError_t sweep_nb(const Mesh &m, int n, const void *H, const void *Cf, double
 
 template <int NB>
 cudaError_t sweep_staged(const Mesh &m, int n, const void *H, const void *Cf, double2 *I, double2 *part,
-                         cudaStream_t st, const int *skip, int quad) {
+                         cudaStream_t st, const int *skip, int quad, int *status) {
   cudaError_t e = staged_prepare<NB>();
   if (e != cudaSuccess) return e;
   const SweepShape sh = staged_shape(m, n);
   double2 *out = sh.nz > 1 ? part : I;
   const size_t smem = kStages * staged_stage_elems(NB) * sizeof(float2);
-  if (quad == kQuadGregory)
+  CUtensorMap tmC, tmH;
+  if (KBE_SWEEP_C64_TMA && staged_tensor_maps<NB>(Cf, H, n, m.nk, &tmC, &tmH)) {
+    if (quad == kQuadGregory)
+      sweep_c64_tma_kernel<NB, kQuadGregory><<<sh.grid, sh.threads, smem, st>>>(tmC, tmH, out, n, m.nk, sh.lchunk,
+                                                                               skip, status);
+    else
+      sweep_c64_tma_kernel<NB, kQuadTrapezoid><<<sh.grid, sh.threads, smem, st>>>(tmC, tmH, out, n, m.nk,
+                                                                                 sh.lchunk, skip, status);
+  } else if (quad == kQuadGregory)
     sweep_c64_staged_kernel<NB, kQuadGregory><<<sh.grid, sh.threads, smem, st>>>(
         (const float2 *)H, (const float2 *)Cf, out, n, m.nk, sh.lchunk, skip);
   else
@@ -791,9 +990,9 @@ cudaError_t sweep_staged(const Mesh &m, int n, const void *H, const void *Cf, do
 
 template <int NB>
 cudaError_t sweep_prec(const Mesh &m, int n, int prec, const void *H, const void *Cf, double2 *I,
-                       double2 *part, cudaStream_t st, const int *skip, int quad) {
+                       double2 *part, cudaStream_t st, const int *skip, int quad, int *status) {
   if constexpr (NB == 1 || NB == 2 || NB == 4 || NB == 8 || NB == 16) {
-    if (use_staged(m, prec)) return sweep_staged<NB>(m, n, H, Cf, I, part, st, skip, quad);
+    if (use_staged(m, prec)) return sweep_staged<NB>(m, n, H, Cf, I, part, st, skip, quad, status);
   }
   if (prec == KBE_PREC_FP64) return sweep_nb<ArithF64, NB>(m, n, H, Cf, I, part, st, skip, quad);
   if (prec == KBE_PREC_DF64) return sweep_nb<ArithDF64, NB>(m, n, H, Cf, I, part, st, skip, quad);
@@ -858,7 +1057,7 @@ cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t nblocks,
 
 cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const void *H,
                          const double2 *Sig, double2 *I, void *work, cudaStream_t st, const int *skip,
-                         int quad) {
+                         int quad, int *status) {
   if (!precision_supported(precision)) return cudaErrorInvalidValue;
   const size_t blk = (size_t)m.nb * m.nb * m.nk;
   const size_t total = (size_t)(n + 1) * blk;
@@ -869,14 +1068,14 @@ cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const v
   coef = (coef + 255) / 256 * 256;
   double2 *part = (double2 *)((char *)work + coef);
   switch (m.nb) {
-    case 1: return sweep_prec<1>(m, n, precision, H, work, I, part, st, skip, quad);
-    case 2: return sweep_prec<2>(m, n, precision, H, work, I, part, st, skip, quad);
-    case 3: return sweep_prec<3>(m, n, precision, H, work, I, part, st, skip, quad);
-    case 4: return sweep_prec<4>(m, n, precision, H, work, I, part, st, skip, quad);
-    case 6: return sweep_prec<6>(m, n, precision, H, work, I, part, st, skip, quad);
-    case 8: return sweep_prec<8>(m, n, precision, H, work, I, part, st, skip, quad);
-    case 12: return sweep_prec<12>(m, n, precision, H, work, I, part, st, skip, quad);
-    case 16: return sweep_prec<16>(m, n, precision, H, work, I, part, st, skip, quad);
+    case 1: return sweep_prec<1>(m, n, precision, H, work, I, part, st, skip, quad, status);
+    case 2: return sweep_prec<2>(m, n, precision, H, work, I, part, st, skip, quad, status);
+    case 3: return sweep_prec<3>(m, n, precision, H, work, I, part, st, skip, quad, status);
+    case 4: return sweep_prec<4>(m, n, precision, H, work, I, part, st, skip, quad, status);
+    case 6: return sweep_prec<6>(m, n, precision, H, work, I, part, st, skip, quad, status);
+    case 8: return sweep_prec<8>(m, n, precision, H, work, I, part, st, skip, quad, status);
+    case 12: return sweep_prec<12>(m, n, precision, H, work, I, part, st, skip, quad, status);
+    case 16: return sweep_prec<16>(m, n, precision, H, work, I, part, st, skip, quad, status);
     default: return cudaErrorInvalidValue;
   }
 }

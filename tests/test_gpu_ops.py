@@ -105,6 +105,35 @@ def test_gregory_collision_row_matches_oracle(nb, L, n, prec):
     assert relerr(gl, Il)[1] < bar and relerr(gg, Ig)[1] < bar
 
 
+@pytest.mark.parametrize("quad", [0, 1])
+@pytest.mark.parametrize("nb,L,n", [(8, (2, 3), 9), (8, (5, 2), 6), (16, (1, 6), 4), (4, (2, 3), 7),
+                                    (4, (13, 2), 12), (8, (4, 4), 40)])
+def test_c64_staged_sweep_ragged_tiles(nb, L, n, quad):
+    """the staged C64 sweep (N_b >= 4, n_k even) with k-tiles that run past n_k
+    (zero-filled copies) and with split l ranges, against the oracle"""
+    rng = np.random.default_rng(400 + nb * 7 + n)
+    nk = L[0] * L[1]
+    dt = 0.03
+    ntri = tri(n, n) + 1
+    Hl = ki.random_blocks(rng, (ntri, nk, nb, nb))
+    Hg = ki.random_blocks(rng, (ntri, nk, nb, nb))
+    Sl = ki.random_blocks(rng, (n + 1, nk, nb, nb))
+    Sg = ki.random_blocks(rng, (n + 1, nk, nb, nb))
+    Il, Ig = oracle.collision_row(nb, nk, n, dt, Hl, Hg, Sl, Sg, quadrature=quad)
+    p = kbe.KBE_PREC_C64
+    H64 = dev(to_dev_blocks(Hl, Hg))
+    H = torch.empty(H64.numel() * 2, dtype=torch.float32, device="cuda")
+    kbe.pack(p, H64, H, ntri, nb * nb * nk)
+    S = dev(to_dev_blocks(Sl, Sg))
+    I = torch.full((n + 1, 2, nb, nb, nk), float("nan"), dtype=torch.complex128, device="cuda")
+    work = torch.empty(kbe.collision_row_workspace(nb, L, n, p) // 4 + 1, dtype=torch.float32, device="cuda")
+    kbe.collision_row(nb, L, n, dt, H, S, I, precision=p, work=work, quadrature=quad)
+    torch.cuda.synchronize()
+    gl, gg = from_dev_blocks(I.cpu().numpy())
+    assert np.all(np.isfinite(gl)) and np.all(np.isfinite(gg))
+    assert relerr(gl, Il)[1] < 1e-5 and relerr(gg, Ig)[1] < 1e-5
+
+
 def _herm_batch(rng, nk, nb, scale=1.5):
     a = ki.random_blocks(rng, (nk, nb, nb), scale)
     return 0.5 * (a + np.conj(np.swapaxes(a, 1, 2)))

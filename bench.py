@@ -58,7 +58,7 @@ PEAKS = {
 # the full c2 run (8.29 GB vs 4.17 GB), df64 / c64 at row 247 of the c2 system
 # (profiles/sweep_c2_n247.md); traffic grows with the triangle like the
 # algorithmic bytes, so the average launch is scaled by the same factor.
-TRAFFIC_RATIO = {"fp64": 1.99, "df64": 1.77, "c64": 1.79}
+TRAFFIC_RATIO = {"fp64": 1.99, "df64": 1.77, "c64": 1.75}
 DTYPES = {"fp64": "f64", "df64": "df64 (f32 hi/lo pairs; everything but the sweep f64)",
           "c64": "c64/f32 history + sweep (everything else f64)"}
 ORACLE_PREFIX = 40

@@ -267,10 +267,11 @@ def run_ours(args, rank, world, local):
                        "dtype": DTYPES[form], "roofline": roofline(pf, form, tf)}
 
     # ---- batched form: uneven systems together vs one after another ----------
-    batched = paper = gradient = None
+    batched = paper = gradient = c3 = None
     if args.forms == "all":
         batched = batched_form(kbe, stream, args)
         paper = paper_shape(kbe, stream)
+        c3 = c3_form(kbe, stream)
     if args.forms in ("all", "gradient"):
         gradient = gradient_form(kbe, stream, args)
 
@@ -294,6 +295,7 @@ def run_ours(args, rank, world, local):
             "batched": batched,
             "paper_shape": paper,
             "gradient": gradient,
+            "c3_prefix": c3,
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(s)
@@ -423,6 +425,42 @@ def gradient_fd_check(args):
                       "A_indices": idx, "adjoint": ad.tolist(), "fd": fd.tolist(),
                       "normwise_rel_err": float(np.linalg.norm(ad - fd) / np.linalg.norm(fd)),
                       "max_rel_err": float(np.max(np.abs(ad - fd)) / np.max(np.abs(fd)))}), flush=True)
+
+
+C3_PREFIX = 96
+
+
+def c3_form(kbe, stream):
+    """c3 (N_b = 8, 16x16, U = 1.5, A0 = 0.5), the mixed forms' showcase, on its
+    first C3_PREFIX steps (the full FP64 run takes ~6 min): each form's
+    trajectory time (CUDA events) and its error against the FP64 trajectory."""
+    import torch
+    s = ki.config("c3", nt=C3_PREFIX)
+    out = {"workload": f"c3: N_b=8, 16x16 mesh (n_k=256), first {C3_PREFIX} of 512 steps, dt=0.02, "
+                       "U=1.5, Peierls A0=0.5, P(EC)^2E"}
+    ref = None
+    for form in ("fp64", "df64", "c64"):
+        g = kbe.KBE.from_system(s, stream=stream, precision=kbe.PRECISIONS[form])
+        g.step(8)   # warm-up (kernels loaded, attributes set)
+        g.reset()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.step(C3_PREFIX)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        nkb, sc = g.observables_all()
+        g.close()
+        o = {"ms": ms, "time_steps_per_s": C3_PREFIX / ms * 1e3}
+        if ref is None:
+            ref = (nkb, sc)
+        else:
+            o["speedup_vs_fp64"] = out["fp64"]["ms"] / ms
+            o["max_abs_err_density"] = float(np.abs(nkb - ref[0]).max())
+            o["max_rel_err_energy"] = float(np.abs(sc[:, 5] - ref[1][:, 5]).max() / np.abs(ref[1][:, 5]).max())
+        out[form] = o
+    return out
 
 
 BATCH_N, BATCH_NT = 16, 64

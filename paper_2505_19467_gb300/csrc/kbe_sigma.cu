@@ -188,9 +188,75 @@ __global__ void __launch_bounds__(128) sigma_products_kernel(const double2 *__re
   }
 }
 
+// The products for the pair pattern v = 1 - delta (every pair of distinct bands
+// interacts; the paper's two-band bar at N_b = 2). Then the sums over a != j and
+// b != m collapse: with T = G^< G^>^+ (per R), the direct sum is
+// tr T - r_j - c_m + M_jm (row and column sums of M_ab = G^<_ab conj(G^>_ab)),
+// the exchange sum (T G^<)_jm - T_jj G^<_jm - G^<_jm (c_m - M_jm), and with
+// T_jj = r_j everything but two terms cancels:
+//   Sigma^<(R) = fac [tr(T) G^< - T G^<],   Sigma^> = fac [tr(T)* G^> - T^+ G^>]
+// (T^+ = G^> G^<^+): two N_b x N_b products per (l, R) instead of the O(N_b^4)
+// double sums. One thread per (l, j, R) forms row j of both.
+template <int NB>
+__global__ void __launch_bounds__(128) sigma_products_pair_kernel(const double2 *__restrict__ GR,
+                                                                  double2 *__restrict__ SR, int n, int nk,
+                                                                  double Un, const double *__restrict__ Ul,
+                                                                  const int *__restrict__ skip) {
+  if (skip && *skip) return;
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long total = (long)(n + 1) * NB * nk;
+  if (idx >= total) return;
+  const int R = (int)(idx % nk);
+  const long t = idx / nk;
+  const int j = (int)(t % NB);
+  const int l = (int)(t / NB);
+  const size_t blk = (size_t)NB * NB * nk;
+  const double2 *gl = GR + (size_t)l * 2 * blk + R;
+  const double2 *gg = gl + blk;
+  const double fac = -Un * (Ul ? Ul[l] : Un);
+#define AT(M, r, c) M[(size_t)((r) * NB + (c)) * nk]
+  double2 tr = make_double2(0, 0);   // tr(G^< G^>^+) = sum_ab G^<_ab conj(G^>_ab)
+  double2 Tl[NB], Tg[NB];            // row j of T = G^< G^>^+ and of T^+ = G^> G^<^+
+#pragma unroll
+  for (int a = 0; a < NB; ++a) {
+    double2 sl = make_double2(0, 0), sg = make_double2(0, 0);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const double2 xab = AT(gl, a, b), yab = AT(gg, a, b);
+      tr = c_add(tr, c_mulc(xab, yab));
+      sl = c_add(sl, c_mulc(AT(gl, j, b), yab));
+      sg = c_add(sg, c_mulc(AT(gg, j, b), xab));
+    }
+    Tl[a] = sl;
+    Tg[a] = sg;
+  }
+  double2 *sl = SR + (size_t)l * 2 * blk + (size_t)j * NB * nk + R;
+  double2 *sg = sl + blk;
+#pragma unroll 1
+  for (int m = 0; m < NB; ++m) {
+    double2 pl = make_double2(0, 0), pg = make_double2(0, 0);
+#pragma unroll
+    for (int a = 0; a < NB; ++a) {
+      pl = c_fma(Tl[a], AT(gl, a, m), pl);
+      pg = c_fma(Tg[a], AT(gg, a, m), pg);
+    }
+    sl[(size_t)m * nk] = c_scale(fac, c_sub(c_mul(tr, AT(gl, j, m)), pl));
+    sg[(size_t)m * nk] = c_scale(fac, c_sub(c_mul(c_conj(tr), AT(gg, j, m)), pg));
+  }
+#undef AT
+}
+
 template <int NB>
 cudaError_t products_nb(const Mesh &m, const VMat &vm, int n, double Un, const double *Ul,
                         const double2 *GR, double2 *SR, cudaStream_t st, const int *skip) {
+  bool pair = NB >= 3;   // v = 1 - delta exactly (at N_b <= 2 the two forms time the same)
+  for (int a = 0; a < NB; ++a)
+    for (int b = 0; b < NB; ++b) pair = pair && vm.v[a * NB + b] == (a == b ? 0.0 : 1.0);
+  if (pair) {
+    const long total = (long)(n + 1) * NB * m.nk;
+    sigma_products_pair_kernel<NB><<<(unsigned)((total + 127) / 128), 128, 0, st>>>(GR, SR, n, m.nk, Un, Ul, skip);
+    return cudaGetLastError();
+  }
   const long total = (long)(n + 1) * NB * m.nk;
   const int threads = 128;
   const long blocks = (total + threads - 1) / threads;

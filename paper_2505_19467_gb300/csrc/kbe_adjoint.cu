@@ -357,6 +357,95 @@ __global__ void __launch_bounds__(128) sigma_adj_products_kernel(const double2 *
   gpart[idx] = g;
 }
 
+// The same for the pair pattern v = 1 - delta, where the product is
+// z = fac (tau x - x y^+ x), tau = tr(x y^+). With L = fac lam_z and w = tr(x^+ L):
+//   lam_x = conj(tau) L + w y - L x^+ y - y x^+ L,   lam_y = conj(w) x - x L^+ x.
+// Row p of each from the rows p of L x^+, y x^+, x L^+ (and of T = x y^+ for
+// the U-free inner product): O(N_b^2) per output row and product.
+template <int NB>
+__device__ __forceinline__ double prod_adj_pair_row(const double2 *__restrict__ x, const double2 *__restrict__ y,
+                                                    const double2 *__restrict__ lz, int p, int nk, double fac,
+                                                    double2 *lx, double2 *ly) {
+#define AT(M, r, c) M[(size_t)((r) * NB + (c)) * nk]
+  double2 tau = make_double2(0, 0), w = make_double2(0, 0);
+  double2 u[NB], v[NB], s[NB], t[NB];
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    double2 uc = make_double2(0, 0), vc = make_double2(0, 0), sc = make_double2(0, 0), tc = make_double2(0, 0);
+#pragma unroll
+    for (int a = 0; a < NB; ++a) {
+      const double2 xca = AT(x, c, a);
+      uc = c_add(uc, c_mulc(c_scale(fac, AT(lz, p, a)), xca));   // (L x^+)_pc
+      vc = c_add(vc, c_mulc(AT(y, p, a), xca));                  // (y x^+)_pc
+      sc = c_add(sc, c_mulc(AT(x, p, a), c_scale(fac, AT(lz, c, a))));   // (x L^+)_pc
+      tc = c_add(tc, c_mulc(AT(x, p, a), AT(y, c, a)));          // (x y^+)_pc
+    }
+    u[c] = uc;
+    v[c] = vc;
+    s[c] = sc;
+    t[c] = tc;
+  }
+#pragma unroll
+  for (int a = 0; a < NB; ++a)
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      tau = c_add(tau, c_mulc(AT(x, a, b), AT(y, a, b)));
+      w = c_add(w, c_mulc(c_scale(fac, AT(lz, a, b)), AT(x, a, b)));
+    }
+  double g = 0.0;
+#pragma unroll 1
+  for (int q = 0; q < NB; ++q) {
+    const double2 L = c_scale(fac, AT(lz, p, q));
+    double2 ax = c_add(c_mulc(L, tau), c_mul(w, AT(y, p, q)));   // conj(tau) L + w y
+    double2 ay = c_mulc(AT(x, p, q), w);                          // conj(w) x
+    double2 z = c_mul(tau, AT(x, p, q));                          // (tau x - T x)_pq
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+      ax = c_fnma(u[c], AT(y, c, q), ax);
+      ax = c_fnma(v[c], c_scale(fac, AT(lz, c, q)), ax);
+      ay = c_fnma(s[c], AT(x, c, q), ay);
+      z = c_fnma(t[c], AT(x, c, q), z);
+    }
+    lx[q] = c_add(lx[q], ax);
+    ly[q] = c_add(ly[q], ay);
+    const double2 lq = AT(lz, p, q);
+    g += lq.x * z.x + lq.y * z.y;
+  }
+  return g;
+#undef AT
+}
+
+template <int NB>
+__global__ void __launch_bounds__(128) sigma_adj_products_pair_kernel(const double2 *__restrict__ GR,
+                                                                      const double2 *__restrict__ LR,
+                                                                      double2 *__restrict__ GLR, int n, int nk,
+                                                                      double Un, const double *__restrict__ Ul,
+                                                                      double *__restrict__ gpart) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long total = (long)(n + 1) * NB * nk;
+  if (idx >= total) return;
+  const int R = (int)(idx % nk);
+  const long t = idx / nk;
+  const int p = (int)(t % NB);
+  const int l = (int)(t / NB);
+  const size_t blk = (size_t)NB * NB * nk;
+  const double2 *gl = GR + (size_t)l * 2 * blk + R, *gg = gl + blk;
+  const double2 *ll = LR + (size_t)l * 2 * blk + R, *lg = ll + blk;
+  const double fac = -Un * (Ul ? Ul[l] : Un);
+  double2 aL[NB], aG[NB];
+#pragma unroll
+  for (int q = 0; q < NB; ++q) aL[q] = aG[q] = make_double2(0, 0);
+  double g = prod_adj_pair_row<NB>(gl, gg, ll, p, nk, fac, aL, aG);   // Sigma^<: x = G^<, y = G^>
+  g += prod_adj_pair_row<NB>(gg, gl, lg, p, nk, fac, aG, aL);         // Sigma^>: x = G^>, y = G^<
+  double2 *ol = GLR + (size_t)l * 2 * blk + (size_t)p * NB * nk + R, *og = ol + blk;
+#pragma unroll
+  for (int q = 0; q < NB; ++q) {
+    ol[(size_t)q * nk] = aL[q];
+    og[(size_t)q * nk] = aG[q];
+  }
+  gpart[idx] = g;
+}
+
 // dL/dU from the Sigma row n: fac_l = -U_n U_l, so with g_l = sum_{p,R} gpart,
 //   dL/dU_l += -U_n g_l (every l),  dL/dU_n += -sum_l U_l g_l.
 // One CTA, l in a fixed order (deterministic).
@@ -845,8 +934,16 @@ cudaError_t adj_sigma_row(const Mesh &m, const double *v_host, int n, double Un,
   const long total = (long)(n + 1) * m.nb * m.nk;
   const unsigned blocks = (unsigned)((total + 127) / 128);
   double *gpart = (double *)(work + 3 * row);
-  KBE_NB_SWITCH(m.nb, (sigma_adj_products_kernel<NB><<<blocks, 128, 0, st>>>(GR, LR, GLR, n, m.nk, Un, Ul_dev, vm,
-                                                                               gpart)));
+  bool pair = m.nb >= 3;   // v = 1 - delta exactly: the closed form
+  for (int a = 0; a < m.nb; ++a)
+    for (int b = 0; b < m.nb; ++b) pair = pair && v_host[a * m.nb + b] == (a == b ? 0.0 : 1.0);
+  if (pair) {
+    KBE_NB_SWITCH(m.nb, (sigma_adj_products_pair_kernel<NB><<<blocks, 128, 0, st>>>(GR, LR, GLR, n, m.nk, Un,
+                                                                                     Ul_dev, gpart)));
+  } else {
+    KBE_NB_SWITCH(m.nb, (sigma_adj_products_kernel<NB><<<blocks, 128, 0, st>>>(GR, LR, GLR, n, m.nk, Un, Ul_dev,
+                                                                                 vm, gpart)));
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   adj_sigma_u_kernel<<<1, 256, 0, st>>>(gpart, n, m.nb * m.nk, Un, Ul_dev, gU);

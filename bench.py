@@ -78,6 +78,8 @@ def parse():
                    help="also time the other storage forms (speedup and error vs the headline), "
                         "the batched and paper-shaped forms and the gradient; 'gradient': only the last")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="skip kbe_autotune (the sweep's l-split chosen by timing before the timed region)")
     p.add_argument("--gradient-fd", action="store_true",
                    help="check the c5 gradient (512 steps) by central differences on 16 A_i and U, then exit")
     return p.parse_args()
@@ -214,6 +216,9 @@ def run_ours(args, rank, world, local):
     nt = s.nt
     stream = torch.cuda.Stream()
     g = kbe.KBE.from_system(s, stream=stream, precision=kbe.PRECISIONS[args.precision])
+    tuned = {}
+    if not args.no_autotune:   # before the timed region; choices are kept per shape for the process
+        tuned[args.precision] = [int(x) for x in g.autotune() if x]
 
     sampler = ClockSampler(local) if rank == 0 else None
     t_dev, prof, clocks = time_trajectories(g, nt, args.steps, args.warmup, stream, sampler, dist)
@@ -256,6 +261,8 @@ def run_ours(args, rank, world, local):
     forms = {}
     for form in ([] if args.forms != "all" else [f for f in ("fp64", "df64", "c64") if f != args.precision]):
         gf = kbe.KBE.from_system(s, stream=stream, precision=kbe.PRECISIONS[form])
+        if not args.no_autotune:
+            tuned[form] = [int(x) for x in gf.autotune() if x]
         tf, pf, _ = time_trajectories(gf, nt, args.steps, args.warmup, stream, None, dist)
         nkb_f, sc_f = gf.observables_all()
         gf.close()
@@ -285,7 +292,8 @@ def run_ours(args, rank, world, local):
                        "bench_step": f"one trajectory: reset + {nt} time steps",
                        "time_steps_per_bench_step": nt, "n_corr": 2,
                        "l2": "history 4.3 GB > 129 MB L2 (inputs larger than L2)",
-                       "parallelism": f"replicas x{world} (independent systems)"},
+                       "parallelism": f"replicas x{world} (independent systems)",
+                       "autotune": {"sweep_split_ctas_per_sm_by_row_bucket": tuned} if tuned else "off"},
             "roofline": roofline(prof, args.precision, t_dev),
             "e2e": {"value": e2e_value, "unit": "time-steps/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},

@@ -168,6 +168,19 @@ kbe_status kbe_reset(kbe_handle *h);
  * default stream (otherwise steps run ungraphed); profiled steps run ungraphed. */
 kbe_status kbe_set_graphs(kbe_handle *h, int enable);
 
+/* Autotuner of the collision sweep's launch shape. The free parameter is the
+ * split of the memory-time range over CTAs (how many CTAs share one output
+ * column), expressed as the CTAs per SM the grid aims for. kbe_autotune times
+ * candidate splits on this handle's buffers at one row per power-of-two bucket
+ * of n (n + 1 in [2^b, 2^(b+1)), up to nt_max) and keeps the fastest per
+ * (precision, quadrature, N_b, n_k, bucket) for the rest of the process; every
+ * later sweep of that shape (any handle) uses it, untuned shapes keep the
+ * default. Only scratch buffers are written (it may be called between steps);
+ * cached graphs are dropped. targets (host int [KBE_AUTOTUNE_BUCKETS], may be
+ * NULL) receives the choice per bucket (0: bucket above nt_max). Synchronises. */
+#define KBE_AUTOTUNE_BUCKETS 17
+kbe_status kbe_autotune(kbe_handle *h, int *targets);
+
 /* Corrector passes run at each step 0..current (host int [n+1]; entry 0 is 0):
  * n_corr everywhere when corr_tol = 0. Synchronises. */
 kbe_status kbe_corrector_iterations(kbe_handle *h, int *out);

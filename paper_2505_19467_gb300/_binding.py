@@ -36,7 +36,7 @@ EXPORTS = [
     "kbe_batch_destroy", "kbe_batch_system", "kbe_batch_reset", "kbe_batch_step",
     "kbe_batch_synchronize", "kbe_checkpoint_bytes", "kbe_checkpoint_save", "kbe_checkpoint_load",
     "kbe_set_dipole", "kbe_backward", "kbe_backward_memory_bytes", "kbe_corrector_iterations",
-    "kbe_op_collision_row_quad", "kbe_set_graphs",
+    "kbe_op_collision_row_quad", "kbe_set_graphs", "kbe_autotune",
 ]
 
 
@@ -119,6 +119,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "kbe_backward_memory_bytes": (S, [pcfg]),
         "kbe_corrector_iterations": (I, [P, P]),
         "kbe_set_graphs": (I, [P, I]),
+        "kbe_autotune": (I, [P, P]),
         "kbe_op_collision_row_quad": (I, [pmesh, I, D, I, I, P, P, P, P, S, P]),
     }
     for name, (res, args) in sig.items():
@@ -310,6 +311,13 @@ class KBE:
     def restore(self, data: bytes):
         buf = np.frombuffer(data, np.uint8)
         _check(load().kbe_checkpoint_load(self._h, _np_ptr(np.ascontiguousarray(buf)), len(buf)), self._h)
+
+    def autotune(self) -> np.ndarray:
+        """time the sweep's split candidates and keep the fastest (kbe_autotune);
+        returns the choice per row bucket (0 = not tuned)"""
+        out = np.zeros(17, np.int32)
+        _check(load().kbe_autotune(self._h, _np_ptr(out)), self._h)
+        return out
 
     def set_graphs(self, enable: bool = True):
         """replay captured CUDA graphs for repeated kbe_step calls (kbe_set_graphs)"""

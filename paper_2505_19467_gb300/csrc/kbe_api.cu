@@ -227,7 +227,7 @@ kbe_status evaluate_row(kbe_handle *h, int n, const int *skip = nullptr) {
     h->ev_flops_x[h->ev_used] = sweep_flops_executed(h, n);
     h->ev_bytes[h->ev_used] = sweep_bytes(h, n);
     h->ev_used++;
-    h->stats.launches += 5 + (kbe::sweep_splits(h->mesh, n, h->cfg.precision) > 1 ? 1 : 0);
+    h->stats.launches += 5 + (kbe::sweep_splits(h->mesh, n, h->cfg.precision, h->cfg.quadrature) > 1 ? 1 : 0);
   }
   return KBE_OK;
 }
@@ -864,6 +864,21 @@ kbe_status kbe_step(kbe_handle *h, int nsteps) {
     kbe_status s = one_step(h);
     if (s != KBE_OK) return s;
   }
+  return KBE_OK;
+}
+
+kbe_status kbe_autotune(kbe_handle *h, int *targets) {
+  if (!h) return KBE_ERR_ARG;
+  if (h->sticky != KBE_OK) return fail(h, h->sticky, "autotune: handle has a sticky error; reset it");
+  int out[KBE_AUTOTUNE_BUCKETS];
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess)
+    e = kbe::tune_sweep(h->mesh, h->cfg.precision, h->cfg.quadrature, h->cfg.nt_max, h->cfg.dt, h->H, h->Sig, h->Ic,
+                        h->coef, h->stream, out, KBE_AUTOTUNE_BUCKETS);
+  if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
+  drop_graphs(h);   // captured sweeps carry the old splits
+  if (targets)
+    for (int b = 0; b < KBE_AUTOTUNE_BUCKETS; ++b) targets[b] = out[b];
   return KBE_OK;
 }
 

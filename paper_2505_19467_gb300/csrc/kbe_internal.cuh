@@ -119,7 +119,10 @@ bool sweep_supported(int nb);
 bool precision_supported(int prec);
 size_t history_elem_bytes(int prec);
 size_t sweep_workspace_bytes(const Mesh &m, int n, int prec);
-int sweep_splits(const Mesh &m, int n, int prec);   // CTAs sharing one output's l range
+int sweep_splits(const Mesh &m, int n, int prec, int quad);   // CTAs sharing one output's l range
+// autotuner of the l-split (see kbe_sweep.cu); out[b] per row bucket b
+cudaError_t tune_sweep(const Mesh &m, int prec, int quad, int nmax, double dt, const void *H, const double2 *Sig,
+                       double2 *I, void *work, cudaStream_t st, int *out, int nout);
 cudaError_t sweep_prepare(int nb);   // kernel attributes, host side (before stream capture)
 cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t nblocks, size_t blk,
                         cudaStream_t st, const int *skip = nullptr);

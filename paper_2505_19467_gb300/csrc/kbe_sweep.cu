@@ -35,6 +35,11 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
 #include "kbe_internal.cuh"
 
 #ifndef KBE_SWEEP_MINB_F64
@@ -907,43 +912,70 @@ int staged_kt_of(int nb) {
   }
 }
 
-// l-split of the staged form: enough CTAs for ~3 resident per SM, twice over
-SweepShape staged_shape(const Mesh &m, int n) {
+// ---- l-split of the memory-time range (autotuned per shape) ----------------
+// The number of CTAs sharing one output column's l range is chosen so that the
+// grid reaches about `target` CTAs per SM; kbe_autotune times candidate
+// targets per (form, quadrature, N_b, n_k, row bucket) and keeps the best for
+// the process. Every choice obeys nz <= nz_cap(n), which sizes the workspace.
+int nz_cap(int n) { return min(n + 1, 2 + 1024 / (n + 1)); }
+int row_bucket(int n) {
+  int b = 0;
+  while ((2 << b) <= n + 1 && b < 30) ++b;
+  return b;   // floor(log2(n + 1))
+}
+using TuneKey = std::tuple<int, int, int, int, int>;   // precision, quadrature, nb, nk, bucket
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+
+int tuned_target(int prec, int quad, const Mesh &m, int n, int fallback) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(TuneKey(prec, quad, m.nb, m.nk, row_bucket(n)));
+  return it == g_tune.end() ? fallback : it->second;
+}
+
+long split_count(long base, int n, int target) {
+  long nz = (152L * target + base - 1) / base;
+  if (nz > nz_cap(n)) nz = nz_cap(n);
+  return nz < 1 ? 1 : nz;
+}
+
+// l-split of the staged form: enough CTAs for ~target resident per SM
+SweepShape staged_shape(const Mesh &m, int n, int target = KBE_STAGED_TARGET) {
   SweepShape sh;
   sh.threads = kStagedThreads;
   const int kt = staged_kt_of(m.nb);
   const long tx = (m.nk + kt - 1) / kt;
   const long base = (long)(n + 1) * tx;
-  long nz = (152L * KBE_STAGED_TARGET + base - 1) / base;
-  if (nz > n + 1) nz = n + 1;
-  if (nz > 2 + 1024 / (n + 1)) nz = 2 + 1024 / (n + 1);
-  if (nz < 1) nz = 1;
+  long nz = split_count(base, n, target);
   sh.lchunk = (int)((n + 1 + nz - 1) / nz);
   sh.nz = (int)((n + 1 + sh.lchunk - 1) / sh.lchunk);
   sh.grid = dim3((unsigned)tx, n + 1, (unsigned)sh.nz);
   return sh;
 }
 
-SweepShape sweep_shape(const Mesh &m, int n, int V = 1) {
+SweepShape sweep_shape(const Mesh &m, int n, int V = 1, int target = kTargetCtas / 152) {
   SweepShape sh;
   const long elems = (long)m.nb * m.nb * (m.nk / V);
   sh.threads = elems >= 256 ? 256 : (int)((elems + 31) / 32) * 32;
   const long ty = (elems + sh.threads - 1) / sh.threads;
   const long base = (long)(n + 1) * ty;
-  long nz = (kTargetCtas + base - 1) / base;
-  if (nz > n + 1) nz = n + 1;                        // at least one l per split
-  if (nz > 2 + 1024 / (n + 1)) nz = 2 + 1024 / (n + 1);   // bounds the partial-sum scratch
-  if (nz < 1) nz = 1;
+  long nz = split_count(base, n, target);   // at least one l per split, bounded scratch
   sh.lchunk = (int)((n + 1 + nz - 1) / nz);
   sh.nz = (int)((n + 1 + sh.lchunk - 1) / sh.lchunk);
   sh.grid = dim3((unsigned)ty, n + 1, (unsigned)sh.nz);
   return sh;
 }
 
+template <class P> struct PrecOf;
+template <> struct PrecOf<ArithF64> { static constexpr int v = KBE_PREC_FP64; };
+template <> struct PrecOf<ArithDF64> { static constexpr int v = KBE_PREC_DF64; };
+template <> struct PrecOf<ArithC64> { static constexpr int v = KBE_PREC_C64; };
+template <> struct PrecOf<ArithC64x2> { static constexpr int v = KBE_PREC_C64; };
+
 template <class P, int NB>
 cudaError_t sweep_nb(const Mesh &m, int n, const void *H, const void *Cf, double2 *I, double2 *part,
                      cudaStream_t st, const int *skip, int quad) {
-  const SweepShape sh = sweep_shape(m, n, P::V);
+  const SweepShape sh = sweep_shape(m, n, P::V, tuned_target(PrecOf<P>::v, quad, m, n, kTargetCtas / 152));
   double2 *out = sh.nz > 1 ? part : I;
   const int nkS = m.nk / P::V;   // stored elements per (a, b) array
   if (quad == kQuadGregory)
@@ -964,7 +996,7 @@ cudaError_t sweep_staged(const Mesh &m, int n, const void *H, const void *Cf, do
                          cudaStream_t st, const int *skip, int quad, int *status) {
   cudaError_t e = staged_prepare<NB>();
   if (e != cudaSuccess) return e;
-  const SweepShape sh = staged_shape(m, n);
+  const SweepShape sh = staged_shape(m, n, tuned_target(KBE_PREC_C64, quad, m, n, KBE_STAGED_TARGET));
   double2 *out = sh.nz > 1 ? part : I;
   const size_t smem = kStages * staged_stage_elems(NB) * sizeof(float2);
   CUtensorMap tmC, tmH;
@@ -1022,18 +1054,62 @@ size_t sweep_workspace_bytes(const Mesh &m, int n, int prec) {
   size_t coef = (size_t)(n + 1) * 3 * blk * history_elem_bytes(prec);
   coef = (coef + 255) / 256 * 256;
   size_t part = 0;
-  for (int r = 0; r <= n; ++r) {   // the largest partial buffer over rows 0..n
-    const SweepShape sh = use_staged(m, prec) ? staged_shape(m, r) : sweep_shape(m, r, sweep_width(m, prec));
-    if (sh.nz > 1) {
-      const size_t b = (size_t)sh.nz * (r + 1) * 2 * blk * sizeof(double2);
+  (void)prec;
+  for (int r = 0; r <= n; ++r) {   // the largest partial buffer over rows 0..n, any split
+    if (nz_cap(r) > 1) {
+      const size_t b = (size_t)nz_cap(r) * (r + 1) * 2 * blk * sizeof(double2);
       if (b > part) part = b;
     }
   }
   return coef + part;
 }
 
-int sweep_splits(const Mesh &m, int n, int prec) {
-  return use_staged(m, prec) ? staged_shape(m, n).nz : sweep_shape(m, n, sweep_width(m, prec)).nz;
+int sweep_splits(const Mesh &m, int n, int prec, int quad) {
+  if (use_staged(m, prec)) return staged_shape(m, n, tuned_target(prec, quad, m, n, KBE_STAGED_TARGET)).nz;
+  return sweep_shape(m, n, sweep_width(m, prec), tuned_target(prec, quad, m, n, kTargetCtas / 152)).nz;
+}
+
+// Times launch_sweep at one row per power-of-two bucket of n (up to nmax)
+// for each candidate target and keeps the fastest per bucket. H, Sig, I and
+// work are the caller's buffers for row nmax (contents are not used for
+// timing; I and work are overwritten). out[b] = the choice for bucket b.
+cudaError_t tune_sweep(const Mesh &m, int prec, int quad, int nmax, double dt, const void *H, const double2 *Sig,
+                       double2 *I, void *work, cudaStream_t st, int *out, int nout) {
+  const bool staged = use_staged(m, prec);
+  const std::vector<int> cands = staged ? std::vector<int>{3, 6, 12, 24} : std::vector<int>{2, 4, 8, 16, 32};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return cudaErrorUnknown;
+  cudaError_t err = cudaSuccess;
+  for (int b = 0; b < nout; ++b) out[b] = 0;
+  for (int b = 0; err == cudaSuccess && b <= row_bucket(nmax) && b < nout; ++b) {
+    const int n = min(nmax, (3 << b) / 2 - 1 > 0 ? (3 << b) / 2 - 1 : 0);   // mid-bucket row
+    const TuneKey key(prec, quad, m.nb, m.nk, b);
+    float best = 1e30f;
+    int best_t = cands[0];
+    for (int t : cands) {
+      {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = t;
+      }
+      for (int w = 0; w < 2 && err == cudaSuccess; ++w) err = launch_sweep(m, n, dt, prec, H, Sig, I, work, st, nullptr, quad);
+      if (err == cudaSuccess) err = cudaEventRecord(e0, st);
+      for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = launch_sweep(m, n, dt, prec, H, Sig, I, work, st, nullptr, quad);
+      if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      if (err == cudaSuccess && ms < best) {
+        best = ms;
+        best_t = t;
+      }
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best_t;
+    out[b] = best_t;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return err;
 }
 
 // shared-memory limits of the staged kernels (host side, before any capture)

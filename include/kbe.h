@@ -181,6 +181,15 @@ kbe_status kbe_set_graphs(kbe_handle *h, int enable);
 #define KBE_AUTOTUNE_BUCKETS 17
 kbe_status kbe_autotune(kbe_handle *h, int *targets);
 
+/* Fault injection for testing the failure path (no GPU fault, no hang):
+ * KBE_INJECT_STAGED_COPY_LOSS makes the next collision sweep of this handle
+ * (C64, staged form: N_b in {4, 8, 16}, n_k even) lose one CTA's first
+ * copies. Its waits are bounded (one second of device time), so the kernel
+ * marks a timeout and returns; the next synchronising call returns
+ * KBE_ERR_TIMEOUT, which is sticky until kbe_reset. 0 clears. One-shot. */
+#define KBE_INJECT_STAGED_COPY_LOSS 1
+kbe_status kbe_debug_inject(kbe_handle *h, int fault);
+
 /* Corrector passes run at each step 0..current (host int [n+1]; entry 0 is 0):
  * n_corr everywhere when corr_tol = 0. Synchronises. */
 kbe_status kbe_corrector_iterations(kbe_handle *h, int *out);

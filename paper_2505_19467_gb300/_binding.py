@@ -36,7 +36,7 @@ EXPORTS = [
     "kbe_batch_destroy", "kbe_batch_system", "kbe_batch_reset", "kbe_batch_step",
     "kbe_batch_synchronize", "kbe_checkpoint_bytes", "kbe_checkpoint_save", "kbe_checkpoint_load",
     "kbe_set_dipole", "kbe_backward", "kbe_backward_memory_bytes", "kbe_corrector_iterations",
-    "kbe_op_collision_row_quad", "kbe_set_graphs", "kbe_autotune",
+    "kbe_op_collision_row_quad", "kbe_set_graphs", "kbe_autotune", "kbe_debug_inject",
 ]
 
 
@@ -120,6 +120,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "kbe_corrector_iterations": (I, [P, P]),
         "kbe_set_graphs": (I, [P, I]),
         "kbe_autotune": (I, [P, P]),
+        "kbe_debug_inject": (I, [P, I]),
         "kbe_op_collision_row_quad": (I, [pmesh, I, D, I, I, P, P, P, P, S, P]),
     }
     for name, (res, args) in sig.items():
@@ -311,6 +312,10 @@ class KBE:
     def restore(self, data: bytes):
         buf = np.frombuffer(data, np.uint8)
         _check(load().kbe_checkpoint_load(self._h, _np_ptr(np.ascontiguousarray(buf)), len(buf)), self._h)
+
+    def debug_inject(self, fault: int):
+        """one-shot fault injection for the failure-path test (kbe_debug_inject)"""
+        _check(load().kbe_debug_inject(self._h, int(fault)), self._h)
 
     def autotune(self) -> np.ndarray:
         """time the sweep's split candidates and keep the fastest (kbe_autotune);

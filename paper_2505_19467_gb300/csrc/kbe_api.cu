@@ -74,6 +74,7 @@ struct kbe_handle {
   // (first row, step count, order of the I ring), valid for the current inputs
   bool graphs = false;
   std::map<std::tuple<int, int, int>, cudaGraphExec_t> gcache;
+  int inject = 0;   // one-shot fault injection for the timeout test (kbe_debug_inject)
 
   // reverse mode: one device arena, allocated by the first kbe_backward
   void *adj = nullptr;
@@ -219,7 +220,8 @@ kbe_status evaluate_row(kbe_handle *h, int n, const int *skip = nullptr) {
     cudaEventRecord(h->ev[h->ev_used].first, h->stream);
   }
   e = kbe::launch_sweep(m, n, h->cfg.dt, h->cfg.precision, h->H, h->Sig, h->Ic, h->coef, h->stream, skip,
-                        h->cfg.quadrature, h->status);
+                        h->cfg.quadrature, h->status, h->inject);
+  h->inject = 0;
   if (e != cudaSuccess) return cuda_fail(h, e, "collision sweep");
   if (timed) {
     cudaEventRecord(h->ev[h->ev_used].second, h->stream);
@@ -859,7 +861,7 @@ kbe_status kbe_step(kbe_handle *h, int nsteps) {
   if (h->n < 0) return fail(h, KBE_ERR_STATE, "step: call kbe_reset first");
   if (nsteps < 0) return fail(h, KBE_ERR_ARG, "step: negative count");
   if (h->n + nsteps > h->cfg.nt_max) return fail(h, KBE_ERR_STATE, "step: past nt_max");
-  if (h->graphs && !h->prof && h->stream != nullptr && nsteps > 0) return step_graph(h, nsteps);
+  if (h->graphs && !h->prof && !h->inject && h->stream != nullptr && nsteps > 0) return step_graph(h, nsteps);
   for (int i = 0; i < nsteps; ++i) {
     kbe_status s = one_step(h);
     if (s != KBE_OK) return s;
@@ -879,6 +881,16 @@ kbe_status kbe_autotune(kbe_handle *h, int *targets) {
   drop_graphs(h);   // captured sweeps carry the old splits
   if (targets)
     for (int b = 0; b < KBE_AUTOTUNE_BUCKETS; ++b) targets[b] = out[b];
+  return KBE_OK;
+}
+
+kbe_status kbe_debug_inject(kbe_handle *h, int fault) {
+  if (!h) return KBE_ERR_ARG;
+  if (fault != 0 && fault != KBE_INJECT_STAGED_COPY_LOSS) return fail(h, KBE_ERR_ARG, "debug_inject: unknown fault");
+  if (fault == KBE_INJECT_STAGED_COPY_LOSS &&
+      !(h->cfg.precision == KBE_PREC_C64 && h->cfg.nb >= 4 && h->mesh.nk % 2 == 0 && h->cfg.nb != 6 && h->cfg.nb != 12))
+    return fail(h, KBE_ERR_UNSUPPORTED, "debug_inject: the handle's sweep is not the staged C64 form");
+  h->inject = fault;
   return KBE_OK;
 }
 

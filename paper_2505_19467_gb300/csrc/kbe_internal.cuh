@@ -128,9 +128,12 @@ cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t nblocks,
                         cudaStream_t st, const int *skip = nullptr);
 // status (may be NULL): device word that receives kDevTimeout if a staged
 // copy never completes (bounded waits)
+// inject (test only): 1 makes the staged C64 sweep's first CTA omit its first
+// node's copies, so that its bounded waits run out (kDevTimeout), no fault
 cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const void *H,
                          const double2 *Sig, double2 *I, void *work, cudaStream_t st,
-                         const int *skip = nullptr, int quad = kQuadTrapezoid, int *status = nullptr);
+                         const int *skip = nullptr, int quad = kQuadTrapezoid, int *status = nullptr,
+                         int inject = 0);
 
 // a3 propagators / initial state / density
 struct HopTable {

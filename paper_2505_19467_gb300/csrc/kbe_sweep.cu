@@ -687,10 +687,21 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
                : "memory");
 }
-// true when the phase with this parity has completed; false after the limit
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+constexpr unsigned long long kMbarWaitNs = 1000000000ull;   // one second per wait
+
+// true when the phase with this parity has completed; false after one second
+// of device time (%globaltimer) or `limit` rounds, whichever comes first
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, int limit) {
   const unsigned a = smem_addr(bar);
+  const unsigned long long t0 = global_ns();
   for (int it = 0; it < limit; ++it) {
+    if ((it & 255) == 255 && global_ns() - t0 > kMbarWaitNs) return false;
     unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -717,13 +728,13 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *tm, in
       : "memory");
 }
 
-constexpr int kMbarWaitLimit = 1 << 22;   // try_wait rounds before giving up (far beyond any copy)
+constexpr int kMbarWaitLimit = 1 << 30;   // try_wait rounds (a backstop; the time limit comes first)
 
 template <int NB, int QUAD>
 __global__ void __launch_bounds__(kStagedThreads, KBE_STAGED_MINB)
     sweep_c64_tma_kernel(const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmH,
                          double2 *__restrict__ out, int n, int nk, int lchunk, const int *__restrict__ skip,
-                         int *status) {
+                         int *status, int drop_first) {
   if (skip && *skip) return;
   extern __shared__ __align__(128) float4 tma_smem4[];
   __shared__ __align__(8) uint64_t bar[kStages];
@@ -745,7 +756,11 @@ __global__ void __launch_bounds__(kStagedThreads, KBE_STAGED_MINB)
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();
+  // drop_first (fault injection for the timeout test): the first CTA omits
+  // its first node's copies, so that its waits run out
+  const bool drop = drop_first && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0;
   auto issue = [&](int i) {   // node i into stage i % kStages (thread 0)
+    if (drop && i == 0) return;
     const int l = l0 + i, s = i % kStages;
     const int tb = (int)(l >= j ? tri(l, j) : tri(j, l));
     float2 *st = smem + (size_t)s * staged_stage_elems(NB);
@@ -993,7 +1008,7 @@ cudaError_t sweep_nb(const Mesh &m, int n, const void *H, const void *Cf, double
 
 template <int NB>
 cudaError_t sweep_staged(const Mesh &m, int n, const void *H, const void *Cf, double2 *I, double2 *part,
-                         cudaStream_t st, const int *skip, int quad, int *status) {
+                         cudaStream_t st, const int *skip, int quad, int *status, int inject) {
   cudaError_t e = staged_prepare<NB>();
   if (e != cudaSuccess) return e;
   const SweepShape sh = staged_shape(m, n, tuned_target(KBE_PREC_C64, quad, m, n, KBE_STAGED_TARGET));
@@ -1003,10 +1018,10 @@ cudaError_t sweep_staged(const Mesh &m, int n, const void *H, const void *Cf, do
   if (KBE_SWEEP_C64_TMA && staged_tensor_maps<NB>(Cf, H, n, m.nk, &tmC, &tmH)) {
     if (quad == kQuadGregory)
       sweep_c64_tma_kernel<NB, kQuadGregory><<<sh.grid, sh.threads, smem, st>>>(tmC, tmH, out, n, m.nk, sh.lchunk,
-                                                                               skip, status);
+                                                                               skip, status, inject);
     else
       sweep_c64_tma_kernel<NB, kQuadTrapezoid><<<sh.grid, sh.threads, smem, st>>>(tmC, tmH, out, n, m.nk,
-                                                                                 sh.lchunk, skip, status);
+                                                                                 sh.lchunk, skip, status, inject);
   } else if (quad == kQuadGregory)
     sweep_c64_staged_kernel<NB, kQuadGregory><<<sh.grid, sh.threads, smem, st>>>(
         (const float2 *)H, (const float2 *)Cf, out, n, m.nk, sh.lchunk, skip);
@@ -1022,9 +1037,9 @@ cudaError_t sweep_staged(const Mesh &m, int n, const void *H, const void *Cf, do
 
 template <int NB>
 cudaError_t sweep_prec(const Mesh &m, int n, int prec, const void *H, const void *Cf, double2 *I,
-                       double2 *part, cudaStream_t st, const int *skip, int quad, int *status) {
+                       double2 *part, cudaStream_t st, const int *skip, int quad, int *status, int inject) {
   if constexpr (NB == 1 || NB == 2 || NB == 4 || NB == 8 || NB == 16) {
-    if (use_staged(m, prec)) return sweep_staged<NB>(m, n, H, Cf, I, part, st, skip, quad, status);
+    if (use_staged(m, prec)) return sweep_staged<NB>(m, n, H, Cf, I, part, st, skip, quad, status, inject);
   }
   if (prec == KBE_PREC_FP64) return sweep_nb<ArithF64, NB>(m, n, H, Cf, I, part, st, skip, quad);
   if (prec == KBE_PREC_DF64) return sweep_nb<ArithDF64, NB>(m, n, H, Cf, I, part, st, skip, quad);
@@ -1133,7 +1148,7 @@ cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t nblocks,
 
 cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const void *H,
                          const double2 *Sig, double2 *I, void *work, cudaStream_t st, const int *skip,
-                         int quad, int *status) {
+                         int quad, int *status, int inject) {
   if (!precision_supported(precision)) return cudaErrorInvalidValue;
   const size_t blk = (size_t)m.nb * m.nb * m.nk;
   const size_t total = (size_t)(n + 1) * blk;
@@ -1144,14 +1159,14 @@ cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const v
   coef = (coef + 255) / 256 * 256;
   double2 *part = (double2 *)((char *)work + coef);
   switch (m.nb) {
-    case 1: return sweep_prec<1>(m, n, precision, H, work, I, part, st, skip, quad, status);
-    case 2: return sweep_prec<2>(m, n, precision, H, work, I, part, st, skip, quad, status);
-    case 3: return sweep_prec<3>(m, n, precision, H, work, I, part, st, skip, quad, status);
-    case 4: return sweep_prec<4>(m, n, precision, H, work, I, part, st, skip, quad, status);
-    case 6: return sweep_prec<6>(m, n, precision, H, work, I, part, st, skip, quad, status);
-    case 8: return sweep_prec<8>(m, n, precision, H, work, I, part, st, skip, quad, status);
-    case 12: return sweep_prec<12>(m, n, precision, H, work, I, part, st, skip, quad, status);
-    case 16: return sweep_prec<16>(m, n, precision, H, work, I, part, st, skip, quad, status);
+    case 1: return sweep_prec<1>(m, n, precision, H, work, I, part, st, skip, quad, status, inject);
+    case 2: return sweep_prec<2>(m, n, precision, H, work, I, part, st, skip, quad, status, inject);
+    case 3: return sweep_prec<3>(m, n, precision, H, work, I, part, st, skip, quad, status, inject);
+    case 4: return sweep_prec<4>(m, n, precision, H, work, I, part, st, skip, quad, status, inject);
+    case 6: return sweep_prec<6>(m, n, precision, H, work, I, part, st, skip, quad, status, inject);
+    case 8: return sweep_prec<8>(m, n, precision, H, work, I, part, st, skip, quad, status, inject);
+    case 12: return sweep_prec<12>(m, n, precision, H, work, I, part, st, skip, quad, status, inject);
+    case 16: return sweep_prec<16>(m, n, precision, H, work, I, part, st, skip, quad, status, inject);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -497,6 +497,19 @@ def batched_form(kbe, stream, args):
     b.synchronize()
     torch.cuda.synchronize()
     t_batch = (time.perf_counter() - t0) / args.steps
+    b.set_graphs(True)            # each system replays its 64 steps as one captured graph
+    for _ in range(max(1, args.warmup)):
+        b.reset()
+        b.step(BATCH_NT)
+    b.synchronize()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b.reset()
+        b.step(BATCH_NT)
+    b.synchronize()
+    torch.cuda.synchronize()
+    t_graph = (time.perf_counter() - t0) / args.steps
     b.close()
     singles = [kbe.KBE.from_system(x, nt_max=nt, stream=stream) for x, nt in zip(sel, nts)]
     for g, nt in zip(singles, nts):
@@ -519,6 +532,7 @@ def batched_form(kbe, stream, args):
                         f"{BATCH_NT} steps; N_b {sorted(set(x.nb for x in sel))}",
             "value": units / t_batch, "unit": "time-steps/s (summed over systems)",
             "sequential_value": units / t_seq, "speedup_vs_sequential": t_seq / t_batch,
+            "graphs_value": units / t_graph, "graphs_speedup_vs_sequential": t_seq / t_graph,
             "full_64_system_fp64_bytes": int(full), "device_bytes": int(tot),
             "note": "the full 64-system draw needs this many bytes in FP64 and does not fit; "
                     "kbe_batch_create admits systems in order within the device budget"}

@@ -294,6 +294,11 @@ kbe_status kbe_batch_reset(kbe_batch *b);
 kbe_status kbe_batch_step(kbe_batch *b, int nsteps);
 /* Wait for all systems; the first failing system's status. */
 kbe_status kbe_batch_synchronize(kbe_batch *b);
+/* Graph mode for the batch (kbe_set_graphs on every admitted system): each
+ * kbe_batch_step(b, k) then runs every system's k steps as one captured graph
+ * on its own stream (captured on the first call from a given row, replayed
+ * after kbe_batch_reset), instead of interleaving single steps. */
+kbe_status kbe_batch_set_graphs(kbe_batch *b, int enable);
 
 /* Message of the last error of this handle; with NULL, of the last failed
  * create or handle-free operation (kbe_op_*) on the calling thread. */

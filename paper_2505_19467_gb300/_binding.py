@@ -36,7 +36,7 @@ EXPORTS = [
     "kbe_batch_destroy", "kbe_batch_system", "kbe_batch_reset", "kbe_batch_step",
     "kbe_batch_synchronize", "kbe_checkpoint_bytes", "kbe_checkpoint_save", "kbe_checkpoint_load",
     "kbe_set_dipole", "kbe_backward", "kbe_backward_memory_bytes", "kbe_corrector_iterations",
-    "kbe_op_collision_row_quad", "kbe_set_graphs", "kbe_autotune", "kbe_debug_inject",
+    "kbe_op_collision_row_quad", "kbe_set_graphs", "kbe_autotune", "kbe_debug_inject", "kbe_batch_set_graphs",
 ]
 
 
@@ -121,6 +121,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "kbe_set_graphs": (I, [P, I]),
         "kbe_autotune": (I, [P, P]),
         "kbe_debug_inject": (I, [P, I]),
+        "kbe_batch_set_graphs": (I, [P, I]),
         "kbe_op_collision_row_quad": (I, [pmesh, I, D, I, I, P, P, P, P, S, P]),
     }
     for name, (res, args) in sig.items():
@@ -459,6 +460,10 @@ class KBEBatch:
 
     def step(self, nsteps: int):
         _check(load().kbe_batch_step(self._b, int(nsteps)))
+
+    def set_graphs(self, enable: bool = True):
+        """each system replays its steps as one captured graph (kbe_batch_set_graphs)"""
+        _check(load().kbe_batch_set_graphs(self._b, int(enable)))
 
     def synchronize(self):
         _check(load().kbe_batch_synchronize(self._b))

@@ -6,8 +6,10 @@
 // kernels of different systems overlap on the GPU (a small system's launches
 // fill SMs that a large system's tail leaves idle). Steps are enqueued one
 // time step of all systems at a time, so no system runs far ahead of the
-// others. Admission is by device memory: systems are taken in order while
-// their allocation fits the budget; the others are reported as not admitted.
+// others; with graphs on (kbe_batch_set_graphs) each system instead replays
+// the call's steps as one captured graph on its own stream. Admission is by
+// device memory: systems are taken in order while their allocation fits the
+// budget; the others are reported as not admitted.
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -22,6 +24,7 @@ struct kbe_batch {
   std::vector<int> nt_max;
   std::vector<int> cur;             // host copy of each system's current row
   cudaEvent_t fork = nullptr;
+  bool graphs = false;              // each system replays its captured steps (kbe_set_graphs)
 };
 
 namespace {
@@ -160,6 +163,19 @@ kbe_status kbe_batch_step(kbe_batch *b, int nsteps) {
   if (!b || nsteps < 0) return batch_fail(KBE_ERR_ARG, "batch_step: bad arguments");
   cudaError_t e = fork_from_main(b);
   if (e != cudaSuccess) return batch_fail(KBE_ERR_CUDA, std::string("batch_step: ") + cudaGetErrorString(e));
+  if (b->graphs) {   // independent systems: each runs its steps as one replayed graph on its stream
+    for (size_t i = 0; i < b->sys.size(); ++i) {
+      if (!b->sys[i] || b->cur[i] < 0) continue;
+      const int k = nsteps < b->nt_max[i] - b->cur[i] ? nsteps : b->nt_max[i] - b->cur[i];
+      if (k <= 0) continue;
+      kbe_status s = kbe_step(b->sys[i], k);
+      if (s != KBE_OK) return s;
+      b->cur[i] += k;
+    }
+    e = join_to_main(b);
+    if (e != cudaSuccess) return batch_fail(KBE_ERR_CUDA, std::string("batch_step: ") + cudaGetErrorString(e));
+    return KBE_OK;
+  }
   for (int t = 0; t < nsteps; ++t) {
     bool any = false;
     for (size_t i = 0; i < b->sys.size(); ++i) {
@@ -173,6 +189,17 @@ kbe_status kbe_batch_step(kbe_batch *b, int nsteps) {
   }
   e = join_to_main(b);
   if (e != cudaSuccess) return batch_fail(KBE_ERR_CUDA, std::string("batch_step: ") + cudaGetErrorString(e));
+  return KBE_OK;
+}
+
+kbe_status kbe_batch_set_graphs(kbe_batch *b, int enable) {
+  if (!b) return KBE_ERR_ARG;
+  for (size_t i = 0; i < b->sys.size(); ++i) {
+    if (!b->sys[i]) continue;
+    kbe_status s = kbe_set_graphs(b->sys[i], enable);
+    if (s != KBE_OK) return s;
+  }
+  b->graphs = enable != 0;
   return KBE_OK;
 }
 

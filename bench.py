@@ -186,7 +186,7 @@ def time_trajectories(g, nt, steps, warmup, stream, sampler=None, dist=None):
 def roofline(prof, precision, t_dev):
     """achieved: the method's algorithmic flops (24 n^2 N_b^3 n_k per sweep, the
     G^> form of Eq. 6) over the summed sweep event time; the kernel executes
-    5/6 of them (dG form), reported as achieved_executed / frac_executed."""
+    2/3 of them (the I^<, I^> - I^< form), reported as achieved_executed / frac_executed."""
     sweep_s = prof["sweep_ms"] / 1e3
     achieved = prof["sweep_flops"] / sweep_s / 1e9 if sweep_s > 0 else 0.0
     executed = prof["sweep_flops_executed"] / sweep_s / 1e9 if sweep_s > 0 else 0.0

@@ -168,8 +168,8 @@ void free_all(kbe_handle *h) {
 
 // collision sweep flops of one launch at row n: the method's count with the
 // G^> form of Eq. 6 (3 N_b^3 complex multiply-adds per stored block, ~24 n^2
-// N_b^3 n_k flops) and the count this kernel executes with the dG form
-// (2 products per node above the output, 3 on [0, t_j])
+// N_b^3 n_k flops) and the count the kernel executes with the (I^<, I^> - I^<)
+// form (2 products per node, 3 at the two trapezoid end nodes of [0, t_j])
 double sweep_flops(const kbe_handle *h, int n) {
   const double nb3 = (double)h->cfg.nb * h->cfg.nb * h->cfg.nb;
   const double cm = 2.0 * (n + 1.0) * (n + 1.0) + (double)n * (n + 3.0);
@@ -177,7 +177,7 @@ double sweep_flops(const kbe_handle *h, int n) {
 }
 double sweep_flops_executed(const kbe_handle *h, int n) {
   const double nb3 = (double)h->cfg.nb * h->cfg.nb * h->cfg.nb;
-  const double cm = 2.5 * n * (double)n + 5.5 * n + 2.0;
+  const double cm = 2.0 * n * (double)n + 6.0 * n + 2.0;
   return 8.0 * cm * nb3 * h->mesh.nk;
 }
 double sweep_bytes(const kbe_handle *h, int n) {

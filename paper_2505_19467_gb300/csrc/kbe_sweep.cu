@@ -5,16 +5,20 @@
 // for j = 0..n and x in {<, >}. The history holds G only for l >= j; above
 // the diagonal G(l,j) = -G(j,l)^+ (the paper keeps G^> below and G^< above
 // the diagonal for the same reason). It stores, per block, G^< and
-// dG = G^< - G^> (so that G^> never has to be formed): with
-// C1 = w^(n)_l (S^> - S^<), C2^x = dt S^x and f = w^(j)_l / dt,
-//   I^<(n,j) = sum_l C1 G^<(l,j) + sum_{l<=j} f C2^< dG(l,j),
-//   I^>(n,j) = sum_l C1 G^<(l,j) + sum_{l<=j} (f C2^> - C1) dG(l,j)
-//                                - sum_{l>j}  C1 dG(l,j):
-// three complex multiply-adds per element and node for l <= j, two above.
+// dG = G^< - G^> (so that G^> never has to be formed). With
+// C1 = w^(n)_l (S^> - S^<), C2^< = dt S^<, C3 = dt S^> - C1 and f = w^(j)_l / dt
+// the kernels accumulate X = I^< and Y = I^> - I^<:
+//   X(n,j) = sum_l C1 G^<(l,j) + sum_{l<=j} f C2^< dG(l,j),
+//   Y(n,j) = sum_{l<=j} (w^(j)_l - w^(n)_l) (S^> - S^<) dG(l,j) - sum_{l>j} C1 dG(l,j).
+// Both quadratures give every interior node of [0, t_j] the weight dt, so Y
+// takes only the nodes above the output and the few end nodes where the
+// weights differ (there its coefficient is f (C3 - C2^<) + (f - 1) C1): two
+// complex multiply-adds per element and node, three at the end nodes.
 //
-// Work per evaluation: 3 N_b^3 complex multiply-adds per stored block and k,
-// i.e. 24 n^2 N_b^3 n_k flops for n^2 N_b^2 n_k complex numbers read: about
-// 1.5 N_b flop per byte in FP64, far right of the FP64 ridge on GB300 (the
+// Work per evaluation: ~2 N_b^3 complex multiply-adds per stored block, k and
+// use (each block serves one column j as stored and one as an adjoint), i.e.
+// ~16 n^2 N_b^3 n_k flops for n^2 N_b^2 n_k complex numbers read: about
+// N_b flop per byte in FP64, far right of the FP64 ridge on GB300 (the
 // FP64 pipe is ~1.2 TFLOP/s against ~7 TB/s of HBM, and the FP32 pipe ~61x
 // the FP64 one). Three arithmetic forms share one kernel template: every
 // thread owns one output element (k, a, b) of both components and streams
@@ -26,12 +30,11 @@
 //          exactly (p = fl(xh*yh), e = fma(xh, yh, -p) + xh*yl + xl*yh) and
 //          accumulated with an error-free TwoSum into a (hi, lo) pair:
 //          ~2^-44 relative accuracy at FP32-pipe speed.
-//   C64  : complex64 history, FP32 partial products per l, partial sums
-//          added into a compensated (TwoSum) accumulator.
-// The Sigma row is first turned into three coefficient rows
-// C1 = w^(n)_l (S^> - S^<), C2^< = dt S^<, C3 = dt S^> - C1 in the history's
-// storage; the term-2 weights f = w^(j)_l / dt are then exact powers of two
-// (f = 1 inside, 1/2 at l = 0 and l = j, where f C2^> - C1 = (C3 - C1) / 2).
+//   C64  : complex64 history, FP32 partial sums over a group of nodes,
+//          folded into a compensated (TwoSum) accumulator.
+// The Sigma row is first turned into the three coefficient rows C1, C2^<, C3
+// in the history's storage; the trapezoid's term-2 weights f are then exact
+// powers of two (f = 1 inside, 1/2 at l = 0 and l = j).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -71,6 +74,7 @@ struct ArithF64 {
   using S = double2;   // stored complex
   using A = double2;   // accumulator
   static constexpr int V = 1;
+  static constexpr bool kGrouped = false;   // end() after every node (no-op here)
   static constexpr int kUnrollSmallNb = 1;   // nodes per loop iteration at N_b <= 4
   static constexpr int kMinBlocks = KBE_SWEEP_MINB_F64;   // CTAs of 256 per SM (register cap)
   static __device__ __forceinline__ void zero(A &a) { a = make_double2(0.0, 0.0); }
@@ -84,9 +88,9 @@ struct ArithF64 {
   static __device__ __forceinline__ S scale_w(double f, const S &x) { return c_scale(f, x); }
   static __device__ __forceinline__ S add(const S &x, const S &y) { return c_add(x, y); }
   static __device__ __forceinline__ double2 result(const A &a) { return a; }
-  static __device__ __forceinline__ void store(double2 *o, size_t blkc, const A &p, const A &l, const A &g) {
-    o[0] = c_add(p, l);
-    o[blkc] = c_add(p, g);
+  static __device__ __forceinline__ void store(double2 *o, size_t blkc, const A &x, const A &y) {
+    o[0] = x;
+    o[blkc] = c_add(x, y);
   }
 };
 
@@ -145,6 +149,7 @@ struct ArithDF64 {
   using S = float4;
   using A = float4;
   static constexpr int V = 1;
+  static constexpr bool kGrouped = false;   // renormalise after every node
   static constexpr int kUnrollSmallNb = 4;   // timed: +21 % at N_b = 4, a loss at N_b = 8
   static constexpr int kMinBlocks = KBE_SWEEP_MINB_DF64;
   static __device__ __forceinline__ void zero(A &a) { a = make_float4(0.f, 0.f, 0.f, 0.f); }
@@ -187,10 +192,10 @@ struct ArithDF64 {
   static __device__ __forceinline__ double2 result(const A &a) {
     return make_double2((double)a.x + (double)a.y, (double)a.z + (double)a.w);
   }
-  static __device__ __forceinline__ void store(double2 *o, size_t blkc, const A &p, const A &l, const A &g) {
-    const double2 pr = result(p);
-    o[0] = c_add(pr, result(l));
-    o[blkc] = c_add(pr, result(g));
+  static __device__ __forceinline__ void store(double2 *o, size_t blkc, const A &x, const A &y) {
+    const double2 xr = result(x);
+    o[0] = xr;
+    o[blkc] = c_add(xr, result(y));
   }
 };
 
@@ -213,6 +218,7 @@ struct ArithC64 {
   using S = float2;
   using A = AccC64;
   static constexpr int V = 1;
+  static constexpr bool kGrouped = true;    // the plain partial spans several nodes
   static constexpr int kUnrollSmallNb = 1;
   static constexpr int kMinBlocks = KBE_SWEEP_MINB_C64;
   static __device__ __forceinline__ void zero(A &a) { a.sum = make_float4(0.f, 0.f, 0.f, 0.f); }
@@ -237,10 +243,10 @@ struct ArithC64 {
   static __device__ __forceinline__ double2 result(const A &a) {
     return make_double2((double)a.sum.x + (double)a.sum.y, (double)a.sum.z + (double)a.sum.w);
   }
-  static __device__ __forceinline__ void store(double2 *o, size_t blkc, const A &p, const A &l, const A &g) {
-    const double2 pr = result(p);
-    o[0] = c_add(pr, result(l));
-    o[blkc] = c_add(pr, result(g));
+  static __device__ __forceinline__ void store(double2 *o, size_t blkc, const A &x, const A &y) {
+    const double2 xr = result(x);
+    o[0] = xr;
+    o[blkc] = c_add(xr, result(y));
   }
 };
 
@@ -256,6 +262,7 @@ struct ArithC64x2 {
   using S = float4;
   using A = AccC64x2;
   static constexpr int V = 2;
+  static constexpr bool kGrouped = true;
   static constexpr int kUnrollSmallNb = 1;
   static constexpr int kMinBlocks = KBE_SWEEP_MINB_C64X2;
   static __device__ __forceinline__ float2 lo(const S &x) { return make_float2(x.x, x.y); }
@@ -276,27 +283,60 @@ struct ArithC64x2 {
   static __device__ __forceinline__ S add(const S &x, const S &y) {
     return make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
   }
-  static __device__ __forceinline__ void store(double2 *o, size_t blkc, const A &p, const A &l, const A &g) {
-    ArithC64::store(o, blkc, p.h[0], l.h[0], g.h[0]);
-    ArithC64::store(o + 1, blkc, p.h[1], l.h[1], g.h[1]);
+  static __device__ __forceinline__ void store(double2 *o, size_t blkc, const A &x, const A &y) {
+    ArithC64::store(o, blkc, x.h[0], y.h[0]);
+    ArithC64::store(o + 1, blkc, x.h[1], y.h[1]);
   }
 };
 
 // ------------------------------------------------------------ the sweep ----
-// One memory-time node l for this thread's element (k, a, b): MODE 0 is a
-// node above the output (l > j, or j = 0): only C1 G^< and -C1 dG; MODE 1 an
-// interior node of [0, t_j] (f = 1); MODE 2 an end node of [0, t_j] (l = 0
-// or l = j, f = 1/2). LOWER: the block (l, j) is stored (l >= j), else its
-// adjoint -X(j, l)^+ is read.
+// Nodes per compensated group. A node adds N_b products per output into the
+// plain partial (begin() clears it, end() folds it into the compensated sum);
+// the C64 forms fold only every G nodes, so that at most KBE_C64_COMP_TERMS
+// products are summed in plain FP32 (their rounding stays ~1e-6 of the
+// group's magnitude, below the complex64 storage error at the mixed form's
+// accuracy bar) and the TwoSum costs 1/G of what a fold per node costs.
+#ifndef KBE_C64_COMP_TERMS
+#define KBE_C64_COMP_TERMS 32
+#endif
+template <class P, int NB>
+__host__ __device__ constexpr int comp_group() {
+  return P::kGrouped && NB < KBE_C64_COMP_TERMS ? KBE_C64_COMP_TERMS / NB : 1;
+}
+
+// counts the nodes of the current group; at the group's end folds the partials
+template <class P, int G>
+struct CompGroup {
+  int left = G;
+  __device__ __forceinline__ static void fold(typename P::A &x, typename P::A &y) {
+    P::end(x);
+    P::end(y);
+    P::begin(x);
+    P::begin(y);
+  }
+  __device__ __forceinline__ void node(typename P::A &x, typename P::A &y) {
+    if constexpr (G == 1) {
+      fold(x, y);
+    } else {
+      if (--left == 0) {
+        left = G;
+        fold(x, y);
+      }
+    }
+  }
+};
+
+// One memory-time node l for this thread's element (k, a, b), accumulating
+// X = I^< and Y = I^> - I^<: MODE 0 is a node above the output (l > j, or
+// j = 0): X += C1 G^<, Y -= C1 dG; MODE 1 an interior node of [0, t_j], where
+// both quadratures give weight dt and Y gets nothing: X += C1 G^< + C2^< dG;
+// MODE 2 a trapezoid end node of [0, t_j] (l = 0 or l = j, f = 1/2).
+// LOWER: the block (l, j) is stored (l >= j), else its adjoint -X(j, l)^+ is read.
 template <class P, int NB, int MODE, bool LOWER>
 __device__ __forceinline__ void sweep_node(const typename P::S *__restrict__ c1,
                                            const typename P::S *__restrict__ g, size_t blk, int nk,
-                                           int b, typename P::A &accP, typename P::A &accL,
-                                           typename P::A &accG) {
+                                           int b, typename P::A &accX, typename P::A &accY) {
   using S = typename P::S;
-  P::begin(accP);
-  P::begin(accL);
-  P::begin(accG);
 #pragma unroll
   for (int c = 0; c < NB; ++c) {
     const S A1 = c1[(size_t)c * nk];
@@ -308,33 +348,27 @@ __device__ __forceinline__ void sweep_node(const typename P::S *__restrict__ c1,
       Gl = P::negconj(g[(size_t)(b * NB + c) * nk]);
       D = P::negconj(g[blk + (size_t)(b * NB + c) * nk]);
     }
-    P::mac(accP, A1, Gl);
+    P::mac(accX, A1, Gl);
     if (MODE == 0) {
-      P::mac(accG, P::neg(A1), D);
+      P::mac(accY, P::neg(A1), D);
     } else if (MODE == 1) {
-      P::mac(accL, c1[blk + (size_t)c * nk], D);
-      P::mac(accG, c1[2 * blk + (size_t)c * nk], D);
-    } else {   // (f C2^> - C1) = (C3 - C1) / 2 at the end nodes
-      P::mac(accL, P::scale(0.5f, c1[blk + (size_t)c * nk]), D);
-      P::mac(accG, P::scale(0.5f, P::sub(c1[2 * blk + (size_t)c * nk], A1)), D);
+      P::mac(accX, c1[blk + (size_t)c * nk], D);
+    } else {   // f = 1/2: X += C2^< dG / 2, Y += (C3 - C2^< - C1) dG / 2
+      const S K2 = c1[blk + (size_t)c * nk];
+      P::mac(accX, P::scale(0.5f, K2), D);
+      P::mac(accY, P::scale(0.5f, P::sub(P::sub(c1[2 * blk + (size_t)c * nk], K2), A1)), D);
     }
   }
-  P::end(accP);
-  P::end(accL);
-  P::end(accG);
 }
 
 // One node of [0, t_j] with a general weight f = w^(j)_l / dt (the Gregory end
-// nodes): f C2^< dG for I^<, and (f C2^> - C1) dG = (f C3 + (f - 1) C1) dG for I^>.
+// nodes): X += C1 G^< + f C2^< dG and Y += (f (C3 - C2^<) + (f - 1) C1) dG,
+// the last coefficient being (w^(j)_l - w^(n)_l) (S^> - S^<).
 template <class P, int NB, bool LOWER>
 __device__ __forceinline__ void sweep_wnode(const typename P::S *__restrict__ c1,
                                             const typename P::S *__restrict__ g, size_t blk, int nk,
-                                            int b, double f, typename P::A &accP, typename P::A &accL,
-                                            typename P::A &accG) {
+                                            int b, double f, typename P::A &accX, typename P::A &accY) {
   using S = typename P::S;
-  P::begin(accP);
-  P::begin(accL);
-  P::begin(accG);
 #pragma unroll
   for (int c = 0; c < NB; ++c) {
     const S A1 = c1[(size_t)c * nk];
@@ -346,13 +380,11 @@ __device__ __forceinline__ void sweep_wnode(const typename P::S *__restrict__ c1
       Gl = P::negconj(g[(size_t)(b * NB + c) * nk]);
       D = P::negconj(g[blk + (size_t)(b * NB + c) * nk]);
     }
-    P::mac(accP, A1, Gl);
-    P::mac(accL, P::scale_w(f, c1[blk + (size_t)c * nk]), D);
-    P::mac(accG, P::add(P::scale_w(f, c1[2 * blk + (size_t)c * nk]), P::scale_w(f - 1.0, A1)), D);
+    const S K2 = c1[blk + (size_t)c * nk];
+    P::mac(accX, A1, Gl);
+    P::mac(accX, P::scale_w(f, K2), D);
+    P::mac(accY, P::add(P::scale_w(f, P::sub(c1[2 * blk + (size_t)c * nk], K2)), P::scale_w(f - 1.0, A1)), D);
   }
-  P::end(accP);
-  P::end(accL);
-  P::end(accG);
 }
 
 // grid: x = tiles of the N_b^2 n_k output elements, y = output column j
@@ -381,29 +413,39 @@ __global__ void __launch_bounds__(256, P::kMinBlocks) sweep_kernel(const typenam
   const S *cbase = Cf + (size_t)a * NB * nk + k;   // C1(l)_{a, .} at cbase + 3 l blk
   const S *hbase = H + k;
 
-  typename P::A accP, accL, accG;   // sum C1 G^<, the dG terms of I^<, of I^>
-  P::zero(accP);
-  P::zero(accL);
-  P::zero(accG);
+  typename P::A accX, accY;   // I^< and I^> - I^<
+  P::zero(accX);
+  P::zero(accY);
+  P::begin(accX);
+  P::begin(accY);
+  CompGroup<P, comp_group<P, NB>()> grp;
   // interior of [0, t_j] with weight 1: 0 < l < j (trapezoid), 3 <= l <= j - 3 (Gregory)
   const int ia = QUAD == kQuadTrapezoid ? 1 : 3, ib = QUAD == kQuadTrapezoid ? j : j - 2;
   constexpr int U = NB <= 4 ? P::kUnrollSmallNb : 1;
   if (j > 0) {
 #pragma unroll U
-    for (int l = max(l0, ia); l < min(l1, ib); ++l)
+    for (int l = max(l0, ia); l < min(l1, ib); ++l) {
       sweep_node<P, NB, 1, false>(cbase + (size_t)l * 3 * blk, hbase + tri(j, l) * 2 * blk, blk, nk, b,
-                                  accP, accL, accG);
+                                  accX, accY);
+      grp.node(accX, accY);
+    }
   }
 #pragma unroll U
-  for (int l = max(l0, j == 0 ? 0 : j + 1); l < l1; ++l)   // above the output
+  for (int l = max(l0, j == 0 ? 0 : j + 1); l < l1; ++l) {   // above the output
     sweep_node<P, NB, 0, true>(cbase + (size_t)l * 3 * blk, hbase + tri(l, j) * 2 * blk, blk, nk, b,
-                               accP, accL, accG);
+                               accX, accY);
+    grp.node(accX, accY);
+  }
   if (j > 0 && QUAD == kQuadTrapezoid) {
-    if (l0 == 0)   // end node l = 0 (adjoint block, 0 < j)
-      sweep_node<P, NB, 2, false>(cbase, hbase + tri(j, 0) * 2 * blk, blk, nk, b, accP, accL, accG);
-    if (j >= l0 && j < l1)   // end node l = j (diagonal block)
+    if (l0 == 0) {   // end node l = 0 (adjoint block, 0 < j)
+      sweep_node<P, NB, 2, false>(cbase, hbase + tri(j, 0) * 2 * blk, blk, nk, b, accX, accY);
+      grp.node(accX, accY);
+    }
+    if (j >= l0 && j < l1) {   // end node l = j (diagonal block)
       sweep_node<P, NB, 2, true>(cbase + (size_t)j * 3 * blk, hbase + tri(j, j) * 2 * blk, blk, nk, b,
-                                 accP, accL, accG);
+                                 accX, accY);
+      grp.node(accX, accY);
+    }
   } else if (j > 0) {   // Gregory: the three nodes at each end (every node for j <= 4)
     const int ns = j >= 5 ? 6 : j + 1;
     for (int s = 0; s < ns; ++s) {
@@ -412,16 +454,19 @@ __global__ void __launch_bounds__(256, P::kMinBlocks) sweep_kernel(const typenam
       const double f = quad_omega(kQuadGregory, j, l);
       if (l == j)
         sweep_wnode<P, NB, true>(cbase + (size_t)l * 3 * blk, hbase + tri(j, j) * 2 * blk, blk, nk, b, f,
-                                 accP, accL, accG);
+                                 accX, accY);
       else
         sweep_wnode<P, NB, false>(cbase + (size_t)l * 3 * blk, hbase + tri(j, l) * 2 * blk, blk, nk, b, f,
-                                  accP, accL, accG);
+                                  accX, accY);
+      grp.node(accX, accY);
     }
   }
+  P::end(accX);   // the last, partly filled group
+  P::end(accY);
   // outputs in complex numbers: nk, blk and k above count stored elements S
   const size_t blkc = blk * P::V;
   double2 *o = out + ((size_t)blockIdx.z * (n + 1) + j) * 2 * blkc + (size_t)ab * nk * P::V + (size_t)k * P::V;
-  P::store(o, blkc, accP, accL, accG);
+  P::store(o, blkc, accX, accY);
 }
 
 // I = sum over the z partial rows (FP64)
@@ -551,13 +596,14 @@ __device__ __forceinline__ void staged_issue(float2 *st, const float2 *__restric
   }
 }
 
-// one node on the staged operands; KIND 0: above the output (stored block,
-// C1 G^< and -C1 dG); 1: stored diagonal block; 2: adjoint block (-X(j, l)^+);
-// kinds 1 and 2 take the node weight f (1: the plain form, else f C2^< and
-// f C3 + (f - 1) C1)
+// one node on the staged operands, into X = I^< and Y = I^> - I^<. KIND 0:
+// above the output (stored block): X += C1 G^<, Y -= C1 dG; 3: interior of
+// [0, t_j] (adjoint block, both quadratures weigh it dt): X += C1 G^< + C2^< dG;
+// 1 (stored diagonal block) and 2 (adjoint block): a node of weight f = w^(j)_l / dt,
+// X += C1 G^< + f C2^< dG, Y += (f (C3 - C2^<) + (f - 1) C1) dG
 template <int NB, int KIND>
-__device__ __forceinline__ void staged_node(const float2 *st, int kk, int a, int b0, float f, AccC64 *accP,
-                                            AccC64 *accL, AccC64 *accG) {
+__device__ __forceinline__ void staged_node(const float2 *st, int kk, int a, int b0, float f, AccC64 *accX,
+                                            AccC64 *accY) {
   constexpr int KT = staged_kt(NB), NBB = staged_nbb(NB), NB2 = NB * NB;
   const float2 *c1 = st + (size_t)(0 * NB2 + a * NB) * KT + kk;
   const float2 *c2 = st + (size_t)(1 * NB2 + a * NB) * KT + kk;
@@ -565,28 +611,23 @@ __device__ __forceinline__ void staged_node(const float2 *st, int kk, int a, int
   const float2 *gl = st + (size_t)(3 * NB2) * KT + kk;
   const float2 *dg = st + (size_t)(4 * NB2) * KT + kk;
 #pragma unroll
-  for (int q = 0; q < NBB; ++q) {
-    ArithC64::begin(accP[q]);
-    ArithC64::begin(accL[q]);
-    ArithC64::begin(accG[q]);
-  }
-#pragma unroll
   for (int c = 0; c < NB; ++c) {
     const float2 A1 = c1[(size_t)c * KT];
-    float2 K2 = make_float2(0.f, 0.f), K3 = make_float2(0.f, 0.f);
-    if (KIND != 0) {
+    float2 K2 = make_float2(0.f, 0.f), KY = make_float2(0.f, 0.f);
+    if (KIND == 0) {
+      KY = make_float2(-A1.x, -A1.y);
+    } else if (KIND == 3) {
       K2 = c2[(size_t)c * KT];
-      K3 = c3[(size_t)c * KT];
-      if (f != 1.0f) {
-        K3 = make_float2(f * K3.x + (f - 1.0f) * A1.x, f * K3.y + (f - 1.0f) * A1.y);
-        K2 = make_float2(f * K2.x, f * K2.y);
-      }
+    } else {
+      const float2 k2 = c2[(size_t)c * KT], k3 = c3[(size_t)c * KT];
+      K2 = make_float2(f * k2.x, f * k2.y);
+      KY = make_float2(f * (k3.x - k2.x) + (f - 1.0f) * A1.x, f * (k3.y - k2.y) + (f - 1.0f) * A1.y);
     }
 #pragma unroll
     for (int q = 0; q < NBB; ++q) {
       const int b = b0 + q;
       float2 G, D;
-      if (KIND == 2) {   // X(l, j)_cb = -conj(G(j, l)_bc)
+      if (KIND >= 2) {   // X(l, j)_cb = -conj(G(j, l)_bc)
         const float2 g = gl[(size_t)(b * NB + c) * KT], d = dg[(size_t)(b * NB + c) * KT];
         G = make_float2(-g.x, g.y);
         D = make_float2(-d.x, d.y);
@@ -594,20 +635,48 @@ __device__ __forceinline__ void staged_node(const float2 *st, int kk, int a, int
         G = gl[(size_t)(c * NB + b) * KT];
         D = dg[(size_t)(c * NB + b) * KT];
       }
-      ArithC64::mac(accP[q], A1, G);
-      if (KIND == 0) {
-        ArithC64::mac(accG[q], make_float2(-A1.x, -A1.y), D);
-      } else {
-        ArithC64::mac(accL[q], K2, D);
-        ArithC64::mac(accG[q], K3, D);
-      }
+      ArithC64::mac(accX[q], A1, G);
+      if (KIND != 0) ArithC64::mac(accX[q], K2, D);
+      if (KIND != 3) ArithC64::mac(accY[q], KY, D);
     }
   }
+}
+
+// the staged kernels' compensated groups (comp_group nodes each) over their NBB outputs
+template <int NB>
+struct StagedGroup {
+  static constexpr int G = comp_group<ArithC64, NB>();
+  int left = G;
+  __device__ __forceinline__ static void fold(AccC64 *accX, AccC64 *accY) {
 #pragma unroll
-  for (int q = 0; q < NBB; ++q) {
-    ArithC64::end(accP[q]);
-    ArithC64::end(accL[q]);
-    ArithC64::end(accG[q]);
+    for (int q = 0; q < staged_nbb(NB); ++q) {
+      ArithC64::end(accX[q]);
+      ArithC64::end(accY[q]);
+      ArithC64::begin(accX[q]);
+      ArithC64::begin(accY[q]);
+    }
+  }
+  __device__ __forceinline__ void node(AccC64 *accX, AccC64 *accY) {
+    if (--left == 0) {
+      left = G;
+      fold(accX, accY);
+    }
+  }
+};
+
+// node l of output column j: above the output, interior of [0, t_j], or a
+// weighted node (stored diagonal / adjoint end node)
+template <int NB, int QUAD>
+__device__ __forceinline__ void staged_any_node(const float2 *st, int kk, int a, int b0, int j, int l,
+                                                AccC64 *accX, AccC64 *accY) {
+  if (l > j || j == 0) {
+    staged_node<NB, 0>(st, kk, a, b0, 1.0f, accX, accY);
+  } else if (QUAD == kQuadTrapezoid ? (l > 0 && l < j) : (l >= 3 && l <= j - 3)) {
+    staged_node<NB, 3>(st, kk, a, b0, 1.0f, accX, accY);
+  } else {
+    const float f = (float)quad_omega(QUAD, j, l);
+    if (l == j) staged_node<NB, 1>(st, kk, a, b0, f, accX, accY);
+    else staged_node<NB, 2>(st, kk, a, b0, f, accX, accY);
   }
 }
 
@@ -628,13 +697,15 @@ __global__ void __launch_bounds__(kStagedThreads, KBE_STAGED_MINB)
   const int l0 = blockIdx.z * lchunk;
   const int l1 = min(n + 1, l0 + lchunk);
   const int nodes = max(l1 - l0, 0);
-  AccC64 accP[NBB], accL[NBB], accG[NBB];
+  AccC64 accX[NBB], accY[NBB];   // I^< and I^> - I^<
 #pragma unroll
   for (int q = 0; q < NBB; ++q) {
-    ArithC64::zero(accP[q]);
-    ArithC64::zero(accL[q]);
-    ArithC64::zero(accG[q]);
+    ArithC64::zero(accX[q]);
+    ArithC64::zero(accY[q]);
+    ArithC64::begin(accX[q]);
+    ArithC64::begin(accY[q]);
   }
+  StagedGroup<NB> grp;
   // node i is l = l0 + i; its block is stored at (l, j) when l >= j, else (j, l)
   auto tblk = [&](int l) -> size_t { return l >= j ? tri(l, j) : tri(j, l); };
 #pragma unroll
@@ -651,22 +722,17 @@ __global__ void __launch_bounds__(kStagedThreads, KBE_STAGED_MINB)
     cp_async_wait<kStages - 1>();   // this thread's copies of node i have landed
     __syncthreads();                // and everybody else's
     const float2 *st = smem + (size_t)(i % kStages) * staged_stage_elems(NB);
-    const int l = l0 + i;
-    if (l > j || j == 0) {
-      staged_node<NB, 0>(st, kk, a, b0, 1.0f, accP, accL, accG);
-    } else {
-      const float f = (float)quad_omega(QUAD, j, l);
-      if (l == j) staged_node<NB, 1>(st, kk, a, b0, f, accP, accL, accG);
-      else staged_node<NB, 2>(st, kk, a, b0, f, accP, accL, accG);
-    }
+    staged_any_node<NB, QUAD>(st, kk, a, b0, j, l0 + i, accX, accY);
+    grp.node(accX, accY);
     __syncthreads();                // the stage may be refilled next iteration
   }
+  StagedGroup<NB>::fold(accX, accY);   // the last, partly filled group
   const int k = k0 + kk;
   if (k >= nk) return;
   const size_t blk = (size_t)NB * NB * nk;
   double2 *o = out + ((size_t)blockIdx.z * (n + 1) + j) * 2 * blk + k;
 #pragma unroll
-  for (int q = 0; q < NBB; ++q) ArithC64::store(o + (size_t)(a * NB + b0 + q) * nk, blk, accP[q], accL[q], accG[q]);
+  for (int q = 0; q < NBB; ++q) ArithC64::store(o + (size_t)(a * NB + b0 + q) * nk, blk, accX[q], accY[q]);
 }
 
 
@@ -768,13 +834,15 @@ __global__ void __launch_bounds__(kStagedThreads, KBE_STAGED_MINB)
     tma_load_3d(st, &tmC, 2 * k0, 0, 3 * l, &bar[s]);
     tma_load_4d(st + (size_t)3 * NB2 * KT, &tmH, 2 * k0, 0, 0, tb, &bar[s]);
   };
-  AccC64 accP[NBB], accL[NBB], accG[NBB];
+  AccC64 accX[NBB], accY[NBB];   // I^< and I^> - I^<
 #pragma unroll
   for (int q = 0; q < NBB; ++q) {
-    ArithC64::zero(accP[q]);
-    ArithC64::zero(accL[q]);
-    ArithC64::zero(accG[q]);
+    ArithC64::zero(accX[q]);
+    ArithC64::zero(accY[q]);
+    ArithC64::begin(accX[q]);
+    ArithC64::begin(accY[q]);
   }
+  StagedGroup<NB> grp;
   if (tid == 0)
     for (int i = 0; i < kStages - 1 && i < nodes; ++i) issue(i);
   int issued = min(kStages - 1, nodes);
@@ -796,22 +864,17 @@ __global__ void __launch_bounds__(kStagedThreads, KBE_STAGED_MINB)
       return;
     }
     const float2 *st = smem + (size_t)s * staged_stage_elems(NB);
-    const int l = l0 + i;
-    if (l > j || j == 0) {
-      staged_node<NB, 0>(st, kk, a, b0, 1.0f, accP, accL, accG);
-    } else {
-      const float f = (float)quad_omega(QUAD, j, l);
-      if (l == j) staged_node<NB, 1>(st, kk, a, b0, f, accP, accL, accG);
-      else staged_node<NB, 2>(st, kk, a, b0, f, accP, accL, accG);
-    }
+    staged_any_node<NB, QUAD>(st, kk, a, b0, j, l0 + i, accX, accY);
+    grp.node(accX, accY);
     __syncthreads();   // stage s is free for the copy issued next iteration
   }
+  StagedGroup<NB>::fold(accX, accY);   // the last, partly filled group
   const int k = k0 + kk;
   if (k >= nk) return;
   const size_t blk = (size_t)NB2 * nk;
   double2 *o = out + ((size_t)blockIdx.z * (n + 1) + j) * 2 * blk + k;
 #pragma unroll
-  for (int q = 0; q < NBB; ++q) ArithC64::store(o + (size_t)(a * NB + b0 + q) * nk, blk, accP[q], accL[q], accG[q]);
+  for (int q = 0; q < NBB; ++q) ArithC64::store(o + (size_t)(a * NB + b0 + q) * nk, blk, accX[q], accY[q]);
 }
 
 // cuTensorMapEncodeTiled from the driver (no link against libcuda)

@@ -54,11 +54,11 @@ PEAKS = {
             "FP32 FMA: 152 SM x 128 lanes x 2 flop x 2.07 GHz"),
 }
 # DRAM traffic of the sweep per launch as a multiple of its algorithmic bytes,
-# from ncu (dram__bytes_read.sum + dram__bytes_write.sum): fp64 at row 501 of
-# the full c2 run (8.29 GB vs 4.17 GB), df64 / c64 at row 247 of the c2 system
-# (profiles/sweep_c2_n247.md); traffic grows with the triangle like the
-# algorithmic bytes, so the average launch is scaled by the same factor.
-TRAFFIC_RATIO = {"fp64": 1.99, "df64": 1.77, "c64": 1.75}
+# from ncu (dram__bytes_read.sum + dram__bytes_write.sum) at row 501 of the
+# full c2 run, all three forms (profiles/sweep_c2_n501_dram.md); traffic grows
+# with the triangle like the algorithmic bytes, so the average launch is
+# scaled by the same factor.
+TRAFFIC_RATIO = {"fp64": 2.00, "df64": 2.77, "c64": 1.87}
 DTYPES = {"fp64": "f64", "df64": "df64 (f32 hi/lo pairs; everything but the sweep f64)",
           "c64": "c64/f32 history + sweep (everything else f64)"}
 ORACLE_PREFIX = 40

@@ -469,6 +469,125 @@ __global__ void __launch_bounds__(256, P::kMinBlocks) sweep_kernel(const typenam
   P::store(o, blkc, accX, accY);
 }
 
+// ---------------------------------------------- C64, register-blocked ----
+// At N_b <= 2 a thread owns one k and all N_b^2 outputs (a, b) of both
+// components: each stored value and each coefficient is loaded once per node
+// and feeds N_b multiply-adds, against one per load in the per-element form
+// (whose loads, not its FP32 arithmetic, bound it at small N_b). Same
+// arithmetic and node classes as sweep_kernel.
+template <class P, int NB, int MODE, bool LOWER>
+__device__ __forceinline__ void blocked_node(const typename P::S *__restrict__ cf,
+                                             const typename P::S *__restrict__ g, size_t blk, int nk, double f,
+                                             typename P::A *X, typename P::A *Y) {
+  using S = typename P::S;
+  S Gm[NB * NB], Dm[NB * NB];   // X(l, j)_cb, dG(l, j)_cb
+#pragma unroll
+  for (int c = 0; c < NB; ++c)
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      if (LOWER) {
+        Gm[c * NB + b] = g[(size_t)(c * NB + b) * nk];
+        Dm[c * NB + b] = g[blk + (size_t)(c * NB + b) * nk];
+      } else {
+        Gm[c * NB + b] = P::negconj(g[(size_t)(b * NB + c) * nk]);
+        Dm[c * NB + b] = P::negconj(g[blk + (size_t)(b * NB + c) * nk]);
+      }
+    }
+#pragma unroll
+  for (int a = 0; a < NB; ++a)
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+      const S A1 = cf[(size_t)(a * NB + c) * nk];
+      S K2, KY;
+      if (MODE == 0) {            // above the output
+        KY = P::neg(A1);
+      } else if (MODE == 1) {     // interior of [0, t_j]
+        K2 = cf[blk + (size_t)(a * NB + c) * nk];
+      } else {                    // weighted node (f), Y coefficient f (C3 - C2^<) + (f - 1) C1
+        const S k2 = cf[blk + (size_t)(a * NB + c) * nk], k3 = cf[2 * blk + (size_t)(a * NB + c) * nk];
+        K2 = P::scale_w(f, k2);
+        KY = P::add(P::scale_w(f, P::sub(k3, k2)), P::scale_w(f - 1.0, A1));
+      }
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        P::mac(X[a * NB + b], A1, Gm[c * NB + b]);
+        if (MODE != 0) P::mac(X[a * NB + b], K2, Dm[c * NB + b]);
+        if (MODE != 1) P::mac(Y[a * NB + b], KY, Dm[c * NB + b]);
+      }
+    }
+}
+
+template <class P, int NB>
+__device__ __forceinline__ void blocked_fold(typename P::A *X, typename P::A *Y) {
+#pragma unroll
+  for (int e = 0; e < NB * NB; ++e) CompGroup<P, 1>::fold(X[e], Y[e]);
+}
+
+// grid: x = tiles of n_k, y = output column j, z = split of the l range; out as
+// for sweep_kernel
+#ifndef KBE_BLOCKED_THREADS
+#define KBE_BLOCKED_THREADS 128
+#endif
+#ifndef KBE_BLOCKED_MINB
+#define KBE_BLOCKED_MINB 3   // 168 registers without spills at N_b = 2
+#endif
+template <class P, int NB, int QUAD>
+__global__ void __launch_bounds__(KBE_BLOCKED_THREADS, KBE_BLOCKED_MINB) sweep_blocked_kernel(const typename P::S *__restrict__ H,
+                                                               const typename P::S *__restrict__ Cf,
+                                                               double2 *__restrict__ out, int n, int nk,
+                                                               int lchunk, const int *__restrict__ skip) {
+  if (skip && *skip) return;
+  constexpr int NB2 = NB * NB, G = comp_group<P, NB>();
+  const int j = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nk) return;
+  const int l0 = blockIdx.z * lchunk;
+  const int l1 = min(n + 1, l0 + lchunk);
+  const size_t blk = (size_t)NB2 * nk;
+  const typename P::S *cbase = Cf + k, *hbase = H + k;
+  typename P::A X[NB2], Y[NB2];   // I^< and I^> - I^< for every (a, b)
+#pragma unroll
+  for (int e = 0; e < NB2; ++e) {
+    P::zero(X[e]);
+    P::zero(Y[e]);
+    P::begin(X[e]);
+    P::begin(Y[e]);
+  }
+  int left = G;
+  auto tick = [&]() {
+    if (--left == 0) {
+      left = G;
+      blocked_fold<P, NB>(X, Y);
+    }
+  };
+  const int ia = QUAD == kQuadTrapezoid ? 1 : 3, ib = QUAD == kQuadTrapezoid ? j : j - 2;
+  if (j > 0)
+    for (int l = max(l0, ia); l < min(l1, ib); ++l) {   // interior, adjoint blocks
+      blocked_node<P, NB, 1, false>(cbase + (size_t)l * 3 * blk, hbase + tri(j, l) * 2 * blk, blk, nk, 1.0, X, Y);
+      tick();
+    }
+  for (int l = max(l0, j == 0 ? 0 : j + 1); l < l1; ++l) {   // above the output
+    blocked_node<P, NB, 0, true>(cbase + (size_t)l * 3 * blk, hbase + tri(l, j) * 2 * blk, blk, nk, 1.0, X, Y);
+    tick();
+  }
+  if (j > 0) {   // the end nodes: l = 0 and l = j (trapezoid), three at each end (Gregory)
+    const int ns = QUAD == kQuadTrapezoid ? 2 : (j >= 5 ? 6 : j + 1);
+    for (int s = 0; s < ns; ++s) {
+      const int l = QUAD == kQuadTrapezoid ? (s == 0 ? 0 : j) : ((j >= 5 && s >= 3) ? j - 5 + s : s);
+      if (l < l0 || l >= l1) continue;
+      const double f = quad_omega(QUAD, j, l);
+      if (l == j)
+        blocked_node<P, NB, 2, true>(cbase + (size_t)l * 3 * blk, hbase + tri(j, j) * 2 * blk, blk, nk, f, X, Y);
+      else
+        blocked_node<P, NB, 2, false>(cbase + (size_t)l * 3 * blk, hbase + tri(j, l) * 2 * blk, blk, nk, f, X, Y);
+    }
+  }
+  blocked_fold<P, NB>(X, Y);
+  double2 *o = out + ((size_t)blockIdx.z * (n + 1) + j) * 2 * blk + k;
+#pragma unroll
+  for (int e = 0; e < NB2; ++e) P::store(o + (size_t)e * nk, blk, X[e], Y[e]);
+}
+
 // I = sum over the z partial rows (FP64)
 __global__ void reduce_partials_kernel(const double2 *__restrict__ part, double2 *__restrict__ I,
                                        size_t count, int nz, const int *__restrict__ skip) {
@@ -975,6 +1094,12 @@ bool use_staged(const Mesh &m, int prec) {
          m.nk % 2 == 0;
 }
 
+// C64 at N_b <= 2: one thread per k owns all N_b^2 outputs
+#ifndef KBE_SWEEP_C64_BLOCKED
+#define KBE_SWEEP_C64_BLOCKED 1
+#endif
+bool use_blocked(const Mesh &m, int prec) { return KBE_SWEEP_C64_BLOCKED && prec == KBE_PREC_C64 && m.nb <= 2; }
+
 // V: complex values of consecutive k per thread (the C64 pair form)
 int sweep_width(const Mesh &m, int prec) {
   return (KBE_SWEEP_C64_PAIRS && prec == KBE_PREC_C64 && m.nk % 2 == 0) ? 2 : 1;
@@ -1031,10 +1156,10 @@ SweepShape staged_shape(const Mesh &m, int n, int target = KBE_STAGED_TARGET) {
   return sh;
 }
 
-SweepShape sweep_shape(const Mesh &m, int n, int V = 1, int target = kTargetCtas / 152) {
+SweepShape sweep_shape(const Mesh &m, int n, int V = 1, int target = kTargetCtas / 152, int maxthreads = 256) {
   SweepShape sh;
   const long elems = (long)m.nb * m.nb * (m.nk / V);
-  sh.threads = elems >= 256 ? 256 : (int)((elems + 31) / 32) * 32;
+  sh.threads = elems >= maxthreads ? maxthreads : (int)((elems + 31) / 32) * 32;
   const long ty = (elems + sh.threads - 1) / sh.threads;
   const long base = (long)(n + 1) * ty;
   long nz = split_count(base, n, target);   // at least one l per split, bounded scratch
@@ -1062,6 +1187,26 @@ cudaError_t sweep_nb(const Mesh &m, int n, const void *H, const void *Cf, double
   else
     sweep_kernel<P, NB, kQuadTrapezoid><<<sh.grid, sh.threads, 0, st>>>(
         (const typename P::S *)H, (const typename P::S *)Cf, out, n, nkS, sh.lchunk, skip);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || sh.nz == 1) return e;
+  const size_t count = (size_t)(n + 1) * 2 * m.nb * m.nb * m.nk;
+  reduce_partials_kernel<<<grid_for(count), 256, 0, st>>>(part, I, count, sh.nz, skip);
+  return cudaGetLastError();
+}
+
+template <int NB>
+cudaError_t sweep_blocked(const Mesh &m, int n, const void *H, const void *Cf, double2 *I, double2 *part,
+                          cudaStream_t st, const int *skip, int quad) {
+  const Mesh m1{1, m.L0, m.L1, m.nk};   // one thread per k
+  SweepShape sh = sweep_shape(m1, n, 1, tuned_target(KBE_PREC_C64, quad, m, n, kTargetCtas / 152),
+                              KBE_BLOCKED_THREADS);
+  double2 *out = sh.nz > 1 ? part : I;
+  if (quad == kQuadGregory)
+    sweep_blocked_kernel<ArithC64, NB, kQuadGregory><<<sh.grid, sh.threads, 0, st>>>(
+        (const float2 *)H, (const float2 *)Cf, out, n, m.nk, sh.lchunk, skip);
+  else
+    sweep_blocked_kernel<ArithC64, NB, kQuadTrapezoid><<<sh.grid, sh.threads, 0, st>>>(
+        (const float2 *)H, (const float2 *)Cf, out, n, m.nk, sh.lchunk, skip);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || sh.nz == 1) return e;
   const size_t count = (size_t)(n + 1) * 2 * m.nb * m.nb * m.nk;
@@ -1103,6 +1248,9 @@ cudaError_t sweep_prec(const Mesh &m, int n, int prec, const void *H, const void
                        double2 *part, cudaStream_t st, const int *skip, int quad, int *status, int inject) {
   if constexpr (NB == 1 || NB == 2 || NB == 4 || NB == 8 || NB == 16) {
     if (use_staged(m, prec)) return sweep_staged<NB>(m, n, H, Cf, I, part, st, skip, quad, status, inject);
+  }
+  if constexpr (NB <= 2) {
+    if (use_blocked(m, prec)) return sweep_blocked<NB>(m, n, H, Cf, I, part, st, skip, quad);
   }
   if (prec == KBE_PREC_FP64) return sweep_nb<ArithF64, NB>(m, n, H, Cf, I, part, st, skip, quad);
   if (prec == KBE_PREC_DF64) return sweep_nb<ArithDF64, NB>(m, n, H, Cf, I, part, st, skip, quad);

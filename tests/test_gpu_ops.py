@@ -134,6 +134,36 @@ def test_c64_staged_sweep_ragged_tiles(nb, L, n, quad):
     assert relerr(gl, Il)[1] < 1e-5 and relerr(gg, Ig)[1] < 1e-5
 
 
+@pytest.mark.parametrize("quad", [0, 1])
+@pytest.mark.parametrize("nb,L,n", [(1, (7, 1), 5), (2, (8, 1), 0), (2, (129, 1), 9), (2, (3, 3), 1),
+                                    (2, (300, 1), 40), (1, (131, 1), 33)])
+def test_c64_blocked_sweep_small_nb(nb, L, n, quad):
+    """the register-blocked C64 sweep (N_b <= 2, one thread per k owning every
+    (a, b)): odd n_k leave the last CTA ragged, and the larger rows split the l
+    range over CTAs; against the oracle at the mixed form's bar"""
+    rng = np.random.default_rng(500 + nb * 7 + n)
+    nk = L[0] * L[1]
+    dt = 0.03
+    ntri = tri(n, n) + 1
+    Hl = ki.random_blocks(rng, (ntri, nk, nb, nb))
+    Hg = ki.random_blocks(rng, (ntri, nk, nb, nb))
+    Sl = ki.random_blocks(rng, (n + 1, nk, nb, nb))
+    Sg = ki.random_blocks(rng, (n + 1, nk, nb, nb))
+    Il, Ig = oracle.collision_row(nb, nk, n, dt, Hl, Hg, Sl, Sg, quadrature=quad)
+    p = kbe.KBE_PREC_C64
+    H64 = dev(to_dev_blocks(Hl, Hg))
+    H = torch.empty(H64.numel() * 2, dtype=torch.float32, device="cuda")
+    kbe.pack(p, H64, H, ntri, nb * nb * nk)
+    S = dev(to_dev_blocks(Sl, Sg))
+    I = torch.full((n + 1, 2, nb, nb, nk), float("nan"), dtype=torch.complex128, device="cuda")
+    work = torch.empty(kbe.collision_row_workspace(nb, L, n, p) // 4 + 1, dtype=torch.float32, device="cuda")
+    kbe.collision_row(nb, L, n, dt, H, S, I, precision=p, work=work, quadrature=quad)
+    torch.cuda.synchronize()
+    gl, gg = from_dev_blocks(I.cpu().numpy())
+    assert np.all(np.isfinite(gl)) and np.all(np.isfinite(gg))
+    assert relerr(gl, Il)[1] < 1e-5 and relerr(gg, Ig)[1] < 1e-5
+
+
 def _herm_batch(rng, nk, nb, scale=1.5):
     a = ki.random_blocks(rng, (nk, nb, nb), scale)
     return 0.5 * (a + np.conj(np.swapaxes(a, 1, 2)))

@@ -8,8 +8,8 @@
 // rows, h, U, V, the Sigma and collision rows of every stage) are recomputed
 // from the history, then the step's operations are transposed in reverse
 // order. The transposes are those of the kernels' own arithmetic (the
-// trapezoid sweep in the dG form, the DFT Sigma, the truncated power series
-// of the propagators), so the gradient is that of the computed trajectory.
+// sweep in its (I^<, I^> - I^<) form, the DFT Sigma, the truncated power
+// series of the propagators), so the gradient is that of the computed trajectory.
 //
 // Convention: for a complex variable z the adjoint lam_z is defined by
 // dL = Re sum conj(lam_z) dz. A holomorphic use z = c w gives lam_w += conj(c)
@@ -52,51 +52,29 @@ __global__ void unpack_fp64_kernel(const double2 *__restrict__ src, double2 *__r
 }
 
 // ------------------------------------------ collision row: coefficients ----
-// Forward (one output column j, l = 0..n, X = G(l, j) or -G(j, l)^+):
-//   I^<(j) = sum_l C1(l) X^<(l,j) + f(j,l) C2^<(l) D(l,j)
-//   I^>(j) = sum_l C1(l) X^>(l,j) + f(j,l) C2^>(l) D(l,j),  D = X^< - X^>
-// with C1 = w^(n)_l (S^> - S^<), C2^x = dt S^x, f = w^(j)_l / dt (trapezoid or
-// Gregory weights, quad_omega). Transposed,
-// for each l:
-//   lam_C1(l)  = sum_j lam^<_j X^<(l,j)^+ + lam^>_j X^>(l,j)^+
-//              = sum_j (lam^<_j + lam^>_j) X^<(l,j)^+ - lam^>_j D(l,j)^+
-//   lam_C2x(l) = sum_j f(j,l) lam^x_j D(l,j)^+
-//   lam_S^<(l) = -w^(n)_l lam_C1 + dt lam_C2^<,  lam_S^>(l) = w^(n)_l lam_C1 + dt lam_C2^>.
-// Stored block (l, j), j <= l: X^+_{cb} = conj(G(l,j)_bc); for j > l the
-// block (j, l) is read: X(l,j)^+_{cb} = -G(j,l)_cb.
-// One node j for the output (l; a, b) in fused form: with lam^P = lam^< + lam^>,
-//   LOWER (block (l, j)):  a1 += lam^P conj(G^<)_bc - lam^> conj(dG)_bc,  aL/aG += lam^x conj(dG)_bc
-//   upper (block (j, l)):  a1 += -lam^P G^<_cb + lam^> dG_cb,            aL/aG += -lam^x dG_cb
-// (f is applied by the caller: it is uniform over each run of nodes).
-template <int NB, bool LOWER, bool F>
-__device__ __forceinline__ void coef_node(const double2 *__restrict__ lam, const double2 *__restrict__ g,
-                                          size_t blk, int nk, int b, double2 &a1, double2 &aL,
-                                          double2 &aG) {
-#pragma unroll
-  for (int c = 0; c < NB; ++c) {
-    const double2 LL = lam[(size_t)c * nk], LG = lam[blk + (size_t)c * nk];
-    const double2 LP = c_add(LL, LG);
-    if (LOWER) {
-      const double2 gl = g[(size_t)(b * NB + c) * nk], dg = g[blk + (size_t)(b * NB + c) * nk];
-      a1 = c_fmac(LP, gl, a1);
-      a1 = c_fnmac(LG, dg, a1);
-      if (F) {
-        aL = c_fmac(LL, dg, aL);
-        aG = c_fmac(LG, dg, aG);
-      }
-    } else {
-      const double2 gl = g[(size_t)(c * NB + b) * nk], dg = g[blk + (size_t)(c * NB + b) * nk];
-      a1 = c_fnma(LP, gl, a1);
-      a1 = c_fma(LG, dg, a1);
-      if (F) {
-        aL = c_fnma(LL, dg, aL);
-        aG = c_fnma(LG, dg, aG);
-      }
-    }
-  }
+// Forward, in the form the sweep computes (one output column j, l = 0..n,
+// X_lj = G^<(l, j) or -G^<(j, l)^+, D_lj the same of dG = G^< - G^>, w_l = w^(n)_l,
+// Delta = S^> - S^<): X = I^< and Y = I^> - I^<,
+//   X(j) = sum_l w_l Delta_l X_lj + sum_{l<=j} w^(j)_l S^<_l D_lj
+//   Y(j) = -sum_{l>j} w_l Delta_l D_lj + sum_{l<=j} (w^(j)_l - w_l) Delta_l D_lj.
+// With lam_X = lam^< + lam^>, lam_Y = lam^> the transpose for each l is
+//   lam_Delta(l) = w_l (T1 - T2) + T4,  lam_S^>(l) = lam_Delta,  lam_S^<(l) = T3 - lam_Delta,
+//   T1 = sum_j lam_X(j) X_lj^+,            T2 = sum_{j<l} lam_Y(j) D_lj^+,
+//   T3 = sum_{j>=l} w^(j)_l lam_X(j) D_lj^+, T4 = sum_{j>=l} (w^(j)_l - w_l) lam_Y(j) D_lj^+.
+// Above the diagonal (j > l) w^(j)_l equals w_l except for the few j whose
+// grid puts l among its end weights (trapezoid: none; Gregory: j < l + 3 or
+// j < 5): those "special" nodes carry T4 and their own T3 weight, the rest
+// (the bulk) two products. Stored block (l, j), j <= l: X_lj^+ {cb} = conj(G(l,j)_bc);
+// for j > l the block (j, l) is read: X_lj^+ {cb} = -G(j,l)_cb.
+template <int NB>
+__device__ __forceinline__ void lam_xy(const double2 *__restrict__ lam, size_t blk, int nk, int c, double2 &lx,
+                                       double2 &ly) {
+  const double2 ll = lam[(size_t)c * nk], lg = lam[blk + (size_t)c * nk];
+  lx = c_add(ll, lg);
+  ly = lg;
 }
 
-// grid: x = tiles of the N_b^2 n_k elements (a, b, k) of one l, y = l (0..n),
+// grid: x = tiles of the N_b^2 n_k outputs (l; a, b; k), y = l (0..n),
 // z = split of the j range; out is lam_Sigma when gridDim.z == 1, else the
 // partial rows [z][l][x][a][b][k].
 template <int NB, int QUAD>
@@ -116,35 +94,63 @@ __global__ void __launch_bounds__(256, 2) adj_coef_kernel(const double2 *__restr
   const double2 *lbase = lamI + (size_t)a * NB * nk + k;   // lam_j(a, c) at + j 2 blk + c nk
   const double2 *hbase = H + k;
   const double2 z = make_double2(0, 0);
-  double2 a1 = z, aL = z, aG = z, dL = z, dG = z;
-  for (int j = j0; j < min(j1, l); ++j)   // stored blocks below the diagonal, f = 0
-    coef_node<NB, true, false>(lbase + (size_t)j * 2 * blk, hbase + tri(l, j) * 2 * blk, blk, nk, b, a1, aL, aG);
-  if (l >= j0 && l < j1) {                // the diagonal block, f = 1/2 (0 at l = 0)
-    if (l >= 1)
-      coef_node<NB, true, true>(lbase + (size_t)l * 2 * blk, hbase + tri(l, l) * 2 * blk, blk, nk, b, a1, dL, dG);
-    else
-      coef_node<NB, true, false>(lbase, hbase, blk, nk, b, a1, dL, dG);
-  }
-  if (QUAD == kQuadTrapezoid) {   // j > l: f = 1, or 1/2 when l = 0 is the end node
-    for (int j = max(j0, l + 1); j < j1; ++j)
-      coef_node<NB, false, true>(lbase + (size_t)j * 2 * blk, hbase + tri(j, l) * 2 * blk, blk, nk, b, a1, aL, aG);
-  } else {   // Gregory: f = w^(j)_l / dt per node
-    for (int j = max(j0, l + 1); j < j1; ++j) {
-      double2 tL = z, tG = z;
-      coef_node<NB, false, true>(lbase + (size_t)j * 2 * blk, hbase + tri(j, l) * 2 * blk, blk, nk, b, a1, tL, tG);
-      const double f = quad_omega(QUAD, j, l);
-      aL = make_double2(fma(f, tL.x, aL.x), fma(f, tL.y, aL.y));
-      aG = make_double2(fma(f, tG.x, aG.x), fma(f, tG.y, aG.y));
+  const double wn = dt * quad_omega(QUAD, n, l);
+  const int jb = QUAD == kQuadTrapezoid ? l + 1 : max(l + 3, 5);   // first bulk node above l
+  double2 t1 = z, t2 = z, t3 = z, s3 = z, s4 = z;
+  for (int j = j0; j < min(j1, l); ++j) {   // stored blocks (l, j) below the diagonal
+    const double2 *lj = lbase + (size_t)j * 2 * blk, *g = hbase + tri(l, j) * 2 * blk;
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+      double2 lx, ly;
+      lam_xy<NB>(lj, blk, nk, c, lx, ly);
+      t1 = c_fmac(lx, g[(size_t)(b * NB + c) * nk], t1);
+      t2 = c_fmac(ly, g[blk + (size_t)(b * NB + c) * nk], t2);
     }
   }
-  const double fu = (QUAD == kQuadTrapezoid && l == 0) ? 0.5 : 1.0;
-  const double fd = quad_omega(QUAD, l, l);   // the diagonal node's weight (0 at l = 0)
-  aL = c_add(c_scale(fu, aL), c_scale(fd, dL));
-  aG = c_add(c_scale(fu, aG), c_scale(fd, dG));
-  const double w1 = dt * quad_omega(QUAD, n, l);
+  // weighted nodes: the diagonal j = l and the special nodes above it
+  auto weighted = [&](int j) {
+    const bool diag = j == l;
+    const double2 *lj = lbase + (size_t)j * 2 * blk;
+    const double2 *g = hbase + (diag ? tri(l, l) : tri(j, l)) * 2 * blk;
+    double2 p = z, q = z;
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+      double2 lx, ly;
+      lam_xy<NB>(lj, blk, nk, c, lx, ly);
+      if (diag) {
+        t1 = c_fmac(lx, g[(size_t)(b * NB + c) * nk], t1);
+        const double2 dg = g[blk + (size_t)(b * NB + c) * nk];
+        p = c_fmac(lx, dg, p);
+        q = c_fmac(ly, dg, q);
+      } else {
+        t1 = c_fnma(lx, g[(size_t)(c * NB + b) * nk], t1);
+        const double2 dg = g[blk + (size_t)(c * NB + b) * nk];
+        p = c_fnma(lx, dg, p);
+        q = c_fnma(ly, dg, q);
+      }
+    }
+    const double wj = dt * quad_omega(QUAD, j, l);
+    s3 = make_double2(fma(wj, p.x, s3.x), fma(wj, p.y, s3.y));
+    s4 = make_double2(fma(wj - wn, q.x, s4.x), fma(wj - wn, q.y, s4.y));
+  };
+  if (l >= j0 && l < j1) weighted(l);
+  for (int j = max(j0, l + 1); j < min(j1, jb); ++j) weighted(j);
+  for (int j = max(j0, jb); j < j1; ++j) {   // bulk above the diagonal: w^(j)_l = w_l
+    const double2 *lj = lbase + (size_t)j * 2 * blk, *g = hbase + tri(j, l) * 2 * blk;
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+      double2 lx, ly;
+      lam_xy<NB>(lj, blk, nk, c, lx, ly);
+      t1 = c_fnma(lx, g[(size_t)(c * NB + b) * nk], t1);
+      t3 = c_fnma(lx, g[blk + (size_t)(c * NB + b) * nk], t3);
+    }
+  }
+  // lam_Delta = wn (t1 - t2) + s4; T3 = s3 + wn t3
+  const double2 ld = c_add(c_scale(wn, c_sub(t1, t2)), s4);
+  const double2 T3 = c_add(s3, c_scale(wn, t3));
   double2 *o = out + ((size_t)blockIdx.z * (n + 1) + l) * 2 * blk + (size_t)ab * nk + k;
-  o[0] = c_add(c_scale(-w1, a1), c_scale(dt, aL));
-  o[blk] = c_add(c_scale(w1, a1), c_scale(dt, aG));
+  o[0] = c_sub(T3, ld);
+  o[blk] = ld;
 }
 
 // C1(l) = w^(n)_l (S^>(l) - S^<(l)), l = 0..n, one block per l
@@ -168,15 +174,20 @@ __global__ void sum_partials_kernel(const double2 *__restrict__ part, double2 *_
 }
 
 // ----------------------------------------------- collision row: history ----
-// Every stored block (i, j'), i <= n, is used twice by the forward sweep:
-// as X(l = i, j = j') and, for j' < i, as X(l = j', j = i) = -G(i, j')^+.
-// In the (G^<, G^>) pair, I^< = C1 X^< + f C2^< (X^< - X^>) and
-// I^> = C1 X^> + f C2^> (X^< - X^>), so with c = f (C2^<^+ lam^< + C2^>^+ lam^>):
-//   use 1 (f = f(j', i)):  lam^<(i,j') += C1(i)^+ lam^<_j' + c,  lam^>(i,j') += C1(i)^+ lam^>_j' - c
-//   use 2 (f = f(i, j')):  lam^<(i,j') -= [C1(j')^+ lam^<_i + c]^+,  lam^>(i,j') -= [C1(j')^+ lam^>_i - c]^+
+// Every stored block (i, j'), i <= n, is used twice by the forward sweep (the
+// X / Y form above, lam_X = lam^< + lam^>, lam_Y = lam^>):
+//   use 1, node l = i of column j' (stored block):
+//     j' < i: lam_G^<(i,j') += C1(i)^+ lam_X(j'),  lam_dG(i,j') -= C1(i)^+ lam_Y(j')
+//     j' = i: lam_G^< += C1(i)^+ lam_X(i),
+//             lam_dG  += (w^(i)_i S^<_i)^+ lam_X(i) + ((w^(i)_i - w_i) Delta_i)^+ lam_Y(i)
+//   use 2 (j' < i), node l = j' of column i (adjoint block -G(i,j')^+):
+//     lam_G^<(i,j') -= [C1(j')^+ lam_X(i)]^+,
+//     lam_dG(i,j')  -= [w^(i)_j' S^<_j'^+ lam_X(i) + (w^(i)_j' - w_j') Delta_j'^+ lam_Y(i)]^+
+//   (the last term only where the two weights differ: never for the trapezoid).
+// The history's adjoint is kept for (G^<, G^>): lam^< += lam_G^< + lam_dG, lam^> -= lam_dG.
 // Row n of the triangle goes to lamRowN (the stage being differentiated).
 // C1 is precomputed per launch (adj_c1_kernel); each thread keeps its
-// column p of C1(i) and lam_i in registers.
+// column p of C1(i), lam_X(i) and lam_Y(i) in registers.
 // grid: x = tiles of the N_b^2 n_k elements (p, q, k), y = row i, z = chunk
 // of j' (each block written by exactly one thread: no reduction).
 template <int NB>
@@ -196,58 +207,61 @@ __global__ void __launch_bounds__(256, 2) adj_hist_kernel(const double2 *__restr
   const int j1 = min(i + 1, j0 + jchunk);
   const size_t blk = (size_t)NB * NB * nk;
   const size_t cs = (size_t)NB * nk;   // stride of the row index c
-  // this thread's column p of C1(i) and of lam_i, elements (c, p)
-  double2 c1i[NB], Li[NB], Gi[NB];
+  // this thread's column p of C1(i), lam_X(i) and lam_Y(i), elements (c, p)
+  double2 c1i[NB], LXi[NB], LYi[NB];
   {
     const double2 *ci = C1 + (size_t)i * blk + (size_t)p * nk + k;
     const double2 *li = lamI + (size_t)i * 2 * blk + (size_t)p * nk + k;
 #pragma unroll
     for (int c = 0; c < NB; ++c) {
       c1i[c] = ci[c * cs];
-      Li[c] = li[c * cs];
-      Gi[c] = li[blk + c * cs];
+      LYi[c] = li[blk + c * cs];
+      LXi[c] = c_add(li[c * cs], LYi[c]);
     }
   }
   const double2 z = make_double2(0, 0);
+  const double wni = dt * quad_omega(quad, n, i);
   for (int jp = j0; jp < j1; ++jp) {
     const double2 *lj = lamI + (size_t)jp * 2 * blk + (size_t)q * nk + k;   // lam_j'(c, q)
-    double2 dl = z, dg = z;
-#pragma unroll
-    for (int c = 0; c < NB; ++c) {   // use 1: C1(i)^+ lam_j'
-      dl = c_fmac(lj[c * cs], c1i[c], dl);
-      dg = c_fmac(lj[blk + c * cs], c1i[c], dg);
-    }
-    if (jp < i) {   // use 2: -[C1(j')^+ lam_i + c]^+ with c = f dt (S^<^+ lam^<_i + S^>^+ lam^>_i)
+    double2 gl = z, gd = z;
+    if (jp < i) {
       const double2 *cj = C1 + (size_t)jp * blk + (size_t)q * nk + k;     // C1(j')_{cq}
       const double2 *sj = Sig + (size_t)jp * 2 * blk + (size_t)q * nk + k; // S(j')_{cq}
       double2 t = z;
 #pragma unroll
       for (int c = 0; c < NB; ++c) {
-        const double2 cc = cj[c * cs];
-        dl = c_fnmac(cc, Li[c], dl);
-        dg = c_fnmac(cc, Gi[c], dg);
-        t = c_fmac(sj[c * cs], Li[c], t);
-        t = c_fmac(sj[blk + c * cs], Gi[c], t);
+        const double2 ly = lj[blk + c * cs], lx = c_add(lj[c * cs], ly);
+        gl = c_fmac(lx, c1i[c], gl);           // use 1: C1(i)^+ lam_X(j')
+        gd = c_fnmac(ly, c1i[c], gd);          //        -C1(i)^+ lam_Y(j')
+        gl = c_fnmac(cj[c * cs], LXi[c], gl);  // use 2: -[C1(j')^+ lam_X(i)]^+
+        t = c_fmac(sj[c * cs], LXi[c], t);     //        [S^<(j')^+ lam_X(i)]^+
       }
-      const double fB = quad_omega(quad, i, jp) * dt;
-      dl = make_double2(fma(-fB, t.x, dl.x), fma(-fB, t.y, dl.y));
-      dg = make_double2(fma(fB, t.x, dg.x), fma(fB, t.y, dg.y));
-    } else if (i >= 1) {   // the diagonal block, use 1 with f = 1/2: + c, - c
+      const double wB = dt * quad_omega(quad, i, jp), wY = wB - dt * quad_omega(quad, n, jp);
+      gd = make_double2(fma(-wB, t.x, gd.x), fma(-wB, t.y, gd.y));
+      if (wY != 0.0) {   // the weights of the two grids differ at this node (Gregory ends)
+        double2 u = z;
+#pragma unroll
+        for (int c = 0; c < NB; ++c) u = c_fmac(c_sub(sj[blk + c * cs], sj[c * cs]), LYi[c], u);
+        gd = make_double2(fma(-wY, u.x, gd.x), fma(-wY, u.y, gd.y));
+      }
+    } else {   // the diagonal block (node l = j = i)
       const double2 *si = Sig + (size_t)i * 2 * blk + (size_t)p * nk + k;   // S(i)_{cp}
-      double2 t = z;
+      double2 t = z, u = z;
 #pragma unroll
       for (int c = 0; c < NB; ++c) {
-        t = c_fmac(lj[c * cs], si[c * cs], t);
-        t = c_fmac(lj[blk + c * cs], si[blk + c * cs], t);
+        const double2 ly = lj[blk + c * cs], lx = c_add(lj[c * cs], ly);
+        const double2 sl = si[c * cs];
+        gl = c_fmac(lx, c1i[c], gl);
+        t = c_fmac(lx, sl, t);
+        u = c_fmac(ly, c_sub(si[blk + c * cs], sl), u);
       }
-      const double fA = quad_omega(quad, i, i) * dt;
-      dl = make_double2(fma(fA, t.x, dl.x), fma(fA, t.y, dl.y));
-      dg = make_double2(fma(-fA, t.x, dg.x), fma(-fA, t.y, dg.y));
+      const double wA = dt * quad_omega(quad, i, i), wY = wA - wni;
+      gd = make_double2(wA * t.x + wY * u.x, wA * t.y + wY * u.y);
     }
     double2 *dst = (i == n) ? lamRowN + (size_t)jp * 2 * blk : lamH + tri(i, jp) * 2 * blk;
     double2 *e0 = dst + (size_t)pq * nk + k;
-    *e0 = c_add(*e0, dl);
-    e0[blk] = c_add(e0[blk], dg);
+    *e0 = c_add(*e0, c_add(gl, gd));
+    e0[blk] = c_sub(e0[blk], gd);
   }
 }
 

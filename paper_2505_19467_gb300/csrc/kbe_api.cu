@@ -412,14 +412,14 @@ struct PhaseTimer {
   }
 };
 
-// flops of the collision-row transposes at row n (8 per complex multiply-add):
-// the coefficient transpose takes 2 per pair (l, j) below the diagonal and 4
-// on and above it; the history transpose 2 per block for the first use (4 on
-// the diagonal) and 4 for the second, per N_b^3 n_k
+// flops of the collision-row transposes at row n, in complex multiply-adds per
+// N_b^3 n_k: the coefficient transpose takes 2 per pair (l, j) off the diagonal
+// and 3 on it; the history transpose 4 per block below the diagonal (2 per use)
+// and 3 on it (the few Gregory end nodes with extra terms are not counted)
 double adj_sweep_flops(const kbe_handle *h, int n) {
   const double nb3 = (double)h->cfg.nb * h->cfg.nb * h->cfg.nb, N = n;
-  const double coef = 2.0 * N * (N + 1) / 2 + 4.0 * (N + 1) + 4.0 * N * (N + 1) / 2;
-  const double hist = 6.0 * N * (N + 1) / 2 + 4.0 * (N + 1);
+  const double coef = 2.0 * N * (N + 1) + 3.0 * (N + 1);
+  const double hist = 2.0 * N * (N + 1) + 3.0 * (N + 1);
   return 8.0 * (coef + hist) * nb3 * h->mesh.nk;
 }
 

@@ -294,10 +294,15 @@ kbe_status kbe_batch_reset(kbe_batch *b);
 kbe_status kbe_batch_step(kbe_batch *b, int nsteps);
 /* Wait for all systems; the first failing system's status. */
 kbe_status kbe_batch_synchronize(kbe_batch *b);
-/* Graph mode for the batch (kbe_set_graphs on every admitted system): each
- * kbe_batch_step(b, k) then runs every system's k steps as one captured graph
- * on its own stream (captured on the first call from a given row, replayed
- * after kbe_batch_reset), instead of interleaving single steps. */
+/* Graph mode for the batch. With a non-default stream, each kbe_batch_step(b, k)
+ * runs the k steps of every admitted system as ONE captured graph launched on
+ * that stream (each system's kernels on its own stream inside the graph):
+ * captured on the first call with a given (rows, counts, ring order) shape,
+ * replayed by later calls of the same shape, e.g. after kbe_batch_reset.
+ * Changing a system's inputs (kbe_set_*, kbe_autotune) invalidates the
+ * graph. On the default stream each system replays its own graph
+ * (kbe_set_graphs). Results are bitwise those of the stream-ordered batch.
+ * Synchronises the batch's stream. enable = 0 switches back. */
 kbe_status kbe_batch_set_graphs(kbe_batch *b, int enable);
 
 /* Message of the last error of this handle; with NULL, of the last failed

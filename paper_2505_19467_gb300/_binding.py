@@ -462,7 +462,8 @@ class KBEBatch:
         _check(load().kbe_batch_step(self._b, int(nsteps)))
 
     def set_graphs(self, enable: bool = True):
-        """each system replays its steps as one captured graph (kbe_batch_set_graphs)"""
+        """graph mode: one captured graph per batch step call on a non-default
+        stream, per-system graphs on the default one (kbe_batch_set_graphs)"""
         _check(load().kbe_batch_set_graphs(self._b, int(enable)))
 
     def synchronize(self):

@@ -74,6 +74,7 @@ struct kbe_handle {
   // (first row, step count, order of the I ring), valid for the current inputs
   bool graphs = false;
   std::map<std::tuple<int, int, int>, cudaGraphExec_t> gcache;
+  unsigned graph_gen = 0;   // bumped whenever captured kernels would carry stale inputs
   int inject = 0;   // one-shot fault injection for the timeout test (kbe_debug_inject)
 
   // reverse mode: one device arena, allocated by the first kbe_backward
@@ -145,6 +146,7 @@ cudaError_t dalloc(kbe_handle *h, T **p, size_t count) {
 void drop_graphs(kbe_handle *h) {
   for (auto &kv : h->gcache) cudaGraphExecDestroy(kv.second);
   h->gcache.clear();
+  ++h->graph_gen;
 }
 
 void free_all(kbe_handle *h) {
@@ -629,6 +631,54 @@ Mesh to_mesh(const kbe_mesh *m) { return Mesh{m->nb, m->L[0], m->L[1], m->L[0] *
 }  // namespace
 
 void kbe::set_last_error(const std::string &msg) { g_create_err = msg; }
+
+// ---- pieces of kbe_step for a graph that spans several handles (kbe_batch) ----
+kbe_status kbe::step_check(kbe_handle *h, int nsteps) {
+  if (!h) return KBE_ERR_ARG;
+  if (h->sticky != KBE_OK) return fail(h, h->sticky, "step: handle has a sticky error; reset it");
+  if (h->n < 0) return fail(h, KBE_ERR_STATE, "step: call kbe_reset first");
+  if (nsteps < 0) return fail(h, KBE_ERR_ARG, "step: negative count");
+  if (h->n + nsteps > h->cfg.nt_max) return fail(h, KBE_ERR_STATE, "step: past nt_max");
+  return KBE_OK;
+}
+
+bool kbe::step_capturable(const kbe_handle *h) { return !h->prof && !h->inject && h->stream != nullptr; }
+
+kbe_status kbe::step_prepare(kbe_handle *h) {
+  cudaError_t e = kbe::dft_prepare(h->mesh.L0, h->mesh.L1);
+  if (e == cudaSuccess) e = kbe::sweep_prepare(h->cfg.nb);
+  return e == cudaSuccess ? KBE_OK : cuda_fail(h, e, "graph prepare");
+}
+
+// enqueue nsteps steps on the handle's stream (being captured by the caller)
+// and roll the host-side state back: the steps run when the graph is replayed
+kbe_status kbe::step_record(kbe_handle *h, int nsteps) {
+  const int n0 = h->n;
+  double2 *ip = h->Ip, *ic = h->Ic;
+  kbe_status s = KBE_OK;
+  for (int i = 0; i < nsteps && s == KBE_OK; ++i) s = one_step(h);
+  h->n = n0;
+  h->Ip = ip;
+  h->Ic = ic;
+  return s;
+}
+
+// the host-side state nsteps replayed steps leave (what one_step advances)
+void kbe::step_advance(kbe_handle *h, int nsteps) {
+  for (int i = 0; i < nsteps; ++i) {
+    std::swap(h->Ip, h->Ic);
+    h->n += 1;
+  }
+}
+
+// what a captured step depends on besides its arguments: the I-ring order
+// and the inputs' generation
+void kbe::step_key(const kbe_handle *h, int *ring, unsigned *gen) {
+  *ring = h->Ip == h->Ip0 ? 0 : 1;
+  *gen = h->graph_gen;
+}
+
+cudaStream_t kbe::handle_stream(const kbe_handle *h) { return h->stream; }
 
 // device bytes of one handle (the allocations of kbe_create)
 static size_t handle_bytes(const kbe_config *cfg) {

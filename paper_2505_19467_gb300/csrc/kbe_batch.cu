@@ -6,11 +6,16 @@
 // kernels of different systems overlap on the GPU (a small system's launches
 // fill SMs that a large system's tail leaves idle). Steps are enqueued one
 // time step of all systems at a time, so no system runs far ahead of the
-// others; with graphs on (kbe_batch_set_graphs) each system instead replays
-// the call's steps as one captured graph on its own stream. Admission is by
+// others. With graphs on (kbe_batch_set_graphs) and a non-default stream, one
+// call's steps of every system are captured into a single graph (each system's
+// kernels on its own stream inside it, forked from and joined to the caller's
+// stream) and later calls with the same row, count and ring order replay it
+// with one launch; on the default stream each system replays its own graph.
+// Admission is by
 // device memory: systems are taken in order while their allocation fits the
 // budget; the others are reported as not admitted.
 #include <cstdio>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -24,7 +29,8 @@ struct kbe_batch {
   std::vector<int> nt_max;
   std::vector<int> cur;             // host copy of each system's current row
   cudaEvent_t fork = nullptr;
-  bool graphs = false;              // each system replays its captured steps (kbe_set_graphs)
+  bool graphs = false;              // replay captured steps (kbe_batch_set_graphs)
+  std::map<std::vector<long>, cudaGraphExec_t> gcache;   // one graph per call shape of the batch
 };
 
 namespace {
@@ -34,7 +40,13 @@ kbe_status batch_fail(kbe_status s, const std::string &msg) {
   return s;
 }
 
+void drop_batch_graphs(kbe_batch *b) {
+  for (auto &kv : b->gcache) cudaGraphExecDestroy(kv.second);
+  b->gcache.clear();
+}
+
 void destroy_all(kbe_batch *b) {
+  drop_batch_graphs(b);
   for (size_t i = 0; i < b->sys.size(); ++i) {
     if (b->sys[i]) kbe_destroy(b->sys[i]);
     if (b->streams[i]) cudaStreamDestroy(b->streams[i]);
@@ -60,6 +72,85 @@ cudaError_t join_to_main(kbe_batch *b) {
       if (e == cudaSuccess) e = cudaStreamWaitEvent(b->main, b->done[i], 0);
     }
   return e;
+}
+
+// steps of every system for one kbe_batch_step call (k_i each)
+std::vector<int> step_counts(const kbe_batch *b, int nsteps) {
+  std::vector<int> k(b->sys.size(), 0);
+  for (size_t i = 0; i < b->sys.size(); ++i) {
+    if (!b->sys[i] || b->cur[i] < 0) continue;
+    const int left = b->nt_max[i] - b->cur[i];
+    k[i] = nsteps < left ? nsteps : left;
+  }
+  return k;
+}
+
+// one graph for the whole batch: captured on the caller's stream, each system
+// forked onto its own stream inside the capture and joined back
+kbe_status batch_graph_step(kbe_batch *b, int nsteps) {
+  // the graph runs on the caller's stream: order it after work enqueued on a
+  // system's own stream outside the batch calls (kbe_set_* on a borrowed handle)
+  cudaError_t ej = join_to_main(b);
+  if (ej != cudaSuccess) return batch_fail(KBE_ERR_CUDA, std::string("batch_step: ") + cudaGetErrorString(ej));
+  const std::vector<int> k = step_counts(b, nsteps);
+  std::vector<long> key{nsteps};
+  for (size_t i = 0; i < b->sys.size(); ++i) {
+    if (!b->sys[i] || k[i] <= 0) continue;
+    kbe_status s = kbe::step_check(b->sys[i], k[i]);
+    if (s != KBE_OK) return s;
+    int ring = 0;
+    unsigned gen = 0;
+    kbe::step_key(b->sys[i], &ring, &gen);
+    key.insert(key.end(), {(long)i, (long)b->cur[i], (long)k[i], (long)ring, (long)gen});
+  }
+  auto it = b->gcache.find(key);
+  if (it == b->gcache.end()) {
+    for (size_t i = 0; i < b->sys.size(); ++i)
+      if (b->sys[i] && k[i] > 0) {
+        kbe_status s = kbe::step_prepare(b->sys[i]);
+        if (s != KBE_OK) return s;
+      }
+    cudaError_t e = cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return batch_fail(KBE_ERR_CUDA, std::string("batch graph capture: ") + cudaGetErrorString(e));
+    kbe_status s = KBE_OK;
+    e = cudaEventRecord(b->fork, b->main);
+    for (size_t i = 0; i < b->sys.size() && s == KBE_OK && e == cudaSuccess; ++i) {
+      if (!b->sys[i] || k[i] <= 0) continue;
+      e = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+      if (e == cudaSuccess) s = kbe::step_record(b->sys[i], k[i]);
+      if (s == KBE_OK && e == cudaSuccess) e = cudaEventRecord(b->done[i], b->streams[i]);
+      if (s == KBE_OK && e == cudaSuccess) e = cudaStreamWaitEvent(b->main, b->done[i], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(b->main, &graph);
+    if (s != KBE_OK || e != cudaSuccess || ee != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      if (s != KBE_OK) return s;
+      return batch_fail(KBE_ERR_CUDA, std::string("batch graph capture: ") +
+                                          cudaGetErrorString(e != cudaSuccess ? e : ee));
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return batch_fail(KBE_ERR_CUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
+    it = b->gcache.emplace(key, exec).first;
+  }
+  cudaError_t e = cudaGraphLaunch(it->second, b->main);
+  if (e != cudaSuccess) return batch_fail(KBE_ERR_CUDA, std::string("batch graph launch: ") + cudaGetErrorString(e));
+  for (size_t i = 0; i < b->sys.size(); ++i)
+    if (b->sys[i] && k[i] > 0) {
+      kbe::step_advance(b->sys[i], k[i]);
+      b->cur[i] += k[i];
+    }
+  return KBE_OK;
+}
+
+bool batch_capturable(const kbe_batch *b) {
+  if (b->main == nullptr) return false;   // the legacy default stream cannot be captured
+  for (size_t i = 0; i < b->sys.size(); ++i)
+    if (b->sys[i] && !kbe::step_capturable(b->sys[i])) return false;
+  return true;
 }
 
 }  // namespace
@@ -161,9 +252,17 @@ kbe_status kbe_batch_reset(kbe_batch *b) {
 
 kbe_status kbe_batch_step(kbe_batch *b, int nsteps) {
   if (!b || nsteps < 0) return batch_fail(KBE_ERR_ARG, "batch_step: bad arguments");
-  cudaError_t e = fork_from_main(b);
+  cudaError_t e;
+  if (b->graphs && batch_capturable(b)) {
+    kbe_status s = batch_graph_step(b, nsteps);
+    if (s != KBE_OK) return s;
+    e = fork_from_main(b);   // later work on a system's own stream follows the replayed graph
+    if (e != cudaSuccess) return batch_fail(KBE_ERR_CUDA, std::string("batch_step: ") + cudaGetErrorString(e));
+    return KBE_OK;
+  }
+  e = fork_from_main(b);
   if (e != cudaSuccess) return batch_fail(KBE_ERR_CUDA, std::string("batch_step: ") + cudaGetErrorString(e));
-  if (b->graphs) {   // independent systems: each runs its steps as one replayed graph on its stream
+  if (b->graphs) {   // default stream: each system replays its own graph on its stream
     for (size_t i = 0; i < b->sys.size(); ++i) {
       if (!b->sys[i] || b->cur[i] < 0) continue;
       const int k = nsteps < b->nt_max[i] - b->cur[i] ? nsteps : b->nt_max[i] - b->cur[i];
@@ -194,6 +293,9 @@ kbe_status kbe_batch_step(kbe_batch *b, int nsteps) {
 
 kbe_status kbe_batch_set_graphs(kbe_batch *b, int enable) {
   if (!b) return KBE_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(b->main);
+  if (e != cudaSuccess) return batch_fail(KBE_ERR_CUDA, std::string("batch_set_graphs: ") + cudaGetErrorString(e));
+  drop_batch_graphs(b);
   for (size_t i = 0; i < b->sys.size(); ++i) {
     if (!b->sys[i]) continue;
     kbe_status s = kbe_set_graphs(b->sys[i], enable);

@@ -233,5 +233,13 @@ cudaError_t launch_adj_density(const Mesh &m, const double2 *lamRho, double scal
                                cudaStream_t st);
 // message returned by kbe_last_error(NULL) on this thread
 void set_last_error(const std::string &msg);
+// kbe_step in pieces, for a graph that spans the steps of several handles
+kbe_status step_check(kbe_handle *h, int nsteps);
+bool step_capturable(const kbe_handle *h);
+kbe_status step_prepare(kbe_handle *h);
+kbe_status step_record(kbe_handle *h, int nsteps);
+void step_advance(kbe_handle *h, int nsteps);
+void step_key(const kbe_handle *h, int *ring, unsigned *gen);
+cudaStream_t handle_stream(const kbe_handle *h);
 
 }  // namespace kbe

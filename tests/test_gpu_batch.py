@@ -81,3 +81,35 @@ def test_batch_graphs_match_eager_bitwise():
                     assert np.array_equal(x.row(i, c), y.row(i, c)), (rep, s.name, i, c)
     a.close()
     g.close()
+
+
+def test_batch_wide_graph_on_a_stream_matches_eager_bitwise():
+    """on a non-default stream the whole batch step is one captured graph:
+    rows equal the stream-ordered batch bit for bit, across resets, uneven
+    stops, and a drive changed on one system between calls (which must drop
+    the captured graph)"""
+    systems = uneven_batch()
+    st = torch.cuda.Stream()
+    a = kbe.KBEBatch(systems, stream=st)
+    g = kbe.KBEBatch(systems, stream=st)
+    g.set_graphs(True)
+    for rep in range(3):
+        if rep == 2:   # new drive samples on system 0 (a driven one) of both batches
+            assert systems[0].A is not None
+            for bb in (a, g):
+                bb.systems[0].set_drive(np.asarray(systems[0].A) * 0.5)
+        a.reset()
+        g.reset()
+        for k in (5, 9):
+            a.step(k)
+            g.step(k)
+        a.synchronize()
+        g.synchronize()
+        st.synchronize()
+        for s, x, y in zip(systems, a.systems, g.systems):
+            assert x.n == y.n == min(14, s.nt)
+            for i in (1, x.n // 2, x.n):
+                for c in (0, 1):
+                    assert np.array_equal(x.row(i, c), y.row(i, c)), (rep, s.name, i, c)
+    a.close()
+    g.close()

@@ -63,8 +63,9 @@ typedef enum {
  *   DF64: history as pairs of FP32 (hi, lo) per real part (the same 8 bytes;
  *         48-bit significand), sweep in double-float arithmetic on the FP32
  *         pipe: exact products (FMA) and error-free sums, FP64-level result.
- *   C64:  history complex64 (half the bytes), sweep in FP32 with a
- *         compensated (error-free) sum over the memory time. */
+ *   C64:  history complex64 (half the bytes), sweep in FP32: plain sums
+ *         over groups of at most 32 products per output, the groups added
+ *         into a compensated (error-free TwoSum) sum over the memory time. */
 enum {
   KBE_PREC_FP64 = 0,
   KBE_PREC_DF64 = 1,

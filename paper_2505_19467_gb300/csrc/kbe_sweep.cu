@@ -665,8 +665,10 @@ __global__ void coef_kernel(int prec, const double2 *__restrict__ Sig, void *__r
 // arithmetic (zero-filled past n_k). Each thread keeps NBB <= 4 outputs
 // (a, b..b+NBB) of both components in registers, so one shared-memory load
 // of a coefficient feeds NBB multiply-adds. The waits are cp.async group
-// waits and barriers only. Same C64 arithmetic as ArithC64 (FP32 products,
-// TwoSum-compensated sum over the nodes).
+// waits and barriers only. Same C64 arithmetic as ArithC64 (FP32 products
+// summed over groups of comp_group nodes, the groups folded into a
+// TwoSum-compensated sum). The TMA variant below replaces the per-thread
+// copies and is the one used when a tensor map can be encoded.
 #ifndef KBE_STAGED_STAGES
 #define KBE_STAGED_STAGES 3   // timed: 4 stages (2 CTAs/SM) 9 % slower, 2 stages no better
 #endif

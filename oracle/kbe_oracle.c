@@ -15,8 +15,8 @@
  *     paper's bar convention at N_b = 2) and a Peierls drive h0(k - A d).
  *   - Second-Born self-energy, Eq. 7, in the factorised form of Eqs. 8-9 for
  *     the direct term and an exchange intermediate X_jba(d) for the second
- *     term (O(n_k^2) per time pair); orc_sigma_pair_literal is Eq. 7 / Alg. 2
- *     written out as the O(n_k^3) triple sum.
+ *     term (O(n_k^2) per time pair); orc_sigma_pair_literal is Eq. 7 summed
+ *     directly over both momenta (O(n_k^3)).
  *   - Collision integrals, Eq. 6, read as the left (Sigma * G) form
  *         I^x(n,j) = sum_{l<=n} w^(n)_l [S^> - S^<](n,l) G^x(l,j)
  *                  + sum_{l<=j} w^(j)_l  S^x(n,l) [G^< - G^>](l,j)
@@ -29,6 +29,9 @@
  *     G(n,n) = U G(n-1,n-1) U^+ - i W[(W^+ Sbar W) o D] W^+.
  *   - Hartree-Fock mean field and the -U n_c term of Eq. 2 inside h.
  *   - Equal-time observables (density, particle number, energies).
+ *   - Full-grid mode (tiny grids): the upper triangle propagated on its own
+ *     with the right-hand equation and Eq. 6 as printed (G * Sigma), so that
+ *     the adjoint symmetry becomes a checked result instead of an assumption.
  *
  * Storage: the lower triangle of the two-time grid, block (i, j), i >= j, at
  * index i(i+1)/2 + j; every block is [k][a][b] complex. G(l, j) for l < j is
@@ -249,47 +252,66 @@ void orc_sigma_pair(int nb, int L0, int L1, const double *v, double UnUl, const 
 }
 
 /*
- * Eq. 7 / Algorithm 2 written out as the O(n_k^3) double sum over q and k'.
- * With v == NULL (N_b = 2 only) the band structure is the paper's bar
- * convention, jbar = 1 - j; otherwise the generalised pairing sum over a, b
- * with weights v_ja v_mb.
+ * Eq. 7 summed term by term over the two momenta, O(n_k^3) per time pair,
+ * with both time orderings given explicitly:
+ *   Gf = G^x(k; t, t')      and   Gb = G^{xbar}(k; t', t),   both [k][a][b].
+ * For every output (k, j, m), every interacting pair of bands (a, b) with
+ * weight v_ja v_mb, every transfer p (the paper's q) and loop momentum r (the
+ * paper's k'):
+ *   + Gf_ab(r + p) Gb_ba(r) Gf_jm(k - p)          (direct term)
+ *   - Gf_jb(r) Gb_ba(r + p - k) Gf_am(p)          (exchange term)
+ * scaled by U(t) U(t') / n_k^2. With v == NULL (N_b = 2 only) the band
+ * indices are the paper's bar convention: the one pair a = 1 - j, b = 1 - m.
+ * No symmetry of G is used here; the caller decides where Gb comes from.
  */
-static void sigma_literal_one(int nb, mesh m, const double *v, double UnUl, const cplx *G,
-                              const cplx *Gp, cplx *S) {
+static void sigma_eq7(int nb, mesh m, const double *v, double UtUt, const cplx *Gf, const cplx *Gb,
+                      cplx *S) {
   int nk = m.L0 * m.L1, nb2 = nb * nb;
-  double scale = UnUl / ((double)nk * nk);
-#define GT(k, a, b) (-conj(Gp[(k) * nb2 + (b) * nb + (a)])) /* G^{xbar}_ab(k; t_l, t_n) */
+  double scale = UtUt / ((double)nk * nk);
   for (int k = 0; k < nk; ++k)
     for (int j = 0; j < nb; ++j)
       for (int mm = 0; mm < nb; ++mm) {
-        cplx s = 0;
-        for (int q = 0; q < nk; ++q)
-          for (int kp = 0; kp < nk; ++kp) {
-            int kpq = k_add(m, kp, q), kmq = k_sub(m, k, q), kx = k_sub(m, kpq, k);
-            if (v == NULL) {
-              int jb = 1 - j, mb = 1 - mm;
-              s += G[kpq * nb2 + jb * nb + mb] * GT(kp, mb, jb) * G[kmq * nb2 + j * nb + mm];
-              s -= G[kp * nb2 + j * nb + mb] * GT(kx, mb, jb) * G[q * nb2 + jb * nb + mm];
-            } else {
-              for (int a = 0; a < nb; ++a)
-                for (int b = 0; b < nb; ++b) {
-                  double vv = v[j * nb + a] * v[mm * nb + b];
-                  if (vv == 0.0) continue;
-                  s += vv * G[kpq * nb2 + a * nb + b] * GT(kp, b, a) * G[kmq * nb2 + j * nb + mm];
-                  s -= vv * G[kp * nb2 + j * nb + b] * GT(kx, b, a) * G[q * nb2 + a * nb + mm];
-                }
+        cplx acc = 0;
+        for (int a = 0; a < nb; ++a)
+          for (int b = 0; b < nb; ++b) {
+            double wgt;
+            if (v == NULL) wgt = (a == 1 - j && b == 1 - mm) ? 1.0 : 0.0;
+            else wgt = v[j * nb + a] * v[mm * nb + b];
+            if (wgt == 0.0) continue;
+            cplx direct = 0, exch = 0;
+            for (int p = 0; p < nk; ++p) {
+              int kmp = k_sub(m, k, p);
+              for (int r = 0; r < nk; ++r) {
+                int rp = k_add(m, r, p), rpk = k_sub(m, rp, k);
+                direct += Gf[rp * nb2 + a * nb + b] * Gb[r * nb2 + b * nb + a] * Gf[kmp * nb2 + j * nb + mm];
+                exch += Gf[r * nb2 + j * nb + b] * Gb[rpk * nb2 + b * nb + a] * Gf[p * nb2 + a * nb + mm];
+              }
             }
+            acc += wgt * (direct - exch);
           }
-        S[k * nb2 + j * nb + mm] = scale * s;
+        S[k * nb2 + j * nb + mm] = scale * acc;
       }
-#undef GT
 }
 
+/* Eq. 7 as a direct sum for the pair (t_n, t_l), given G^<, G^>(k; t_n, t_l):
+ * the reversed-time factors come from the adjoint symmetry,
+ * G^{xbar}_ab(k; t_l, t_n) = -conj(G^{xbar}_ba(k; t_n, t_l)). */
 void orc_sigma_pair_literal(int nb, int L0, int L1, const double *v, double UnUl,
-                            const double *Gl, const double *Gg, double *Sl, double *Sg) {
+                            const double *Gl_, const double *Gg_, double *Sl, double *Sg) {
   mesh m = {L0, L1};
-  sigma_literal_one(nb, m, v, UnUl, (const cplx *)Gl, (const cplx *)Gg, (cplx *)Sl);
-  sigma_literal_one(nb, m, v, UnUl, (const cplx *)Gg, (const cplx *)Gl, (cplx *)Sg);
+  int nk = L0 * L1, nb2 = nb * nb;
+  const cplx *Gl = (const cplx *)Gl_, *Gg = (const cplx *)Gg_;
+  cplx *Bl = malloc(sizeof(cplx) * nk * nb2), *Bg = malloc(sizeof(cplx) * nk * nb2);
+  for (int k = 0; k < nk; ++k)
+    for (int a = 0; a < nb; ++a)
+      for (int b = 0; b < nb; ++b) {
+        Bl[k * nb2 + a * nb + b] = -conj(Gl[k * nb2 + b * nb + a]);
+        Bg[k * nb2 + a * nb + b] = -conj(Gg[k * nb2 + b * nb + a]);
+      }
+  sigma_eq7(nb, m, v, UnUl, Gl, Bg, (cplx *)Sl);
+  sigma_eq7(nb, m, v, UnUl, Gg, Bl, (cplx *)Sg);
+  free(Bl);
+  free(Bg);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -338,17 +360,26 @@ static void fetch(int nb, int nk, const cplx *H, int l, int j, int k, cplx *out)
   }
 }
 
+/* block G^x(l, j) at one k: from the lower triangle H when l >= j, else from
+ * the separately propagated column store C (full-grid mode; nothing is
+ * mirrored), or, with C == NULL, by the adjoint symmetry from H */
+static void fetch_grid(int nb, int nk, const cplx *H, const cplx *C, int l, int j, int k, cplx *out) {
+  if (l < j && C != NULL)
+    memcpy(out, C + tri(j, l) * (size_t)nk * nb * nb + (size_t)k * nb * nb, sizeof(cplx) * nb * nb);
+  else
+    fetch(nb, nk, H, l, j, k, out);
+}
+
 /*
  * I^x(n, j), j = 0..n, x in {<, >}:
  *   sum_{l=0}^{n} w^(n)_l [S^>(n,l) - S^<(n,l)] G^x(l,j)
  * + sum_{l=0}^{j} w^(j)_l S^x(n,l) [G^<(l,j) - G^>(l,j)].
- * H*: triangle with rows 0..n; S*: [l][k][a][b], l <= n; I*: [j][k][a][b].
+ * H*: triangle with rows 0..n; C*: column store or NULL; S*: [l][k][a][b],
+ * l <= n; I*: [j][k][a][b].
  */
-void orc_collision_row_q(int nb, int nk, int n, double dt, int quad, const double *Hl_, const double *Hg_,
-                         const double *Sl_, const double *Sg_, double *Il_, double *Ig_) {
-  const cplx *Hl = (const cplx *)Hl_, *Hg = (const cplx *)Hg_;
-  const cplx *Sl = (const cplx *)Sl_, *Sg = (const cplx *)Sg_;
-  cplx *Il = (cplx *)Il_, *Ig = (cplx *)Ig_;
+static void collision_left(int nb, int nk, int n, double dt, int quad, const cplx *Hl, const cplx *Hg,
+                           const cplx *Cl, const cplx *Cg, const cplx *Sl, const cplx *Sg, cplx *Il,
+                           cplx *Ig) {
   size_t blk = (size_t)nk * nb * nb;
   int nb2 = nb * nb;
 #pragma omp parallel for schedule(dynamic) collapse(2)
@@ -359,8 +390,8 @@ void orc_collision_row_q(int nb, int nk, int n, double dt, int quad, const doubl
       for (int e = 0; e < nb2; ++e) accl[e] = accg[e] = 0;
       for (int l = 0; l <= n; ++l) {
         const cplx *sl = Sl + l * blk + (size_t)k * nb2, *sg = Sg + l * blk + (size_t)k * nb2;
-        fetch(nb, nk, Hl, l, j, k, gl);
-        fetch(nb, nk, Hg, l, j, k, gg);
+        fetch_grid(nb, nk, Hl, Cl, l, j, k, gl);
+        fetch_grid(nb, nk, Hg, Cg, l, j, k, gg);
         double w1 = quad_w(quad, n, l, dt);
         for (int e = 0; e < nb2; ++e) sr[e] = w1 * (sg[e] - sl[e]);
         mat_mul(nb, sr, gl, tl);
@@ -383,6 +414,12 @@ void orc_collision_row_q(int nb, int nk, int n, double dt, int quad, const doubl
       memcpy(Il + j * blk + (size_t)k * nb2, accl, sizeof(cplx) * nb2);
       memcpy(Ig + j * blk + (size_t)k * nb2, accg, sizeof(cplx) * nb2);
     }
+}
+
+void orc_collision_row_q(int nb, int nk, int n, double dt, int quad, const double *Hl, const double *Hg,
+                         const double *Sl, const double *Sg, double *Il, double *Ig) {
+  collision_left(nb, nk, n, dt, quad, (const cplx *)Hl, (const cplx *)Hg, NULL, NULL, (const cplx *)Sl,
+                 (const cplx *)Sg, (cplx *)Il, (cplx *)Ig);
 }
 
 void orc_collision_row(int nb, int nk, int n, double dt, const double *Hl, const double *Hg,
@@ -539,6 +576,15 @@ typedef struct orc {
   double *lam;
   double *obs; /* [(nt_max+1)][6] */
   double *nkb; /* [(nt_max+1)][nk][nb] */
+  /* full-grid mode (orc_enable_full): the strict upper triangle G(j, i),
+   * j < i, kept as its own column at index tri(i, j) and propagated with the
+   * right-hand equation; right-form collision rows I_R(j, n) and the column
+   * self-energy Sigma(l, n) */
+  int full;
+  int right_limit_printed; /* 1: the second integral of I_R up to t as printed */
+  cplx *Cl, *Cg;
+  cplx *Rpl, *Rpg, *Rcl, *Rcg;
+  cplx *Tl, *Tg;
 } orc;
 
 orc *orc_create(int nb, int dim, int L0, int L1, int nt_max, double dt, double beta, double mu,
@@ -598,6 +644,8 @@ void orc_destroy(orc *s) {
   free(s->Hl); free(s->Hg); free(s->Ipl); free(s->Ipg); free(s->Icl); free(s->Icg);
   free(s->Sl); free(s->Sg); free(s->rho); free(s->h); free(s->Uk); free(s->Vk);
   free(s->Wk); free(s->lam); free(s->obs); free(s->nkb); free(s->iters);
+  free(s->Cl); free(s->Cg); free(s->Rpl); free(s->Rpg); free(s->Rcl); free(s->Rcg);
+  free(s->Tl); free(s->Tg);
   free(s);
 }
 
@@ -787,6 +835,183 @@ static void observables(orc *s, int n) {
   o[5] = o[1] + o[2] + o[3] + o[4];
 }
 
+/* ------------------------------------------------------------------------ */
+/* full two-time grid (tiny grids only)                                      */
+/* ------------------------------------------------------------------------ */
+/*
+ * A second way through the same equations that never uses the adjoint
+ * symmetry G^x(t,t')^+ = -G^x(t',t): the row G(t_n, t_j) is advanced with the
+ * left equation i d/dt G = h G + I_L as in orc_step, and the column
+ * G(t_j, t_n), j < n, with the right equation -i d/dt' G = G h + I_R, whose
+ * collision integral is Eq. 6 as printed (the G * Sigma form):
+ *   I_R^x(j, n) = sum_{l<=j} w^(j)_l [G^> - G^<](j,l) Sigma^x(l,n)
+ *               + sum_{l<=L} w^(L)_l G^x(j,l) [Sigma^< - Sigma^>](l,n),
+ * L = n (the second upper limit read as t'), or L = j (the limit t as printed,
+ * right_limit_printed = 1). Every block with l < j comes from the column
+ * store; Sigma(n, l) and Sigma(l, n) are both summed from Eq. 7 with the
+ * stored G(n, l) and G(l, n). The exponential step of the right equation is
+ * G(j, n) = G(j, n-1) U^+ + Ibar_R(j) V^+ (the adjoint of the row step), and
+ * the time diagonal i dG(t,t)/dt = [h, G] + I_L(t,t) - I_R(t,t) takes the
+ * divided-difference form with Sbar = Ibar_L(n,n) - Ibar_R(n,n).
+ */
+static const cplx *grid_block(const orc *s, const cplx *H, const cplx *C, int l, int j) {
+  return l >= j ? H + tri(l, j) * s->blk : C + tri(j, l) * s->blk;
+}
+
+int orc_enable_full(orc *s, int right_limit_printed) {
+  if (s->n > 0) return -4;
+  size_t ntri = tri(s->nt_max, s->nt_max) + 1;
+  size_t rowb = sizeof(cplx) * (size_t)(s->nt_max + 1) * s->blk;
+  if (!s->full) {
+    s->Cl = calloc(ntri * s->blk, sizeof(cplx));
+    s->Cg = calloc(ntri * s->blk, sizeof(cplx));
+    s->Rpl = calloc(1, rowb);
+    s->Rpg = calloc(1, rowb);
+    s->Rcl = calloc(1, rowb);
+    s->Rcg = calloc(1, rowb);
+    s->Tl = calloc(1, rowb);
+    s->Tg = calloc(1, rowb);
+    if (!s->Cl || !s->Cg || !s->Rpl || !s->Rpg || !s->Rcl || !s->Rcg || !s->Tl || !s->Tg) return -2;
+  }
+  s->full = 1;
+  s->right_limit_printed = right_limit_printed ? 1 : 0;
+  return 0;
+}
+
+/* Sigma(n, l) into S* and Sigma(l, n) into T*, l = 0..n, each from Eq. 7 */
+static void full_sigma(orc *s, int n) {
+  mesh m = {s->L0, s->L1};
+  size_t blk = s->blk;
+#pragma omp parallel for schedule(dynamic)
+  for (int l = 0; l <= n; ++l) {
+    double UU = U_at(s, n) * U_at(s, l);
+    const cplx *fl = grid_block(s, s->Hl, s->Cl, n, l), *fg = grid_block(s, s->Hg, s->Cg, n, l);
+    const cplx *bl = grid_block(s, s->Hl, s->Cl, l, n), *bg = grid_block(s, s->Hg, s->Cg, l, n);
+    sigma_eq7(s->nb, m, s->v, UU, fl, bg, s->Sl + l * blk);
+    sigma_eq7(s->nb, m, s->v, UU, fg, bl, s->Sg + l * blk);
+    sigma_eq7(s->nb, m, s->v, UU, bl, fg, s->Tl + l * blk);
+    sigma_eq7(s->nb, m, s->v, UU, bg, fl, s->Tg + l * blk);
+  }
+}
+
+/* I_R^x(j, n), j = 0..n, into Rcl / Rcg (Eq. 6 as printed, G * Sigma) */
+static void full_collision_right(orc *s, int n) {
+  int nb = s->nb, nb2 = nb * nb, nk = s->nk;
+  size_t blk = s->blk;
+#pragma omp parallel for collapse(2)
+  for (int j = 0; j <= n; ++j)
+    for (int k = 0; k < nk; ++k) {
+      cplx d[MAXNB * MAXNB], t[MAXNB * MAXNB], accl[MAXNB * MAXNB], accg[MAXNB * MAXNB];
+      for (int e = 0; e < nb2; ++e) accl[e] = accg[e] = 0;
+      for (int l = 0; l <= j; ++l) { /* retarded G on [0, t_j] */
+        const cplx *gl = grid_block(s, s->Hl, s->Cl, j, l) + (size_t)k * nb2;
+        const cplx *gg = grid_block(s, s->Hg, s->Cg, j, l) + (size_t)k * nb2;
+        double w = quad_w(s->quad, j, l, s->dt);
+        for (int e = 0; e < nb2; ++e) d[e] = w * (gg[e] - gl[e]);
+        mat_mul(nb, d, s->Tl + l * blk + (size_t)k * nb2, t);
+        for (int e = 0; e < nb2; ++e) accl[e] += t[e];
+        mat_mul(nb, d, s->Tg + l * blk + (size_t)k * nb2, t);
+        for (int e = 0; e < nb2; ++e) accg[e] += t[e];
+      }
+      int L = s->right_limit_printed ? j : n;
+      for (int l = 0; l <= L; ++l) { /* advanced Sigma on [0, t_L] */
+        const cplx *tl = s->Tl + l * blk + (size_t)k * nb2, *tg = s->Tg + l * blk + (size_t)k * nb2;
+        double w = quad_w(s->quad, L, l, s->dt);
+        for (int e = 0; e < nb2; ++e) d[e] = w * (tl[e] - tg[e]);
+        mat_mul(nb, grid_block(s, s->Hl, s->Cl, j, l) + (size_t)k * nb2, d, t);
+        for (int e = 0; e < nb2; ++e) accl[e] += t[e];
+        mat_mul(nb, grid_block(s, s->Hg, s->Cg, j, l) + (size_t)k * nb2, d, t);
+        for (int e = 0; e < nb2; ++e) accg[e] += t[e];
+      }
+      memcpy(s->Rcl + j * blk + (size_t)k * nb2, accl, sizeof(cplx) * nb2);
+      memcpy(s->Rcg + j * blk + (size_t)k * nb2, accg, sizeof(cplx) * nb2);
+    }
+}
+
+static void full_evaluate(orc *s, int n) {
+  full_sigma(s, n);
+  collision_left(s->nb, s->nk, n, s->dt, s->quad, s->Hl, s->Hg, s->Cl, s->Cg, s->Sl, s->Sg, s->Icl, s->Icg);
+  full_collision_right(s, n);
+}
+
+/* row n (left equation), column n (right equation) and the time diagonal */
+static void full_update(orc *s, int n, double theta) {
+  int nb = s->nb, nb2 = nb * nb, nk = s->nk;
+  size_t blk = s->blk;
+  /* rows j < n exactly as in triangle mode; its diagonal is replaced below */
+  update(s, n, theta);
+#pragma omp parallel for collapse(2)
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < nk; ++k) {
+      const cplx *Uk = s->Uk + (size_t)k * nb2, *Vk = s->Vk + (size_t)k * nb2;
+      cplx ib[MAXNB * MAXNB], t1[MAXNB * MAXNB], t2[MAXNB * MAXNB];
+      for (int x = 0; x < 2; ++x) {
+        const cplx *gp = grid_block(s, x ? s->Hg : s->Hl, x ? s->Cg : s->Cl, j, n - 1) + (size_t)k * nb2;
+        const cplx *rp = (x ? s->Rpg : s->Rpl) + j * blk + (size_t)k * nb2;
+        const cplx *rc = (x ? s->Rcg : s->Rcl) + j * blk + (size_t)k * nb2;
+        for (int e = 0; e < nb2; ++e) ib[e] = (1.0 - theta) * rp[e] + (theta != 0.0 ? theta * rc[e] : 0.0);
+        mat_mul_adj(nb, gp, Uk, t1);
+        mat_mul_adj(nb, ib, Vk, t2);
+        cplx *dst = (x ? s->Cg : s->Cl) + tri(n, j) * blk + (size_t)k * nb2;
+        for (int e = 0; e < nb2; ++e) dst[e] = t1[e] + t2[e];
+      }
+    }
+  for (int k = 0; k < nk; ++k) {
+    const cplx *Uk = s->Uk + (size_t)k * nb2, *Wk = s->Wk + (size_t)k * nb2;
+    const double *lk = s->lam + (size_t)k * nb;
+    cplx S[MAXNB * MAXNB], T[MAXNB * MAXNB], T2[MAXNB * MAXNB], G[MAXNB * MAXNB];
+    size_t op = (size_t)(n - 1) * blk + (size_t)k * nb2, oc = (size_t)n * blk + (size_t)k * nb2;
+    for (int e = 0; e < nb2; ++e) {
+      S[e] = (1.0 - theta) * (s->Ipl[op + e] - s->Rpl[op + e]);
+      if (theta != 0.0) S[e] += theta * (s->Icl[oc + e] - s->Rcl[oc + e]);
+    }
+    mat_adj_mul(nb, Wk, S, T);
+    mat_mul(nb, T, Wk, T2);
+    for (int a = 0; a < nb; ++a)
+      for (int b = 0; b < nb; ++b) T2[a * nb + b] *= phi_d(lk[a] - lk[b], s->dt);
+    mat_mul(nb, Wk, T2, T);
+    mat_mul_adj(nb, T, Wk, T2);
+    mat_mul(nb, Uk, s->Hl + tri(n - 1, n - 1) * blk + (size_t)k * nb2, T);
+    mat_mul_adj(nb, T, Uk, G);
+    cplx *dl = s->Hl + tri(n, n) * blk + (size_t)k * nb2, *dg = s->Hg + tri(n, n) * blk + (size_t)k * nb2;
+    for (int a = 0; a < nb; ++a)
+      for (int b = 0; b < nb; ++b) {
+        cplx g = G[a * nb + b] - IU * T2[a * nb + b];
+        dl[a * nb + b] = g;
+        dg[a * nb + b] = g - (a == b ? IU : 0.0);
+      }
+  }
+}
+
+/* one step of Algorithm 1 on the full grid (fixed corrector count) */
+static void full_step(orc *s) {
+  int nb2 = s->nb * s->nb, n = s->n + 1;
+  cplx mid[MAXNB * MAXNB], cur[MAXNB * MAXNB];
+  const cplx *r1 = s->rho + (size_t)(n - 1) * nb2;
+  const cplx *r2 = s->rho + (size_t)(n >= 2 ? n - 2 : 0) * nb2;
+  for (int e = 0; e < nb2; ++e) mid[e] = n >= 2 ? 1.5 * r1[e] - 0.5 * r2[e] : r1[e];
+  build_h_and_props(s, n, mid);
+  full_update(s, n, 0.0);
+  s->iters[n] = 0;
+  for (int c = 0; c < s->n_corr; ++c) {
+    local_density(s, n, cur);
+    for (int e = 0; e < nb2; ++e) mid[e] = 0.5 * (r1[e] + cur[e]);
+    build_h_and_props(s, n, mid);
+    full_evaluate(s, n);
+    full_update(s, n, 0.5);
+    s->iters[n] += 1;
+  }
+  full_evaluate(s, n);
+  local_density(s, n, s->rho + (size_t)n * nb2);
+  s->n = n;
+  observables(s, n);
+  cplx *t;
+  t = s->Ipl; s->Ipl = s->Icl; s->Icl = t;
+  t = s->Ipg; s->Ipg = s->Icg; s->Icg = t;
+  t = s->Rpl; s->Rpl = s->Rcl; s->Rcl = t;
+  t = s->Rpg; s->Rpg = s->Rcg; s->Rcg = t;
+}
+
 /* t = 0: uncorrelated Fermi state of the field-free h0, G^<(0,0) = i f(h0) */
 int orc_reset(orc *s) {
   int nb = s->nb, nb2 = nb * nb;
@@ -809,6 +1034,12 @@ int orc_reset(orc *s) {
   memset(s->Ipg, 0, sizeof(cplx) * s->blk);
   memset(s->Icl, 0, sizeof(cplx) * s->blk);
   memset(s->Icg, 0, sizeof(cplx) * s->blk);
+  if (s->full) {
+    memset(s->Rpl, 0, sizeof(cplx) * s->blk);
+    memset(s->Rpg, 0, sizeof(cplx) * s->blk);
+    memset(s->Rcl, 0, sizeof(cplx) * s->blk);
+    memset(s->Rcg, 0, sizeof(cplx) * s->blk);
+  }
   s->n = 0;
   local_density(s, 0, s->rho);
   observables(s, 0);
@@ -820,6 +1051,11 @@ int orc_step(orc *s, int nsteps) {
   int nb2 = s->nb * s->nb;
   if (s->n < 0) return -4;
   if (s->n + nsteps > s->nt_max) return -4;
+  if (s->full) {
+    if (s->corr_tol > 0.0) return -1; /* the full-grid mode runs a fixed corrector count */
+    for (int it = 0; it < nsteps; ++it) full_step(s);
+    return 0;
+  }
   for (int it = 0; it < nsteps; ++it) {
     int n = s->n + 1;
     cplx mid[MAXNB * MAXNB], cur[MAXNB * MAXNB];
@@ -878,11 +1114,14 @@ int orc_get_iters(const orc *s, int *out) {
   return 0;
 }
 
-/* G^x(i, j) for any i, j <= n (x = 0: lesser, 1: greater), [k][a][b] */
+/* G^x(i, j) for any i, j <= n (x = 0: lesser, 1: greater), [k][a][b]; for
+ * i < j in full-grid mode the propagated column, otherwise -G^x(j, i)^+ */
 int orc_get_block(const orc *s, int i, int j, int which, double *out) {
   if (i < 0 || j < 0 || i > s->n || j > s->n) return -1;
   const cplx *H = which == 0 ? s->Hl : s->Hg;
-  for (int k = 0; k < s->nk; ++k) fetch(s->nb, s->nk, H, i, j, k, (cplx *)out + (size_t)k * s->nb * s->nb);
+  const cplx *C = s->full ? (which == 0 ? s->Cl : s->Cg) : NULL;
+  for (int k = 0; k < s->nk; ++k)
+    fetch_grid(s->nb, s->nk, H, C, i, j, k, (cplx *)out + (size_t)k * s->nb * s->nb);
   return 0;
 }
 

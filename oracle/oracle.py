@@ -65,6 +65,7 @@ def _load():
             lib.orc_get_iters.argtypes = [P, P]
             lib.orc_set_threads.argtypes = [i]
             lib.orc_threads.restype = i
+            lib.orc_enable_full.argtypes = [P, i]
             _lib = lib
     return _lib
 
@@ -148,7 +149,13 @@ class Oracle:
 
     def __init__(self, sys, nt_max: Optional[int] = None, n_corr: Optional[int] = None,
                  hf: Optional[int] = None, paper_shift: Optional[int] = None,
-                 U: Optional[np.ndarray] = None):
+                 U: Optional[np.ndarray] = None, full_grid: bool = False,
+                 right_limit_printed: bool = False):
+        """full_grid: propagate the upper triangle G(t_j, t_n) with the right
+        equation (Eq. 6 as printed, G * Sigma) instead of mirroring the lower
+        one; tiny grids only (Eq. 7 is summed directly, O(n_k^3) per pair).
+        right_limit_printed: in that mode, end the second integral of Eq. 6 at
+        t as printed instead of t'."""
         lib = _load()
         self.sys = sys
         self.nb, self.nk, self.L = sys.nb, sys.nk, sys.L
@@ -181,6 +188,8 @@ class Oracle:
             self._keep = self._keep + (E, M)
         lib.orc_set_corr_tol(self._h, float(getattr(sys, "corr_tol", 0.0)))
         lib.orc_set_quadrature(self._h, int(getattr(sys, "quadrature", 0)))
+        if full_grid and lib.orc_enable_full(self._h, int(bool(right_limit_printed))) != 0:
+            raise MemoryError("oracle: full-grid storage")
         if lib.orc_reset(self._h) != 0:
             raise RuntimeError("oracle: reset failed")
 

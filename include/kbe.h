@@ -182,12 +182,16 @@ kbe_status kbe_set_graphs(kbe_handle *h, int enable);
 #define KBE_AUTOTUNE_BUCKETS 17
 kbe_status kbe_autotune(kbe_handle *h, int *targets);
 
-/* Fault injection for testing the failure path (no GPU fault, no hang):
+/* TEST ONLY -- not for production use. Fault injection for testing the
+ * failure path (no GPU fault, no hang):
  * KBE_INJECT_STAGED_COPY_LOSS makes the next collision sweep of this handle
  * (C64, staged form: N_b in {4, 8, 16}, n_k even) lose one CTA's first
  * copies. Its waits are bounded (one second of device time), so the kernel
  * marks a timeout and returns; the next synchronising call returns
- * KBE_ERR_TIMEOUT, which is sticky until kbe_reset. 0 clears. One-shot. */
+ * KBE_ERR_TIMEOUT, which is sticky until kbe_reset. 0 clears. One-shot.
+ * (If a timed-out kernel could not also drain its own copies in flight, the
+ * handle is unusable: kbe_reset and kbe_checkpoint_load return KBE_ERR_STATE
+ * and the handle must be destroyed and recreated.) */
 #define KBE_INJECT_STAGED_COPY_LOSS 1
 kbe_status kbe_debug_inject(kbe_handle *h, int fault);
 
@@ -217,6 +221,16 @@ kbe_status kbe_observables_all(kbe_handle *h, double *n_kb, double *scalars);
 /* Row i of G^x (which 0: lesser, 1: greater), blocks j = 0..i, into host c128
  * [(i+1)][nk][nb][nb]. Synchronises. */
 kbe_status kbe_get_row(kbe_handle *h, int i, int which, double *out);
+
+/* Device-pointer forms of kbe_observables_all and kbe_get_row, for callers
+ * whose buffers live on the GPU (e.g. torch tensors): the same data and
+ * layouts, written into caller-owned device memory of the current device.
+ * The work is enqueued on the handle's stream and the call returns before it
+ * completes (order later work after that stream or synchronise it). These
+ * calls do not synchronise, so they do not read the sticky device status:
+ * the next synchronising call (kbe_synchronize) reports it. */
+kbe_status kbe_observables_all_dev(kbe_handle *h, double *n_kb_dev, double *scalars_dev);
+kbe_status kbe_get_row_dev(kbe_handle *h, int i, int which, void *out_dev);
 
 /* Collision-integral sweep timing (CUDA events around each sweep launch). */
 kbe_status kbe_profile_enable(kbe_handle *h, int enable);
@@ -305,6 +319,12 @@ kbe_status kbe_batch_synchronize(kbe_batch *b);
  * (kbe_set_graphs). Results are bitwise those of the stream-ordered batch.
  * Synchronises the batch's stream. enable = 0 switches back. */
 kbe_status kbe_batch_set_graphs(kbe_batch *b, int enable);
+
+/* Diagnostics of the loaded library on the current device: binary_version
+ * (may be NULL) receives the compute capability its kernels were compiled for
+ * (cudaFuncGetAttributes; 103 for sm_103a), sm_count (may be NULL) the
+ * device's streaming multiprocessors, against which grids are sized. */
+kbe_status kbe_device_info(int *binary_version, int *sm_count);
 
 /* Message of the last error of this handle; with NULL, of the last failed
  * create or handle-free operation (kbe_op_*) on the calling thread. */
@@ -406,7 +426,10 @@ kbe_status kbe_op_update_row(const kbe_mesh *m, int n, double dt, double theta, 
  * KBE_ERR_ARG and a message in kbe_last_error(NULL), before any GPU work.
  * Set-up: the first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture begins.
+ * before any stream capture begins. The address is then kept for the life of
+ * the process: after cudaDeviceReset (or anything else that destroys the
+ * device's primary context) it is stale, so do not call this entry point
+ * again in that process.
  * Sharing: all calls use the same array and it keeps the last call's
  * contents (no call depends on them); calls whose GPU work overlaps, e.g. on
  * two streams or from two host threads, race on it and must be serialised by

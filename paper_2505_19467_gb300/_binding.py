@@ -37,6 +37,7 @@ EXPORTS = [
     "kbe_batch_synchronize", "kbe_checkpoint_bytes", "kbe_checkpoint_save", "kbe_checkpoint_load",
     "kbe_set_dipole", "kbe_backward", "kbe_backward_memory_bytes", "kbe_corrector_iterations",
     "kbe_op_collision_row_quad", "kbe_set_graphs", "kbe_autotune", "kbe_debug_inject", "kbe_batch_set_graphs",
+    "kbe_observables_all_dev", "kbe_get_row_dev", "kbe_device_info",
 ]
 
 
@@ -123,6 +124,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "kbe_debug_inject": (I, [P, I]),
         "kbe_batch_set_graphs": (I, [P, I]),
         "kbe_op_collision_row_quad": (I, [pmesh, I, D, I, I, P, P, P, P, S, P]),
+        "kbe_observables_all_dev": (I, [P, P, P]),
+        "kbe_get_row_dev": (I, [P, I, I, P]),
+        "kbe_device_info": (I, [P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -303,6 +307,17 @@ class KBE:
         _check(load().kbe_get_row(self._h, int(i), int(which), _np_ptr(out)), self._h)
         return out
 
+    def row_dev(self, i: int, which: int, out) -> None:
+        """row i of G^which into a caller-owned device tensor (complex128,
+        [(i+1), nk, nb, nb], contiguous), enqueued on the handle's stream"""
+        _check(load().kbe_get_row_dev(self._h, int(i), int(which), _tptr(out)), self._h)
+
+    def observables_all_dev(self, nkb_out=None, scalars_out=None) -> None:
+        """n_kb [(n+1), nk, nb] and scalars [(n+1), 6] (float64 device tensors,
+        either may be None), enqueued on the handle's stream"""
+        _check(load().kbe_observables_all_dev(self._h, None if nkb_out is None else _tptr(nkb_out),
+                                              None if scalars_out is None else _tptr(scalars_out)), self._h)
+
     def checkpoint(self) -> bytes:
         """The state after the current row, as bytes (history rows 0..n etc.)."""
         nbytes = int(load().kbe_checkpoint_bytes(self._h))
@@ -482,3 +497,10 @@ class KBEBatch:
             self.close()
         except Exception:
             pass
+
+
+def device_info():
+    """(binary version the kernels were built for, SM count of the current device)"""
+    bv, sm = ctypes.c_int(), ctypes.c_int()
+    _check(load().kbe_device_info(ctypes.byref(bv), ctypes.byref(sm)))
+    return bv.value, sm.value

@@ -34,7 +34,8 @@ size_t blkof(const Mesh &m) { return (size_t)m.nb * m.nb * m.nk; }
 
 unsigned grid_for_count(size_t count) {
   size_t b = (count + 255) / 256;
-  return (unsigned)(b < 152 * 64 ? (b ? b : 1) : 152 * 64);
+  const size_t cap = (size_t)device_sms() * 64;
+  return (unsigned)(b < cap ? (b ? b : 1) : cap);
 }
 
 // (G^<, dG) blocks of the FP64 history -> (G^<, G^> = G^< - dG)
@@ -814,7 +815,7 @@ CoefShape coef_shape(const Mesh &m, int n) {
   sh.threads = elems >= 256 ? 256 : (int)((elems + 31) / 32) * 32;
   const long ty = (elems + sh.threads - 1) / sh.threads;
   const long base = (long)(n + 1) * ty;
-  long nz = (152L * 8 + base - 1) / base;
+  long nz = ((long)device_sms() * 8 + base - 1) / base;
   if (nz > n + 1) nz = n + 1;
   if (nz > 2 + 1024 / (n + 1)) nz = 2 + 1024 / (n + 1);
   if (nz < 1) nz = 1;
@@ -830,7 +831,7 @@ constexpr int kUvMaxSplit = 64;
 int uv_splits(const Mesh &m, int n) {
   const long elems = (long)m.nb * m.nb * m.nk;
   const long tiles = (elems + 255) / 256;
-  long nz = (152L * 8 + tiles - 1) / tiles;
+  long nz = ((long)device_sms() * 8 + tiles - 1) / tiles;
   if (nz > n) nz = n;
   if (nz > kUvMaxSplit) nz = kUvMaxSplit;
   return nz < 1 ? 1 : (int)nz;

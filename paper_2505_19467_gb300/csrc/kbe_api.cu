@@ -68,12 +68,13 @@ struct kbe_handle {
   int n = -1;                  // last completed row
   bool ham_set = false;
   kbe_status sticky = KBE_OK;
+  bool poisoned = false;   // a timed-out copy may have landed after its CTA exited: recreate the handle
   std::string err;
 
   // graph replay of kbe_step (kbe_set_graphs): one instantiated graph per
   // (first row, step count, order of the I ring), valid for the current inputs
   bool graphs = false;
-  std::map<std::tuple<int, int, int>, cudaGraphExec_t> gcache;
+  kbe::GraphCache<std::tuple<int, int, int>> gcache;
   unsigned graph_gen = 0;   // bumped whenever captured kernels would carry stale inputs
   int inject = 0;   // one-shot fault injection for the timeout test (kbe_debug_inject)
 
@@ -144,7 +145,6 @@ cudaError_t dalloc(kbe_handle *h, T **p, size_t count) {
 }
 
 void drop_graphs(kbe_handle *h) {
-  for (auto &kv : h->gcache) cudaGraphExecDestroy(kv.second);
   h->gcache.clear();
   ++h->graph_gen;
 }
@@ -563,8 +563,8 @@ kbe_status backward_step(kbe_handle *h, const AdjPtrs &P, int n, int nc, double2
 // the same key replay it and only advance the host-side state.
 kbe_status step_graph(kbe_handle *h, int nsteps) {
   const auto key = std::make_tuple(h->n, nsteps, h->Ip == h->Ip0 ? 0 : 1);
-  auto it = h->gcache.find(key);
-  if (it == h->gcache.end()) {
+  cudaGraphExec_t exec = h->gcache.find(key);
+  if (!exec) {
     cudaError_t e = kbe::dft_prepare(h->mesh.L0, h->mesh.L1);
     if (e == cudaSuccess) e = kbe::sweep_prepare(h->cfg.nb);
     if (e != cudaSuccess) return cuda_fail(h, e, "graph prepare");
@@ -586,13 +586,12 @@ kbe_status step_graph(kbe_handle *h, int nsteps) {
       h->sticky = KBE_OK;
       return s != KBE_OK ? s : cuda_fail(h, e, "graph capture");
     }
-    cudaGraphExec_t exec = nullptr;
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
-    it = h->gcache.emplace(key, exec).first;
+    h->gcache.put(key, exec);
   }
-  cudaError_t e = cudaGraphLaunch(it->second, h->stream);
+  cudaError_t e = cudaGraphLaunch(exec, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
   for (int i = 0; i < nsteps; ++i) {   // the host-side state one_step keeps
     std::swap(h->Ip, h->Ic);
@@ -613,6 +612,13 @@ kbe_status check_device_status(kbe_handle *h) {
   if (st & kbe::kDevEigNoConv) {
     h->sticky = KBE_ERR_NONFINITE;
     return fail(h, KBE_ERR_NONFINITE, "eigen-solver did not converge (non-finite or huge h)");
+  }
+  if (st & kbe::kDevTimeoutDrain) {
+    h->sticky = KBE_ERR_TIMEOUT;
+    h->poisoned = true;
+    return fail(h, KBE_ERR_TIMEOUT,
+                "a staged copy of the collision sweep did not complete and the copies in flight could not be "
+                "drained: destroy and recreate the handle");
   }
   if (st & kbe::kDevTimeout) {
     h->sticky = KBE_ERR_TIMEOUT;
@@ -882,6 +888,8 @@ kbe_status kbe_set_dipole(kbe_handle *h, int len, const double *E, const double 
 kbe_status kbe_reset(kbe_handle *h) {
   if (!h) return KBE_ERR_ARG;
   if (!h->ham_set) return fail(h, KBE_ERR_STATE, "reset: set_hamiltonian first");
+  if (h->poisoned)
+    return fail(h, KBE_ERR_STATE, "reset: an undrained copy timed out on this handle; destroy and recreate it");
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "reset sync");
   h->sticky = KBE_OK;
@@ -993,6 +1001,31 @@ kbe_status kbe_observables_all(kbe_handle *h, double *n_kb, double *scalars) {
     e = cudaMemcpyAsync(scalars, h->obs, sizeof(double) * rows * 6, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "observables_all copy");
+  return KBE_OK;
+}
+
+kbe_status kbe_observables_all_dev(kbe_handle *h, double *n_kb_dev, double *scalars_dev) {
+  if (!h) return KBE_ERR_ARG;
+  if (h->n < 0) return fail(h, KBE_ERR_STATE, "observables_all_dev: call kbe_reset first");
+  const size_t rows = (size_t)h->n + 1;
+  cudaError_t e = cudaSuccess;
+  if (n_kb_dev)
+    e = cudaMemcpyAsync(n_kb_dev, h->nkb, sizeof(double) * rows * h->mesh.nk * h->cfg.nb,
+                        cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess && scalars_dev)
+    e = cudaMemcpyAsync(scalars_dev, h->obs, sizeof(double) * rows * 6, cudaMemcpyDeviceToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "observables_all_dev copy");
+  return KBE_OK;
+}
+
+kbe_status kbe_get_row_dev(kbe_handle *h, int i, int which, void *out_dev) {
+  if (!h || !out_dev) return KBE_ERR_ARG;
+  if (i < 0 || i > h->n || (which != 0 && which != 1)) return fail(h, KBE_ERR_ARG, "get_row_dev: bad row or component");
+  const bool fp64_copy = i >= h->n - 1;   // the two newest rows are kept in FP64
+  cudaError_t e = kbe::launch_row_out(h->cfg.precision, fp64_copy ? frow(h, i) : nullptr,
+                                      (const char *)h->H + tri(i, 0) * 2 * h->blk * h->esz, (size_t)i + 1,
+                                      h->mesh, which, (double2 *)out_dev, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_row_dev");
   return KBE_OK;
 }
 
@@ -1168,6 +1201,8 @@ kbe_status kbe_checkpoint_save(kbe_handle *h, void *host, size_t bytes) {
 
 kbe_status kbe_checkpoint_load(kbe_handle *h, const void *host, size_t bytes) {
   if (!h || !host || bytes < sizeof(CkptHeader)) return KBE_ERR_ARG;
+  if (h->poisoned)
+    return fail(h, KBE_ERR_STATE, "checkpoint_load: an undrained copy timed out on this handle; recreate it");
   CkptHeader hd;
   memcpy(&hd, host, sizeof hd);
   if (memcmp(hd.magic, "KBECKPT", 8) != 0 || hd.version != 2 || hd.nb != h->cfg.nb ||

@@ -30,7 +30,7 @@ struct kbe_batch {
   std::vector<int> cur;             // host copy of each system's current row
   cudaEvent_t fork = nullptr;
   bool graphs = false;              // replay captured steps (kbe_batch_set_graphs)
-  std::map<std::vector<long>, cudaGraphExec_t> gcache;   // one graph per call shape of the batch
+  kbe::GraphCache<std::vector<long>> gcache;   // one graph per call shape of the batch
 };
 
 namespace {
@@ -40,9 +40,23 @@ kbe_status batch_fail(kbe_status s, const std::string &msg) {
   return s;
 }
 
-void drop_batch_graphs(kbe_batch *b) {
-  for (auto &kv : b->gcache) cudaGraphExecDestroy(kv.second);
-  b->gcache.clear();
+void drop_batch_graphs(kbe_batch *b) { b->gcache.clear(); }
+
+// a cached batch graph whose key holds an outdated input generation of one of
+// its systems can never be replayed again (key: nsteps, then per stepped
+// system i, row, count, ring order, generation)
+void drop_stale_batch_graphs(kbe_batch *b) {
+  b->gcache.drop_if([b](const std::vector<long> &key) {
+    for (size_t q = 1; q + 4 < key.size(); q += 5) {
+      const size_t i = (size_t)key[q];
+      if (i >= b->sys.size() || !b->sys[i]) return true;
+      int ring = 0;
+      unsigned gen = 0;
+      kbe::step_key(b->sys[i], &ring, &gen);
+      if ((long)gen != key[q + 4]) return true;
+    }
+    return false;
+  });
 }
 
 void destroy_all(kbe_batch *b) {
@@ -103,8 +117,9 @@ kbe_status batch_graph_step(kbe_batch *b, int nsteps) {
     kbe::step_key(b->sys[i], &ring, &gen);
     key.insert(key.end(), {(long)i, (long)b->cur[i], (long)k[i], (long)ring, (long)gen});
   }
-  auto it = b->gcache.find(key);
-  if (it == b->gcache.end()) {
+  cudaGraphExec_t exec = b->gcache.find(key);
+  if (!exec) {
+    drop_stale_batch_graphs(b);
     for (size_t i = 0; i < b->sys.size(); ++i)
       if (b->sys[i] && k[i] > 0) {
         kbe_status s = kbe::step_prepare(b->sys[i]);
@@ -130,13 +145,12 @@ kbe_status batch_graph_step(kbe_batch *b, int nsteps) {
       return batch_fail(KBE_ERR_CUDA, std::string("batch graph capture: ") +
                                           cudaGetErrorString(e != cudaSuccess ? e : ee));
     }
-    cudaGraphExec_t exec = nullptr;
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return batch_fail(KBE_ERR_CUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
-    it = b->gcache.emplace(key, exec).first;
+    b->gcache.put(key, exec);
   }
-  cudaError_t e = cudaGraphLaunch(it->second, b->main);
+  cudaError_t e = cudaGraphLaunch(exec, b->main);
   if (e != cudaSuccess) return batch_fail(KBE_ERR_CUDA, std::string("batch graph launch: ") + cudaGetErrorString(e));
   for (size_t i = 0; i < b->sys.size(); ++i)
     if (b->sys[i] && k[i] > 0) {

@@ -12,6 +12,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 
 #include "kbe.h"
@@ -89,8 +90,68 @@ __device__ __forceinline__ double2 c_fnmac(double2 a, double2 b, double2 acc) {
   return make_double2(fma(-a.x, b.x, fma(-a.y, b.y, acc.x)), fma(-a.y, b.x, fma(a.x, b.y, acc.y)));
 }
 
+// Instantiated CUDA graphs keyed by the call shape they replay. At most kCap
+// are kept; to make room the least recently used one is destroyed (a graph
+// that is still running is freed by the runtime once it completes).
+template <class Key>
+struct GraphCache {
+  static constexpr size_t kCap = 64;
+  struct Entry {
+    cudaGraphExec_t exec;
+    unsigned long long used;
+  };
+  std::map<Key, Entry> m;
+  unsigned long long clock = 0;
+  cudaGraphExec_t find(const Key &k) {
+    auto it = m.find(k);
+    if (it == m.end()) return nullptr;
+    it->second.used = ++clock;
+    return it->second.exec;
+  }
+  void put(const Key &k, cudaGraphExec_t e) {
+    if (m.size() >= kCap) {
+      auto lru = m.begin();
+      for (auto it = m.begin(); it != m.end(); ++it)
+        if (it->second.used < lru->second.used) lru = it;
+      cudaGraphExecDestroy(lru->second.exec);
+      m.erase(lru);
+    }
+    m[k] = Entry{e, ++clock};
+  }
+  template <class Pred>
+  void drop_if(Pred stale) {
+    for (auto it = m.begin(); it != m.end();) {
+      if (stale(it->first)) {
+        cudaGraphExecDestroy(it->second.exec);
+        it = m.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
+  void clear() {
+    for (auto &kv : m) cudaGraphExecDestroy(kv.second.exec);
+    m.clear();
+  }
+  size_t size() const { return m.size(); }
+};
+
+// streaming multiprocessors of the current device (queried once per device,
+// cached; grids are sized in multiples of it)
+int device_sms();
+
 // ---- status word written by kernels (sticky, read by the host) -----------
-enum : int { kDevOk = 0, kDevNonFinite = 1, kDevEigNoConv = 2, kDevAdjUnsupported = 4, kDevTimeout = 8 };
+// kDevTimeoutDrain: after a timeout, the wait for a CTA's own copies in
+// flight also ran out, so a copy may still land in shared memory that a later
+// CTA owns: the handle's results can no longer be trusted, even after a reset
+enum : int {
+  kDevOk = 0,
+  kDevNonFinite = 1,
+  kDevEigNoConv = 2,
+  kDevAdjUnsupported = 4,
+  kDevTimeout = 8,
+  kDevTimeoutDrain = 16
+};
 
 // ---- kernels launch wrappers (return cudaGetLastError()) ------------------
 // a1 self-energy row
@@ -126,6 +187,10 @@ cudaError_t tune_sweep(const Mesh &m, int prec, int quad, int nmax, double dt, c
 cudaError_t sweep_prepare(int nb);   // kernel attributes, host side (before stream capture)
 cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t nblocks, size_t blk,
                         cudaStream_t st, const int *skip = nullptr);
+// component `which` of nblk blocks into [j][k][a][b]: from the FP64 working
+// row when fp64 != NULL, else from the history storage of precision prec
+cudaError_t launch_row_out(int prec, const double2 *fp64, const void *packed, size_t nblk, const Mesh &m,
+                           int which, double2 *out, cudaStream_t st);
 // status (may be NULL): device word that receives kDevTimeout if a staged
 // copy never completes (bounded waits)
 // inject (test only): 1 makes the staged C64 sweep's first CTA omit its first

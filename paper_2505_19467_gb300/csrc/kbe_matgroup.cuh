@@ -134,7 +134,8 @@ __device__ __forceinline__ double2 mm_hadj(const MatGroup<NB> &g, const double2 
 template <int NB>
 int matgroup_kpc(int nk) {
   const int E = NB * NB, maxk = 256 / E > 0 ? 256 / E : 1;
-  int kpc = (nk + 151) / 152;
+  const int sms = device_sms();
+  int kpc = (nk + sms - 1) / sms;
   return kpc < 1 ? 1 : (kpc > maxk ? maxk : kpc);
 }
 template <int NB>

@@ -16,6 +16,8 @@
 // Cost per pair: O(N_b^2 n_k log n_k) for power-of-two meshes (FFT), else
 // O(N_b^2 n_k (L0 + L1)), and O(N_b^3 n_k) for the products, against
 // O(N_b^4 n_k^3) for Algorithm 2.
+#include <mutex>
+
 #include "kbe_internal.cuh"
 
 namespace kbe {
@@ -273,15 +275,24 @@ size_t dft_smem_bytes(int L0, int L1) {
 }  // namespace
 
 // raise the DFT kernel's dynamic shared-memory limit for this mesh (a host-side
-// attribute, done before any stream capture that launches it)
+// attribute of the current device's context, done before any stream capture
+// that launches it); the raised limit is kept per device, under a lock
 cudaError_t dft_prepare(int L0, int L1) {
-  static size_t attr_bytes = 48 * 1024;  // default opt-in limit
+  constexpr size_t kDefault = 48 * 1024;   // no opt-in needed below this
+  constexpr int kMaxDev = 64;
+  static std::mutex mu;
+  static size_t raised[kMaxDev] = {};
   const size_t smem = dft_smem_bytes(L0, L1);
-  if (smem > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(dft_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+  if (smem <= kDefault) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(mu);
+  if (smem > raised[dev]) {
+    e = cudaFuncSetAttribute(dft_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    attr_bytes = smem;
+    raised[dev] = smem;
   }
   return cudaSuccess;
 }
@@ -294,7 +305,8 @@ cudaError_t launch_dft_rows(const double2 *in, double2 *out, long narr, int L0, 
   cudaError_t pe = dft_prepare(L0, L1);
   if (pe != cudaSuccess) return pe;
   int threads = nk >= 256 ? 256 : ((nk + 31) / 32) * 32;
-  long blocks = narr < 152L * 8 ? narr : 152L * 8;
+  const long cap = (long)device_sms() * 8;
+  long blocks = narr < cap ? narr : cap;
   dft_rows_kernel<<<(unsigned)blocks, threads, smem, st>>>(in, out, narr, L0, L1, sign, scale,
                                                             accumulate ? 1 : 0, skip);
   return cudaGetLastError();

@@ -38,6 +38,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -631,6 +632,40 @@ __global__ void pack_kernel(int prec, const double2 *__restrict__ src, void *__r
   }
 }
 
+// one component of nblk blocks into [j][k][a][b] (the getters' layout): from
+// the FP64 working row (G^<, G^>) when fp64 != NULL, else from the history's
+// (G^<, dG) storage of precision prec (G^> = G^< - dG)
+__global__ void row_out_kernel(int prec, const double2 *__restrict__ fp64, const void *__restrict__ packed,
+                               size_t nblk, int nb, int nk, int which, double2 *__restrict__ out) {
+  const size_t blk = (size_t)nb * nb * nk, count = nblk * blk;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t j = i / blk, r = i - j * blk;   // r = (k nb + a) nb + b
+    const int k = (int)(r / ((size_t)nb * nb)), ab = (int)(r - (size_t)k * nb * nb);
+    const size_t s0 = j * 2 * blk + (size_t)ab * nk + k, s1 = s0 + blk;
+    double2 v;
+    if (fp64) {
+      v = fp64[which ? s1 : s0];
+    } else {
+      double2 gl, dg;
+      if (prec == KBE_PREC_DF64) {
+        const float4 a = ((const float4 *)packed)[s0], b = ((const float4 *)packed)[s1];
+        gl = make_double2((double)a.x + (double)a.y, (double)a.z + (double)a.w);
+        dg = make_double2((double)b.x + (double)b.y, (double)b.z + (double)b.w);
+      } else if (prec == KBE_PREC_C64) {
+        const float2 a = ((const float2 *)packed)[s0], b = ((const float2 *)packed)[s1];
+        gl = make_double2(a.x, a.y);
+        dg = make_double2(b.x, b.y);
+      } else {
+        gl = ((const double2 *)packed)[s0];
+        dg = ((const double2 *)packed)[s1];
+      }
+      v = which ? c_sub(gl, dg) : gl;
+    }
+    out[i] = v;
+  }
+}
+
 // coefficient rows [l][3][a][c][k]: C1 = w^(n)_l (S^> - S^<), C2^< = dt S^<, C3 = dt S^> - C1
 __global__ void coef_kernel(int prec, const double2 *__restrict__ Sig, void *__restrict__ Cf, int n,
                             int nk, int nb2, double dt, const int *__restrict__ skip, int quad) {
@@ -864,7 +899,9 @@ __global__ void __launch_bounds__(kStagedThreads, KBE_STAGED_MINB)
 // that stage's mbarrier; the hardware zero-fills past n_k. The shared-memory
 // layout is the cp.async form's, so the arithmetic is shared. Every wait on
 // an mbarrier is bounded: past the limit the kernel marks kDevTimeout in the
-// status word and stops after waiting (bounded) for its copies in flight.
+// status word and stops after waiting (bounded) for its copies in flight; if
+// that wait runs out too it also marks kDevTimeoutDrain (a copy may still be
+// writing into shared memory the CTA gives up).
 __device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
@@ -977,9 +1014,10 @@ __global__ void __launch_bounds__(kStagedThreads, KBE_STAGED_MINB)
     __syncthreads();
     if (failed) {   // a copy did not arrive: flag it, let the in-flight ones land, stop
       if (tid == 0) {
-        if (status) atomicOr(status, kDevTimeout);
+        int st = kDevTimeout;
         for (int q = i; q < issued; ++q)
-          mbar_wait(&bar[q % kStages], (unsigned)((q / kStages) & 1), kMbarWaitLimit);
+          if (!mbar_wait(&bar[q % kStages], (unsigned)((q / kStages) & 1), kMbarWaitLimit)) st |= kDevTimeoutDrain;
+        if (status) atomicOr(status, st);
       }
       __syncthreads();
       return;
@@ -998,19 +1036,19 @@ __global__ void __launch_bounds__(kStagedThreads, KBE_STAGED_MINB)
   for (int q = 0; q < NBB; ++q) ArithC64::store(o + (size_t)(a * NB + b0 + q) * nk, blk, accX[q], accY[q]);
 }
 
-// cuTensorMapEncodeTiled from the driver (no link against libcuda)
+// cuTensorMapEncodeTiled from the driver (no link against libcuda); resolved
+// once per process (a thread-safe static: the entry point is not per device)
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
     void *p = nullptr;
     cudaDriverEntryPointQueryResult q;
+    PFN_cuTensorMapEncodeTiled_v12000 r = nullptr;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+      r = (PFN_cuTensorMapEncodeTiled_v12000)p;
     cudaGetLastError();
-  }
+    return r;
+  }();
   return fn;
 }
 
@@ -1046,13 +1084,23 @@ bool staged_tensor_maps(const void *Cf, const void *H, int n, int nk, CUtensorMa
   return true;
 }
 
+// shared-memory limits of the staged kernels, raised once per device (the
+// attribute belongs to the current device's context), under a lock
 template <int NB>
 cudaError_t staged_prepare() {
-  static bool done = false;
-  if (done) return cudaSuccess;
+  constexpr int kMaxDev = 64;
+  static std::mutex mu;
+  static bool done[kMaxDev] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+  tensor_map_encoder();   // resolve the driver entry point outside any stream capture
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return cudaSuccess;
   const int bytes = (int)(kStages * staged_stage_elems(NB) * sizeof(float2));
-  cudaError_t e = cudaFuncSetAttribute(sweep_c64_staged_kernel<NB, kQuadTrapezoid>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  e = cudaFuncSetAttribute(sweep_c64_staged_kernel<NB, kQuadTrapezoid>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(sweep_c64_staged_kernel<NB, kQuadGregory>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              bytes);
@@ -1062,19 +1110,18 @@ cudaError_t staged_prepare() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(sweep_c64_tma_kernel<NB, kQuadGregory>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              bytes);
-  if (e == cudaSuccess) done = true;
-  tensor_map_encoder();   // resolve the driver entry point outside any stream capture
+  if (e == cudaSuccess) done[dev] = true;
   return e;
 }
 
 unsigned grid_for(size_t count) {
-  size_t b = (count + 255) / 256;
-  return (unsigned)(b < 152 * 64 ? (b ? b : 1) : 152 * 64);
+  const size_t b = (count + 255) / 256, cap = (size_t)device_sms() * 64;
+  return (unsigned)(b < cap ? (b ? b : 1) : cap);
 }
 
 // l-split: enough CTAs to give every SM ~8 resident CTAs; the number of
 // partial rows nz (n+1) stays below 2(n+1) + 1024
-constexpr int kTargetCtas = 152 * 8;
+constexpr int kTargetPerSm = 8;
 
 struct SweepShape {
   dim3 grid;
@@ -1139,7 +1186,7 @@ int tuned_target(int prec, int quad, const Mesh &m, int n, int fallback) {
 }
 
 long split_count(long base, int n, int target) {
-  long nz = (152L * target + base - 1) / base;
+  long nz = ((long)device_sms() * target + base - 1) / base;
   if (nz > nz_cap(n)) nz = nz_cap(n);
   return nz < 1 ? 1 : nz;
 }
@@ -1158,7 +1205,7 @@ SweepShape staged_shape(const Mesh &m, int n, int target = KBE_STAGED_TARGET) {
   return sh;
 }
 
-SweepShape sweep_shape(const Mesh &m, int n, int V = 1, int target = kTargetCtas / 152, int maxthreads = 256) {
+SweepShape sweep_shape(const Mesh &m, int n, int V = 1, int target = kTargetPerSm, int maxthreads = 256) {
   SweepShape sh;
   const long elems = (long)m.nb * m.nb * (m.nk / V);
   sh.threads = elems >= maxthreads ? maxthreads : (int)((elems + 31) / 32) * 32;
@@ -1180,7 +1227,7 @@ template <> struct PrecOf<ArithC64x2> { static constexpr int v = KBE_PREC_C64; }
 template <class P, int NB>
 cudaError_t sweep_nb(const Mesh &m, int n, const void *H, const void *Cf, double2 *I, double2 *part,
                      cudaStream_t st, const int *skip, int quad) {
-  const SweepShape sh = sweep_shape(m, n, P::V, tuned_target(PrecOf<P>::v, quad, m, n, kTargetCtas / 152));
+  const SweepShape sh = sweep_shape(m, n, P::V, tuned_target(PrecOf<P>::v, quad, m, n, kTargetPerSm));
   double2 *out = sh.nz > 1 ? part : I;
   const int nkS = m.nk / P::V;   // stored elements per (a, b) array
   if (quad == kQuadGregory)
@@ -1200,7 +1247,7 @@ template <int NB>
 cudaError_t sweep_blocked(const Mesh &m, int n, const void *H, const void *Cf, double2 *I, double2 *part,
                           cudaStream_t st, const int *skip, int quad) {
   const Mesh m1{1, m.L0, m.L1, m.nk};   // one thread per k
-  SweepShape sh = sweep_shape(m1, n, 1, tuned_target(KBE_PREC_C64, quad, m, n, kTargetCtas / 152),
+  SweepShape sh = sweep_shape(m1, n, 1, tuned_target(KBE_PREC_C64, quad, m, n, kTargetPerSm),
                               KBE_BLOCKED_THREADS);
   double2 *out = sh.nz > 1 ? part : I;
   if (quad == kQuadGregory)
@@ -1262,6 +1309,27 @@ cudaError_t sweep_prec(const Mesh &m, int n, int prec, const void *H, const void
 
 }  // namespace
 
+int device_sms() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cache[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    dev = -1;
+  }
+  if (dev >= 0 && dev < kMaxDev) {
+    const int c = cache[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
+  int v = 0;
+  if (dev < 0 || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (dev < kMaxDev) cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
 bool sweep_supported(int nb) {
   switch (nb) {
     case 1: case 2: case 3: case 4: case 6: case 8: case 12: case 16: return true;
@@ -1294,7 +1362,7 @@ size_t sweep_workspace_bytes(const Mesh &m, int n, int prec) {
 
 int sweep_splits(const Mesh &m, int n, int prec, int quad) {
   if (use_staged(m, prec)) return staged_shape(m, n, tuned_target(prec, quad, m, n, KBE_STAGED_TARGET)).nz;
-  return sweep_shape(m, n, sweep_width(m, prec), tuned_target(prec, quad, m, n, kTargetCtas / 152)).nz;
+  return sweep_shape(m, n, sweep_width(m, prec), tuned_target(prec, quad, m, n, kTargetPerSm)).nz;
 }
 
 // Times launch_sweep at one row per power-of-two bucket of n (up to nmax)
@@ -1359,6 +1427,14 @@ cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t nblocks,
   return cudaGetLastError();
 }
 
+cudaError_t launch_row_out(int prec, const double2 *fp64, const void *packed, size_t nblk, const Mesh &m,
+                           int which, double2 *out, cudaStream_t st) {
+  const size_t count = nblk * (size_t)m.nb * m.nb * m.nk;
+  if (count == 0) return cudaSuccess;
+  row_out_kernel<<<grid_for(count), 256, 0, st>>>(prec, fp64, packed, nblk, m.nb, m.nk, which, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const void *H,
                          const double2 *Sig, double2 *I, void *work, cudaStream_t st, const int *skip,
                          int quad, int *status, int inject) {
@@ -1385,3 +1461,18 @@ cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const v
 }
 
 }  // namespace kbe
+
+// build and device facts for diagnostics (include/kbe.h)
+extern "C" kbe_status kbe_device_info(int *binary_version, int *sm_count) {
+  if (binary_version) {
+    cudaFuncAttributes fa{};
+    const cudaError_t e = cudaFuncGetAttributes(&fa, kbe::reduce_partials_kernel);
+    if (e != cudaSuccess) {
+      kbe::set_last_error(std::string("device_info: ") + cudaGetErrorString(e));
+      return KBE_ERR_CUDA;
+    }
+    *binary_version = fa.binaryVersion;
+  }
+  if (sm_count) *sm_count = kbe::device_sms();
+  return KBE_OK;
+}

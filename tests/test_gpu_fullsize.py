@@ -93,3 +93,60 @@ def test_c64_full_c2_density_and_energy(golden):
     escale = np.abs(golden["obs"][:, 5]).max()
     assert np.abs(sc[:, 1:] - golden["obs"][:, 1:]).max() <= 1e-5 * escale
     g.close()
+
+
+# ---- c3 (N_b = 8, 16x16 mesh, driven): the first 24 steps against the oracle ----
+GOLDEN_C3 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "c3_prefix.npz")
+C3_FLOOR = 1e-4   # the short-run floor (the conditioning bar above applies from ~100 steps)
+
+
+@pytest.fixture(scope="module")
+def golden_c3():
+    return np.load(GOLDEN_C3)
+
+
+def run_c3(prec, nsteps):
+    s = ki.config("c3")
+    g = kbe.KBE.from_system(s, precision=prec, nt_max=nsteps)
+    g.step(nsteps)
+    g.synchronize()
+    return g
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_c3_prefix_every_sample(golden_c3, prec):
+    """c3's first 24 steps in the FP64 and DF64 forms: 4096 sampled entries of
+    rows 4..24 and the time-diagonal blocks element-wise at 1e-10 (floor 1e-4
+    of the row scale), observables at 1e-10"""
+    gold = golden_c3
+    g = run_c3(kbe.PRECISIONS[prec], int(gold["nsteps"]))
+    samples, values = gold["samples"], gold["values"]
+    for i in sorted(set(samples[:, 0].tolist())):
+        sel = samples[:, 0] == i
+        lt, gt = g.row(int(i), 0), g.row(int(i), 1)
+        scale = max(np.abs(lt).max(), np.abs(gt).max())
+        got = np.array([(lt if x == 0 else gt)[j, k, a, b] for (_, j, x, k, a, b) in samples[sel]])
+        d = np.abs(got - values[sel])
+        assert (d / np.maximum(np.abs(values[sel]), C3_FLOOR * scale)).max() < EL_TOL, i
+    for r, i in enumerate(gold["diag_rows"]):
+        scale = max(np.abs(gold["diag_lesser"][r]).max(), np.abs(gold["diag_greater"][r]).max())
+        for x, key in ((0, "diag_lesser"), (1, "diag_greater")):
+            d = np.abs(g.row(int(i), x)[int(i)] - gold[key][r])
+            assert (d / np.maximum(np.abs(gold[key][r]), C3_FLOOR * scale)).max() < EL_TOL, (i, x)
+    nkb, sc = g.observables_all()
+    assert np.abs(nkb - gold["nkb"]).max() < 1e-10
+    assert np.abs(sc - gold["obs"]).max() < 1e-10 * np.abs(gold["obs"]).max()
+    g.close()
+
+
+def test_c3_prefix_c64_density_and_energy(golden_c3):
+    """c3's first 24 steps in the complex64 form: occupations and every
+    energy within 1e-5 of the oracle (relative to their largest magnitude)"""
+    gold = golden_c3
+    g = run_c3(kbe.KBE_PREC_C64, int(gold["nsteps"]))
+    nkb, sc = g.observables_all()
+    assert np.abs(nkb - gold["nkb"]).max() <= 1e-5 * np.abs(gold["nkb"]).max()
+    escale = np.abs(gold["obs"][:, 5]).max()
+    assert np.abs(sc[:, 1:] - gold["obs"][:, 1:]).max() <= 1e-5 * escale
+    assert np.abs(sc[:, 0] - gold["obs"][:, 0]).max() <= 1e-5 * gold["obs"][0, 0]
+    g.close()

@@ -56,7 +56,12 @@ def test_collision_row_reduced_storage(prec, tol, nb, L, n):
     kbe.collision_row(nb, L, n, dt, H, S, I, precision=prec, work=work)
     torch.cuda.synchronize()
     gl, gg = from_dev_blocks(I.cpu().numpy())
-    assert relerr(gl, Il)[1] < tol and relerr(gg, Ig)[1] < tol
+    # normwise bar, and element-wise: DF64 1e-10 above 1e-4 of the scale,
+    # C64 1e-4 above 1e-2 of it (complex64 rounds every stored input at 6e-8)
+    floor, el_bar = (1e-4, 1e-10) if prec == 1 else (1e-2, 1e-4)
+    for got, ref in ((gl, Il), (gg, Ig)):
+        el, nw = relerr(got, ref, floor_frac=floor)
+        assert nw < tol and el < el_bar, (el, nw)
 
 
 def _trajectory(sys, prec, nsteps):

@@ -161,3 +161,30 @@ def test_checkpoint_resume_is_exact(prec):
     c = kbe.KBE(s.nb, s.dim, (2, 3), s.nt, s.dt, s.beta, s.mu, precision=prec)
     with pytest.raises(kbe.KBEError):
         c.restore(ck)                    # another mesh
+
+
+@pytest.mark.parametrize("prec", [kbe.KBE_PREC_FP64, kbe.KBE_PREC_DF64, kbe.KBE_PREC_C64])
+def test_device_getters_match_host_getters(prec):
+    """kbe_get_row_dev / kbe_observables_all_dev write the same values as the
+    host getters into caller-owned device tensors: stored rows (unpacked from
+    the history's storage) and the two newest FP64 rows, both components"""
+    s = ki.config("c2", nt=6)
+    g = kbe.KBE.from_system(s, precision=prec)
+    g.step(6)
+    g.synchronize()
+    dev = torch.device("cuda")
+    for i in (0, 2, 5, 6):
+        for x in (0, 1):
+            out = torch.full((i + 1, s.nk, s.nb, s.nb), float("nan"), dtype=torch.complex128, device=dev)
+            torch.cuda.synchronize()   # the fill is done before the handle's stream writes
+            g.row_dev(i, x, out)
+            g.synchronize()
+            assert np.array_equal(out.cpu().numpy(), g.row(i, x)), (i, x)
+    nkb = torch.empty((7, s.nk, s.nb), dtype=torch.float64, device=dev)
+    sc = torch.empty((7, 6), dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    g.observables_all_dev(nkb, sc)
+    g.synchronize()
+    nkb_h, sc_h = g.observables_all()
+    assert np.array_equal(nkb.cpu().numpy(), nkb_h) and np.array_equal(sc.cpu().numpy(), sc_h)
+    g.close()

@@ -326,6 +326,15 @@ kbe_status kbe_batch_set_graphs(kbe_batch *b, int enable);
  * device's streaming multiprocessors, against which grids are sized. */
 kbe_status kbe_device_info(int *binary_version, int *sm_count);
 
+/* Measured FMA throughput of the current device in GFLOP/s (2 flops per
+ * FMA): FP64 (fp64_gflops) and FP32 (fp32_gflops), either may be NULL. A
+ * grid of 8 CTAs per SM runs independent FMA chains, timed with CUDA events
+ * on the default stream (best of three runs after a warm-up; synchronises).
+ * These are the denominators of the ALU-bound sweep forms' roofline
+ * fractions: the FP64 form on the FP64 pipe, the double-float and complex64
+ * forms on the FP32 pipe. Allocates and frees 8 bytes of device memory. */
+kbe_status kbe_measure_fma_peaks(double *fp64_gflops, double *fp32_gflops);
+
 /* Message of the last error of this handle; with NULL, of the last failed
  * create or handle-free operation (kbe_op_*) on the calling thread. */
 const char *kbe_last_error(const kbe_handle *h);

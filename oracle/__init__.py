@@ -8,7 +8,7 @@ Block layout on this side is [k][a][b] (band indices fastest).
 Parity status of each function (what pins it) is listed in ``PINS`` below and
 checked by ``tests/test_oracle_pins.py``.
 """
-from .oracle import (Oracle, build, sigma_pair, sigma_pair_literal, collision_row,
+from .oracle import (Oracle, build, sigma_pair, sigma_pair_literal, collision_row, evaluate_row_on,
                      propagators, update_row, library_path)
 from . import gradient
 

@@ -790,6 +790,24 @@ static void evaluate_row(orc *s, int n) {
                       (double *)s->Icg);
 }
 
+/* One evaluation of row n as orc_step performs it (the Sigma row from the
+ * triangle's row n, then the collision row), on caller arrays: Hl, Hg the
+ * triangle with rows 0..n, S* and I* (n+1) blocks each, all [k][a][b]. U(t)
+ * is the constant U. Used to time the oracle at sampled rows of a long
+ * trajectory without running the steps before them. */
+void orc_evaluate_row_on(int nb, int L0, int L1, const double *v, double U, int n, double dt,
+                         const double *Hl_, const double *Hg_, double *Sl_, double *Sg_, double *Il_,
+                         double *Ig_) {
+  const cplx *Hl = (const cplx *)Hl_, *Hg = (const cplx *)Hg_;
+  cplx *Sl = (cplx *)Sl_, *Sg = (cplx *)Sg_;
+  size_t blk = (size_t)L0 * L1 * nb * nb;
+#pragma omp parallel for schedule(dynamic)
+  for (int l = 0; l <= n; ++l)
+    orc_sigma_pair(nb, L0, L1, v, U * U, (const double *)(Hl + tri(n, l) * blk),
+                   (const double *)(Hg + tri(n, l) * blk), (double *)(Sl + l * blk), (double *)(Sg + l * blk));
+  collision_left(nb, L0 * L1, n, dt, 0, Hl, Hg, NULL, NULL, Sl, Sg, (cplx *)Il_, (cplx *)Ig_);
+}
+
 static void update(orc *s, int n, double theta) {
   size_t blk = s->blk;
   orc_update_row(s->nb, s->nk, n, s->dt, theta, (const double *)s->Uk, (const double *)s->Vk,

@@ -66,6 +66,7 @@ def _load():
             lib.orc_set_threads.argtypes = [i]
             lib.orc_threads.restype = i
             lib.orc_enable_full.argtypes = [P, i]
+            lib.orc_evaluate_row_on.argtypes = [i, i, i, P, d, i, d, P, P, P, P, P, P]
             _lib = lib
     return _lib
 
@@ -117,6 +118,20 @@ def collision_row(nb, nk, n, dt, Hl, Hg, Sl, Sg, quadrature=0):
     lib.orc_collision_row_q(nb, nk, n, float(dt), int(quadrature), _ptr(Hl), _ptr(Hg), _ptr(Sl), _ptr(Sg),
                             _ptr(Il), _ptr(Ig))
     return Il, Ig
+
+
+def evaluate_row_on(nb, L, v, U, n, dt, Hl, Hg):
+    """One row evaluation as the stepper performs it (Sigma row n of the
+    triangle's row n, then the collision row) on caller arrays: Hl, Hg hold a
+    triangle with at least rows 0..n ([ntri, nk, nb, nb] complex128). Returns
+    (Sl, Sg, Il, Ig), each [n+1, nk, nb, nb]. For timing sampled rows."""
+    lib = _load()
+    nk = L[0] * L[1]
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    S = [np.empty((n + 1, nk, nb, nb), np.complex128) for _ in range(4)]
+    lib.orc_evaluate_row_on(nb, L[0], L[1], _ptr(v), float(U), int(n), float(dt), _ptr(Hl), _ptr(Hg),
+                            *(_ptr(x) for x in S))
+    return tuple(S)
 
 
 def propagators(nb, nk, dt, h):

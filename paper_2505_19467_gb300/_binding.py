@@ -37,7 +37,7 @@ EXPORTS = [
     "kbe_batch_synchronize", "kbe_checkpoint_bytes", "kbe_checkpoint_save", "kbe_checkpoint_load",
     "kbe_set_dipole", "kbe_backward", "kbe_backward_memory_bytes", "kbe_corrector_iterations",
     "kbe_op_collision_row_quad", "kbe_set_graphs", "kbe_autotune", "kbe_debug_inject", "kbe_batch_set_graphs",
-    "kbe_observables_all_dev", "kbe_get_row_dev", "kbe_device_info",
+    "kbe_observables_all_dev", "kbe_get_row_dev", "kbe_device_info", "kbe_measure_fma_peaks",
 ]
 
 
@@ -127,6 +127,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "kbe_observables_all_dev": (I, [P, P, P]),
         "kbe_get_row_dev": (I, [P, I, I, P]),
         "kbe_device_info": (I, [P, P]),
+        "kbe_measure_fma_peaks": (I, [P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -504,3 +505,10 @@ def device_info():
     bv, sm = ctypes.c_int(), ctypes.c_int()
     _check(load().kbe_device_info(ctypes.byref(bv), ctypes.byref(sm)))
     return bv.value, sm.value
+
+
+def measure_fma_peaks():
+    """(FP64, FP32) FMA throughput of the current device in GFLOP/s (measured)"""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().kbe_measure_fma_peaks(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value

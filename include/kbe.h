@@ -176,7 +176,9 @@ kbe_status kbe_set_graphs(kbe_handle *h, int enable);
  * of n (n + 1 in [2^b, 2^(b+1)), up to nt_max) and keeps the fastest per
  * (precision, quadrature, N_b, n_k, bucket) for the rest of the process; every
  * later sweep of that shape (any handle) uses it, untuned shapes keep the
- * default. Only scratch buffers are written (it may be called between steps);
+ * default. For complex64 histories the candidates include the single-read
+ * tile sweep (see kbe_set_sweep_choice). Only scratch buffers are written
+ * (it may be called between steps);
  * cached graphs are dropped. targets (host int [KBE_AUTOTUNE_BUCKETS], may be
  * NULL) receives the choice per bucket (0: bucket above nt_max). Synchronises. */
 #define KBE_AUTOTUNE_BUCKETS 17
@@ -353,6 +355,22 @@ typedef struct kbe_mesh {
   int nb;    /* bands (see kbe_config)           */
   int L[2];  /* mesh extents, L[1] = 1 for 1-D   */
 } kbe_mesh;
+
+/* The choice kbe_autotune stores, set by hand for one sweep shape (mesh m,
+ * precision, quadrature) and row bucket (n + 1 in [2^bucket, 2^(bucket+1));
+ * -1: every bucket), for every handle and stateless call of that shape:
+ *   choice > 0 (<= 64): the per-column sweep, its l-split aiming at `choice`
+ *                       CTAs per SM;
+ *   choice < 0:         the single-read tile sweep (KBE_PREC_C64, N_b in
+ *                       {2, 4, 8}, n_k even), -choice >= 32 rows per work
+ *                       item: each stored block is read from HBM once and
+ *                       feeds both of its uses;
+ *   choice = 0:         back to the built-in default (the tile sweep from
+ *                       row 255 on where it applies).
+ * The choice changes the summation order only. KBE_ERR_ARG if the choice does
+ * not apply to the shape. kbe_autotune's targets use the same encoding. Not
+ * thread safe against concurrent sweeps of the same shape. */
+kbe_status kbe_set_sweep_choice(const kbe_mesh *m, int precision, int quadrature, int bucket, int choice);
 
 /* (a1) Second-Born self-energy row, Eq. 7:
  *   Sigma^x(k; t_n, t_l), l = 0..n, from row n of G (blocks (n, l)),

@@ -7,13 +7,14 @@ from ._binding import (KBE, KBEError, KBE_PREC_FP64, KBE_PREC_DF64, KBE_PREC_C64
                        EXPORTS, collision_row_workspace, pack, LIB_PATH, load, collision_row,
                        propagators, sigma_row, sigma_row_noalloc, sigma_row_workspace, update_row,
                        NOALLOC_SCRATCH_BYTES, KBEBatch, memory_bytes, backward_memory_bytes,
-                       system_config, device_info, measure_fma_peaks)
+                       system_config, device_info, measure_fma_peaks,
+                       set_sweep_choice)
 from .builder import build
 
 __all__ = ["KBE", "KBEError", "KBE_PREC_FP64", "KBE_PREC_DF64", "KBE_PREC_C64", "PRECISIONS",
            "collision_row_workspace", "pack", "EXPORTS", "LIB_PATH", "load", "build",
            "sigma_row", "sigma_row_noalloc", "sigma_row_workspace", "NOALLOC_SCRATCH_BYTES", "collision_row", "propagators", "update_row",
-           "KBEBatch", "memory_bytes", "backward_memory_bytes", "system_config", "device_info", "measure_fma_peaks", "occupations",
+           "KBEBatch", "memory_bytes", "backward_memory_bytes", "system_config", "device_info", "measure_fma_peaks", "set_sweep_choice", "occupations",
            "KBEFunction"]
 
 

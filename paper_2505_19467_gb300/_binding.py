@@ -38,6 +38,7 @@ EXPORTS = [
     "kbe_set_dipole", "kbe_backward", "kbe_backward_memory_bytes", "kbe_corrector_iterations",
     "kbe_op_collision_row_quad", "kbe_set_graphs", "kbe_autotune", "kbe_debug_inject", "kbe_batch_set_graphs",
     "kbe_observables_all_dev", "kbe_get_row_dev", "kbe_device_info", "kbe_measure_fma_peaks",
+    "kbe_set_sweep_choice",
 ]
 
 
@@ -128,6 +129,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "kbe_get_row_dev": (I, [P, I, I, P]),
         "kbe_device_info": (I, [P, P]),
         "kbe_measure_fma_peaks": (I, [P, P]),
+        "kbe_set_sweep_choice": (I, [pmesh, I, I, I, I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -512,3 +514,11 @@ def measure_fma_peaks():
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(load().kbe_measure_fma_peaks(ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def set_sweep_choice(nb, L, precision, choice, quadrature=0, bucket=-1):
+    """the sweep's launch choice for a shape (kbe_set_sweep_choice): > 0 the
+    per-column sweep's CTAs per SM, < 0 the single-read tile sweep with -choice
+    rows per work item, 0 the default"""
+    m = mesh(nb, L)
+    _check(load().kbe_set_sweep_choice(ctypes.byref(m), int(precision), int(quadrature), int(bucket), int(choice)))

@@ -1436,4 +1436,13 @@ kbe_status kbe_op_update_row(const kbe_mesh *m, int n, double dt, double theta, 
   return KBE_OK;
 }
 
+kbe_status kbe_set_sweep_choice(const kbe_mesh *m, int precision, int quadrature, int bucket, int choice) {
+  if (!mesh_ok(m) || !kbe::precision_supported(precision) ||
+      (quadrature != KBE_QUAD_TRAPEZOID && quadrature != KBE_QUAD_GREGORY))
+    return fail(nullptr, KBE_ERR_ARG, "set_sweep_choice: bad mesh, precision or quadrature");
+  if (!kbe::set_sweep_choice(to_mesh(m), precision, quadrature, bucket, choice))
+    return fail(nullptr, KBE_ERR_ARG, "set_sweep_choice: choice or bucket out of range for this shape");
+  return KBE_OK;
+}
+
 }  // extern "C"

@@ -185,6 +185,16 @@ int sweep_splits(const Mesh &m, int n, int prec, int quad);   // CTAs sharing on
 cudaError_t tune_sweep(const Mesh &m, int prec, int quad, int nmax, double dt, const void *H, const double2 *Sig,
                        double2 *I, void *work, cudaStream_t st, int *out, int nout);
 cudaError_t sweep_prepare(int nb);   // kernel attributes, host side (before stream capture)
+// set (choice != 0) or clear (0) the tuned launch choice of a sweep shape for
+// row bucket `bucket` (-1: all); false if the choice does not apply
+bool set_sweep_choice(const Mesh &m, int prec, int quad, int bucket, int choice);
+// the single-read complex64 sweep (kbe_sweep_tile.cu): N_b in {2, 4, 8}, n_k
+// even; TI rows per work item; part holds its partial sums (tile_part_bytes)
+bool tile_supported(const Mesh &m, int prec);
+size_t tile_part_bytes(const Mesh &m, int n, int TI);
+cudaError_t tile_prepare(int nb);
+cudaError_t launch_sweep_tile(const Mesh &m, int n, const void *H, const void *Cf, double2 *I, void *part,
+                              cudaStream_t st, const int *skip, int quad, int *status, int TI);
 cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t nblocks, size_t blk,
                         cudaStream_t st, const int *skip = nullptr);
 // component `which` of nblk blocks into [j][k][a][b]: from the FP64 working

@@ -45,6 +45,7 @@
 #include <vector>
 
 #include "kbe_internal.cuh"
+#include "kbe_tma.cuh"
 
 #ifndef KBE_SWEEP_MINB_F64
 #define KBE_SWEEP_MINB_F64 2
@@ -902,57 +903,6 @@ __global__ void __launch_bounds__(kStagedThreads, KBE_STAGED_MINB)
 // status word and stops after waiting (bounded) for its copies in flight; if
 // that wait runs out too it also marks kDevTimeoutDrain (a copy may still be
 // writing into shared memory the CTA gives up).
-__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-
-constexpr unsigned long long kMbarWaitNs = 1000000000ull;   // one second per wait
-
-// true when the phase with this parity has completed; false after one second
-// of device time (%globaltimer) or `limit` rounds, whichever comes first
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, int limit) {
-  const unsigned a = smem_addr(bar);
-  const unsigned long long t0 = global_ns();
-  for (int it = 0; it < limit; ++it) {
-    if ((it & 255) == 255 && global_ns() - t0 > kMbarWaitNs) return false;
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *tm, int x, int y, int z, uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-      "[%5];\n" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *tm, int x, int y, int z, int w,
-                                            uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-      "%5}], [%6];\n" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_addr(bar))
-      : "memory");
-}
-
-constexpr int kMbarWaitLimit = 1 << 30;   // try_wait rounds (a backstop; the time limit comes first)
 
 template <int NB, int QUAD>
 __global__ void __launch_bounds__(kStagedThreads, KBE_STAGED_MINB)
@@ -1034,22 +984,6 @@ __global__ void __launch_bounds__(kStagedThreads, KBE_STAGED_MINB)
   double2 *o = out + ((size_t)blockIdx.z * (n + 1) + j) * 2 * blk + k;
 #pragma unroll
   for (int q = 0; q < NBB; ++q) ArithC64::store(o + (size_t)(a * NB + b0 + q) * nk, blk, accX[q], accY[q]);
-}
-
-// cuTensorMapEncodeTiled from the driver (no link against libcuda); resolved
-// once per process (a thread-safe static: the entry point is not per device)
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    PFN_cuTensorMapEncodeTiled_v12000 r = nullptr;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      r = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    cudaGetLastError();
-    return r;
-  }();
-  return fn;
 }
 
 // tensor maps of the coefficient rows (rows 0..n) and the stored triangle (rows
@@ -1292,9 +1226,24 @@ cudaError_t sweep_staged(const Mesh &m, int n, const void *H, const void *Cf, do
   return cudaGetLastError();
 }
 
+// The complex64 sweep's form per row: a negative tuned choice -TI selects the
+// single-read tile kernel with TI rows per work item (kbe_sweep_tile.cu);
+// untuned rows take it from n = 255 on (TI = 64), where its work items fill
+// the GPU. Fault injection always takes the staged kernel.
+constexpr int kTileMinTI = 32;
+int tile_default(const Mesh &m, int prec, int n) {
+  return tile_supported(m, prec) && n >= 255 ? -64 : 0;
+}
+
 template <int NB>
 cudaError_t sweep_prec(const Mesh &m, int n, int prec, const void *H, const void *Cf, double2 *I,
                        double2 *part, cudaStream_t st, const int *skip, int quad, int *status, int inject) {
+  if constexpr (NB == 2 || NB == 4 || NB == 8) {
+    if (tile_supported(m, prec) && !inject) {
+      const int t = tuned_target(prec, quad, m, n, tile_default(m, prec, n));
+      if (t < 0) return launch_sweep_tile(m, n, H, Cf, I, part, st, skip, quad, status, -t);
+    }
+  }
   if constexpr (NB == 1 || NB == 2 || NB == 4 || NB == 8 || NB == 16) {
     if (use_staged(m, prec)) return sweep_staged<NB>(m, n, H, Cf, I, part, st, skip, quad, status, inject);
   }
@@ -1308,6 +1257,22 @@ cudaError_t sweep_prec(const Mesh &m, int n, int prec, const void *H, const void
 }
 
 }  // namespace
+
+// cuTensorMapEncodeTiled from the driver (no link against libcuda); resolved
+// once per process (a thread-safe static: the entry point is not per device)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    PFN_cuTensorMapEncodeTiled_v12000 r = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      r = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    cudaGetLastError();
+    return r;
+  }();
+  return fn;
+}
 
 int device_sms() {
   constexpr int kMaxDev = 64;
@@ -1344,7 +1309,7 @@ bool precision_supported(int prec) {
 size_t history_elem_bytes(int prec) { return prec == KBE_PREC_C64 ? sizeof(float2) : 16; }
 
 // coefficient rows (n+1) x 3 blocks in the storage format, then the partial
-// sums of the l split (FP64)
+// sums of the l split (FP64) or of the tile form (complex64)
 size_t sweep_workspace_bytes(const Mesh &m, int n, int prec) {
   const size_t blk = (size_t)m.nb * m.nb * m.nk;
   size_t coef = (size_t)(n + 1) * 3 * blk * history_elem_bytes(prec);
@@ -1357,10 +1322,17 @@ size_t sweep_workspace_bytes(const Mesh &m, int n, int prec) {
       if (b > part) part = b;
     }
   }
+  if (tile_supported(m, prec)) {   // the tile form's partials at its smallest TI (grows with n)
+    const size_t b = tile_part_bytes(m, n, kTileMinTI);
+    if (b > part) part = b;
+  }
   return coef + part;
 }
 
 int sweep_splits(const Mesh &m, int n, int prec, int quad) {
+  if ((m.nb == 2 || m.nb == 4 || m.nb == 8) && tile_supported(m, prec) &&
+      tuned_target(prec, quad, m, n, tile_default(m, prec, n)) < 0)
+    return 2;   // the tile kernel and its reduction
   if (use_staged(m, prec)) return staged_shape(m, n, tuned_target(prec, quad, m, n, KBE_STAGED_TARGET)).nz;
   return sweep_shape(m, n, sweep_width(m, prec), tuned_target(prec, quad, m, n, kTargetPerSm)).nz;
 }
@@ -1372,7 +1344,9 @@ int sweep_splits(const Mesh &m, int n, int prec, int quad) {
 cudaError_t tune_sweep(const Mesh &m, int prec, int quad, int nmax, double dt, const void *H, const double2 *Sig,
                        double2 *I, void *work, cudaStream_t st, int *out, int nout) {
   const bool staged = use_staged(m, prec);
-  const std::vector<int> cands = staged ? std::vector<int>{3, 6, 12, 24} : std::vector<int>{2, 4, 8, 16, 32};
+  std::vector<int> cands = staged ? std::vector<int>{3, 6, 12, 24} : std::vector<int>{2, 4, 8, 16, 32};
+  if (tile_supported(m, prec))   // the single-read tile form, TI rows per work item
+    for (int ti : {kTileMinTI, 64, 128}) cands.push_back(-ti);
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return cudaErrorUnknown;
   cudaError_t err = cudaSuccess;
@@ -1408,8 +1382,24 @@ cudaError_t tune_sweep(const Mesh &m, int prec, int quad, int nmax, double dt, c
   return err;
 }
 
+// manual form of the autotuner's table (kbe_set_sweep_choice): bucket -1 sets
+// every bucket; choice 0 removes the entry (the default applies again)
+bool set_sweep_choice(const Mesh &m, int prec, int quad, int bucket, int choice) {
+  if (choice < 0 && (!tile_supported(m, prec) || -choice < kTileMinTI || -choice > 4096)) return false;
+  if (choice > 64 || bucket < -1 || bucket >= 31) return false;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (int b = bucket < 0 ? 0 : bucket; b <= (bucket < 0 ? 30 : bucket); ++b) {
+    const TuneKey key(prec, quad, m.nb, m.nk, b);
+    if (choice == 0) g_tune.erase(key);
+    else g_tune[key] = choice;
+  }
+  return true;
+}
+
 // shared-memory limits of the staged kernels (host side, before any capture)
 cudaError_t sweep_prepare(int nb) {
+  const cudaError_t e = tile_prepare(nb);
+  if (e != cudaSuccess) return e;
   switch (nb) {
     case 1: return staged_prepare<1>();
     case 2: return staged_prepare<2>();

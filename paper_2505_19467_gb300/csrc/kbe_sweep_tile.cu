@@ -1,0 +1,484 @@
+// (a2) Collision-integral sweep of the complex64 history that reads every
+// stored block from HBM once per evaluation (Eq. 6, left form).
+//
+// The sweep needs each stored block B = (G^<, dG)(t_i, t_m), i > m, twice:
+//   column use (output column m, memory-time node i > m):
+//       X(m) += C1(i) B^<,        Y(m) -= C1(i) dB,
+//   row use (output column i, node m < i, through G(t_m, t_i) = -B^+):
+//       X(i) += C1(m) G^<(m,i) + f C2^<(m) dG(m,i),
+// with X = I^<, Y = I^> - I^<, C1 = w^(n)_l (S^> - S^<), C2^< = dt S^<,
+// C3 = dt S^> - C1, and f = w^(i)_m / dt the weight of node m on [0, t_i]
+// (1 in the interior). The diagonal block (j, j) is the end node l = j of
+// column j: X(j) += C1 B^< + f C2^< dB, Y(j) += (f (C3 - C2^<) + (f - 1) C1) dB
+// (for j = 0 it is an ordinary node above the output, X += C1 B^<,
+// Y -= C1 dB). The per-column sweep (kbe_sweep.cu) serves the two uses from
+// different CTAs, so every block crosses HBM twice.
+//
+// Here a CTA owns a strip of TM output columns [M0, M0 + TM), a chunk of at
+// most TI rows [R0, R1) below the strip's top, and KT consecutive k. It walks
+// the chunk one row i at a time: the row segment, blocks (i, M0 .. M0+TM-1),
+// is contiguous in the triangle, so one 4-D TMA box brings it (with the C1(i)
+// coefficient row) into a 3-stage shared-memory ring, and every block of it
+// feeds both uses from shared memory:
+//   - warp g handles the TMW columns M0 + g TMW + q; a lane is one (k, a)
+//     pair, so a lane owns the output row a of X(m), Y(m) for its columns and
+//     keeps them in registers over the whole chunk (column use);
+//   - the same lane adds the row use of its columns to X(i)_{a, .}; the warps'
+//     shares are summed through shared memory once per row.
+// Every lane of a warp reads the same block (lanes differ in k and a), so a
+// load is KT consecutive complex64 values, conflict-free.
+//
+// Partial sums are complex64: the column partials of one chunk (X, Y of each
+// column, summed over <= TI rows) and the row partials of one strip (X of each
+// row, summed over the strip's TM columns). tile_reduce_kernel adds them in
+// FP64 in a fixed order (the result is deterministic) and adds the row use's
+// Y terms at the few nodes where the weights of [0, t_j] and [0, t_n] differ
+// (none for the trapezoid rule; the Gregory end nodes). The extra traffic is
+// ~(1/TI + 1/(2 TM)) of the triangle's bytes, written once and read once.
+//
+// Every wait on an mbarrier is bounded (kbe_tma.cuh): a copy that never lands
+// marks kDevTimeout (and kDevTimeoutDrain if the copies in flight cannot be
+// drained) in the status word and the CTA stops.
+#include <mutex>
+
+#include "kbe_internal.cuh"
+#include "kbe_tma.cuh"
+
+namespace kbe {
+
+namespace {
+
+// per N_b: KT k per CTA (a lane is one (k, a): KT N_b = 32), TMW columns per warp
+template <int NB>
+struct TileCfg;
+template <>
+struct TileCfg<2> {
+  static constexpr int KT = 16, TMW = 4;
+};
+template <>
+struct TileCfg<4> {
+  static constexpr int KT = 8, TMW = 4;
+};
+template <>
+struct TileCfg<8> {
+  static constexpr int KT = 4, TMW = 2;
+};
+
+constexpr int kTileWarps = 8;
+constexpr int kTileThreads = 32 * kTileWarps;
+constexpr int kTileStages = 3;
+
+template <int NB>
+__host__ __device__ constexpr int tile_tm() {
+  return TileCfg<NB>::TMW * kTileWarps;
+}
+// complex64 values of one stage: the TM blocks [q][x][a b][kk], then C1(i) [a c][kk]
+template <int NB>
+__host__ __device__ constexpr int tile_block_elems() {
+  return tile_tm<NB>() * 2 * NB * NB * TileCfg<NB>::KT;
+}
+template <int NB>
+__host__ __device__ constexpr int tile_stage_elems() {
+  return tile_block_elems<NB>() + NB * NB * TileCfg<NB>::KT;
+}
+template <int NB>
+__host__ __device__ constexpr int tile_red_elems() {
+  return kTileWarps * NB * 32;
+}
+template <int NB>
+constexpr size_t tile_smem_bytes() {
+  return sizeof(float2) * ((size_t)kTileStages * tile_stage_elems<NB>() + tile_red_elems<NB>());
+}
+static_assert(tile_smem_bytes<2>() <= 227 * 1024 && tile_smem_bytes<4>() <= 227 * 1024 &&
+                  tile_smem_bytes<8>() <= 227 * 1024,
+              "tile sweep shared memory");
+static_assert((tile_block_elems<4>() * sizeof(float2)) % 128 == 0 && (tile_stage_elems<4>() * sizeof(float2)) % 128 == 0,
+              "stage alignment");
+
+// acc + x * y, acc - x * y, acc + x * conj(y) on complex64 (FP32 FMAs)
+__device__ __forceinline__ float2 f_fma(float2 x, float2 y, float2 acc) {
+  return make_float2(fmaf(x.x, y.x, fmaf(-x.y, y.y, acc.x)), fmaf(x.x, y.y, fmaf(x.y, y.x, acc.y)));
+}
+__device__ __forceinline__ float2 f_fnma(float2 x, float2 y, float2 acc) {
+  return make_float2(fmaf(-x.x, y.x, fmaf(x.y, y.y, acc.x)), fmaf(-x.x, y.y, fmaf(-x.y, y.x, acc.y)));
+}
+__device__ __forceinline__ float2 f_fmac(float2 x, float2 y, float2 acc) {
+  return make_float2(fmaf(x.x, y.x, fmaf(x.y, y.y, acc.x)), fmaf(x.y, y.x, fmaf(-x.x, y.y, acc.y)));
+}
+
+// (strip, chunk) of work item p: strip s covers columns [s TM, (s+1) TM) and
+// rows [s TM, n], split into chunks of TI rows; false past the last item
+__device__ __forceinline__ bool tile_item(int p, int n, int TM, int TI, int *s_out, int *c_out) {
+  const int strips = (n + TM) / TM;
+  for (int s = 0; s < strips; ++s) {
+    const int cs = (n + 1 - s * TM + TI - 1) / TI;
+    if (p < cs) {
+      *s_out = s;
+      *c_out = p;
+      return true;
+    }
+    p -= cs;
+  }
+  return false;
+}
+
+// grid: x = k tiles of KT, y = (strip, chunk) work items. CP: column partials
+// [chunk][j][x][a][b][k], RP: row partials [strip][j][a][b][k] (complex64).
+template <int NB, int QUAD>
+__global__ void __launch_bounds__(kTileThreads, 1)
+    sweep_tile_kernel(const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmH,
+                      const float2 *__restrict__ Cf, float2 *__restrict__ CP, float2 *__restrict__ RP, int n,
+                      int nk, int TI, const int *__restrict__ skip, int *status) {
+  if (skip && *skip) return;
+  constexpr int KT = TileCfg<NB>::KT, TMW = TileCfg<NB>::TMW, TM = tile_tm<NB>(), NB2 = NB * NB;
+  constexpr int SE = tile_stage_elems<NB>(), BE = tile_block_elems<NB>();
+  constexpr unsigned kBytesH = (unsigned)BE * sizeof(float2), kBytesC = (unsigned)NB2 * KT * sizeof(float2);
+  extern __shared__ __align__(128) float4 tile_smem4[];
+  __shared__ __align__(8) uint64_t bar[kTileStages];
+  __shared__ int failed;
+  float2 *smem = reinterpret_cast<float2 *>(tile_smem4);
+  float2 *red = smem + (size_t)kTileStages * SE;
+
+  int s = 0, c = 0;
+  if (!tile_item(blockIdx.y, n, TM, TI, &s, &c)) return;
+  const int M0 = s * TM, R0 = M0 + c * TI, R1 = min(M0 + (c + 1) * TI, n + 1);
+  const int rows = R1 - R0;
+  const int k0 = blockIdx.x * KT;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kk = lane % KT, a = lane / KT;
+  const int k = k0 + kk;
+  const bool kvalid = k < nk;
+  const size_t blk = (size_t)NB2 * nk;
+
+  // C1(m), C2^<(m) of this lane's columns (row a, this k), kept for the chunk
+  float2 C1m[TMW][NB], C2m[TMW][NB];
+#pragma unroll
+  for (int q = 0; q < TMW; ++q) {
+    const int m = M0 + warp * TMW + q;
+#pragma unroll
+    for (int cc = 0; cc < NB; ++cc) {
+      const bool ok = m <= n && kvalid;
+      const size_t o = (size_t)(a * NB + cc) * nk + k;
+      C1m[q][cc] = ok ? Cf[(size_t)m * 3 * blk + o] : make_float2(0.f, 0.f);
+      C2m[q][cc] = ok ? Cf[((size_t)m * 3 + 1) * blk + o] : make_float2(0.f, 0.f);
+    }
+  }
+  float2 X[TMW][NB], Y[TMW][NB];   // column use: X(m)_{a,b}, Y(m)_{a,b}
+#pragma unroll
+  for (int q = 0; q < TMW; ++q)
+#pragma unroll
+    for (int b = 0; b < NB; ++b) X[q][b] = Y[q][b] = make_float2(0.f, 0.f);
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kTileStages; ++st) mbar_init(&bar[st], 1);
+    failed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int r) {   // row R0 + r into stage r % kTileStages (thread 0)
+    const int i = R0 + r, st = r % kTileStages;
+    float2 *dst = smem + (size_t)st * SE;
+    mbar_expect_tx(&bar[st], kBytesH + kBytesC);
+    tma_load_4d(dst, &tmH, 2 * k0, 0, 0, (int)tri(i, M0), &bar[st]);
+    tma_load_3d(dst + BE, &tmC, 2 * k0, 0, 3 * i, &bar[st]);
+  };
+  if (threadIdx.x == 0)
+    for (int r = 0; r < kTileStages - 1 && r < rows; ++r) issue(r);
+  int issued = min(kTileStages - 1, rows);
+
+  for (int r = 0; r < rows; ++r) {
+    if (threadIdx.x == 0 && issued < rows && issued == r + kTileStages - 1) issue(issued);
+    issued = min(r + kTileStages, rows);
+    const int st = r % kTileStages;
+    if (!mbar_wait(&bar[st], (unsigned)((r / kTileStages) & 1), kMbarWaitLimit)) failed = 1;
+    __syncthreads();
+    if (failed) {   // a copy did not arrive: flag it, let the in-flight ones land, stop
+      if (threadIdx.x == 0) {
+        int code = kDevTimeout;
+        for (int q = r; q < issued; ++q)
+          if (!mbar_wait(&bar[q % kTileStages], (unsigned)((q / kTileStages) & 1), kMbarWaitLimit))
+            code |= kDevTimeoutDrain;
+        if (status) atomicOr(status, code);
+      }
+      __syncthreads();
+      return;
+    }
+    const int i = R0 + r;
+    const float2 *stg = smem + (size_t)st * SE;
+    float2 C1i[NB];
+#pragma unroll
+    for (int cc = 0; cc < NB; ++cc) C1i[cc] = stg[BE + (a * NB + cc) * KT + kk];
+    float2 T[NB];   // row use, summed over this warp's columns: X(i)_{a,cc} = -T[cc]
+#pragma unroll
+    for (int cc = 0; cc < NB; ++cc) T[cc] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < TMW; ++q) {
+      const int m = M0 + warp * TMW + q;
+      if (m > i) continue;   // past the diagonal (warp-uniform)
+      const float2 *B = stg + (size_t)(warp * TMW + q) * 2 * NB2 * KT + kk;   // [x][r s][kk]
+      if (m < i) {
+        const float f = (float)quad_omega(QUAD, i, m);
+        float2 K2[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) K2[b] = f == 1.0f ? C2m[q][b] : make_float2(f * C2m[q][b].x, f * C2m[q][b].y);
+#pragma unroll
+        for (int cc = 0; cc < NB; ++cc)
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            const float2 x = B[(cc * NB + b) * KT], d = B[(NB2 + cc * NB + b) * KT];
+            X[q][b] = f_fma(C1i[cc], x, X[q][b]);
+            Y[q][b] = f_fnma(C1i[cc], d, Y[q][b]);
+            T[cc] = f_fmac(C1m[q][b], x, T[cc]);
+            T[cc] = f_fmac(K2[b], d, T[cc]);
+          }
+      } else if (i == 0) {   // the only node of column 0 on the diagonal: above the output
+#pragma unroll
+        for (int cc = 0; cc < NB; ++cc)
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            const float2 x = B[(cc * NB + b) * KT], d = B[(NB2 + cc * NB + b) * KT];
+            X[q][b] = f_fma(C1i[cc], x, X[q][b]);
+            Y[q][b] = f_fnma(C1i[cc], d, Y[q][b]);
+          }
+      } else {   // end node l = j of column j = i: weight f, Y coefficient f (C3 - C2^<) + (f - 1) C1
+        const float f = (float)quad_omega(QUAD, i, i);
+#pragma unroll
+        for (int cc = 0; cc < NB; ++cc) {
+          const float2 k3 = kvalid ? Cf[((size_t)i * 3 + 2) * blk + (size_t)(a * NB + cc) * nk + k]
+                                   : make_float2(0.f, 0.f);
+          const float2 k2 = C2m[q][cc], k1 = C1i[cc];
+          const float2 K2 = make_float2(f * k2.x, f * k2.y);
+          const float2 KY = make_float2(f * (k3.x - k2.x) + (f - 1.0f) * k1.x, f * (k3.y - k2.y) + (f - 1.0f) * k1.y);
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            const float2 x = B[(cc * NB + b) * KT], d = B[(NB2 + cc * NB + b) * KT];
+            X[q][b] = f_fma(k1, x, X[q][b]);
+            X[q][b] = f_fma(K2, d, X[q][b]);
+            Y[q][b] = f_fma(KY, d, Y[q][b]);
+          }
+        }
+      }
+    }
+    // the warps' row-use shares: red[w][cc][a][kk], summed by the first NB * 32 threads
+#pragma unroll
+    for (int cc = 0; cc < NB; ++cc) red[((warp * NB + cc) * NB + a) * KT + kk] = T[cc];
+    __syncthreads();
+    if (threadIdx.x < NB * 32) {
+      const int t = threadIdx.x;   // (a', cc', kk') with kk' fastest: coalesced writes
+      const int kk2 = t % KT, ac = t / KT, cc2 = ac % NB, a2 = ac / NB;
+      float2 sum = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int w = 0; w < kTileWarps; ++w) {
+        const float2 v = red[((w * NB + cc2) * NB + a2) * KT + kk2];
+        sum.x += v.x;
+        sum.y += v.y;
+      }
+      const int k2 = k0 + kk2;
+      if (k2 < nk)
+        RP[(((size_t)s * (n + 1) + i) * NB2 + a2 * NB + cc2) * nk + k2] = make_float2(-sum.x, -sum.y);
+    }
+    __syncthreads();   // the stage and the reduction buffer are free again
+  }
+  // column partials of this chunk
+#pragma unroll
+  for (int q = 0; q < TMW; ++q) {
+    const int m = M0 + warp * TMW + q;
+    if (m > n || !kvalid) continue;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const size_t o = (size_t)(a * NB + b) * nk + k;
+      CP[(((size_t)c * (n + 1) + m) * 2) * blk + o] = X[q][b];
+      CP[(((size_t)c * (n + 1) + m) * 2 + 1) * blk + o] = Y[q][b];
+    }
+  }
+}
+
+// I(j) from the partials, FP64: X = sum of the column partials of column j
+// (one per chunk of its strip) and of its row partials (one per strip left of
+// it); Y = the column partials' Y plus the row use's Y at nodes m < j whose
+// weight on [0, t_j] differs from the one on [0, t_n]: (f (C3 - C2^<) +
+// (f - 1) C1)(m) dG(m, j), dG(m, j) = -dB(j, m)^+ (Gregory end nodes; the
+// trapezoid has none: its only such node, l = 0, has f = w^(n)_0 / dt).
+template <int NB, int QUAD>
+__global__ void tile_reduce_kernel(const float2 *__restrict__ CP, const float2 *__restrict__ RP,
+                                   const float2 *__restrict__ Cf, const float2 *__restrict__ H,
+                                   double2 *__restrict__ I, int n, int nk, int TI, int TM,
+                                   const int *__restrict__ skip) {
+  if (skip && *skip) return;
+  constexpr int NB2 = NB * NB;
+  const size_t blk = (size_t)NB2 * nk, count = (size_t)(n + 1) * blk;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < count;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / blk);
+    const size_t r = idx - (size_t)j * blk;   // (a b) nk + k
+    const int ab = (int)(r / nk), k = (int)(r - (size_t)ab * nk);
+    const int a = ab / NB, b = ab - a * NB;
+    const int M0 = (j / TM) * TM;
+    const int chunks = (n + 1 - M0 + TI - 1) / TI, strips = j / TM + 1;
+    double xr = 0.0, xi = 0.0, yr = 0.0, yi = 0.0;
+    for (int c = 0; c < chunks; ++c) {
+      const float2 x = CP[(((size_t)c * (n + 1) + j) * 2) * blk + r];
+      const float2 y = CP[(((size_t)c * (n + 1) + j) * 2 + 1) * blk + r];
+      xr += x.x;
+      xi += x.y;
+      yr += y.x;
+      yi += y.y;
+    }
+    for (int s = 0; s < strips; ++s) {
+      const float2 x = RP[((size_t)s * (n + 1) + j) * blk + r];
+      xr += x.x;
+      xi += x.y;
+    }
+    if (QUAD != kQuadTrapezoid && j > 0 && n >= 1) {
+      const int ns = j >= 5 ? 5 : j;   // nodes 0, 1, 2, j-2, j-1 (every m < j for j <= 4)
+      for (int t = 0; t < ns; ++t) {
+        const int m = (j >= 5 && t >= 3) ? j - 5 + t : t;
+        const float f = (float)quad_omega(QUAD, j, m);
+        const float2 *dB = H + (tri(j, m) * 2 + 1) * blk + k;   // dG(j, m), [r s] rows of n_k
+        float2 acc = make_float2(0.f, 0.f);
+        for (int cc = 0; cc < NB; ++cc) {
+          const size_t o = (size_t)(a * NB + cc) * nk + k;
+          const float2 k1 = Cf[(size_t)m * 3 * blk + o], k2 = Cf[((size_t)m * 3 + 1) * blk + o],
+                       k3 = Cf[((size_t)m * 3 + 2) * blk + o];
+          const float2 KY = make_float2(f * (k3.x - k2.x) + (f - 1.0f) * k1.x, f * (k3.y - k2.y) + (f - 1.0f) * k1.y);
+          // dG(m, j)_{cc, b} = -conj(dB(j, m)_{b, cc})
+          acc = f_fmac(KY, dB[(size_t)(b * NB + cc) * nk], acc);
+        }
+        yr -= acc.x;
+        yi -= acc.y;
+      }
+    }
+    I[((size_t)j * 2) * blk + r] = make_double2(xr, xi);
+    I[((size_t)j * 2 + 1) * blk + r] = make_double2(xr + yr, xi + yi);
+  }
+}
+
+template <int NB>
+bool tile_maps(const void *Cf, const void *H, int n, int nk, CUtensorMap *tmC, CUtensorMap *tmH) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  constexpr int KT = TileCfg<NB>::KT, NB2 = NB * NB, TM = tile_tm<NB>();
+  const cuuint64_t row = (cuuint64_t)2 * nk * sizeof(float);   // one (a, c) row of k, bytes
+  {
+    const cuuint64_t dim[3] = {(cuuint64_t)2 * nk, (cuuint64_t)NB2, (cuuint64_t)3 * (n + 1)};
+    const cuuint64_t stride[2] = {row, row * NB2};
+    const cuuint32_t box[3] = {(cuuint32_t)(2 * KT), (cuuint32_t)NB2, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    if (enc(tmC, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(Cf), dim, stride, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  {
+    const cuuint64_t ntri = (cuuint64_t)tri(n, n) + 1;
+    const cuuint64_t dim[4] = {(cuuint64_t)2 * nk, (cuuint64_t)NB2, 2, ntri};
+    const cuuint64_t stride[3] = {row, row * NB2, row * NB2 * 2};
+    const cuuint32_t box[4] = {(cuuint32_t)(2 * KT), (cuuint32_t)NB2, 2, (cuuint32_t)TM};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    if (enc(tmH, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(H), dim, stride, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
+}
+
+// shared-memory limit of the tile kernels, raised once per device under a lock
+template <int NB>
+cudaError_t tile_prepare_nb() {
+  constexpr int kMaxDev = 64;
+  static std::mutex mu;
+  static bool done[kMaxDev] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+  tensor_map_encoder();
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return cudaSuccess;
+  const int bytes = (int)tile_smem_bytes<NB>();
+  e = cudaFuncSetAttribute(sweep_tile_kernel<NB, kQuadTrapezoid>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sweep_tile_kernel<NB, kQuadGregory>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done[dev] = true;
+  return e;
+}
+
+int tile_tm_of(int nb) { return nb == 2 ? tile_tm<2>() : nb == 4 ? tile_tm<4>() : tile_tm<8>(); }
+int tile_kt_of(int nb) { return nb == 2 ? TileCfg<2>::KT : nb == 4 ? TileCfg<4>::KT : TileCfg<8>::KT; }
+
+long tile_items(int n, int TM, int TI) {
+  long p = 0;
+  for (int s = 0; s * TM <= n; ++s) p += (n + 1 - s * TM + TI - 1) / TI;
+  return p;
+}
+
+template <int NB>
+cudaError_t tile_launch(const Mesh &m, int n, const void *H, const void *Cf, double2 *I, void *part,
+                        cudaStream_t st, const int *skip, int quad, int *status, int TI) {
+  cudaError_t e = tile_prepare_nb<NB>();
+  if (e != cudaSuccess) return e;
+  CUtensorMap tmC, tmH;
+  if (!tile_maps<NB>(Cf, H, n, m.nk, &tmC, &tmH)) return cudaErrorNotSupported;
+  constexpr int TM = tile_tm<NB>(), KT = TileCfg<NB>::KT;
+  const size_t blk = (size_t)NB * NB * m.nk;
+  float2 *CP = (float2 *)part;
+  float2 *RP = CP + (size_t)((n + TI) / TI) * (n + 1) * 2 * blk;
+  const dim3 grid((unsigned)((m.nk + KT - 1) / KT), (unsigned)tile_items(n, TM, TI));
+  const size_t smem = tile_smem_bytes<NB>();
+  if (quad == kQuadGregory)
+    sweep_tile_kernel<NB, kQuadGregory><<<grid, kTileThreads, smem, st>>>(tmC, tmH, (const float2 *)Cf, CP, RP, n,
+                                                                          m.nk, TI, skip, status);
+  else
+    sweep_tile_kernel<NB, kQuadTrapezoid><<<grid, kTileThreads, smem, st>>>(tmC, tmH, (const float2 *)Cf, CP, RP,
+                                                                            n, m.nk, TI, skip, status);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t count = (size_t)(n + 1) * blk;
+  size_t blocks = (count + 255) / 256;
+  const size_t cap = (size_t)device_sms() * 16;
+  if (blocks > cap) blocks = cap;
+  if (quad == kQuadGregory)
+    tile_reduce_kernel<NB, kQuadGregory><<<(unsigned)blocks, 256, 0, st>>>(CP, RP, (const float2 *)Cf,
+                                                                          (const float2 *)H, I, n, m.nk, TI, TM, skip);
+  else
+    tile_reduce_kernel<NB, kQuadTrapezoid><<<(unsigned)blocks, 256, 0, st>>>(CP, RP, (const float2 *)Cf,
+                                                                            (const float2 *)H, I, n, m.nk, TI, TM, skip);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tile_supported(const Mesh &m, int prec) {
+  return prec == KBE_PREC_C64 && (m.nb == 2 || m.nb == 4 || m.nb == 8) && m.nk % 2 == 0;
+}
+
+size_t tile_part_bytes(const Mesh &m, int n, int TI) {
+  if (!(m.nb == 2 || m.nb == 4 || m.nb == 8)) return 0;
+  const size_t blk = (size_t)m.nb * m.nb * m.nk;
+  const int TM = tile_tm_of(m.nb);
+  const size_t cp = (size_t)((n + TI) / TI) * (n + 1) * 2 * blk;
+  const size_t rp = (size_t)((n + TM) / TM) * (n + 1) * blk;
+  return (cp + rp) * sizeof(float2);
+}
+
+cudaError_t tile_prepare(int nb) {
+  switch (nb) {
+    case 2: return tile_prepare_nb<2>();
+    case 4: return tile_prepare_nb<4>();
+    case 8: return tile_prepare_nb<8>();
+    default: return cudaSuccess;
+  }
+}
+
+cudaError_t launch_sweep_tile(const Mesh &m, int n, const void *H, const void *Cf, double2 *I, void *part,
+                              cudaStream_t st, const int *skip, int quad, int *status, int TI) {
+  switch (m.nb) {
+    case 2: return tile_launch<2>(m, n, H, Cf, I, part, st, skip, quad, status, TI);
+    case 4: return tile_launch<4>(m, n, H, Cf, I, part, st, skip, quad, status, TI);
+    case 8: return tile_launch<8>(m, n, H, Cf, I, part, st, skip, quad, status, TI);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace kbe

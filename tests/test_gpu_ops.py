@@ -263,3 +263,57 @@ def test_collision_row_paper_shape(prec):
     gl, gg = from_dev_blocks(I.cpu().numpy())
     assert_close(gl, Il, prec)
     assert_close(gg, Ig, prec)
+
+
+@pytest.mark.parametrize("quad", [0, 1])
+@pytest.mark.parametrize("nb,L,n,TI", [(4, (8, 8), 70, 32), (4, (6, 5), 45, 64), (8, (4, 4), 40, 32),
+                                       (8, (2, 3), 35, 128), (2, (64, 1), 70, 32), (2, (30, 1), 33, 128),
+                                       (4, (2, 1), 0, 32), (4, (2, 1), 1, 32), (4, (2, 1), 6, 32)])
+def test_c64_tile_sweep_matches_oracle(nb, L, n, TI, quad):
+    """the single-read tile sweep (each stored block read once, both uses from
+    shared memory; kbe_set_sweep_choice forces it on every row): several column
+    strips and row chunks, k-tiles that run past n_k, the diagonal and end
+    nodes, both quadratures; against the oracle at the mixed form's bar, and
+    bitwise repeatable (the partial sums are added in a fixed order)"""
+    rng = np.random.default_rng(900 + nb * 7 + n)
+    nk = L[0] * L[1]
+    dt = 0.03
+    ntri = tri(n, n) + 1
+    Hl = ki.random_blocks(rng, (ntri, nk, nb, nb))
+    Hg = ki.random_blocks(rng, (ntri, nk, nb, nb))
+    Sl = ki.random_blocks(rng, (n + 1, nk, nb, nb))
+    Sg = ki.random_blocks(rng, (n + 1, nk, nb, nb))
+    Il, Ig = oracle.collision_row(nb, nk, n, dt, Hl, Hg, Sl, Sg, quadrature=quad)
+    p = kbe.KBE_PREC_C64
+    H64 = dev(to_dev_blocks(Hl, Hg))
+    H = torch.empty(H64.numel() * 2, dtype=torch.float32, device="cuda")
+    kbe.pack(p, H64, H, ntri, nb * nb * nk)
+    S = dev(to_dev_blocks(Sl, Sg))
+    work = torch.empty(kbe.collision_row_workspace(nb, L, n, p) // 4 + 1, dtype=torch.float32, device="cuda")
+    kbe.set_sweep_choice(nb, L, p, -TI, quadrature=quad)
+    try:
+        outs = []
+        for _ in range(2):
+            I = torch.full((n + 1, 2, nb, nb, nk), float("nan"), dtype=torch.complex128, device="cuda")
+            work.fill_(float("nan"))   # nothing may depend on stale scratch
+            kbe.collision_row(nb, L, n, dt, H, S, I, precision=p, work=work, quadrature=quad)
+            torch.cuda.synchronize()
+            outs.append(I.cpu().numpy())
+    finally:
+        kbe.set_sweep_choice(nb, L, p, 0, quadrature=quad)
+    assert np.array_equal(outs[0], outs[1])
+    gl, gg = from_dev_blocks(outs[0])
+    assert np.all(np.isfinite(gl)) and np.all(np.isfinite(gg))
+    assert_close(gl, Il, "c64")
+    assert_close(gg, Ig, "c64")
+
+
+def test_c64_tile_sweep_rejected_where_it_does_not_apply():
+    with pytest.raises(kbe.KBEError):
+        kbe.set_sweep_choice(3, (4, 4), kbe.KBE_PREC_C64, -32)      # N_b = 3
+    with pytest.raises(kbe.KBEError):
+        kbe.set_sweep_choice(4, (5, 3), kbe.KBE_PREC_C64, -32)      # odd n_k
+    with pytest.raises(kbe.KBEError):
+        kbe.set_sweep_choice(4, (4, 4), kbe.KBE_PREC_FP64, -32)     # FP64 history
+    with pytest.raises(kbe.KBEError):
+        kbe.set_sweep_choice(4, (4, 4), kbe.KBE_PREC_C64, -16)      # TI below 32

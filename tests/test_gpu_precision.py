@@ -115,3 +115,23 @@ def test_c64_density_and_energy_within_1e5(name, nsteps):
         escale = max(abs(sc_o[1]), abs(sc_o[5]))
         assert np.abs(sc[n][1:] - sc_o[1:]).max() <= 1e-5 * escale, (n, sc[n], sc_o)
         assert abs(sc[n][0] - sc_o[0]) <= 1e-5 * abs(sc_o[0])
+
+
+def test_c64_tile_sweep_trajectory_matches_oracle():
+    """c2's first 20 steps in the complex64 form with the single-read tile sweep
+    forced on every row: density and energies within 1e-5 of the oracle"""
+    s = ki.config("c2", nt=20)
+    kbe.set_sweep_choice(s.nb, s.L, kbe.KBE_PREC_C64, -32)
+    try:
+        g = kbe.KBE.from_system(s, precision=kbe.KBE_PREC_C64)
+        g.step(20)
+        nkb, sc = g.observables_all()
+        g.close()
+    finally:
+        kbe.set_sweep_choice(s.nb, s.L, kbe.KBE_PREC_C64, 0)
+    o = oracle.Oracle(s)
+    o.step(20)
+    nkb_o = np.array([o.observables(i)[0] for i in range(21)])
+    sc_o = np.array([o.observables(i)[1] for i in range(21)])
+    assert np.abs(nkb - nkb_o).max() <= 1e-5 * np.abs(nkb_o).max()
+    assert np.abs(sc[:, 1:] - sc_o[:, 1:]).max() <= 1e-5 * np.abs(sc_o[:, 5]).max()

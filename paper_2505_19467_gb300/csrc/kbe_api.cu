@@ -206,7 +206,9 @@ kbe_status evaluate_row(kbe_handle *h, int n, const int *skip = nullptr) {
   const Mesh &m = h->mesh;
   double2 *Hrow = frow(h, n);
   const double *Ul = h->Useq.size() == 1 ? nullptr : h->d_U;
-  cudaError_t e = kbe::sigma_row(m, h->v.data(), n, U_at(h, n), Ul, Hrow, h->Sig, h->work, h->stream, skip);
+  // the complex64 form holds Sigma in complex FP32 (its coefficient rows round it to complex64)
+  cudaError_t e = kbe::sigma_row(m, h->v.data(), n, U_at(h, n), Ul, Hrow, h->Sig, h->work, h->stream, skip,
+                                 h->cfg.precision == KBE_PREC_C64);
   if (e != cudaSuccess) return cuda_fail(h, e, "sigma_row");
   const bool timed = h->prof;
   if (timed) {
@@ -262,11 +264,13 @@ kbe_status update(kbe_handle *h, int n, double theta, const int *skip = nullptr,
                   unsigned long long *maxdiff = nullptr) {
   double2 *prev = frow(h, n - 1);
   double2 *row = frow(h, n);
+  // the update kernels also store row n into the history triangle ("publish")
+  char *hist = (char *)h->H + tri(n, 0) * 2 * h->blk * h->esz;
   cudaError_t e = kbe::launch_update_row(h->mesh, n, h->cfg.dt, theta, h->hk, h->U, h->V, prev, h->Ip,
-                                         h->Ic, row, h->stream, skip, maxdiff);
+                                         h->Ic, row, h->stream, skip, maxdiff, hist, h->cfg.precision);
   if (e != cudaSuccess) return cuda_fail(h, e, "update_row");
   if (h->prof) h->stats.launches += 2;
-  return publish(h, n, skip);
+  return KBE_OK;
 }
 
 kbe_status density(kbe_handle *h, int n, double2 *out, const int *skip = nullptr) {

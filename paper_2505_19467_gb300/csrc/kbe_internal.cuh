@@ -140,6 +140,50 @@ struct GraphCache {
 // cached; grids are sized in multiples of it)
 int device_sms();
 
+// ---- float2 complex helpers (the complex64 form's FP32 arithmetic) --------
+__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 c_scale(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+__device__ __forceinline__ float2 c_conj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 c_mulc(float2 a, float2 b) {
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ float2 c_fma(float2 a, float2 b, float2 acc) {
+  return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y)));
+}
+// conversions between the two complex types
+template <class C>
+__device__ __forceinline__ C c_from(double2 z);
+template <>
+__device__ __forceinline__ double2 c_from<double2>(double2 z) { return z; }
+template <>
+__device__ __forceinline__ float2 c_from<float2>(double2 z) { return make_float2((float)z.x, (float)z.y); }
+__device__ __forceinline__ double2 c_widen(double2 z) { return z; }
+__device__ __forceinline__ double2 c_widen(float2 z) { return make_double2(z.x, z.y); }
+
+// ---- history storage of one (G^<, dG) pair (see kbe_op_pack) --------------
+// dG = G^< - G^> is formed in FP64 by the caller; o0 / o1 index the stored
+// complex numbers of component 0 and 1
+__device__ __forceinline__ float4 split_df(double2 x) {
+  const float rh = __double2float_rn(x.x), ih = __double2float_rn(x.y);
+  return make_float4(rh, __double2float_rn(x.x - (double)rh), ih, __double2float_rn(x.y - (double)ih));
+}
+__device__ __forceinline__ void pack_store(int prec, void *dst, size_t o0, size_t o1, double2 gl, double2 dg) {
+  if (prec == KBE_PREC_DF64) {
+    ((float4 *)dst)[o0] = split_df(gl);
+    ((float4 *)dst)[o1] = split_df(dg);
+  } else if (prec == KBE_PREC_C64) {
+    ((float2 *)dst)[o0] = make_float2((float)gl.x, (float)gl.y);
+    ((float2 *)dst)[o1] = make_float2((float)dg.x, (float)dg.y);
+  } else {
+    ((double2 *)dst)[o0] = gl;
+    ((double2 *)dst)[o1] = dg;
+  }
+}
+
 // ---- status word written by kernels (sticky, read by the host) -----------
 // kDevTimeoutDrain: after a timeout, the wait for a CTA's own copies in
 // flight also ran out, so a copy may still land in shared memory that a later
@@ -168,9 +212,11 @@ cudaError_t launch_sigma_products(const Mesh &m, const double *v, int n, double 
                                   const double *Ul_dev, const double2 *GR, double2 *SR,
                                   cudaStream_t st, const int *skip = nullptr);
 size_t sigma_workspace_bytes(const Mesh &m, int n);
+// fp32: the transforms and products in complex FP32 (the complex64 history
+// form, whose coefficient rows round Sigma to complex64 anyway); Sig is FP64
 cudaError_t sigma_row(const Mesh &m, const double *v_host, int n, double Un, const double *Ul_dev,
                       const double2 *Grow, double2 *Sig, double2 *work, cudaStream_t st,
-                      const int *skip = nullptr);
+                      const int *skip = nullptr, bool fp32 = false);
 
 // a2 collision row. H is the history triangle in the precision's storage
 // (double2 / float4 hi-lo pairs / float2), each block holding G^< and
@@ -242,11 +288,13 @@ cudaError_t launch_build_props(const Mesh &m, const HopTable &hop, const PropPar
 // a4 update: rows j < n and the time diagonal (h, U, V of the step).
 // maxdiff (may be NULL): max over the new row of |G^< - its previous value in
 // out| is folded in (atomicMax on the bits of a non-negative double).
+// packed (may be NULL): the history's row n in the storage of precision prec,
+// written with the row ((G^<, dG) per block, as kbe_op_pack would).
 cudaError_t launch_update_row(const Mesh &m, int n, double dt, double theta, const double2 *h,
                               const double2 *U, const double2 *V, const double2 *Gprev,
                               const double2 *Iprev, const double2 *Icur, double2 *out,
                               cudaStream_t st, const int *skip = nullptr,
-                              unsigned long long *maxdiff = nullptr);
+                              unsigned long long *maxdiff = nullptr, void *packed = nullptr, int prec = 0);
 // Algorithm 1's convergence test after a corrector pass (one thread): unless
 // skip is set, count the pass in *iters, set skip when *maxdiff <= tol, and
 // clear *maxdiff for the next pass.

@@ -186,7 +186,8 @@ __global__ void __launch_bounds__(256) update_diag_kernel(int n, int nk, double 
                                                           const double2 *__restrict__ Ic,
                                                           double2 *__restrict__ out, int kpc,
                                                           const int *__restrict__ skip,
-                                                          unsigned long long *maxdiff) {
+                                                          unsigned long long *maxdiff, void *__restrict__ packed,
+                                                          int prec) {
   if (skip && *skip) return;
   using G = MatGroup<NB>;
   const int span = kpc * G::E;
@@ -253,8 +254,13 @@ __global__ void __launch_bounds__(256) update_diag_kernel(int n, int nk, double 
       const double2 d = c_sub(gg, ol[0]);
       atomicMax(maxdiff, (unsigned long long)__double_as_longlong(sqrt(d.x * d.x + d.y * d.y)));
     }
+    const double2 gG = (g.a == g.b) ? make_double2(gg.x, gg.y - 1.0) : gg;
     ol[0] = gg;
-    ol[blk] = (g.a == g.b) ? make_double2(gg.x, gg.y - 1.0) : gg;
+    ol[blk] = gG;
+    if (packed) {
+      const size_t o0 = (size_t)n * 2 * blk + (size_t)g.e * nk + k;
+      pack_store(prec, packed, o0, o0 + blk, gg, c_sub(gg, gG));
+    }
   }
 }
 
@@ -314,16 +320,18 @@ __global__ void local_density_kernel(int nb, int nk, const double2 *__restrict__
   }
 }
 
-// rows j < n: G^x(n,j) = U G^x(n-1,j) + V [(1-theta) Ip^x(j) + theta Ic^x(j)]
+// rows j < n: G^x(n,j) = U G^x(n-1,j) + V [(1-theta) Ip^x(j) + theta Ic^x(j)];
+// one thread per (j, a, b, k) forms both components, so that it can also store
+// the history's (G^<, dG) pair of the element (packed != NULL)
 template <int NB>
 __global__ void update_rows_kernel(int n, int nk, double theta, const double2 *__restrict__ U,
                                    const double2 *__restrict__ V, const double2 *__restrict__ Gprev,
                                    const double2 *__restrict__ Ip, const double2 *__restrict__ Ic,
                                    double2 *__restrict__ out, const int *__restrict__ skip,
-                                   unsigned long long *maxdiff) {
+                                   unsigned long long *maxdiff, void *__restrict__ packed, int prec) {
   if (skip && *skip) return;
   const size_t blk = (size_t)NB * NB * nk;
-  const size_t total = (size_t)n * 2 * blk;
+  const size_t total = (size_t)n * blk;
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   double dmax = 0.0;
   if (idx < total) {
@@ -332,24 +340,32 @@ __global__ void update_rows_kernel(int n, int nk, double theta, const double2 *_
     const int b = (int)(t % NB);
     t /= NB;
     const int a = (int)(t % NB);
-    t /= NB;   // t = j * 2 + x
-    const size_t base = t * blk;
-    double2 acc = make_double2(0, 0);
+    const size_t j = t / NB;
+    const size_t base = j * 2 * blk;
+    double2 acc0 = make_double2(0, 0), acc1 = make_double2(0, 0);
 #pragma unroll
     for (int c = 0; c < NB; ++c) {
       const size_t oc = (size_t)(c * NB + b) * nk + k;
       const size_t ou = (size_t)(a * NB + c) * nk + k;
-      double2 ib = c_scale(1.0 - theta, Ip[base + oc]);
-      if (theta != 0.0) ib = c_fma(make_double2(theta, 0.0), Ic[base + oc], ib);
-      acc = c_fma(U[ou], Gprev[base + oc], acc);
-      acc = c_fma(V[ou], ib, acc);
+      const double2 u = U[ou], v = V[ou];
+      double2 ib0 = c_scale(1.0 - theta, Ip[base + oc]), ib1 = c_scale(1.0 - theta, Ip[base + blk + oc]);
+      if (theta != 0.0) {
+        ib0 = c_fma(make_double2(theta, 0.0), Ic[base + oc], ib0);
+        ib1 = c_fma(make_double2(theta, 0.0), Ic[base + blk + oc], ib1);
+      }
+      acc0 = c_fma(u, Gprev[base + oc], acc0);
+      acc0 = c_fma(v, ib0, acc0);
+      acc1 = c_fma(u, Gprev[base + blk + oc], acc1);
+      acc1 = c_fma(v, ib1, acc1);
     }
-    double2 *o = out + base + (size_t)(a * NB + b) * nk + k;
-    if (maxdiff && (t & 1) == 0) {   // G^< entries
-      const double2 d = c_sub(acc, *o);
+    const size_t oo = base + (size_t)(a * NB + b) * nk + k;
+    if (maxdiff) {   // G^< entries
+      const double2 d = c_sub(acc0, out[oo]);
       dmax = sqrt(d.x * d.x + d.y * d.y);
     }
-    *o = acc;
+    out[oo] = acc0;
+    out[oo + blk] = acc1;
+    if (packed) pack_store(prec, packed, oo, oo + blk, acc0, c_sub(acc0, acc1));
   }
   if (maxdiff) {   // every lane reaches here (blockDim is a multiple of 32)
 #pragma unroll
@@ -458,20 +474,23 @@ cudaError_t launch_build_props(const Mesh &m, const HopTable &hop, const PropPar
 cudaError_t launch_update_row(const Mesh &m, int n, double dt, double theta, const double2 *h,
                               const double2 *U, const double2 *V, const double2 *Gprev,
                               const double2 *Iprev, const double2 *Icur, double2 *out,
-                              cudaStream_t st, const int *skip, unsigned long long *maxdiff) {
+                              cudaStream_t st, const int *skip, unsigned long long *maxdiff, void *packed,
+                              int prec) {
   const size_t blk = (size_t)m.nb * m.nb * m.nk;
-  const size_t total = (size_t)n * 2 * blk;
+  const size_t total = (size_t)n * blk;
   const int threads = 256;
   const unsigned blocks = (unsigned)((total + threads - 1) / threads);
   const double2 *ic = (theta != 0.0) ? Icur : Iprev;
-  KBE_NB_SWITCH(m.nb, (update_rows_kernel<NB><<<blocks, threads, 0, st>>>(n, m.nk, theta, U, V, Gprev, Iprev, ic, out,
-                                                                           skip, maxdiff)));
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (total > 0) {
+    KBE_NB_SWITCH(m.nb, (update_rows_kernel<NB><<<blocks, threads, 0, st>>>(n, m.nk, theta, U, V, Gprev, Iprev, ic,
+                                                                             out, skip, maxdiff, packed, prec)));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   KBE_NB_SWITCH(m.nb, (update_diag_kernel<NB><<<matgroup_blocks<NB>(m.nk), matgroup_threads<NB>(m.nk),
                                                  matgroup_smem<NB>(m.nk, 5), st>>>(
                           n, m.nk, dt, theta, h, Gprev, Iprev, ic, out, matgroup_kpc<NB>(m.nk), skip,
-                          maxdiff)));
+                          maxdiff, packed, prec)));
   return cudaGetLastError();
 }
 

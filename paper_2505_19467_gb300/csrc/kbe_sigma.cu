@@ -27,17 +27,26 @@ namespace {
 // Separable 2-D DFT of length-n_k arrays (mesh L0 x L1, k = k0 * L1 + k1):
 //   out[R] (+)= scale * sum_k exp(sign * i * 2 pi (k0 R0 / L0 + k1 R1 / L1)) in[k]
 // (added to out when accumulating).
-// One array at a time per CTA (grid-stride over arrays), in shared memory.
-// An axis whose length is a power of two is transformed in place by a
-// radix-2 FFT (bit reversal, then log2 L butterfly stages; O(L log L));
-// other lengths use the direct sum over that axis (O(L^2)). The twiddle
-// tables e^{sign 2 pi i m / L} are built once per CTA.
+// A CTA transforms P arrays at a time (P n_k <= 512 points; grid-stride over
+// the groups of arrays) in shared memory, so that each barrier of the
+// transform covers P arrays' work. An axis whose length is a power of two is
+// transformed in place by a radix-2 FFT (bit reversal, then log2 L butterfly
+// stages; O(L log L)); other lengths use the direct sum over that axis
+// (O(L^2)). The twiddle tables e^{sign 2 pi i m / L} are built once per CTA.
+// C is the arithmetic type (double2, or float2 for the complex64 form).
 
 __device__ __forceinline__ bool is_pow2(int L) { return L > 0 && (L & (L - 1)) == 0; }
 
-// in-place FFT of `count` sequences of length L, element i of sequence q at
-// x[q * qstride + i * stride]; tw[m] = e^{sign 2 pi i m / L}
-__device__ void fft_axis(double2 *x, int L, int stride, int count, int qstride, const double2 *tw) {
+// sequence q of an axis pass: groups of gsize sequences (one group per array,
+// gstride apart), qstride apart within a group; element i at + i * stride
+__device__ __forceinline__ int seq_base(int q, int gsize, int qstride, int gstride) {
+  const int g = q / gsize;
+  return g * gstride + (q - g * gsize) * qstride;
+}
+
+// in-place FFT of `count` sequences of length L; tw[m] = e^{sign 2 pi i m / L}
+template <class C>
+__device__ void fft_axis(C *x, int L, int stride, int count, int gsize, int qstride, int gstride, const C *tw) {
   int logL = 0;
   while ((1 << logL) < L) ++logL;
   const int total = count * L;
@@ -45,8 +54,8 @@ __device__ void fft_axis(double2 *x, int L, int stride, int count, int qstride, 
     const int q = e / L, i = e - q * L;
     const int r = __brev(i) >> (32 - logL);
     if (logL > 0 && i < r) {
-      double2 *p = x + q * qstride;
-      const double2 t = p[i * stride];
+      C *p = x + seq_base(q, gsize, qstride, gstride);
+      const C t = p[i * stride];
       p[i * stride] = p[r * stride];
       p[r * stride] = t;
     }
@@ -57,10 +66,10 @@ __device__ void fft_axis(double2 *x, int L, int stride, int count, int qstride, 
     for (int e = threadIdx.x; e < nbf; e += blockDim.x) {
       const int q = e / (L >> 1), bq = e - q * (L >> 1);
       const int grp = bq / half, pos = bq - grp * half;
-      double2 *p = x + q * qstride;
+      C *p = x + seq_base(q, gsize, qstride, gstride);
       const int i = grp * len + pos, j = i + half;
-      const double2 u = p[i * stride];
-      const double2 t = c_mul(tw[pos * step], p[j * stride]);
+      const C u = p[i * stride];
+      const C t = c_mul(tw[pos * step], p[j * stride]);
       p[i * stride] = c_add(u, t);
       p[j * stride] = c_sub(u, t);
     }
@@ -69,13 +78,14 @@ __device__ void fft_axis(double2 *x, int L, int stride, int count, int qstride, 
 }
 
 // direct transform of `count` sequences of length L (x -> tmp -> x)
-__device__ void dft_axis(double2 *x, double2 *tmp, int L, int stride, int count, int qstride,
-                         const double2 *tw) {
+template <class C>
+__device__ void dft_axis(C *x, C *tmp, int L, int stride, int count, int gsize, int qstride, int gstride,
+                         const C *tw) {
   const int total = count * L;
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     const int q = e / L, R = e - q * L;
-    const double2 *p = x + q * qstride;
-    double2 acc = make_double2(0.0, 0.0);
+    const C *p = x + seq_base(q, gsize, qstride, gstride);
+    C acc = c_scale(0, tw[0]);
     int ph = 0;
     for (int kk = 0; kk < L; ++kk) {
       acc = c_fma(tw[ph], p[kk * stride], acc);
@@ -87,49 +97,70 @@ __device__ void dft_axis(double2 *x, double2 *tmp, int L, int stride, int count,
   __syncthreads();
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     const int q = e / L, R = e - q * L;
-    x[q * qstride + R * stride] = tmp[e];
+    x[seq_base(q, gsize, qstride, gstride) + R * stride] = tmp[e];
   }
   __syncthreads();
 }
 
-__global__ void dft_rows_kernel(const double2 *__restrict__ in, double2 *__restrict__ out,
-                                long narr, int L0, int L1, int sign, double scale, int accumulate,
-                                const int *__restrict__ skip) {
+__device__ __forceinline__ void store_as(double2 *p, double2 v) { *p = v; }
+__device__ __forceinline__ void store_as(double2 *p, float2 v) { *p = make_double2(v.x, v.y); }
+__device__ __forceinline__ void store_as(float2 *p, float2 v) { *p = v; }
+__device__ __forceinline__ void add_as(double2 *p, double2 v) { *p = c_add(*p, v); }
+__device__ __forceinline__ void add_as(double2 *p, float2 v) { *p = c_add(*p, make_double2(v.x, v.y)); }
+__device__ __forceinline__ void add_as(float2 *p, float2 v) { *p = c_add(*p, v); }
+__device__ __forceinline__ double2 load_as_d(double2 v) { return v; }
+__device__ __forceinline__ double2 load_as_d(float2 v) { return make_double2(v.x, v.y); }
+
+// P arrays per CTA iteration (a power of two when n_k is one)
+__host__ __device__ __forceinline__ int dft_group(int nk) {
+  int P = 1;
+  while (2 * P * nk <= 512) P *= 2;
+  return P;
+}
+
+template <class C, class Tin, class Tout>
+__global__ void dft_rows_kernel(const Tin *__restrict__ in, Tout *__restrict__ out, long narr, int L0, int L1,
+                                int sign, double scale, int accumulate, const int *__restrict__ skip) {
   if (skip && *skip) return;
-  extern __shared__ double2 sm[];
-  const int nk = L0 * L1;
-  double2 *x = sm;
-  double2 *t = x + nk;
-  double2 *tw0 = t + nk;
-  double2 *tw1 = tw0 + L0;
+  extern __shared__ double2 sm_d2[];
+  C *sm = reinterpret_cast<C *>(sm_d2);
+  const int nk = L0 * L1, P = dft_group(nk);
+  C *x = sm;
+  C *t = x + P * nk;
+  C *tw0 = t + P * nk;
+  C *tw1 = tw0 + L0;
   for (int i = threadIdx.x; i < L0; i += blockDim.x) {
     double s, c;
     sincospi(2.0 * i / L0, &s, &c);
-    tw0[i] = make_double2(c, sign * s);
+    tw0[i] = c_from<C>(make_double2(c, sign * s));
   }
   for (int i = threadIdx.x; i < L1; i += blockDim.x) {
     double s, c;
     sincospi(2.0 * i / L1, &s, &c);
-    tw1[i] = make_double2(c, sign * s);
+    tw1[i] = c_from<C>(make_double2(c, sign * s));
   }
-  for (long arr = blockIdx.x; arr < narr; arr += gridDim.x) {
-    const double2 *src = in + arr * nk;
+  const long ngroups = (narr + P - 1) / P;
+  for (long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+    const long arr0 = grp * P;
+    const int pa = (int)(narr - arr0 < P ? narr - arr0 : P);   // arrays in this group
+    const Tin *src = in + arr0 * nk;
     __syncthreads();
-    for (int e = threadIdx.x; e < nk; e += blockDim.x) x[e] = src[e];
+    for (int e = threadIdx.x; e < pa * nk; e += blockDim.x) x[e] = c_from<C>(load_as_d(src[e]));
     __syncthreads();
-    if (L1 > 1) {   // axis 1: L0 contiguous sequences of length L1
-      if (is_pow2(L1)) fft_axis(x, L1, 1, L0, L1, tw1);
-      else dft_axis(x, t, L1, 1, L0, L1, tw1);
+    if (L1 > 1) {   // axis 1: L0 contiguous sequences of length L1 per array
+      if (is_pow2(L1)) fft_axis<C>(x, L1, 1, pa * L0, L0, L1, nk, tw1);
+      else dft_axis<C>(x, t, L1, 1, pa * L0, L0, L1, nk, tw1);
     }
-    if (L0 > 1) {   // axis 0: L1 sequences of length L0, stride L1
-      if (is_pow2(L0)) fft_axis(x, L0, L1, L1, 1, tw0);
-      else dft_axis(x, t, L0, L1, L1, 1, tw0);
+    if (L0 > 1) {   // axis 0: L1 sequences of length L0, stride L1, per array
+      if (is_pow2(L0)) fft_axis<C>(x, L0, L1, pa * L1, L1, 1, nk, tw0);
+      else dft_axis<C>(x, t, L0, L1, pa * L1, L1, 1, nk, tw0);
     }
-    double2 *dst = out + arr * nk;
+    Tout *dst = out + arr0 * nk;
+    const C sc = c_from<C>(make_double2(scale, 0.0));
     if (accumulate)
-      for (int e = threadIdx.x; e < nk; e += blockDim.x) dst[e] = c_add(dst[e], c_scale(scale, x[e]));
+      for (int e = threadIdx.x; e < pa * nk; e += blockDim.x) add_as(dst + e, c_mul(sc, x[e]));
     else
-      for (int e = threadIdx.x; e < nk; e += blockDim.x) dst[e] = c_scale(scale, x[e]);
+      for (int e = threadIdx.x; e < pa * nk; e += blockDim.x) store_as(dst + e, c_mul(sc, x[e]));
   }
 }
 
@@ -137,43 +168,54 @@ struct VMat {
   double v[kMaxNb * kMaxNb];
 };
 
+template <class C>
+struct RealOf;
+template <>
+struct RealOf<double2> {
+  using T = double;
+};
+template <>
+struct RealOf<float2> {
+  using T = float;
+};
+
 // Real-space second-Born products for one (l, j, R): all m, both components.
-template <int NB>
-__global__ void __launch_bounds__(128) sigma_products_kernel(const double2 *__restrict__ GR,
-                                                             double2 *__restrict__ SR, int n, int nk,
-                                                             double Un, const double *__restrict__ Ul,
+template <class C, int NB>
+__global__ void __launch_bounds__(128) sigma_products_kernel(const C *__restrict__ GR, C *__restrict__ SR, int n,
+                                                             int nk, double Un, const double *__restrict__ Ul,
                                                              VMat vm, const int *__restrict__ skip) {
+  using R = typename RealOf<C>::T;
   if (skip && *skip) return;
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long total = (long)(n + 1) * NB * nk;
   if (idx >= total) return;
-  const int R = (int)(idx % nk);
+  const int Rp = (int)(idx % nk);
   const long t = idx / nk;
   const int j = (int)(t % NB);
   const int l = (int)(t / NB);
   const size_t blk = (size_t)NB * NB * nk;
-  const double2 *gl = GR + (size_t)l * 2 * blk + R;
-  const double2 *gg = gl + blk;
-  const double fac = -Un * (Ul ? Ul[l] : Un);
-  double2 *sl = SR + (size_t)l * 2 * blk + (size_t)j * NB * nk + R;
-  double2 *sg = sl + blk;
+  const C *gl = GR + (size_t)l * 2 * blk + Rp;
+  const C *gg = gl + blk;
+  const R fac = (R)(-Un * (Ul ? Ul[l] : Un));
+  const C zero = c_from<C>(make_double2(0.0, 0.0));
+  C *sl = SR + (size_t)l * 2 * blk + (size_t)j * NB * nk + Rp;
+  C *sg = sl + blk;
 #pragma unroll 1
   for (int m = 0; m < NB; ++m) {
-    double2 QL = make_double2(0, 0), QG = make_double2(0, 0);
-    double2 EL = make_double2(0, 0), EG = make_double2(0, 0);
+    C QL = zero, QG = zero, EL = zero, EG = zero;
 #pragma unroll 1
     for (int a = 0; a < NB; ++a) {
-      const double vja = vm.v[j * NB + a];
-      if (vja == 0.0) continue;
-      double2 zl = make_double2(0, 0), yl = make_double2(0, 0), yg = make_double2(0, 0);
+      const R vja = (R)vm.v[j * NB + a];
+      if (vja == (R)0) continue;
+      C zl = zero, yl = zero, yg = zero;
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
-        const double vmb = vm.v[m * NB + b];
-        if (vmb == 0.0) continue;
-        const double2 gl_ab = gl[(size_t)(a * NB + b) * nk];
-        const double2 gg_ab = gg[(size_t)(a * NB + b) * nk];
-        const double2 gl_jb = gl[(size_t)(j * NB + b) * nk];
-        const double2 gg_jb = gg[(size_t)(j * NB + b) * nk];
+        const R vmb = (R)vm.v[m * NB + b];
+        if (vmb == (R)0) continue;
+        const C gl_ab = gl[(size_t)(a * NB + b) * nk];
+        const C gg_ab = gg[(size_t)(a * NB + b) * nk];
+        const C gl_jb = gl[(size_t)(j * NB + b) * nk];
+        const C gg_jb = gg[(size_t)(j * NB + b) * nk];
         zl = c_add(zl, c_scale(vmb, c_mulc(gl_ab, gg_ab)));   // M_ab = G^<_ab conj(G^>_ab)
         yl = c_add(yl, c_scale(vmb, c_mulc(gl_jb, gg_ab)));   // G^<_jb conj(G^>_ab)
         yg = c_add(yg, c_scale(vmb, c_mulc(gg_jb, gl_ab)));   // G^>_jb conj(G^<_ab)
@@ -183,8 +225,8 @@ __global__ void __launch_bounds__(128) sigma_products_kernel(const double2 *__re
       EL = c_fma(c_scale(vja, gl[(size_t)(a * NB + m) * nk]), yl, EL);
       EG = c_fma(c_scale(vja, gg[(size_t)(a * NB + m) * nk]), yg, EG);
     }
-    const double2 gl_jm = gl[(size_t)(j * NB + m) * nk];
-    const double2 gg_jm = gg[(size_t)(j * NB + m) * nk];
+    const C gl_jm = gl[(size_t)(j * NB + m) * nk];
+    const C gg_jm = gg[(size_t)(j * NB + m) * nk];
     sl[(size_t)m * nk] = c_scale(fac, c_sub(c_mul(gl_jm, QL), EL));
     sg[(size_t)m * nk] = c_scale(fac, c_sub(c_mul(gg_jm, QG), EG));
   }
@@ -199,32 +241,34 @@ __global__ void __launch_bounds__(128) sigma_products_kernel(const double2 *__re
 //   Sigma^<(R) = fac [tr(T) G^< - T G^<],   Sigma^> = fac [tr(T)* G^> - T^+ G^>]
 // (T^+ = G^> G^<^+): two N_b x N_b products per (l, R) instead of the O(N_b^4)
 // double sums. One thread per (l, j, R) forms row j of both.
-template <int NB>
-__global__ void __launch_bounds__(128) sigma_products_pair_kernel(const double2 *__restrict__ GR,
-                                                                  double2 *__restrict__ SR, int n, int nk,
-                                                                  double Un, const double *__restrict__ Ul,
+template <class C, int NB>
+__global__ void __launch_bounds__(128) sigma_products_pair_kernel(const C *__restrict__ GR, C *__restrict__ SR,
+                                                                  int n, int nk, double Un,
+                                                                  const double *__restrict__ Ul,
                                                                   const int *__restrict__ skip) {
+  using R = typename RealOf<C>::T;
   if (skip && *skip) return;
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long total = (long)(n + 1) * NB * nk;
   if (idx >= total) return;
-  const int R = (int)(idx % nk);
+  const int Rp = (int)(idx % nk);
   const long t = idx / nk;
   const int j = (int)(t % NB);
   const int l = (int)(t / NB);
   const size_t blk = (size_t)NB * NB * nk;
-  const double2 *gl = GR + (size_t)l * 2 * blk + R;
-  const double2 *gg = gl + blk;
-  const double fac = -Un * (Ul ? Ul[l] : Un);
+  const C *gl = GR + (size_t)l * 2 * blk + Rp;
+  const C *gg = gl + blk;
+  const R fac = (R)(-Un * (Ul ? Ul[l] : Un));
+  const C zero = c_from<C>(make_double2(0.0, 0.0));
 #define AT(M, r, c) M[(size_t)((r) * NB + (c)) * nk]
-  double2 tr = make_double2(0, 0);   // tr(G^< G^>^+) = sum_ab G^<_ab conj(G^>_ab)
-  double2 Tl[NB], Tg[NB];            // row j of T = G^< G^>^+ and of T^+ = G^> G^<^+
+  C tr = zero;        // tr(G^< G^>^+) = sum_ab G^<_ab conj(G^>_ab)
+  C Tl[NB], Tg[NB];   // row j of T = G^< G^>^+ and of T^+ = G^> G^<^+
 #pragma unroll
   for (int a = 0; a < NB; ++a) {
-    double2 sl = make_double2(0, 0), sg = make_double2(0, 0);
+    C sl = zero, sg = zero;
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-      const double2 xab = AT(gl, a, b), yab = AT(gg, a, b);
+      const C xab = AT(gl, a, b), yab = AT(gg, a, b);
       tr = c_add(tr, c_mulc(xab, yab));
       sl = c_add(sl, c_mulc(AT(gl, j, b), yab));
       sg = c_add(sg, c_mulc(AT(gg, j, b), xab));
@@ -232,11 +276,11 @@ __global__ void __launch_bounds__(128) sigma_products_pair_kernel(const double2 
     Tl[a] = sl;
     Tg[a] = sg;
   }
-  double2 *sl = SR + (size_t)l * 2 * blk + (size_t)j * NB * nk + R;
-  double2 *sg = sl + blk;
+  C *sl = SR + (size_t)l * 2 * blk + (size_t)j * NB * nk + Rp;
+  C *sg = sl + blk;
 #pragma unroll 1
   for (int m = 0; m < NB; ++m) {
-    double2 pl = make_double2(0, 0), pg = make_double2(0, 0);
+    C pl = zero, pg = zero;
 #pragma unroll
     for (int a = 0; a < NB; ++a) {
       pl = c_fma(Tl[a], AT(gl, a, m), pl);
@@ -248,41 +292,52 @@ __global__ void __launch_bounds__(128) sigma_products_pair_kernel(const double2 
 #undef AT
 }
 
-template <int NB>
-cudaError_t products_nb(const Mesh &m, const VMat &vm, int n, double Un, const double *Ul,
-                        const double2 *GR, double2 *SR, cudaStream_t st, const int *skip) {
+template <class C, int NB>
+cudaError_t products_nb(const Mesh &m, const VMat &vm, int n, double Un, const double *Ul, const C *GR, C *SR,
+                        cudaStream_t st, const int *skip) {
   bool pair = NB >= 3;   // v = 1 - delta exactly (at N_b <= 2 the two forms time the same)
   for (int a = 0; a < NB; ++a)
     for (int b = 0; b < NB; ++b) pair = pair && vm.v[a * NB + b] == (a == b ? 0.0 : 1.0);
-  if (pair) {
-    const long total = (long)(n + 1) * NB * m.nk;
-    sigma_products_pair_kernel<NB><<<(unsigned)((total + 127) / 128), 128, 0, st>>>(GR, SR, n, m.nk, Un, Ul, skip);
-    return cudaGetLastError();
-  }
   const long total = (long)(n + 1) * NB * m.nk;
-  const int threads = 128;
-  const long blocks = (total + threads - 1) / threads;
-  sigma_products_kernel<NB><<<(unsigned)blocks, threads, 0, st>>>(GR, SR, n, m.nk, Un, Ul, vm, skip);
+  const unsigned blocks = (unsigned)((total + 127) / 128);
+  if (pair)
+    sigma_products_pair_kernel<C, NB><<<blocks, 128, 0, st>>>(GR, SR, n, m.nk, Un, Ul, skip);
+  else
+    sigma_products_kernel<C, NB><<<blocks, 128, 0, st>>>(GR, SR, n, m.nk, Un, Ul, vm, skip);
   return cudaGetLastError();
 }
 
-}  // namespace
-
-namespace {
-size_t dft_smem_bytes(int L0, int L1) {
-  return sizeof(double2) * (2 * (size_t)L0 * L1 + L0 + L1);
+template <class C>
+cudaError_t products_any(const Mesh &m, const double *v, int n, double Un, const double *Ul_dev, const C *GR, C *SR,
+                         cudaStream_t st, const int *skip) {
+  VMat vm;
+  for (int i = 0; i < kMaxNb * kMaxNb; ++i) vm.v[i] = 0.0;
+  for (int i = 0; i < m.nb * m.nb; ++i) vm.v[i] = v[i];
+  switch (m.nb) {
+    case 1: return products_nb<C, 1>(m, vm, n, Un, Ul_dev, GR, SR, st, skip);
+    case 2: return products_nb<C, 2>(m, vm, n, Un, Ul_dev, GR, SR, st, skip);
+    case 3: return products_nb<C, 3>(m, vm, n, Un, Ul_dev, GR, SR, st, skip);
+    case 4: return products_nb<C, 4>(m, vm, n, Un, Ul_dev, GR, SR, st, skip);
+    case 6: return products_nb<C, 6>(m, vm, n, Un, Ul_dev, GR, SR, st, skip);
+    case 8: return products_nb<C, 8>(m, vm, n, Un, Ul_dev, GR, SR, st, skip);
+    case 12: return products_nb<C, 12>(m, vm, n, Un, Ul_dev, GR, SR, st, skip);
+    case 16: return products_nb<C, 16>(m, vm, n, Un, Ul_dev, GR, SR, st, skip);
+    default: return cudaErrorInvalidValue;
+  }
 }
-}  // namespace
 
-// raise the DFT kernel's dynamic shared-memory limit for this mesh (a host-side
-// attribute of the current device's context, done before any stream capture
-// that launches it); the raised limit is kept per device, under a lock
-cudaError_t dft_prepare(int L0, int L1) {
+size_t dft_smem_bytes(int L0, int L1, size_t csize) {
+  const int nk = L0 * L1;
+  return csize * (2 * (size_t)dft_group(nk) * nk + L0 + L1);
+}
+
+template <class C, class Tin, class Tout>
+cudaError_t dft_prepare_t(int L0, int L1) {
   constexpr size_t kDefault = 48 * 1024;   // no opt-in needed below this
   constexpr int kMaxDev = 64;
   static std::mutex mu;
   static size_t raised[kMaxDev] = {};
-  const size_t smem = dft_smem_bytes(L0, L1);
+  const size_t smem = dft_smem_bytes(L0, L1, sizeof(C));
   if (smem <= kDefault) return cudaSuccess;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -290,45 +345,50 @@ cudaError_t dft_prepare(int L0, int L1) {
   if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(mu);
   if (smem > raised[dev]) {
-    e = cudaFuncSetAttribute(dft_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(dft_rows_kernel<C, Tin, Tout>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     raised[dev] = smem;
   }
   return cudaSuccess;
 }
 
+template <class C, class Tin, class Tout>
+cudaError_t dft_launch(const Tin *in, Tout *out, long narr, int L0, int L1, int sign, double scale, cudaStream_t st,
+                       bool accumulate, const int *skip) {
+  if (narr <= 0) return cudaSuccess;
+  const int nk = L0 * L1, P = dft_group(nk);
+  cudaError_t pe = dft_prepare_t<C, Tin, Tout>(L0, L1);
+  if (pe != cudaSuccess) return pe;
+  const int pts = P * nk;
+  const int threads = pts >= 256 ? 256 : ((pts + 31) / 32) * 32;
+  const long groups = (narr + P - 1) / P, cap = (long)device_sms() * 8;
+  const long blocks = groups < cap ? groups : cap;
+  dft_rows_kernel<C, Tin, Tout><<<(unsigned)blocks, threads, dft_smem_bytes(L0, L1, sizeof(C)), st>>>(
+      in, out, narr, L0, L1, sign, scale, accumulate ? 1 : 0, skip);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// raise the DFT kernels' dynamic shared-memory limits for this mesh (host-side
+// attributes of the current device's context, done before any stream capture
+// that launches them); the raised limits are kept per device, under a lock
+cudaError_t dft_prepare(int L0, int L1) {
+  cudaError_t e = dft_prepare_t<double2, double2, double2>(L0, L1);
+  if (e == cudaSuccess) e = dft_prepare_t<float2, double2, float2>(L0, L1);
+  if (e == cudaSuccess) e = dft_prepare_t<float2, float2, double2>(L0, L1);
+  return e;
+}
+
 cudaError_t launch_dft_rows(const double2 *in, double2 *out, long narr, int L0, int L1, int sign,
                             double scale, cudaStream_t st, bool accumulate, const int *skip) {
-  if (narr <= 0) return cudaSuccess;
-  const int nk = L0 * L1;
-  const size_t smem = dft_smem_bytes(L0, L1);
-  cudaError_t pe = dft_prepare(L0, L1);
-  if (pe != cudaSuccess) return pe;
-  int threads = nk >= 256 ? 256 : ((nk + 31) / 32) * 32;
-  const long cap = (long)device_sms() * 8;
-  long blocks = narr < cap ? narr : cap;
-  dft_rows_kernel<<<(unsigned)blocks, threads, smem, st>>>(in, out, narr, L0, L1, sign, scale,
-                                                            accumulate ? 1 : 0, skip);
-  return cudaGetLastError();
+  return dft_launch<double2, double2, double2>(in, out, narr, L0, L1, sign, scale, st, accumulate, skip);
 }
 
 cudaError_t launch_sigma_products(const Mesh &m, const double *v, int n, double Un,
                                   const double *Ul_dev, const double2 *GR, double2 *SR,
                                   cudaStream_t st, const int *skip) {
-  VMat vm;
-  for (int i = 0; i < kMaxNb * kMaxNb; ++i) vm.v[i] = 0.0;
-  for (int i = 0; i < m.nb * m.nb; ++i) vm.v[i] = v[i];
-  switch (m.nb) {
-    case 1: return products_nb<1>(m, vm, n, Un, Ul_dev, GR, SR, st, skip);
-    case 2: return products_nb<2>(m, vm, n, Un, Ul_dev, GR, SR, st, skip);
-    case 3: return products_nb<3>(m, vm, n, Un, Ul_dev, GR, SR, st, skip);
-    case 4: return products_nb<4>(m, vm, n, Un, Ul_dev, GR, SR, st, skip);
-    case 6: return products_nb<6>(m, vm, n, Un, Ul_dev, GR, SR, st, skip);
-    case 8: return products_nb<8>(m, vm, n, Un, Ul_dev, GR, SR, st, skip);
-    case 12: return products_nb<12>(m, vm, n, Un, Ul_dev, GR, SR, st, skip);
-    case 16: return products_nb<16>(m, vm, n, Un, Ul_dev, GR, SR, st, skip);
-    default: return cudaErrorInvalidValue;
-  }
+  return products_any<double2>(m, v, n, Un, Ul_dev, GR, SR, st, skip);
 }
 
 size_t sigma_workspace_bytes(const Mesh &m, int n) {
@@ -337,9 +397,19 @@ size_t sigma_workspace_bytes(const Mesh &m, int n) {
 }
 
 cudaError_t sigma_row(const Mesh &m, const double *v_host, int n, double Un, const double *Ul_dev,
-                      const double2 *Grow, double2 *Sig, double2 *work, cudaStream_t st, const int *skip) {
+                      const double2 *Grow, double2 *Sig, double2 *work, cudaStream_t st, const int *skip,
+                      bool fp32) {
   const size_t blk = (size_t)m.nb * m.nb * m.nk;
   const long narr = (long)(n + 1) * 2 * m.nb * m.nb;
+  if (fp32) {   // complex64 transforms and products (half the workspace)
+    float2 *GR = (float2 *)work;
+    float2 *SR = GR + (size_t)(n + 1) * 2 * blk;
+    cudaError_t e = dft_launch<float2, double2, float2>(Grow, GR, narr, m.L0, m.L1, +1, 1.0 / m.nk, st, false, skip);
+    if (e != cudaSuccess) return e;
+    e = products_any<float2>(m, v_host, n, Un, Ul_dev, GR, SR, st, skip);
+    if (e != cudaSuccess) return e;
+    return dft_launch<float2, float2, double2>(SR, Sig, narr, m.L0, m.L1, -1, 1.0, st, false, skip);
+  }
   double2 *GR = work;
   double2 *SR = work + (size_t)(n + 1) * 2 * blk;
   cudaError_t e = launch_dft_rows(Grow, GR, narr, m.L0, m.L1, +1, 1.0 / m.nk, st, false, skip);

@@ -603,11 +603,6 @@ __global__ void reduce_partials_kernel(const double2 *__restrict__ part, double2
 }
 
 // --------------------------------------------------- packing and coefficients
-__device__ __forceinline__ float4 split_df(double2 x) {
-  const float rh = __double2float_rn(x.x), ih = __double2float_rn(x.y);
-  return make_float4(rh, __double2float_rn(x.x - (double)rh), ih, __double2float_rn(x.y - (double)ih));
-}
-
 // nblocks blocks [2][nb][nb][nk] of (G^<, G^>) in FP64 -> (G^<, dG = G^< - G^>)
 // in the history storage (dG formed in FP64 before rounding)
 __global__ void pack_kernel(int prec, const double2 *__restrict__ src, void *__restrict__ dst,
@@ -619,17 +614,7 @@ __global__ void pack_kernel(int prec, const double2 *__restrict__ src, void *__r
     const size_t bq = i / blk, r = i - bq * blk;
     const size_t o0 = bq * 2 * blk + r, o1 = o0 + blk;
     const double2 gl = src[o0];
-    const double2 dg = c_sub(gl, src[o1]);
-    if (prec == KBE_PREC_DF64) {
-      ((float4 *)dst)[o0] = split_df(gl);
-      ((float4 *)dst)[o1] = split_df(dg);
-    } else if (prec == KBE_PREC_C64) {
-      ((float2 *)dst)[o0] = make_float2((float)gl.x, (float)gl.y);
-      ((float2 *)dst)[o1] = make_float2((float)dg.x, (float)dg.y);
-    } else {
-      ((double2 *)dst)[o0] = gl;
-      ((double2 *)dst)[o1] = dg;
-    }
+    pack_store(prec, dst, o0, o1, gl, c_sub(gl, src[o1]));
   }
 }
 
@@ -965,8 +950,10 @@ __global__ void __launch_bounds__(kStagedThreads, KBE_STAGED_MINB)
     if (failed) {   // a copy did not arrive: flag it, let the in-flight ones land, stop
       if (tid == 0) {
         int st = kDevTimeout;
-        for (int q = i; q < issued; ++q)
+        for (int q = i; q < issued; ++q) {
+          if (drop && q == 0) continue;   // never issued (fault injection): nothing in flight
           if (!mbar_wait(&bar[q % kStages], (unsigned)((q / kStages) & 1), kMbarWaitLimit)) st |= kDevTimeoutDrain;
+        }
         if (status) atomicOr(status, st);
       }
       __syncthreads();

@@ -1,4 +1,5 @@
-"""Build libkbe.so in-tree with nvcc for sm_103a (one -gencode, parallel TUs)."""
+"""Build libkbe.so in-tree with nvcc for sm_103a (one -gencode, one nvcc per
+translation unit, all in parallel)."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -49,7 +50,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             print(r.stdout + r.stderr, file=sys.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(os.cpu_count() or 8, len(srcs)))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]

@@ -1,0 +1,926 @@
+// Reverse mode (discrete adjoint) of one time step, FP64 history: the kernels
+// and their per-N_b launchers. Internal to libkbe; the launchers are
+// instantiated by N_b group in kbe_adjoint_nb*.cu (to compile in parallel)
+// and dispatched by kbe_adjoint.cu.
+//
+//
+// kbe_backward differentiates a loss of the final-time occupations n_kb(t_N)
+// with respect to the Peierls samples A_i and the interaction U by walking
+// the steps n = N..1 backwards. Everything step n reads is the history
+// triangle (rows < n are final once written) and I_{n-1}, itself a function
+// of that history, so the step's intermediates (predictor and corrector
+// rows, h, U, V, the Sigma and collision rows of every stage) are recomputed
+// from the history, then the step's operations are transposed in reverse
+// order. The transposes are those of the kernels' own arithmetic (the
+// sweep in its (I^<, I^> - I^<) form, the DFT Sigma, the truncated power
+// series of the propagators), so the gradient is that of the computed trajectory.
+//
+// Convention: for a complex variable z the adjoint lam_z is defined by
+// dL = Re sum conj(lam_z) dz. A holomorphic use z = c w gives lam_w += conj(c)
+// lam_z, an anti-holomorphic one z = c conj(w) gives lam_w += conj(lam_z) c;
+// a matrix product Z = A B gives lam_A += lam_Z B^+ and lam_B += A^+ lam_Z.
+//
+// Pieces (forward operation -> kernel here):
+//   collision row (a2), coefficients  -> adj_coef_kernel: lam of the Sigma row
+//   collision row (a2), history       -> adj_hist_kernel: lam of every block
+//   Sigma row (a1)                    -> DFT, sigma_adj_products_kernel, DFT
+//   row / diagonal update (a4)        -> adj_rows_kernel, adj_uv_kernel,
+//                                        adj_diag_kernel (series reversed)
+//   h from A, mean field, shift (a3)  -> adj_hvec_kernel (dL/dA_i, dL/dU)
+#pragma once
+
+#include "kbe_internal.cuh"
+#include "kbe_matgroup.cuh"
+
+namespace kbe {
+
+struct VMat {
+  double v[kMaxNb * kMaxNb];
+};
+
+struct HvecAdj {
+  double A, U;
+  int hf, paper_shift;
+  double v[kMaxNb * kMaxNb];
+  const double2 *rho_a, *rho_b;   // mid density = ca rho_a + cb rho_b
+  double ca, cb;
+  double2 *lam_rho_a, *lam_rho_b; // receive ca lam_mid, cb lam_mid (NULL: skip)
+  double2 *lam_cur;               // G^<(n,n) block receiving i cur_scale lam_mid (NULL: skip)
+  double cur_scale;
+  double *gA, *gU_a, *gU_b;       // dL/dU_mid goes half to each (U_mid = (U_{n-1} + U_n) / 2)
+};
+
+namespace {
+
+
+size_t blkof(const Mesh &m) { return (size_t)m.nb * m.nb * m.nk; }
+
+unsigned grid_for_count(size_t count) {
+  size_t b = (count + 255) / 256;
+  const size_t cap = (size_t)device_sms() * 64;
+  return (unsigned)(b < cap ? (b ? b : 1) : cap);
+}
+
+// (G^<, dG) blocks of the FP64 history -> (G^<, G^> = G^< - dG)
+__global__ void unpack_fp64_kernel(const double2 *__restrict__ src, double2 *__restrict__ dst,
+                                   size_t nblocks, size_t blk) {
+  const size_t count = nblocks * blk;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t bq = i / blk, r = i - bq * blk;
+    const size_t o0 = bq * 2 * blk + r, o1 = o0 + blk;
+    const double2 gl = src[o0];
+    dst[o0] = gl;
+    dst[o1] = c_sub(gl, src[o1]);
+  }
+}
+
+// ------------------------------------------ collision row: coefficients ----
+// Forward, in the form the sweep computes (one output column j, l = 0..n,
+// X_lj = G^<(l, j) or -G^<(j, l)^+, D_lj the same of dG = G^< - G^>, w_l = w^(n)_l,
+// Delta = S^> - S^<): X = I^< and Y = I^> - I^<,
+//   X(j) = sum_l w_l Delta_l X_lj + sum_{l<=j} w^(j)_l S^<_l D_lj
+//   Y(j) = -sum_{l>j} w_l Delta_l D_lj + sum_{l<=j} (w^(j)_l - w_l) Delta_l D_lj.
+// With lam_X = lam^< + lam^>, lam_Y = lam^> the transpose for each l is
+//   lam_Delta(l) = w_l (T1 - T2) + T4,  lam_S^>(l) = lam_Delta,  lam_S^<(l) = T3 - lam_Delta,
+//   T1 = sum_j lam_X(j) X_lj^+,            T2 = sum_{j<l} lam_Y(j) D_lj^+,
+//   T3 = sum_{j>=l} w^(j)_l lam_X(j) D_lj^+, T4 = sum_{j>=l} (w^(j)_l - w_l) lam_Y(j) D_lj^+.
+// Above the diagonal (j > l) w^(j)_l equals w_l except for the few j whose
+// grid puts l among its end weights (trapezoid: none; Gregory: j < l + 3 or
+// j < 5): those "special" nodes carry T4 and their own T3 weight, the rest
+// (the bulk) two products. Stored block (l, j), j <= l: X_lj^+ {cb} = conj(G(l,j)_bc);
+// for j > l the block (j, l) is read: X_lj^+ {cb} = -G(j,l)_cb.
+template <int NB>
+__device__ __forceinline__ void lam_xy(const double2 *__restrict__ lam, size_t blk, int nk, int c, double2 &lx,
+                                       double2 &ly) {
+  const double2 ll = lam[(size_t)c * nk], lg = lam[blk + (size_t)c * nk];
+  lx = c_add(ll, lg);
+  ly = lg;
+}
+
+// grid: x = tiles of the N_b^2 n_k outputs (l; a, b; k), y = l (0..n),
+// z = split of the j range; out is lam_Sigma when gridDim.z == 1, else the
+// partial rows [z][l][x][a][b][k].
+template <int NB, int QUAD>
+__global__ void __launch_bounds__(256, 2) adj_coef_kernel(const double2 *__restrict__ H,
+                                                          const double2 *__restrict__ lamI,
+                                                          double2 *__restrict__ out, int n, int nk,
+                                                          int jchunk, double dt) {
+  const int l = blockIdx.y;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= NB * NB * nk) return;
+  const int k = idx % nk;
+  const int ab = idx / nk;
+  const int a = ab / NB, b = ab - (ab / NB) * NB;
+  const int j0 = blockIdx.z * jchunk;
+  const int j1 = min(n + 1, j0 + jchunk);
+  const size_t blk = (size_t)NB * NB * nk;
+  const double2 *lbase = lamI + (size_t)a * NB * nk + k;   // lam_j(a, c) at + j 2 blk + c nk
+  const double2 *hbase = H + k;
+  const double2 z = make_double2(0, 0);
+  const double wn = dt * quad_omega(QUAD, n, l);
+  const int jb = QUAD == kQuadTrapezoid ? l + 1 : max(l + 3, 5);   // first bulk node above l
+  double2 t1 = z, t2 = z, t3 = z, s3 = z, s4 = z;
+  for (int j = j0; j < min(j1, l); ++j) {   // stored blocks (l, j) below the diagonal
+    const double2 *lj = lbase + (size_t)j * 2 * blk, *g = hbase + tri(l, j) * 2 * blk;
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+      double2 lx, ly;
+      lam_xy<NB>(lj, blk, nk, c, lx, ly);
+      t1 = c_fmac(lx, g[(size_t)(b * NB + c) * nk], t1);
+      t2 = c_fmac(ly, g[blk + (size_t)(b * NB + c) * nk], t2);
+    }
+  }
+  // weighted nodes: the diagonal j = l and the special nodes above it
+  auto weighted = [&](int j) {
+    const bool diag = j == l;
+    const double2 *lj = lbase + (size_t)j * 2 * blk;
+    const double2 *g = hbase + (diag ? tri(l, l) : tri(j, l)) * 2 * blk;
+    double2 p = z, q = z;
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+      double2 lx, ly;
+      lam_xy<NB>(lj, blk, nk, c, lx, ly);
+      if (diag) {
+        t1 = c_fmac(lx, g[(size_t)(b * NB + c) * nk], t1);
+        const double2 dg = g[blk + (size_t)(b * NB + c) * nk];
+        p = c_fmac(lx, dg, p);
+        q = c_fmac(ly, dg, q);
+      } else {
+        t1 = c_fnma(lx, g[(size_t)(c * NB + b) * nk], t1);
+        const double2 dg = g[blk + (size_t)(c * NB + b) * nk];
+        p = c_fnma(lx, dg, p);
+        q = c_fnma(ly, dg, q);
+      }
+    }
+    const double wj = dt * quad_omega(QUAD, j, l);
+    s3 = make_double2(fma(wj, p.x, s3.x), fma(wj, p.y, s3.y));
+    s4 = make_double2(fma(wj - wn, q.x, s4.x), fma(wj - wn, q.y, s4.y));
+  };
+  if (l >= j0 && l < j1) weighted(l);
+  for (int j = max(j0, l + 1); j < min(j1, jb); ++j) weighted(j);
+  for (int j = max(j0, jb); j < j1; ++j) {   // bulk above the diagonal: w^(j)_l = w_l
+    const double2 *lj = lbase + (size_t)j * 2 * blk, *g = hbase + tri(j, l) * 2 * blk;
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+      double2 lx, ly;
+      lam_xy<NB>(lj, blk, nk, c, lx, ly);
+      t1 = c_fnma(lx, g[(size_t)(c * NB + b) * nk], t1);
+      t3 = c_fnma(lx, g[blk + (size_t)(c * NB + b) * nk], t3);
+    }
+  }
+  // lam_Delta = wn (t1 - t2) + s4; T3 = s3 + wn t3
+  const double2 ld = c_add(c_scale(wn, c_sub(t1, t2)), s4);
+  const double2 T3 = c_add(s3, c_scale(wn, t3));
+  double2 *o = out + ((size_t)blockIdx.z * (n + 1) + l) * 2 * blk + (size_t)ab * nk + k;
+  o[0] = c_sub(T3, ld);
+  o[blk] = ld;
+}
+
+// C1(l) = w^(n)_l (S^>(l) - S^<(l)), l = 0..n, one block per l
+__global__ void adj_c1_kernel(const double2 *__restrict__ Sig, double2 *__restrict__ C1, int n, size_t blk,
+                              double dt, int quad) {
+  const size_t total = (size_t)(n + 1) * blk;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t l = i / blk, r = i - l * blk;
+    C1[i] = c_scale(dt * quad_omega(quad, n, (int)l), c_sub(Sig[(l * 2 + 1) * blk + r], Sig[l * 2 * blk + r]));
+  }
+}
+
+__global__ void sum_partials_kernel(const double2 *__restrict__ part, double2 *__restrict__ out,
+                                    size_t count, int nz) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x) {
+    double2 s = part[i];
+    for (int z = 1; z < nz; ++z) s = c_add(s, part[(size_t)z * count + i]);
+    out[i] = s;
+  }
+}
+
+// ----------------------------------------------- collision row: history ----
+// Every stored block (i, j'), i <= n, is used twice by the forward sweep (the
+// X / Y form above, lam_X = lam^< + lam^>, lam_Y = lam^>):
+//   use 1, node l = i of column j' (stored block):
+//     j' < i: lam_G^<(i,j') += C1(i)^+ lam_X(j'),  lam_dG(i,j') -= C1(i)^+ lam_Y(j')
+//     j' = i: lam_G^< += C1(i)^+ lam_X(i),
+//             lam_dG  += (w^(i)_i S^<_i)^+ lam_X(i) + ((w^(i)_i - w_i) Delta_i)^+ lam_Y(i)
+//   use 2 (j' < i), node l = j' of column i (adjoint block -G(i,j')^+):
+//     lam_G^<(i,j') -= [C1(j')^+ lam_X(i)]^+,
+//     lam_dG(i,j')  -= [w^(i)_j' S^<_j'^+ lam_X(i) + (w^(i)_j' - w_j') Delta_j'^+ lam_Y(i)]^+
+//   (the last term only where the two weights differ: never for the trapezoid).
+// The history's adjoint is kept for (G^<, G^>): lam^< += lam_G^< + lam_dG, lam^> -= lam_dG.
+// Row n of the triangle goes to lamRowN (the stage being differentiated).
+// C1 is precomputed per launch (adj_c1_kernel); each thread keeps its
+// column p of C1(i), lam_X(i) and lam_Y(i) in registers.
+// grid: x = tiles of the N_b^2 n_k elements (p, q, k), y = row i, z = chunk
+// of j' (each block written by exactly one thread: no reduction).
+template <int NB>
+__global__ void __launch_bounds__(256, 2) adj_hist_kernel(const double2 *__restrict__ Sig,
+                                                          const double2 *__restrict__ C1,
+                                                          const double2 *__restrict__ lamI,
+                                                          double2 *lamH, double2 *lamRowN, int n, int nk,
+                                                          int jchunk, double dt, int quad) {
+  const int i = blockIdx.y;
+  const int j0 = blockIdx.z * jchunk;
+  if (j0 > i) return;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= NB * NB * nk) return;
+  const int k = idx % nk;
+  const int pq = idx / nk;
+  const int p = pq / NB, q = pq - (pq / NB) * NB;
+  const int j1 = min(i + 1, j0 + jchunk);
+  const size_t blk = (size_t)NB * NB * nk;
+  const size_t cs = (size_t)NB * nk;   // stride of the row index c
+  // this thread's column p of C1(i), lam_X(i) and lam_Y(i), elements (c, p)
+  double2 c1i[NB], LXi[NB], LYi[NB];
+  {
+    const double2 *ci = C1 + (size_t)i * blk + (size_t)p * nk + k;
+    const double2 *li = lamI + (size_t)i * 2 * blk + (size_t)p * nk + k;
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+      c1i[c] = ci[c * cs];
+      LYi[c] = li[blk + c * cs];
+      LXi[c] = c_add(li[c * cs], LYi[c]);
+    }
+  }
+  const double2 z = make_double2(0, 0);
+  const double wni = dt * quad_omega(quad, n, i);
+  for (int jp = j0; jp < j1; ++jp) {
+    const double2 *lj = lamI + (size_t)jp * 2 * blk + (size_t)q * nk + k;   // lam_j'(c, q)
+    double2 gl = z, gd = z;
+    if (jp < i) {
+      const double2 *cj = C1 + (size_t)jp * blk + (size_t)q * nk + k;     // C1(j')_{cq}
+      const double2 *sj = Sig + (size_t)jp * 2 * blk + (size_t)q * nk + k; // S(j')_{cq}
+      double2 t = z;
+#pragma unroll
+      for (int c = 0; c < NB; ++c) {
+        const double2 ly = lj[blk + c * cs], lx = c_add(lj[c * cs], ly);
+        gl = c_fmac(lx, c1i[c], gl);           // use 1: C1(i)^+ lam_X(j')
+        gd = c_fnmac(ly, c1i[c], gd);          //        -C1(i)^+ lam_Y(j')
+        gl = c_fnmac(cj[c * cs], LXi[c], gl);  // use 2: -[C1(j')^+ lam_X(i)]^+
+        t = c_fmac(sj[c * cs], LXi[c], t);     //        [S^<(j')^+ lam_X(i)]^+
+      }
+      const double wB = dt * quad_omega(quad, i, jp), wY = wB - dt * quad_omega(quad, n, jp);
+      gd = make_double2(fma(-wB, t.x, gd.x), fma(-wB, t.y, gd.y));
+      if (wY != 0.0) {   // the weights of the two grids differ at this node (Gregory ends)
+        double2 u = z;
+#pragma unroll
+        for (int c = 0; c < NB; ++c) u = c_fmac(c_sub(sj[blk + c * cs], sj[c * cs]), LYi[c], u);
+        gd = make_double2(fma(-wY, u.x, gd.x), fma(-wY, u.y, gd.y));
+      }
+    } else {   // the diagonal block (node l = j = i)
+      const double2 *si = Sig + (size_t)i * 2 * blk + (size_t)p * nk + k;   // S(i)_{cp}
+      double2 t = z, u = z;
+#pragma unroll
+      for (int c = 0; c < NB; ++c) {
+        const double2 ly = lj[blk + c * cs], lx = c_add(lj[c * cs], ly);
+        const double2 sl = si[c * cs];
+        gl = c_fmac(lx, c1i[c], gl);
+        t = c_fmac(lx, sl, t);
+        u = c_fmac(ly, c_sub(si[blk + c * cs], sl), u);
+      }
+      const double wA = dt * quad_omega(quad, i, i), wY = wA - wni;
+      gd = make_double2(wA * t.x + wY * u.x, wA * t.y + wY * u.y);
+    }
+    double2 *dst = (i == n) ? lamRowN + (size_t)jp * 2 * blk : lamH + tri(i, jp) * 2 * blk;
+    double2 *e0 = dst + (size_t)pq * nk + k;
+    *e0 = c_add(*e0, c_add(gl, gd));
+    e0[blk] = c_sub(e0[blk], gd);
+  }
+}
+
+// ----------------------------------------------------------- Sigma row ----
+
+// One real-space product z = fac (x_jm Q_jm - E_jm) with
+// Q_jm = sum_ab v_ja v_mb x_ab conj(y_ab), E_jm = sum_ab v_ja v_mb x_jb conj(y_ab) x_am
+// (the forward band products), transposed: adds lam_x(p, q) and lam_y(p, q)
+// for the output lam_z. With lam_Q = fac conj(x) lam_z, lam_E = -fac lam_z and
+// W_pq = sum_jm v_jp v_mq lam_Q_jm:
+//   lam_x_pq = fac conj(Q_pq) lam_z_pq + y_pq W_pq
+//            + sum_a v_pa y_aq sum_m v_mq conj(x_am) lam_E_pm
+//            + sum_j v_jp lam_E_jq sum_b v_qb conj(x_jb) y_pb
+//   lam_y_pq = x_pq conj(W_pq) + sum_j v_jp x_jq sum_m v_mq conj(lam_E_jm) x_pm
+//   and returns Re conj(lam_z_pq) (x_pq Q_pq - E_pq), the U-free product's share of dL/dfac.
+template <int NB>
+__device__ __forceinline__ double prod_adj(const double2 *__restrict__ x, const double2 *__restrict__ y,
+                                           const double2 *__restrict__ lz, int p, int q, int nk, double fac,
+                                           const VMat &vm, double2 &lx, double2 &ly) {
+#define AT(M, r, c) M[(size_t)((r) * NB + (c)) * nk]
+  double2 Q = make_double2(0, 0), W = make_double2(0, 0), E = make_double2(0, 0);
+  double2 t3 = make_double2(0, 0), t4 = make_double2(0, 0), t6 = make_double2(0, 0);
+#pragma unroll 1
+  for (int a = 0; a < NB; ++a) {
+    const double va = vm.v[p * NB + a];   // v_pa (Q, t3)
+    const double vj = vm.v[a * NB + p];   // v_jp with j = a (W, t4, t6)
+    double2 sq = make_double2(0, 0), sw = make_double2(0, 0), s3 = make_double2(0, 0);
+    double2 s4 = make_double2(0, 0), s6 = make_double2(0, 0), se = make_double2(0, 0);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const double vb = vm.v[q * NB + b];   // v_qb
+      const double vm_ = vm.v[b * NB + q];  // v_mq with m = b
+      if (va != 0.0) {
+        if (vb != 0.0) {
+          sq = c_add(sq, c_scale(vb, c_mulc(AT(x, a, b), AT(y, a, b))));
+          se = c_add(se, c_scale(vb, c_mulc(AT(x, p, b), AT(y, a, b))));   // x_pb conj(y_ab)
+        }
+        if (vm_ != 0.0) s3 = c_add(s3, c_scale(vm_, c_mulc(AT(lz, p, b), AT(x, a, b))));
+      }
+      if (vj != 0.0) {
+        if (vm_ != 0.0) {
+          sw = c_add(sw, c_scale(vm_, c_mulc(AT(lz, a, b), AT(x, a, b))));
+          s6 = c_add(s6, c_scale(vm_, c_mulc(AT(x, p, b), AT(lz, a, b))));
+        }
+        if (vb != 0.0) s4 = c_add(s4, c_scale(vb, c_mulc(AT(y, p, b), AT(x, a, b))));
+      }
+    }
+    if (va != 0.0) {
+      Q = c_add(Q, c_scale(va, sq));
+      E = c_fma(c_scale(va, AT(x, a, q)), se, E);
+      t3 = c_fma(c_scale(va, AT(y, a, q)), s3, t3);
+    }
+    if (vj != 0.0) {
+      W = c_add(W, c_scale(vj, sw));
+      t4 = c_fma(c_scale(vj, AT(lz, a, q)), s4, t4);
+      t6 = c_fma(c_scale(vj, AT(x, a, q)), s6, t6);
+    }
+  }
+  W = c_scale(fac, W);
+  lx = c_add(lx, c_mulc(c_scale(fac, AT(lz, p, q)), Q));
+  lx = c_fma(AT(y, p, q), W, lx);
+  lx = c_add(lx, c_scale(-fac, c_add(t3, t4)));
+  ly = c_add(ly, c_mulc(AT(x, p, q), W));
+  ly = c_add(ly, c_scale(-fac, t6));
+  const double2 z = c_sub(c_mul(AT(x, p, q), Q), E);
+  const double2 l = AT(lz, p, q);
+  return l.x * z.x + l.y * z.y;
+#undef AT
+}
+
+// one thread per (l, p, R): row p of lam_G^<(R) and lam_G^>(R) of pair l.
+// Sigma^< is the product with (x, y) = (G^<, G^>), Sigma^> with (G^>, G^<);
+// fac = -U_n U_l. gpart[l][p][R] receives this thread's share of
+// g_l = Re <lam_Sigma(n,l), Sigma(n,l) / fac>, evaluated in real space (the
+// DFT pair makes the k-space and real-space inner products equal).
+template <int NB>
+__global__ void __launch_bounds__(128) sigma_adj_products_kernel(const double2 *__restrict__ GR,
+                                                                 const double2 *__restrict__ LR,
+                                                                 double2 *__restrict__ GLR, int n,
+                                                                 int nk, double Un,
+                                                                 const double *__restrict__ Ul, VMat vm,
+                                                                 double *__restrict__ gpart) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long total = (long)(n + 1) * NB * nk;
+  if (idx >= total) return;
+  const int R = (int)(idx % nk);
+  const long t = idx / nk;
+  const int p = (int)(t % NB);
+  const int l = (int)(t / NB);
+  const size_t blk = (size_t)NB * NB * nk;
+  const double2 *gl = GR + (size_t)l * 2 * blk + R, *gg = gl + blk;
+  const double2 *ll = LR + (size_t)l * 2 * blk + R, *lg = ll + blk;
+  double2 *ol = GLR + (size_t)l * 2 * blk + (size_t)p * NB * nk + R, *og = ol + blk;
+  const double fac = -Un * (Ul ? Ul[l] : Un);
+  double g = 0.0;
+#pragma unroll 1
+  for (int q = 0; q < NB; ++q) {
+    double2 aL = make_double2(0, 0), aG = make_double2(0, 0);
+    g += prod_adj<NB>(gl, gg, ll, p, q, nk, fac, vm, aL, aG);
+    g += prod_adj<NB>(gg, gl, lg, p, q, nk, fac, vm, aG, aL);
+    ol[(size_t)q * nk] = aL;
+    og[(size_t)q * nk] = aG;
+  }
+  gpart[idx] = g;
+}
+
+// The same for the pair pattern v = 1 - delta, where the product is
+// z = fac (tau x - x y^+ x), tau = tr(x y^+). With L = fac lam_z and w = tr(x^+ L):
+//   lam_x = conj(tau) L + w y - L x^+ y - y x^+ L,   lam_y = conj(w) x - x L^+ x.
+// Row p of each from the rows p of L x^+, y x^+, x L^+ (and of T = x y^+ for
+// the U-free inner product): O(N_b^2) per output row and product.
+template <int NB>
+__device__ __forceinline__ double prod_adj_pair_row(const double2 *__restrict__ x, const double2 *__restrict__ y,
+                                                    const double2 *__restrict__ lz, int p, int nk, double fac,
+                                                    double2 *lx, double2 *ly) {
+#define AT(M, r, c) M[(size_t)((r) * NB + (c)) * nk]
+  double2 tau = make_double2(0, 0), w = make_double2(0, 0);
+  double2 u[NB], v[NB], s[NB], t[NB];
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    double2 uc = make_double2(0, 0), vc = make_double2(0, 0), sc = make_double2(0, 0), tc = make_double2(0, 0);
+#pragma unroll
+    for (int a = 0; a < NB; ++a) {
+      const double2 xca = AT(x, c, a);
+      uc = c_add(uc, c_mulc(c_scale(fac, AT(lz, p, a)), xca));   // (L x^+)_pc
+      vc = c_add(vc, c_mulc(AT(y, p, a), xca));                  // (y x^+)_pc
+      sc = c_add(sc, c_mulc(AT(x, p, a), c_scale(fac, AT(lz, c, a))));   // (x L^+)_pc
+      tc = c_add(tc, c_mulc(AT(x, p, a), AT(y, c, a)));          // (x y^+)_pc
+    }
+    u[c] = uc;
+    v[c] = vc;
+    s[c] = sc;
+    t[c] = tc;
+  }
+#pragma unroll
+  for (int a = 0; a < NB; ++a)
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      tau = c_add(tau, c_mulc(AT(x, a, b), AT(y, a, b)));
+      w = c_add(w, c_mulc(c_scale(fac, AT(lz, a, b)), AT(x, a, b)));
+    }
+  double g = 0.0;
+#pragma unroll 1
+  for (int q = 0; q < NB; ++q) {
+    const double2 L = c_scale(fac, AT(lz, p, q));
+    double2 ax = c_add(c_mulc(L, tau), c_mul(w, AT(y, p, q)));   // conj(tau) L + w y
+    double2 ay = c_mulc(AT(x, p, q), w);                          // conj(w) x
+    double2 z = c_mul(tau, AT(x, p, q));                          // (tau x - T x)_pq
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+      ax = c_fnma(u[c], AT(y, c, q), ax);
+      ax = c_fnma(v[c], c_scale(fac, AT(lz, c, q)), ax);
+      ay = c_fnma(s[c], AT(x, c, q), ay);
+      z = c_fnma(t[c], AT(x, c, q), z);
+    }
+    lx[q] = c_add(lx[q], ax);
+    ly[q] = c_add(ly[q], ay);
+    const double2 lq = AT(lz, p, q);
+    g += lq.x * z.x + lq.y * z.y;
+  }
+  return g;
+#undef AT
+}
+
+template <int NB>
+__global__ void __launch_bounds__(128) sigma_adj_products_pair_kernel(const double2 *__restrict__ GR,
+                                                                      const double2 *__restrict__ LR,
+                                                                      double2 *__restrict__ GLR, int n, int nk,
+                                                                      double Un, const double *__restrict__ Ul,
+                                                                      double *__restrict__ gpart) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long total = (long)(n + 1) * NB * nk;
+  if (idx >= total) return;
+  const int R = (int)(idx % nk);
+  const long t = idx / nk;
+  const int p = (int)(t % NB);
+  const int l = (int)(t / NB);
+  const size_t blk = (size_t)NB * NB * nk;
+  const double2 *gl = GR + (size_t)l * 2 * blk + R, *gg = gl + blk;
+  const double2 *ll = LR + (size_t)l * 2 * blk + R, *lg = ll + blk;
+  const double fac = -Un * (Ul ? Ul[l] : Un);
+  double2 aL[NB], aG[NB];
+#pragma unroll
+  for (int q = 0; q < NB; ++q) aL[q] = aG[q] = make_double2(0, 0);
+  double g = prod_adj_pair_row<NB>(gl, gg, ll, p, nk, fac, aL, aG);   // Sigma^<: x = G^<, y = G^>
+  g += prod_adj_pair_row<NB>(gg, gl, lg, p, nk, fac, aG, aL);         // Sigma^>: x = G^>, y = G^<
+  double2 *ol = GLR + (size_t)l * 2 * blk + (size_t)p * NB * nk + R, *og = ol + blk;
+#pragma unroll
+  for (int q = 0; q < NB; ++q) {
+    ol[(size_t)q * nk] = aL[q];
+    og[(size_t)q * nk] = aG[q];
+  }
+  gpart[idx] = g;
+}
+
+// dL/dU from the Sigma row n: fac_l = -U_n U_l, so with g_l = sum_{p,R} gpart,
+//   dL/dU_l += -U_n g_l (every l),  dL/dU_n += -sum_l U_l g_l.
+// One CTA, l in a fixed order (deterministic).
+__global__ void adj_sigma_u_kernel(const double *__restrict__ gpart, int n, int per_l, double Un,
+                                   const double *__restrict__ Ul, double *__restrict__ gU) {
+  __shared__ double red[32];
+  __shared__ double acc;
+  if (threadIdx.x == 0) acc = 0.0;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  for (int l = 0; l <= n; ++l) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < per_l; i += blockDim.x) s += gpart[(size_t)l * per_l + i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double g = 0.0;
+      for (int w = 0; w < nw; ++w) g += red[w];
+      const double ul = Ul ? Ul[l] : Un;
+      if (Ul) gU[l] += -Un * g;
+      else gU[n] += -Un * g;
+      acc += ul * g;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) gU[n] += -acc;
+}
+
+// ------------------------------------------------------------- update ----
+// Forward rows j < n: G^x(n,j) = U G^x(n-1,j) + V Ibar^x(j),
+// Ibar = (1 - theta) Ip + theta Ic. Transposed per element:
+//   lam_Gprev += U^+ lam,  lam_Ip += (1 - theta) V^+ lam,  lam_Ic += theta V^+ lam.
+template <int NB>
+__global__ void adj_rows_kernel(int n, int nk, double theta, const double2 *__restrict__ U,
+                                const double2 *__restrict__ V, const double2 *__restrict__ lam,
+                                double2 *__restrict__ lamGprev, double2 *__restrict__ lamIp,
+                                double2 *__restrict__ lamIc) {
+  const size_t blk = (size_t)NB * NB * nk;
+  const size_t total = (size_t)n * 2 * blk;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int k = (int)(idx % nk);
+  size_t t = idx / nk;
+  const int q = (int)(t % NB);
+  t /= NB;
+  const int p = (int)(t % NB);
+  t /= NB;   // t = j * 2 + x
+  const size_t base = t * blk;
+  double2 gu = make_double2(0, 0), gv = make_double2(0, 0);
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    const double2 lo = lam[base + (size_t)(c * NB + q) * nk + k];
+    const size_t ocp = (size_t)(c * NB + p) * nk + k;
+    gu = c_add(gu, c_mulc(lo, U[ocp]));
+    gv = c_add(gv, c_mulc(lo, V[ocp]));
+  }
+  const size_t o = base + (size_t)(p * NB + q) * nk + k;
+  lamGprev[o] = c_add(lamGprev[o], gu);
+  lamIp[o] = c_add(lamIp[o], c_scale(1.0 - theta, gv));
+  if (theta != 0.0) lamIc[o] = c_add(lamIc[o], c_scale(theta, gv));
+}
+
+// lam_U = sum_{j<n, x} lam^x_j G^x(n-1,j)^+ and lam_V = sum lam^x_j Ibar^x_j^+,
+// per k, partial over a chunk of j (grid y); partial rows [z][2][p][q][k]
+template <int NB>
+__global__ void adj_uv_kernel(int n, int nk, double theta, const double2 *__restrict__ lam,
+                              const double2 *__restrict__ Gprev, const double2 *__restrict__ Ip,
+                              const double2 *__restrict__ Ic, double2 *__restrict__ part, int jchunk) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= NB * NB * nk) return;
+  const int k = idx % nk;
+  const int pq = idx / nk;
+  const int p = pq / NB, q = pq - (pq / NB) * NB;
+  const int z = blockIdx.y;
+  const int j0 = z * jchunk, j1 = min(n, j0 + jchunk);
+  const size_t blk = (size_t)NB * NB * nk;
+  double2 lu = make_double2(0, 0), lv = make_double2(0, 0);
+  for (int j = j0; j < j1; ++j)
+    for (int x = 0; x < 2; ++x) {
+      const size_t base = (size_t)(j * 2 + x) * blk + k;
+#pragma unroll
+      for (int c = 0; c < NB; ++c) {
+        const double2 lo = lam[base + (size_t)(p * NB + c) * nk];
+        const size_t oq = base + (size_t)(q * NB + c) * nk;
+        double2 ib = c_scale(1.0 - theta, Ip[oq]);
+        if (theta != 0.0) ib = c_add(ib, c_scale(theta, Ic[oq]));
+        lu = c_add(lu, c_mulc(lo, Gprev[oq]));
+        lv = c_add(lv, c_mulc(lo, ib));
+      }
+    }
+  part[(size_t)z * 2 * blk + (size_t)pq * nk + k] = lu;
+  part[((size_t)z * 2 + 1) * blk + (size_t)pq * nk + k] = lv;
+}
+
+// Time diagonal and propagators, per k (one matrix group per k-point):
+//   G^<(n,n) = U Gd U^+ - i X,  G^>(n,n) = G^<(n,n) - i,
+//   X = tau sum_{m=0}^{18} Q_m / (m+1),  Q_m = (-i tau / m)(h Q_{m-1} - Q_{m-1} h),  Q_0 = Sbar,
+//   U = sum_{m=0}^{14} P_m,  V = -i tau sum_m P_m / (m+1),  P_m = P_{m-1} (-i tau h) / m,
+// with tau = dt (no doubling; a step that needed one sets kDevAdjUnsupported).
+// Transposed, with ld = lam^<(n,n) + lam^>(n,n):
+//   lam_U += ld U Gd^+ + ld^+ U Gd,  lam_Gd += U^+ ld U,  lam_X = i ld,
+//   series reversed from the top: lam_Q_{m-1} = tau/m lam_X + conj(a_m) (h lam_Q_m - lam_Q_m h),
+//   lam_h += conj(a_m) (lam_Q_m Q_{m-1}^+ - Q_{m-1}^+ lam_Q_m),  a_m = -i tau / m;
+//   lam_P_{m-1} = lam_U + (i tau / m) lam_V + lam_P_m (-i tau h)^+ / m,
+//   lam_(-i tau h) += P_{m-1}^+ lam_P_m / m, lam_h += i tau lam_(-i tau h);
+//   lam_Sbar = lam_Q_0 -> lam_I^<(diag) += (1-theta or theta) (lam_Sbar + lam_Sbar^+).
+// The forward chains Q_0..Q_17 and P_0..P_13 are kept in `chain` (global,
+// [m][a][b][k]); each thread reads back only what it wrote itself.
+template <int NB>
+__global__ void __launch_bounds__(256) adj_diag_kernel(
+    int n, int nk, double dt, double theta, const double2 *__restrict__ h, const double2 *__restrict__ U,
+    const double2 *__restrict__ Gprev, const double2 *__restrict__ Ip, const double2 *__restrict__ Ic,
+    const double2 *__restrict__ lam, const double2 *__restrict__ part, int nz, double2 *lamGprev,
+    double2 *lamIp, double2 *lamIc, double2 *__restrict__ lamh, double2 *__restrict__ chain, int *status,
+    int kpc) {
+  using G = MatGroup<NB>;
+  const int span = kpc * G::E;
+  double2 *Hs = kbe_dsm, *Us = kbe_dsm + span, *LD = kbe_dsm + 2 * span, *A1 = kbe_dsm + 3 * span,
+          *A2 = kbe_dsm + 4 * span, *Qm = kbe_dsm + 5 * span;
+  double *red = (double *)(kbe_dsm + 6 * span);
+  const G g;
+  const int k = blockIdx.x * kpc + g.kk;
+  const bool active = k < nk;
+  const int nvalid = min(kpc, nk - (int)blockIdx.x * kpc);
+  const int o = g.kk * G::E + g.e;
+  const size_t blk = (size_t)G::E * nk;
+  const size_t oab = (size_t)g.e * nk + k, oba = (size_t)(g.b * NB + g.a) * nk + k;
+  const double2 zero = make_double2(0, 0);
+  double2 hv = zero, uv = zero, ld = zero, gd = zero, sv = zero, lu = zero, lv = zero;
+  if (active) {
+    hv = h[oab];
+    uv = U[oab];
+    const double2 *lr = lam + (size_t)n * 2 * blk;
+    ld = c_add(lr[oab], lr[blk + oab]);
+    gd = Gprev[(size_t)(n - 1) * 2 * blk + oab];
+    const double2 *ipd = Ip + (size_t)(n - 1) * 2 * blk;
+    sv = c_scale(1.0 - theta, c_add(ipd[oab], c_conj(ipd[oba])));
+    if (theta != 0.0) {
+      const double2 *icd = Ic + (size_t)n * 2 * blk;
+      sv = c_add(sv, c_scale(theta, c_add(icd[oab], c_conj(icd[oba]))));
+    }
+    for (int z = 0; z < nz; ++z) {
+      lu = c_add(lu, part[(size_t)z * 2 * blk + oab]);
+      lv = c_add(lv, part[((size_t)z * 2 + 1) * blk + oab]);
+    }
+  }
+  Hs[o] = hv;
+  __syncthreads();
+  const int s = doublings<NB>(g, Hs, kpc, nvalid, dt, red);
+  if (s != 0) {   // uniform over the CTA
+    if (threadIdx.x == 0) atomicOr(status, kDevAdjUnsupported);
+    return;
+  }
+  const double tau = dt;
+  Us[o] = uv;
+  LD[o] = ld;
+  A1[o] = gd;
+  __syncthreads();
+  A2[o] = g.mm_adj(Us, A1);   // U Gd^+
+  Qm[o] = g.mm(Us, A1);       // U Gd
+  __syncthreads();
+  lu = c_add(lu, c_add(g.mm(LD, A2), mm_hadj<NB>(g, LD, Qm)));
+  __syncthreads();
+  A2[o] = g.mm(LD, Us);       // ld U
+  __syncthreads();
+  const double2 gpd = mm_hadj<NB>(g, Us, A2);   // U^+ ld U
+  if (active) {
+    double2 *t = lamGprev + (size_t)(n - 1) * 2 * blk + oab;
+    *t = c_add(*t, gpd);
+  }
+  // X series: forward chain Q_0..Q_17
+  Qm[o] = sv;
+  if (active) chain[oab] = sv;
+  __syncthreads();
+  for (int m = 1; m <= 17; ++m) {
+    const double2 c = c_sub(g.mm(Hs, Qm), g.mm(Qm, Hs));
+    const double2 qv = make_double2(tau * c.y / m, -tau * c.x / m);
+    __syncthreads();
+    Qm[o] = qv;
+    if (active) chain[(size_t)m * blk + oab] = qv;
+    __syncthreads();
+  }
+  const double2 lX = c_i(ld);
+  double2 cur = c_scale(tau / 19.0, lX), lh = zero;
+  for (int m = 18; m >= 1; --m) {
+    A1[o] = cur;
+    Qm[o] = active ? chain[(size_t)(m - 1) * blk + oab] : zero;
+    __syncthreads();
+    const double2 ca = make_double2(0.0, tau / m);   // conj(-i tau / m)
+    lh = c_fma(ca, c_sub(g.mm_adj(A1, Qm), mm_hadj<NB>(g, Qm, A1)), lh);
+    const double2 t2 = c_sub(g.mm(Hs, A1), g.mm(A1, Hs));
+    __syncthreads();
+    cur = c_add(c_scale(tau / m, lX), c_mul(ca, t2));
+  }
+  A1[o] = cur;
+  __syncthreads();
+  const double2 lsh = c_add(cur, c_conj(A1[g.kk * G::E + g.b * NB + g.a]));   // lam_S + lam_S^+
+  if (active) {
+    double2 *t = lamIp + (size_t)(n - 1) * 2 * blk + oab;
+    *t = c_add(*t, c_scale(1.0 - theta, lsh));
+    if (theta != 0.0) {
+      double2 *u = lamIc + (size_t)n * 2 * blk + oab;
+      *u = c_add(*u, c_scale(theta, lsh));
+    }
+  }
+  __syncthreads();
+  // propagator series: forward chain P_0..P_13
+  const double2 one = make_double2(g.a == g.b ? 1.0 : 0.0, 0.0);
+  Qm[o] = one;
+  if (active) chain[oab] = one;
+  __syncthreads();
+  for (int m = 1; m <= 13; ++m) {
+    const double2 c = g.mm(Qm, Hs);
+    const double2 pv = make_double2(tau * c.y / m, -tau * c.x / m);
+    __syncthreads();
+    Qm[o] = pv;
+    if (active) chain[(size_t)m * blk + oab] = pv;
+    __syncthreads();
+  }
+  double2 lY = zero;
+  cur = c_add(lu, c_mul(make_double2(0.0, tau / 15.0), lv));
+  for (int m = 14; m >= 1; --m) {
+    A1[o] = cur;
+    Qm[o] = active ? chain[(size_t)(m - 1) * blk + oab] : zero;
+    __syncthreads();
+    lY = c_add(lY, c_scale(1.0 / m, mm_hadj<NB>(g, Qm, A1)));
+    const double2 t = g.mm(A1, Hs);   // lam_P h
+    __syncthreads();
+    const double2 im = make_double2(0.0, tau / m);
+    cur = c_add(lu, c_add(c_mul(im, lv), c_mul(im, t)));
+  }
+  lh = c_add(lh, c_mul(make_double2(0.0, tau), lY));
+  if (active) lamh[oab] = lh;
+}
+
+// -------------------------------------------------- h from A and the MF ----
+
+// h_k = h0(k - A d) + U hf(mid) (- U on the last band, paper shift) (+ dipole),
+// U = U_mid of the step.
+//   dL/dA += Re sum_k tr(lam_h^+ dh0/dA),  dh0/dA = sum_r t(R_r) e^{i theta_r} (-i d.R_r);
+//   Lam = sum_k lam_h; dL/dU_mid = Re tr(Lam^+ hf(mid)) - Re Lam_{N_b N_b} (shift);
+//   lam_mid_jm = -U v_jm Lam_jm,  lam_mid_aa += U sum_j v_ja Lam_jj.
+// One CTA: a warp per element (a, b) reduces over k; thread 0 finishes.
+template <int NB>
+__global__ void adj_hvec_kernel(Mesh m, HopTable hop, HvecAdj p, const double2 *__restrict__ lamh) {
+  __shared__ double2 Lam[NB * NB];
+  __shared__ double2 lmid[NB * NB];
+  __shared__ double red[32];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  double ga = 0.0;
+  for (int e = warp; e < NB * NB; e += nw) {
+    double2 acc = make_double2(0, 0);
+    for (int k = lane; k < m.nk; k += 32) {
+      const double2 lh = lamh[(size_t)e * m.nk + k];
+      acc = c_add(acc, lh);
+      const int k0 = k / m.L1, k1 = k - (k / m.L1) * m.L1;
+      double2 dh = make_double2(0, 0);
+      for (int r = 0; r < hop.nhop; ++r) {
+        const int R0 = hop.R[2 * r], R1 = hop.R[2 * r + 1];
+        const double dR = hop.d0 * R0 + hop.d1 * R1;
+        if (dR == 0.0) continue;
+        const int m0 = ((k0 * R0) % m.L0 + m.L0) % m.L0, m1 = ((k1 * R1) % m.L1 + m.L1) % m.L1;
+        const double th = 2.0 * M_PI * ((double)m0 / m.L0 + (double)m1 / m.L1) - p.A * dR;
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        const double2 tv = c_mul(hop.T[(size_t)r * NB * NB + e], make_double2(cs, sn));
+        dh = c_add(dh, c_scale(dR, make_double2(tv.y, -tv.x)));   // (-i dR) t e^{i theta}
+      }
+      ga += lh.x * dh.x + lh.y * dh.y;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+    }
+    if (lane == 0) Lam[e] = acc;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, off);
+  if (lane == 0) red[warp] = ga;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double gsum = 0.0;
+    for (int w = 0; w < nw; ++w) gsum += red[w];
+    *p.gA += gsum;
+    double gu = 0.0;
+    for (int e = 0; e < NB * NB; ++e) lmid[e] = make_double2(0, 0);
+    if (p.hf) {
+      for (int j = 0; j < NB; ++j)
+        for (int mm = 0; mm < NB; ++mm) {
+          const int e = j * NB + mm;
+          const double2 mid = c_add(c_scale(p.ca, p.rho_a[e]), c_scale(p.cb, p.rho_b[e]));
+          double2 x = c_scale(-p.v[e], mid);
+          if (j == mm)
+            for (int a = 0; a < NB; ++a) {
+              const int ea = a * NB + a;
+              x = c_add(x, c_scale(p.v[j * NB + a], c_add(c_scale(p.ca, p.rho_a[ea]), c_scale(p.cb, p.rho_b[ea]))));
+            }
+          gu += Lam[e].x * x.x + Lam[e].y * x.y;
+          lmid[e] = c_add(lmid[e], c_scale(-p.U * p.v[e], Lam[e]));
+        }
+      for (int j = 0; j < NB; ++j)
+        for (int a = 0; a < NB; ++a)
+          lmid[a * NB + a] = c_add(lmid[a * NB + a], c_scale(p.U * p.v[j * NB + a], Lam[j * NB + j]));
+    }
+    if (p.paper_shift) gu -= Lam[NB * NB - 1].x;
+    *p.gU_a += 0.5 * gu;
+    *p.gU_b += 0.5 * gu;
+    for (int e = 0; e < NB * NB; ++e) {
+      if (p.lam_rho_a) p.lam_rho_a[e] = c_add(p.lam_rho_a[e], c_scale(p.ca, lmid[e]));
+      if (p.lam_rho_b) p.lam_rho_b[e] = c_add(p.lam_rho_b[e], c_scale(p.cb, lmid[e]));
+    }
+  }
+  __syncthreads();
+  if (p.lam_cur) {   // the current density is (1/n_k) sum_k (-i) G^<(k; n, n)
+    for (int i = threadIdx.x; i < NB * NB * m.nk; i += blockDim.x) {
+      const int e = i / m.nk;
+      p.lam_cur[i] = c_add(p.lam_cur[i], c_i(c_scale(p.cur_scale, lmid[e])));
+    }
+  }
+}
+
+// lamDiag[e][k] += i scale lamRho[e]  (transpose of rho = (1/n_k) sum_k -i G^<)
+__global__ void adj_density_kernel(int e_count, int nk, const double2 *__restrict__ lamRho, double scale,
+                                   double2 *__restrict__ lamDiag) {
+  const int total = e_count * nk;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x)
+    lamDiag[i] = c_add(lamDiag[i], c_i(c_scale(scale, lamRho[i / nk])));
+}
+
+// shapes ------------------------------------------------------------------
+struct CoefShape {
+  dim3 grid;
+  int threads, jchunk, nz;
+};
+
+CoefShape coef_shape(const Mesh &m, int n) {
+  CoefShape sh;
+  const long elems = (long)m.nb * m.nb * m.nk;
+  sh.threads = elems >= 256 ? 256 : (int)((elems + 31) / 32) * 32;
+  const long ty = (elems + sh.threads - 1) / sh.threads;
+  const long base = (long)(n + 1) * ty;
+  long nz = ((long)device_sms() * 8 + base - 1) / base;
+  if (nz > n + 1) nz = n + 1;
+  if (nz > 2 + 1024 / (n + 1)) nz = 2 + 1024 / (n + 1);
+  if (nz < 1) nz = 1;
+  sh.jchunk = (int)((n + 1 + nz - 1) / nz);
+  sh.nz = (int)((n + 1 + sh.jchunk - 1) / sh.jchunk);
+  sh.grid = dim3((unsigned)ty, n + 1, (unsigned)sh.nz);
+  return sh;
+}
+
+constexpr int kHistChunk = 32;
+constexpr int kUvMaxSplit = 64;
+
+int uv_splits(const Mesh &m, int n) {
+  const long elems = (long)m.nb * m.nb * m.nk;
+  const long tiles = (elems + 255) / 256;
+  long nz = ((long)device_sms() * 8 + tiles - 1) / tiles;
+  if (nz > n) nz = n;
+  if (nz > kUvMaxSplit) nz = kUvMaxSplit;
+  return nz < 1 ? 1 : (int)nz;
+}
+
+}  // namespace
+
+template <int NB>
+cudaError_t adj_sweep_nb(const Mesh &m, int n, double dt, const double2 *H, const double2 *Sig,
+                         const double2 *lamI, double2 *lamSig, double2 *lamH, double2 *lamRowN,
+                         double2 *coef_work, double2 *c1_work, cudaStream_t st, int quad) {
+  const CoefShape sh = coef_shape(m, n);
+  double2 *out = sh.nz > 1 ? coef_work : lamSig;
+  if (quad == kQuadGregory)
+    adj_coef_kernel<NB, kQuadGregory><<<sh.grid, sh.threads, 0, st>>>(H, lamI, out, n, m.nk, sh.jchunk, dt);
+  else
+    adj_coef_kernel<NB, kQuadTrapezoid><<<sh.grid, sh.threads, 0, st>>>(H, lamI, out, n, m.nk, sh.jchunk, dt);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  adj_c1_kernel<<<grid_for_count((size_t)(n + 1) * blkof(m)), 256, 0, st>>>(Sig, c1_work, n, blkof(m), dt, quad);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int nch = n / kHistChunk + 1;   // chunks covering j' = 0..n
+  const long elems = (long)NB * NB * m.nk;
+  const dim3 hgrid((unsigned)((elems + 255) / 256), n + 1, (unsigned)nch);
+  adj_hist_kernel<NB><<<hgrid, 256, 0, st>>>(Sig, c1_work, lamI, lamH, lamRowN, n, m.nk, kHistChunk, dt, quad);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || sh.nz == 1) return e;
+  const size_t count = (size_t)(n + 1) * 2 * blkof(m);
+  sum_partials_kernel<<<grid_for_count(count), 256, 0, st>>>(coef_work, lamSig, count, sh.nz);
+  return cudaGetLastError();
+}
+
+template <int NB>
+cudaError_t adj_update_nb(const Mesh &m, int n, double dt, double theta, const double2 *h, const double2 *U,
+                          const double2 *V, const double2 *Gprev, const double2 *Ip, const double2 *Ic,
+                          const double2 *lam, double2 *lamGprev, double2 *lamIp, double2 *lamIc, double2 *lamh,
+                          double2 *work, int *status, cudaStream_t st) {
+  const size_t blk = (size_t)NB * NB * m.nk;
+  const size_t total = (size_t)n * 2 * blk;
+  const double2 *ic = theta != 0.0 ? Ic : Ip;
+  double2 *lic = theta != 0.0 ? lamIc : lamIp;
+  adj_rows_kernel<NB><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n, m.nk, theta, U, V, lam, lamGprev,
+                                                                        lamIp, lic);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int nz = uv_splits(m, n);
+  const int jchunk = (n + nz - 1) / nz;
+  const int nzr = (n + jchunk - 1) / jchunk;
+  double2 *part = work;
+  double2 *chain = work + (size_t)kUvMaxSplit * 2 * blk;
+  const long elems = (long)NB * NB * m.nk;
+  adj_uv_kernel<NB><<<dim3((unsigned)((elems + 255) / 256), (unsigned)nzr), 256, 0, st>>>(
+      n, m.nk, theta, lam, Gprev, Ip, ic, part, jchunk);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem = matgroup_smem<NB>(m.nk, 6);
+  adj_diag_kernel<NB><<<matgroup_blocks<NB>(m.nk), matgroup_threads<NB>(m.nk), smem, st>>>(
+      n, m.nk, dt, theta, h, U, Gprev, Ip, ic, lam, part, nzr, lamGprev, lamIp, lic, lamh, chain, status,
+      matgroup_kpc<NB>(m.nk));
+  return cudaGetLastError();
+}
+
+
+template <int NB>
+cudaError_t adj_products_nb(bool pair, const double2 *GR, const double2 *LR, double2 *GLR, int n, int nk, double Un,
+                            const double *Ul_dev, const VMat &vm, double *gpart, cudaStream_t st) {
+  const long total = (long)(n + 1) * NB * nk;
+  const unsigned blocks = (unsigned)((total + 127) / 128);
+  if (pair)
+    sigma_adj_products_pair_kernel<NB><<<blocks, 128, 0, st>>>(GR, LR, GLR, n, nk, Un, Ul_dev, gpart);
+  else
+    sigma_adj_products_kernel<NB><<<blocks, 128, 0, st>>>(GR, LR, GLR, n, nk, Un, Ul_dev, vm, gpart);
+  return cudaGetLastError();
+}
+
+template <int NB>
+cudaError_t adj_hvec_nb(const Mesh &m, const HopTable &hop, const HvecAdj &p, const double2 *lamh, cudaStream_t st) {
+  adj_hvec_kernel<NB><<<1, 256, 0, st>>>(m, hop, p, lamh);
+  return cudaGetLastError();
+}
+
+}  // namespace kbe

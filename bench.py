@@ -81,6 +81,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-autotune", action="store_true",
                    help="skip kbe_autotune (the sweep's l-split chosen by timing before the timed region)")
+    p.add_argument("--sweep-row", type=int, default=None,
+                   help="time the collision sweep alone at this row on random history of c2's and c3's "
+                        "shape, every launch choice of the C64 form, then exit")
+    p.add_argument("--sweep-shapes", default="c2,c3", help="workloads for --sweep-row")
     p.add_argument("--gradient-fd", action="store_true",
                    help="check the c5 gradient (512 steps) by central differences on 16 A_i and U, then exit")
     return p.parse_args()
@@ -640,6 +644,69 @@ class OracleSampler:
         return float(np.sum(3 * np.maximum(np.polyval(ce, xs), 0) + 3 * np.maximum(np.polyval(cu, xs), 0)))
 
 
+def sweep_row_study(kbe, row, names, reps=5):
+    """The collision sweep (Sigma row -> coefficient rows -> sweep -> I row) alone at
+    row `row` on random history of each workload's shape: every launch choice of
+    the C64 form (the single-read tile form at TI = 32, 64, 128 rows per work item;
+    the per-column staged / blocked kernel at its default split) and, at c2, the
+    FP64 and DF64 forms. Time per launch from CUDA events on the launching stream
+    (after 2 untimed launches; the history is larger than L2), algorithmic
+    bytes (the triangle read once in the form's storage, the Sigma row read and
+    the I row written in FP64) per time, and the fraction of the HBM peak."""
+    import torch
+    hbm, hsrc = hbm_peak()
+    stream = torch.cuda.Stream()
+    out = {"row": row, "hbm_peak_gbs": hbm, "hbm_peak_source": hsrc}
+    for name in names:
+        s = ki.config(name)
+        nb, L, nk = s.nb, s.L, s.nk
+        n = min(row, s.nt - 1)
+        blk = nb * nb * nk
+        ntri = (n + 1) * (n + 2) // 2
+        g = torch.Generator(device="cuda").manual_seed(11)
+        sig = torch.randn((n + 1, 2, nb, nb, nk), dtype=torch.complex128, device="cuda", generator=g)
+        I = torch.empty_like(sig)
+        res = {"shape": f"N_b={nb}, n_k={nk}, row n={n}"}
+        forms = ["c64", "fp64", "df64"] if name == "c2" else ["c64"]
+        for form in forms:
+            prec = kbe.PRECISIONS[form]
+            esz = 8 if form == "c64" else 16
+            H = torch.randn(ntri * 2 * blk * esz // 4, dtype=torch.float32, device="cuda", generator=g)
+            w = torch.empty(kbe.collision_row_workspace(nb, L, n, prec) // 4 + 1, dtype=torch.float32, device="cuda")
+            alg = 2.0 * blk * (ntri * esz + 2.0 * (n + 1) * 16.0)
+            choices = [("default", 0)]
+            if form == "c64":
+                choices = [("per_column", 12 if nb >= 4 else 8)]
+                if nb in (2, 4, 8):
+                    choices += [(f"tile_TI{t}", -t) for t in (32, 64, 128)]
+            for label, choice in choices:
+                if choice:
+                    kbe.set_sweep_choice(nb, L, prec, choice)
+                try:
+                    with torch.cuda.stream(stream):
+                        for _ in range(2):
+                            kbe.collision_row(nb, L, n, s.dt, H, sig, I, precision=prec, work=w, stream=stream)
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        for _ in range(reps):
+                            kbe.collision_row(nb, L, n, s.dt, H, sig, I, precision=prec, work=w, stream=stream)
+                        e1.record(stream)
+                        e1.synchronize()
+                    ms = e0.elapsed_time(e1) / reps
+                    gbs = alg / (ms * 1e-3) / 1e9
+                    res[f"{form}_{label}"] = {"ms": ms, "alg_gbs": gbs, "hbm_frac": gbs / hbm}
+                finally:
+                    if choice:
+                        kbe.set_sweep_choice(nb, L, prec, 0)
+            res[f"{form}_alg_bytes"] = alg
+            del H, w
+            torch.cuda.empty_cache()
+        out[name] = res
+        del sig, I
+        torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline(s):
     """The FP64 oracle on the host cores (all of them, and one thread): its
     whole-trajectory c2 rate integrated from timed rows across the trajectory."""
@@ -706,6 +773,14 @@ def main():
     if args.gradient_fd:
         if rank == 0:
             gradient_fd_check(args)
+        return
+    if args.sweep_row is not None:
+        if rank == 0:
+            import torch
+            import paper_2505_19467_gb300 as kbe
+            torch.cuda.set_device(local)
+            print(json.dumps({"sweep_row": sweep_row_study(kbe, args.sweep_row, args.sweep_shapes.split(","))}),
+                  flush=True)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)

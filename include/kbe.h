@@ -329,9 +329,11 @@ kbe_status kbe_batch_set_graphs(kbe_batch *b, int enable);
 kbe_status kbe_device_info(int *binary_version, int *sm_count);
 
 /* Measured FMA throughput of the current device in GFLOP/s (2 flops per
- * FMA): FP64 (fp64_gflops) and FP32 (fp32_gflops), either may be NULL. A
- * grid of 8 CTAs per SM runs independent FMA chains, timed with CUDA events
- * on the default stream (best of three runs after a warm-up; synchronises).
+ * FMA): FP64 (fp64_gflops) and FP32 (fp32_gflops), either may be NULL.
+ * Grids of 4 and 8 CTAs per SM run 4, 8 or 16 independent FMA chains per
+ * thread, timed with CUDA events on the default stream (best of three runs
+ * after a warm-up each; the largest rate of the six configurations; takes
+ * about two seconds and synchronises).
  * These are the denominators of the ALU-bound sweep forms' roofline
  * fractions: the FP64 form on the FP64 pipe, the double-float and complex64
  * forms on the FP32 pipe. Allocates and frees 8 bytes of device memory. */

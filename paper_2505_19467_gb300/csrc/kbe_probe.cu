@@ -3,9 +3,9 @@
 // roofline fractions of the ALU-bound sweep forms (the FP64 sweep is bound by
 // the FP64 pipe, the double-float and complex64 forms by the FP32 pipe).
 //
-// Each thread runs kChains independent FMA chains (enough to cover the pipe's
-// latency) for `iters` rounds; the grid is a multiple of the SM count with
-// several CTAs per SM. The chains' values are folded into one store that the
+// Each thread runs 4, 8 or 16 independent FMA accumulations for `iters`
+// rounds, on a grid of 4 or 8 CTAs of 256 threads per SM; the largest rate of
+// the six configurations is the result. The chains' values are folded into one store that the
 // compiler cannot remove (it happens only if the sum is exactly a sentinel
 // that finite inputs never reach).
 #include <string>
@@ -14,42 +14,43 @@
 
 namespace {
 
-constexpr int kChains = 8;
 constexpr int kThreads = 256;
 
-template <class T>
+// CHAINS independent accumulations per thread, `iters` rounds, in the form the
+// sweep uses the pipe: acc = fma(p, q, acc) with register operands
+template <class T, int CHAINS>
 __global__ void __launch_bounds__(kThreads) fma_probe_kernel(int iters, T a, T b, T *sink) {
-  T x[kChains];
+  T x[CHAINS], p[CHAINS];
+  const T q = b * (T)(1 + (threadIdx.x & 1));
 #pragma unroll
-  for (int c = 0; c < kChains; ++c) x[c] = (T)(threadIdx.x + c) * (T)1e-3;
+  for (int c = 0; c < CHAINS; ++c) {
+    x[c] = (T)(threadIdx.x + c) * (T)1e-3;
+    p[c] = a * (T)(c + 1);
+  }
+#pragma unroll 2
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
-    for (int c = 0; c < kChains; ++c) x[c] = fma(x[c], a, b);
+    for (int c = 0; c < CHAINS; ++c) x[c] = fma(p[c], q, x[c]);
   }
   T s = 0;
 #pragma unroll
-  for (int c = 0; c < kChains; ++c) s += x[c];
+  for (int c = 0; c < CHAINS; ++c) s += x[c];
   if (s == (T)-12345.678) *sink = s;
 }
 
-template <class T>
-cudaError_t run_probe(double *gflops) {
-  const int sms = kbe::device_sms();
-  const unsigned blocks = (unsigned)sms * 8;
-  const int iters = sizeof(T) == 8 ? (1 << 14) : (1 << 18);   // ~50 ms and ~20 ms per run
-  T *sink = nullptr;
-  cudaError_t e = cudaMalloc(&sink, sizeof(T));
-  if (e != cudaSuccess) return e;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  e = cudaEventCreate(&e0);
-  if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  // a and b keep x bounded (|a| < 1): no overflow, no subnormals
-  const T a = (T)0.999, b = (T)1e-4;
+// best of three timed runs (after one untimed) of one configuration, GFLOP/s
+template <class T, int CHAINS>
+cudaError_t probe_config(int ctas_per_sm, T *sink, cudaEvent_t e0, cudaEvent_t e1, double *gflops) {
+  const unsigned blocks = (unsigned)(kbe::device_sms() * ctas_per_sm);
+  // ~80 ms per FP64 run, ~20 ms per FP32 run at the nominal rates
+  const int iters = (sizeof(T) == 8 ? (1 << 20) : (1 << 24)) / (CHAINS * ctas_per_sm);
+  const T a = (T)1e-3, b = (T)1e-3;   // increments of ~1e-6 per round keep x ~ 1: no overflow or subnormals
   float best = 1e30f;
-  for (int r = 0; r < 4 && e == cudaSuccess; ++r) {   // the first round is a warm-up
+  cudaError_t e = cudaSuccess;
+  for (int r = 0; r < 4 && e == cudaSuccess; ++r) {
     e = cudaEventRecord(e0, 0);
     if (e == cudaSuccess) {
-      fma_probe_kernel<T><<<blocks, kThreads>>>(iters, a, b, sink);
+      fma_probe_kernel<T, CHAINS><<<blocks, kThreads>>>(iters, a, b, sink);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
@@ -58,12 +59,35 @@ cudaError_t run_probe(double *gflops) {
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
     if (e == cudaSuccess && r > 0 && ms < best) best = ms;
   }
+  if (e == cudaSuccess) *gflops = 2.0 * CHAINS * (double)iters * kThreads * blocks / (best * 1e-3) / 1e9;
+  return e;
+}
+
+// the largest rate over chain counts and occupancies (a single configuration
+// can sit below the pipe's rate on dependency latency or issue)
+template <class T>
+cudaError_t run_probe(double *gflops) {
+  T *sink = nullptr;
+  cudaError_t e = cudaMalloc(&sink, sizeof(T));
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  double best = 0.0;
+  for (int occ : {4, 8}) {
+    double g = 0.0;
+    if (e == cudaSuccess) e = probe_config<T, 4>(occ, sink, e0, e1, &g);
+    best = g > best ? g : best;
+    if (e == cudaSuccess) e = probe_config<T, 8>(occ, sink, e0, e1, &g);
+    best = g > best ? g : best;
+    if (e == cudaSuccess) e = probe_config<T, 16>(occ, sink, e0, e1, &g);
+    best = g > best ? g : best;
+  }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaFree(sink);
   if (e != cudaSuccess) return e;
-  const double flops = 2.0 * kChains * (double)iters * kThreads * blocks;
-  *gflops = flops / (best * 1e-3) / 1e9;
+  *gflops = best;
   return cudaSuccess;
 }
 

@@ -1215,11 +1215,11 @@ cudaError_t sweep_staged(const Mesh &m, int n, const void *H, const void *Cf, do
 
 // The complex64 sweep's form per row: a negative tuned choice -TI selects the
 // single-read tile kernel with TI rows per work item (kbe_sweep_tile.cu);
-// untuned rows take it from n = 255 on (TI = 64), where its work items fill
+// untuned rows take it from n = 255 on (TI = 32), where its work items fill
 // the GPU. Fault injection always takes the staged kernel.
 constexpr int kTileMinTI = 32;
 int tile_default(const Mesh &m, int prec, int n) {
-  return tile_supported(m, prec) && n >= 255 ? -64 : 0;
+  return tile_supported(m, prec) && n >= 255 ? -32 : 0;
 }
 
 template <int NB>

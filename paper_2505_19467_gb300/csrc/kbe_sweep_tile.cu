@@ -48,29 +48,35 @@ namespace kbe {
 
 namespace {
 
-// per N_b: KT k per CTA (a lane is one (k, a): KT N_b = 32), TMW columns per warp
+// per N_b: KT k per CTA (a lane is one (k, a): KT N_b = 32), TMW columns per
+// warp, W warps (TM = TMW W columns per strip), S stages of the ring, RB row
+// reduction buffers (2: one barrier per row). One CTA of 512 threads per SM:
+// 16 warps at <= 128 registers, so that two warps per scheduler hide the FMA
+// and shared-memory latencies.
 template <int NB>
 struct TileCfg;
 template <>
 struct TileCfg<2> {
-  static constexpr int KT = 16, TMW = 4;
+  static constexpr int KT = 16, TMW = 2, W = 16, S = 3, RB = 2;
 };
 template <>
 struct TileCfg<4> {
-  static constexpr int KT = 8, TMW = 4;
+  static constexpr int KT = 8, TMW = 2, W = 16, S = 3, RB = 1;
 };
 template <>
 struct TileCfg<8> {
-  static constexpr int KT = 4, TMW = 2;
+  static constexpr int KT = 4, TMW = 1, W = 16, S = 2, RB = 2;
 };
 
-constexpr int kTileWarps = 8;
-constexpr int kTileThreads = 32 * kTileWarps;
-constexpr int kTileStages = 3;
+constexpr size_t kTileCounterBytes = 256;   // the work-unit counter ahead of the partial sums
 
 template <int NB>
 __host__ __device__ constexpr int tile_tm() {
-  return TileCfg<NB>::TMW * kTileWarps;
+  return TileCfg<NB>::TMW * TileCfg<NB>::W;
+}
+template <int NB>
+__host__ __device__ constexpr int tile_threads() {
+  return 32 * TileCfg<NB>::W;
 }
 // complex64 values of one stage: the TM blocks [q][x][a b][kk], then C1(i) [a c][kk]
 template <int NB>
@@ -83,16 +89,18 @@ __host__ __device__ constexpr int tile_stage_elems() {
 }
 template <int NB>
 __host__ __device__ constexpr int tile_red_elems() {
-  return kTileWarps * NB * 32;
+  return TileCfg<NB>::W * NB * 32;
 }
 template <int NB>
 constexpr size_t tile_smem_bytes() {
-  return sizeof(float2) * ((size_t)kTileStages * tile_stage_elems<NB>() + tile_red_elems<NB>());
+  return sizeof(float2) * ((size_t)TileCfg<NB>::S * tile_stage_elems<NB>() +
+                           (size_t)TileCfg<NB>::RB * tile_red_elems<NB>());
 }
-static_assert(tile_smem_bytes<2>() <= 227 * 1024 && tile_smem_bytes<4>() <= 227 * 1024 &&
-                  tile_smem_bytes<8>() <= 227 * 1024,
+static_assert(tile_smem_bytes<2>() + 256 <= 227 * 1024 && tile_smem_bytes<4>() + 256 <= 227 * 1024 &&
+                  tile_smem_bytes<8>() + 256 <= 227 * 1024,
               "tile sweep shared memory");
-static_assert((tile_block_elems<4>() * sizeof(float2)) % 128 == 0 && (tile_stage_elems<4>() * sizeof(float2)) % 128 == 0,
+static_assert((tile_block_elems<4>() * sizeof(float2)) % 128 == 0 && (tile_stage_elems<4>() * sizeof(float2)) % 128 == 0 &&
+                  (tile_stage_elems<2>() * sizeof(float2)) % 128 == 0 && (tile_stage_elems<8>() * sizeof(float2)) % 128 == 0,
               "stage alignment");
 
 // acc + x * y, acc - x * y, acc + x * conj(y) on complex64 (FP32 FMAs)
@@ -122,173 +130,192 @@ __device__ __forceinline__ bool tile_item(int p, int n, int TM, int TI, int *s_o
   return false;
 }
 
-// grid: x = k tiles of KT, y = (strip, chunk) work items. CP: column partials
-// [chunk][j][x][a][b][k], RP: row partials [strip][j][a][b][k] (complex64).
+// Persistent: one CTA per SM claims work units from a counter (unit u: k-tile
+// u % ktiles of work item u / ktiles, the k-tiles of one item adjacent so that
+// their DRAM pages are read together); items come strip by strip, so the last
+// units claimed are the short strips near the diagonal's end. The shared-memory
+// ring and its mbarrier phases run on over the units (g = rows consumed so far).
+// CP: column partials [chunk][j][x][a][b][k], RP: row partials [strip][j][a][b][k]
+// (complex64). counter: zeroed before the launch.
 template <int NB, int QUAD>
-__global__ void __launch_bounds__(kTileThreads, 1)
+__global__ void __launch_bounds__(tile_threads<NB>(), 1)
     sweep_tile_kernel(const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmH,
                       const float2 *__restrict__ Cf, float2 *__restrict__ CP, float2 *__restrict__ RP, int n,
-                      int nk, int TI, const int *__restrict__ skip, int *status) {
+                      int nk, int TI, int units, int *counter, const int *__restrict__ skip, int *status) {
   if (skip && *skip) return;
   constexpr int KT = TileCfg<NB>::KT, TMW = TileCfg<NB>::TMW, TM = tile_tm<NB>(), NB2 = NB * NB;
-  constexpr int SE = tile_stage_elems<NB>(), BE = tile_block_elems<NB>();
+  constexpr int SE = tile_stage_elems<NB>(), BE = tile_block_elems<NB>(), RB = TileCfg<NB>::RB;
+  constexpr int kStg = TileCfg<NB>::S, kW = TileCfg<NB>::W;
   constexpr unsigned kBytesH = (unsigned)BE * sizeof(float2), kBytesC = (unsigned)NB2 * KT * sizeof(float2);
   extern __shared__ __align__(128) float4 tile_smem4[];
-  __shared__ __align__(8) uint64_t bar[kTileStages];
-  __shared__ int failed;
+  __shared__ __align__(8) uint64_t bar[kStg];
+  __shared__ int failed, s_unit;
   float2 *smem = reinterpret_cast<float2 *>(tile_smem4);
-  float2 *red = smem + (size_t)kTileStages * SE;
-
-  int s = 0, c = 0;
-  if (!tile_item(blockIdx.y, n, TM, TI, &s, &c)) return;
-  const int M0 = s * TM, R0 = M0 + c * TI, R1 = min(M0 + (c + 1) * TI, n + 1);
-  const int rows = R1 - R0;
-  const int k0 = blockIdx.x * KT;
+  float2 *redbase = smem + (size_t)kStg * SE;
+  const int ktiles = (nk + KT - 1) / KT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kk = lane % KT, a = lane / KT;
-  const int k = k0 + kk;
-  const bool kvalid = k < nk;
   const size_t blk = (size_t)NB2 * nk;
 
-  // C1(m), C2^<(m) of this lane's columns (row a, this k), kept for the chunk
-  float2 C1m[TMW][NB], C2m[TMW][NB];
-#pragma unroll
-  for (int q = 0; q < TMW; ++q) {
-    const int m = M0 + warp * TMW + q;
-#pragma unroll
-    for (int cc = 0; cc < NB; ++cc) {
-      const bool ok = m <= n && kvalid;
-      const size_t o = (size_t)(a * NB + cc) * nk + k;
-      C1m[q][cc] = ok ? Cf[(size_t)m * 3 * blk + o] : make_float2(0.f, 0.f);
-      C2m[q][cc] = ok ? Cf[((size_t)m * 3 + 1) * blk + o] : make_float2(0.f, 0.f);
-    }
-  }
-  float2 X[TMW][NB], Y[TMW][NB];   // column use: X(m)_{a,b}, Y(m)_{a,b}
-#pragma unroll
-  for (int q = 0; q < TMW; ++q)
-#pragma unroll
-    for (int b = 0; b < NB; ++b) X[q][b] = Y[q][b] = make_float2(0.f, 0.f);
-
   if (threadIdx.x == 0) {
-    for (int st = 0; st < kTileStages; ++st) mbar_init(&bar[st], 1);
+    for (int st = 0; st < kStg; ++st) mbar_init(&bar[st], 1);
     failed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();
-  auto issue = [&](int r) {   // row R0 + r into stage r % kTileStages (thread 0)
-    const int i = R0 + r, st = r % kTileStages;
-    float2 *dst = smem + (size_t)st * SE;
-    mbar_expect_tx(&bar[st], kBytesH + kBytesC);
-    tma_load_4d(dst, &tmH, 2 * k0, 0, 0, (int)tri(i, M0), &bar[st]);
-    tma_load_3d(dst + BE, &tmC, 2 * k0, 0, 3 * i, &bar[st]);
-  };
-  if (threadIdx.x == 0)
-    for (int r = 0; r < kTileStages - 1 && r < rows; ++r) issue(r);
-  int issued = min(kTileStages - 1, rows);
-
-  for (int r = 0; r < rows; ++r) {
-    if (threadIdx.x == 0 && issued < rows && issued == r + kTileStages - 1) issue(issued);
-    issued = min(r + kTileStages, rows);
-    const int st = r % kTileStages;
-    if (!mbar_wait(&bar[st], (unsigned)((r / kTileStages) & 1), kMbarWaitLimit)) failed = 1;
+  int g0 = 0;   // rows this CTA consumed in earlier units
+  for (;;) {
+    if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
     __syncthreads();
-    if (failed) {   // a copy did not arrive: flag it, let the in-flight ones land, stop
-      if (threadIdx.x == 0) {
-        int code = kDevTimeout;
-        for (int q = r; q < issued; ++q)
-          if (!mbar_wait(&bar[q % kTileStages], (unsigned)((q / kTileStages) & 1), kMbarWaitLimit))
-            code |= kDevTimeoutDrain;
-        if (status) atomicOr(status, code);
-      }
-      __syncthreads();
-      return;
-    }
-    const int i = R0 + r;
-    const float2 *stg = smem + (size_t)st * SE;
-    float2 C1i[NB];
-#pragma unroll
-    for (int cc = 0; cc < NB; ++cc) C1i[cc] = stg[BE + (a * NB + cc) * KT + kk];
-    float2 T[NB];   // row use, summed over this warp's columns: X(i)_{a,cc} = -T[cc]
-#pragma unroll
-    for (int cc = 0; cc < NB; ++cc) T[cc] = make_float2(0.f, 0.f);
+    const int unit = s_unit;
+    if (unit >= units) break;
+    int s = 0, c = 0;
+    if (!tile_item(unit / ktiles, n, TM, TI, &s, &c)) break;   // cannot happen: units = ktiles x items
+    const int M0 = s * TM, R0 = M0 + c * TI, R1 = min(M0 + (c + 1) * TI, n + 1);
+    const int rows = R1 - R0;
+    const int k0 = (unit % ktiles) * KT;
+    const int k = k0 + kk;
+    const bool kvalid = k < nk;
+
+    // C1(m), C2^<(m) of this lane's columns (row a, this k), kept for the unit
+    float2 C1m[TMW][NB], C2m[TMW][NB];
 #pragma unroll
     for (int q = 0; q < TMW; ++q) {
       const int m = M0 + warp * TMW + q;
-      if (m > i) continue;   // past the diagonal (warp-uniform)
-      const float2 *B = stg + (size_t)(warp * TMW + q) * 2 * NB2 * KT + kk;   // [x][r s][kk]
-      if (m < i) {
-        const float f = (float)quad_omega(QUAD, i, m);
-        float2 K2[NB];
 #pragma unroll
-        for (int b = 0; b < NB; ++b) K2[b] = f == 1.0f ? C2m[q][b] : make_float2(f * C2m[q][b].x, f * C2m[q][b].y);
+      for (int cc = 0; cc < NB; ++cc) {
+        const bool ok = m <= n && kvalid;
+        const size_t o = (size_t)(a * NB + cc) * nk + k;
+        C1m[q][cc] = ok ? Cf[(size_t)m * 3 * blk + o] : make_float2(0.f, 0.f);
+        C2m[q][cc] = ok ? Cf[((size_t)m * 3 + 1) * blk + o] : make_float2(0.f, 0.f);
+      }
+    }
+    float2 X[TMW][NB], Y[TMW][NB];   // column use: X(m)_{a,b}, Y(m)_{a,b}
 #pragma unroll
-        for (int cc = 0; cc < NB; ++cc)
+    for (int q = 0; q < TMW; ++q)
 #pragma unroll
-          for (int b = 0; b < NB; ++b) {
-            const float2 x = B[(cc * NB + b) * KT], d = B[(NB2 + cc * NB + b) * KT];
-            X[q][b] = f_fma(C1i[cc], x, X[q][b]);
-            Y[q][b] = f_fnma(C1i[cc], d, Y[q][b]);
-            T[cc] = f_fmac(C1m[q][b], x, T[cc]);
-            T[cc] = f_fmac(K2[b], d, T[cc]);
+      for (int b = 0; b < NB; ++b) X[q][b] = Y[q][b] = make_float2(0.f, 0.f);
+
+    auto issue = [&](int r) {   // row R0 + r (the CTA's row g0 + r) into stage (g0 + r) % kStg
+      const int i = R0 + r, st = (g0 + r) % kStg;
+      float2 *dst = smem + (size_t)st * SE;
+      mbar_expect_tx(&bar[st], kBytesH + kBytesC);
+      tma_load_4d(dst, &tmH, 2 * k0, 0, 0, (int)tri(i, M0), &bar[st]);
+      tma_load_3d(dst + BE, &tmC, 2 * k0, 0, 3 * i, &bar[st]);
+    };
+    if (threadIdx.x == 0)
+      for (int r = 0; r < kStg - 1 && r < rows; ++r) issue(r);
+    int issued = min(kStg - 1, rows);
+
+    for (int r = 0; r < rows; ++r) {
+      const int g = g0 + r;   // the ring's stage and phase
+      if (threadIdx.x == 0 && issued < rows && issued == r + kStg - 1) issue(issued);
+      issued = min(r + kStg, rows);
+      const int st = g % kStg;
+      if (!mbar_wait(&bar[st], (unsigned)((g / kStg) & 1), kMbarWaitLimit)) failed = 1;
+      __syncthreads();
+      if (failed) {   // a copy did not arrive: flag it, let the in-flight ones land, stop
+        if (threadIdx.x == 0) {
+          int code = kDevTimeout;
+          for (int q = r; q < issued; ++q) {
+            const int gq = g0 + q;
+            if (!mbar_wait(&bar[gq % kStg], (unsigned)((gq / kStg) & 1), kMbarWaitLimit))
+              code |= kDevTimeoutDrain;
           }
-      } else if (i == 0) {   // the only node of column 0 on the diagonal: above the output
+          if (status) atomicOr(status, code);
+        }
+        __syncthreads();
+        return;
+      }
+      const int i = R0 + r;
+      const float2 *stg = smem + (size_t)st * SE;
+      float2 C1i[NB];
 #pragma unroll
-        for (int cc = 0; cc < NB; ++cc)
+      for (int cc = 0; cc < NB; ++cc) C1i[cc] = stg[BE + (a * NB + cc) * KT + kk];
+      float2 T[NB];   // row use, summed over this warp's columns: X(i)_{a,cc} = -T[cc]
 #pragma unroll
-          for (int b = 0; b < NB; ++b) {
-            const float2 x = B[(cc * NB + b) * KT], d = B[(NB2 + cc * NB + b) * KT];
-            X[q][b] = f_fma(C1i[cc], x, X[q][b]);
-            Y[q][b] = f_fnma(C1i[cc], d, Y[q][b]);
-          }
-      } else {   // end node l = j of column j = i: weight f, Y coefficient f (C3 - C2^<) + (f - 1) C1
-        const float f = (float)quad_omega(QUAD, i, i);
+      for (int cc = 0; cc < NB; ++cc) T[cc] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int cc = 0; cc < NB; ++cc) {
-          const float2 k3 = kvalid ? Cf[((size_t)i * 3 + 2) * blk + (size_t)(a * NB + cc) * nk + k]
-                                   : make_float2(0.f, 0.f);
-          const float2 k2 = C2m[q][cc], k1 = C1i[cc];
-          const float2 K2 = make_float2(f * k2.x, f * k2.y);
-          const float2 KY = make_float2(f * (k3.x - k2.x) + (f - 1.0f) * k1.x, f * (k3.y - k2.y) + (f - 1.0f) * k1.y);
+      for (int q = 0; q < TMW; ++q) {
+        const int m = M0 + warp * TMW + q;
+        if (m > i) continue;   // past the diagonal (warp-uniform)
+        const float2 *B = stg + (size_t)(warp * TMW + q) * 2 * NB2 * KT + kk;   // [x][r s][kk]
+        if (m < i) {
+          const float f = (float)quad_omega(QUAD, i, m);
+          float2 K2[NB];
 #pragma unroll
-          for (int b = 0; b < NB; ++b) {
-            const float2 x = B[(cc * NB + b) * KT], d = B[(NB2 + cc * NB + b) * KT];
-            X[q][b] = f_fma(k1, x, X[q][b]);
-            X[q][b] = f_fma(K2, d, X[q][b]);
-            Y[q][b] = f_fma(KY, d, Y[q][b]);
+          for (int b = 0; b < NB; ++b) K2[b] = f == 1.0f ? C2m[q][b] : make_float2(f * C2m[q][b].x, f * C2m[q][b].y);
+#pragma unroll
+          for (int cc = 0; cc < NB; ++cc)
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+              const float2 x = B[(cc * NB + b) * KT], d = B[(NB2 + cc * NB + b) * KT];
+              X[q][b] = f_fma(C1i[cc], x, X[q][b]);
+              Y[q][b] = f_fnma(C1i[cc], d, Y[q][b]);
+              T[cc] = f_fmac(C1m[q][b], x, T[cc]);
+              T[cc] = f_fmac(K2[b], d, T[cc]);
+            }
+        } else if (i == 0) {   // the only node of column 0 on the diagonal: above the output
+#pragma unroll
+          for (int cc = 0; cc < NB; ++cc)
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+              const float2 x = B[(cc * NB + b) * KT], d = B[(NB2 + cc * NB + b) * KT];
+              X[q][b] = f_fma(C1i[cc], x, X[q][b]);
+              Y[q][b] = f_fnma(C1i[cc], d, Y[q][b]);
+            }
+        } else {   // end node l = j of column j = i: weight f, Y coefficient f (C3 - C2^<) + (f - 1) C1
+          const float f = (float)quad_omega(QUAD, i, i);
+#pragma unroll
+          for (int cc = 0; cc < NB; ++cc) {
+            const float2 k3 = kvalid ? Cf[((size_t)i * 3 + 2) * blk + (size_t)(a * NB + cc) * nk + k]
+                                     : make_float2(0.f, 0.f);
+            const float2 k2 = C2m[q][cc], k1 = C1i[cc];
+            const float2 K2 = make_float2(f * k2.x, f * k2.y);
+            const float2 KY = make_float2(f * (k3.x - k2.x) + (f - 1.0f) * k1.x, f * (k3.y - k2.y) + (f - 1.0f) * k1.y);
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+              const float2 x = B[(cc * NB + b) * KT], d = B[(NB2 + cc * NB + b) * KT];
+              X[q][b] = f_fma(k1, x, X[q][b]);
+              X[q][b] = f_fma(K2, d, X[q][b]);
+              Y[q][b] = f_fma(KY, d, Y[q][b]);
+            }
           }
         }
       }
-    }
-    // the warps' row-use shares: red[w][cc][a][kk], summed by the first NB * 32 threads
+      // the warps' row-use shares: red[w][cc][a][kk], summed by the first NB * 32 threads
+      float2 *red = redbase + (size_t)(g % RB) * tile_red_elems<NB>();
 #pragma unroll
-    for (int cc = 0; cc < NB; ++cc) red[((warp * NB + cc) * NB + a) * KT + kk] = T[cc];
-    __syncthreads();
-    if (threadIdx.x < NB * 32) {
-      const int t = threadIdx.x;   // (a', cc', kk') with kk' fastest: coalesced writes
-      const int kk2 = t % KT, ac = t / KT, cc2 = ac % NB, a2 = ac / NB;
-      float2 sum = make_float2(0.f, 0.f);
+      for (int cc = 0; cc < NB; ++cc) red[((warp * NB + cc) * NB + a) * KT + kk] = T[cc];
+      __syncthreads();   // the stage is consumed and the shares are written
+      if (threadIdx.x < NB * 32) {
+        const int t = threadIdx.x;   // (a', cc', kk') with kk' fastest: coalesced writes
+        const int kk2 = t % KT, ac = t / KT, cc2 = ac % NB, a2 = ac / NB;
+        float2 sum = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int w = 0; w < kTileWarps; ++w) {
-        const float2 v = red[((w * NB + cc2) * NB + a2) * KT + kk2];
-        sum.x += v.x;
-        sum.y += v.y;
+        for (int w = 0; w < kW; ++w) {
+          const float2 v = red[((w * NB + cc2) * NB + a2) * KT + kk2];
+          sum.x += v.x;
+          sum.y += v.y;
+        }
+        const int k2 = k0 + kk2;
+        if (k2 < nk)
+          RP[(((size_t)s * (n + 1) + i) * NB2 + a2 * NB + cc2) * nk + k2] = make_float2(-sum.x, -sum.y);
       }
-      const int k2 = k0 + kk2;
-      if (k2 < nk)
-        RP[(((size_t)s * (n + 1) + i) * NB2 + a2 * NB + cc2) * nk + k2] = make_float2(-sum.x, -sum.y);
+      if (RB == 1) __syncthreads();   // single buffer: its sums are read before the next row writes it
     }
-    __syncthreads();   // the stage and the reduction buffer are free again
-  }
-  // column partials of this chunk
+    g0 += rows;
+    // column partials of this unit's chunk
 #pragma unroll
-  for (int q = 0; q < TMW; ++q) {
-    const int m = M0 + warp * TMW + q;
-    if (m > n || !kvalid) continue;
+    for (int q = 0; q < TMW; ++q) {
+      const int m = M0 + warp * TMW + q;
+      if (m > n || !kvalid) continue;
 #pragma unroll
-    for (int b = 0; b < NB; ++b) {
-      const size_t o = (size_t)(a * NB + b) * nk + k;
-      CP[(((size_t)c * (n + 1) + m) * 2) * blk + o] = X[q][b];
-      CP[(((size_t)c * (n + 1) + m) * 2 + 1) * blk + o] = Y[q][b];
+      for (int b = 0; b < NB; ++b) {
+        const size_t o = (size_t)(a * NB + b) * nk + k;
+        CP[(((size_t)c * (n + 1) + m) * 2) * blk + o] = X[q][b];
+        CP[(((size_t)c * (n + 1) + m) * 2 + 1) * blk + o] = Y[q][b];
+      }
     }
   }
 }
@@ -422,16 +449,22 @@ cudaError_t tile_launch(const Mesh &m, int n, const void *H, const void *Cf, dou
   if (!tile_maps<NB>(Cf, H, n, m.nk, &tmC, &tmH)) return cudaErrorNotSupported;
   constexpr int TM = tile_tm<NB>(), KT = TileCfg<NB>::KT;
   const size_t blk = (size_t)NB * NB * m.nk;
-  float2 *CP = (float2 *)part;
+  int *counter = (int *)part;   // the work-unit counter, then the partial sums
+  float2 *CP = (float2 *)((char *)part + kTileCounterBytes);
   float2 *RP = CP + (size_t)((n + TI) / TI) * (n + 1) * 2 * blk;
-  const dim3 grid((unsigned)((m.nk + KT - 1) / KT), (unsigned)tile_items(n, TM, TI));
+  const long units = (long)((m.nk + KT - 1) / KT) * tile_items(n, TM, TI);
+  const long sms = device_sms();
+  const unsigned grid = (unsigned)(units < sms ? units : sms);
   const size_t smem = tile_smem_bytes<NB>();
+  e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
   if (quad == kQuadGregory)
-    sweep_tile_kernel<NB, kQuadGregory><<<grid, kTileThreads, smem, st>>>(tmC, tmH, (const float2 *)Cf, CP, RP, n,
-                                                                          m.nk, TI, skip, status);
+    sweep_tile_kernel<NB, kQuadGregory><<<grid, tile_threads<NB>(), smem, st>>>(tmC, tmH, (const float2 *)Cf, CP, RP, n,
+                                                                          m.nk, TI, (int)units, counter, skip, status);
   else
-    sweep_tile_kernel<NB, kQuadTrapezoid><<<grid, kTileThreads, smem, st>>>(tmC, tmH, (const float2 *)Cf, CP, RP,
-                                                                            n, m.nk, TI, skip, status);
+    sweep_tile_kernel<NB, kQuadTrapezoid><<<grid, tile_threads<NB>(), smem, st>>>(tmC, tmH, (const float2 *)Cf, CP, RP,
+                                                                            n, m.nk, TI, (int)units, counter, skip,
+                                                                            status);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t count = (size_t)(n + 1) * blk;
@@ -459,7 +492,7 @@ size_t tile_part_bytes(const Mesh &m, int n, int TI) {
   const int TM = tile_tm_of(m.nb);
   const size_t cp = (size_t)((n + TI) / TI) * (n + 1) * 2 * blk;
   const size_t rp = (size_t)((n + TM) / TM) * (n + 1) * blk;
-  return (cp + rp) * sizeof(float2);
+  return kTileCounterBytes + (cp + rp) * sizeof(float2);
 }
 
 cudaError_t tile_prepare(int nb) {

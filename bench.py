@@ -679,6 +679,7 @@ def sweep_row_study(kbe, row, names, reps=5):
                 choices = [("per_column", 12 if nb >= 4 else 8)]
                 if nb in (2, 4, 8):
                     choices += [(f"tile_TI{t}", -t) for t in (32, 64, 128)]
+                    choices += [(f"tile_TI{t}_one_unit_per_cta", -(t + 1)) for t in (32, 64, 128)]
             for label, choice in choices:
                 if choice:
                     kbe.set_sweep_choice(nb, L, prec, choice)

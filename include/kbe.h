@@ -331,9 +331,10 @@ kbe_status kbe_device_info(int *binary_version, int *sm_count);
 /* Measured FMA throughput of the current device in GFLOP/s (2 flops per
  * FMA): FP64 (fp64_gflops) and FP32 (fp32_gflops), either may be NULL.
  * Grids of 4 and 8 CTAs per SM run 4, 8 or 16 independent FMA chains per
- * thread, timed with CUDA events on the default stream (best of three runs
- * after a warm-up each; the largest rate of the six configurations; takes
- * about two seconds and synchronises).
+ * thread in two forms (accumulation with register operands; iteration),
+ * timed with CUDA events on the default stream (best of three runs after a
+ * warm-up each; the largest rate of the twelve configurations; takes a few
+ * seconds and synchronises).
  * These are the denominators of the ALU-bound sweep forms' roofline
  * fractions: the FP64 form on the FP64 pipe, the double-float and complex64
  * forms on the FP32 pipe. Allocates and frees 8 bytes of device memory. */
@@ -364,9 +365,11 @@ typedef struct kbe_mesh {
  *   choice > 0 (<= 64): the per-column sweep, its l-split aiming at `choice`
  *                       CTAs per SM;
  *   choice < 0:         the single-read tile sweep (KBE_PREC_C64, N_b in
- *                       {2, 4, 8}, n_k even), -choice >= 32 rows per work
- *                       item: each stored block is read from HBM once and
- *                       feeds both of its uses;
+ *                       {2, 4, 8}, n_k even), TI = -choice rows per work
+ *                       item (TI >= 32; an odd -choice means -choice - 1 rows
+ *                       with one CTA per work unit instead of persistent CTAs
+ *                       that claim units): each stored block is read from HBM
+ *                       once and feeds both of its uses;
  *   choice = 0:         back to the built-in default (the tile sweep from
  *                       row 255 on where it applies).
  * The choice changes the summation order only. KBE_ERR_ARG if the choice does

@@ -3,9 +3,11 @@
 // roofline fractions of the ALU-bound sweep forms (the FP64 sweep is bound by
 // the FP64 pipe, the double-float and complex64 forms by the FP32 pipe).
 //
-// Each thread runs 4, 8 or 16 independent FMA accumulations for `iters`
-// rounds, on a grid of 4 or 8 CTAs of 256 threads per SM; the largest rate of
-// the six configurations is the result. The chains' values are folded into one store that the
+// Each thread runs 4, 8 or 16 independent FMA chains for `iters` rounds, in
+// two forms (accumulation with register operands, and iteration), on a grid of
+// 4 or 8 CTAs of 256 threads per SM; the largest rate of the twelve
+// configurations is the result (a single one can sit below the pipe's rate on
+// dependency latency or operand handling). The chains' values are folded into one store that the
 // compiler cannot remove (it happens only if the sum is exactly a sentinel
 // that finite inputs never reach).
 #include <string>
@@ -16,9 +18,10 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// CHAINS independent accumulations per thread, `iters` rounds, in the form the
-// sweep uses the pipe: acc = fma(p, q, acc) with register operands
-template <class T, int CHAINS>
+// CHAINS independent chains per thread, `iters` rounds, in one of two forms:
+// ACC = 1 accumulates (acc = fma(p, q, acc), register operands, as the sweep
+// uses the pipe), ACC = 0 iterates x = fma(x, a, b). Both stay bounded.
+template <class T, int CHAINS, int ACC>
 __global__ void __launch_bounds__(kThreads) fma_probe_kernel(int iters, T a, T b, T *sink) {
   T x[CHAINS], p[CHAINS];
   const T q = b * (T)(1 + (threadIdx.x & 1));
@@ -30,7 +33,7 @@ __global__ void __launch_bounds__(kThreads) fma_probe_kernel(int iters, T a, T b
 #pragma unroll 2
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
-    for (int c = 0; c < CHAINS; ++c) x[c] = fma(p[c], q, x[c]);
+    for (int c = 0; c < CHAINS; ++c) x[c] = ACC ? fma(p[c], q, x[c]) : fma(x[c], (T)0.999, q);
   }
   T s = 0;
 #pragma unroll
@@ -39,18 +42,18 @@ __global__ void __launch_bounds__(kThreads) fma_probe_kernel(int iters, T a, T b
 }
 
 // best of three timed runs (after one untimed) of one configuration, GFLOP/s
-template <class T, int CHAINS>
+template <class T, int CHAINS, int ACC>
 cudaError_t probe_config(int ctas_per_sm, T *sink, cudaEvent_t e0, cudaEvent_t e1, double *gflops) {
   const unsigned blocks = (unsigned)(kbe::device_sms() * ctas_per_sm);
   // ~80 ms per FP64 run, ~20 ms per FP32 run at the nominal rates
   const int iters = (sizeof(T) == 8 ? (1 << 20) : (1 << 24)) / (CHAINS * ctas_per_sm);
-  const T a = (T)1e-3, b = (T)1e-3;   // increments of ~1e-6 per round keep x ~ 1: no overflow or subnormals
+  const T a = (T)1e-3, b = (T)1e-3;   // x stays ~ 1 in both forms: no overflow or subnormals
   float best = 1e30f;
   cudaError_t e = cudaSuccess;
   for (int r = 0; r < 4 && e == cudaSuccess; ++r) {
     e = cudaEventRecord(e0, 0);
     if (e == cudaSuccess) {
-      fma_probe_kernel<T, CHAINS><<<blocks, kThreads>>>(iters, a, b, sink);
+      fma_probe_kernel<T, CHAINS, ACC><<<blocks, kThreads>>>(iters, a, b, sink);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
@@ -75,13 +78,14 @@ cudaError_t run_probe(double *gflops) {
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   double best = 0.0;
   for (int occ : {4, 8}) {
-    double g = 0.0;
-    if (e == cudaSuccess) e = probe_config<T, 4>(occ, sink, e0, e1, &g);
-    best = g > best ? g : best;
-    if (e == cudaSuccess) e = probe_config<T, 8>(occ, sink, e0, e1, &g);
-    best = g > best ? g : best;
-    if (e == cudaSuccess) e = probe_config<T, 16>(occ, sink, e0, e1, &g);
-    best = g > best ? g : best;
+    double g[6] = {0, 0, 0, 0, 0, 0};
+    if (e == cudaSuccess) e = probe_config<T, 4, 1>(occ, sink, e0, e1, &g[0]);
+    if (e == cudaSuccess) e = probe_config<T, 8, 1>(occ, sink, e0, e1, &g[1]);
+    if (e == cudaSuccess) e = probe_config<T, 16, 1>(occ, sink, e0, e1, &g[2]);
+    if (e == cudaSuccess) e = probe_config<T, 4, 0>(occ, sink, e0, e1, &g[3]);
+    if (e == cudaSuccess) e = probe_config<T, 8, 0>(occ, sink, e0, e1, &g[4]);
+    if (e == cudaSuccess) e = probe_config<T, 16, 0>(occ, sink, e0, e1, &g[5]);
+    for (double x : g) best = x > best ? x : best;
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);

@@ -1332,8 +1332,11 @@ cudaError_t tune_sweep(const Mesh &m, int prec, int quad, int nmax, double dt, c
                        double2 *I, void *work, cudaStream_t st, int *out, int nout) {
   const bool staged = use_staged(m, prec);
   std::vector<int> cands = staged ? std::vector<int>{3, 6, 12, 24} : std::vector<int>{2, 4, 8, 16, 32};
-  if (tile_supported(m, prec))   // the single-read tile form, TI rows per work item
-    for (int ti : {kTileMinTI, 64, 128}) cands.push_back(-ti);
+  if (tile_supported(m, prec))   // the single-read tile form, TI rows per work item (odd: one CTA per unit)
+    for (int ti : {kTileMinTI, 64, 128}) {
+      cands.push_back(-ti);
+      cands.push_back(-(ti + 1));
+    }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return cudaErrorUnknown;
   cudaError_t err = cudaSuccess;

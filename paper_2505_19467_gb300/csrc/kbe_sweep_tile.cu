@@ -50,22 +50,24 @@ namespace {
 
 // per N_b: KT k per CTA (a lane is one (k, a): KT N_b = 32), TMW columns per
 // warp, W warps (TM = TMW W columns per strip), S stages of the ring, RB row
-// reduction buffers (2: one barrier per row). One CTA of 512 threads per SM:
-// 16 warps at <= 128 registers, so that two warps per scheduler hide the FMA
-// and shared-memory latencies.
+// reduction buffers (2: one barrier per row). One CTA of 8 warps per SM (its
+// shared memory): four columns per warp amortise the per-row work (the C1(i)
+// row, the reduction of the row use over the warps, the barrier) over four
+// blocks. (Timed: 16 warps of two columns each at <= 128 registers ran 20 %
+// slower at row 511 of c2, on barrier and dispatch stalls.)
 template <int NB>
 struct TileCfg;
 template <>
 struct TileCfg<2> {
-  static constexpr int KT = 16, TMW = 2, W = 16, S = 3, RB = 2;
+  static constexpr int KT = 16, TMW = 4, W = 8, S = 3, RB = 2;
 };
 template <>
 struct TileCfg<4> {
-  static constexpr int KT = 8, TMW = 2, W = 16, S = 3, RB = 1;
+  static constexpr int KT = 8, TMW = 4, W = 8, S = 3, RB = 2;
 };
 template <>
 struct TileCfg<8> {
-  static constexpr int KT = 4, TMW = 1, W = 16, S = 2, RB = 2;
+  static constexpr int KT = 4, TMW = 2, W = 8, S = 3, RB = 1;
 };
 
 constexpr size_t kTileCounterBytes = 256;   // the work-unit counter ahead of the partial sums
@@ -130,18 +132,20 @@ __device__ __forceinline__ bool tile_item(int p, int n, int TM, int TI, int *s_o
   return false;
 }
 
-// Persistent: one CTA per SM claims work units from a counter (unit u: k-tile
-// u % ktiles of work item u / ktiles, the k-tiles of one item adjacent so that
-// their DRAM pages are read together); items come strip by strip, so the last
-// units claimed are the short strips near the diagonal's end. The shared-memory
-// ring and its mbarrier phases run on over the units (g = rows consumed so far).
+// Work unit u: k-tile u % ktiles of work item u / ktiles (the k-tiles of one
+// item adjacent, so that their DRAM pages are read together); items come strip
+// by strip, so the last units are the short strips near the diagonal's end.
+// persistent != 0: one CTA per SM claims units from a counter; the
+// shared-memory ring and its mbarrier phases run on over the units (g = rows
+// consumed so far). Otherwise one CTA per unit.
 // CP: column partials [chunk][j][x][a][b][k], RP: row partials [strip][j][a][b][k]
 // (complex64). counter: zeroed before the launch.
 template <int NB, int QUAD>
 __global__ void __launch_bounds__(tile_threads<NB>(), 1)
     sweep_tile_kernel(const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmH,
                       const float2 *__restrict__ Cf, float2 *__restrict__ CP, float2 *__restrict__ RP, int n,
-                      int nk, int TI, int units, int *counter, const int *__restrict__ skip, int *status) {
+                      int nk, int TI, int units, int *counter, int persistent, const int *__restrict__ skip,
+                      int *status) {
   if (skip && *skip) return;
   constexpr int KT = TileCfg<NB>::KT, TMW = TileCfg<NB>::TMW, TM = tile_tm<NB>(), NB2 = NB * NB;
   constexpr int SE = tile_stage_elems<NB>(), BE = tile_block_elems<NB>(), RB = TileCfg<NB>::RB;
@@ -164,9 +168,14 @@ __global__ void __launch_bounds__(tile_threads<NB>(), 1)
   }
   __syncthreads();
   int g0 = 0;   // rows this CTA consumed in earlier units
-  for (;;) {
-    if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
-    __syncthreads();
+  for (int pass = 0;; ++pass) {
+    if (persistent) {
+      if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
+      __syncthreads();
+    } else if (threadIdx.x == 0) {
+      s_unit = pass == 0 ? (int)blockIdx.x : units;   // one unit per CTA
+    }
+    if (!persistent) __syncthreads();
     const int unit = s_unit;
     if (unit >= units) break;
     int s = 0, c = 0;
@@ -442,7 +451,7 @@ long tile_items(int n, int TM, int TI) {
 
 template <int NB>
 cudaError_t tile_launch(const Mesh &m, int n, const void *H, const void *Cf, double2 *I, void *part,
-                        cudaStream_t st, const int *skip, int quad, int *status, int TI) {
+                        cudaStream_t st, const int *skip, int quad, int *status, int TI, bool persistent) {
   cudaError_t e = tile_prepare_nb<NB>();
   if (e != cudaSuccess) return e;
   CUtensorMap tmC, tmH;
@@ -454,17 +463,18 @@ cudaError_t tile_launch(const Mesh &m, int n, const void *H, const void *Cf, dou
   float2 *RP = CP + (size_t)((n + TI) / TI) * (n + 1) * 2 * blk;
   const long units = (long)((m.nk + KT - 1) / KT) * tile_items(n, TM, TI);
   const long sms = device_sms();
-  const unsigned grid = (unsigned)(units < sms ? units : sms);
+  const unsigned grid = persistent ? (unsigned)(units < sms ? units : sms) : (unsigned)units;
   const size_t smem = tile_smem_bytes<NB>();
   e = cudaMemsetAsync(counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   if (quad == kQuadGregory)
     sweep_tile_kernel<NB, kQuadGregory><<<grid, tile_threads<NB>(), smem, st>>>(tmC, tmH, (const float2 *)Cf, CP, RP, n,
-                                                                          m.nk, TI, (int)units, counter, skip, status);
+                                                                          m.nk, TI, (int)units, counter,
+                                                                          persistent ? 1 : 0, skip, status);
   else
     sweep_tile_kernel<NB, kQuadTrapezoid><<<grid, tile_threads<NB>(), smem, st>>>(tmC, tmH, (const float2 *)Cf, CP, RP,
-                                                                            n, m.nk, TI, (int)units, counter, skip,
-                                                                            status);
+                                                                            n, m.nk, TI, (int)units, counter,
+                                                                            persistent ? 1 : 0, skip, status);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t count = (size_t)(n + 1) * blk;
@@ -506,10 +516,12 @@ cudaError_t tile_prepare(int nb) {
 
 cudaError_t launch_sweep_tile(const Mesh &m, int n, const void *H, const void *Cf, double2 *I, void *part,
                               cudaStream_t st, const int *skip, int quad, int *status, int TI) {
+  const bool persistent = (TI & 1) == 0;   // an odd TI asks for one CTA per work unit (TI - 1 rows)
+  TI &= ~1;
   switch (m.nb) {
-    case 2: return tile_launch<2>(m, n, H, Cf, I, part, st, skip, quad, status, TI);
-    case 4: return tile_launch<4>(m, n, H, Cf, I, part, st, skip, quad, status, TI);
-    case 8: return tile_launch<8>(m, n, H, Cf, I, part, st, skip, quad, status, TI);
+    case 2: return tile_launch<2>(m, n, H, Cf, I, part, st, skip, quad, status, TI, persistent);
+    case 4: return tile_launch<4>(m, n, H, Cf, I, part, st, skip, quad, status, TI, persistent);
+    case 8: return tile_launch<8>(m, n, H, Cf, I, part, st, skip, quad, status, TI, persistent);
     default: return cudaErrorInvalidValue;
   }
 }

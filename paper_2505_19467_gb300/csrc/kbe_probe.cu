@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(kThreads) fma_probe_kernel(int iters, T a, T b
     x[c] = (T)(threadIdx.x + c) * (T)1e-3;
     p[c] = a * (T)(c + 1);
   }
-#pragma unroll 2
+#pragma unroll 8   // iters is a multiple of 8: the loop's own instructions stay negligible
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
     for (int c = 0; c < CHAINS; ++c) x[c] = ACC ? fma(p[c], q, x[c]) : fma(x[c], (T)0.999, q);

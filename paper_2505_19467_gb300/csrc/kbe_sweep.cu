@@ -590,6 +590,140 @@ __global__ void __launch_bounds__(KBE_BLOCKED_THREADS, KBE_BLOCKED_MINB) sweep_b
   for (int e = 0; e < NB2; ++e) P::store(o + (size_t)e * nk, blk, X[e], Y[e]);
 }
 
+// ------------------------------------------- FP64, three-multiplication --
+// The FP64 sweep is bound by the FP64 pipe, so it pays to spend fewer DFMAs.
+// A complex product needs three real multiplications:
+//   A B = (P1 - P2) + i (P3 - P1 - P2),  P1 = Ar Br, P2 = Ai Bi,
+//   P3 = (Ar + Ai)(Br + Bi),
+// and the sums of products over a column's nodes can be kept as the three
+// sums P1, P2, P3. The extra additions are shared: coef_kernel stores
+// Ar + Ai of every coefficient (Cs), and a thread owns one column b of the
+// output for every row a, so the sum Br + Bi of each history element it
+// loads feeds N_b products. 6 N_b DFMAs per output and node (X and Y, or the
+// two products of an interior node) instead of 8 N_b. Exact algebra; only
+// the rounding differs. Same node classes and launch shape as sweep_kernel.
+template <int NB>
+struct F64m {
+  double p[3][NB];   // P1, P2, P3 of rows a
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int t = 0; t < 3; ++t)
+#pragma unroll
+      for (int a = 0; a < NB; ++a) p[t][a] = 0.0;
+  }
+  // += (or -= when NEG) A B for row a; as = Ar + Ai, bs = Br + Bi
+  template <bool NEG>
+  __device__ __forceinline__ void mac(int a, double2 A, double as, double2 B, double bs) {
+    const double s = NEG ? -1.0 : 1.0;
+    p[0][a] = fma(s * A.x, B.x, p[0][a]);
+    p[1][a] = fma(s * A.y, B.y, p[1][a]);
+    p[2][a] = fma(s * as, bs, p[2][a]);
+  }
+  __device__ __forceinline__ double2 value(int a) const {
+    return make_double2(p[0][a] - p[1][a], p[2][a] - p[0][a] - p[1][a]);
+  }
+};
+
+// one node: B = the block's column b as used (G, dG of (l, j); LOWER: stored,
+// else -conj of the stored (j, l)), the coefficient planes at node l
+template <int NB, int MODE, bool LOWER>
+__device__ __forceinline__ void f64m_node(const double2 *__restrict__ cf, const double *__restrict__ cs,
+                                          const double2 *__restrict__ g, size_t blk, int nk, int b, double f,
+                                          F64m<NB> &X, F64m<NB> &Y) {
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    double2 G, D;
+    if (LOWER) {
+      G = g[(size_t)(c * NB + b) * nk];
+      D = g[blk + (size_t)(c * NB + b) * nk];
+    } else {
+      const double2 g0 = g[(size_t)(b * NB + c) * nk], d0 = g[blk + (size_t)(b * NB + c) * nk];
+      G = make_double2(-g0.x, g0.y);
+      D = make_double2(-d0.x, d0.y);
+    }
+    const double gs = G.x + G.y, ds = D.x + D.y;
+#pragma unroll
+    for (int a = 0; a < NB; ++a) {
+      const size_t o = (size_t)(a * NB + c) * nk;
+      const double2 A1 = cf[o];
+      const double a1s = cs[o];
+      X.template mac<false>(a, A1, a1s, G, gs);
+      if (MODE == 0) {   // above the output: Y -= C1 dG
+        Y.template mac<true>(a, A1, a1s, D, ds);
+      } else if (MODE == 1) {   // interior of [0, t_j]: X += C2^< dG
+        X.template mac<false>(a, cf[blk + o], cs[blk + o], D, ds);
+      } else {   // weighted node: X += f C2^< dG, Y += (f (C3 - C2^<) + (f - 1) C1) dG
+        const double2 k2 = cf[blk + o], k3 = cf[2 * blk + o];
+        const double2 K2 = make_double2(f * k2.x, f * k2.y);
+        const double2 KY = make_double2(f * (k3.x - k2.x) + (f - 1.0) * A1.x, f * (k3.y - k2.y) + (f - 1.0) * A1.y);
+        X.template mac<false>(a, K2, K2.x + K2.y, D, ds);
+        Y.template mac<false>(a, KY, KY.x + KY.y, D, ds);
+      }
+    }
+  }
+}
+
+constexpr int kF64mThreads = 128;
+// CTAs per SM the register cap aims for: N_b >= 6 keeps its 6 N_b accumulators
+// and the unrolled node in registers at 2 (the FP64 pipe needs few warps)
+__host__ __device__ constexpr int f64m_minb(int NB) { return NB >= 6 ? 2 : 4; }
+
+// grid: x = k tiles of 128 / N_b, y = output column j, z = split of the l range;
+// thread (kk, b) with b fastest (the N_b lanes of one k read each coefficient
+// together); out as for sweep_kernel
+template <int NB, int QUAD>
+__global__ void __launch_bounds__(kF64mThreads, f64m_minb(NB)) sweep_f64m_kernel(const double2 *__restrict__ H,
+                                                                      const double2 *__restrict__ Cf,
+                                                                      const double *__restrict__ Cs,
+                                                                      double2 *__restrict__ out, int n, int nk,
+                                                                      int lchunk, const int *__restrict__ skip) {
+  if (skip && *skip) return;
+  constexpr int KT = kF64mThreads / NB;
+  if ((int)threadIdx.x >= KT * NB) return;
+  const int b = threadIdx.x % NB, kk = threadIdx.x / NB;
+  const int k = blockIdx.x * KT + kk;
+  if (k >= nk) return;
+  const int j = blockIdx.y;
+  const int l0 = blockIdx.z * lchunk;
+  const int l1 = min(n + 1, l0 + lchunk);
+  const size_t blk = (size_t)NB * NB * nk;
+  const double2 *cbase = Cf + k;
+  const double *sbase = Cs + k;
+  const double2 *hbase = H + k;
+  F64m<NB> X, Y;   // I^< and I^> - I^< of column b
+  X.zero();
+  Y.zero();
+  const int ia = QUAD == kQuadTrapezoid ? 1 : 3, ib = QUAD == kQuadTrapezoid ? j : j - 2;
+  if (j > 0)
+    for (int l = max(l0, ia); l < min(l1, ib); ++l)   // interior of [0, t_j], adjoint blocks
+      f64m_node<NB, 1, false>(cbase + (size_t)l * 3 * blk, sbase + (size_t)l * 3 * blk, hbase + tri(j, l) * 2 * blk,
+                              blk, nk, b, 1.0, X, Y);
+  for (int l = max(l0, j == 0 ? 0 : j + 1); l < l1; ++l)   // above the output, stored blocks
+    f64m_node<NB, 0, true>(cbase + (size_t)l * 3 * blk, sbase + (size_t)l * 3 * blk, hbase + tri(l, j) * 2 * blk,
+                           blk, nk, b, 1.0, X, Y);
+  if (j > 0) {   // the end nodes: l = 0 and l = j (trapezoid), three at each end (Gregory)
+    const int ns = QUAD == kQuadTrapezoid ? 2 : (j >= 5 ? 6 : j + 1);
+    for (int t = 0; t < ns; ++t) {
+      const int l = QUAD == kQuadTrapezoid ? (t == 0 ? 0 : j) : ((j >= 5 && t >= 3) ? j - 5 + t : t);
+      if (l < l0 || l >= l1) continue;
+      const double f = quad_omega(QUAD, j, l);
+      if (l == j)
+        f64m_node<NB, 2, true>(cbase + (size_t)l * 3 * blk, sbase + (size_t)l * 3 * blk, hbase + tri(j, j) * 2 * blk,
+                               blk, nk, b, f, X, Y);
+      else
+        f64m_node<NB, 2, false>(cbase + (size_t)l * 3 * blk, sbase + (size_t)l * 3 * blk, hbase + tri(j, l) * 2 * blk,
+                                blk, nk, b, f, X, Y);
+    }
+  }
+  double2 *o = out + ((size_t)blockIdx.z * (n + 1) + j) * 2 * blk + k;
+#pragma unroll
+  for (int a = 0; a < NB; ++a) {
+    const double2 x = X.value(a), y = Y.value(a);
+    o[(size_t)(a * NB + b) * nk] = x;
+    o[blk + (size_t)(a * NB + b) * nk] = c_add(x, y);
+  }
+}
+
 // I = sum over the z partial rows (FP64)
 __global__ void reduce_partials_kernel(const double2 *__restrict__ part, double2 *__restrict__ I,
                                        size_t count, int nz, const int *__restrict__ skip) {
@@ -653,8 +787,11 @@ __global__ void row_out_kernel(int prec, const double2 *__restrict__ fp64, const
 }
 
 // coefficient rows [l][3][a][c][k]: C1 = w^(n)_l (S^> - S^<), C2^< = dt S^<, C3 = dt S^> - C1
+// (FP64 also stores re + im of every coefficient in Cs, [l][3][a][c][k], for the
+// three-multiplication products of sweep_f64m_kernel)
 __global__ void coef_kernel(int prec, const double2 *__restrict__ Sig, void *__restrict__ Cf, int n,
-                            int nk, int nb2, double dt, const int *__restrict__ skip, int quad) {
+                            int nk, int nb2, double dt, const int *__restrict__ skip, int quad,
+                            double *__restrict__ Cs) {
   if (skip && *skip) return;
   const size_t blk = (size_t)nb2 * nk;
   const size_t total = (size_t)(n + 1) * blk;
@@ -670,6 +807,7 @@ __global__ void coef_kernel(int prec, const double2 *__restrict__ Sig, void *__r
       if (prec == KBE_PREC_DF64) ((float4 *)Cf)[o] = split_df(v[q]);
       else if (prec == KBE_PREC_C64) ((float2 *)Cf)[o] = make_float2((float)v[q].x, (float)v[q].y);
       else ((double2 *)Cf)[o] = v[q];
+      if (Cs) Cs[o] = v[q].x + v[q].y;
     }
   }
 }
@@ -1164,6 +1302,37 @@ cudaError_t sweep_nb(const Mesh &m, int n, const void *H, const void *Cf, double
   return cudaGetLastError();
 }
 
+// the three-multiplication FP64 sweep (N_b <= 8): k tiles of 128 / N_b, split as sweep_kernel
+#ifndef KBE_SWEEP_F64_3M
+#define KBE_SWEEP_F64_3M 1
+#endif
+bool use_f64m(const Mesh &m, int prec) { return KBE_SWEEP_F64_3M && prec == KBE_PREC_FP64 && m.nb <= 8; }
+
+template <int NB>
+cudaError_t sweep_f64m(const Mesh &m, int n, const void *H, const void *Cf, const double *Cs, double2 *I,
+                       double2 *part, cudaStream_t st, const int *skip, int quad) {
+  constexpr int KT = kF64mThreads / NB;
+  SweepShape sh;
+  sh.threads = kF64mThreads;
+  const long tx = (m.nk + KT - 1) / KT;
+  const long nz = split_count((long)(n + 1) * tx, n, tuned_target(KBE_PREC_FP64, quad, m, n, kTargetPerSm));
+  sh.lchunk = (int)((n + 1 + nz - 1) / nz);
+  sh.nz = (int)((n + 1 + sh.lchunk - 1) / sh.lchunk);
+  sh.grid = dim3((unsigned)tx, n + 1, (unsigned)sh.nz);
+  double2 *out = sh.nz > 1 ? part : I;
+  if (quad == kQuadGregory)
+    sweep_f64m_kernel<NB, kQuadGregory><<<sh.grid, sh.threads, 0, st>>>((const double2 *)H, (const double2 *)Cf, Cs,
+                                                                         out, n, m.nk, sh.lchunk, skip);
+  else
+    sweep_f64m_kernel<NB, kQuadTrapezoid><<<sh.grid, sh.threads, 0, st>>>((const double2 *)H, (const double2 *)Cf, Cs,
+                                                                           out, n, m.nk, sh.lchunk, skip);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || sh.nz == 1) return e;
+  const size_t count = (size_t)(n + 1) * 2 * m.nb * m.nb * m.nk;
+  reduce_partials_kernel<<<grid_for(count), 256, 0, st>>>(part, I, count, sh.nz, skip);
+  return cudaGetLastError();
+}
+
 template <int NB>
 cudaError_t sweep_blocked(const Mesh &m, int n, const void *H, const void *Cf, double2 *I, double2 *part,
                           cudaStream_t st, const int *skip, int quad) {
@@ -1237,6 +1406,12 @@ cudaError_t sweep_prec(const Mesh &m, int n, int prec, const void *H, const void
   if constexpr (NB <= 2) {
     if (use_blocked(m, prec)) return sweep_blocked<NB>(m, n, H, Cf, I, part, st, skip, quad);
   }
+  if constexpr (NB <= 8) {
+    if (use_f64m(m, prec)) {
+      const size_t cn = (size_t)(n + 1) * 3 * NB * NB * m.nk;   // Cs follows the coefficient rows
+      return sweep_f64m<NB>(m, n, H, Cf, (const double *)((const double2 *)Cf + cn), I, part, st, skip, quad);
+    }
+  }
   if (prec == KBE_PREC_FP64) return sweep_nb<ArithF64, NB>(m, n, H, Cf, I, part, st, skip, quad);
   if (prec == KBE_PREC_DF64) return sweep_nb<ArithDF64, NB>(m, n, H, Cf, I, part, st, skip, quad);
   if (sweep_width(m, prec) == 2) return sweep_nb<ArithC64x2, NB>(m, n, H, Cf, I, part, st, skip, quad);
@@ -1297,10 +1472,16 @@ size_t history_elem_bytes(int prec) { return prec == KBE_PREC_C64 ? sizeof(float
 
 // coefficient rows (n+1) x 3 blocks in the storage format, then the partial
 // sums of the l split (FP64) or of the tile form (complex64)
+// coefficient rows in the storage format (FP64: followed by their re + im sums)
+size_t coef_region_bytes(const Mesh &m, int n, int prec) {
+  const size_t cn = (size_t)(n + 1) * 3 * m.nb * m.nb * m.nk;
+  size_t coef = cn * history_elem_bytes(prec) + (prec == KBE_PREC_FP64 ? cn * sizeof(double) : 0);
+  return (coef + 255) / 256 * 256;
+}
+
 size_t sweep_workspace_bytes(const Mesh &m, int n, int prec) {
   const size_t blk = (size_t)m.nb * m.nb * m.nk;
-  size_t coef = (size_t)(n + 1) * 3 * blk * history_elem_bytes(prec);
-  coef = (coef + 255) / 256 * 256;
+  const size_t coef = coef_region_bytes(m, n, prec);
   size_t part = 0;
   (void)prec;
   for (int r = 0; r <= n; ++r) {   // the largest partial buffer over rows 0..n, any split
@@ -1421,12 +1602,11 @@ cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const v
   if (!precision_supported(precision)) return cudaErrorInvalidValue;
   const size_t blk = (size_t)m.nb * m.nb * m.nk;
   const size_t total = (size_t)(n + 1) * blk;
-  coef_kernel<<<grid_for(total), 256, 0, st>>>(precision, Sig, work, n, m.nk, m.nb * m.nb, dt, skip, quad);
+  double *Cs = precision == KBE_PREC_FP64 ? (double *)((double2 *)work + (size_t)(n + 1) * 3 * blk) : nullptr;
+  coef_kernel<<<grid_for(total), 256, 0, st>>>(precision, Sig, work, n, m.nk, m.nb * m.nb, dt, skip, quad, Cs);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  size_t coef = (size_t)(n + 1) * 3 * blk * history_elem_bytes(precision);
-  coef = (coef + 255) / 256 * 256;
-  double2 *part = (double2 *)((char *)work + coef);
+  double2 *part = (double2 *)((char *)work + coef_region_bytes(m, n, precision));
   switch (m.nb) {
     case 1: return sweep_prec<1>(m, n, precision, H, work, I, part, st, skip, quad, status, inject);
     case 2: return sweep_prec<2>(m, n, precision, H, work, I, part, st, skip, quad, status, inject);

@@ -56,7 +56,8 @@ HBM_FALLBACK_GBS = 6800.0
 # from ncu (dram__bytes_read.sum + dram__bytes_write.sum) at row 501 of the
 # full c2 run, one launch per form; traffic grows with the triangle like the
 # algorithmic bytes, so the average launch is scaled by the same factor.
-TRAFFIC_RATIO = {"fp64": 2.00, "df64": 2.77, "c64": 1.87}
+# None: the form's kernel changed after its counters were taken.
+TRAFFIC_RATIO = {"fp64": None, "df64": 2.77, "c64": None}
 DTYPES = {"fp64": "f64", "df64": "df64 (f32 hi/lo pairs; everything but the sweep f64)",
           "c64": "c64/f32 history + sweep (everything else f64)"}
 # rows of the c2 trajectory at which the oracle is timed (its cost grows as n^2)
@@ -216,7 +217,8 @@ def roofline(prof, precision, t_dev, peaks):
     executed = prof["sweep_flops_executed"] / sweep_s / 1e9 if sweep_s > 0 else 0.0
     gbs = prof["sweep_bytes"] / sweep_s / 1e9 if sweep_s > 0 else 0.0
     hbm, hsrc = hbm_peak()
-    common = {"kernel": "collision sweep (a2)", "traffic": TRAFFIC_RATIO[precision] * alg_bytes,
+    ratio = TRAFFIC_RATIO[precision]
+    common = {"kernel": "collision sweep (a2)", "traffic": ratio * alg_bytes if ratio else None,
               "traffic_unit": "bytes per launch", "algorithmic_bytes_per_launch": alg_bytes,
               "launches": prof["sweep_launches"],
               "sweep_share_of_step": sweep_s / t_dev if t_dev > 0 else None,

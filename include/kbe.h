@@ -108,7 +108,9 @@ typedef struct kbe_profile_stats {
   int sweep_launches;       /* sweep launches timed                               */
   double sweep_ms;          /* summed event time of those launches                */
   double sweep_flops;       /* algorithmic flops of those launches (24 n^2 N_b^3 n_k) */
-  double sweep_flops_executed; /* flops the kernel executes (~16 n^2 N_b^3 n_k)     */
+  double sweep_flops_executed; /* flops the kernel executes (~16 n^2 N_b^3 n_k; FP64 at
+                               * N_b <= 8: its FP64-pipe operations, ~(12 + 4/N_b)
+                               * n^2 N_b^3 n_k, three-multiplication products) */
   double sweep_bytes;       /* algorithmic bytes (stored history read once + I row) */
   int launches;             /* all kernels launched while enabled                 */
   /* kbe_backward while enabled (CUDA events around each phase): the steps'

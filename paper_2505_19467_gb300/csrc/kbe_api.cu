@@ -171,7 +171,11 @@ void free_all(kbe_handle *h) {
 // collision sweep flops of one launch at row n: the method's count with the
 // G^> form of Eq. 6 (3 N_b^3 complex multiply-adds per stored block, ~24 n^2
 // N_b^3 n_k flops) and the count the kernel executes with the (I^<, I^> - I^<)
-// form (2 products per node, 3 at the two trapezoid end nodes of [0, t_j])
+// form (2 products per node, 3 at the two trapezoid end nodes of [0, t_j]).
+// The three-multiplication FP64 kernel issues 3 DFMAs per complex multiply-add
+// instead of 4, plus one DADD per history element and column (the element's
+// re + im, shared by N_b products): its FP64-pipe operations, counted at 2
+// flops each as the FMA probe counts them, are (3/4 + 1/(4 N_b)) of the count.
 double sweep_flops(const kbe_handle *h, int n) {
   const double nb3 = (double)h->cfg.nb * h->cfg.nb * h->cfg.nb;
   const double cm = 2.0 * (n + 1.0) * (n + 1.0) + (double)n * (n + 3.0);
@@ -180,7 +184,8 @@ double sweep_flops(const kbe_handle *h, int n) {
 double sweep_flops_executed(const kbe_handle *h, int n) {
   const double nb3 = (double)h->cfg.nb * h->cfg.nb * h->cfg.nb;
   const double cm = 2.0 * n * (double)n + 6.0 * n + 2.0;
-  return 8.0 * cm * nb3 * h->mesh.nk;
+  const double f3m = kbe::use_f64m(h->mesh, h->cfg.precision) ? 0.75 + 0.25 / h->cfg.nb : 1.0;
+  return 8.0 * cm * nb3 * h->mesh.nk * f3m;
 }
 double sweep_bytes(const kbe_handle *h, int n) {
   const double blk2 = 2.0 * (double)h->blk;

@@ -223,6 +223,7 @@ cudaError_t sigma_row(const Mesh &m, const double *v_host, int n, double Un, con
 // dG = G^< - G^>; work holds the coefficient rows and the l-split partial
 // sums (sweep_workspace_bytes).
 bool sweep_supported(int nb);
+bool use_f64m(const Mesh &m, int prec);   // the FP64 sweep takes the three-multiplication kernel
 bool precision_supported(int prec);
 size_t history_elem_bytes(int prec);
 size_t sweep_workspace_bytes(const Mesh &m, int n, int prec);

@@ -1303,10 +1303,6 @@ cudaError_t sweep_nb(const Mesh &m, int n, const void *H, const void *Cf, double
 }
 
 // the three-multiplication FP64 sweep (N_b <= 8): k tiles of 128 / N_b, split as sweep_kernel
-#ifndef KBE_SWEEP_F64_3M
-#define KBE_SWEEP_F64_3M 1
-#endif
-bool use_f64m(const Mesh &m, int prec) { return KBE_SWEEP_F64_3M && prec == KBE_PREC_FP64 && m.nb <= 8; }
 
 template <int NB>
 cudaError_t sweep_f64m(const Mesh &m, int n, const void *H, const void *Cf, const double *Cs, double2 *I,
@@ -1419,6 +1415,8 @@ cudaError_t sweep_prec(const Mesh &m, int n, int prec, const void *H, const void
 }
 
 }  // namespace
+
+bool use_f64m(const Mesh &m, int prec) { return prec == KBE_PREC_FP64 && m.nb <= 8; }
 
 // cuTensorMapEncodeTiled from the driver (no link against libcuda); resolved
 // once per process (a thread-safe static: the entry point is not per device)

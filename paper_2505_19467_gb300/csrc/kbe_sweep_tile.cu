@@ -48,33 +48,36 @@ namespace kbe {
 
 namespace {
 
-// per N_b: KT k per CTA (a lane is one (k, a): KT N_b = 32), TMW columns per
-// warp, W warps (TM = TMW W columns per strip), S stages of the ring, RB row
-// reduction buffers (2: one barrier per row). One CTA of 8 warps per SM (its
-// shared memory): four columns per warp amortise the per-row work (the C1(i)
-// row, the reduction of the row use over the warps, the barrier) over four
-// blocks. (Timed: 16 warps of two columns each at <= 128 registers ran 20 %
-// slower at row 511 of c2, on barrier and dispatch stalls.)
+// per N_b: KG warps share one column group, each on 32 / N_b of the CTA's
+// KT = KG 32 / N_b consecutive k (a lane is one (k, a)); TMW columns per
+// column group, W warps (TM = TMW W / KG columns per strip), S stages of the
+// ring, RB row-reduction buffers (2: one barrier per row), MINB CTAs per SM.
+// Four columns per warp amortise the per-row work (the C1(i) row, the
+// reduction of the row use over the column groups, the barrier) over four
+// blocks. (Timed at row 511 of c2, against one CTA of 8 warps of four
+// columns: 16 warps of two columns at <= 128 registers 20 % slower; 128-byte
+// TMA rows (two warps per column group) no faster; two CTAs of 4 warps per
+// SM 3 % slower.)
 template <int NB>
 struct TileCfg;
 template <>
 struct TileCfg<2> {
-  static constexpr int KT = 16, TMW = 4, W = 8, S = 3, RB = 2;
+  static constexpr int KG = 1, KT = 16, TMW = 4, W = 8, S = 3, RB = 2, MINB = 1;
 };
 template <>
 struct TileCfg<4> {
-  static constexpr int KT = 8, TMW = 4, W = 8, S = 3, RB = 2;
+  static constexpr int KG = 1, KT = 8, TMW = 4, W = 8, S = 3, RB = 2, MINB = 1;
 };
 template <>
 struct TileCfg<8> {
-  static constexpr int KT = 4, TMW = 2, W = 8, S = 3, RB = 1;
+  static constexpr int KG = 1, KT = 4, TMW = 2, W = 8, S = 3, RB = 1, MINB = 1;
 };
 
 constexpr size_t kTileCounterBytes = 256;   // the work-unit counter ahead of the partial sums
 
 template <int NB>
 __host__ __device__ constexpr int tile_tm() {
-  return TileCfg<NB>::TMW * TileCfg<NB>::W;
+  return TileCfg<NB>::TMW * TileCfg<NB>::W / TileCfg<NB>::KG;
 }
 template <int NB>
 __host__ __device__ constexpr int tile_threads() {
@@ -91,7 +94,7 @@ __host__ __device__ constexpr int tile_stage_elems() {
 }
 template <int NB>
 __host__ __device__ constexpr int tile_red_elems() {
-  return TileCfg<NB>::W * NB * 32;
+  return TileCfg<NB>::W / TileCfg<NB>::KG * NB * NB * TileCfg<NB>::KT;   // [column group][cc][a][kk]
 }
 template <int NB>
 constexpr size_t tile_smem_bytes() {
@@ -141,7 +144,7 @@ __device__ __forceinline__ bool tile_item(int p, int n, int TM, int TI, int *s_o
 // CP: column partials [chunk][j][x][a][b][k], RP: row partials [strip][j][a][b][k]
 // (complex64). counter: zeroed before the launch.
 template <int NB, int QUAD>
-__global__ void __launch_bounds__(tile_threads<NB>(), 1)
+__global__ void __launch_bounds__(tile_threads<NB>(), TileCfg<NB>::MINB)
     sweep_tile_kernel(const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmH,
                       const float2 *__restrict__ Cf, float2 *__restrict__ CP, float2 *__restrict__ RP, int n,
                       int nk, int TI, int units, int *counter, int persistent, const int *__restrict__ skip,
@@ -156,9 +159,11 @@ __global__ void __launch_bounds__(tile_threads<NB>(), 1)
   __shared__ int failed, s_unit;
   float2 *smem = reinterpret_cast<float2 *>(tile_smem4);
   float2 *redbase = smem + (size_t)kStg * SE;
+  constexpr int KG = TileCfg<NB>::KG, KW = KT / KG, NCG = kW / KG;   // k per warp, column groups
   const int ktiles = (nk + KT - 1) / KT;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int kk = lane % KT, a = lane / KT;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = wid / KG;                              // column group
+  const int kk = (wid % KG) * KW + lane % KW, a = lane / KW;   // k within the tile, row a
   const size_t blk = (size_t)NB2 * nk;
 
   if (threadIdx.x == 0) {
@@ -292,17 +297,17 @@ __global__ void __launch_bounds__(tile_threads<NB>(), 1)
           }
         }
       }
-      // the warps' row-use shares: red[w][cc][a][kk], summed by the first NB * 32 threads
+      // the column groups' row-use shares: red[cg][cc][a][kk], summed by the first NB NB KT threads
       float2 *red = redbase + (size_t)(g % RB) * tile_red_elems<NB>();
 #pragma unroll
       for (int cc = 0; cc < NB; ++cc) red[((warp * NB + cc) * NB + a) * KT + kk] = T[cc];
       __syncthreads();   // the stage is consumed and the shares are written
-      if (threadIdx.x < NB * 32) {
+      if (threadIdx.x < NB * NB * KT) {
         const int t = threadIdx.x;   // (a', cc', kk') with kk' fastest: coalesced writes
         const int kk2 = t % KT, ac = t / KT, cc2 = ac % NB, a2 = ac / NB;
         float2 sum = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int w = 0; w < kW; ++w) {
+        for (int w = 0; w < NCG; ++w) {
           const float2 v = red[((w * NB + cc2) * NB + a2) * KT + kk2];
           sum.x += v.x;
           sum.y += v.y;
@@ -462,8 +467,8 @@ cudaError_t tile_launch(const Mesh &m, int n, const void *H, const void *Cf, dou
   float2 *CP = (float2 *)((char *)part + kTileCounterBytes);
   float2 *RP = CP + (size_t)((n + TI) / TI) * (n + 1) * 2 * blk;
   const long units = (long)((m.nk + KT - 1) / KT) * tile_items(n, TM, TI);
-  const long sms = device_sms();
-  const unsigned grid = persistent ? (unsigned)(units < sms ? units : sms) : (unsigned)units;
+  const long slots = (long)device_sms() * TileCfg<NB>::MINB;   // resident CTAs
+  const unsigned grid = persistent ? (unsigned)(units < slots ? units : slots) : (unsigned)units;
   const size_t smem = tile_smem_bytes<NB>();
   e = cudaMemsetAsync(counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;

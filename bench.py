@@ -57,9 +57,11 @@ HBM_FALLBACK_GBS = 6800.0
 # full c2 run, one launch per form; traffic grows with the triangle like the
 # algorithmic bytes, so the average launch is scaled by the same factor.
 # None: the form's kernel changed after its counters were taken.
-TRAFFIC_RATIO = {"fp64": None, "df64": 2.77, "c64": None}
+TRAFFIC_RATIO = {"fp64": None, "df64": 2.77, "c64": None, "f16x2": None}
 DTYPES = {"fp64": "f64", "df64": "df64 (f32 hi/lo pairs; everything but the sweep f64)",
-          "c64": "c64/f32 history + sweep (everything else f64)"}
+          "c64": "c64/f32 history + sweep (everything else f64)",
+          "f16x2": "split-f16 pair history, tcgen05 f16 MMAs with f32 accumulation (Sigma c64; everything else f64)"}
+FORMS = ("fp64", "df64", "c64", "f16x2")
 # rows of the c2 trajectory at which the oracle is timed (its cost grows as n^2)
 ORACLE_ROWS = [63, 127, 191, 255, 319, 383, 447, 511]
 ORACLE_ROWS_1T = [31, 95, 159]
@@ -72,7 +74,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--nt", type=int, default=None, help="truncate N_t (testing only)")
-    p.add_argument("--precision", default="fp64", choices=["fp64", "df64", "c64"],
+    p.add_argument("--precision", default="fp64", choices=["fp64", "df64", "c64", "f16x2"],
                    help="history storage / sweep arithmetic of the headline value (fp64 meets "
                         "the 1e-10 bar; df64 / c64 are the reduced-storage forms)")
     p.add_argument("--forms", default="all", choices=["all", "none", "gradient", "batched"],
@@ -86,6 +88,10 @@ def parse():
                    help="time the collision sweep alone at this row on random history of c2's and c3's "
                         "shape, every launch choice of the C64 form, then exit")
     p.add_argument("--sweep-shapes", default="c2,c3", help="workloads for --sweep-row")
+    p.add_argument("--sweep-forms", default=None,
+                   help="comma list of forms for --sweep-row (default: every form of the workload)")
+    p.add_argument("--sweep-ti", type=int, default=None,
+                   help="--sweep-row: only the tile / tensor-core choices with this TI")
     p.add_argument("--gradient-fd", action="store_true",
                    help="check the c5 gradient (512 steps) by central differences on 16 A_i and U, then exit")
     return p.parse_args()
@@ -198,6 +204,17 @@ def hbm_peak():
         return HBM_FALLBACK_GBS, "fallback (no measured HBM peak on this box)"
 
 
+def tensor_peak():
+    """(GFLOP/s, source): dense FP16 tensor rate = the measured sustained bf16
+    cuBLAS rate (the same tensor-core rate), else the fallback"""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return (float(json.load(f)["bf16_tflops_sustained"]) * 1e3,
+                    "measured (MEASURED_PEAKS.json bf16_tflops_sustained; FP16 dense runs at the bf16 rate)")
+    except Exception:
+        return 1.7e6, "fallback (1.7 PFLOP/s sustained bf16)"
+
+
 def alu_peaks(kbe):
     """measured FMA throughput (GFLOP/s) of this GPU: {"fp64": .., "fp32": ..}"""
     f64, f32 = kbe.measure_fma_peaks()
@@ -230,6 +247,12 @@ def roofline(prof, precision, t_dev, peaks):
                 "alu": {"achieved_executed": executed, "peak": fp32, "unit": "GFLOP/s FP32",
                         "frac_executed": executed / fp32,
                         "peak_source": "measured FP32 FMA throughput (kbe_measure_fma_peaks)"}}
+    if precision == "f16x2":   # executed = the MMAs' flops (hi and lo parts of both operands)
+        tpk, tsrc = tensor_peak()
+        return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                "peak_source": hsrc, **common,
+                "tensor": {"achieved_executed": executed, "peak": tpk, "unit": "GFLOP/s FP16 dense",
+                           "frac_executed": executed / tpk, "peak_source": tsrc}}
     if precision == "df64":
         peak = peaks["fp32"] / 6.0
         unit, src = ("GFLOP/s FP64-equivalent (double-float)",
@@ -299,7 +322,7 @@ def run_ours(args, rank, world, local):
 
     # ---- the reduced-storage forms on the same workload (speedup, error) ----
     forms = {}
-    for form in ([] if args.forms != "all" else [f for f in ("fp64", "df64", "c64") if f != args.precision]):
+    for form in ([] if args.forms != "all" else [f for f in FORMS if f != args.precision]):
         gf = kbe.KBE.from_system(s, stream=stream, precision=kbe.PRECISIONS[form])
         if not args.no_autotune:
             tuned[form] = [int(x) for x in gf.autotune() if x]
@@ -497,7 +520,7 @@ def c3_form(kbe, stream, peaks):
     out = {"workload": f"c3: N_b=8, 16x16 mesh (n_k=256), N_t={nt}, dt=0.02, U=1.5, Peierls A0=0.5, "
                        "P(EC)^2E, one full trajectory per form"}
     ref = None
-    for form in ("fp64", "df64", "c64"):
+    for form in FORMS:
         g = kbe.KBE.from_system(s, stream=stream, precision=kbe.PRECISIONS[form])
         g.step(8)   # warm-up (kernels loaded, attributes set)
         g.reset()
@@ -646,12 +669,13 @@ class OracleSampler:
         return float(np.sum(3 * np.maximum(np.polyval(ce, xs), 0) + 3 * np.maximum(np.polyval(cu, xs), 0)))
 
 
-def sweep_row_study(kbe, row, names, reps=5):
+def sweep_row_study(kbe, row, names, reps=5, only_forms=None, only_ti=None):
     """The collision sweep (Sigma row -> coefficient rows -> sweep -> I row) alone at
     row `row` on random history of each workload's shape: every launch choice of
     the C64 form (the single-read tile form at TI = 32, 64, 128 rows per work item;
-    the per-column staged / blocked kernel at its default split) and, at c2, the
-    FP64 and DF64 forms. Time per launch from CUDA events on the launching stream
+    the per-column staged / blocked kernel at its default split), the tensor-core
+    sweep of the split-FP16 form at TI = 32, 64 (and 128 at N_b = 4) rows per
+    panel and, at c2, the FP64 and DF64 forms. Time per launch from CUDA events on the launching stream
     (after 2 untimed launches; the history is larger than L2), algorithmic
     bytes (the triangle read once in the form's storage, the Sigma row read and
     the I row written in FP64) per time, and the fraction of the HBM peak."""
@@ -669,19 +693,29 @@ def sweep_row_study(kbe, row, names, reps=5):
         sig = torch.randn((n + 1, 2, nb, nb, nk), dtype=torch.complex128, device="cuda", generator=g)
         I = torch.empty_like(sig)
         res = {"shape": f"N_b={nb}, n_k={nk}, row n={n}"}
-        forms = ["c64", "fp64", "df64"] if name == "c2" else ["c64"]
+        forms = ["f16x2", "c64", "fp64", "df64"] if name == "c2" else ["f16x2", "c64"]
+        if only_forms:
+            forms = [f for f in forms if f in only_forms]
         for form in forms:
             prec = kbe.PRECISIONS[form]
-            esz = 8 if form == "c64" else 16
-            H = torch.randn(ntri * 2 * blk * esz // 4, dtype=torch.float32, device="cuda", generator=g)
+            esz = 8 if form in ("c64", "f16x2") else 16
+            if form == "f16x2":   # finite random halves (hi and lo parts of every real), padded rows
+                H = torch.randn(kbe.history_bytes(nb, L, n, prec) // 2, dtype=torch.float16, device="cuda",
+                                generator=g)
+            else:
+                H = torch.randn(ntri * 2 * blk * esz // 4, dtype=torch.float32, device="cuda", generator=g)
             w = torch.empty(kbe.collision_row_workspace(nb, L, n, prec) // 4 + 1, dtype=torch.float32, device="cuda")
             alg = 2.0 * blk * (ntri * esz + 2.0 * (n + 1) * 16.0)
             choices = [("default", 0)]
+            if form == "f16x2":
+                choices = [(f"tc_TI{t}", -t) for t in (32, 64, 128) if nb == 4 or t <= 64]
             if form == "c64":
                 choices = [("per_column", 12 if nb >= 4 else 8)]
                 if nb in (2, 4, 8):
                     choices += [(f"tile_TI{t}", -t) for t in (32, 64, 128)]
                     choices += [(f"tile_TI{t}_one_unit_per_cta", -(t + 1)) for t in (32, 64, 128)]
+            if only_ti:
+                choices = [(lb, c) for lb, c in choices if c in (-only_ti, -(only_ti + 1))] or choices[:1]
             for label, choice in choices:
                 if choice:
                     kbe.set_sweep_choice(nb, L, prec, choice)
@@ -782,7 +816,9 @@ def main():
             import torch
             import paper_2505_19467_gb300 as kbe
             torch.cuda.set_device(local)
-            print(json.dumps({"sweep_row": sweep_row_study(kbe, args.sweep_row, args.sweep_shapes.split(","))}),
+            print(json.dumps({"sweep_row": sweep_row_study(
+                kbe, args.sweep_row, args.sweep_shapes.split(","),
+                only_forms=args.sweep_forms.split(",") if args.sweep_forms else None, only_ti=args.sweep_ti)}),
                   flush=True)
         return
     if args.impl == "reference":

@@ -65,11 +65,21 @@ typedef enum {
  *         pipe: exact products (FMA) and error-free sums, FP64-level result.
  *   C64:  history complex64 (half the bytes), sweep in FP32: plain sums
  *         over groups of at most 32 products per output, the groups added
- *         into a compensated (error-free TwoSum) sum over the memory time. */
+ *         into a compensated (error-free TwoSum) sum over the memory time.
+ *   F16X2: history as split FP16 pairs, hi = fp16(S x), lo = fp16(S x - hi)
+ *         per real part with S = 4096 (the same 8 bytes per complex number
+ *         as C64; 22-bit significand, absolute error below 2^-37 for tiny
+ *         entries), stored k-outer in the operand layout of the tensor cores;
+ *         the sweep runs on the tensor cores (tcgen05.mma, FP16 products of
+ *         the hi and lo parts, FP32 accumulation in tensor memory) with the
+ *         coefficient rows split the same way under a power-of-two scale.
+ *         N_b in {4, 8}. The self-energy is computed in complex FP32 as for
+ *         C64; everything else is FP64. */
 enum {
   KBE_PREC_FP64 = 0,
   KBE_PREC_DF64 = 1,
-  KBE_PREC_C64 = 2
+  KBE_PREC_C64 = 2,
+  KBE_PREC_F16X2 = 3
 };
 
 typedef struct kbe_config {
@@ -398,6 +408,20 @@ kbe_status kbe_op_sigma_row(const kbe_mesh *m, const double *v, int n, double Un
  * hi = fl32(x), lo = fl32(x - hi) (DF64), or complex64 (C64). */
 kbe_status kbe_op_pack(int precision, const void *src_dev, void *dst_dev, size_t nblocks,
                        size_t block_elems, void *stream);
+
+/* kbe_op_pack for a history triangle of mesh m from row 0 (nblocks =
+ * (n+1)(n+2)/2 for rows 0..n), in every precision including KBE_PREC_F16X2,
+ * whose layout depends on N_b and n_k (kbe_op_pack refuses it with
+ * KBE_ERR_UNSUPPORTED). dst_dev holds kbe_history_bytes(m, n, precision). */
+kbe_status kbe_op_pack_mesh(const kbe_mesh *m, int precision, const void *src_dev, void *dst_dev,
+                            size_t nblocks, void *stream);
+
+/* Bytes of a history triangle with rows 0..n in a precision's storage:
+ * (n+1)(n+2)/2 blocks of 2 nb^2 nk stored complex numbers (16 bytes each in
+ * FP64 and DF64, 8 in C64); KBE_PREC_F16X2 (8 bytes per complex number) pads
+ * every row to whole strips of 16 (N_b = 4) or 8 (N_b = 8) blocks. 0 if the
+ * arguments are invalid. */
+size_t kbe_history_bytes(const kbe_mesh *m, int n, int precision);
 
 /* (a2) Collision-integral row, Eq. 6 in left form:
  *   I^x(n, j) = sum_{l=0}^{n} w^(n)_l [S^>(n,l) - S^<(n,l)] G^x(l, j)

@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(PKG, "libkbe.so")
 KBE_PREC_FP64 = 0
 KBE_PREC_DF64 = 1
 KBE_PREC_C64 = 2
-PRECISIONS = {"fp64": KBE_PREC_FP64, "df64": KBE_PREC_DF64, "c64": KBE_PREC_C64}
+KBE_PREC_F16X2 = 3
+PRECISIONS = {"fp64": KBE_PREC_FP64, "df64": KBE_PREC_DF64, "c64": KBE_PREC_C64, "f16x2": KBE_PREC_F16X2}
 
 STATUS = {
     0: "KBE_OK", -1: "KBE_ERR_ARG", -2: "KBE_ERR_OOM", -3: "KBE_ERR_CUDA", -4: "KBE_ERR_STATE",
@@ -38,7 +39,7 @@ EXPORTS = [
     "kbe_set_dipole", "kbe_backward", "kbe_backward_memory_bytes", "kbe_corrector_iterations",
     "kbe_op_collision_row_quad", "kbe_set_graphs", "kbe_autotune", "kbe_debug_inject", "kbe_batch_set_graphs",
     "kbe_observables_all_dev", "kbe_get_row_dev", "kbe_device_info", "kbe_measure_fma_peaks",
-    "kbe_set_sweep_choice",
+    "kbe_set_sweep_choice", "kbe_op_pack_mesh", "kbe_history_bytes",
 ]
 
 
@@ -103,6 +104,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "kbe_op_collision_row": (I, [pmesh, I, D, I, P, P, P, P, S, P]),
         "kbe_op_collision_row_workspace": (S, [pmesh, I, I]),
         "kbe_op_pack": (I, [I, P, P, S, S, P]),
+        "kbe_op_pack_mesh": (I, [pmesh, I, P, P, S, P]),
+        "kbe_history_bytes": (S, [pmesh, I, I]),
         "kbe_op_propagators": (I, [pmesh, D, P, P, P, P]),
         "kbe_op_update_row": (I, [pmesh, I, D, D, P, P, P, P, P, P, P, P]),
         "kbe_op_sigma_row_noalloc": (I, [pmesh, P, I, D, P, P, P, P]),
@@ -416,10 +419,23 @@ def collision_row(nb, L, n, dt, H, Sigma, I, precision=KBE_PREC_FP64, work=None,
                                                 None if work is None else _c(work), wb, _stream_ptr(stream)))
 
 
-def pack(precision, src, dst, nblocks, block_elems, stream=None):
+def history_bytes(nb, L, n, precision) -> int:
+    """bytes of a history triangle with rows 0..n in `precision`'s storage
+    (kbe_history_bytes)"""
+    m = mesh(nb, L)
+    return int(load().kbe_history_bytes(ctypes.byref(m), int(n), int(precision)))
+
+
+def pack(precision, src, dst, nblocks, block_elems, stream=None, nb=None, L=None):
     """FP64 (G^<, G^>) blocks [nblocks][2][nb][nb][nk] -> history storage of
     `precision`, (G^<, dG) per block (dst bytes: 16 per complex for FP64 and
-    DF64, 8 for C64)."""
+    DF64, 8 for C64 and F16X2). With the mesh (nb, L) it calls
+    kbe_op_pack_mesh, which every precision accepts (F16X2 requires it)."""
+    if nb is not None:
+        m = mesh(nb, L)
+        _check(load().kbe_op_pack_mesh(ctypes.byref(m), int(precision), _c(src), _c(dst), int(nblocks),
+                                       _stream_ptr(stream)))
+        return
     _check(load().kbe_op_pack(int(precision), _c(src), _c(dst), int(nblocks), int(block_elems),
                               _stream_ptr(stream)))
 

@@ -181,7 +181,9 @@ double sweep_flops(const kbe_handle *h, int n) {
   const double cm = 2.0 * (n + 1.0) * (n + 1.0) + (double)n * (n + 3.0);
   return 8.0 * cm * nb3 * h->mesh.nk;
 }
+// (the tensor-core form: the flops its MMAs execute, hi and lo parts included)
 double sweep_flops_executed(const kbe_handle *h, int n) {
+  if (h->cfg.precision == KBE_PREC_F16X2) return kbe::sweep_tc_flops(h->mesh, h->cfg.precision, h->cfg.quadrature, n);
   const double nb3 = (double)h->cfg.nb * h->cfg.nb * h->cfg.nb;
   const double cm = 2.0 * n * (double)n + 6.0 * n + 2.0;
   const double f3m = kbe::use_f64m(h->mesh, h->cfg.precision) ? 0.75 + 0.25 / h->cfg.nb : 1.0;
@@ -200,8 +202,9 @@ double2 *frow(kbe_handle *h, int i) { return h->Wrow[i & 1]; }
 
 // store row i into the history triangle: (G^<, dG) in the storage format
 kbe_status publish(kbe_handle *h, int i, const int *skip = nullptr) {
-  char *dst = (char *)h->H + tri(i, 0) * 2 * h->blk * h->esz;
-  cudaError_t e = kbe::launch_pack(h->cfg.precision, frow(h, i), dst, (size_t)(i + 1), h->blk, h->stream, skip);
+  char *dst = (char *)h->H + kbe::history_row_offset(h->mesh, h->cfg.precision, i);
+  cudaError_t e = kbe::launch_pack(h->cfg.precision, frow(h, i), dst, (size_t)(i + 1), h->blk, h->stream, skip,
+                                   h->cfg.nb, i);
   if (e != cudaSuccess) return cuda_fail(h, e, "publish row");
   if (h->prof) h->stats.launches += 1;
   return KBE_OK;
@@ -211,9 +214,10 @@ kbe_status evaluate_row(kbe_handle *h, int n, const int *skip = nullptr) {
   const Mesh &m = h->mesh;
   double2 *Hrow = frow(h, n);
   const double *Ul = h->Useq.size() == 1 ? nullptr : h->d_U;
-  // the complex64 form holds Sigma in complex FP32 (its coefficient rows round it to complex64)
+  // the complex64 and split-FP16 forms hold Sigma in complex FP32 (their coefficient rows round
+  // it to complex64)
   cudaError_t e = kbe::sigma_row(m, h->v.data(), n, U_at(h, n), Ul, Hrow, h->Sig, h->work, h->stream, skip,
-                                 h->cfg.precision == KBE_PREC_C64);
+                                 h->cfg.precision == KBE_PREC_C64 || h->cfg.precision == KBE_PREC_F16X2);
   if (e != cudaSuccess) return cuda_fail(h, e, "sigma_row");
   const bool timed = h->prof;
   if (timed) {
@@ -270,7 +274,7 @@ kbe_status update(kbe_handle *h, int n, double theta, const int *skip = nullptr,
   double2 *prev = frow(h, n - 1);
   double2 *row = frow(h, n);
   // the update kernels also store row n into the history triangle ("publish")
-  char *hist = (char *)h->H + tri(n, 0) * 2 * h->blk * h->esz;
+  char *hist = (char *)h->H + kbe::history_row_offset(h->mesh, h->cfg.precision, n);
   cudaError_t e = kbe::launch_update_row(h->mesh, n, h->cfg.dt, theta, h->hk, h->U, h->V, prev, h->Ip,
                                          h->Ic, row, h->stream, skip, maxdiff, hist, h->cfg.precision);
   if (e != cudaSuccess) return cuda_fail(h, e, "update_row");
@@ -700,7 +704,8 @@ static size_t handle_bytes(const kbe_config *cfg) {
   const Mesh m{cfg->nb, cfg->L[0], cfg->L[1], cfg->L[0] * cfg->L[1]};
   const size_t T = (size_t)cfg->nt_max, nb2 = (size_t)cfg->nb * cfg->nb, blk = nb2 * m.nk;
   const size_t ntri = tri((int)T, (int)T) + 1, row = (T + 1) * 2 * blk * sizeof(double2);
-  size_t b = ntri * 2 * blk * kbe::history_elem_bytes(cfg->precision);
+  size_t b = kbe::history_bytes(m, cfg->precision, (int)T);
+  (void)ntri;
   b += 2 * row;                                                   // FP64 working rows
   b += kbe::sweep_workspace_bytes(m, (int)T, cfg->precision);      // sweep coefficients, partials
   b += 3 * row;                                                   // I rows, Sigma row
@@ -726,6 +731,8 @@ kbe_status kbe_create(const kbe_config *cfg, void *stream, kbe_handle **out) {
   if (!(cfg->dt > 0.0) || !std::isfinite(cfg->dt)) return fail(nullptr, KBE_ERR_ARG, "kbe_create: dt must be > 0");
   if (!std::isfinite(cfg->beta) || !std::isfinite(cfg->mu)) return fail(nullptr, KBE_ERR_ARG, "kbe_create: beta/mu not finite");
   if (!kbe::precision_supported(cfg->precision)) return fail(nullptr, KBE_ERR_UNSUPPORTED, "kbe_create: unknown precision");
+  if (cfg->precision == KBE_PREC_F16X2 && cfg->nb != 4 && cfg->nb != 8)
+    return fail(nullptr, KBE_ERR_UNSUPPORTED, "kbe_create: the split-FP16 (tensor-core) form needs nb 4 or 8");
   if (cfg->n_corr < 0 || cfg->n_corr > 64) return fail(nullptr, KBE_ERR_ARG, "kbe_create: n_corr out of range");
   if (!std::isfinite(cfg->corr_tol) || cfg->corr_tol < 0.0)
     return fail(nullptr, KBE_ERR_ARG, "kbe_create: corr_tol must be finite and >= 0");
@@ -748,7 +755,7 @@ kbe_status kbe_create(const kbe_config *cfg, void *stream, kbe_handle **out) {
   const size_t row = (T + 1) * 2 * h->blk;
   h->esz = kbe::history_elem_bytes(cfg->precision);
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = dalloc(h, (char **)&h->H, ntri * 2 * h->blk * h->esz);
+  if (e == cudaSuccess) e = dalloc(h, (char **)&h->H, kbe::history_bytes(h->mesh, cfg->precision, (int)T));
   if (e == cudaSuccess) e = dalloc(h, &h->Wrow[0], row);
   if (e == cudaSuccess) e = dalloc(h, &h->Wrow[1], row);
   if (e == cudaSuccess) e = dalloc(h, (char **)&h->coef, kbe::sweep_workspace_bytes(h->mesh, (int)T, cfg->precision));
@@ -1032,8 +1039,8 @@ kbe_status kbe_get_row_dev(kbe_handle *h, int i, int which, void *out_dev) {
   if (i < 0 || i > h->n || (which != 0 && which != 1)) return fail(h, KBE_ERR_ARG, "get_row_dev: bad row or component");
   const bool fp64_copy = i >= h->n - 1;   // the two newest rows are kept in FP64
   cudaError_t e = kbe::launch_row_out(h->cfg.precision, fp64_copy ? frow(h, i) : nullptr,
-                                      (const char *)h->H + tri(i, 0) * 2 * h->blk * h->esz, (size_t)i + 1,
-                                      h->mesh, which, (double2 *)out_dev, h->stream);
+                                      (const char *)h->H + kbe::history_row_offset(h->mesh, h->cfg.precision, i),
+                                      (size_t)i + 1, h->mesh, which, (double2 *)out_dev, h->stream, i);
   if (e != cudaSuccess) return cuda_fail(h, e, "get_row_dev");
   return KBE_OK;
 }
@@ -1051,15 +1058,26 @@ kbe_status kbe_get_row(kbe_handle *h, int i, int which, double *out) {
     e = cudaMemcpyAsync(tmp.data(), frow(h, i), sizeof(double2) * cnt, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   } else {                                                    // unpack the stored row
-    std::vector<char> raw(cnt * h->esz);
-    e = cudaMemcpyAsync(raw.data(), (char *)h->H + tri(i, 0) * 2 * h->blk * h->esz, raw.size(),
-                        cudaMemcpyDeviceToHost, h->stream);
+    const size_t off = kbe::history_row_offset(h->mesh, h->cfg.precision, i);
+    std::vector<char> raw(kbe::history_row_offset(h->mesh, h->cfg.precision, i + 1) - off);
+    e = cudaMemcpyAsync(raw.data(), (char *)h->H + off, raw.size(), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e == cudaSuccess) {
       const float *f = (const float *)raw.data();
       const double2 *d = (const double2 *)raw.data();
+      const __half *hv = (const __half *)raw.data();
+      const int nb = h->cfg.nb, nk = h->mesh.nk;
       for (size_t q = 0; q < cnt; ++q) {
-        if (h->cfg.precision == KBE_PREC_DF64)
+        if (h->cfg.precision == KBE_PREC_F16X2) {   // q = (block 2 + x) blk + (r nb + s) nk + k
+          const size_t bq = q / (2 * h->blk), rem = q - bq * 2 * h->blk;
+          const int x = (int)(rem / h->blk), rs = (int)((rem % h->blk) / nk), k = (int)(rem % nk);
+          const int r = rs / nb, sc = rs % nb;
+          const size_t o0 = kbe::f16x2_in_row(i, (int)bq, k, 0, x, r, sc, nb);
+          const size_t o1 = kbe::f16x2_in_row(i, (int)bq, k, 1, x, r, sc, nb);
+          tmp[q] = make_double2(((double)__half2float(hv[o0]) + (double)__half2float(hv[o1])) / kbe::kF16HistScale,
+                                ((double)__half2float(hv[o0 + 1]) + (double)__half2float(hv[o1 + 1])) /
+                                    kbe::kF16HistScale);
+        } else if (h->cfg.precision == KBE_PREC_DF64)
           tmp[q] = make_double2((double)f[4 * q] + (double)f[4 * q + 1], (double)f[4 * q + 2] + (double)f[4 * q + 3]);
         else if (h->cfg.precision == KBE_PREC_C64)
           tmp[q] = make_double2((double)f[2 * q], (double)f[2 * q + 1]);
@@ -1160,7 +1178,7 @@ std::vector<Region> state_regions(kbe_handle *h) {
   const int n = h->n;
   const size_t row = (size_t)(n + 1) * 2 * h->blk * sizeof(double2);
   std::vector<Region> r;
-  r.push_back({h->H, h->H, (tri(n, n) + 1) * 2 * h->blk * h->esz});
+  r.push_back({h->H, h->H, kbe::history_bytes(h->mesh, h->cfg.precision, n)});
   r.push_back({frow(h, n), frow(h, n), row});
   if (n >= 1) r.push_back({frow(h, n - 1), frow(h, n - 1), (size_t)n * 2 * h->blk * sizeof(double2)});
   r.push_back({h->Ip, h->Ip, row});
@@ -1381,9 +1399,28 @@ kbe_status kbe_op_pack(int precision, const void *src_dev, void *dst_dev, size_t
                        size_t block_elems, void *stream) {
   if (!kbe::precision_supported(precision) || (nblocks && block_elems && (!src_dev || !dst_dev)))
     return fail(nullptr, KBE_ERR_ARG, "op_pack: bad arguments");
+  if (precision == KBE_PREC_F16X2)
+    return fail(nullptr, KBE_ERR_UNSUPPORTED, "op_pack: the split-FP16 layout needs the mesh (kbe_op_pack_mesh)");
   cudaError_t e = kbe::launch_pack(precision, (const double2 *)src_dev, dst_dev, nblocks, block_elems,
                                    (cudaStream_t)stream);
   if (e != cudaSuccess) return fail(nullptr, KBE_ERR_CUDA, std::string("op_pack: ") + cudaGetErrorString(e));
+  return KBE_OK;
+}
+
+size_t kbe_history_bytes(const kbe_mesh *m, int n, int precision) {
+  if (!mesh_ok(m) || n < 0 || !kbe::precision_supported(precision)) return 0;
+  if (precision == KBE_PREC_F16X2 && m->nb != 4 && m->nb != 8) return 0;
+  return kbe::history_bytes(to_mesh(m), precision, n);
+}
+
+kbe_status kbe_op_pack_mesh(const kbe_mesh *m, int precision, const void *src_dev, void *dst_dev,
+                            size_t nblocks, void *stream) {
+  if (!mesh_ok(m) || !kbe::precision_supported(precision) || (nblocks && (!src_dev || !dst_dev)))
+    return fail(nullptr, KBE_ERR_ARG, "op_pack_mesh: bad arguments");
+  const kbe::Mesh mm = to_mesh(m);
+  cudaError_t e = kbe::launch_pack(precision, (const double2 *)src_dev, dst_dev, nblocks,
+                                   (size_t)mm.nb * mm.nb * mm.nk, (cudaStream_t)stream, nullptr, mm.nb, -1);
+  if (e != cudaSuccess) return fail(nullptr, KBE_ERR_CUDA, std::string("op_pack_mesh: ") + cudaGetErrorString(e));
   return KBE_OK;
 }
 

@@ -8,6 +8,7 @@
 // consecutive 16-byte elements.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -171,8 +172,93 @@ __device__ __forceinline__ float4 split_df(double2 x) {
   const float rh = __double2float_rn(x.x), ih = __double2float_rn(x.y);
   return make_float4(rh, __double2float_rn(x.x - (double)rh), ih, __double2float_rn(x.y - (double)ih));
 }
-__device__ __forceinline__ void pack_store(int prec, void *dst, size_t o0, size_t o1, double2 gl, double2 dg) {
-  if (prec == KBE_PREC_DF64) {
+// Split-FP16 pair history (KBE_PREC_F16X2): every stored complex number z is
+// kept as hi = fp16(S z), lo = fp16(S z - hi) per real part, S =
+// kF16HistScale (|G| <= 1 and |dG| <= 2, so S z stays far inside the FP16
+// range; below 2^-16 the pair keeps an absolute error of 2^-25 / S). The
+// layout is the tensor-core sweep's operand layout (kbe_sweep_tc.cu): row i
+// holds, for each k, its blocks in strips of TM = f16x2_tm(N_b) (the last
+// strip padded), and each strip is one contiguous "slot" of 16 N_b^2 TM bytes:
+//   [r / 4][h][x][block within the strip][s][r % 4][re/im]  halves
+// (h: hi / lo part, x: G^< / dG, element (r, s) of the N_b x N_b matrix), so
+// that a single bulk copy brings a row segment into shared memory as core
+// matrices of 8 rows x 16 bytes. Rows follow each other: row i starts after
+// n_k * (strips of rows 0 .. i-1) slots, and within it the slots are [k][strip].
+constexpr double kF16HistScale = 4096.0;
+__host__ __device__ constexpr int f16x2_tm(int nb) { return nb == 4 ? 16 : 8; }
+__host__ __device__ constexpr size_t f16x2_slot_halves(int nb) { return (size_t)8 * nb * nb * f16x2_tm(nb); }
+// strips in rows 0 .. i-1 (row i' has i' / TM + 1)
+__host__ __device__ inline size_t f16x2_strips_before(int i, int nb) {
+  const size_t tm = (size_t)f16x2_tm(nb), q = (size_t)i / tm, r = (size_t)i % tm;
+  return tm * q * (q + 1) / 2 + r * (q + 1);
+}
+// halves from the start of row i to element (h, x, r, s) of block (i, j) at k
+__host__ __device__ inline size_t f16x2_in_row(int i, int j, int k, int h, int x, int r, int s, int nb) {
+  const int tm = f16x2_tm(nb);
+  const size_t slot = (size_t)k * (i / tm + 1) + (size_t)(j / tm);
+  return slot * f16x2_slot_halves(nb) +
+         ((((size_t)(r / 4) * 4 + (size_t)(h * 2 + x)) * tm + (size_t)(j % tm)) * nb + (size_t)s) * 8 +
+         (size_t)(r % 4) * 2;
+}
+__host__ __device__ inline size_t f16x2_row_start(int i, int nb, int nk) {
+  return (size_t)nk * f16x2_strips_before(i, nb) * f16x2_slot_halves(nb);
+}
+// bytes of rows 0 .. n
+__host__ __device__ inline size_t f16x2_history_bytes(int n, int nb, int nk) {
+  return 2 * f16x2_row_start(n + 1, nb, nk);
+}
+// (hi, lo) of S z as two half2 values (re, im)
+__device__ __forceinline__ void f16x2_split(double2 z, __half2 &hi, __half2 &lo) {
+  const double sr = z.x * kF16HistScale, si = z.y * kF16HistScale;
+  const __half hr = __double2half(sr), hm = __double2half(si);
+  hi = __halves2half2(hr, hm);
+  lo = __halves2half2(__double2half(sr - (double)__half2float(hr)), __double2half(si - (double)__half2float(hm)));
+}
+// element (r, s) of component x of block (i, j) at k, as complex128 (H: the triangle)
+__device__ __forceinline__ double2 f16x2_get(const __half *H, int i, int j, int k, int x, int r, int s, int nb,
+                                             int nk) {
+  const __half *row = H + f16x2_row_start(i, nb, nk);
+  const __half2 hi = *reinterpret_cast<const __half2 *>(row + f16x2_in_row(i, j, k, 0, x, r, s, nb));
+  const __half2 lo = *reinterpret_cast<const __half2 *>(row + f16x2_in_row(i, j, k, 1, x, r, s, nb));
+  return make_double2(((double)__low2float(hi) + (double)__low2float(lo)) / kF16HistScale,
+                      ((double)__high2float(hi) + (double)__high2float(lo)) / kF16HistScale);
+}
+// block index bq of a triangle counted from row 0 -> (row, column)
+__device__ __forceinline__ void tri_decode(size_t bq, int &i, int &j) {
+  int ii = (int)((sqrt(8.0 * (double)bq + 1.0) - 1.0) / 2.0);
+  while ((size_t)ii * (ii + 1) / 2 > bq) --ii;
+  while ((size_t)(ii + 1) * (ii + 2) / 2 <= bq) ++ii;
+  i = ii;
+  j = (int)(bq - (size_t)ii * (ii + 1) / 2);
+}
+// o0 indexes component 0 of a block in the [block][x][r][s][k] numbering of the
+// other forms (block bq = o0 / (2 blk)); row >= 0: dst is the start of row
+// `row` and bq its column, row < 0: dst is the triangle and bq counts from row 0
+__device__ __forceinline__ void pack_store_f16x2(void *dst, size_t o0, int nb, int nk, int row, double2 gl,
+                                                 double2 dg) {
+  const size_t blk = (size_t)nb * nb * nk, bq = o0 / (2 * blk), rem = o0 - bq * 2 * blk;
+  const int rs = (int)(rem / nk), k = (int)(rem - (size_t)rs * nk), r = rs / nb, s = rs - r * nb;
+  int i = row, j = (int)bq;
+  __half *base = (__half *)dst;
+  if (row < 0) {
+    tri_decode(bq, i, j);
+    base += f16x2_row_start(i, nb, nk);
+  }
+  __half2 hi, lo;
+  f16x2_split(gl, hi, lo);
+  *reinterpret_cast<__half2 *>(base + f16x2_in_row(i, j, k, 0, 0, r, s, nb)) = hi;
+  *reinterpret_cast<__half2 *>(base + f16x2_in_row(i, j, k, 1, 0, r, s, nb)) = lo;
+  f16x2_split(dg, hi, lo);
+  *reinterpret_cast<__half2 *>(base + f16x2_in_row(i, j, k, 0, 1, r, s, nb)) = hi;
+  *reinterpret_cast<__half2 *>(base + f16x2_in_row(i, j, k, 1, 1, r, s, nb)) = lo;
+}
+// nb, nk, row: the mesh and the row dst starts (KBE_PREC_F16X2 only; row < 0:
+// dst is the whole triangle)
+__device__ __forceinline__ void pack_store(int prec, void *dst, size_t o0, size_t o1, double2 gl, double2 dg,
+                                           int nb = 0, int nk = 0, int row = -1) {
+  if (prec == KBE_PREC_F16X2) {
+    pack_store_f16x2(dst, o0, nb, nk, row, gl, dg);
+  } else if (prec == KBE_PREC_DF64) {
     ((float4 *)dst)[o0] = split_df(gl);
     ((float4 *)dst)[o1] = split_df(dg);
   } else if (prec == KBE_PREC_C64) {
@@ -242,12 +328,33 @@ size_t tile_part_bytes(const Mesh &m, int n, int TI);
 cudaError_t tile_prepare(int nb);
 cudaError_t launch_sweep_tile(const Mesh &m, int n, const void *H, const void *Cf, double2 *I, void *part,
                               cudaStream_t st, const int *skip, int quad, int *status, int TI);
+// the tensor-core sweep of the split-FP16 form (kbe_sweep_tc.cu): N_b in {4, 8};
+// TI rows per panel (a multiple of 16, at most tc_max_ti); part holds its
+// coefficient operands and partial sums (tc_part_bytes), headed by the word
+// that receives coef_kernel's largest |coefficient| (tc_cmax_word)
+bool tc_supported(const Mesh &m, int prec);
+int tc_max_ti(int nb);
+size_t tc_part_bytes(const Mesh &m, int n, int TI);
+unsigned *tc_cmax_word(void *part);
+double tc_tensor_flops(const Mesh &m, int n, int TI);   // tensor-core flops of one launch at row n
+// the tensor-core flops one sweep launch executes at row n with the panel
+// height the sweep will use (0 unless the form is the tensor-core one)
+double sweep_tc_flops(const Mesh &m, int prec, int quad, int n);
+cudaError_t tc_prepare(int nb);
+cudaError_t launch_sweep_tc(const Mesh &m, int n, const void *H, const void *Cf, double2 *I, void *part,
+                            cudaStream_t st, const int *skip, int quad, int *status, int TI);
+// nb: the mesh's N_b (required by KBE_PREC_F16X2, whose layout needs it);
+// row >= 0: the blocks are row `row` and dst is that row's start
+// (history_row_offset), row < 0: a triangle from row 0 and dst its start
 cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t nblocks, size_t blk,
-                        cudaStream_t st, const int *skip = nullptr);
+                        cudaStream_t st, const int *skip = nullptr, int nb = 0, int row = -1);
+// byte offset of row i in the history, and the bytes of rows 0 .. n
+size_t history_row_offset(const Mesh &m, int prec, int i);
+size_t history_bytes(const Mesh &m, int prec, int n);
 // component `which` of nblk blocks into [j][k][a][b]: from the FP64 working
 // row when fp64 != NULL, else from the history storage of precision prec
 cudaError_t launch_row_out(int prec, const double2 *fp64, const void *packed, size_t nblk, const Mesh &m,
-                           int which, double2 *out, cudaStream_t st);
+                           int which, double2 *out, cudaStream_t st, int row = -1);
 // status (may be NULL): device word that receives kDevTimeout if a staged
 // copy never completes (bounded waits)
 // inject (test only): 1 makes the staged C64 sweep's first CTA omit its first

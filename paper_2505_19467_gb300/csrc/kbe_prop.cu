@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(256) update_diag_kernel(int n, int nk, double 
     ol[blk] = gG;
     if (packed) {
       const size_t o0 = (size_t)n * 2 * blk + (size_t)g.e * nk + k;
-      pack_store(prec, packed, o0, o0 + blk, gg, c_sub(gg, gG));
+      pack_store(prec, packed, o0, o0 + blk, gg, c_sub(gg, gG), NB, nk, n);
     }
   }
 }
@@ -365,7 +365,7 @@ __global__ void update_rows_kernel(int n, int nk, double theta, const double2 *_
     }
     out[oo] = acc0;
     out[oo + blk] = acc1;
-    if (packed) pack_store(prec, packed, oo, oo + blk, acc0, c_sub(acc0, acc1));
+    if (packed) pack_store(prec, packed, oo, oo + blk, acc0, c_sub(acc0, acc1), NB, nk, n);
   }
   if (maxdiff) {   // every lane reaches here (blockDim is a multiple of 32)
 #pragma unroll

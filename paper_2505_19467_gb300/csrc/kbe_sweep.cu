@@ -739,8 +739,9 @@ __global__ void reduce_partials_kernel(const double2 *__restrict__ part, double2
 // --------------------------------------------------- packing and coefficients
 // nblocks blocks [2][nb][nb][nk] of (G^<, G^>) in FP64 -> (G^<, dG = G^< - G^>)
 // in the history storage (dG formed in FP64 before rounding)
+// (nb, nk, row: the mesh and the row of the blocks, used by the F16X2 layout)
 __global__ void pack_kernel(int prec, const double2 *__restrict__ src, void *__restrict__ dst,
-                            size_t nblocks, size_t blk, const int *__restrict__ skip) {
+                            size_t nblocks, size_t blk, const int *__restrict__ skip, int nb, int nk, int row) {
   if (skip && *skip) return;
   const size_t count = nblocks * blk;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
@@ -748,15 +749,16 @@ __global__ void pack_kernel(int prec, const double2 *__restrict__ src, void *__r
     const size_t bq = i / blk, r = i - bq * blk;
     const size_t o0 = bq * 2 * blk + r, o1 = o0 + blk;
     const double2 gl = src[o0];
-    pack_store(prec, dst, o0, o1, gl, c_sub(gl, src[o1]));
+    pack_store(prec, dst, o0, o1, gl, c_sub(gl, src[o1]), nb, nk, row);
   }
 }
 
 // one component of nblk blocks into [j][k][a][b] (the getters' layout): from
 // the FP64 working row (G^<, G^>) when fp64 != NULL, else from the history's
 // (G^<, dG) storage of precision prec (G^> = G^< - dG)
+// (row: the row index of the blocks, used by the F16X2 layout; packed is that row's start)
 __global__ void row_out_kernel(int prec, const double2 *__restrict__ fp64, const void *__restrict__ packed,
-                               size_t nblk, int nb, int nk, int which, double2 *__restrict__ out) {
+                               size_t nblk, int nb, int nk, int which, double2 *__restrict__ out, int row) {
   const size_t blk = (size_t)nb * nb * nk, count = nblk * blk;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (size_t)gridDim.x * blockDim.x) {
@@ -768,7 +770,19 @@ __global__ void row_out_kernel(int prec, const double2 *__restrict__ fp64, const
       v = fp64[which ? s1 : s0];
     } else {
       double2 gl, dg;
-      if (prec == KBE_PREC_DF64) {
+      if (prec == KBE_PREC_F16X2) {
+        const int a = ab / nb, b = ab - a * nb;
+        const __half *P = (const __half *)packed;
+        double2 z[2];
+        for (int x = 0; x < 2; ++x) {
+          const __half2 hi = *reinterpret_cast<const __half2 *>(P + f16x2_in_row(row, (int)j, k, 0, x, a, b, nb));
+          const __half2 lo = *reinterpret_cast<const __half2 *>(P + f16x2_in_row(row, (int)j, k, 1, x, a, b, nb));
+          z[x] = make_double2(((double)__low2float(hi) + (double)__low2float(lo)) / kF16HistScale,
+                              ((double)__high2float(hi) + (double)__high2float(lo)) / kF16HistScale);
+        }
+        gl = z[0];
+        dg = z[1];
+      } else if (prec == KBE_PREC_DF64) {
         const float4 a = ((const float4 *)packed)[s0], b = ((const float4 *)packed)[s1];
         gl = make_double2((double)a.x + (double)a.y, (double)a.z + (double)a.w);
         dg = make_double2((double)b.x + (double)b.y, (double)b.z + (double)b.w);
@@ -789,12 +803,16 @@ __global__ void row_out_kernel(int prec, const double2 *__restrict__ fp64, const
 // coefficient rows [l][3][a][c][k]: C1 = w^(n)_l (S^> - S^<), C2^< = dt S^<, C3 = dt S^> - C1
 // (FP64 also stores re + im of every coefficient in Cs, [l][3][a][c][k], for the
 // three-multiplication products of sweep_f64m_kernel)
+// cmax (may be NULL, zeroed before the launch): the largest |re|, |im| of C1
+// and C2^< over the row, as the bits of a non-negative float (the scale of the
+// tensor-core sweep's FP16 coefficient pairs)
 __global__ void coef_kernel(int prec, const double2 *__restrict__ Sig, void *__restrict__ Cf, int n,
                             int nk, int nb2, double dt, const int *__restrict__ skip, int quad,
-                            double *__restrict__ Cs) {
+                            double *__restrict__ Cs, unsigned *__restrict__ cmax) {
   if (skip && *skip) return;
   const size_t blk = (size_t)nb2 * nk;
   const size_t total = (size_t)(n + 1) * blk;
+  double big = 0.0;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
     const size_t l = i / blk, r = i - l * blk;
@@ -805,10 +823,17 @@ __global__ void coef_kernel(int prec, const double2 *__restrict__ Sig, void *__r
     for (int q = 0; q < 3; ++q) {
       const size_t o = (l * 3 + q) * blk + r;
       if (prec == KBE_PREC_DF64) ((float4 *)Cf)[o] = split_df(v[q]);
-      else if (prec == KBE_PREC_C64) ((float2 *)Cf)[o] = make_float2((float)v[q].x, (float)v[q].y);
+      else if (prec == KBE_PREC_C64 || prec == KBE_PREC_F16X2)
+        ((float2 *)Cf)[o] = make_float2((float)v[q].x, (float)v[q].y);
       else ((double2 *)Cf)[o] = v[q];
       if (Cs) Cs[o] = v[q].x + v[q].y;
     }
+    big = fmax(big, fmax(fmax(fabs(v[0].x), fabs(v[0].y)), fmax(fabs(v[1].x), fabs(v[1].y))));
+  }
+  if (cmax) {   // blockDim is a multiple of 32
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) big = fmax(big, __shfl_xor_sync(0xffffffffu, big, off));
+    if ((threadIdx.x & 31) == 0 && big > 0.0) atomicMax(cmax, __float_as_uint((float)big));
   }
 }
 
@@ -1387,9 +1412,20 @@ int tile_default(const Mesh &m, int prec, int n) {
   return tile_supported(m, prec) && n >= 255 ? -32 : 0;
 }
 
+// the tensor-core sweep of the split-FP16 form: TI = -choice rows per panel
+constexpr int kTcDefaultTI = 64;
+int tc_choice(const Mesh &m, int prec, int quad, int n) {
+  const int t = tuned_target(prec, quad, m, n, -kTcDefaultTI);
+  return t < 0 ? -t : kTcDefaultTI;
+}
+
 template <int NB>
 cudaError_t sweep_prec(const Mesh &m, int n, int prec, const void *H, const void *Cf, double2 *I,
                        double2 *part, cudaStream_t st, const int *skip, int quad, int *status, int inject) {
+  if (prec == KBE_PREC_F16X2) {
+    if (!tc_supported(m, prec)) return cudaErrorInvalidValue;
+    return launch_sweep_tc(m, n, H, Cf, I, part, st, skip, quad, status, tc_choice(m, prec, quad, n));
+  }
   if constexpr (NB == 2 || NB == 4 || NB == 8) {
     if (tile_supported(m, prec) && !inject) {
       const int t = tuned_target(prec, quad, m, n, tile_default(m, prec, n));
@@ -1417,6 +1453,10 @@ cudaError_t sweep_prec(const Mesh &m, int n, int prec, const void *H, const void
 }  // namespace
 
 bool use_f64m(const Mesh &m, int prec) { return prec == KBE_PREC_FP64 && m.nb <= 8; }
+
+double sweep_tc_flops(const Mesh &m, int prec, int quad, int n) {
+  return tc_supported(m, prec) ? tc_tensor_flops(m, n, tc_choice(m, prec, quad, n)) : 0.0;
+}
 
 // cuTensorMapEncodeTiled from the driver (no link against libcuda); resolved
 // once per process (a thread-safe static: the entry point is not per device)
@@ -1463,10 +1503,13 @@ bool sweep_supported(int nb) {
 }
 
 bool precision_supported(int prec) {
-  return prec == KBE_PREC_FP64 || prec == KBE_PREC_DF64 || prec == KBE_PREC_C64;
+  return prec == KBE_PREC_FP64 || prec == KBE_PREC_DF64 || prec == KBE_PREC_C64 || prec == KBE_PREC_F16X2;
 }
 
-size_t history_elem_bytes(int prec) { return prec == KBE_PREC_C64 ? sizeof(float2) : 16; }
+// bytes per stored complex number (F16X2: four halves)
+size_t history_elem_bytes(int prec) {
+  return prec == KBE_PREC_C64 || prec == KBE_PREC_F16X2 ? sizeof(float2) : 16;
+}
 
 // coefficient rows (n+1) x 3 blocks in the storage format, then the partial
 // sums of the l split (FP64) or of the tile form (complex64)
@@ -1492,10 +1535,15 @@ size_t sweep_workspace_bytes(const Mesh &m, int n, int prec) {
     const size_t b = tile_part_bytes(m, n, kTileMinTI);
     if (b > part) part = b;
   }
+  if (tc_supported(m, prec)) {     // the tensor-core form's operands and partials at its smallest TI
+    const size_t b = tc_part_bytes(m, n, kTileMinTI);
+    if (b > part) part = b;
+  }
   return coef + part;
 }
 
 int sweep_splits(const Mesh &m, int n, int prec, int quad) {
+  if (tc_supported(m, prec)) return 2;   // operand preparation, the MMA kernel, the reduction
   if ((m.nb == 2 || m.nb == 4 || m.nb == 8) && tile_supported(m, prec) &&
       tuned_target(prec, quad, m, n, tile_default(m, prec, n)) < 0)
     return 2;   // the tile kernel and its reduction
@@ -1516,6 +1564,11 @@ cudaError_t tune_sweep(const Mesh &m, int prec, int quad, int nmax, double dt, c
       cands.push_back(-ti);
       cands.push_back(-(ti + 1));
     }
+  if (tc_supported(m, prec)) {   // the tensor-core form: TI rows per panel only
+    cands.clear();
+    for (int ti : {kTileMinTI, 64, 128})
+      if (ti <= tc_max_ti(m.nb)) cands.push_back(-ti);
+  }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return cudaErrorUnknown;
   cudaError_t err = cudaSuccess;
@@ -1554,7 +1607,11 @@ cudaError_t tune_sweep(const Mesh &m, int prec, int quad, int nmax, double dt, c
 // manual form of the autotuner's table (kbe_set_sweep_choice): bucket -1 sets
 // every bucket; choice 0 removes the entry (the default applies again)
 bool set_sweep_choice(const Mesh &m, int prec, int quad, int bucket, int choice) {
-  if (choice < 0 && (!tile_supported(m, prec) || -choice < kTileMinTI || -choice > 4096)) return false;
+  if (tc_supported(m, prec)) {   // the tensor-core form takes only TI = -choice (a multiple of 16)
+    if (choice > 0 || (choice < 0 && (-choice < 16 || -choice % 16 != 0 || -choice > tc_max_ti(m.nb)))) return false;
+  } else if (choice < 0 && (!tile_supported(m, prec) || -choice < kTileMinTI || -choice > 4096)) {
+    return false;
+  }
   if (choice > 64 || bucket < -1 || bucket >= 31) return false;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   for (int b = bucket < 0 ? 0 : bucket; b <= (bucket < 0 ? 30 : bucket); ++b) {
@@ -1567,7 +1624,8 @@ bool set_sweep_choice(const Mesh &m, int prec, int quad, int bucket, int choice)
 
 // shared-memory limits of the staged kernels (host side, before any capture)
 cudaError_t sweep_prepare(int nb) {
-  const cudaError_t e = tile_prepare(nb);
+  cudaError_t e = tile_prepare(nb);
+  if (e == cudaSuccess) e = tc_prepare(nb);
   if (e != cudaSuccess) return e;
   switch (nb) {
     case 1: return staged_prepare<1>();
@@ -1580,17 +1638,30 @@ cudaError_t sweep_prepare(int nb) {
 }
 
 cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t nblocks, size_t blk,
-                        cudaStream_t st, const int *skip) {
+                        cudaStream_t st, const int *skip, int nb, int row) {
   if (nblocks == 0 || blk == 0) return cudaSuccess;
-  pack_kernel<<<grid_for(nblocks * blk), 256, 0, st>>>(prec, src, dst, nblocks, blk, skip);
+  if (prec == KBE_PREC_F16X2 && (!(nb == 4 || nb == 8) || blk % ((size_t)nb * nb) != 0)) return cudaErrorInvalidValue;
+  const int nk = nb > 0 ? (int)(blk / ((size_t)nb * nb)) : 0;
+  pack_kernel<<<grid_for(nblocks * blk), 256, 0, st>>>(prec, src, dst, nblocks, blk, skip, nb, nk, row);
   return cudaGetLastError();
 }
 
+size_t history_row_offset(const Mesh &m, int prec, int i) {
+  if (prec == KBE_PREC_F16X2) return 2 * f16x2_row_start(i, m.nb, m.nk);
+  return tri(i, 0) * 2 * (size_t)m.nb * m.nb * m.nk * history_elem_bytes(prec);
+}
+
+size_t history_bytes(const Mesh &m, int prec, int n) {
+  if (prec == KBE_PREC_F16X2) return f16x2_history_bytes(n, m.nb, m.nk);
+  return (tri(n, n) + 1) * 2 * (size_t)m.nb * m.nb * m.nk * history_elem_bytes(prec);
+}
+
 cudaError_t launch_row_out(int prec, const double2 *fp64, const void *packed, size_t nblk, const Mesh &m,
-                           int which, double2 *out, cudaStream_t st) {
+                           int which, double2 *out, cudaStream_t st, int row) {
   const size_t count = nblk * (size_t)m.nb * m.nb * m.nk;
   if (count == 0) return cudaSuccess;
-  row_out_kernel<<<grid_for(count), 256, 0, st>>>(prec, fp64, packed, nblk, m.nb, m.nk, which, out);
+  if (prec == KBE_PREC_F16X2 && !fp64 && row < 0) return cudaErrorInvalidValue;
+  row_out_kernel<<<grid_for(count), 256, 0, st>>>(prec, fp64, packed, nblk, m.nb, m.nk, which, out, row);
   return cudaGetLastError();
 }
 
@@ -1601,10 +1672,17 @@ cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const v
   const size_t blk = (size_t)m.nb * m.nb * m.nk;
   const size_t total = (size_t)(n + 1) * blk;
   double *Cs = precision == KBE_PREC_FP64 ? (double *)((double2 *)work + (size_t)(n + 1) * 3 * blk) : nullptr;
-  coef_kernel<<<grid_for(total), 256, 0, st>>>(precision, Sig, work, n, m.nk, m.nb * m.nb, dt, skip, quad, Cs);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
   double2 *part = (double2 *)((char *)work + coef_region_bytes(m, n, precision));
+  unsigned *cmax = nullptr;   // the tensor-core form's coefficient scale
+  cudaError_t e = cudaSuccess;
+  if (tc_supported(m, precision)) {
+    cmax = tc_cmax_word(part);
+    e = cudaMemsetAsync(cmax, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+  }
+  coef_kernel<<<grid_for(total), 256, 0, st>>>(precision, Sig, work, n, m.nk, m.nb * m.nb, dt, skip, quad, Cs, cmax);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   switch (m.nb) {
     case 1: return sweep_prec<1>(m, n, precision, H, work, I, part, st, skip, quad, status, inject);
     case 2: return sweep_prec<2>(m, n, precision, H, work, I, part, st, skip, quad, status, inject);

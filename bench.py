@@ -707,8 +707,9 @@ def sweep_row_study(kbe, row, names, reps=5, only_forms=None, only_ti=None):
             w = torch.empty(kbe.collision_row_workspace(nb, L, n, prec) // 4 + 1, dtype=torch.float32, device="cuda")
             alg = 2.0 * blk * (ntri * esz + 2.0 * (n + 1) * 16.0)
             choices = [("default", 0)]
-            if form == "f16x2":
+            if form == "f16x2":   # bulk copies of row groups, or loader warps (odd choice)
                 choices = [(f"tc_TI{t}", -t) for t in (32, 64, 128) if nb == 4 or t <= 64]
+                choices += [(f"tc_TI{t}_loader_warps", -(t + 1)) for t in (32, 64, 128) if nb == 4 or t <= 64]
             if form == "c64":
                 choices = [("per_column", 12 if nb >= 4 else 8)]
                 if nb in (2, 4, 8):

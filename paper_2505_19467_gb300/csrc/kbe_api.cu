@@ -204,7 +204,7 @@ double2 *frow(kbe_handle *h, int i) { return h->Wrow[i & 1]; }
 kbe_status publish(kbe_handle *h, int i, const int *skip = nullptr) {
   char *dst = (char *)h->H + kbe::history_row_offset(h->mesh, h->cfg.precision, i);
   cudaError_t e = kbe::launch_pack(h->cfg.precision, frow(h, i), dst, (size_t)(i + 1), h->blk, h->stream, skip,
-                                   h->cfg.nb, i);
+                                   h->cfg.nb, i, h->cfg.nt_max + 1);
   if (e != cudaSuccess) return cuda_fail(h, e, "publish row");
   if (h->prof) h->stats.launches += 1;
   return KBE_OK;
@@ -233,7 +233,7 @@ kbe_status evaluate_row(kbe_handle *h, int n, const int *skip = nullptr) {
     cudaEventRecord(h->ev[h->ev_used].first, h->stream);
   }
   e = kbe::launch_sweep(m, n, h->cfg.dt, h->cfg.precision, h->H, h->Sig, h->Ic, h->coef, h->stream, skip,
-                        h->cfg.quadrature, h->status, h->inject);
+                        h->cfg.quadrature, h->status, h->inject, h->cfg.nt_max + 1);
   h->inject = 0;
   if (e != cudaSuccess) return cuda_fail(h, e, "collision sweep");
   if (timed) {
@@ -276,7 +276,8 @@ kbe_status update(kbe_handle *h, int n, double theta, const int *skip = nullptr,
   // the update kernels also store row n into the history triangle ("publish")
   char *hist = (char *)h->H + kbe::history_row_offset(h->mesh, h->cfg.precision, n);
   cudaError_t e = kbe::launch_update_row(h->mesh, n, h->cfg.dt, theta, h->hk, h->U, h->V, prev, h->Ip,
-                                         h->Ic, row, h->stream, skip, maxdiff, hist, h->cfg.precision);
+                                         h->Ic, row, h->stream, skip, maxdiff, hist, h->cfg.precision,
+                                         h->cfg.nt_max + 1);
   if (e != cudaSuccess) return cuda_fail(h, e, "update_row");
   if (h->prof) h->stats.launches += 2;
   return KBE_OK;
@@ -950,7 +951,7 @@ kbe_status kbe_autotune(kbe_handle *h, int *targets) {
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e == cudaSuccess)
     e = kbe::tune_sweep(h->mesh, h->cfg.precision, h->cfg.quadrature, h->cfg.nt_max, h->cfg.dt, h->H, h->Sig, h->Ic,
-                        h->coef, h->stream, out, KBE_AUTOTUNE_BUCKETS);
+                        h->coef, h->stream, out, KBE_AUTOTUNE_BUCKETS, h->cfg.nt_max + 1);
   if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
   drop_graphs(h);   // captured sweeps carry the old splits
   if (targets)
@@ -1040,7 +1041,8 @@ kbe_status kbe_get_row_dev(kbe_handle *h, int i, int which, void *out_dev) {
   const bool fp64_copy = i >= h->n - 1;   // the two newest rows are kept in FP64
   cudaError_t e = kbe::launch_row_out(h->cfg.precision, fp64_copy ? frow(h, i) : nullptr,
                                       (const char *)h->H + kbe::history_row_offset(h->mesh, h->cfg.precision, i),
-                                      (size_t)i + 1, h->mesh, which, (double2 *)out_dev, h->stream, i);
+                                      (size_t)i + 1, h->mesh, which, (double2 *)out_dev, h->stream, i,
+                                      h->cfg.nt_max + 1);
   if (e != cudaSuccess) return cuda_fail(h, e, "get_row_dev");
   return KBE_OK;
 }
@@ -1052,6 +1054,18 @@ kbe_status kbe_get_row(kbe_handle *h, int i, int which, double *out) {
   if (s != KBE_OK && s != KBE_ERR_NONFINITE) return s;
   const size_t nblk = (size_t)i + 1;
   const size_t cnt = nblk * 2 * h->blk;
+  if (h->cfg.precision == KBE_PREC_F16X2 && i < h->n - 1) {
+    // the split-FP16 storage spreads the row over its strips: decode it on the
+    // device into the Sigma row buffer (a whole row of complex128, rewritten by
+    // the next step before use), then copy it out
+    cudaError_t e = kbe::launch_row_out(h->cfg.precision, nullptr, h->H, nblk, h->mesh, which, h->Sig, h->stream, i,
+                                        h->cfg.nt_max + 1);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out, h->Sig, sizeof(double2) * nblk * h->blk, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "get_row decode");
+    return KBE_OK;
+  }
   std::vector<double2> tmp(cnt);
   cudaError_t e;
   if (i >= h->n - 1) {                                        // an FP64 copy exists
@@ -1065,19 +1079,8 @@ kbe_status kbe_get_row(kbe_handle *h, int i, int which, double *out) {
     if (e == cudaSuccess) {
       const float *f = (const float *)raw.data();
       const double2 *d = (const double2 *)raw.data();
-      const __half *hv = (const __half *)raw.data();
-      const int nb = h->cfg.nb, nk = h->mesh.nk;
       for (size_t q = 0; q < cnt; ++q) {
-        if (h->cfg.precision == KBE_PREC_F16X2) {   // q = (block 2 + x) blk + (r nb + s) nk + k
-          const size_t bq = q / (2 * h->blk), rem = q - bq * 2 * h->blk;
-          const int x = (int)(rem / h->blk), rs = (int)((rem % h->blk) / nk), k = (int)(rem % nk);
-          const int r = rs / nb, sc = rs % nb;
-          const size_t o0 = kbe::f16x2_in_row(i, (int)bq, k, 0, x, r, sc, nb);
-          const size_t o1 = kbe::f16x2_in_row(i, (int)bq, k, 1, x, r, sc, nb);
-          tmp[q] = make_double2(((double)__half2float(hv[o0]) + (double)__half2float(hv[o1])) / kbe::kF16HistScale,
-                                ((double)__half2float(hv[o0 + 1]) + (double)__half2float(hv[o1 + 1])) /
-                                    kbe::kF16HistScale);
-        } else if (h->cfg.precision == KBE_PREC_DF64)
+        if (h->cfg.precision == KBE_PREC_DF64)
           tmp[q] = make_double2((double)f[4 * q] + (double)f[4 * q + 1], (double)f[4 * q + 2] + (double)f[4 * q + 3]);
         else if (h->cfg.precision == KBE_PREC_C64)
           tmp[q] = make_double2((double)f[2 * q], (double)f[2 * q + 1]);
@@ -1178,7 +1181,9 @@ std::vector<Region> state_regions(kbe_handle *h) {
   const int n = h->n;
   const size_t row = (size_t)(n + 1) * 2 * h->blk * sizeof(double2);
   std::vector<Region> r;
-  r.push_back({h->H, h->H, kbe::history_bytes(h->mesh, h->cfg.precision, n)});
+  // (the split-FP16 storage spreads every row over its strips: all of it)
+  r.push_back({h->H, h->H, kbe::history_bytes(h->mesh, h->cfg.precision,
+                                              h->cfg.precision == KBE_PREC_F16X2 ? h->cfg.nt_max : n)});
   r.push_back({frow(h, n), frow(h, n), row});
   if (n >= 1) r.push_back({frow(h, n - 1), frow(h, n - 1), (size_t)n * 2 * h->blk * sizeof(double2)});
   r.push_back({h->Ip, h->Ip, row});
@@ -1418,8 +1423,12 @@ kbe_status kbe_op_pack_mesh(const kbe_mesh *m, int precision, const void *src_de
   if (!mesh_ok(m) || !kbe::precision_supported(precision) || (nblocks && (!src_dev || !dst_dev)))
     return fail(nullptr, KBE_ERR_ARG, "op_pack_mesh: bad arguments");
   const kbe::Mesh mm = to_mesh(m);
+  int cap = 0;   // the F16X2 layout holds rows 0 .. cap - 1: nblocks must be a triangle
+  while ((size_t)cap * (cap + 1) / 2 < nblocks) ++cap;
+  if (precision == KBE_PREC_F16X2 && (size_t)cap * (cap + 1) / 2 != nblocks)
+    return fail(nullptr, KBE_ERR_ARG, "op_pack_mesh: F16X2 needs a whole triangle, nblocks = (n+1)(n+2)/2");
   cudaError_t e = kbe::launch_pack(precision, (const double2 *)src_dev, dst_dev, nblocks,
-                                   (size_t)mm.nb * mm.nb * mm.nk, (cudaStream_t)stream, nullptr, mm.nb, -1);
+                                   (size_t)mm.nb * mm.nb * mm.nk, (cudaStream_t)stream, nullptr, mm.nb, -1, cap);
   if (e != cudaSuccess) return fail(nullptr, KBE_ERR_CUDA, std::string("op_pack_mesh: ") + cudaGetErrorString(e));
   return KBE_OK;
 }

@@ -176,36 +176,41 @@ __device__ __forceinline__ float4 split_df(double2 x) {
 // kept as hi = fp16(S z), lo = fp16(S z - hi) per real part, S =
 // kF16HistScale (|G| <= 1 and |dG| <= 2, so S z stays far inside the FP16
 // range; below 2^-16 the pair keeps an absolute error of 2^-25 / S). The
-// layout is the tensor-core sweep's operand layout (kbe_sweep_tc.cu): row i
-// holds, for each k, its blocks in strips of TM = f16x2_tm(N_b) (the last
-// strip padded), and each strip is one contiguous "slot" of 16 N_b^2 TM bytes:
-//   [r / 4][h][x][block within the strip][s][r % 4][re/im]  halves
-// (h: hi / lo part, x: G^< / dG, element (r, s) of the N_b x N_b matrix), so
-// that a single bulk copy brings a row segment into shared memory as core
-// matrices of 8 rows x 16 bytes. Rows follow each other: row i starts after
-// n_k * (strips of rows 0 .. i-1) slots, and within it the slots are [k][strip].
+// layout is the tensor-core sweep's operand layout (kbe_sweep_tc.cu). Column
+// blocks come in strips of TM = f16x2_tm(N_b); block (i, j) at k belongs to
+// strip s = j / TM, and one "slot" of 16 N_b^2 TM bytes holds the strip's
+// blocks of row i:
+//   [r / 4][h][x][j % TM][s][r % 4][re/im]  halves
+// (h: hi / lo part, x: G^< / dG, element (r, s) of the N_b x N_b matrix).
+// Per k, the strips follow each other and each strip holds its rows
+// s TM .. cap - 1 as consecutive slots, cap = the rows the storage holds. A
+// group of consecutive rows of one strip is therefore one contiguous range:
+// one bulk copy lands it in shared memory as core matrices of 8 rows x 16
+// bytes. Padding slots (blocks beyond a row's end) are never written.
 constexpr double kF16HistScale = 4096.0;
 __host__ __device__ constexpr int f16x2_tm(int nb) { return nb == 4 ? 16 : 8; }
 __host__ __device__ constexpr size_t f16x2_slot_halves(int nb) { return (size_t)8 * nb * nb * f16x2_tm(nb); }
-// strips in rows 0 .. i-1 (row i' has i' / TM + 1)
-__host__ __device__ inline size_t f16x2_strips_before(int i, int nb) {
-  const size_t tm = (size_t)f16x2_tm(nb), q = (size_t)i / tm, r = (size_t)i % tm;
-  return tm * q * (q + 1) / 2 + r * (q + 1);
+// first slot of strip s within one k (strips hold rows s TM .. cap - 1)
+__host__ __device__ inline size_t f16x2_colstart(int s, int cap, int nb) {
+  return (size_t)s * cap - (size_t)f16x2_tm(nb) * s * (s - 1) / 2;
 }
-// halves from the start of row i to element (h, x, r, s) of block (i, j) at k
-__host__ __device__ inline size_t f16x2_in_row(int i, int j, int k, int h, int x, int r, int s, int nb) {
+__host__ __device__ inline size_t f16x2_kslots(int cap, int nb) {
+  return f16x2_colstart((cap - 1) / f16x2_tm(nb) + 1, cap, nb);
+}
+// slot of row i in strip s at k
+__host__ __device__ inline size_t f16x2_slot(int i, int s, int k, int cap, int nb) {
+  return (size_t)k * f16x2_kslots(cap, nb) + f16x2_colstart(s, cap, nb) + (size_t)(i - s * f16x2_tm(nb));
+}
+// halves from the storage start to element (h, x, r, s) of block (i, j) at k
+__host__ __device__ inline size_t f16x2_index(int i, int j, int k, int h, int x, int r, int s, int nb, int cap) {
   const int tm = f16x2_tm(nb);
-  const size_t slot = (size_t)k * (i / tm + 1) + (size_t)(j / tm);
-  return slot * f16x2_slot_halves(nb) +
+  return f16x2_slot(i, j / tm, k, cap, nb) * f16x2_slot_halves(nb) +
          ((((size_t)(r / 4) * 4 + (size_t)(h * 2 + x)) * tm + (size_t)(j % tm)) * nb + (size_t)s) * 8 +
          (size_t)(r % 4) * 2;
 }
-__host__ __device__ inline size_t f16x2_row_start(int i, int nb, int nk) {
-  return (size_t)nk * f16x2_strips_before(i, nb) * f16x2_slot_halves(nb);
-}
-// bytes of rows 0 .. n
-__host__ __device__ inline size_t f16x2_history_bytes(int n, int nb, int nk) {
-  return 2 * f16x2_row_start(n + 1, nb, nk);
+// bytes of a storage holding rows 0 .. cap - 1
+__host__ __device__ inline size_t f16x2_history_bytes(int cap, int nb, int nk) {
+  return (size_t)nk * f16x2_kslots(cap, nb) * f16x2_slot_halves(nb) * 2;
 }
 // (hi, lo) of S z as two half2 values (re, im)
 __device__ __forceinline__ void f16x2_split(double2 z, __half2 &hi, __half2 &lo) {
@@ -214,14 +219,25 @@ __device__ __forceinline__ void f16x2_split(double2 z, __half2 &hi, __half2 &lo)
   hi = __halves2half2(hr, hm);
   lo = __halves2half2(__double2half(sr - (double)__half2float(hr)), __double2half(si - (double)__half2float(hm)));
 }
-// element (r, s) of component x of block (i, j) at k, as complex128 (H: the triangle)
-__device__ __forceinline__ double2 f16x2_get(const __half *H, int i, int j, int k, int x, int r, int s, int nb,
-                                             int nk) {
-  const __half *row = H + f16x2_row_start(i, nb, nk);
-  const __half2 hi = *reinterpret_cast<const __half2 *>(row + f16x2_in_row(i, j, k, 0, x, r, s, nb));
-  const __half2 lo = *reinterpret_cast<const __half2 *>(row + f16x2_in_row(i, j, k, 1, x, r, s, nb));
+__device__ __forceinline__ double2 f16x2_value(__half2 hi, __half2 lo) {
   return make_double2(((double)__low2float(hi) + (double)__low2float(lo)) / kF16HistScale,
                       ((double)__high2float(hi) + (double)__high2float(lo)) / kF16HistScale);
+}
+// element (r, s) of component x of block (i, j) at k, as complex128
+// halves between the x planes of a slot (the h planes are twice as far apart)
+__host__ __device__ constexpr size_t f16x2_xplane(int nb) { return (size_t)8 * nb * f16x2_tm(nb); }
+__device__ __forceinline__ double2 f16x2_get(const __half *H, int i, int j, int k, int x, int r, int s, int nb,
+                                             int cap) {
+  const size_t o = f16x2_index(i, j, k, 0, x, r, s, nb, cap), lo = 2 * f16x2_xplane(nb);   // the h = 1 plane
+  return f16x2_value(*reinterpret_cast<const __half2 *>(H + o), *reinterpret_cast<const __half2 *>(H + o + lo));
+}
+// the same in FP32 (hi + lo is exact in FP32: the pair spans 22 bits)
+__device__ __forceinline__ float2 f16x2_getf(const __half *H, int i, int j, int k, int x, int r, int s, int nb, int cap) {
+  const size_t o = f16x2_index(i, j, k, 0, x, r, s, nb, cap), lo = 2 * f16x2_xplane(nb);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(H + o));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(H + o + lo));
+  constexpr float inv = (float)(1.0 / kF16HistScale);
+  return make_float2((a.x + b.x) * inv, (a.y + b.y) * inv);
 }
 // block index bq of a triangle counted from row 0 -> (row, column)
 __device__ __forceinline__ void tri_decode(size_t bq, int &i, int &j) {
@@ -232,32 +248,31 @@ __device__ __forceinline__ void tri_decode(size_t bq, int &i, int &j) {
   j = (int)(bq - (size_t)ii * (ii + 1) / 2);
 }
 // o0 indexes component 0 of a block in the [block][x][r][s][k] numbering of the
-// other forms (block bq = o0 / (2 blk)); row >= 0: dst is the start of row
-// `row` and bq its column, row < 0: dst is the triangle and bq counts from row 0
-__device__ __forceinline__ void pack_store_f16x2(void *dst, size_t o0, int nb, int nk, int row, double2 gl,
+// other forms (block bq = o0 / (2 blk)); dst is the storage start; row >= 0:
+// the blocks are row `row` and bq its column, row < 0: bq counts from row 0
+__device__ __forceinline__ void pack_store_f16x2(void *dst, size_t o0, int nb, int nk, int row, int cap, double2 gl,
                                                  double2 dg) {
   const size_t blk = (size_t)nb * nb * nk, bq = o0 / (2 * blk), rem = o0 - bq * 2 * blk;
   const int rs = (int)(rem / nk), k = (int)(rem - (size_t)rs * nk), r = rs / nb, s = rs - r * nb;
   int i = row, j = (int)bq;
-  __half *base = (__half *)dst;
-  if (row < 0) {
-    tri_decode(bq, i, j);
-    base += f16x2_row_start(i, nb, nk);
-  }
-  __half2 hi, lo;
-  f16x2_split(gl, hi, lo);
-  *reinterpret_cast<__half2 *>(base + f16x2_in_row(i, j, k, 0, 0, r, s, nb)) = hi;
-  *reinterpret_cast<__half2 *>(base + f16x2_in_row(i, j, k, 1, 0, r, s, nb)) = lo;
-  f16x2_split(dg, hi, lo);
-  *reinterpret_cast<__half2 *>(base + f16x2_in_row(i, j, k, 0, 1, r, s, nb)) = hi;
-  *reinterpret_cast<__half2 *>(base + f16x2_in_row(i, j, k, 1, 1, r, s, nb)) = lo;
+  if (row < 0) tri_decode(bq, i, j);
+  __half *H = (__half *)dst;
+  const size_t o = f16x2_index(i, j, k, 0, 0, r, s, nb, cap), dx = f16x2_xplane(nb), lo = 2 * dx;
+  __half2 hi, lw;
+  f16x2_split(gl, hi, lw);
+  *reinterpret_cast<__half2 *>(H + o) = hi;
+  *reinterpret_cast<__half2 *>(H + o + lo) = lw;
+  f16x2_split(dg, hi, lw);
+  *reinterpret_cast<__half2 *>(H + o + dx) = hi;
+  *reinterpret_cast<__half2 *>(H + o + dx + lo) = lw;
 }
-// nb, nk, row: the mesh and the row dst starts (KBE_PREC_F16X2 only; row < 0:
-// dst is the whole triangle)
+// nb, nk, row, cap: the mesh, the row of the blocks (< 0: a triangle from row
+// 0) and the rows the storage holds (KBE_PREC_F16X2 only; dst is then the
+// storage start)
 __device__ __forceinline__ void pack_store(int prec, void *dst, size_t o0, size_t o1, double2 gl, double2 dg,
-                                           int nb = 0, int nk = 0, int row = -1) {
+                                           int nb = 0, int nk = 0, int row = -1, int cap = 0) {
   if (prec == KBE_PREC_F16X2) {
-    pack_store_f16x2(dst, o0, nb, nk, row, gl, dg);
+    pack_store_f16x2(dst, o0, nb, nk, row, cap, gl, dg);
   } else if (prec == KBE_PREC_DF64) {
     ((float4 *)dst)[o0] = split_df(gl);
     ((float4 *)dst)[o1] = split_df(dg);
@@ -316,7 +331,7 @@ size_t sweep_workspace_bytes(const Mesh &m, int n, int prec);
 int sweep_splits(const Mesh &m, int n, int prec, int quad);   // CTAs sharing one output's l range
 // autotuner of the l-split (see kbe_sweep.cu); out[b] per row bucket b
 cudaError_t tune_sweep(const Mesh &m, int prec, int quad, int nmax, double dt, const void *H, const double2 *Sig,
-                       double2 *I, void *work, cudaStream_t st, int *out, int nout);
+                       double2 *I, void *work, cudaStream_t st, int *out, int nout, int cap = 0);
 cudaError_t sweep_prepare(int nb);   // kernel attributes, host side (before stream capture)
 // set (choice != 0) or clear (0) the tuned launch choice of a sweep shape for
 // row bucket `bucket` (-1: all); false if the choice does not apply
@@ -342,27 +357,31 @@ double tc_tensor_flops(const Mesh &m, int n, int TI);   // tensor-core flops of 
 double sweep_tc_flops(const Mesh &m, int prec, int quad, int n);
 cudaError_t tc_prepare(int nb);
 cudaError_t launch_sweep_tc(const Mesh &m, int n, const void *H, const void *Cf, double2 *I, void *part,
-                            cudaStream_t st, const int *skip, int quad, int *status, int TI);
+                            cudaStream_t st, const int *skip, int quad, int *status, int TI, int cap);
 // nb: the mesh's N_b (required by KBE_PREC_F16X2, whose layout needs it);
 // row >= 0: the blocks are row `row` and dst is that row's start
-// (history_row_offset), row < 0: a triangle from row 0 and dst its start
+// (history_row_offset), row < 0: a triangle from row 0 and dst its start;
+// cap: the rows the storage holds (F16X2)
 cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t nblocks, size_t blk,
-                        cudaStream_t st, const int *skip = nullptr, int nb = 0, int row = -1);
-// byte offset of row i in the history, and the bytes of rows 0 .. n
+                        cudaStream_t st, const int *skip = nullptr, int nb = 0, int row = -1, int cap = 0);
+// byte offset of row i in the history (0 for F16X2, whose rows are spread
+// over the strips: its kernels address the whole storage), and the bytes of
+// a storage for rows 0 .. n
 size_t history_row_offset(const Mesh &m, int prec, int i);
 size_t history_bytes(const Mesh &m, int prec, int n);
 // component `which` of nblk blocks into [j][k][a][b]: from the FP64 working
 // row when fp64 != NULL, else from the history storage of precision prec
 cudaError_t launch_row_out(int prec, const double2 *fp64, const void *packed, size_t nblk, const Mesh &m,
-                           int which, double2 *out, cudaStream_t st, int row = -1);
+                           int which, double2 *out, cudaStream_t st, int row = -1, int cap = 0);
 // status (may be NULL): device word that receives kDevTimeout if a staged
 // copy never completes (bounded waits)
 // inject (test only): 1 makes the staged C64 sweep's first CTA omit its first
 // node's copies, so that its bounded waits run out (kDevTimeout), no fault
+// cap: the rows H holds (the F16X2 layout depends on it; <= 0: n + 1)
 cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const void *H,
                          const double2 *Sig, double2 *I, void *work, cudaStream_t st,
                          const int *skip = nullptr, int quad = kQuadTrapezoid, int *status = nullptr,
-                         int inject = 0);
+                         int inject = 0, int cap = 0);
 
 // a3 propagators / initial state / density
 struct HopTable {
@@ -397,12 +416,14 @@ cudaError_t launch_build_props(const Mesh &m, const HopTable &hop, const PropPar
 // maxdiff (may be NULL): max over the new row of |G^< - its previous value in
 // out| is folded in (atomicMax on the bits of a non-negative double).
 // packed (may be NULL): the history's row n in the storage of precision prec,
-// written with the row ((G^<, dG) per block, as kbe_op_pack would).
+// written with the row ((G^<, dG) per block, as kbe_op_pack would); for
+// KBE_PREC_F16X2 the storage start, holding cap rows.
 cudaError_t launch_update_row(const Mesh &m, int n, double dt, double theta, const double2 *h,
                               const double2 *U, const double2 *V, const double2 *Gprev,
                               const double2 *Iprev, const double2 *Icur, double2 *out,
                               cudaStream_t st, const int *skip = nullptr,
-                              unsigned long long *maxdiff = nullptr, void *packed = nullptr, int prec = 0);
+                              unsigned long long *maxdiff = nullptr, void *packed = nullptr, int prec = 0,
+                              int cap = 0);
 // Algorithm 1's convergence test after a corrector pass (one thread): unless
 // skip is set, count the pass in *iters, set skip when *maxdiff <= tol, and
 // clear *maxdiff for the next pass.

@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(256) update_diag_kernel(int n, int nk, double 
                                                           double2 *__restrict__ out, int kpc,
                                                           const int *__restrict__ skip,
                                                           unsigned long long *maxdiff, void *__restrict__ packed,
-                                                          int prec) {
+                                                          int prec, int cap) {
   if (skip && *skip) return;
   using G = MatGroup<NB>;
   const int span = kpc * G::E;
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(256) update_diag_kernel(int n, int nk, double 
     ol[blk] = gG;
     if (packed) {
       const size_t o0 = (size_t)n * 2 * blk + (size_t)g.e * nk + k;
-      pack_store(prec, packed, o0, o0 + blk, gg, c_sub(gg, gG), NB, nk, n);
+      pack_store(prec, packed, o0, o0 + blk, gg, c_sub(gg, gG), NB, nk, n, cap);
     }
   }
 }
@@ -328,7 +328,7 @@ __global__ void update_rows_kernel(int n, int nk, double theta, const double2 *_
                                    const double2 *__restrict__ V, const double2 *__restrict__ Gprev,
                                    const double2 *__restrict__ Ip, const double2 *__restrict__ Ic,
                                    double2 *__restrict__ out, const int *__restrict__ skip,
-                                   unsigned long long *maxdiff, void *__restrict__ packed, int prec) {
+                                   unsigned long long *maxdiff, void *__restrict__ packed, int prec, int cap) {
   if (skip && *skip) return;
   const size_t blk = (size_t)NB * NB * nk;
   const size_t total = (size_t)n * blk;
@@ -365,7 +365,7 @@ __global__ void update_rows_kernel(int n, int nk, double theta, const double2 *_
     }
     out[oo] = acc0;
     out[oo + blk] = acc1;
-    if (packed) pack_store(prec, packed, oo, oo + blk, acc0, c_sub(acc0, acc1), NB, nk, n);
+    if (packed) pack_store(prec, packed, oo, oo + blk, acc0, c_sub(acc0, acc1), NB, nk, n, cap);
   }
   if (maxdiff) {   // every lane reaches here (blockDim is a multiple of 32)
 #pragma unroll
@@ -475,7 +475,7 @@ cudaError_t launch_update_row(const Mesh &m, int n, double dt, double theta, con
                               const double2 *U, const double2 *V, const double2 *Gprev,
                               const double2 *Iprev, const double2 *Icur, double2 *out,
                               cudaStream_t st, const int *skip, unsigned long long *maxdiff, void *packed,
-                              int prec) {
+                              int prec, int cap) {
   const size_t blk = (size_t)m.nb * m.nb * m.nk;
   const size_t total = (size_t)n * blk;
   const int threads = 256;
@@ -483,14 +483,15 @@ cudaError_t launch_update_row(const Mesh &m, int n, double dt, double theta, con
   const double2 *ic = (theta != 0.0) ? Icur : Iprev;
   if (total > 0) {
     KBE_NB_SWITCH(m.nb, (update_rows_kernel<NB><<<blocks, threads, 0, st>>>(n, m.nk, theta, U, V, Gprev, Iprev, ic,
-                                                                             out, skip, maxdiff, packed, prec)));
+                                                                             out, skip, maxdiff, packed, prec,
+                                                                             cap)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   KBE_NB_SWITCH(m.nb, (update_diag_kernel<NB><<<matgroup_blocks<NB>(m.nk), matgroup_threads<NB>(m.nk),
                                                  matgroup_smem<NB>(m.nk, 5), st>>>(
                           n, m.nk, dt, theta, h, Gprev, Iprev, ic, out, matgroup_kpc<NB>(m.nk), skip,
-                          maxdiff, packed, prec)));
+                          maxdiff, packed, prec, cap)));
   return cudaGetLastError();
 }
 

@@ -741,7 +741,8 @@ __global__ void reduce_partials_kernel(const double2 *__restrict__ part, double2
 // in the history storage (dG formed in FP64 before rounding)
 // (nb, nk, row: the mesh and the row of the blocks, used by the F16X2 layout)
 __global__ void pack_kernel(int prec, const double2 *__restrict__ src, void *__restrict__ dst,
-                            size_t nblocks, size_t blk, const int *__restrict__ skip, int nb, int nk, int row) {
+                            size_t nblocks, size_t blk, const int *__restrict__ skip, int nb, int nk, int row,
+                            int cap) {
   if (skip && *skip) return;
   const size_t count = nblocks * blk;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
@@ -749,16 +750,18 @@ __global__ void pack_kernel(int prec, const double2 *__restrict__ src, void *__r
     const size_t bq = i / blk, r = i - bq * blk;
     const size_t o0 = bq * 2 * blk + r, o1 = o0 + blk;
     const double2 gl = src[o0];
-    pack_store(prec, dst, o0, o1, gl, c_sub(gl, src[o1]), nb, nk, row);
+    pack_store(prec, dst, o0, o1, gl, c_sub(gl, src[o1]), nb, nk, row, cap);
   }
 }
 
 // one component of nblk blocks into [j][k][a][b] (the getters' layout): from
 // the FP64 working row (G^<, G^>) when fp64 != NULL, else from the history's
 // (G^<, dG) storage of precision prec (G^> = G^< - dG)
-// (row: the row index of the blocks, used by the F16X2 layout; packed is that row's start)
+// (row, cap: the row of the blocks and the rows the storage holds, used by the
+// F16X2 layout, for which packed is the storage start)
 __global__ void row_out_kernel(int prec, const double2 *__restrict__ fp64, const void *__restrict__ packed,
-                               size_t nblk, int nb, int nk, int which, double2 *__restrict__ out, int row) {
+                               size_t nblk, int nb, int nk, int which, double2 *__restrict__ out, int row,
+                               int cap) {
   const size_t blk = (size_t)nb * nb * nk, count = nblk * blk;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (size_t)gridDim.x * blockDim.x) {
@@ -772,16 +775,8 @@ __global__ void row_out_kernel(int prec, const double2 *__restrict__ fp64, const
       double2 gl, dg;
       if (prec == KBE_PREC_F16X2) {
         const int a = ab / nb, b = ab - a * nb;
-        const __half *P = (const __half *)packed;
-        double2 z[2];
-        for (int x = 0; x < 2; ++x) {
-          const __half2 hi = *reinterpret_cast<const __half2 *>(P + f16x2_in_row(row, (int)j, k, 0, x, a, b, nb));
-          const __half2 lo = *reinterpret_cast<const __half2 *>(P + f16x2_in_row(row, (int)j, k, 1, x, a, b, nb));
-          z[x] = make_double2(((double)__low2float(hi) + (double)__low2float(lo)) / kF16HistScale,
-                              ((double)__high2float(hi) + (double)__high2float(lo)) / kF16HistScale);
-        }
-        gl = z[0];
-        dg = z[1];
+        gl = f16x2_get((const __half *)packed, row, (int)j, k, 0, a, b, nb, cap);
+        dg = f16x2_get((const __half *)packed, row, (int)j, k, 1, a, b, nb, cap);
       } else if (prec == KBE_PREC_DF64) {
         const float4 a = ((const float4 *)packed)[s0], b = ((const float4 *)packed)[s1];
         gl = make_double2((double)a.x + (double)a.y, (double)a.z + (double)a.w);
@@ -1414,6 +1409,7 @@ int tile_default(const Mesh &m, int prec, int n) {
 
 // the tensor-core sweep of the split-FP16 form: TI = -choice rows per panel
 constexpr int kTcDefaultTI = 64;
+// (odd: TI - 1 rows per panel, the row segments copied by loader warps)
 int tc_choice(const Mesh &m, int prec, int quad, int n) {
   const int t = tuned_target(prec, quad, m, n, -kTcDefaultTI);
   return t < 0 ? -t : kTcDefaultTI;
@@ -1421,10 +1417,11 @@ int tc_choice(const Mesh &m, int prec, int quad, int n) {
 
 template <int NB>
 cudaError_t sweep_prec(const Mesh &m, int n, int prec, const void *H, const void *Cf, double2 *I,
-                       double2 *part, cudaStream_t st, const int *skip, int quad, int *status, int inject) {
+                       double2 *part, cudaStream_t st, const int *skip, int quad, int *status, int inject,
+                       int cap) {
   if (prec == KBE_PREC_F16X2) {
     if (!tc_supported(m, prec)) return cudaErrorInvalidValue;
-    return launch_sweep_tc(m, n, H, Cf, I, part, st, skip, quad, status, tc_choice(m, prec, quad, n));
+    return launch_sweep_tc(m, n, H, Cf, I, part, st, skip, quad, status, tc_choice(m, prec, quad, n), cap);
   }
   if constexpr (NB == 2 || NB == 4 || NB == 8) {
     if (tile_supported(m, prec) && !inject) {
@@ -1556,7 +1553,7 @@ int sweep_splits(const Mesh &m, int n, int prec, int quad) {
 // work are the caller's buffers for row nmax (contents are not used for
 // timing; I and work are overwritten). out[b] = the choice for bucket b.
 cudaError_t tune_sweep(const Mesh &m, int prec, int quad, int nmax, double dt, const void *H, const double2 *Sig,
-                       double2 *I, void *work, cudaStream_t st, int *out, int nout) {
+                       double2 *I, void *work, cudaStream_t st, int *out, int nout, int cap) {
   const bool staged = use_staged(m, prec);
   std::vector<int> cands = staged ? std::vector<int>{3, 6, 12, 24} : std::vector<int>{2, 4, 8, 16, 32};
   if (tile_supported(m, prec))   // the single-read tile form, TI rows per work item (odd: one CTA per unit)
@@ -1564,10 +1561,13 @@ cudaError_t tune_sweep(const Mesh &m, int prec, int quad, int nmax, double dt, c
       cands.push_back(-ti);
       cands.push_back(-(ti + 1));
     }
-  if (tc_supported(m, prec)) {   // the tensor-core form: TI rows per panel only
+  if (tc_supported(m, prec)) {   // the tensor-core form: TI rows per panel, bulk or loader-warp copies
     cands.clear();
     for (int ti : {kTileMinTI, 64, 128})
-      if (ti <= tc_max_ti(m.nb)) cands.push_back(-ti);
+      if (ti <= tc_max_ti(m.nb)) {
+        cands.push_back(-ti);
+        cands.push_back(-(ti + 1));
+      }
   }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return cudaErrorUnknown;
@@ -1583,9 +1583,11 @@ cudaError_t tune_sweep(const Mesh &m, int prec, int quad, int nmax, double dt, c
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune[key] = t;
       }
-      for (int w = 0; w < 2 && err == cudaSuccess; ++w) err = launch_sweep(m, n, dt, prec, H, Sig, I, work, st, nullptr, quad);
+      for (int w = 0; w < 2 && err == cudaSuccess; ++w)
+        err = launch_sweep(m, n, dt, prec, H, Sig, I, work, st, nullptr, quad, nullptr, 0, cap);
       if (err == cudaSuccess) err = cudaEventRecord(e0, st);
-      for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = launch_sweep(m, n, dt, prec, H, Sig, I, work, st, nullptr, quad);
+      for (int r = 0; r < 3 && err == cudaSuccess; ++r)
+        err = launch_sweep(m, n, dt, prec, H, Sig, I, work, st, nullptr, quad, nullptr, 0, cap);
       if (err == cudaSuccess) err = cudaEventRecord(e1, st);
       if (err == cudaSuccess) err = cudaEventSynchronize(e1);
       float ms = 0.f;
@@ -1607,8 +1609,9 @@ cudaError_t tune_sweep(const Mesh &m, int prec, int quad, int nmax, double dt, c
 // manual form of the autotuner's table (kbe_set_sweep_choice): bucket -1 sets
 // every bucket; choice 0 removes the entry (the default applies again)
 bool set_sweep_choice(const Mesh &m, int prec, int quad, int bucket, int choice) {
-  if (tc_supported(m, prec)) {   // the tensor-core form takes only TI = -choice (a multiple of 16)
-    if (choice > 0 || (choice < 0 && (-choice < 16 || -choice % 16 != 0 || -choice > tc_max_ti(m.nb)))) return false;
+  if (tc_supported(m, prec)) {   // the tensor-core form takes only TI = -choice (a multiple of 16; + 1: loader warps)
+    const int ti = (-choice) & ~1;
+    if (choice > 0 || (choice < 0 && (ti < 16 || ti % 16 != 0 || ti > tc_max_ti(m.nb)))) return false;
   } else if (choice < 0 && (!tile_supported(m, prec) || -choice < kTileMinTI || -choice > 4096)) {
     return false;
   }
@@ -1638,37 +1641,40 @@ cudaError_t sweep_prepare(int nb) {
 }
 
 cudaError_t launch_pack(int prec, const double2 *src, void *dst, size_t nblocks, size_t blk,
-                        cudaStream_t st, const int *skip, int nb, int row) {
+                        cudaStream_t st, const int *skip, int nb, int row, int cap) {
   if (nblocks == 0 || blk == 0) return cudaSuccess;
-  if (prec == KBE_PREC_F16X2 && (!(nb == 4 || nb == 8) || blk % ((size_t)nb * nb) != 0)) return cudaErrorInvalidValue;
+  if (prec == KBE_PREC_F16X2 && (!(nb == 4 || nb == 8) || blk % ((size_t)nb * nb) != 0 || cap <= 0))
+    return cudaErrorInvalidValue;
   const int nk = nb > 0 ? (int)(blk / ((size_t)nb * nb)) : 0;
-  pack_kernel<<<grid_for(nblocks * blk), 256, 0, st>>>(prec, src, dst, nblocks, blk, skip, nb, nk, row);
+  pack_kernel<<<grid_for(nblocks * blk), 256, 0, st>>>(prec, src, dst, nblocks, blk, skip, nb, nk, row, cap);
   return cudaGetLastError();
 }
 
 size_t history_row_offset(const Mesh &m, int prec, int i) {
-  if (prec == KBE_PREC_F16X2) return 2 * f16x2_row_start(i, m.nb, m.nk);
+  if (prec == KBE_PREC_F16X2) return 0;
   return tri(i, 0) * 2 * (size_t)m.nb * m.nb * m.nk * history_elem_bytes(prec);
 }
 
 size_t history_bytes(const Mesh &m, int prec, int n) {
-  if (prec == KBE_PREC_F16X2) return f16x2_history_bytes(n, m.nb, m.nk);
+  if (prec == KBE_PREC_F16X2) return f16x2_history_bytes(n + 1, m.nb, m.nk);
   return (tri(n, n) + 1) * 2 * (size_t)m.nb * m.nb * m.nk * history_elem_bytes(prec);
 }
 
 cudaError_t launch_row_out(int prec, const double2 *fp64, const void *packed, size_t nblk, const Mesh &m,
-                           int which, double2 *out, cudaStream_t st, int row) {
+                           int which, double2 *out, cudaStream_t st, int row, int cap) {
   const size_t count = nblk * (size_t)m.nb * m.nb * m.nk;
   if (count == 0) return cudaSuccess;
-  if (prec == KBE_PREC_F16X2 && !fp64 && row < 0) return cudaErrorInvalidValue;
-  row_out_kernel<<<grid_for(count), 256, 0, st>>>(prec, fp64, packed, nblk, m.nb, m.nk, which, out, row);
+  if (prec == KBE_PREC_F16X2 && !fp64 && (row < 0 || cap <= row)) return cudaErrorInvalidValue;
+  row_out_kernel<<<grid_for(count), 256, 0, st>>>(prec, fp64, packed, nblk, m.nb, m.nk, which, out, row, cap);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const void *H,
                          const double2 *Sig, double2 *I, void *work, cudaStream_t st, const int *skip,
-                         int quad, int *status, int inject) {
+                         int quad, int *status, int inject, int cap) {
   if (!precision_supported(precision)) return cudaErrorInvalidValue;
+  if (cap <= 0) cap = n + 1;
+  if (cap < n + 1) return cudaErrorInvalidValue;
   const size_t blk = (size_t)m.nb * m.nb * m.nk;
   const size_t total = (size_t)(n + 1) * blk;
   double *Cs = precision == KBE_PREC_FP64 ? (double *)((double2 *)work + (size_t)(n + 1) * 3 * blk) : nullptr;
@@ -1684,14 +1690,14 @@ cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const v
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   switch (m.nb) {
-    case 1: return sweep_prec<1>(m, n, precision, H, work, I, part, st, skip, quad, status, inject);
-    case 2: return sweep_prec<2>(m, n, precision, H, work, I, part, st, skip, quad, status, inject);
-    case 3: return sweep_prec<3>(m, n, precision, H, work, I, part, st, skip, quad, status, inject);
-    case 4: return sweep_prec<4>(m, n, precision, H, work, I, part, st, skip, quad, status, inject);
-    case 6: return sweep_prec<6>(m, n, precision, H, work, I, part, st, skip, quad, status, inject);
-    case 8: return sweep_prec<8>(m, n, precision, H, work, I, part, st, skip, quad, status, inject);
-    case 12: return sweep_prec<12>(m, n, precision, H, work, I, part, st, skip, quad, status, inject);
-    case 16: return sweep_prec<16>(m, n, precision, H, work, I, part, st, skip, quad, status, inject);
+    case 1: return sweep_prec<1>(m, n, precision, H, work, I, part, st, skip, quad, status, inject, cap);
+    case 2: return sweep_prec<2>(m, n, precision, H, work, I, part, st, skip, quad, status, inject, cap);
+    case 3: return sweep_prec<3>(m, n, precision, H, work, I, part, st, skip, quad, status, inject, cap);
+    case 4: return sweep_prec<4>(m, n, precision, H, work, I, part, st, skip, quad, status, inject, cap);
+    case 6: return sweep_prec<6>(m, n, precision, H, work, I, part, st, skip, quad, status, inject, cap);
+    case 8: return sweep_prec<8>(m, n, precision, H, work, I, part, st, skip, quad, status, inject, cap);
+    case 12: return sweep_prec<12>(m, n, precision, H, work, I, part, st, skip, quad, status, inject, cap);
+    case 16: return sweep_prec<16>(m, n, precision, H, work, I, part, st, skip, quad, status, inject, cap);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -68,16 +68,21 @@ struct TcCfg;
 // into one accumulator wait on each other (~57 ns each at N <= 128 on
 // GB300), so consecutive MMAs alternate between accumulators (and between the
 // column and row uses), which the epilogue sums
+// SETS row groups in flight in the shared-memory ring (three fit at N_b = 4)
 template <>
 struct TcCfg<4> {
-  static constexpr int TM = 16, RG = 16, NC = 4;
+  static constexpr int TM = 16, RG = 16, NC = 4, SETS = 3;
 };
 template <>
 struct TcCfg<8> {
-  static constexpr int TM = 8, RG = 8, NC = 2;
+  static constexpr int TM = 8, RG = 8, NC = 2, SETS = 2;
 };
 
-constexpr int kTcThreads = 192;   // warp 0 copies, warp 1 MMA, warps 2-5 epilogue
+// warp 0 bulk copies, warp 1 MMA, warps 2-5 epilogue; with WC, warps 6-9 copy
+// the row segments with 16-byte cp.async (many small requests in flight)
+// instead of one bulk copy per row group
+constexpr int kTcLoaders = 128;
+__host__ __device__ constexpr int tc_threads(bool wc) { return wc ? 192 + kTcLoaders : 192; }
 
 // the row use reads the slot ring as an MN-major A operand: core matrices
 // 4096 bytes apart along M (rows, or r halves at N_b = 8), 128 apart along K
@@ -87,7 +92,6 @@ constexpr int kTcThreads = 192;   // warp 0 copies, warp 1 MMA, warps 2-5 epilog
 #ifndef KBE_TC_MN_SBO
 #define KBE_TC_MN_SBO 4096u
 #endif
-constexpr int kTcSets = 2;        // row-ring slot sets (one row group each)
 
 template <int NB>
 __host__ __device__ constexpr int tc_n() { return 4 * NB; }   // MMA N: (part, a, re/im)
@@ -103,7 +107,8 @@ __host__ __device__ constexpr unsigned tc_btile() { return 64u * NB; }   // one 
 // column-use B tile (the operand of the MMAs that clear unused accumulators)
 template <int NB>
 __host__ __device__ constexpr size_t tc_smem_bytes() {
-  return (size_t)kTcSets * TcCfg<NB>::RG * (tc_slot<NB>() + tc_bcol<NB>()) + 2 * (size_t)tc_brow<NB>() + tc_bcol<NB>();
+  return (size_t)TcCfg<NB>::SETS * TcCfg<NB>::RG * (tc_slot<NB>() + tc_bcol<NB>()) + 2 * (size_t)tc_brow<NB>() +
+         tc_bcol<NB>();
 }
 static_assert(tc_smem_bytes<4>() + 1024 <= 227 * 1024 && tc_smem_bytes<8>() + 1024 <= 227 * 1024, "tc smem");
 
@@ -236,22 +241,24 @@ __global__ void tc_coef_kernel(const float2 *__restrict__ Cf, const unsigned *__
 
 // ---- the sweep -----------------------------------------------------------
 // CP [panel][j][k][x][a][b], RP [j][k][a][b] (complex64)
-template <int NB>
-__global__ void __launch_bounds__(kTcThreads, 1)
+template <int NB, bool WC>
+__global__ void __launch_bounds__(tc_threads(WC), 1)
     sweep_tc_kernel(const __half *__restrict__ Hh, const __half *__restrict__ Bcg,
                     const __half *__restrict__ Brg, const unsigned *__restrict__ cmax, float2 *__restrict__ CP,
-                    float2 *__restrict__ RP, int n, int nk, int TI, int lt, uint32_t tcols, int NR,
+                    float2 *__restrict__ RP, int n, int nk, int TI, int lt, uint32_t tcols, int NR, int cap,
                     const int *__restrict__ skip, int *status) {
   if (skip && *skip) return;
   constexpr int TM = TcCfg<NB>::TM, RG = TcCfg<NB>::RG, N = tc_n<NB>(), NG = NB / 2, NC = TcCfg<NB>::NC;
+  constexpr int SETS = TcCfg<NB>::SETS;
   constexpr unsigned SLOT = tc_slot<NB>(), BCOL = tc_bcol<NB>(), BROW = tc_brow<NB>();
   constexpr int CSTEP = 8 / NB;   // row slots per column-use MMA (K = 16 halves)
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   unsigned char *sA = tc_smem;
-  unsigned char *sBc = sA + (size_t)kTcSets * RG * SLOT;
-  unsigned char *sBr = sBc + (size_t)kTcSets * RG * BCOL;
+  unsigned char *sBc = sA + (size_t)SETS * RG * SLOT;
+  unsigned char *sBr = sBc + (size_t)SETS * RG * BCOL;
   unsigned char *sZero = sBr + 2 * (size_t)BROW;   // a zero column-use B tile
-  __shared__ __align__(8) uint64_t full[kTcSets], empty[kTcSets], brf[2], bre[2], dcf[2], dce[2], drf, dre, done;
+  __shared__ __align__(8) uint64_t full[SETS], empty[SETS], brf[2], bre[2], dcf[2], dce[2], drf, dre, done;
+  static_assert(SETS <= 3, "slot sets");
   __shared__ uint32_t tbase;
   __shared__ volatile int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -259,14 +266,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int units = P * nk;
 
   // zero the ring (stale slots then always hold finite values), barriers, TMEM
-  for (size_t o = (size_t)threadIdx.x * 16; o < (size_t)kTcSets * RG * (SLOT + BCOL); o += (size_t)blockDim.x * 16)
+  for (size_t o = (size_t)threadIdx.x * 16; o < (size_t)SETS * RG * (SLOT + BCOL); o += (size_t)blockDim.x * 16)
     *reinterpret_cast<uint4 *>(sA + o) = make_uint4(0, 0, 0, 0);
   for (unsigned o = threadIdx.x * 16; o < BCOL; o += blockDim.x * 16)
     *reinterpret_cast<uint4 *>(sZero + o) = make_uint4(0, 0, 0, 0);
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   if (threadIdx.x == 0) {
-    for (int q = 0; q < kTcSets; ++q) {
-      mbar_init(&full[q], 1);
+    for (int q = 0; q < SETS; ++q) {
+      mbar_init(&full[q], WC ? 1 + kTcLoaders : 1);   // (WC: the loaders' cp.async arrivals too)
       mbar_init(&empty[q], 1);
     }
     for (int q = 0; q < 2; ++q) {
@@ -319,25 +326,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                       Brg + (((size_t)x * nk + k) * lt + (size_t)M0 * NB / 8) * (tc_btile<NB>() / 2), BROW / 2,
                       &brf[b]);
           for (int G0 = max(R0, M0); G0 < R1 && !abort_flag; G0 += RG, ++gcount) {
-            const int set = gcount & 1, use2 = gcount >> 1;
+            const int set = gcount % SETS, use2 = gcount / SETS;
             if (use2 >= 1 && !wait(&empty[set], (unsigned)((use2 - 1) & 1))) break;
             const int rows = min(RG, R1 - G0);
-            mbar_expect_tx(&full[set], (unsigned)rows * (SLOT + BCOL));
-            for (int r = 0; r < rows; ++r) {   // the row segment is one contiguous slot of the history
-              const int i = G0 + r, slot = set * RG + r;
-              const __half *src = Hh + f16x2_row_start(i, NB, nk) + ((size_t)k * (i / TM + 1) + s) * (SLOT / 2);
-              bulk_load(sA + (size_t)slot * SLOT, src, SLOT, &full[set]);
-              bulk_load(sBc + (size_t)slot * BCOL, Bcg + ((size_t)k * (n + 1) + i) * (BCOL / 2), BCOL, &full[set]);
-            }
+            // the group's row segments of strip s are consecutive slots of the history,
+            // and its column-use coefficient tiles consecutive tiles: two bulk copies
+            mbar_expect_tx(&full[set], (unsigned)rows * ((WC ? 0 : SLOT) + BCOL));
+            if (!WC)
+              bulk_load(sA + (size_t)set * RG * SLOT, Hh + f16x2_slot(G0, s, k, cap, NB) * (SLOT / 2),
+                        (unsigned)rows * SLOT, &full[set]);
+            bulk_load(sBc + (size_t)set * RG * BCOL, Bcg + ((size_t)k * (n + 1) + G0) * (BCOL / 2),
+                      (unsigned)rows * BCOL, &full[set]);
           }
         }
       }
-      // let the copies in flight land before the CTA can exit
-      for (int q = 0; q < kTcSets && gcount > 0; ++q) {
-        const int last = gcount - 1 - ((gcount - 1 - q) & 1);   // the last group that used set (gcount-1-q)&1
-        if (last >= 0 && !mbar_wait(&full[last & 1], (unsigned)((last >> 1) & 1), kMbarWaitLimit) && status)
+      // let the copies in flight land before the CTA can exit (the last group of each set)
+      for (int last = gcount - 1; last >= 0 && last >= gcount - SETS; --last)
+        if (!mbar_wait(&full[last % SETS], (unsigned)((last / SETS) & 1), kMbarWaitLimit) && status)
           atomicOr(status, kDevTimeout | kDevTimeoutDrain);
-      }
       if (scount > 0) {
         const int last = scount - 1;
         if (!mbar_wait(&brf[last & 1], (unsigned)((last >> 1) & 1), kMbarWaitLimit) && status)
@@ -347,7 +353,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA
     const uint32_t id_col = tc_idesc(N, 0), id_row = tc_idesc(N, 1);
-    const unsigned aBase = smem_addr(sA), bcBase = smem_addr(sBc), brBase = smem_addr(sBr);
+    const unsigned aBase = smem_addr(sA);
+    const uint64_t descA_col = tc_desc(aBase, kTcFar, kTcCore);
+    const uint64_t descB_col = tc_desc(smem_addr(sBc), (unsigned)NG * kTcCore, kTcCore);
+    const uint64_t descA_row = tc_desc(aBase, KBE_TC_MN_LBO, KBE_TC_MN_SBO);
+    const uint64_t descB_row = tc_desc(smem_addr(sBr), (unsigned)NG * kTcCore, kTcCore);
     int gcount = 0, scount = 0, ucount = 0;
     for (int u = blockIdx.x; u < units && !abort_flag; u += gridDim.x, ++ucount) {
       const int p = P - 1 - u / nk;
@@ -361,7 +371,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tc_fence_after();
         unsigned colinit = 0;   // column-use accumulators written in this strip
         for (int G0 = max(R0, M0); G0 < R1 && !abort_flag; G0 += RG, ++gcount) {
-          const int set = gcount & 1, use2 = gcount >> 1, gi = (G0 - R0) / RG;
+          const int set = gcount % SETS, use2 = gcount / SETS, gi = (G0 - R0) / RG;
           const int rows = min(RG, R1 - G0);
           if (!wait(&full[set], (unsigned)(use2 & 1))) break;
           // blocks on and above the diagonal (m >= i) of rows i < M0 + TM take no part
@@ -397,28 +407,28 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           if (lane == 0) {
             tc_fence_after();
             const uint32_t dcol = tmem + (uint32_t)(b * NC * N), drow = tmem + (uint32_t)((2 * NC + gi * NR) * N);
-            const int ncm = (rows + CSTEP - 1) / CSTEP, ncol = 2 * ncm;
-            // column use: (h, cm) -> accumulator q % NC; row use: (h, t) -> accumulator q % NR;
-            // the two uses alternate so that independent MMAs follow each other
-#pragma unroll 1
-            for (int q = 0; q < 16 || q < ncol; ++q) {
-              if (q < ncol) {
-                const int h = q / ncm, cm = q % ncm, c = q % NC;
-                const int slot = set * RG + cm * CSTEP;
-                const uint64_t da = tc_desc(aBase + (unsigned)slot * SLOT + (unsigned)h * kTcPlane, kTcFar, kTcCore);
-                const uint64_t db = tc_desc(bcBase + (unsigned)slot * BCOL, (unsigned)NG * kTcCore, kTcCore);
-                tc_mma(dcol + (uint32_t)(c * N), da, db, id_col, (colinit >> c) & 1);
-                colinit |= 1u << c;
+            const int ncm = (rows + CSTEP - 1) / CSTEP;
+            // descriptors advance by (byte offset >> 4) in their start-address field
+            const uint64_t dAc = descA_col + ((unsigned)(set * RG) * SLOT >> 4);
+            const uint64_t dBc = descB_col + ((unsigned)(set * RG) * BCOL >> 4);
+            const uint64_t dAr = descA_row + ((unsigned)(set * RG) * SLOT >> 4);
+            const uint64_t dBr = descB_row + ((unsigned)b * BROW >> 4);
+            // column use: (h, cm) -> accumulator (h * ncm + cm) % NC; row use: (h, t) ->
+            // accumulator t % NR; the two uses alternate so that independent MMAs follow
+            // each other
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                if (q < ncm) {
+                  const int c = (h * ncm + q) % NC;
+                  tc_mma(dcol + (uint32_t)(c * N), dAc + ((unsigned)(q * CSTEP) * SLOT + h * kTcPlane >> 4),
+                         dBc + ((unsigned)(q * CSTEP) * BCOL >> 4), id_col, (colinit >> c) & 1);
+                  colinit |= 1u << c;
+                }
+                tc_mma(drow + (uint32_t)((q % NR) * N), dAr + (h * kTcPlane + 2u * q * kTcCore >> 4),
+                       dBr + (2u * q * NG * kTcCore >> 4), id_row, (s == 0 && h == 0 && q < NR) ? 0 : 1);
               }
-              if (q < 16) {
-                const int h = q / 8, t = q % 8;
-                const uint64_t da = tc_desc(aBase + (unsigned)(set * RG) * SLOT + (unsigned)h * kTcPlane + 2u * t * kTcCore,
-                                            KBE_TC_MN_LBO, KBE_TC_MN_SBO);
-                const uint64_t db =
-                    tc_desc(brBase + (unsigned)b * BROW + 2u * t * NG * kTcCore, (unsigned)NG * kTcCore, kTcCore);
-                tc_mma(drow + (uint32_t)((q % NR) * N), da, db, id_row, (s == 0 && q < NR) ? 0 : 1);
-              }
-            }
             tc_commit(&empty[set]);
           }
           __syncwarp();
@@ -443,6 +453,29 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (!mbar_wait(&done, 0, kMbarWaitLimit) && status) atomicOr(status, kDevTimeout | kDevTimeoutDrain);
     }
     __syncwarp();
+  } else if (WC && warp >= 6) {
+    // ------------------------------------------------- row-segment loaders
+    const int lt_id = threadIdx.x - 192;
+    int gcount = 0;
+    for (int u = blockIdx.x; u < units && !abort_flag; u += gridDim.x) {
+      const int p = P - 1 - u / nk, k = u % nk;
+      const int R0 = p * TI, R1 = min(R0 + TI, n + 1);
+      const int S = (R1 - 1) / TM + 1;
+      for (int s = 0; s < S && !abort_flag; ++s)
+        for (int G0 = max(R0, s * TM); G0 < R1 && !abort_flag; G0 += RG, ++gcount) {
+          const int set = gcount % SETS, use2 = gcount / SETS;
+          if (use2 >= 1 && !wait(&empty[set], (unsigned)((use2 - 1) & 1))) break;
+          const int rows = min(RG, R1 - G0);
+          const char *src = (const char *)(Hh + f16x2_slot(G0, s, k, cap, NB) * (SLOT / 2));
+          const unsigned dst = smem_addr(sA + (size_t)set * RG * SLOT);
+          for (unsigned c = lt_id; c < (unsigned)rows * (SLOT / 16); c += kTcLoaders)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + c * 16), "l"(src + (size_t)c * 16)
+                         : "memory");
+          asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_addr(&full[set]))
+                       : "memory");
+        }
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");   // no copy outlives the CTA
   } else {
     // ----------------------------------------------------------- epilogue
     const int ew = warp & 3;                  // tensor-memory lane quarter of this warp
@@ -538,23 +571,39 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // output), the row use at nodes m < j whose weight f = w^(j)_m / dt is not 1
 // (X -= (f - 1) C2^<(m) conj(dB(j, m))^T), and the Gregory Y terms of the
 // row use (the nodes where the weights of [0, t_j] and [0, t_n] differ).
+// A CTA owns column j and KTR consecutive k: it reads the k-outer partials
+// and stages the coefficient rows of node j coalesced, sums in FP64, and
+// writes I (k fastest) through shared memory.
+template <int NB>
+__host__ __device__ constexpr int tc_red_kt() { return NB == 4 ? 32 : 8; }
+
 template <int NB, int QUAD>
-__global__ void tc_reduce_kernel(const float2 *__restrict__ CP, const float2 *__restrict__ RP,
-                                 const float2 *__restrict__ Cf, const __half *__restrict__ H, double2 *__restrict__ I,
-                                 int n, int nk, int TI, const int *__restrict__ skip) {
+__global__ void __launch_bounds__(256)
+    tc_reduce_kernel(const float2 *__restrict__ CP, const float2 *__restrict__ RP, const float2 *__restrict__ Cf,
+                     const __half *__restrict__ H, double2 *__restrict__ I, int n, int nk, int TI, int cap,
+                     const int *__restrict__ skip) {
   if (skip && *skip) return;
-  constexpr int TM = TcCfg<NB>::TM, NB2 = NB * NB;
-  const size_t blk = (size_t)NB2 * nk, count = (size_t)(n + 1) * blk;
+  constexpr int TM = TcCfg<NB>::TM, NB2 = NB * NB, KTR = tc_red_kt<NB>(), ITEMS = KTR * NB2;
+  __shared__ double2 sI[2][NB2][KTR];      // [x][ab][kk]
+  __shared__ float2 sC[3][NB2][KTR];       // C1, C2^<, C3 of node j: [q][a c][kk]
+  const size_t blk = (size_t)NB2 * nk;
   const int P = (n + TI) / TI;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < count;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int ab = (int)(idx % NB2);
-    const size_t jk = idx / NB2;
-    const int k = (int)(jk % nk), j = (int)(jk / nk);
+  const int ktiles = (nk + KTR - 1) / KTR;
+  const int j = blockIdx.x / ktiles, k0 = (blockIdx.x % ktiles) * KTR;
+  if (j > n) return;
+  for (int t = threadIdx.x; t < 3 * ITEMS; t += blockDim.x) {   // coalesced along k
+    const int kk = t % KTR, ac = (t / KTR) % NB2, q = t / ITEMS;
+    sC[q][ac][kk] = k0 + kk < nk ? Cf[((size_t)j * 3 + q) * blk + (size_t)ac * nk + k0 + kk] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int pmin = (j / TM) * TM / TI;
+  for (int t = threadIdx.x; t < ITEMS; t += blockDim.x) {   // ab fastest: the partials are [k][x][a b]
+    const int ab = t % NB2, kk = t / NB2, k = k0 + kk;
+    if (k >= nk) continue;
     const int a = ab / NB, b = ab % NB;
-    const float2 rp = RP[idx];
+    const float2 rp = RP[((size_t)j * nk + k) * NB2 + ab];
     double xr = rp.x, xi = rp.y, yr = 0.0, yi = 0.0;
-    for (int p = (j / TM) * TM / TI; p < P; ++p) {
+    for (int p = pmin; p < P; ++p) {
       const size_t o = ((((size_t)p * (n + 1) + j) * nk + k) * 2) * NB2 + ab;
       const float2 x = CP[o], y = CP[o + NB2];
       xr += x.x;
@@ -562,68 +611,55 @@ __global__ void tc_reduce_kernel(const float2 *__restrict__ CP, const float2 *__
       yr += y.x;
       yi += y.y;
     }
-    auto coef = [&](int l, int q, int c) {
-      const float2 v = Cf[((size_t)l * 3 + q) * blk + (size_t)(a * NB + c) * nk + k];
-      return make_double2(v.x, v.y);
-    };
-    // diagonal block (j, j)
-    {
-      const double f = quad_omega(QUAD, j, j);
-      for (int c = 0; c < NB; ++c) {
-        const double2 gl = f16x2_get(H, j, j, k, 0, c, b, NB, nk), dg = f16x2_get(H, j, j, k, 1, c, b, NB, nk);
-        const double2 k1 = coef(j, 0, c);
-        double2 t = c_mul(k1, gl);
-        xr += t.x;
-        xi += t.y;
-        if (j == 0) {
-          t = c_mul(k1, dg);
-          yr -= t.x;
-          yi -= t.y;
-        } else {
-          const double2 k2 = coef(j, 1, c), k3 = coef(j, 2, c);
-          t = c_mul(make_double2(f * k2.x, f * k2.y), dg);
-          xr += t.x;
-          xi += t.y;
-          const double2 ky = make_double2(f * (k3.x - k2.x) + (f - 1.0) * k1.x, f * (k3.y - k2.y) + (f - 1.0) * k1.y);
-          t = c_mul(ky, dg);
-          yr += t.x;
-          yi += t.y;
-        }
+    // the diagonal block and the end-node terms in FP32 (their operands are
+    // complex64 coefficients and 22-bit history values), added to the FP64 sums
+    float2 tx = make_float2(0.f, 0.f), ty = make_float2(0.f, 0.f);
+    const float f = (float)quad_omega(QUAD, j, j);
+    for (int c = 0; c < NB; ++c) {   // diagonal block (j, j)
+      const float2 gl = f16x2_getf(H, j, j, k, 0, c, b, NB, cap), dg = f16x2_getf(H, j, j, k, 1, c, b, NB, cap);
+      const float2 k1 = sC[0][a * NB + c][kk];
+      tx = c_fma(k1, gl, tx);
+      if (j == 0) {
+        ty = c_fma(make_float2(-k1.x, -k1.y), dg, ty);
+      } else {
+        const float2 k2 = sC[1][a * NB + c][kk], k3 = sC[2][a * NB + c][kk];
+        tx = c_fma(make_float2(f * k2.x, f * k2.y), dg, tx);
+        ty = c_fma(make_float2(f * (k3.x - k2.x) + (f - 1.f) * k1.x, f * (k3.y - k2.y) + (f - 1.f) * k1.y), dg, ty);
       }
     }
     // nodes m < j with a weight on [0, t_j] other than dt: trapezoid node 0;
     // Gregory nodes 0, 1, 2, j-2, j-1 (every m < j for j <= 4)
     if (j > 0) {
       const int ns = QUAD == kQuadTrapezoid ? 1 : (j >= 5 ? 5 : j);
-      for (int t = 0; t < ns; ++t) {
-        const int mnode = (QUAD != kQuadTrapezoid && j >= 5 && t >= 3) ? j - 5 + t : t;
-        const double f = quad_omega(QUAD, j, mnode);
-        double2 accx = make_double2(0.0, 0.0), accy = make_double2(0.0, 0.0);
+      for (int t2 = 0; t2 < ns; ++t2) {
+        const int mnode = (QUAD != kQuadTrapezoid && j >= 5 && t2 >= 3) ? j - 5 + t2 : t2;
+        const float fm = (float)quad_omega(QUAD, j, mnode);
         for (int c = 0; c < NB; ++c) {
-          // dG(j, m)_{b, c}: the row use pairs output (a, b) with conj(dB(j, m)[b, c])
-          const double2 dg = f16x2_get(H, j, mnode, k, 1, b, c, NB, nk);
-          const double2 cd = make_double2(dg.x, -dg.y);
-          const double2 k2 = coef(mnode, 1, c);
-          const double2 tx = c_mul(k2, cd);
-          accx.x += (f - 1.0) * tx.x;
-          accx.y += (f - 1.0) * tx.y;
+          // the row use pairs output (a, b) with conj(dB(j, m)[b, c])
+          const float2 dg = f16x2_getf(H, j, mnode, k, 1, b, c, NB, cap);
+          const float2 cd = make_float2(dg.x, -dg.y);
+          const size_t o = (size_t)(a * NB + c) * nk + k;
+          const float2 k2 = Cf[((size_t)mnode * 3 + 1) * blk + o];
+          tx = c_fma(make_float2(-(fm - 1.f) * k2.x, -(fm - 1.f) * k2.y), cd, tx);
           if (QUAD != kQuadTrapezoid) {
-            const double2 k1 = coef(mnode, 0, c), k3 = coef(mnode, 2, c);
-            const double2 ky = make_double2(f * (k3.x - k2.x) + (f - 1.0) * k1.x, f * (k3.y - k2.y) + (f - 1.0) * k1.y);
-            const double2 ty = c_mul(ky, cd);
-            accy.x += ty.x;
-            accy.y += ty.y;
+            const float2 k1 = Cf[(size_t)mnode * 3 * blk + o], k3 = Cf[((size_t)mnode * 3 + 2) * blk + o];
+            ty = c_fma(make_float2(-(fm * (k3.x - k2.x) + (fm - 1.f) * k1.x), -(fm * (k3.y - k2.y) + (fm - 1.f) * k1.y)),
+                       cd, ty);
           }
         }
-        xr -= accx.x;
-        xi -= accx.y;
-        yr -= accy.x;
-        yi -= accy.y;
       }
     }
-    const size_t o = ((size_t)j * 2) * blk + (size_t)ab * nk + k;
-    I[o] = make_double2(xr, xi);
-    I[o + blk] = make_double2(xr + yr, xi + yi);
+    xr += tx.x;
+    xi += tx.y;
+    yr += ty.x;
+    yi += ty.y;
+    sI[0][ab][kk] = make_double2(xr, xi);
+    sI[1][ab][kk] = make_double2(xr + yr, xi + yi);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 2 * ITEMS; t += blockDim.x) {   // k fastest: I is [j][x][a b][k]
+    const int kk = t % KTR, ab = (t / KTR) % NB2, x = t / ITEMS;
+    if (k0 + kk < nk) I[((size_t)j * 2 + x) * blk + (size_t)ab * nk + k0 + kk] = sI[x][ab][kk];
   }
 }
 
@@ -639,7 +675,11 @@ cudaError_t tc_prepare_nb() {
   tensor_map_encoder();
   std::lock_guard<std::mutex> lk(mu);
   if (done[dev]) return cudaSuccess;
-  e = cudaFuncSetAttribute(sweep_tc_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes<NB>());
+  e = cudaFuncSetAttribute(sweep_tc_kernel<NB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tc_smem_bytes<NB>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sweep_tc_kernel<NB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tc_smem_bytes<NB>());
   if (e == cudaSuccess) done[dev] = true;
   return e;
 }
@@ -674,7 +714,7 @@ TcParts tc_parts(const Mesh &m, int n, int TI, void *part) {
 
 template <int NB>
 cudaError_t tc_launch(const Mesh &m, int n, const void *H, const void *Cf, double2 *I, void *part, cudaStream_t st,
-                      const int *skip, int quad, int *status, int TI) {
+                      const int *skip, int quad, int *status, int TI, int cap, bool wc) {
   cudaError_t e = tc_prepare_nb<NB>();
   if (e != cudaSuccess) return e;
   const TcParts t = tc_parts(m, n, TI, part);
@@ -699,21 +739,21 @@ cudaError_t tc_launch(const Mesh &m, int n, const void *H, const void *Cf, doubl
   const long units = (long)((n + TI) / TI) * m.nk;
   const long slots = device_sms();
   const unsigned grid = (unsigned)(units < slots ? units : slots);
-  sweep_tc_kernel<NB><<<grid, kTcThreads, tc_smem_bytes<NB>(), st>>>((const __half *)H, t.Bc, t.Br, t.cmax, t.CP,
-                                                                     t.RP, n, m.nk, TI,
-                                                                     lt, tcols, NR, skip, status);
+  if (wc)
+    sweep_tc_kernel<NB, true><<<grid, tc_threads(true), tc_smem_bytes<NB>(), st>>>(
+        (const __half *)H, t.Bc, t.Br, t.cmax, t.CP, t.RP, n, m.nk, TI, lt, tcols, NR, cap, skip, status);
+  else
+    sweep_tc_kernel<NB, false><<<grid, tc_threads(false), tc_smem_bytes<NB>(), st>>>(
+        (const __half *)H, t.Bc, t.Br, t.cmax, t.CP, t.RP, n, m.nk, TI, lt, tcols, NR, cap, skip, status);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t count = (size_t)(n + 1) * NB * NB * m.nk;
-  size_t blocks = (count + 255) / 256;
-  const size_t cap = (size_t)device_sms() * 16;
-  if (blocks > cap) blocks = cap;
+  const unsigned rblocks = (unsigned)((n + 1) * ((m.nk + tc_red_kt<NB>() - 1) / tc_red_kt<NB>()));
   if (quad == kQuadGregory)
-    tc_reduce_kernel<NB, kQuadGregory><<<(unsigned)blocks, 256, 0, st>>>(t.CP, t.RP, (const float2 *)Cf,
-                                                                        (const __half *)H, I, n, m.nk, TI, skip);
+    tc_reduce_kernel<NB, kQuadGregory><<<rblocks, 256, 0, st>>>(t.CP, t.RP, (const float2 *)Cf, (const __half *)H, I, n,
+                                                               m.nk, TI, cap, skip);
   else
-    tc_reduce_kernel<NB, kQuadTrapezoid><<<(unsigned)blocks, 256, 0, st>>>(t.CP, t.RP, (const float2 *)Cf,
-                                                                          (const __half *)H, I, n, m.nk, TI, skip);
+    tc_reduce_kernel<NB, kQuadTrapezoid><<<rblocks, 256, 0, st>>>(t.CP, t.RP, (const float2 *)Cf, (const __half *)H, I,
+                                                                 n, m.nk, TI, cap, skip);
   return cudaGetLastError();
 }
 
@@ -764,12 +804,15 @@ cudaError_t tc_prepare(int nb) {
   }
 }
 
+// TI odd: TI - 1 rows per panel with the row segments copied by loader warps
 cudaError_t launch_sweep_tc(const Mesh &m, int n, const void *H, const void *Cf, double2 *I, void *part,
-                            cudaStream_t st, const int *skip, int quad, int *status, int TI) {
-  if (TI < 16 || TI % 16 != 0 || TI > tc_max_ti(m.nb)) return cudaErrorInvalidValue;
+                            cudaStream_t st, const int *skip, int quad, int *status, int TI, int cap) {
+  const bool wc = (TI & 1) != 0;
+  TI &= ~1;
+  if (TI < 16 || TI % 16 != 0 || TI > tc_max_ti(m.nb) || cap < n + 1) return cudaErrorInvalidValue;
   switch (m.nb) {
-    case 4: return tc_launch<4>(m, n, H, Cf, I, part, st, skip, quad, status, TI);
-    case 8: return tc_launch<8>(m, n, H, Cf, I, part, st, skip, quad, status, TI);
+    case 4: return tc_launch<4>(m, n, H, Cf, I, part, st, skip, quad, status, TI, cap, wc);
+    case 8: return tc_launch<8>(m, n, H, Cf, I, part, st, skip, quad, status, TI, cap, wc);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -5,9 +5,9 @@ The history keeps hi = fp16(4096 x), lo = fp16(4096 x - hi) per real part
 (22-bit significand); the sweep multiplies the hi and lo parts on the tensor
 cores with FP32 accumulation, the coefficient rows split the same way under a
 power-of-two scale. Checked here:
-  - the storage itself: the packed halves (rows padded to whole strips of
-    blocks, k-outer within a row), decoded on the host from the documented
-    layout, give back every input to 2^-21 of the scale;
+  - the storage itself: the packed halves (per k, strips of column blocks,
+    each holding its rows as consecutive slots), decoded on the host from the
+    documented layout, give back every input to 2^-21 of the scale;
   - per-row collision integrals (Eq. 6) on random histories and self-energy
     rows, for several panels and strips, ragged n, both quadratures and every
     panel height, at the mixed form's bar (1e-5 normwise, 1e-4 element-wise
@@ -41,28 +41,32 @@ def packed_f16x2(arr, nb, L, n):
     return dst
 
 
-def strips_before(i, tm):
-    q, r = divmod(i, tm)
-    return tm * q * (q + 1) // 2 + r * (q + 1)
-
-
 def decode_f16x2(h, n, nb, nk):
-    """host decode of the documented layout: row i starts after n_k x (strips of
-    rows < i) slots of 8 nb^2 TM halves; within the row [k][strip], within a
-    slot [r / 4][part hi/lo][x][block][s][r % 4][re/im] -> (G^<, dG) as
-    [ntri, 2, nb, nb, nk] ([x][r][s][k])"""
+    """host decode of the documented layout for a storage of rows 0..n: per k,
+    strips s of TM columns, each holding rows s TM .. n as consecutive slots of
+    8 nb^2 TM halves; within a slot [r / 4][part hi/lo][x][block][s][r % 4][re/im]
+    -> (G^<, dG) as [ntri, 2, nb, nb, nk] ([x][r][s][k])"""
     tm = 16 if nb == 4 else 8
     slot = 8 * nb * nb * tm
+    cap = n + 1
+    nstrips = (cap - 1) // tm + 1
+    colstart = [st * cap - tm * st * (st - 1) // 2 for st in range(nstrips + 1)]
+    kslots = colstart[nstrips]
+    assert h.size == nk * kslots * slot
+    with np.errstate(invalid="ignore", over="ignore"):   # padding blocks are never written
+        v = h.astype(np.float64)
     out = np.zeros(((n + 1) * (n + 2) // 2, 2, nb, nb, nk), np.complex128)
-    for i in range(n + 1):
-        S = i // tm + 1
-        with np.errstate(invalid="ignore", over="ignore"):   # the padding of the last strip is never written
-            row = h[nk * strips_before(i, tm) * slot:][:nk * S * slot].astype(np.float64)
-        v = row.reshape(nk, S, nb // 4, 2, 2, tm, nb, 4, 2)   # [k][strip][r/4][h][x][block][s][r%4][ri]
-        z = (v[:, :, :, 0] + v[:, :, :, 1]) / 4096.0           # [k][strip][r/4][x][block][s][r%4][ri]
-        c = z[..., 0] + 1j * z[..., 1]
-        c = c.transpose(1, 4, 3, 2, 6, 5, 0).reshape(S * tm, 2, nb, nb, nk)   # [block][x][r][s][k]
-        out[tri(i, 0):tri(i, 0) + i + 1] = c[:i + 1]
+    for k in range(nk):
+        for st in range(nstrips):
+            for i in range(st * tm, cap):
+                o = (k * kslots + colstart[st] + i - st * tm) * slot
+                w = v[o:o + slot].reshape(nb // 4, 2, 2, tm, nb, 4, 2)   # [r/4][h][x][block][s][r%4][ri]
+                z = (w[:, 0] + w[:, 1]) / 4096.0                          # [r/4][x][block][s][r%4][ri]
+                c = (z[..., 0] + 1j * z[..., 1]).transpose(2, 1, 0, 4, 3).reshape(tm, 2, nb, nb)   # [block][x][r][s]
+                for jj in range(tm):
+                    j = st * tm + jj
+                    if j <= i:
+                        out[tri(i, j), :, :, :, k] = c[jj]
     return out
 
 
@@ -117,10 +121,12 @@ def _collision(nb, L, n, quad, TI, seed, reps=2):
     (4, (8, 8), 70, 32), (4, (6, 5), 45, 64), (4, (3, 1), 130, 128), (4, (2, 1), 0, 32),
     (4, (2, 1), 1, 32), (4, (2, 1), 6, 64), (4, (5, 1), 17, 16), (8, (4, 4), 40, 32),
     (8, (2, 3), 35, 64), (8, (3, 1), 9, 16), (8, (1, 1), 0, 32), (8, (2, 1), 71, 32),
+    (4, (8, 8), 70, 33), (4, (3, 1), 130, 129), (8, (4, 4), 40, 33), (8, (2, 1), 71, 65),
 ])
 def test_f16x2_collision_row_matches_oracle(nb, L, n, TI, quad):
     """several panels (TI rows) and strips, the diagonal strips, odd row counts
-    (N_b = 4 pairs rows in one MMA), n below one strip; bitwise repeatable"""
+    (N_b = 4 pairs rows in one MMA), n below one strip, both copy paths (an odd
+    choice TI + 1: loader warps); bitwise repeatable"""
     outs, Il, Ig = _collision(nb, L, n, quad, TI, 1300 + nb * 7 + n)
     assert np.array_equal(outs[0], outs[1])
     gl, gg = from_dev_blocks(outs[0])

@@ -82,6 +82,11 @@ struct TcCfg<8> {
 // the row segments with 16-byte cp.async (many small requests in flight)
 // instead of one bulk copy per row group
 constexpr int kTcLoaders = 128;
+// the row-use accumulators are drained every tc_sd strips (complex64 partial
+// per (strip group, row, k)), which bounds their FP32 chains: 4 strips of 128
+// K-terms at N_b = 8, 16 strips of 128 at N_b = 4 (whose full-panel chains
+// were already within the mixed bar; every drain is a wait of the MMA warp)
+__host__ __device__ constexpr int tc_sd(int nb) { return nb == 8 ? 4 : 16; }
 __host__ __device__ constexpr int tc_threads(bool wc) { return wc ? 192 + kTcLoaders : 192; }
 
 // the row use reads the slot ring as an MN-major A operand: core matrices
@@ -249,7 +254,7 @@ __global__ void __launch_bounds__(tc_threads(WC), 1)
                     const int *__restrict__ skip, int *status) {
   if (skip && *skip) return;
   constexpr int TM = TcCfg<NB>::TM, RG = TcCfg<NB>::RG, N = tc_n<NB>(), NG = NB / 2, NC = TcCfg<NB>::NC;
-  constexpr int SETS = TcCfg<NB>::SETS;
+  constexpr int SETS = TcCfg<NB>::SETS, SD = tc_sd(NB);
   constexpr unsigned SLOT = tc_slot<NB>(), BCOL = tc_bcol<NB>(), BROW = tc_brow<NB>();
   constexpr int CSTEP = 8 / NB;   // row slots per column-use MMA (K = 16 halves)
   extern __shared__ __align__(1024) unsigned char tc_smem[];
@@ -358,14 +363,15 @@ __global__ void __launch_bounds__(tc_threads(WC), 1)
     const uint64_t descB_col = tc_desc(smem_addr(sBc), (unsigned)NG * kTcCore, kTcCore);
     const uint64_t descA_row = tc_desc(aBase, KBE_TC_MN_LBO, KBE_TC_MN_SBO);
     const uint64_t descB_row = tc_desc(smem_addr(sBr), (unsigned)NG * kTcCore, kTcCore);
-    int gcount = 0, scount = 0, ucount = 0;
-    for (int u = blockIdx.x; u < units && !abort_flag; u += gridDim.x, ++ucount) {
+    int gcount = 0, scount = 0, dcount = 0;   // dcount: row-use drains so far
+    for (int u = blockIdx.x; u < units && !abort_flag; u += gridDim.x) {
       const int p = P - 1 - u / nk;
       const int R0 = p * TI, R1 = min(R0 + TI, n + 1);
       const int S = (R1 - 1) / TM + 1;
-      if (ucount >= 1 && !wait(&dre, (unsigned)((ucount - 1) & 1))) break;
       for (int s = 0; s < S && !abort_flag; ++s, ++scount) {
         const int M0 = s * TM, b = scount & 1, use = scount >> 1;
+        // a strip group starts: its row-use accumulators are overwritten once drained
+        if (s % SD == 0 && dcount >= 1 && !wait(&dre, (unsigned)((dcount - 1) & 1))) break;
         if (!wait(&brf[b], (unsigned)(use & 1))) break;
         if (use >= 1 && !wait(&dce[b], (unsigned)((use - 1) & 1))) break;
         tc_fence_after();
@@ -427,7 +433,7 @@ __global__ void __launch_bounds__(tc_threads(WC), 1)
                   colinit |= 1u << c;
                 }
                 tc_mma(drow + (uint32_t)((q % NR) * N), dAr + (h * kTcPlane + 2u * q * kTcCore >> 4),
-                       dBr + (2u * q * NG * kTcCore >> 4), id_row, (s == 0 && h == 0 && q < NR) ? 0 : 1);
+                       dBr + (2u * q * NG * kTcCore >> 4), id_row, (s % SD == 0 && h == 0 && q < NR) ? 0 : 1);
               }
             tc_commit(&empty[set]);
           }
@@ -442,11 +448,11 @@ __global__ void __launch_bounds__(tc_threads(WC), 1)
                      tc_desc(smem_addr(sZero), 0, 0), id_col, 0);
           tc_commit(&dcf[b]);
           tc_commit(&bre[b]);
+          if (s % SD == SD - 1 || s == S - 1) tc_commit(&drf);   // the strip group's row use
         }
+        if (s % SD == SD - 1 || s == S - 1) ++dcount;
         __syncwarp();
       }
-      if (lane == 0) tc_commit(&drf);
-      __syncwarp();
     }
     if (lane == 0) {   // every MMA done before the columns are released
       tc_commit(&done);
@@ -483,8 +489,8 @@ __global__ void __launch_bounds__(tc_threads(WC), 1)
     const uint32_t lane_addr = tmem + ((uint32_t)(ew * 32) << 16);
     const float inv = 1.f / ((float)kF16HistScale * tc_coef_scale(cmax));
     const size_t nb2 = (size_t)NB * NB;
-    int scount = 0, ucount = 0;
-    for (int u = blockIdx.x; u < units && !abort_flag; u += gridDim.x, ++ucount) {
+    int scount = 0, dcount = 0;
+    for (int u = blockIdx.x; u < units && !abort_flag; u += gridDim.x) {
       const int p = P - 1 - u / nk, k = u % nk;
       const int R0 = p * TI, R1 = min(R0 + TI, n + 1);
       const int S = (R1 - 1) / TM + 1;
@@ -492,70 +498,79 @@ __global__ void __launch_bounds__(tc_threads(WC), 1)
         const int M0 = s * TM, b = scount & 1, use = scount >> 1;
         if (!wait(&dcf[b], (unsigned)(use & 1))) break;
         tc_fence_after();
-        float v[N];
+        {
+          float v[N];
 #pragma unroll
-        for (int c = 0; c < N; c += 16) tc_ld16(lane_addr + (uint32_t)(b * NC * N + c), v + c);
+          for (int c = 0; c < N; c += 16) tc_ld16(lane_addr + (uint32_t)(b * NC * N + c), v + c);
 #pragma unroll
-        for (int acc = 1; acc < NC; ++acc) {
-          float w[N];
+          for (int acc = 1; acc < NC; ++acc) {
+            float w[N];
 #pragma unroll
-          for (int c = 0; c < N; c += 16) tc_ld16(lane_addr + (uint32_t)((b * NC + acc) * N + c), w + c);
+            for (int c = 0; c < N; c += 16) tc_ld16(lane_addr + (uint32_t)((b * NC + acc) * N + c), w + c);
+            tc_wait_ld();
+#pragma unroll
+            for (int c = 0; c < N; ++c) v[c] += w[c];
+          }
           tc_wait_ld();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&dce[b]);
+          // row L = (x, m, s): value (a, re/im) = part hi + part lo
+          const int x = L / 64, ml = (L % 64) / NB, sc = L % NB, m = M0 + ml;
+          if (ml < TM && m <= n) {
+            const float sg = x ? -inv : inv;   // Y -= C1 dB
+            float2 *dst = CP + ((((size_t)p * (n + 1) + m) * nk + k) * 2 + x) * nb2 + sc;
 #pragma unroll
-          for (int c = 0; c < N; ++c) v[c] += w[c];
+            for (int a = 0; a < NB; ++a)
+              dst[(size_t)a * NB] =
+                  make_float2(sg * (v[2 * a] + v[2 * NB + 2 * a]), sg * (v[2 * a + 1] + v[2 * NB + 2 * a + 1]));
+          }
         }
-        tc_wait_ld();
+        if (!(s % SD == SD - 1 || s == S - 1)) continue;
+        // end of a strip group: drain the row-use accumulators of the groups its
+        // first strip reached (every later strip of the group reaches a subset)
+        if (abort_flag || !wait(&drf, (unsigned)(dcount & 1))) break;
+        ++dcount;
+        tc_fence_after();
+        const int s0 = s - s % SD, sg = s0 / SD;
+        const int groups = (R1 - R0 + RG - 1) / RG, g0 = (max(R0, s0 * TM) - R0) / RG;
+        for (int gi = g0; gi < groups; ++gi) {
+          float v[N];
+#pragma unroll
+          for (int c = 0; c < N; c += 16) tc_ld16(lane_addr + (uint32_t)((2 * NC + gi * NR) * N + c), v + c);
+          tc_wait_ld();
+          for (int acc = 1; acc < NR; ++acc) {
+            float w[N];
+#pragma unroll
+            for (int c = 0; c < N; c += 16) tc_ld16(lane_addr + (uint32_t)((2 * NC + gi * NR + acc) * N + c), w + c);
+            tc_wait_ld();
+#pragma unroll
+            for (int c = 0; c < N; ++c) v[c] += w[c];
+          }
+          // row L = (i, r, re/im of B); value (a, re/im of C) = part hi + part lo
+          float pr[NB], pi[NB];   // P[mine][re][a], P[mine][im][a]
+#pragma unroll
+          for (int a = 0; a < NB; ++a) {
+            pr[a] = v[2 * a] + v[2 * NB + 2 * a];
+            pi[a] = v[2 * a + 1] + v[2 * NB + 2 * a + 1];
+          }
+          const int il = L / (2 * NB), r = (L % (2 * NB)) / 2, riA = L & 1, i = R0 + gi * RG + il;
+          // conj(B) C = (P[re][re] + P[im][im]) + i (P[re][im] - P[im][re]); the re lane
+          // writes a < NB/2, the im lane a >= NB/2
+#pragma unroll
+          for (int a = 0; a < NB; ++a) {
+            const float or_ = __shfl_xor_sync(0xffffffffu, pr[a], 1), oi = __shfl_xor_sync(0xffffffffu, pi[a], 1);
+            const float prr = riA ? or_ : pr[a], pii = riA ? pi[a] : oi;    // P[re][re], P[im][im]
+            const float pri = riA ? oi : pi[a], pir = riA ? pr[a] : or_;    // P[re][im], P[im][re]
+            if ((a < NB / 2) == (riA == 0) && il < RG && i < R1)
+              RP[((((size_t)sg * (n + 1) + i) * nk + k) * NB + a) * NB + r] =
+                  make_float2(-inv * (prr + pii), -inv * (pri - pir));
+          }
+        }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&dce[b]);
-        // row L = (x, m, s): value (a, re/im) = part hi + part lo
-        const int x = L / 64, ml = (L % 64) / NB, sc = L % NB, m = M0 + ml;
-        if (ml < TM && m <= n) {
-          const float sg = x ? -inv : inv;   // Y -= C1 dB
-          float2 *dst = CP + ((((size_t)p * (n + 1) + m) * nk + k) * 2 + x) * nb2 + sc;
-#pragma unroll
-          for (int a = 0; a < NB; ++a)
-            dst[(size_t)a * NB] = make_float2(sg * (v[2 * a] + v[2 * NB + 2 * a]), sg * (v[2 * a + 1] + v[2 * NB + 2 * a + 1]));
-        }
+        if (lane == 0) mbar_arrive(&dre);
       }
-      if (abort_flag || !wait(&drf, (unsigned)(ucount & 1))) break;
-      tc_fence_after();
-      const int groups = (R1 - R0 + RG - 1) / RG;
-      for (int gi = 0; gi < groups; ++gi) {
-        float v[N];
-#pragma unroll
-        for (int c = 0; c < N; c += 16) tc_ld16(lane_addr + (uint32_t)((2 * NC + gi * NR) * N + c), v + c);
-        tc_wait_ld();
-        for (int acc = 1; acc < NR; ++acc) {
-          float w[N];
-#pragma unroll
-          for (int c = 0; c < N; c += 16) tc_ld16(lane_addr + (uint32_t)((2 * NC + gi * NR + acc) * N + c), w + c);
-          tc_wait_ld();
-#pragma unroll
-          for (int c = 0; c < N; ++c) v[c] += w[c];
-        }
-        // row L = (i, r, re/im of B); value (a, re/im of C) = part hi + part lo
-        float pr[NB], pi[NB];   // P[mine][re][a], P[mine][im][a]
-#pragma unroll
-        for (int a = 0; a < NB; ++a) {
-          pr[a] = v[2 * a] + v[2 * NB + 2 * a];
-          pi[a] = v[2 * a + 1] + v[2 * NB + 2 * a + 1];
-        }
-        const int il = L / (2 * NB), r = (L % (2 * NB)) / 2, riA = L & 1, i = R0 + gi * RG + il;
-        // conj(B) C = (P[re][re] + P[im][im]) + i (P[re][im] - P[im][re]); the re lane
-        // writes a < NB/2, the im lane a >= NB/2
-#pragma unroll
-        for (int a = 0; a < NB; ++a) {
-          const float or_ = __shfl_xor_sync(0xffffffffu, pr[a], 1), oi = __shfl_xor_sync(0xffffffffu, pi[a], 1);
-          const float prr = riA ? or_ : pr[a], pii = riA ? pi[a] : oi;    // P[re][re], P[im][im]
-          const float pri = riA ? oi : pi[a], pir = riA ? pr[a] : or_;    // P[re][im], P[im][re]
-          if ((a < NB / 2) == (riA == 0) && il < RG && i < R1)
-            RP[(((size_t)i * nk + k) * NB + a) * NB + r] = make_float2(-inv * (prr + pii), -inv * (pri - pir));
-        }
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&dre);
     }
   }
   tc_fence_before();
@@ -583,7 +598,7 @@ __global__ void __launch_bounds__(256)
                      const __half *__restrict__ H, double2 *__restrict__ I, int n, int nk, int TI, int cap,
                      const int *__restrict__ skip) {
   if (skip && *skip) return;
-  constexpr int TM = TcCfg<NB>::TM, NB2 = NB * NB, KTR = tc_red_kt<NB>(), ITEMS = KTR * NB2;
+  constexpr int TM = TcCfg<NB>::TM, NB2 = NB * NB, KTR = tc_red_kt<NB>(), ITEMS = KTR * NB2, SD = tc_sd(NB);
   __shared__ double2 sI[2][NB2][KTR];      // [x][ab][kk]
   __shared__ float2 sC[3][NB2][KTR];       // C1, C2^<, C3 of node j: [q][a c][kk]
   const size_t blk = (size_t)NB2 * nk;
@@ -601,8 +616,12 @@ __global__ void __launch_bounds__(256)
     const int ab = t % NB2, kk = t / NB2, k = k0 + kk;
     if (k >= nk) continue;
     const int a = ab / NB, b = ab % NB;
-    const float2 rp = RP[((size_t)j * nk + k) * NB2 + ab];
-    double xr = rp.x, xi = rp.y, yr = 0.0, yi = 0.0;
+    double xr = 0.0, xi = 0.0, yr = 0.0, yi = 0.0;
+    for (int sg = 0; sg * SD * TM <= j; ++sg) {   // the row use's partial of each strip group reaching row j
+      const float2 rp = RP[(((size_t)sg * (n + 1) + j) * nk + k) * NB2 + ab];
+      xr += rp.x;
+      xi += rp.y;
+    }
     for (int p = pmin; p < P; ++p) {
       const size_t o = ((((size_t)p * (n + 1) + j) * nk + k) * 2) * NB2 + ab;
       const float2 x = CP[o], y = CP[o + NB2];
@@ -690,7 +709,10 @@ int tc_lt(int nb, int n) {   // row-use coefficient tiles per (x, k): strips x T
   return (n / tm + 1) * tm * nb / 8;
 }
 
-// part: [256-byte header (cmax)][Bc][Br][CP][RP]
+// strip groups of a row: strips of TM columns, SD at a time
+int tc_strip_groups(int nb, int n) { return (n / tc_tm_of(nb) + tc_sd(nb)) / tc_sd(nb); }
+
+// part: [256-byte header (cmax)][Bc][Br][CP][RP per strip group]
 struct TcParts {
   unsigned *cmax;
   __half *Bc, *Br;
@@ -772,7 +794,7 @@ size_t tc_part_bytes(const Mesh &m, int n, int TI) {
   b += ((size_t)m.nk * (n + 1) * 16 * m.nb * m.nb + 255) / 256 * 256;
   b += ((size_t)2 * m.nk * tc_lt(m.nb, n) * 64 * m.nb + 255) / 256 * 256;
   b += (((size_t)((n + TI) / TI) * (n + 1) * 2 * blk) * sizeof(float2) + 255) / 256 * 256;
-  b += (size_t)(n + 1) * blk * sizeof(float2);
+  b += (size_t)tc_strip_groups(m.nb, n) * (n + 1) * blk * sizeof(float2);
   return b;
 }
 

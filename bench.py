@@ -549,71 +549,99 @@ def c3_form(kbe, stream, peaks):
     return out
 
 
-BATCH_N, BATCH_NT = 16, 64
+BATCH_WINDOW = 128   # timed steps per system (every drawn N_t is >= 256)
+BATCH_MARGIN = 8 << 30
 
 
 def batched_form(kbe, stream, args):
-    """The first 16 systems of the uneven 64-system draw (N_b 2..16, 4x4..12x12,
-    each truncated to 64 steps), advanced together (kbe_batch_*, one stream
-    per system) and one after another on one stream; FP64."""
+    """The uneven 64-system draw (seed 3: N_b in {2, 4, 6, 8, 12, 16}, 4x4..12x12
+    meshes, N_t in [256, 1024]; FP64). Admission: systems allocated at their
+    drawn N_t, taken while they fit in device memory (free memory less a margin),
+    in the order: the smallest system of each N_b class, then the others
+    ascending by size. Each distinct (N_b, mesh) shape is autotuned first
+    (kbe_autotune on a handle of that shape over the window's rows). Every
+    admitted system then runs its first BATCH_WINDOW steps (a truncation of its
+    drawn N_t, reported per system), three ways: the stream form (one stream per
+    system), the persistent form (stage-major steps, the sweeps of all systems in
+    one launch per N_b class), and one system after another. One untimed pass,
+    one timed pass each (a pass is reset + the window, all systems)."""
     import torch
     systems = ki.batched(64)
-    full = sum(kbe.memory_bytes(kbe.system_config(x)) for x in systems)
-    sel = systems[:BATCH_N]
-    nts = [min(BATCH_NT, x.nt) for x in sel]
-    units = sum(nts)
-    b = kbe.KBEBatch(sel, nt_max=nts, stream=stream)
-    for _ in range(max(1, args.warmup)):
-        b.reset()
-        b.step(BATCH_NT)
-    b.synchronize()
+    need = [kbe.memory_bytes(kbe.system_config(x)) for x in systems]
+    classes = sorted(set(x.nb for x in systems))
+    first = [min((i for i in range(len(systems)) if systems[i].nb == c), key=lambda i: need[i]) for c in classes]
+    order = first + sorted((i for i in range(len(systems)) if i not in first), key=lambda i: need[i])
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        b.reset()
-        b.step(BATCH_NT)
-    b.synchronize()
-    torch.cuda.synchronize()
-    t_batch = (time.perf_counter() - t0) / args.steps
-    b.set_graphs(True)            # each system replays its 64 steps as one captured graph
-    for _ in range(max(1, args.warmup)):
-        b.reset()
-        b.step(BATCH_NT)
-    b.synchronize()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        b.reset()
-        b.step(BATCH_NT)
-    b.synchronize()
-    torch.cuda.synchronize()
-    t_graph = (time.perf_counter() - t0) / args.steps
-    b.close()
-    singles = [kbe.KBE.from_system(x, nt_max=nt, stream=stream) for x, nt in zip(sel, nts)]
-    for g, nt in zip(singles, nts):
-        g.reset()
-        g.step(nt)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        for g, nt in zip(singles, nts):
-            g.reset()
-            g.step(nt)
-    for g in singles:
-        g.synchronize()
-    torch.cuda.synchronize()
-    t_seq = (time.perf_counter() - t0) / args.steps
-    for g in singles:
-        g.close()
+    torch.cuda.empty_cache()
     free, tot = torch.cuda.mem_get_info()
-    return {"workload": f"first {BATCH_N} of the 64 uneven systems (seed 3), each truncated to "
-                        f"{BATCH_NT} steps; N_b {sorted(set(x.nb for x in sel))}",
-            "value": units / t_batch, "unit": "time-steps/s (summed over systems)",
-            "sequential_value": units / t_seq, "speedup_vs_sequential": t_seq / t_batch,
-            "graphs_value": units / t_graph, "graphs_speedup_vs_sequential": t_seq / t_graph,
-            "full_64_system_fp64_bytes": int(full), "device_bytes": int(tot),
-            "note": "the full 64-system draw needs this many bytes in FP64 and does not fit; "
-                    "kbe_batch_create admits systems in order within the device budget"}
+    budget = max(0, free - BATCH_MARGIN)
+    expect, used = [], 0
+    for i in order:            # kbe_batch_create's rule: in order, while the allocation fits
+        if used + need[i] <= budget:
+            expect.append(i)
+            used += need[i]
+    tiles = {}
+    for i in expect:           # one tuning per distinct shape (the table is per shape and row bucket)
+        x = systems[i]
+        key = f"N_b={x.nb} {x.L[0]}x{x.L[1]}"
+        if key in tiles:
+            continue
+        g = kbe.KBE.from_system(x, nt_max=BATCH_WINDOW, stream=stream)
+        g.reset()
+        t = g.autotune()
+        g.close()
+        tiles[key] = [int(v) for v in t if v != 0]
+    sel = [systems[i] for i in order]
+    b = kbe.KBEBatch(sel, budget_bytes=budget, stream=stream)
+    adm = [order[q] for q in range(len(order)) if b.admitted[q]]
+    runs = [b.systems[q] for q in range(len(order)) if b.admitted[q]]
+    units = sum(min(BATCH_WINDOW, systems[i].nt) for i in adm)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    def batch_pass():
+        b.reset()
+        b.step(BATCH_WINDOW)
+        b.synchronize()
+
+    def sequential_pass():
+        for g in runs:
+            g.reset()
+            g.step(BATCH_WINDOW)
+            g.synchronize()
+
+    t_stream = timed(batch_pass)
+    b.set_persistent(True)
+    l0 = b.sweep_launches()
+    t_pers = timed(batch_pass)
+    launches = (b.sweep_launches() - l0) // 2
+    b.set_persistent(False)
+    t_seq = timed(sequential_pass)
+    b.close()
+    return {"workload": f"uneven 64-system draw (seed 3), FP64: {len(adm)} systems admitted at their drawn N_t "
+                        f"({used / 1e9:.1f} GB of {tot / 1e9:.1f} GB), each timed over its first "
+                        f"{BATCH_WINDOW} steps",
+            "value": units / t_pers, "unit": "time-steps/s (summed over systems)",
+            "persistent_value": units / t_pers, "stream_value": units / t_stream,
+            "sequential_value": units / t_seq,
+            "persistent_speedup_vs_sequential": t_seq / t_pers,
+            "persistent_speedup_vs_stream": t_stream / t_pers,
+            "stream_speedup_vs_sequential": t_seq / t_stream,
+            "persistent_sweep_launches_per_pass": int(launches),
+            "admitted": [{"system": i, "N_b": systems[i].nb, "mesh": f"{systems[i].L[0]}x{systems[i].L[1]}",
+                          "drawn_N_t": systems[i].nt, "steps_timed": min(BATCH_WINDOW, systems[i].nt)}
+                         for i in adm],
+            "not_admitted": sorted(set(range(len(systems))) - set(adm)),
+            "autotuned_l_split_targets_per_row_bucket": tiles,
+            "full_64_system_fp64_bytes": int(sum(need)), "device_bytes": int(tot),
+            "truncation": f"every admitted system runs steps 1..{BATCH_WINDOW} of its drawn N_t "
+                          "(allocation and admission at the drawn N_t)"}
 
 
 class OracleSampler:

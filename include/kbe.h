@@ -333,6 +333,22 @@ kbe_status kbe_batch_synchronize(kbe_batch *b);
  * (kbe_set_graphs). Results are bitwise those of the stream-ordered batch.
  * Synchronises the batch's stream. enable = 0 switches back. */
 kbe_status kbe_batch_set_graphs(kbe_batch *b, int enable);
+/* Persistent mode for the batch (FP64 histories only; KBE_ERR_UNSUPPORTED
+ * otherwise, or while a system has profiling or an injected fault on). Each
+ * kbe_batch_step runs the steps stage-major: every system advances on its own
+ * stream up to its next collision sweep (Eq. 6, the memory integrals of the
+ * predictor-corrector step of Sec. 3), then the sweeps of all systems of one
+ * sweep class (N_b, quadrature, kernel form) run as ONE persistent launch on
+ * that class's stream: the CTAs walk the concatenated block lists of the
+ * systems, each at its own autotuned l-split (kbe_autotune); then those
+ * systems continue. Classes do not wait for one another. With
+ * graphs on (kbe_batch_set_graphs) and a non-default stream the call is one
+ * captured graph as before. Results are bitwise those of the stream-ordered
+ * batch. Synchronises the batch's stream; enable = 0 switches back. */
+kbe_status kbe_batch_set_persistent(kbe_batch *b, int enable);
+/* Persistent sweep launches that kbe_batch_step has enqueued in the eager
+ * persistent mode (graph replays are not counted); -1 for a NULL batch. */
+long kbe_batch_sweep_launches(const kbe_batch *b);
 
 /* Diagnostics of the loaded library on the current device: binary_version
  * (may be NULL) receives the compute capability its kernels were compiled for

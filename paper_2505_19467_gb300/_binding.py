@@ -39,7 +39,8 @@ EXPORTS = [
     "kbe_set_dipole", "kbe_backward", "kbe_backward_memory_bytes", "kbe_corrector_iterations",
     "kbe_op_collision_row_quad", "kbe_set_graphs", "kbe_autotune", "kbe_debug_inject", "kbe_batch_set_graphs",
     "kbe_observables_all_dev", "kbe_get_row_dev", "kbe_device_info", "kbe_measure_fma_peaks",
-    "kbe_set_sweep_choice", "kbe_op_pack_mesh", "kbe_history_bytes",
+    "kbe_set_sweep_choice", "kbe_op_pack_mesh", "kbe_history_bytes", "kbe_batch_set_persistent",
+    "kbe_batch_sweep_launches",
 ]
 
 
@@ -127,6 +128,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "kbe_autotune": (I, [P, P]),
         "kbe_debug_inject": (I, [P, I]),
         "kbe_batch_set_graphs": (I, [P, I]),
+        "kbe_batch_set_persistent": (I, [P, I]),
+        "kbe_batch_sweep_launches": (ctypes.c_long, [P]),
         "kbe_op_collision_row_quad": (I, [pmesh, I, D, I, I, P, P, P, P, S, P]),
         "kbe_observables_all_dev": (I, [P, P, P]),
         "kbe_get_row_dev": (I, [P, I, I, P]),
@@ -499,6 +502,15 @@ class KBEBatch:
         """graph mode: one captured graph per batch step call on a non-default
         stream, per-system graphs on the default one (kbe_batch_set_graphs)"""
         _check(load().kbe_batch_set_graphs(self._b, int(enable)))
+
+    def set_persistent(self, enable: bool = True):
+        """stage-major steps with the sweeps of all systems in one persistent
+        launch per (N_b, quadrature, form); FP64 histories (kbe_batch_set_persistent)"""
+        _check(load().kbe_batch_set_persistent(self._b, int(enable)))
+
+    def sweep_launches(self) -> int:
+        """persistent sweep launches enqueued eagerly so far (kbe_batch_sweep_launches)"""
+        return int(load().kbe_batch_sweep_launches(self._b))
 
     def synchronize(self):
         _check(load().kbe_batch_synchronize(self._b))

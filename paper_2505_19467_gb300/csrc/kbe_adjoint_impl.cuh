@@ -578,8 +578,9 @@ __global__ void adj_uv_kernel(int n, int nk, double theta, const double2 *__rest
 
 // Time diagonal and propagators, per k (one matrix group per k-point):
 //   G^<(n,n) = U Gd U^+ - i X,  G^>(n,n) = G^<(n,n) - i,
-//   X = tau sum_{m=0}^{18} Q_m / (m+1),  Q_m = (-i tau / m)(h Q_{m-1} - Q_{m-1} h),  Q_0 = Sbar,
-//   U = sum_{m=0}^{14} P_m,  V = -i tau sum_m P_m / (m+1),  P_m = P_{m-1} (-i tau h) / m,
+//   X = tau sum_{m=0}^{mx} Q_m / (m+1),  Q_m = (-i tau / m)(h Q_{m-1} - Q_{m-1} h),  Q_0 = Sbar,
+//   U = sum_{m=0}^{mexp} P_m,  V = -i tau sum_m P_m / (m+1),  P_m = P_{m-1} (-i tau h) / m,
+// with the forward kernel's series lengths mx, mexp (series_plan),
 // with tau = dt (no doubling; a step that needed one sets kDevAdjUnsupported).
 // Transposed, with ld = lam^<(n,n) + lam^>(n,n):
 //   lam_U += ld U Gd^+ + ld^+ U Gd,  lam_Gd += U^+ ld U,  lam_X = i ld,
@@ -588,7 +589,7 @@ __global__ void adj_uv_kernel(int n, int nk, double theta, const double2 *__rest
 //   lam_P_{m-1} = lam_U + (i tau / m) lam_V + lam_P_m (-i tau h)^+ / m,
 //   lam_(-i tau h) += P_{m-1}^+ lam_P_m / m, lam_h += i tau lam_(-i tau h);
 //   lam_Sbar = lam_Q_0 -> lam_I^<(diag) += (1-theta or theta) (lam_Sbar + lam_Sbar^+).
-// The forward chains Q_0..Q_17 and P_0..P_13 are kept in `chain` (global,
+// The forward chains Q_0..Q_{mx-1} and P_0..P_{mexp-1} are kept in `chain` (global,
 // [m][a][b][k]); each thread reads back only what it wrote itself.
 template <int NB>
 __global__ void __launch_bounds__(256) adj_diag_kernel(
@@ -630,8 +631,8 @@ __global__ void __launch_bounds__(256) adj_diag_kernel(
   }
   Hs[o] = hv;
   __syncthreads();
-  const int s = doublings<NB>(g, Hs, kpc, nvalid, dt, red);
-  if (s != 0) {   // uniform over the CTA
+  const SeriesPlan sp = series_plan<NB>(g, Hs, kpc, nvalid, dt, red);
+  if (sp.s != 0) {   // uniform over the CTA
     if (threadIdx.x == 0) atomicOr(status, kDevAdjUnsupported);
     return;
   }
@@ -652,29 +653,31 @@ __global__ void __launch_bounds__(256) adj_diag_kernel(
     double2 *t = lamGprev + (size_t)(n - 1) * 2 * blk + oab;
     *t = c_add(*t, gpd);
   }
-  // X series: forward chain Q_0..Q_17
+  // X series: forward chain Q_0..Q_{mx-1}
   Qm[o] = sv;
   if (active) chain[oab] = sv;
   __syncthreads();
-  for (int m = 1; m <= 17; ++m) {
+  for (int m = 1; m < sp.mx; ++m) {
+    const double cm = tau * kSeriesInv[m];
     const double2 c = c_sub(g.mm(Hs, Qm), g.mm(Qm, Hs));
-    const double2 qv = make_double2(tau * c.y / m, -tau * c.x / m);
+    const double2 qv = make_double2(cm * c.y, -cm * c.x);
     __syncthreads();
     Qm[o] = qv;
     if (active) chain[(size_t)m * blk + oab] = qv;
     __syncthreads();
   }
   const double2 lX = c_i(ld);
-  double2 cur = c_scale(tau / 19.0, lX), lh = zero;
-  for (int m = 18; m >= 1; --m) {
+  double2 cur = c_scale(tau * kSeriesInv[sp.mx + 1], lX), lh = zero;
+  for (int m = sp.mx; m >= 1; --m) {
+    const double cm = tau * kSeriesInv[m];
     A1[o] = cur;
     Qm[o] = active ? chain[(size_t)(m - 1) * blk + oab] : zero;
     __syncthreads();
-    const double2 ca = make_double2(0.0, tau / m);   // conj(-i tau / m)
+    const double2 ca = make_double2(0.0, cm);   // conj(-i tau / m)
     lh = c_fma(ca, c_sub(g.mm_adj(A1, Qm), mm_hadj<NB>(g, Qm, A1)), lh);
     const double2 t2 = c_sub(g.mm(Hs, A1), g.mm(A1, Hs));
     __syncthreads();
-    cur = c_add(c_scale(tau / m, lX), c_mul(ca, t2));
+    cur = c_add(c_scale(cm, lX), c_mul(ca, t2));
   }
   A1[o] = cur;
   __syncthreads();
@@ -688,29 +691,30 @@ __global__ void __launch_bounds__(256) adj_diag_kernel(
     }
   }
   __syncthreads();
-  // propagator series: forward chain P_0..P_13
+  // propagator series: forward chain P_0..P_{mexp-1}
   const double2 one = make_double2(g.a == g.b ? 1.0 : 0.0, 0.0);
   Qm[o] = one;
   if (active) chain[oab] = one;
   __syncthreads();
-  for (int m = 1; m <= 13; ++m) {
+  for (int m = 1; m < sp.mexp; ++m) {
+    const double cm = tau * kSeriesInv[m];
     const double2 c = g.mm(Qm, Hs);
-    const double2 pv = make_double2(tau * c.y / m, -tau * c.x / m);
+    const double2 pv = make_double2(cm * c.y, -cm * c.x);
     __syncthreads();
     Qm[o] = pv;
     if (active) chain[(size_t)m * blk + oab] = pv;
     __syncthreads();
   }
   double2 lY = zero;
-  cur = c_add(lu, c_mul(make_double2(0.0, tau / 15.0), lv));
-  for (int m = 14; m >= 1; --m) {
+  cur = c_add(lu, c_mul(make_double2(0.0, tau * kSeriesInv[sp.mexp + 1]), lv));
+  for (int m = sp.mexp; m >= 1; --m) {
     A1[o] = cur;
     Qm[o] = active ? chain[(size_t)(m - 1) * blk + oab] : zero;
     __syncthreads();
-    lY = c_add(lY, c_scale(1.0 / m, mm_hadj<NB>(g, Qm, A1)));
+    lY = c_add(lY, c_scale(kSeriesInv[m], mm_hadj<NB>(g, Qm, A1)));
     const double2 t = g.mm(A1, Hs);   // lam_P h
     __syncthreads();
-    const double2 im = make_double2(0.0, tau / m);
+    const double2 im = make_double2(0.0, tau * kSeriesInv[m]);
     cur = c_add(lu, c_add(c_mul(im, lv), c_mul(im, t)));
   }
   lh = c_add(lh, c_mul(make_double2(0.0, tau), lY));

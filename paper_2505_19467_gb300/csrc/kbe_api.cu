@@ -27,6 +27,10 @@ struct kbe_handle {
   kbe_config cfg{};
   Mesh mesh{};
   cudaStream_t stream = nullptr;
+  // a second stream for work of a step that does not depend on the main
+  // chain: forked from and joined back to `stream` within one stage
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int device = 0;
   size_t blk = 0;   // complex numbers in one (component) block: nb*nb*nk
   int nb2 = 0;
@@ -166,6 +170,33 @@ void free_all(kbe_handle *h) {
     cudaEventDestroy(pe.b);
   }
   h->bev.clear();
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  h->side = nullptr;
+  h->ev_fork = h->ev_join = nullptr;
+}
+
+// Work of a step stage that does not depend on the stage's main chain runs on
+// the side stream (KBE_SIDE_STREAM 1) or in order on the main stream (0).
+#ifndef KBE_SIDE_STREAM
+#define KBE_SIDE_STREAM 1
+#endif
+
+cudaStream_t side_of(const kbe_handle *h) { return KBE_SIDE_STREAM ? h->side : h->stream; }
+
+// the side stream waits for the main stream's work so far
+cudaError_t side_fork(kbe_handle *h) {
+  if (!KBE_SIDE_STREAM) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(h->ev_fork, h->stream);
+  return e == cudaSuccess ? cudaStreamWaitEvent(h->side, h->ev_fork, 0) : e;
+}
+
+// the main stream waits for the side stream's work so far
+cudaError_t side_join(kbe_handle *h) {
+  if (!KBE_SIDE_STREAM) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(h->ev_join, h->side);
+  return e == cudaSuccess ? cudaStreamWaitEvent(h->stream, h->ev_join, 0) : e;
 }
 
 // collision sweep flops of one launch at row n: the method's count with the
@@ -249,7 +280,7 @@ kbe_status evaluate_row(kbe_handle *h, int n, const int *skip = nullptr) {
 
 kbe_status build_props(kbe_handle *h, int n, const double2 *ra, const double2 *rb, double ca, double cb,
                        double2 *hk = nullptr, double2 *Uk = nullptr, double2 *Vk = nullptr,
-                       const int *skip = nullptr) {
+                       const int *skip = nullptr, bool on_side = false) {
   kbe::PropParams p{};
   p.A = A_at(h, n - 1);
   p.rho_a = ra;
@@ -263,7 +294,7 @@ kbe_status build_props(kbe_handle *h, int n, const double2 *ra, const double2 *r
   p.dipM = h->dipE.empty() ? nullptr : h->d_dipM;
   p.dipE = (n - 1 < (int)h->dipE.size()) ? h->dipE[(size_t)(n - 1)] : 0.0;
   cudaError_t e = kbe::launch_build_props(h->mesh, hop_table(h), p, h->cfg.dt, nullptr, hk ? hk : h->hk,
-                                          Uk ? Uk : h->U, Vk ? Vk : h->V, h->stream, skip);
+                                          Uk ? Uk : h->U, Vk ? Vk : h->V, on_side ? side_of(h) : h->stream, skip);
   if (e != cudaSuccess) return cuda_fail(h, e, "build_props");
   if (h->prof) h->stats.launches += 1;
   return KBE_OK;
@@ -275,16 +306,20 @@ kbe_status update(kbe_handle *h, int n, double theta, const int *skip = nullptr,
   double2 *row = frow(h, n);
   // the update kernels also store row n into the history triangle ("publish")
   char *hist = (char *)h->H + kbe::history_row_offset(h->mesh, h->cfg.precision, n);
-  cudaError_t e = kbe::launch_update_row(h->mesh, n, h->cfg.dt, theta, h->hk, h->U, h->V, prev, h->Ip,
-                                         h->Ic, row, h->stream, skip, maxdiff, hist, h->cfg.precision,
-                                         h->cfg.nt_max + 1);
+  // the time diagonal on the side stream, beside the rows j < n
+  cudaError_t e = side_fork(h);
+  if (e == cudaSuccess)
+    e = kbe::launch_update_row(h->mesh, n, h->cfg.dt, theta, h->hk, h->U, h->V, prev, h->Ip, h->Ic, row, h->stream,
+                               skip, maxdiff, hist, h->cfg.precision, h->cfg.nt_max + 1, side_of(h), true);
+  if (e == cudaSuccess) e = side_join(h);
   if (e != cudaSuccess) return cuda_fail(h, e, "update_row");
   if (h->prof) h->stats.launches += 2;
   return KBE_OK;
 }
 
-kbe_status density(kbe_handle *h, int n, double2 *out, const int *skip = nullptr) {
-  cudaError_t e = kbe::launch_local_density(h->mesh, frow(h, n) + (size_t)n * 2 * h->blk, out, h->stream, skip);
+kbe_status density(kbe_handle *h, int n, double2 *out, const int *skip = nullptr, bool on_side = false) {
+  cudaError_t e = kbe::launch_local_density(h->mesh, frow(h, n) + (size_t)n * 2 * h->blk, out,
+                                            on_side ? side_of(h) : h->stream, skip);
   if (e != cudaSuccess) return cuda_fail(h, e, "local_density");
   if (h->prof) h->stats.launches += 1;
   return KBE_OK;
@@ -329,17 +364,25 @@ kbe_status one_step(kbe_handle *h) {
     if (e != cudaSuccess) return cuda_fail(h, e, "corrector flags");
   }
   for (int c = 0; c < h->cfg.n_corr; ++c) {
-    if ((s = density(h, n, rcur, skip)) != KBE_OK) return s;
-    if ((s = build_props(h, n, r1, rcur, 0.5, 0.5, nullptr, nullptr, nullptr, skip)) != KBE_OK) return s;
+    // the midpoint density and the propagators (side stream) do not depend on
+    // the collision row (main stream): they overlap it
+    cudaError_t e = side_fork(h);
+    if (e != cudaSuccess) return cuda_fail(h, e, "stream fork");
+    if ((s = density(h, n, rcur, skip, true)) != KBE_OK) return s;
+    if ((s = build_props(h, n, r1, rcur, 0.5, 0.5, nullptr, nullptr, nullptr, skip, true)) != KBE_OK) return s;
     if ((s = evaluate_row(h, n, skip)) != KBE_OK) return s;
+    if ((e = side_join(h)) != cudaSuccess) return cuda_fail(h, e, "stream join");
     if ((s = update(h, n, 0.5, skip, md)) != KBE_OK) return s;
     if (tol) {
       cudaError_t e = kbe::launch_corr_check(h->d_maxdiff, h->cfg.corr_tol, h->d_skip, h->d_iters + n, h->stream);
       if (e != cudaSuccess) return cuda_fail(h, e, "corrector check");
     }
   }
+  cudaError_t e = side_fork(h);   // the density of row n beside the final collision row
+  if (e != cudaSuccess) return cuda_fail(h, e, "stream fork");
+  if ((s = density(h, n, h->rho + (size_t)n * nb2, nullptr, true)) != KBE_OK) return s;
   if ((s = evaluate_row(h, n)) != KBE_OK) return s;
-  if ((s = density(h, n, h->rho + (size_t)n * nb2)) != KBE_OK) return s;
+  if ((e = side_join(h)) != cudaSuccess) return cuda_fail(h, e, "stream join");
   if ((s = observables(h, n, h->Ic)) != KBE_OK) return s;
   std::swap(h->Ip, h->Ic);
   h->n = n;
@@ -650,6 +693,89 @@ Mesh to_mesh(const kbe_mesh *m) { return Mesh{m->nb, m->L[0], m->L[1], m->L[0] *
 
 }  // namespace
 
+// ---- one step in segments (batched systems) ---------------------------------
+// The sequence of one_step cut at its n_corr + 1 collision sweeps: segment 0
+// runs the predictor and stops before the first sweep, segments 1 .. n_corr
+// finish the previous sweep and stop before the next, segment n_corr + 1
+// finishes the last one and the step. A stopped segment has enqueued the Sigma
+// row and the coefficient rows and hands back the sweep as a job, which the
+// batch launches together with the other systems' (kbe_batch.cu); the
+// arithmetic and the launch shapes are one_step's, so the results are bitwise
+// one_step's. FP64 history only.
+int step_segment_count(const kbe_handle *h) { return h->cfg.n_corr + 2; }
+
+static kbe_status segment_eval_pre(kbe_handle *h, int n, const int *skip, kbe::SweepJob *job) {
+  const double *Ul = h->Useq.size() == 1 ? nullptr : h->d_U;
+  cudaError_t e = kbe::sigma_row(h->mesh, h->v.data(), n, U_at(h, n), Ul, frow(h, n), h->Sig, h->work, h->stream,
+                                 skip, false);
+  if (e == cudaSuccess)
+    e = kbe::prepare_sweep_job(h->mesh, n, h->cfg.dt, h->H, h->Sig, h->Ic, h->coef, h->stream, skip,
+                               h->cfg.quadrature, job);
+  if (e != cudaSuccess) return cuda_fail(h, e, "sweep job");
+  return KBE_OK;
+}
+
+kbe_status step_segment(kbe_handle *h, int seg, kbe::SweepJob *job, bool *has_job) {
+  *has_job = false;
+  if (h->cfg.precision != KBE_PREC_FP64) return fail(h, KBE_ERR_UNSUPPORTED, "step_segment: FP64 history only");
+  const int nc = h->cfg.n_corr;
+  const int n = h->n + 1;   // the row being computed (h->n advances at the last segment)
+  const int nb2 = h->nb2;
+  double2 *r1 = h->rho + (size_t)(n - 1) * nb2;
+  double2 *r2 = h->rho + (size_t)(n >= 2 ? n - 2 : 0) * nb2;
+  double2 *rcur = h->rho + (size_t)(h->cfg.nt_max + 1) * nb2;
+  const bool tol = h->cfg.corr_tol > 0.0;
+  const int *skip = tol ? h->d_skip : nullptr;
+  unsigned long long *md = tol ? h->d_maxdiff : nullptr;
+  kbe_status s;
+  if (seg > 0) {   // the previous segment's sweep has run: its partial sums into I
+    cudaError_t e = kbe::finish_sweep_job(*job, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sweep job finish");
+  }
+  if (seg == 0) {   // predictor: density extrapolated to the midpoint, Ibar = I_{n-1}
+    if ((s = build_props(h, n, r1, r2, n >= 2 ? 1.5 : 1.0, n >= 2 ? -0.5 : 0.0)) != KBE_OK) return s;
+    if ((s = update(h, n, 0.0)) != KBE_OK) return s;
+    if (tol) {
+      cudaError_t e = cudaMemsetAsync(h->d_skip, 0, sizeof(int), h->stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(h->d_maxdiff, 0, sizeof(unsigned long long), h->stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(h->d_iters + n, 0, sizeof(int), h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e, "corrector flags");
+    }
+  } else if (seg <= nc) {   // the corrector pass seg - 1 completes
+    if ((s = update(h, n, 0.5, skip, md)) != KBE_OK) return s;
+    if (tol) {
+      cudaError_t e = kbe::launch_corr_check(h->d_maxdiff, h->cfg.corr_tol, h->d_skip, h->d_iters + n, h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e, "corrector check");
+    }
+  }
+  if (seg < nc) {   // corrector pass seg: its evaluation
+    if ((s = density(h, n, rcur, skip)) != KBE_OK) return s;
+    if ((s = build_props(h, n, r1, rcur, 0.5, 0.5, nullptr, nullptr, nullptr, skip)) != KBE_OK) return s;
+    if ((s = segment_eval_pre(h, n, skip, job)) != KBE_OK) return s;
+    *has_job = true;
+    return KBE_OK;
+  }
+  if (seg == nc) {   // the final evaluation
+    if ((s = segment_eval_pre(h, n, nullptr, job)) != KBE_OK) return s;
+    *has_job = true;
+    return KBE_OK;
+  }
+  if ((s = density(h, n, h->rho + (size_t)n * nb2)) != KBE_OK) return s;
+  if ((s = observables(h, n, h->Ic)) != KBE_OK) return s;
+  std::swap(h->Ip, h->Ic);
+  h->n = n;
+  return KBE_OK;
+}
+
+kbe_status step_segment_check(kbe_handle *h) {
+  if (h->sticky != KBE_OK) return fail(h, h->sticky, "step: handle has a sticky error; reset it");
+  if (h->n < 0) return fail(h, KBE_ERR_STATE, "step: call kbe_reset first");
+  if (h->n + 1 > h->cfg.nt_max) return fail(h, KBE_ERR_STATE, "step: past nt_max");
+  if (h->cfg.precision != KBE_PREC_FP64 || h->prof || h->inject)
+    return fail(h, KBE_ERR_UNSUPPORTED, "step: the batched sweep needs FP64 history, no profiling, no injection");
+  return KBE_OK;
+}
+
 void kbe::set_last_error(const std::string &msg) { g_create_err = msg; }
 
 // ---- pieces of kbe_step for a graph that spans several handles (kbe_batch) ----
@@ -698,7 +824,16 @@ void kbe::step_key(const kbe_handle *h, int *ring, unsigned *gen) {
   *gen = h->graph_gen;
 }
 
+kbe::StepMark kbe::step_mark(const kbe_handle *h) { return {h->n, h->Ip, h->Ic}; }
+
+void kbe::step_rewind(kbe_handle *h, const kbe::StepMark &mk) {
+  h->n = mk.n;
+  h->Ip = (double2 *)mk.Ip;
+  h->Ic = (double2 *)mk.Ic;
+}
+
 cudaStream_t kbe::handle_stream(const kbe_handle *h) { return h->stream; }
+int kbe::handle_precision(const kbe_handle *h) { return h->cfg.precision; }
 
 // device bytes of one handle (the allocations of kbe_create)
 static size_t handle_bytes(const kbe_config *cfg) {
@@ -744,6 +879,14 @@ kbe_status kbe_create(const kbe_config *cfg, void *stream, kbe_handle **out) {
   h->cfg = *cfg;
   h->mesh = Mesh{cfg->nb, cfg->L[0], cfg->L[1], cfg->L[0] * cfg->L[1]};
   h->stream = (cudaStream_t)stream;
+  if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    free_all(h);
+    delete h;
+    cudaGetLastError();
+    return fail(nullptr, KBE_ERR_CUDA, "kbe_create: side stream / events");
+  }
   h->nb2 = cfg->nb * cfg->nb;
   h->blk = (size_t)h->nb2 * h->mesh.nk;
   h->v.assign((size_t)h->nb2, 0.0);

@@ -11,6 +11,14 @@
 // kernels on its own stream inside it, forked from and joined to the caller's
 // stream) and later calls with the same row, count and ring order replay it
 // with one launch; on the default stream each system replays its own graph.
+// In the persistent mode (kbe_batch_set_persistent, FP64 histories) the steps
+// are enqueued stage-major: every system runs its step up to its next collision
+// sweep on its own stream, then ONE persistent launch per sweep class (N_b,
+// quadrature, kernel form), on that class's own stream, runs the sweeps of all
+// systems of the class, walking the concatenation of their block lists (each
+// system's blocks at its own autotuned split), and the systems continue from
+// there; different classes do not wait for one another. With graphs on and a
+// non-default stream the whole call is again one captured graph.
 // Admission is by
 // device memory: systems are taken in order while their allocation fits the
 // budget; the others are reported as not admitted.
@@ -30,6 +38,11 @@ struct kbe_batch {
   std::vector<int> cur;             // host copy of each system's current row
   cudaEvent_t fork = nullptr;
   bool graphs = false;              // replay captured steps (kbe_batch_set_graphs)
+  bool persistent = false;          // stage-major steps, batched sweeps (kbe_batch_set_persistent)
+  long sweep_launches = 0;          // persistent sweep launches enqueued (for reporting)
+  std::map<int, cudaStream_t> class_streams;   // persistent mode: one stream per sweep class
+  std::vector<int> classes_used;    // the classes the current call launched on (joined at its end)
+  cudaEvent_t class_done = nullptr;
   kbe::GraphCache<std::vector<long>> gcache;   // one graph per call shape of the batch
 };
 
@@ -67,6 +80,9 @@ void destroy_all(kbe_batch *b) {
     if (b->done[i]) cudaEventDestroy(b->done[i]);
   }
   if (b->fork) cudaEventDestroy(b->fork);
+  for (auto &cs : b->class_streams) cudaStreamDestroy(cs.second);
+  b->class_streams.clear();
+  if (b->class_done) cudaEventDestroy(b->class_done);
 }
 
 // streams of the admitted systems wait for the caller's prior work
@@ -99,6 +115,115 @@ std::vector<int> step_counts(const kbe_batch *b, int nsteps) {
   return k;
 }
 
+// the sweep class of a job: the jobs of one class share one persistent launch
+int sweep_class(const kbe::SweepJob &j) { return (j.nb * 2 + j.quad) * 2 + j.f64m; }
+
+cudaError_t class_stream(kbe_batch *b, int cls, cudaStream_t *out) {
+  bool seen = false;
+  for (int c : b->classes_used) seen = seen || c == cls;
+  if (!seen) b->classes_used.push_back(cls);
+  auto it = b->class_streams.find(cls);
+  if (it != b->class_streams.end()) {
+    *out = it->second;
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!b->class_done) e = cudaEventCreateWithFlags(&b->class_done, cudaEventDisableTiming);
+  cudaStream_t st = nullptr;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  b->class_streams[cls] = st;
+  *out = st;
+  return cudaSuccess;
+}
+
+// the caller's stream waits for the class streams the call launched on (a
+// capture must rejoin them; a class stream the call did not use is not part
+// of the capture and must not be waited on inside it)
+cudaError_t join_classes(kbe_batch *b) {
+  cudaError_t e = cudaSuccess;
+  for (int c : b->classes_used) {
+    cudaStream_t cs = b->class_streams[c];
+    if (e == cudaSuccess) e = cudaEventRecord(b->class_done, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->main, b->class_done, 0);
+  }
+  b->classes_used.clear();
+  return e;
+}
+
+// the steps k[i] of every system, stage-major: per time step, each system's
+// segments up to its next collision sweep on its own stream; at each cut the
+// systems that stopped there are grouped by sweep class (N_b, quadrature,
+// form), each class's sweeps run as one launch on the class's stream once
+// its systems have arrived, and its systems continue after it. Systems with
+// fewer steps or segments drop out of the later cuts. Ends with the systems'
+// and the classes' streams ahead of the caller's (join_to_main and
+// join_classes follow).
+kbe_status persistent_enqueue(kbe_batch *b, const std::vector<int> &k) {
+  const size_t ns = b->sys.size();
+  b->classes_used.clear();
+  int kmax = 0;
+  for (size_t i = 0; i < ns; ++i)
+    if (b->sys[i] && k[i] > kmax) kmax = k[i];
+  std::vector<kbe::SweepJob> jobs(ns);
+  std::vector<kbe::SweepJob> group;
+  std::vector<size_t> who;
+  for (int t = 0; t < kmax; ++t) {
+    int segs = 0;
+    for (size_t i = 0; i < ns; ++i) {
+      if (!b->sys[i] || t >= k[i]) continue;
+      kbe_status s = step_segment_check(b->sys[i]);
+      if (s != KBE_OK) return s;
+      const int c = step_segment_count(b->sys[i]);
+      if (c > segs) segs = c;
+    }
+    for (int seg = 0; seg < segs; ++seg) {
+      group.clear();
+      who.clear();
+      for (size_t i = 0; i < ns; ++i) {
+        if (!b->sys[i] || t >= k[i] || seg >= step_segment_count(b->sys[i])) continue;
+        bool has = false;
+        kbe_status s = step_segment(b->sys[i], seg, &jobs[i], &has);
+        if (s != KBE_OK) return s;
+        if (has) {
+          group.push_back(jobs[i]);
+          who.push_back(i);
+        }
+      }
+      if (group.empty()) continue;
+      // one launch per sweep class (N_b, quadrature, form), each on its own
+      // stream: a class waits only for its own systems, the classes overlap
+      std::vector<char> taken(group.size(), 0);
+      for (size_t q0 = 0; q0 < group.size(); ++q0) {
+        if (taken[q0]) continue;
+        const int cls = sweep_class(group[q0]);
+        cudaStream_t cs = nullptr;
+        cudaError_t e = class_stream(b, cls, &cs);
+        std::vector<kbe::SweepJob> sub;
+        std::vector<size_t> subw;
+        for (size_t q = q0; q < group.size(); ++q)
+          if (!taken[q] && sweep_class(group[q]) == cls) {
+            taken[q] = 1;
+            sub.push_back(group[q]);
+            subw.push_back(who[q]);
+          }
+        for (size_t q = 0; q < subw.size() && e == cudaSuccess; ++q) {
+          e = cudaEventRecord(b->done[subw[q]], b->streams[subw[q]]);
+          if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, b->done[subw[q]], 0);
+        }
+        int nl = 0;
+        if (e == cudaSuccess) e = kbe::launch_sweep_batch(sub.data(), (int)sub.size(), cs, &nl);
+        if (e == cudaSuccess) e = cudaEventRecord(b->class_done, cs);
+        for (size_t q = 0; q < subw.size() && e == cudaSuccess; ++q)
+          e = cudaStreamWaitEvent(b->streams[subw[q]], b->class_done, 0);
+        if (e != cudaSuccess) return batch_fail(KBE_ERR_CUDA, std::string("batch sweep: ") + cudaGetErrorString(e));
+        b->sweep_launches += nl;
+      }
+    }
+  }
+  return KBE_OK;
+}
+
 // one graph for the whole batch: captured on the caller's stream, each system
 // forked onto its own stream inside the capture and joined back
 kbe_status batch_graph_step(kbe_batch *b, int nsteps) {
@@ -107,7 +232,7 @@ kbe_status batch_graph_step(kbe_batch *b, int nsteps) {
   cudaError_t ej = join_to_main(b);
   if (ej != cudaSuccess) return batch_fail(KBE_ERR_CUDA, std::string("batch_step: ") + cudaGetErrorString(ej));
   const std::vector<int> k = step_counts(b, nsteps);
-  std::vector<long> key{nsteps};
+  std::vector<long> key{2L * nsteps + (b->persistent ? 1 : 0)};
   for (size_t i = 0; i < b->sys.size(); ++i) {
     if (!b->sys[i] || k[i] <= 0) continue;
     kbe_status s = kbe::step_check(b->sys[i], k[i]);
@@ -129,12 +254,31 @@ kbe_status batch_graph_step(kbe_batch *b, int nsteps) {
     if (e != cudaSuccess) return batch_fail(KBE_ERR_CUDA, std::string("batch graph capture: ") + cudaGetErrorString(e));
     kbe_status s = KBE_OK;
     e = cudaEventRecord(b->fork, b->main);
-    for (size_t i = 0; i < b->sys.size() && s == KBE_OK && e == cudaSuccess; ++i) {
-      if (!b->sys[i] || k[i] <= 0) continue;
-      e = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
-      if (e == cudaSuccess) s = kbe::step_record(b->sys[i], k[i]);
-      if (s == KBE_OK && e == cudaSuccess) e = cudaEventRecord(b->done[i], b->streams[i]);
-      if (s == KBE_OK && e == cudaSuccess) e = cudaStreamWaitEvent(b->main, b->done[i], 0);
+    if (b->persistent) {   // stage-major; the host-side step state is put back after the capture
+      std::vector<kbe::StepMark> mk(b->sys.size());
+      for (size_t i = 0; i < b->sys.size() && e == cudaSuccess; ++i)
+        if (b->sys[i] && k[i] > 0) {
+          mk[i] = kbe::step_mark(b->sys[i]);
+          e = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+        }
+      const long nl0 = b->sweep_launches;
+      if (e == cudaSuccess) s = persistent_enqueue(b, k);
+      b->sweep_launches = nl0;
+      for (size_t i = 0; i < b->sys.size(); ++i)
+        if (b->sys[i] && k[i] > 0) {
+          kbe::step_rewind(b->sys[i], mk[i]);
+          if (s == KBE_OK && e == cudaSuccess) e = cudaEventRecord(b->done[i], b->streams[i]);
+          if (s == KBE_OK && e == cudaSuccess) e = cudaStreamWaitEvent(b->main, b->done[i], 0);
+        }
+      if (s == KBE_OK && e == cudaSuccess) e = join_classes(b);
+    } else {
+      for (size_t i = 0; i < b->sys.size() && s == KBE_OK && e == cudaSuccess; ++i) {
+        if (!b->sys[i] || k[i] <= 0) continue;
+        e = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+        if (e == cudaSuccess) s = kbe::step_record(b->sys[i], k[i]);
+        if (s == KBE_OK && e == cudaSuccess) e = cudaEventRecord(b->done[i], b->streams[i]);
+        if (s == KBE_OK && e == cudaSuccess) e = cudaStreamWaitEvent(b->main, b->done[i], 0);
+      }
     }
     cudaGraph_t graph = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(b->main, &graph);
@@ -276,6 +420,17 @@ kbe_status kbe_batch_step(kbe_batch *b, int nsteps) {
   }
   e = fork_from_main(b);
   if (e != cudaSuccess) return batch_fail(KBE_ERR_CUDA, std::string("batch_step: ") + cudaGetErrorString(e));
+  if (b->persistent) {   // stage-major, eagerly enqueued
+    const std::vector<int> k = step_counts(b, nsteps);
+    kbe_status s = persistent_enqueue(b, k);
+    for (size_t i = 0; i < b->sys.size(); ++i)
+      if (b->sys[i] && k[i] > 0) b->cur[i] = kbe::step_mark(b->sys[i]).n;
+    if (s != KBE_OK) return s;
+    e = join_to_main(b);
+    if (e == cudaSuccess) e = join_classes(b);
+    if (e != cudaSuccess) return batch_fail(KBE_ERR_CUDA, std::string("batch_step: ") + cudaGetErrorString(e));
+    return KBE_OK;
+  }
   if (b->graphs) {   // default stream: each system replays its own graph on its stream
     for (size_t i = 0; i < b->sys.size(); ++i) {
       if (!b->sys[i] || b->cur[i] < 0) continue;
@@ -318,6 +473,24 @@ kbe_status kbe_batch_set_graphs(kbe_batch *b, int enable) {
   b->graphs = enable != 0;
   return KBE_OK;
 }
+
+kbe_status kbe_batch_set_persistent(kbe_batch *b, int enable) {
+  if (!b) return KBE_ERR_ARG;
+  if (enable)
+    for (size_t i = 0; i < b->sys.size(); ++i)
+      if (b->sys[i] && !kbe::step_capturable(b->sys[i]))
+        return batch_fail(KBE_ERR_UNSUPPORTED, "batch_set_persistent: a system has profiling or an injected fault on");
+  for (size_t i = 0; enable && i < b->sys.size(); ++i)
+    if (b->sys[i] && kbe::handle_precision(b->sys[i]) != KBE_PREC_FP64)
+      return batch_fail(KBE_ERR_UNSUPPORTED, "batch_set_persistent: the batched sweep needs FP64 histories");
+  cudaError_t e = cudaStreamSynchronize(b->main);
+  if (e != cudaSuccess) return batch_fail(KBE_ERR_CUDA, std::string("batch_set_persistent: ") + cudaGetErrorString(e));
+  drop_batch_graphs(b);
+  b->persistent = enable != 0;
+  return KBE_OK;
+}
+
+long kbe_batch_sweep_launches(const kbe_batch *b) { return b ? b->sweep_launches : -1; }
 
 kbe_status kbe_batch_synchronize(kbe_batch *b) {
   if (!b) return KBE_ERR_ARG;

@@ -377,6 +377,31 @@ cudaError_t launch_row_out(int prec, const double2 *fp64, const void *packed, si
 // copy never completes (bounded waits)
 // inject (test only): 1 makes the staged C64 sweep's first CTA omit its first
 // node's copies, so that its bounded waits run out (kDevTimeout), no fault
+// One system's FP64 collision sweep, prepared (coefficient rows enqueued) for a
+// batched launch with other systems' sweeps (kbe_batch): its operands, its
+// launch shape (k tiles x columns x l-splits) and where its partials go.
+struct SweepJob {
+  const double2 *H, *Cf;
+  const double *Cs;
+  double2 *out, *I;
+  const int *skip;
+  int n, nk, nb, quad, lchunk, nz, tx, threads, f64m;
+};
+cudaError_t prepare_sweep_job(const Mesh &m, int n, double dt, const void *H, const double2 *Sig, double2 *I,
+                              void *work, cudaStream_t st, const int *skip, int quad, SweepJob *job);
+// the sweeps of many jobs: one persistent launch per (N_b, quadrature, form)
+cudaError_t launch_sweep_batch(const SweepJob *jobs, int njobs, cudaStream_t st, int *launches);
+// the job's partial sums into its I row (when its l range was split)
+cudaError_t finish_sweep_job(const SweepJob &job, cudaStream_t st);
+}  // namespace kbe
+// a step of a handle in segments that stop at each collision sweep (kbe_api.cu;
+// used by kbe_batch.cu): segment 0 .. step_segment_count - 1; a segment with
+// *has_job hands back its sweep, which must run before the next segment
+struct kbe_handle;
+int step_segment_count(const kbe_handle *h);
+kbe_status step_segment(kbe_handle *h, int seg, kbe::SweepJob *job, bool *has_job);
+kbe_status step_segment_check(kbe_handle *h);
+namespace kbe {
 // cap: the rows H holds (the F16X2 layout depends on it; <= 0: n + 1)
 cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const void *H,
                          const double2 *Sig, double2 *I, void *work, cudaStream_t st,
@@ -423,7 +448,7 @@ cudaError_t launch_update_row(const Mesh &m, int n, double dt, double theta, con
                               const double2 *Iprev, const double2 *Icur, double2 *out,
                               cudaStream_t st, const int *skip = nullptr,
                               unsigned long long *maxdiff = nullptr, void *packed = nullptr, int prec = 0,
-                              int cap = 0);
+                              int cap = 0, cudaStream_t st_diag = nullptr, bool diag_apart = false);
 // Algorithm 1's convergence test after a corrector pass (one thread): unless
 // skip is set, count the pass in *iters, set skip when *maxdiff <= tol, and
 // clear *maxdiff for the next pass.
@@ -492,6 +517,15 @@ kbe_status step_prepare(kbe_handle *h);
 kbe_status step_record(kbe_handle *h, int nsteps);
 void step_advance(kbe_handle *h, int nsteps);
 void step_key(const kbe_handle *h, int *ring, unsigned *gen);
+// the host-side step state (row, I-ring order), saved before a capture that
+// records steps and put back after it
+struct StepMark {
+  int n;
+  void *Ip, *Ic;
+};
+StepMark step_mark(const kbe_handle *h);
+void step_rewind(kbe_handle *h, const StepMark &mk);
 cudaStream_t handle_stream(const kbe_handle *h);
+int handle_precision(const kbe_handle *h);
 
 }  // namespace kbe

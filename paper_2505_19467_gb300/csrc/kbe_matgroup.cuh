@@ -44,11 +44,55 @@ struct MatGroup {
   }
 };
 
+// 1/m for the series coefficients tau / m (m = 0 .. 23; entry 0 unused): a
+// multiplication by a tabulated reciprocal in place of an FP64 division,
+// which costs about ten FP64-pipe instructions, per term and element
+static __constant__ double kSeriesInv[24] = {
+    0.0,        1.0,        1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,  1.0 / 6,  1.0 / 7,
+    1.0 / 8,    1.0 / 9,    1.0 / 10, 1.0 / 11, 1.0 / 12, 1.0 / 13, 1.0 / 14, 1.0 / 15,
+    1.0 / 16,   1.0 / 17,   1.0 / 18, 1.0 / 19, 1.0 / 20, 1.0 / 21, 1.0 / 22, 1.0 / 23};
+
+// The series lengths: with nu = tau ||h|| <= 1/4 (rowsum norm, submultiplicative)
+// the m-th term of U_tau (and of V_tau / tau) is bounded by nu^m / m! of the
+// leading term, the m-th term of X_tau by (2 nu)^m / (m + 1)! of tau ||S||. Each
+// series stops before its first term whose bound is below 2^-60 (1/128 of the
+// FP64 unit roundoff; the terms after it decay faster still): at the worst
+// nu = 1/4 that is 13 and 15 terms, at nu ~ 0.12 (dt = 0.02, ||h|| ~ 6) 11 and
+// 12. At most 14 and 18 terms.
+struct SeriesPlan {
+  int s;      // doublings: tau = dt / 2^s
+  int mexp;   // terms m = 1 .. mexp of U_tau (and V_tau)
+  int mx;     // terms m = 1 .. mx of X_tau
+};
+
+__device__ __forceinline__ SeriesPlan series_lengths(double nu) {
+  const double exp_tail = 0x1p-60, x_tail = 0x1p-60;
+  SeriesPlan p{0, 14, 18};
+  double t = 1.0;                    // nu^m / m!
+  for (int m = 1; m <= 14; ++m) {
+    t *= nu * kSeriesInv[m];
+    if (t <= exp_tail) {             // term m is already below the bound: m - 1 terms suffice
+      p.mexp = m > 1 ? m - 1 : 1;
+      break;
+    }
+  }
+  double q = 1.0;                    // (2 nu)^m / m!
+  for (int m = 1; m <= 18; ++m) {
+    q *= 2.0 * nu * kSeriesInv[m];
+    if (q * kSeriesInv[m + 1] <= x_tail) {   // (2 nu)^m / (m + 1)!
+      p.mx = m > 1 ? m - 1 : 1;
+      break;
+    }
+  }
+  return p;
+}
+
 // number of doublings s with (dt / 2^s) * max_k ||h_k||_rowsum <= 1/4, for
-// all k-points of the CTA (uniform across the CTA); h in shared memory
+// all k-points of the CTA (uniform across the CTA), and the series lengths
+// for tau = dt / 2^s; h in shared memory
 template <int NB>
-__device__ int doublings(const MatGroup<NB> &g, const double2 *h, int kpc, int nvalid, double dt,
-                         double *red) {
+__device__ SeriesPlan series_plan(const MatGroup<NB> &g, const double2 *h, int kpc, int nvalid, double dt,
+                                  double *red) {
   if (g.b == 0) {
     double r = 0.0;
     for (int c = 0; c < NB; ++c) {
@@ -58,7 +102,7 @@ __device__ int doublings(const MatGroup<NB> &g, const double2 *h, int kpc, int n
     red[g.kk * NB + g.a] = (g.kk < nvalid) ? r : 0.0;
   }
   __syncthreads();
-  __shared__ int s_sh;
+  __shared__ SeriesPlan plan_sh;
   if (threadIdx.x == 0) {
     double nu = 0.0;
     for (int i = 0; i < kpc * NB; ++i) nu = fmax(nu, red[i]);
@@ -68,30 +112,34 @@ __device__ int doublings(const MatGroup<NB> &g, const double2 *h, int kpc, int n
       nu *= 0.5;
       ++sc;
     }
-    s_sh = sc;
+    SeriesPlan p = series_lengths(nu);
+    p.s = sc;
+    plan_sh = p;
   }
   __syncthreads();
-  return s_sh;
+  return plan_sh;
 }
 
 // U_dt and V_dt of h (shared memory), element (a, b) returned in u, v;
-// P, Q, W are shared scratch of KPC * N_b^2 each.
+// P, Q, W are shared scratch of KPC * N_b^2 each; mt terms of the series
+// (series_plan).
 template <int NB>
 __device__ void exp_and_phi(const MatGroup<NB> &g, const double2 *h, double tau, int s, double2 *P,
-                            double2 *Q, double2 *W, double2 &u, double2 &v) {
+                            double2 *Q, double2 *W, double2 &u, double2 &v, int mt = 14) {
   const int o = g.kk * g.E + g.e;
   const double2 one = make_double2(g.a == g.b ? 1.0 : 0.0, 0.0);
   P[o] = one;
   u = one;
   v = make_double2(0.0, -tau * one.x);   // -i tau P_0 / 1
   __syncthreads();
-  for (int m = 1; m <= 14; ++m) {
+  for (int m = 1; m <= mt; ++m) {
+    const double cm = tau * kSeriesInv[m], cv = tau * kSeriesInv[m + 1];
     double2 t = g.mm(P, h);
-    t = make_double2(tau * t.y / m, -tau * t.x / m);   // (-i tau / m) (P h)
+    t = make_double2(cm * t.y, -cm * t.x);   // (-i tau / m) (P h)
     __syncthreads();
     P[o] = t;
     u = c_add(u, t);
-    v = c_add(v, make_double2(tau * t.y / (m + 1), -tau * t.x / (m + 1)));
+    v = c_add(v, make_double2(cv * t.y, -cv * t.x));
     __syncthreads();
   }
   for (int r = 0; r < s; ++r) {   // V <- (U + 1) V, U <- U U

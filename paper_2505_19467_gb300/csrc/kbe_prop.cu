@@ -16,8 +16,9 @@
 //   U_tau = sum_m (-i tau h)^m / m!,          U_2tau = U_tau^2,
 //   V_tau = -i tau sum_m (-i tau h)^m/(m+1)!,  V_2tau = (U_tau + 1) V_tau,
 //   X_tau = tau sum_m (-i tau)^m ad_h^m(S) / (m+1)!, X_2tau = X_tau + U_tau X_tau U_tau^+,
-// with ad_h(S) = h S - S h; 14 and 18 terms reach the FP64 rounding level
-// (0.25^14/14! and 0.5^18/18! < 1e-19). The trace of X is dt Tr S exactly in
+// with ad_h(S) = h S - S h; each series stops before its first term whose
+// bound (nu^m / m!, (2 nu)^m / (m+1)!, nu = tau ||h||) is below 2^-60: at most
+// 13 and 15 terms at nu = 1/4, fewer at smaller nu. The trace of X is dt Tr S exactly in
 // exact arithmetic, so the particle number is conserved. A Jacobi
 // eigen-solver is used only for the Fermi function of the initial state.
 #include "kbe_internal.cuh"
@@ -135,20 +136,32 @@ __global__ void __launch_bounds__(256) build_props_kernel(Mesh m, HopTable hop, 
   const int nvalid = min(kpc, m.nk - (int)blockIdx.x * kpc);
   const int o = g.kk * G::E + g.e;
   double2 hv = make_double2(0.0, 0.0);
-  if (active) {
-    if (hin) {
-      hv = hin[(size_t)g.e * m.nk + k];
-    } else {
-      // h0_ab(k - A d) = sum_r t_ab(R_r) exp(i (k - A d).R_r), this thread's element
-      const int k0 = k / m.L1, k1 = k - (k / m.L1) * m.L1;
-      for (int r = 0; r < hop.nhop; ++r) {
+  if (!hin) {
+    // h0_ab(k - A d) = sum_r t_ab(R_r) exp(i (k - A d).R_r), this thread's element;
+    // the phases of a k-point are computed once, N_b^2 at a time by its threads
+    double2 *ph = sh[1] + g.kk * G::E;   // sh[1] is free until the series
+    const int k0 = k / m.L1, k1 = k - (k / m.L1) * m.L1;
+    for (int r0 = 0; r0 < hop.nhop; r0 += G::E) {
+      const int r = r0 + g.e;
+      if (active && r < hop.nhop) {
         const int R0 = hop.R[2 * r], R1 = hop.R[2 * r + 1];
         const int m0 = ((k0 * R0) % m.L0 + m.L0) % m.L0, m1 = ((k1 * R1) % m.L1 + m.L1) % m.L1;
         const double th = 2.0 * M_PI * ((double)m0 / m.L0 + (double)m1 / m.L1) - p.A * (hop.d0 * R0 + hop.d1 * R1);
         double sn, cs;
         sincos(th, &sn, &cs);
-        hv = c_fma(hop.T[(size_t)r * G::E + g.e], make_double2(cs, sn), hv);
+        ph[g.e] = make_double2(cs, sn);
       }
+      __syncthreads();
+      if (active)
+        for (int q = 0; q < G::E && r0 + q < hop.nhop; ++q)
+          hv = c_fma(hop.T[(size_t)(r0 + q) * G::E + g.e], ph[q], hv);
+      __syncthreads();
+    }
+  }
+  if (active) {
+    if (hin) {
+      hv = hin[(size_t)g.e * m.nk + k];
+    } else {
       if (p.hf) {   // S_ab = U (delta_ab sum_c v_ac rho_cc - v_ab rho_ab), rho = ca rho_a + cb rho_b
         const double2 rab = c_add(c_scale(p.ca, p.rho_a[g.e]), c_scale(p.cb, p.rho_b[g.e]));
         double2 x = c_scale(-p.v[g.e], rab);
@@ -165,10 +178,10 @@ __global__ void __launch_bounds__(256) build_props_kernel(Mesh m, HopTable hop, 
   }
   sh[0][o] = hv;
   __syncthreads();
-  const int s = doublings<NB>(g, sh[0], kpc, nvalid, dt, red);
-  const double tau = ldexp(dt, -s);
+  const SeriesPlan sp = series_plan<NB>(g, sh[0], kpc, nvalid, dt, red);
+  const double tau = ldexp(dt, -sp.s);
   double2 u, v;
-  exp_and_phi<NB>(g, sh[0], tau, s, sh[1], sh[2], sh[3], u, v);
+  exp_and_phi<NB>(g, sh[0], tau, sp.s, sh[1], sh[2], sh[3], u, v, sp.mexp);
   if (active) {
     const size_t go = (size_t)g.e * m.nk + k;
     if (hout) hout[go] = hv;
@@ -215,20 +228,22 @@ __global__ void __launch_bounds__(256) update_diag_kernel(int n, int nk, double 
   H[o] = hv;
   Qs[o] = sv;
   __syncthreads();
-  const int s = doublings<NB>(g, H, kpc, nvalid, dt, red);
+  const SeriesPlan sp = series_plan<NB>(g, H, kpc, nvalid, dt, red);
+  const int s = sp.s;
   const double tau = ldexp(dt, -s);
   // X_tau = tau sum_m Q_m / (m+1), Q_m = (-i tau / m) [h, Q_{m-1}], Q_0 = Sbar
   double2 x = c_scale(tau, sv);
-  for (int m = 1; m <= 18; ++m) {
+  for (int m = 1; m <= sp.mx; ++m) {
+    const double cm = tau * kSeriesInv[m], cx = tau * kSeriesInv[m + 1];
     const double2 c = c_sub(g.mm(H, Qs), g.mm(Qs, H));
-    const double2 q = make_double2(tau * c.y / m, -tau * c.x / m);
+    const double2 q = make_double2(cm * c.y, -cm * c.x);
     __syncthreads();
     Qs[o] = q;
-    x = c_add(x, c_scale(tau / (m + 1), q));
+    x = c_add(x, c_scale(cx, q));
     __syncthreads();
   }
   double2 u, v;
-  exp_and_phi<NB>(g, H, tau, 0, P, T, Wk, u, v);   // U_tau
+  exp_and_phi<NB>(g, H, tau, 0, P, T, Wk, u, v, sp.mexp);   // U_tau
   (void)v;
   for (int r = 0; r < s; ++r) {   // X <- X + U X U^+, U <- U U
     P[o] = u;
@@ -475,23 +490,25 @@ cudaError_t launch_update_row(const Mesh &m, int n, double dt, double theta, con
                               const double2 *U, const double2 *V, const double2 *Gprev,
                               const double2 *Iprev, const double2 *Icur, double2 *out,
                               cudaStream_t st, const int *skip, unsigned long long *maxdiff, void *packed,
-                              int prec, int cap) {
+                              int prec, int cap, cudaStream_t st_diag, bool diag_apart) {
+  // diag_apart: the time diagonal on st_diag (independent of the rows j < n;
+  // the caller orders st_diag after st's prior work and joins it back)
+  if (!diag_apart) st_diag = st;
   const size_t blk = (size_t)m.nb * m.nb * m.nk;
   const size_t total = (size_t)n * blk;
   const int threads = 256;
   const unsigned blocks = (unsigned)((total + threads - 1) / threads);
   const double2 *ic = (theta != 0.0) ? Icur : Iprev;
-  if (total > 0) {
-    KBE_NB_SWITCH(m.nb, (update_rows_kernel<NB><<<blocks, threads, 0, st>>>(n, m.nk, theta, U, V, Gprev, Iprev, ic,
-                                                                             out, skip, maxdiff, packed, prec,
-                                                                             cap)));
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
+  // the diagonal first: a long latency-bound chain on few SMs, which the rows
+  // (FP64-pipe bound, every SM) then overlap
   KBE_NB_SWITCH(m.nb, (update_diag_kernel<NB><<<matgroup_blocks<NB>(m.nk), matgroup_threads<NB>(m.nk),
-                                                 matgroup_smem<NB>(m.nk, 5), st>>>(
+                                                 matgroup_smem<NB>(m.nk, 5), st_diag>>>(
                           n, m.nk, dt, theta, h, Gprev, Iprev, ic, out, matgroup_kpc<NB>(m.nk), skip,
                           maxdiff, packed, prec, cap)));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || total == 0) return e;
+  KBE_NB_SWITCH(m.nb, (update_rows_kernel<NB><<<blocks, threads, 0, st>>>(n, m.nk, theta, U, V, Gprev, Iprev, ic,
+                                                                           out, skip, maxdiff, packed, prec, cap)));
   return cudaGetLastError();
 }
 

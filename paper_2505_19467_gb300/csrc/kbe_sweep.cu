@@ -396,20 +396,21 @@ __device__ __forceinline__ void sweep_wnode(const typename P::S *__restrict__ c1
 // [z][j][x][a][b][k]. The l range [l0, l1) is walked as three branch-free
 // runs: interior nodes 0 < l < j (adjoint blocks), nodes above l > j (stored
 // blocks), then the two end nodes l = 0 and l = j.
+// one CTA's work, block (bx, by, bz) of `threads` threads (the batched
+// persistent kernel calls it for blocks of many systems)
 template <class P, int NB, int QUAD>
-__global__ void __launch_bounds__(256, P::kMinBlocks) sweep_kernel(const typename P::S *__restrict__ H,
-                                                    const typename P::S *__restrict__ Cf,
-                                                    double2 *__restrict__ out, int n, int nk,
-                                                    int lchunk, const int *__restrict__ skip) {
-  if (skip && *skip) return;
+__device__ __forceinline__ void sweep_block(const typename P::S *__restrict__ H, const typename P::S *__restrict__ Cf,
+                                            double2 *__restrict__ out, int n, int nk, int lchunk, int bx, int by,
+                                            int bz, int threads) {
   using S = typename P::S;
-  const int j = blockIdx.y;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = by;
+  if ((int)threadIdx.x >= threads) return;
+  const int idx = bx * threads + threadIdx.x;
   if (idx >= NB * NB * nk) return;
   const int k = idx % nk;
   const int ab = idx / nk;
   const int a = ab / NB, b = ab - (ab / NB) * NB;
-  const int l0 = blockIdx.z * lchunk;
+  const int l0 = bz * lchunk;
   const int l1 = min(n + 1, l0 + lchunk);
   const size_t blk = (size_t)NB * NB * nk;
   const S *cbase = Cf + (size_t)a * NB * nk + k;   // C1(l)_{a, .} at cbase + 3 l blk
@@ -467,8 +468,17 @@ __global__ void __launch_bounds__(256, P::kMinBlocks) sweep_kernel(const typenam
   P::end(accY);
   // outputs in complex numbers: nk, blk and k above count stored elements S
   const size_t blkc = blk * P::V;
-  double2 *o = out + ((size_t)blockIdx.z * (n + 1) + j) * 2 * blkc + (size_t)ab * nk * P::V + (size_t)k * P::V;
+  double2 *o = out + ((size_t)bz * (n + 1) + j) * 2 * blkc + (size_t)ab * nk * P::V + (size_t)k * P::V;
   P::store(o, blkc, accX, accY);
+}
+
+template <class P, int NB, int QUAD>
+__global__ void __launch_bounds__(256, P::kMinBlocks) sweep_kernel(const typename P::S *__restrict__ H,
+                                                    const typename P::S *__restrict__ Cf,
+                                                    double2 *__restrict__ out, int n, int nk,
+                                                    int lchunk, const int *__restrict__ skip) {
+  if (skip && *skip) return;
+  sweep_block<P, NB, QUAD>(H, Cf, out, n, nk, lchunk, blockIdx.x, blockIdx.y, blockIdx.z, blockDim.x);
 }
 
 // ---------------------------------------------- C64, register-blocked ----
@@ -672,19 +682,16 @@ __host__ __device__ constexpr int f64m_minb(int NB) { return NB >= 6 ? 2 : 4; }
 // thread (kk, b) with b fastest (the N_b lanes of one k read each coefficient
 // together); out as for sweep_kernel
 template <int NB, int QUAD>
-__global__ void __launch_bounds__(kF64mThreads, f64m_minb(NB)) sweep_f64m_kernel(const double2 *__restrict__ H,
-                                                                      const double2 *__restrict__ Cf,
-                                                                      const double *__restrict__ Cs,
-                                                                      double2 *__restrict__ out, int n, int nk,
-                                                                      int lchunk, const int *__restrict__ skip) {
-  if (skip && *skip) return;
+__device__ __forceinline__ void f64m_block(const double2 *__restrict__ H, const double2 *__restrict__ Cf,
+                                           const double *__restrict__ Cs, double2 *__restrict__ out, int n, int nk,
+                                           int lchunk, int bx, int by, int bz) {
   constexpr int KT = kF64mThreads / NB;
   if ((int)threadIdx.x >= KT * NB) return;
   const int b = threadIdx.x % NB, kk = threadIdx.x / NB;
-  const int k = blockIdx.x * KT + kk;
+  const int k = bx * KT + kk;
   if (k >= nk) return;
-  const int j = blockIdx.y;
-  const int l0 = blockIdx.z * lchunk;
+  const int j = by;
+  const int l0 = bz * lchunk;
   const int l1 = min(n + 1, l0 + lchunk);
   const size_t blk = (size_t)NB * NB * nk;
   const double2 *cbase = Cf + k;
@@ -715,13 +722,23 @@ __global__ void __launch_bounds__(kF64mThreads, f64m_minb(NB)) sweep_f64m_kernel
                                 blk, nk, b, f, X, Y);
     }
   }
-  double2 *o = out + ((size_t)blockIdx.z * (n + 1) + j) * 2 * blk + k;
+  double2 *o = out + ((size_t)bz * (n + 1) + j) * 2 * blk + k;
 #pragma unroll
   for (int a = 0; a < NB; ++a) {
     const double2 x = X.value(a), y = Y.value(a);
     o[(size_t)(a * NB + b) * nk] = x;
     o[blk + (size_t)(a * NB + b) * nk] = c_add(x, y);
   }
+}
+
+template <int NB, int QUAD>
+__global__ void __launch_bounds__(kF64mThreads, f64m_minb(NB)) sweep_f64m_kernel(const double2 *__restrict__ H,
+                                                                      const double2 *__restrict__ Cf,
+                                                                      const double *__restrict__ Cs,
+                                                                      double2 *__restrict__ out, int n, int nk,
+                                                                      int lchunk, const int *__restrict__ skip) {
+  if (skip && *skip) return;
+  f64m_block<NB, QUAD>(H, Cf, Cs, out, n, nk, lchunk, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // I = sum over the z partial rows (FP64)
@@ -1447,6 +1464,81 @@ cudaError_t sweep_prec(const Mesh &m, int n, int prec, const void *H, const void
   return sweep_nb<ArithC64, NB>(m, n, H, Cf, I, part, st, skip, quad);
 }
 
+// ---- the FP64 sweeps of many systems in one persistent launch (kbe_batch) --
+// Every system contributes the blocks of its own sweep shape (k tiles x output
+// columns x l-splits, the split chosen per shape by the autotuner); a CTA
+// walks the concatenated block list with a grid stride and runs each block
+// with its system's operands. One launch per (N_b, quadrature, kernel form).
+constexpr int kMaxBatchJobs = 48;
+struct BatchTable {
+  SweepJob job[kMaxBatchJobs];
+  long first[kMaxBatchJobs + 1];   // first[q]: the first block of job q; first[njobs]: all blocks
+  int njobs;
+};
+
+__device__ __forceinline__ int batch_job_of(const BatchTable &t, long w) {
+  int q = 0;
+  while (q + 1 < t.njobs && w >= t.first[q + 1]) ++q;
+  return q;
+}
+
+template <int NB, int QUAD>
+__global__ void __launch_bounds__(kF64mThreads, f64m_minb(NB)) batch_f64m_kernel(const __grid_constant__ BatchTable t) {
+  for (long w = blockIdx.x; w < t.first[t.njobs]; w += gridDim.x) {
+    const SweepJob &jb = t.job[batch_job_of(t, w)];
+    if (jb.skip && *jb.skip) continue;   // a converged corrector pass of that system
+    const long loc = w - t.first[&jb - t.job];
+    const int bx = (int)(loc % jb.tx);
+    const long r = loc / jb.tx;
+    f64m_block<NB, QUAD>(jb.H, jb.Cf, jb.Cs, jb.out, jb.n, jb.nk, jb.lchunk, bx, (int)(r % (jb.n + 1)),
+                         (int)(r / (jb.n + 1)));
+  }
+}
+
+template <int NB, int QUAD>
+__global__ void __launch_bounds__(256, ArithF64::kMinBlocks) batch_plain_kernel(const __grid_constant__ BatchTable t) {
+  for (long w = blockIdx.x; w < t.first[t.njobs]; w += gridDim.x) {
+    const SweepJob &jb = t.job[batch_job_of(t, w)];
+    if (jb.skip && *jb.skip) continue;
+    const long loc = w - t.first[&jb - t.job];
+    const int bx = (int)(loc % jb.tx);
+    const long r = loc / jb.tx;
+    sweep_block<ArithF64, NB, QUAD>(jb.H, jb.Cf, jb.out, jb.n, jb.nk, jb.lchunk, bx, (int)(r % (jb.n + 1)),
+                                    (int)(r / (jb.n + 1)), jb.threads);
+  }
+}
+
+template <int NB, int QUAD>
+cudaError_t batch_launch_nb(const BatchTable &t, bool f64m, cudaStream_t st) {
+  const long total = t.first[t.njobs];
+  if (total == 0) return cudaSuccess;
+  if (f64m) {
+    if constexpr (NB <= 8) {
+      const long slots = (long)device_sms() * f64m_minb(NB);
+      batch_f64m_kernel<NB, QUAD><<<(unsigned)(total < slots ? total : slots), kF64mThreads, 0, st>>>(t);
+    }
+  } else {
+    const long slots = (long)device_sms() * ArithF64::kMinBlocks;
+    batch_plain_kernel<NB, QUAD><<<(unsigned)(total < slots ? total : slots), 256, 0, st>>>(t);
+  }
+  return cudaGetLastError();
+}
+
+template <int QUAD>
+cudaError_t batch_launch(const BatchTable &t, int nb, bool f64m, cudaStream_t st) {
+  switch (nb) {
+    case 1: return batch_launch_nb<1, QUAD>(t, f64m, st);
+    case 2: return batch_launch_nb<2, QUAD>(t, f64m, st);
+    case 3: return batch_launch_nb<3, QUAD>(t, f64m, st);
+    case 4: return batch_launch_nb<4, QUAD>(t, f64m, st);
+    case 6: return batch_launch_nb<6, QUAD>(t, f64m, st);
+    case 8: return batch_launch_nb<8, QUAD>(t, f64m, st);
+    case 12: return batch_launch_nb<12, QUAD>(t, f64m, st);
+    case 16: return batch_launch_nb<16, QUAD>(t, f64m, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace
 
 bool use_f64m(const Mesh &m, int prec) { return prec == KBE_PREC_FP64 && m.nb <= 8; }
@@ -1667,6 +1759,75 @@ cudaError_t launch_row_out(int prec, const double2 *fp64, const void *packed, si
   if (prec == KBE_PREC_F16X2 && !fp64 && (row < 0 || cap <= row)) return cudaErrorInvalidValue;
   row_out_kernel<<<grid_for(count), 256, 0, st>>>(prec, fp64, packed, nblk, m.nb, m.nk, which, out, row, cap);
   return cudaGetLastError();
+}
+
+cudaError_t prepare_sweep_job(const Mesh &m, int n, double dt, const void *H, const double2 *Sig, double2 *I,
+                              void *work, cudaStream_t st, const int *skip, int quad, SweepJob *job) {
+  if (!sweep_supported(m.nb)) return cudaErrorInvalidValue;
+  const size_t blk = (size_t)m.nb * m.nb * m.nk, total = (size_t)(n + 1) * blk;
+  double *Cs = (double *)((double2 *)work + (size_t)(n + 1) * 3 * blk);
+  coef_kernel<<<grid_for(total), 256, 0, st>>>(KBE_PREC_FP64, Sig, work, n, m.nk, m.nb * m.nb, dt, skip, quad, Cs,
+                                              nullptr);   // as launch_sweep
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  SweepJob &jb = *job;
+  jb.H = (const double2 *)H;
+  jb.Cf = (const double2 *)work;
+  jb.Cs = Cs;
+  jb.I = I;
+  jb.skip = skip;
+  jb.n = n;
+  jb.nk = m.nk;
+  jb.nb = m.nb;
+  jb.quad = quad;
+  jb.f64m = use_f64m(m, KBE_PREC_FP64) ? 1 : 0;
+  const int target = tuned_target(KBE_PREC_FP64, quad, m, n, kTargetPerSm);
+  if (jb.f64m) {   // as sweep_f64m
+    const int KT = kF64mThreads / m.nb;
+    jb.tx = (m.nk + KT - 1) / KT;
+    jb.threads = kF64mThreads;
+    const long nz = split_count((long)(n + 1) * jb.tx, n, target);
+    jb.lchunk = (int)((n + 1 + nz - 1) / nz);
+  } else {         // as sweep_nb<ArithF64>
+    const SweepShape sh = sweep_shape(m, n, 1, target);
+    jb.tx = (int)sh.grid.x;
+    jb.threads = sh.threads;
+    jb.lchunk = sh.lchunk;
+  }
+  jb.nz = (n + 1 + jb.lchunk - 1) / jb.lchunk;
+  jb.out = jb.nz > 1 ? (double2 *)((char *)work + coef_region_bytes(m, n, KBE_PREC_FP64)) : I;
+  return cudaSuccess;
+}
+
+cudaError_t finish_sweep_job(const SweepJob &job, cudaStream_t st) {
+  if (job.nz <= 1) return cudaSuccess;
+  const size_t count = (size_t)(job.n + 1) * 2 * job.nb * job.nb * job.nk;
+  reduce_partials_kernel<<<grid_for(count), 256, 0, st>>>(job.out, job.I, count, job.nz, job.skip);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_batch(const SweepJob *jobs, int njobs, cudaStream_t st, int *launches) {
+  std::vector<bool> done((size_t)njobs, false);
+  if (launches) *launches = 0;
+  for (int q0 = 0; q0 < njobs; ++q0) {   // one launch per (N_b, quadrature, form), at most kMaxBatchJobs jobs
+    if (done[q0]) continue;
+    BatchTable t{};
+    t.njobs = 0;
+    t.first[0] = 0;
+    for (int q = q0; q < njobs && t.njobs < kMaxBatchJobs; ++q) {
+      const SweepJob &a = jobs[q0], &b = jobs[q];
+      if (done[q] || b.nb != a.nb || b.quad != a.quad || b.f64m != a.f64m) continue;
+      done[q] = true;
+      t.job[t.njobs] = b;
+      t.first[t.njobs + 1] = t.first[t.njobs] + (long)b.tx * (b.n + 1) * b.nz;
+      ++t.njobs;
+    }
+    cudaError_t e = jobs[q0].quad == kQuadGregory ? batch_launch<kQuadGregory>(t, jobs[q0].nb, jobs[q0].f64m != 0, st)
+                                                  : batch_launch<kQuadTrapezoid>(t, jobs[q0].nb, jobs[q0].f64m != 0, st);
+    if (e != cudaSuccess) return e;
+    if (launches) ++*launches;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const void *H,

@@ -222,11 +222,13 @@ def alu_peaks(kbe):
 
 
 def roofline(prof, precision, t_dev, peaks):
-    """The sweep's roofline. achieved = the method's algorithmic count per
-    launch (24 n^2 N_b^3 n_k flops, the G^> form of Eq. 6; or the triangle read
-    once plus the Sigma and I rows, in bytes) over the summed sweep event time.
-    The kernels execute 2/3 of the flops (the I^<, I^> - I^< form), reported
-    as achieved_executed / frac_executed."""
+    """The sweep's roofline over the summed sweep event time. HBM-bound forms
+    (C64, split-FP16): achieved = the triangle read once plus the Sigma and I
+    rows, in bytes. ALU-bound forms (FP64, DF64): achieved = the flops the
+    kernel's algorithm performs (the I^<, I^> - I^< form: 2/3 of the method's
+    24 n^2 N_b^3 n_k count; the FP64 kernel's three-multiplication products:
+    FP64-pipe operations as flops), so frac is a pipe utilisation; the
+    method's count is reported beside it (achieved_method_count)."""
     sweep_s = prof["sweep_ms"] / 1e3
     nl = max(1, prof["sweep_launches"])
     alg_bytes = prof["sweep_bytes"] / nl
@@ -260,8 +262,8 @@ def roofline(prof, precision, t_dev, peaks):
     else:
         peak = peaks["fp64"]
         unit, src = "GFLOP/s FP64", "measured FP64 FMA throughput (kbe_measure_fma_peaks)"
-    return {"bound": "alu", "achieved": flops, "peak": peak, "unit": unit, "frac": flops / peak,
-            "peak_source": src, "achieved_executed": executed, "frac_executed": executed / peak, **common}
+    return {"bound": "alu", "achieved": executed, "peak": peak, "unit": unit, "frac": executed / peak,
+            "peak_source": src, "achieved_method_count": flops, "frac_method_count": flops / peak, **common}
 
 
 def run_ours(args, rank, world, local):

@@ -474,7 +474,10 @@ kbe_status kbe_op_propagators(const kbe_mesh *m, double dt, const void *h_dev, v
  *   Sbar = (1-theta)(I^<_{n-1}(n-1) + h.c.) + theta (I^<_n(n) + h.c.),
  *   G^>(n, n) = G^<(n, n) - i.
  * Gprev_dev: row n-1 (n blocks); Iprev_dev: n blocks; Icur_dev: n+1 blocks
- * (read only if theta != 0); out_dev: row n (n+1 blocks). n >= 1. */
+ * (read only if theta != 0); out_dev: row n (n+1 blocks). n >= 1. U and V
+ * must be h's propagators as kbe_op_propagators returns them: where dt ||h||
+ * <= 1/4 (row-sum norm, the largest over the k-points the time diagonal
+ * groups together) the diagonal takes U as given instead of forming it. */
 kbe_status kbe_op_update_row(const kbe_mesh *m, int n, double dt, double theta, const void *h_dev,
                              const void *U_dev, const void *V_dev, const void *Gprev_dev,
                              const void *Iprev_dev, const void *Icur_dev, void *out_dev,

@@ -27,10 +27,6 @@ struct kbe_handle {
   kbe_config cfg{};
   Mesh mesh{};
   cudaStream_t stream = nullptr;
-  // a second stream for work of a step that does not depend on the main
-  // chain: forked from and joined back to `stream` within one stage
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int device = 0;
   size_t blk = 0;   // complex numbers in one (component) block: nb*nb*nk
   int nb2 = 0;
@@ -61,6 +57,8 @@ struct kbe_handle {
   double *obs = nullptr;       // [(nt_max+1)][6]
   double *nkb = nullptr;       // [(nt_max+1)][nk][nb]
   int *status = nullptr;
+  double *obs_part = nullptr;            // per-CTA partial sums of the observables kernel
+  unsigned *obs_ticket = nullptr;        // its last-CTA counter (kept at 0 between launches)
   int *d_skip = nullptr;                 // corrector passes skipped once converged (corr_tol > 0)
   unsigned long long *d_maxdiff = nullptr;   // max |G^< change| of the last corrector pass (bits)
   int *d_iters = nullptr;                // corrector passes run at each step [(nt_max+1)]
@@ -156,7 +154,7 @@ void drop_graphs(kbe_handle *h) {
 void free_all(kbe_handle *h) {
   drop_graphs(h);
   void *ptrs[] = {h->H, h->Wrow[0], h->Wrow[1], h->coef, h->Ip, h->Ic, h->Sig, h->work, h->U, h->V,
-                  h->hk, h->rho, h->obs, h->nkb, h->status, h->d_hopR, h->d_hopT, h->d_U,
+                  h->hk, h->rho, h->obs, h->nkb, h->status, h->obs_part, h->obs_ticket, h->d_hopR, h->d_hopT, h->d_U,
                   h->d_dipM, h->adj, h->d_skip, h->d_maxdiff, h->d_iters};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -170,34 +168,8 @@ void free_all(kbe_handle *h) {
     cudaEventDestroy(pe.b);
   }
   h->bev.clear();
-  if (h->side) cudaStreamDestroy(h->side);
-  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
-  if (h->ev_join) cudaEventDestroy(h->ev_join);
-  h->side = nullptr;
-  h->ev_fork = h->ev_join = nullptr;
 }
 
-// Work of a step stage that does not depend on the stage's main chain runs on
-// the side stream (KBE_SIDE_STREAM 1) or in order on the main stream (0).
-#ifndef KBE_SIDE_STREAM
-#define KBE_SIDE_STREAM 1
-#endif
-
-cudaStream_t side_of(const kbe_handle *h) { return KBE_SIDE_STREAM ? h->side : h->stream; }
-
-// the side stream waits for the main stream's work so far
-cudaError_t side_fork(kbe_handle *h) {
-  if (!KBE_SIDE_STREAM) return cudaSuccess;
-  cudaError_t e = cudaEventRecord(h->ev_fork, h->stream);
-  return e == cudaSuccess ? cudaStreamWaitEvent(h->side, h->ev_fork, 0) : e;
-}
-
-// the main stream waits for the side stream's work so far
-cudaError_t side_join(kbe_handle *h) {
-  if (!KBE_SIDE_STREAM) return cudaSuccess;
-  cudaError_t e = cudaEventRecord(h->ev_join, h->side);
-  return e == cudaSuccess ? cudaStreamWaitEvent(h->stream, h->ev_join, 0) : e;
-}
 
 // collision sweep flops of one launch at row n: the method's count with the
 // G^> form of Eq. 6 (3 N_b^3 complex multiply-adds per stored block, ~24 n^2
@@ -280,7 +252,7 @@ kbe_status evaluate_row(kbe_handle *h, int n, const int *skip = nullptr) {
 
 kbe_status build_props(kbe_handle *h, int n, const double2 *ra, const double2 *rb, double ca, double cb,
                        double2 *hk = nullptr, double2 *Uk = nullptr, double2 *Vk = nullptr,
-                       const int *skip = nullptr, bool on_side = false) {
+                       const int *skip = nullptr) {
   kbe::PropParams p{};
   p.A = A_at(h, n - 1);
   p.rho_a = ra;
@@ -294,7 +266,7 @@ kbe_status build_props(kbe_handle *h, int n, const double2 *ra, const double2 *r
   p.dipM = h->dipE.empty() ? nullptr : h->d_dipM;
   p.dipE = (n - 1 < (int)h->dipE.size()) ? h->dipE[(size_t)(n - 1)] : 0.0;
   cudaError_t e = kbe::launch_build_props(h->mesh, hop_table(h), p, h->cfg.dt, nullptr, hk ? hk : h->hk,
-                                          Uk ? Uk : h->U, Vk ? Vk : h->V, on_side ? side_of(h) : h->stream, skip);
+                                          Uk ? Uk : h->U, Vk ? Vk : h->V, h->stream, skip);
   if (e != cudaSuccess) return cuda_fail(h, e, "build_props");
   if (h->prof) h->stats.launches += 1;
   return KBE_OK;
@@ -306,20 +278,16 @@ kbe_status update(kbe_handle *h, int n, double theta, const int *skip = nullptr,
   double2 *row = frow(h, n);
   // the update kernels also store row n into the history triangle ("publish")
   char *hist = (char *)h->H + kbe::history_row_offset(h->mesh, h->cfg.precision, n);
-  // the time diagonal on the side stream, beside the rows j < n
-  cudaError_t e = side_fork(h);
-  if (e == cudaSuccess)
-    e = kbe::launch_update_row(h->mesh, n, h->cfg.dt, theta, h->hk, h->U, h->V, prev, h->Ip, h->Ic, row, h->stream,
-                               skip, maxdiff, hist, h->cfg.precision, h->cfg.nt_max + 1, side_of(h), true);
-  if (e == cudaSuccess) e = side_join(h);
+  cudaError_t e = kbe::launch_update_row(h->mesh, n, h->cfg.dt, theta, h->hk, h->U, h->V, prev, h->Ip,
+                                         h->Ic, row, h->stream, skip, maxdiff, hist, h->cfg.precision,
+                                         h->cfg.nt_max + 1);
   if (e != cudaSuccess) return cuda_fail(h, e, "update_row");
   if (h->prof) h->stats.launches += 2;
   return KBE_OK;
 }
 
-kbe_status density(kbe_handle *h, int n, double2 *out, const int *skip = nullptr, bool on_side = false) {
-  cudaError_t e = kbe::launch_local_density(h->mesh, frow(h, n) + (size_t)n * 2 * h->blk, out,
-                                            on_side ? side_of(h) : h->stream, skip);
+kbe_status density(kbe_handle *h, int n, double2 *out, const int *skip = nullptr) {
+  cudaError_t e = kbe::launch_local_density(h->mesh, frow(h, n) + (size_t)n * 2 * h->blk, out, h->stream, skip);
   if (e != cudaSuccess) return cuda_fail(h, e, "local_density");
   if (h->prof) h->stats.launches += 1;
   return KBE_OK;
@@ -335,7 +303,7 @@ kbe_status observables(kbe_handle *h, int n, const double2 *Irow) {
   cudaError_t e = kbe::launch_observables(h->mesh, hop_table(h), p, frow(h, n) + (size_t)n * 2 * h->blk,
                                           Irow + (size_t)n * 2 * h->blk, h->rho + (size_t)n * h->nb2,
                                           h->obs + (size_t)n * 6, h->nkb + (size_t)n * h->mesh.nk * h->cfg.nb,
-                                          h->status, h->stream);
+                                          h->status, h->obs_part, h->obs_ticket, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "observables");
   if (h->prof) h->stats.launches += 1;
   return KBE_OK;
@@ -364,25 +332,17 @@ kbe_status one_step(kbe_handle *h) {
     if (e != cudaSuccess) return cuda_fail(h, e, "corrector flags");
   }
   for (int c = 0; c < h->cfg.n_corr; ++c) {
-    // the midpoint density and the propagators (side stream) do not depend on
-    // the collision row (main stream): they overlap it
-    cudaError_t e = side_fork(h);
-    if (e != cudaSuccess) return cuda_fail(h, e, "stream fork");
-    if ((s = density(h, n, rcur, skip, true)) != KBE_OK) return s;
-    if ((s = build_props(h, n, r1, rcur, 0.5, 0.5, nullptr, nullptr, nullptr, skip, true)) != KBE_OK) return s;
+    if ((s = density(h, n, rcur, skip)) != KBE_OK) return s;
+    if ((s = build_props(h, n, r1, rcur, 0.5, 0.5, nullptr, nullptr, nullptr, skip)) != KBE_OK) return s;
     if ((s = evaluate_row(h, n, skip)) != KBE_OK) return s;
-    if ((e = side_join(h)) != cudaSuccess) return cuda_fail(h, e, "stream join");
     if ((s = update(h, n, 0.5, skip, md)) != KBE_OK) return s;
     if (tol) {
       cudaError_t e = kbe::launch_corr_check(h->d_maxdiff, h->cfg.corr_tol, h->d_skip, h->d_iters + n, h->stream);
       if (e != cudaSuccess) return cuda_fail(h, e, "corrector check");
     }
   }
-  cudaError_t e = side_fork(h);   // the density of row n beside the final collision row
-  if (e != cudaSuccess) return cuda_fail(h, e, "stream fork");
-  if ((s = density(h, n, h->rho + (size_t)n * nb2, nullptr, true)) != KBE_OK) return s;
   if ((s = evaluate_row(h, n)) != KBE_OK) return s;
-  if ((e = side_join(h)) != cudaSuccess) return cuda_fail(h, e, "stream join");
+  if ((s = density(h, n, h->rho + (size_t)n * nb2)) != KBE_OK) return s;
   if ((s = observables(h, n, h->Ic)) != KBE_OK) return s;
   std::swap(h->Ip, h->Ic);
   h->n = n;
@@ -850,6 +810,7 @@ static size_t handle_bytes(const kbe_config *cfg) {
   b += (T + 2) * nb2 * sizeof(double2) + (T + 1) * (6 + (size_t)m.nk * cfg->nb) * sizeof(double);
   b += (T + 1) * sizeof(double) + 64;
   b += (T + 1) * sizeof(int) + 16;                                // corrector counts and flags
+  b += 3 * (size_t)m.nk * sizeof(double) + sizeof(unsigned);       // observables partials, ticket
   return b;
 }
 
@@ -879,14 +840,6 @@ kbe_status kbe_create(const kbe_config *cfg, void *stream, kbe_handle **out) {
   h->cfg = *cfg;
   h->mesh = Mesh{cfg->nb, cfg->L[0], cfg->L[1], cfg->L[0] * cfg->L[1]};
   h->stream = (cudaStream_t)stream;
-  if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
-    free_all(h);
-    delete h;
-    cudaGetLastError();
-    return fail(nullptr, KBE_ERR_CUDA, "kbe_create: side stream / events");
-  }
   h->nb2 = cfg->nb * cfg->nb;
   h->blk = (size_t)h->nb2 * h->mesh.nk;
   h->v.assign((size_t)h->nb2, 0.0);
@@ -914,6 +867,8 @@ kbe_status kbe_create(const kbe_config *cfg, void *stream, kbe_handle **out) {
   if (e == cudaSuccess) e = dalloc(h, &h->obs, (T + 1) * 6);
   if (e == cudaSuccess) e = dalloc(h, &h->nkb, (T + 1) * h->mesh.nk * cfg->nb);
   if (e == cudaSuccess) e = dalloc(h, &h->status, 1);
+  if (e == cudaSuccess) e = dalloc(h, &h->obs_part, 3 * (size_t)h->mesh.nk);
+  if (e == cudaSuccess) e = dalloc(h, &h->obs_ticket, 1);
   if (e == cudaSuccess) e = dalloc(h, &h->d_U, T + 1);
   if (e == cudaSuccess) e = dalloc(h, &h->d_skip, 1);
   if (e == cudaSuccess) e = dalloc(h, &h->d_maxdiff, 1);
@@ -926,6 +881,7 @@ kbe_status kbe_create(const kbe_config *cfg, void *stream, kbe_handle **out) {
     return fail(nullptr, e == cudaErrorMemoryAllocation ? KBE_ERR_OOM : KBE_ERR_CUDA, msg);
   }
   cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
+  cudaMemsetAsync(h->obs_ticket, 0, sizeof(unsigned), h->stream);
   cudaMemsetAsync(h->rho, 0, sizeof(double2) * (T + 2) * h->nb2, h->stream);
   cudaMemsetAsync(h->d_iters, 0, sizeof(int) * (T + 1), h->stream);
   h->Ip0 = h->Ip;
@@ -1054,6 +1010,7 @@ kbe_status kbe_reset(kbe_handle *h) {
   if (e != cudaSuccess) return cuda_fail(h, e, "reset sync");
   h->sticky = KBE_OK;
   cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
+  cudaMemsetAsync(h->obs_ticket, 0, sizeof(unsigned), h->stream);
   h->Ip = h->Ip0;   // a fixed order, so that a replayed graph sees the pointers it captured
   h->Ic = h->Ic0;
   cudaMemsetAsync(h->Ip, 0, sizeof(double2) * 2 * h->blk, h->stream);

@@ -165,6 +165,24 @@ __device__ __forceinline__ float2 c_from<float2>(double2 z) { return make_float2
 __device__ __forceinline__ double2 c_widen(double2 z) { return z; }
 __device__ __forceinline__ double2 c_widen(float2 z) { return make_double2(z.x, z.y); }
 
+// A running sum of FP32 terms kept as an unevaluated pair hi + lo on the FP32
+// pipe: every addition is Knuth's TwoSum (s = hi + x and its exact rounding
+// error), the errors summed in lo. For the few tens of terms of a partial-sum
+// reduction the pair carries the sum to about 2^-44 of its largest term, as an
+// FP64 running sum would for FP32 terms, at FP32 rate (GB300 issues FP64 at
+// 1/64 of it).
+struct FSum {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+    hi = s;
+    lo = __fadd_rn(lo, err);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // ---- history storage of one (G^<, dG) pair (see kbe_op_pack) --------------
 // dG = G^< - G^> is formed in FP64 by the caller; o0 / o1 index the stored
 // complex numbers of component 0 and 1
@@ -448,7 +466,7 @@ cudaError_t launch_update_row(const Mesh &m, int n, double dt, double theta, con
                               const double2 *Iprev, const double2 *Icur, double2 *out,
                               cudaStream_t st, const int *skip = nullptr,
                               unsigned long long *maxdiff = nullptr, void *packed = nullptr, int prec = 0,
-                              int cap = 0, cudaStream_t st_diag = nullptr, bool diag_apart = false);
+                              int cap = 0);
 // Algorithm 1's convergence test after a corrector pass (one thread): unless
 // skip is set, count the pass in *iters, set skip when *maxdiff <= tol, and
 // clear *maxdiff for the next pass.
@@ -461,9 +479,11 @@ struct ObsParams {
   int hf, paper_shift;
   double v[kMaxNb * kMaxNb];
 };
+// part: 3 doubles per CTA (at most n_k CTAs); ticket: one zeroed word
 cudaError_t launch_observables(const Mesh &m, const HopTable &hop, const ObsParams &p,
                                const double2 *Gdiag, const double2 *Idiag, const double2 *rho_n,
-                               double *obs_out, double *nkb_out, int *status, cudaStream_t st);
+                               double *obs_out, double *nkb_out, int *status, double *part, unsigned *ticket,
+                               cudaStream_t st);
 
 // reverse mode (FP64 history; see kbe_adjoint.cu). Rows are [l][x][a][b][k]
 // with x = (G^<, G^>) or their adjoints.

@@ -24,23 +24,34 @@ struct MatGroup {
     a = e / NB;
     b = e - a * NB;
   }
-  // (A B)_ab of this thread's k-point
+  // (A B)_ab of this thread's k-point. The sum over c runs as two independent
+  // chains (even and odd c) added at the end: the series kernels are chains of
+  // these products on one warp per SM sub-partition, so the dependent FP64
+  // latency, not the pipe, sets their time.
   __device__ __forceinline__ double2 mm(const double2 *A, const double2 *B) const {
     const double2 *Ar = A + kk * E + a * NB;
     const double2 *Bc = B + kk * E + b;
-    double2 s = make_double2(0.0, 0.0);
+    double2 s0 = make_double2(0.0, 0.0), s1 = make_double2(0.0, 0.0);
 #pragma unroll
-    for (int c = 0; c < NB; ++c) s = c_fma(Ar[c], Bc[c * NB], s);
-    return s;
+    for (int c = 0; c + 1 < NB; c += 2) {
+      s0 = c_fma(Ar[c], Bc[c * NB], s0);
+      s1 = c_fma(Ar[c + 1], Bc[(c + 1) * NB], s1);
+    }
+    if (NB % 2) s0 = c_fma(Ar[NB - 1], Bc[(NB - 1) * NB], s0);
+    return c_add(s0, s1);
   }
-  // (A B^+)_ab
+  // (A B^+)_ab, two chains as mm
   __device__ __forceinline__ double2 mm_adj(const double2 *A, const double2 *B) const {
     const double2 *Ar = A + kk * E + a * NB;
     const double2 *Br = B + kk * E + b * NB;
-    double2 s = make_double2(0.0, 0.0);
+    double2 s0 = make_double2(0.0, 0.0), s1 = make_double2(0.0, 0.0);
 #pragma unroll
-    for (int c = 0; c < NB; ++c) s = c_add(s, c_mulc(Ar[c], Br[c]));
-    return s;
+    for (int c = 0; c + 1 < NB; c += 2) {
+      s0 = c_add(s0, c_mulc(Ar[c], Br[c]));
+      s1 = c_add(s1, c_mulc(Ar[c + 1], Br[c + 1]));
+    }
+    if (NB % 2) s0 = c_add(s0, c_mulc(Ar[NB - 1], Br[NB - 1]));
+    return c_add(s0, s1);
   }
 };
 
@@ -159,10 +170,14 @@ template <int NB>
 __device__ __forceinline__ double2 mm_hadj(const MatGroup<NB> &g, const double2 *A, const double2 *B) {
   const double2 *Ac = A + g.kk * g.E + g.a;
   const double2 *Bc = B + g.kk * g.E + g.b;
-  double2 s = make_double2(0.0, 0.0);
+  double2 s0 = make_double2(0.0, 0.0), s1 = make_double2(0.0, 0.0);
 #pragma unroll
-  for (int c = 0; c < NB; ++c) s = c_add(s, c_mulc(Bc[c * NB], Ac[c * NB]));
-  return s;
+  for (int c = 0; c + 1 < NB; c += 2) {
+    s0 = c_add(s0, c_mulc(Bc[c * NB], Ac[c * NB]));
+    s1 = c_add(s1, c_mulc(Bc[(c + 1) * NB], Ac[(c + 1) * NB]));
+  }
+  if (NB % 2) s0 = c_add(s0, c_mulc(Bc[(NB - 1) * NB], Ac[(NB - 1) * NB]));
+  return c_add(s0, s1);
 }
 
 #define KBE_NB_SWITCH(nb, CALL)          \

@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(256) update_diag_kernel(int n, int nk, double 
                                                           double2 *__restrict__ out, int kpc,
                                                           const int *__restrict__ skip,
                                                           unsigned long long *maxdiff, void *__restrict__ packed,
-                                                          int prec, int cap) {
+                                                          int prec, int cap, const double2 *__restrict__ Uin) {
   if (skip && *skip) return;
   using G = MatGroup<NB>;
   const int span = kpc * G::E;
@@ -231,20 +231,30 @@ __global__ void __launch_bounds__(256) update_diag_kernel(int n, int nk, double 
   const SeriesPlan sp = series_plan<NB>(g, H, kpc, nvalid, dt, red);
   const int s = sp.s;
   const double tau = ldexp(dt, -s);
-  // X_tau = tau sum_m Q_m / (m+1), Q_m = (-i tau / m) [h, Q_{m-1}], Q_0 = Sbar
+  // X_tau = tau sum_m Q_m / (m+1), Q_m = (-i tau / m) [h, Q_{m-1}], Q_0 = Sbar.
+  // Sbar is Hermitian, and so is every Q_m (h is): [h, Q] = hQ - (hQ)^+, one
+  // product per term; the element (b, a) of hQ comes through shared memory (T).
+  // Formed this way every Q_m is exactly Hermitian in floating point.
   double2 x = c_scale(tau, sv);
   for (int m = 1; m <= sp.mx; ++m) {
     const double cm = tau * kSeriesInv[m], cx = tau * kSeriesInv[m + 1];
-    const double2 c = c_sub(g.mm(H, Qs), g.mm(Qs, H));
-    const double2 q = make_double2(cm * c.y, -cm * c.x);
+    const double2 pm = g.mm(H, Qs);   // (h Q_{m-1})_ab
+    T[o] = pm;
     __syncthreads();
+    const double2 pt = T[g.kk * G::E + g.b * NB + g.a];   // (h Q_{m-1})_ba
+    const double2 c = make_double2(pm.x - pt.x, pm.y + pt.y);   // (hQ)_ab - conj((hQ)_ba)
+    const double2 q = make_double2(cm * c.y, -cm * c.x);
     Qs[o] = q;
     x = c_add(x, c_scale(cx, q));
     __syncthreads();
   }
   double2 u, v;
-  exp_and_phi<NB>(g, H, tau, 0, P, T, Wk, u, v, sp.mexp);   // U_tau
-  (void)v;
+  if (s == 0 && Uin) {   // U_tau = U_dt: the step's propagator, built from the same h by the same series
+    u = active ? Uin[(size_t)g.e * nk + k] : make_double2(0.0, 0.0);
+  } else {
+    exp_and_phi<NB>(g, H, tau, 0, P, T, Wk, u, v, sp.mexp);   // U_tau
+    (void)v;
+  }
   for (int r = 0; r < s; ++r) {   // X <- X + U X U^+, U <- U U
     P[o] = u;
     Qs[o] = x;
@@ -336,8 +346,16 @@ __global__ void local_density_kernel(int nb, int nk, const double2 *__restrict__
 }
 
 // rows j < n: G^x(n,j) = U G^x(n-1,j) + V [(1-theta) Ip^x(j) + theta Ic^x(j)];
-// one thread per (j, a, b, k) forms both components, so that it can also store
-// the history's (G^<, dG) pair of the element (packed != NULL)
+// one thread per (j, b, k) and a chunk of UA rows a (all N_b rows up to N_b =
+// 8): the column b of G(n-1, j) and of the blended Ibar(j) is loaded and
+// blended once per thread and reused for every row a of the chunk (the FP64
+// blend was 3/7 of the pipe work when every output formed it again). Each
+// output accumulates in the same order as a per-output sum over c. The thread
+// forms both components of its outputs, so that it can also store the
+// history's (G^<, dG) pair of each (packed != NULL).
+template <int NB>
+__host__ __device__ constexpr int update_chunk() { return NB <= 8 ? NB : 4; }
+
 template <int NB>
 __global__ void update_rows_kernel(int n, int nk, double theta, const double2 *__restrict__ U,
                                    const double2 *__restrict__ V, const double2 *__restrict__ Gprev,
@@ -345,8 +363,9 @@ __global__ void update_rows_kernel(int n, int nk, double theta, const double2 *_
                                    double2 *__restrict__ out, const int *__restrict__ skip,
                                    unsigned long long *maxdiff, void *__restrict__ packed, int prec, int cap) {
   if (skip && *skip) return;
+  constexpr int UA = update_chunk<NB>(), NCH = NB / UA;
   const size_t blk = (size_t)NB * NB * nk;
-  const size_t total = (size_t)n * blk;
+  const size_t total = (size_t)n * NCH * NB * nk;
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   double dmax = 0.0;
   if (idx < total) {
@@ -354,33 +373,42 @@ __global__ void update_rows_kernel(int n, int nk, double theta, const double2 *_
     size_t t = idx / nk;
     const int b = (int)(t % NB);
     t /= NB;
-    const int a = (int)(t % NB);
-    const size_t j = t / NB;
+    const int a0 = (int)(t % NCH) * UA;
+    const size_t j = t / NCH;
     const size_t base = j * 2 * blk;
-    double2 acc0 = make_double2(0, 0), acc1 = make_double2(0, 0);
+    double2 acc0[UA], acc1[UA];
+#pragma unroll
+    for (int q = 0; q < UA; ++q) acc0[q] = acc1[q] = make_double2(0, 0);
 #pragma unroll
     for (int c = 0; c < NB; ++c) {
       const size_t oc = (size_t)(c * NB + b) * nk + k;
-      const size_t ou = (size_t)(a * NB + c) * nk + k;
-      const double2 u = U[ou], v = V[ou];
       double2 ib0 = c_scale(1.0 - theta, Ip[base + oc]), ib1 = c_scale(1.0 - theta, Ip[base + blk + oc]);
       if (theta != 0.0) {
         ib0 = c_fma(make_double2(theta, 0.0), Ic[base + oc], ib0);
         ib1 = c_fma(make_double2(theta, 0.0), Ic[base + blk + oc], ib1);
       }
-      acc0 = c_fma(u, Gprev[base + oc], acc0);
-      acc0 = c_fma(v, ib0, acc0);
-      acc1 = c_fma(u, Gprev[base + blk + oc], acc1);
-      acc1 = c_fma(v, ib1, acc1);
+      const double2 g0 = Gprev[base + oc], g1 = Gprev[base + blk + oc];
+#pragma unroll
+      for (int q = 0; q < UA; ++q) {
+        const size_t ou = (size_t)((a0 + q) * NB + c) * nk + k;
+        const double2 u = U[ou], v = V[ou];
+        acc0[q] = c_fma(u, g0, acc0[q]);
+        acc0[q] = c_fma(v, ib0, acc0[q]);
+        acc1[q] = c_fma(u, g1, acc1[q]);
+        acc1[q] = c_fma(v, ib1, acc1[q]);
+      }
     }
-    const size_t oo = base + (size_t)(a * NB + b) * nk + k;
-    if (maxdiff) {   // G^< entries
-      const double2 d = c_sub(acc0, out[oo]);
-      dmax = sqrt(d.x * d.x + d.y * d.y);
+#pragma unroll
+    for (int q = 0; q < UA; ++q) {
+      const size_t oo = base + (size_t)((a0 + q) * NB + b) * nk + k;
+      if (maxdiff) {   // G^< entries
+        const double2 d = c_sub(acc0[q], out[oo]);
+        dmax = fmax(dmax, sqrt(d.x * d.x + d.y * d.y));
+      }
+      out[oo] = acc0[q];
+      out[oo + blk] = acc1[q];
+      if (packed) pack_store(prec, packed, oo, oo + blk, acc0[q], c_sub(acc0[q], acc1[q]), NB, nk, n, cap);
     }
-    out[oo] = acc0;
-    out[oo + blk] = acc1;
-    if (packed) pack_store(prec, packed, oo, oo + blk, acc0, c_sub(acc0, acc1), NB, nk, n, cap);
   }
   if (maxdiff) {   // every lane reaches here (blockDim is a multiple of 32)
 #pragma unroll
@@ -397,72 +425,108 @@ __global__ void corr_check_kernel(unsigned long long *maxdiff, double tol, int *
   *maxdiff = 0ull;
 }
 
-// equal-time observables of row n; one CTA
+// equal-time observables of row n. One matrix group per k-point (kpc k-points
+// per CTA, as the propagator kernels): the threads of a k-point compute its
+// Peierls phases together, N_b^2 at a time, then thread (a, b) forms h0_ab(k)
+// and its terms of the sums; each CTA reduces its terms in a fixed tree and
+// writes (N, K, C) to part[3 blockIdx]; the CTA that finishes last (a ticket
+// counter, reset by it) adds the partials in CTA order and writes obs. The
+// result does not depend on the order in which the CTAs ran.
 template <int NB>
-__global__ void observables_kernel(Mesh m, HopTable hop, ObsParams p, const double2 *__restrict__ G,
-                                   const double2 *__restrict__ Idg, const double2 *__restrict__ rho,
-                                   double *obs, double *nkb, int *status) {
-  __shared__ double red[3][32];
+__global__ void __launch_bounds__(256) observables_kernel(Mesh m, HopTable hop, ObsParams p,
+                                                          const double2 *__restrict__ G,
+                                                          const double2 *__restrict__ Idg,
+                                                          const double2 *__restrict__ rho, double *obs, double *nkb,
+                                                          int *status, int kpc, double *part, unsigned *ticket) {
+  using Gp = MatGroup<NB>;
+  double2 *ph = kbe_dsm;                                   // [kk][E] phases
+  double *red = (double *)(kbe_dsm + (size_t)kpc * Gp::E);  // [3][threads]
+  __shared__ bool last;
+  const Gp g;
+  const int k = blockIdx.x * kpc + g.kk;
+  const bool active = k < m.nk;
+  const int nt = blockDim.x;
+  double2 hv = make_double2(0.0, 0.0);
+  const int k0 = k / m.L1, k1 = k - (k / m.L1) * m.L1;
+  for (int r0 = 0; r0 < hop.nhop; r0 += Gp::E) {
+    const int r = r0 + g.e;
+    if (active && r < hop.nhop) {
+      const int R0 = hop.R[2 * r], R1 = hop.R[2 * r + 1];
+      // reduce the lattice phase exactly before converting to an angle
+      const int m0 = ((k0 * R0) % m.L0 + m.L0) % m.L0, m1 = ((k1 * R1) % m.L1 + m.L1) % m.L1;
+      const double th = 2.0 * M_PI * ((double)m0 / m.L0 + (double)m1 / m.L1) - p.Abar * (hop.d0 * R0 + hop.d1 * R1);
+      double sn, cs;
+      sincos(th, &sn, &cs);
+      ph[g.kk * Gp::E + g.e] = make_double2(cs, sn);
+    }
+    __syncthreads();
+    if (active)
+      for (int q = 0; q < Gp::E && r0 + q < hop.nhop; ++q)
+        hv = c_fma(hop.T[(size_t)(r0 + q) * Gp::E + g.e], ph[g.kk * Gp::E + q], hv);
+    __syncthreads();
+  }
   double sN = 0.0, sK = 0.0, sC = 0.0;
-  double2 h[NB * NB];
-  for (int k = threadIdx.x; k < m.nk; k += blockDim.x) {
-    bare_h<NB>(hop, k, m.L0, m.L1, p.Abar, h);
-#pragma unroll 1
-    for (int a = 0; a < NB; ++a) {
-      const double naa = G[(size_t)(a * NB + a) * m.nk + k].y;   // Re(-i G_aa)
-      nkb[(size_t)k * NB + a] = naa;
-      sN += naa;
-      sC += Idg[(size_t)(a * NB + a) * m.nk + k].y;               // Re(-i I_aa)
-#pragma unroll 1
-      for (int b = 0; b < NB; ++b) {
-        const double2 g = G[(size_t)(b * NB + a) * m.nk + k];    // rho_ba = -i G_ba
-        const double2 r = make_double2(g.y, -g.x);
-        sK += c_mul(h[a * NB + b], r).x;
-      }
+  if (active) {
+    const double2 gba = G[(size_t)(g.b * NB + g.a) * m.nk + k];   // rho_ba = -i G_ba
+    sK = c_mul(hv, make_double2(gba.y, -gba.x)).x;
+    if (g.a == g.b) {
+      sN = gba.y;                                                 // Re(-i G_aa)
+      nkb[(size_t)k * NB + g.a] = sN;
+      sC = Idg[(size_t)(g.a * NB + g.a) * m.nk + k].y;            // Re(-i I_aa)
     }
   }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    sN += __shfl_xor_sync(0xffffffffu, sN, off);
-    sK += __shfl_xor_sync(0xffffffffu, sK, off);
-    sC += __shfl_xor_sync(0xffffffffu, sC, off);
+  red[threadIdx.x] = sN;
+  red[nt + threadIdx.x] = sK;
+  red[2 * nt + threadIdx.x] = sC;
+  __syncthreads();
+  int span = 1;
+  while (span < nt) span <<= 1;
+  for (int st = span >> 1; st > 0; st >>= 1) {   // fixed tree over the CTA's threads
+    if ((int)threadIdx.x < st && (int)threadIdx.x + st < nt)
+      for (int q = 0; q < 3; ++q) red[q * nt + threadIdx.x] += red[q * nt + threadIdx.x + st];
+    __syncthreads();
   }
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  if (lane == 0) {
-    red[0][warp] = sN;
-    red[1][warp] = sK;
-    red[2][warp] = sC;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 3; ++q) part[3 * blockIdx.x + q] = red[q * nt];
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double N = 0, K = 0, C = 0;
-    for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
-      N += red[0][w];
-      K += red[1][w];
-      C += red[2][w];
-    }
-    double Ehf = 0.0, Esh = 0.0;
-    if (p.hf) {
-      for (int jj = 0; jj < NB; ++jj)
-        for (int mm = 0; mm < NB; ++mm) {
-          double2 x = c_scale(-p.v[jj * NB + mm], rho[jj * NB + mm]);
-          if (jj == mm)
-            for (int a = 0; a < NB; ++a) x = c_add(x, c_scale(p.v[jj * NB + a], rho[a * NB + a]));
-          Ehf += 0.5 * c_mul(c_scale(p.Un, x), rho[mm * NB + jj]).x;
-        }
-    }
-    if (p.paper_shift) Esh = -p.Un * rho[(NB - 1) * NB + NB - 1].x;
-    obs[0] = N / m.nk;
-    obs[1] = K / m.nk;
-    obs[2] = Ehf;
-    obs[3] = 0.5 * C / m.nk;
-    obs[4] = Esh;
-    obs[5] = obs[1] + obs[2] + obs[3] + obs[4];
-    if (!isfinite(obs[0]) || !isfinite(obs[5])) atomicOr(status, kDevNonFinite);
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  double N = 0, K = 0, C = 0;
+  for (int c = 0; c < (int)gridDim.x; ++c) {
+    N += __ldcg(part + 3 * c);
+    K += __ldcg(part + 3 * c + 1);
+    C += __ldcg(part + 3 * c + 2);
   }
+  *ticket = 0u;   // ready for the next launch (stream order)
+  double Ehf = 0.0, Esh = 0.0;
+  if (p.hf) {
+    for (int jj = 0; jj < NB; ++jj)
+      for (int mm = 0; mm < NB; ++mm) {
+        double2 x = c_scale(-p.v[jj * NB + mm], rho[jj * NB + mm]);
+        if (jj == mm)
+          for (int a = 0; a < NB; ++a) x = c_add(x, c_scale(p.v[jj * NB + a], rho[a * NB + a]));
+        Ehf += 0.5 * c_mul(c_scale(p.Un, x), rho[mm * NB + jj]).x;
+      }
+  }
+  if (p.paper_shift) Esh = -p.Un * rho[(NB - 1) * NB + NB - 1].x;
+  obs[0] = N / m.nk;
+  obs[1] = K / m.nk;
+  obs[2] = Ehf;
+  obs[3] = 0.5 * C / m.nk;
+  obs[4] = Esh;
+  obs[5] = obs[1] + obs[2] + obs[3] + obs[4];
+  if (!isfinite(obs[0]) || !isfinite(obs[5])) atomicOr(status, kDevNonFinite);
 }
 
 }  // namespace
+
+template <int NB>
+size_t obs_smem(int nk) {
+  return sizeof(double2) * (size_t)matgroup_kpc<NB>(nk) * NB * NB + sizeof(double) * 3 * matgroup_threads<NB>(nk);
+}
 
 cudaError_t launch_init_state(const Mesh &m, const HopTable &hop, double beta, double mu,
                               double2 *H00, int *status, cudaStream_t st) {
@@ -490,21 +554,15 @@ cudaError_t launch_update_row(const Mesh &m, int n, double dt, double theta, con
                               const double2 *U, const double2 *V, const double2 *Gprev,
                               const double2 *Iprev, const double2 *Icur, double2 *out,
                               cudaStream_t st, const int *skip, unsigned long long *maxdiff, void *packed,
-                              int prec, int cap, cudaStream_t st_diag, bool diag_apart) {
-  // diag_apart: the time diagonal on st_diag (independent of the rows j < n;
-  // the caller orders st_diag after st's prior work and joins it back)
-  if (!diag_apart) st_diag = st;
-  const size_t blk = (size_t)m.nb * m.nb * m.nk;
-  const size_t total = (size_t)n * blk;
+                              int prec, int cap) {
+  const size_t total = (size_t)n * (m.nb / (m.nb <= 8 ? m.nb : 4)) * m.nb * m.nk;   // (j, a chunk, b, k)
   const int threads = 256;
   const unsigned blocks = (unsigned)((total + threads - 1) / threads);
   const double2 *ic = (theta != 0.0) ? Icur : Iprev;
-  // the diagonal first: a long latency-bound chain on few SMs, which the rows
-  // (FP64-pipe bound, every SM) then overlap
   KBE_NB_SWITCH(m.nb, (update_diag_kernel<NB><<<matgroup_blocks<NB>(m.nk), matgroup_threads<NB>(m.nk),
-                                                 matgroup_smem<NB>(m.nk, 5), st_diag>>>(
+                                                 matgroup_smem<NB>(m.nk, 5), st>>>(
                           n, m.nk, dt, theta, h, Gprev, Iprev, ic, out, matgroup_kpc<NB>(m.nk), skip,
-                          maxdiff, packed, prec, cap)));
+                          maxdiff, packed, prec, cap, U)));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || total == 0) return e;
   KBE_NB_SWITCH(m.nb, (update_rows_kernel<NB><<<blocks, threads, 0, st>>>(n, m.nk, theta, U, V, Gprev, Iprev, ic,
@@ -520,8 +578,12 @@ cudaError_t launch_corr_check(unsigned long long *maxdiff, double tol, int *skip
 
 cudaError_t launch_observables(const Mesh &m, const HopTable &hop, const ObsParams &p,
                                const double2 *Gdiag, const double2 *Idiag, const double2 *rho_n,
-                               double *obs_out, double *nkb_out, int *status, cudaStream_t st) {
-  KBE_NB_SWITCH(m.nb, (observables_kernel<NB><<<1, 256, 0, st>>>(m, hop, p, Gdiag, Idiag, rho_n, obs_out, nkb_out, status)));
+                               double *obs_out, double *nkb_out, int *status, double *part, unsigned *ticket,
+                               cudaStream_t st) {
+  KBE_NB_SWITCH(m.nb, (observables_kernel<NB><<<matgroup_blocks<NB>(m.nk), matgroup_threads<NB>(m.nk),
+                                                 obs_smem<NB>(m.nk), st>>>(
+                          m, hop, p, Gdiag, Idiag, rho_n, obs_out, nkb_out, status, matgroup_kpc<NB>(m.nk), part,
+                          ticket)));
   return cudaGetLastError();
 }
 

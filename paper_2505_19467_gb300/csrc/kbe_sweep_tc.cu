@@ -42,7 +42,7 @@
 //   warps 2-5  epilogue: tensor memory -> registers -> complex64 partial
 //              sums: one column partial per (panel, column, k), one row
 //              partial per (row, k).
-// tc_reduce_kernel then sums the partials in FP64 and adds what the MMAs leave
+// tc_reduce_kernel then sums the partials (hi + lo FP32 pairs) and adds what the MMAs leave
 // out: the diagonal block (the end node of column j), the row use's weights
 // f != 1 (trapezoid: node 0; Gregory: its end nodes) and the Gregory Y terms.
 //
@@ -616,20 +616,21 @@ __global__ void __launch_bounds__(256)
     const int ab = t % NB2, kk = t / NB2, k = k0 + kk;
     if (k >= nk) continue;
     const int a = ab / NB, b = ab % NB;
-    double xr = 0.0, xi = 0.0, yr = 0.0, yi = 0.0;
+    FSum sxr, sxi, syr, syi;   // the complex64 partials, summed on the FP32 pipe
     for (int sg = 0; sg * SD * TM <= j; ++sg) {   // the row use's partial of each strip group reaching row j
       const float2 rp = RP[(((size_t)sg * (n + 1) + j) * nk + k) * NB2 + ab];
-      xr += rp.x;
-      xi += rp.y;
+      sxr.add(rp.x);
+      sxi.add(rp.y);
     }
     for (int p = pmin; p < P; ++p) {
       const size_t o = ((((size_t)p * (n + 1) + j) * nk + k) * 2) * NB2 + ab;
       const float2 x = CP[o], y = CP[o + NB2];
-      xr += x.x;
-      xi += x.y;
-      yr += y.x;
-      yi += y.y;
+      sxr.add(x.x);
+      sxi.add(x.y);
+      syr.add(y.x);
+      syi.add(y.y);
     }
+    double xr = sxr.value(), xi = sxi.value(), yr = syr.value(), yi = syi.value();
     // the diagonal block and the end-node terms in FP32 (their operands are
     // complex64 coefficients and 22-bit history values), added to the FP64 sums
     float2 tx = make_float2(0.f, 0.f), ty = make_float2(0.f, 0.f);

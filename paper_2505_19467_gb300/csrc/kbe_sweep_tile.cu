@@ -30,8 +30,8 @@
 //
 // Partial sums are complex64: the column partials of one chunk (X, Y of each
 // column, summed over <= TI rows) and the row partials of one strip (X of each
-// row, summed over the strip's TM columns). tile_reduce_kernel adds them in
-// FP64 in a fixed order (the result is deterministic) and adds the row use's
+// row, summed over the strip's TM columns). tile_reduce_kernel adds them as
+// hi + lo FP32 pairs (FSum) in a fixed order (the result is deterministic) and adds the row use's
 // Y terms at the few nodes where the weights of [0, t_j] and [0, t_n] differ
 // (none for the trapezoid rule; the Gregory end nodes). The extra traffic is
 // ~(1/TI + 1/(2 TM)) of the triangle's bytes, written once and read once.
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(tile_threads<NB>(), TileCfg<NB>::MINB)
   }
 }
 
-// I(j) from the partials, FP64: X = sum of the column partials of column j
+// I(j) from the partials (hi + lo FP32 pairs, FP64 result): X = sum of the column partials of column j
 // (one per chunk of its strip) and of its row partials (one per strip left of
 // it); Y = the column partials' Y plus the row use's Y at nodes m < j whose
 // weight on [0, t_j] differs from the one on [0, t_n]: (f (C3 - C2^<) +
@@ -356,20 +356,21 @@ __global__ void tile_reduce_kernel(const float2 *__restrict__ CP, const float2 *
     const int a = ab / NB, b = ab - a * NB;
     const int M0 = (j / TM) * TM;
     const int chunks = (n + 1 - M0 + TI - 1) / TI, strips = j / TM + 1;
-    double xr = 0.0, xi = 0.0, yr = 0.0, yi = 0.0;
+    FSum sxr, sxi, syr, syi;   // the complex64 partials, summed on the FP32 pipe
     for (int c = 0; c < chunks; ++c) {
       const float2 x = CP[(((size_t)c * (n + 1) + j) * 2) * blk + r];
       const float2 y = CP[(((size_t)c * (n + 1) + j) * 2 + 1) * blk + r];
-      xr += x.x;
-      xi += x.y;
-      yr += y.x;
-      yi += y.y;
+      sxr.add(x.x);
+      sxi.add(x.y);
+      syr.add(y.x);
+      syi.add(y.y);
     }
     for (int s = 0; s < strips; ++s) {
       const float2 x = RP[((size_t)s * (n + 1) + j) * blk + r];
-      xr += x.x;
-      xi += x.y;
+      sxr.add(x.x);
+      sxi.add(x.y);
     }
+    double xr = sxr.value(), xi = sxi.value(), yr = syr.value(), yi = syi.value();
     if (QUAD != kQuadTrapezoid && j > 0 && n >= 1) {
       const int ns = j >= 5 ? 5 : j;   // nodes 0, 1, 2, j-2, j-1 (every m < j for j <= 4)
       for (int t = 0; t < ns; ++t) {

@@ -118,16 +118,101 @@ __host__ __device__ __forceinline__ int dft_group(int nk) {
   return P;
 }
 
+// Axes of at most kRegDft points, or of 16, are transformed one sequence per thread in
+// registers: a CTA loads a group of PR arrays into shared memory (rows padded
+// to L1 + 1 points, so that the row pass is close to conflict-free), each
+// thread transforms whole rows, then whole columns, and the group is stored;
+// three barriers per group instead of two per FFT stage. The butterflies and
+// the direct sums are the shared-memory path's, in the same order, so both
+// paths give the same bits.
+constexpr int kRegDft = 12;   // and 16 (a power of two: radix-2 in registers)
+__host__ __device__ __forceinline__ bool dft_axis_in_registers(int L) { return L <= kRegDft || L == 16; }
+__host__ __device__ __forceinline__ bool dft_in_registers(int L0, int L1) {
+  return dft_axis_in_registers(L0) && dft_axis_in_registers(L1);
+}
+__host__ __device__ __forceinline__ int dft_group_reg(int L0, int L1) {
+  const int nk = L0 * L1, padded = L0 * (L1 + 1);
+  const int a = 2048 / nk, b = 2560 / padded;
+  const int P = a < b ? a : b;
+  return P > 0 ? P : 1;
+}
+
+// one sequence of L points at p[i * stride], in place, in registers
+template <class C, int L>
+__device__ __forceinline__ void seq_transform(C *p, int stride, const C *tw) {
+  C v[L];
+  if constexpr ((L & (L - 1)) == 0) {
+    constexpr int logL = L == 1 ? 0 : (L == 2 ? 1 : (L == 4 ? 2 : (L == 8 ? 3 : 4)));
+#pragma unroll
+    for (int i = 0; i < L; ++i) v[i] = p[(logL ? (int)(__brev((unsigned)i) >> (32 - logL)) : 0) * stride];
+#pragma unroll
+    for (int len = 2; len <= L; len <<= 1) {
+      const int half = len >> 1, step = L / len;
+#pragma unroll
+      for (int grp = 0; grp < L / len; ++grp)
+#pragma unroll
+        for (int pos = 0; pos < half; ++pos) {
+          const int i = grp * len + pos, j = i + half;
+          const C u = v[i];
+          const C t = c_mul(tw[pos * step], v[j]);
+          v[i] = c_add(u, t);
+          v[j] = c_sub(u, t);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < L; ++i) p[i * stride] = v[i];
+  } else {   // direct sum; every output is stored as it is formed (the inputs are all in v)
+#pragma unroll
+    for (int i = 0; i < L; ++i) v[i] = p[i * stride];
+#pragma unroll
+    for (int R = 0; R < L; ++R) {
+      C acc = c_scale(0, tw[0]);
+#pragma unroll
+      for (int kk = 0; kk < L; ++kk) acc = c_fma(tw[(R * kk) % L], v[kk], acc);
+      p[R * stride] = acc;
+    }
+  }
+}
+
+template <class C>
+__device__ __forceinline__ void seq_transform_any(int L, C *p, int stride, const C *tw) {
+  switch (L) {
+    case 2: seq_transform<C, 2>(p, stride, tw); break;
+    case 3: seq_transform<C, 3>(p, stride, tw); break;
+    case 4: seq_transform<C, 4>(p, stride, tw); break;
+    case 5: seq_transform<C, 5>(p, stride, tw); break;
+    case 6: seq_transform<C, 6>(p, stride, tw); break;
+    case 7: seq_transform<C, 7>(p, stride, tw); break;
+    case 8: seq_transform<C, 8>(p, stride, tw); break;
+    case 9: seq_transform<C, 9>(p, stride, tw); break;
+    case 10: seq_transform<C, 10>(p, stride, tw); break;
+    case 11: seq_transform<C, 11>(p, stride, tw); break;
+    case 12: seq_transform<C, 12>(p, stride, tw); break;
+    case 16: seq_transform<C, 16>(p, stride, tw); break;
+    default: break;   // L = 1: nothing to do
+  }
+}
+
+__device__ __forceinline__ float2 load_as(const float2 &v, float2 *) { return v; }
+__device__ __forceinline__ float2 load_as(const double2 &v, float2 *) {
+  return make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
+}
+__device__ __forceinline__ double2 load_as(const double2 &v, double2 *) { return v; }
+__device__ __forceinline__ double2 load_as(const float2 &v, double2 *) { return make_double2(v.x, v.y); }
+
 template <class C, class Tin, class Tout>
 __global__ void dft_rows_kernel(const Tin *__restrict__ in, Tout *__restrict__ out, long narr, int L0, int L1,
                                 int sign, double scale, int accumulate, const int *__restrict__ skip) {
   if (skip && *skip) return;
   extern __shared__ double2 sm_d2[];
   C *sm = reinterpret_cast<C *>(sm_d2);
-  const int nk = L0 * L1, P = dft_group(nk);
+  const int nk = L0 * L1;
+  const bool reg = dft_in_registers(L0, L1);
+  const int P = reg ? dft_group_reg(L0, L1) : dft_group(nk);
+  const int W = reg ? L1 + 1 : L1;   // row pitch in shared memory (points)
   C *x = sm;
-  C *t = x + P * nk;
-  C *tw0 = t + P * nk;
+  C *t = x + (size_t)P * L0 * W;
+  C *tw0 = reg ? t : t + P * nk;
   C *tw1 = tw0 + L0;
   for (int i = threadIdx.x; i < L0; i += blockDim.x) {
     double s, c;
@@ -139,12 +224,37 @@ __global__ void dft_rows_kernel(const Tin *__restrict__ in, Tout *__restrict__ o
     sincospi(2.0 * i / L1, &s, &c);
     tw1[i] = c_from<C>(make_double2(c, sign * s));
   }
+  const C sc = c_from<C>(make_double2(scale, 0.0));
   const long ngroups = (narr + P - 1) / P;
   for (long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
     const long arr0 = grp * P;
     const int pa = (int)(narr - arr0 < P ? narr - arr0 : P);   // arrays in this group
     const Tin *src = in + arr0 * nk;
+    Tout *dst = out + arr0 * nk;
     __syncthreads();
+    if (reg) {
+      for (int e = threadIdx.x; e < pa * nk; e += blockDim.x) {
+        const int row = e / L1;   // (array, k0)
+        x[row * W + (e - row * L1)] = load_as(src[e], (C *)nullptr);
+      }
+      __syncthreads();
+      if (L1 > 1)   // axis 1: rows (array, k0), contiguous
+        for (int q = threadIdx.x; q < pa * L0; q += blockDim.x) seq_transform_any<C>(L1, x + q * W, 1, tw1);
+      __syncthreads();
+      if (L0 > 1)   // axis 0: columns (array, k1), pitch W
+        for (int q = threadIdx.x; q < pa * L1; q += blockDim.x) {
+          const int arr = q / L1, k1 = q - arr * L1;
+          seq_transform_any<C>(L0, x + arr * L0 * W + k1, W, tw0);
+        }
+      __syncthreads();
+      for (int e = threadIdx.x; e < pa * nk; e += blockDim.x) {
+        const int row = e / L1;
+        const C v = c_mul(sc, x[row * W + (e - row * L1)]);
+        if (accumulate) add_as(dst + e, v);
+        else store_as(dst + e, v);
+      }
+      continue;
+    }
     for (int e = threadIdx.x; e < pa * nk; e += blockDim.x) x[e] = c_from<C>(load_as_d(src[e]));
     __syncthreads();
     if (L1 > 1) {   // axis 1: L0 contiguous sequences of length L1 per array
@@ -155,8 +265,6 @@ __global__ void dft_rows_kernel(const Tin *__restrict__ in, Tout *__restrict__ o
       if (is_pow2(L0)) fft_axis<C>(x, L0, L1, pa * L1, L1, 1, nk, tw0);
       else dft_axis<C>(x, t, L0, L1, pa * L1, L1, 1, nk, tw0);
     }
-    Tout *dst = out + arr0 * nk;
-    const C sc = c_from<C>(make_double2(scale, 0.0));
     if (accumulate)
       for (int e = threadIdx.x; e < pa * nk; e += blockDim.x) add_as(dst + e, c_mul(sc, x[e]));
     else
@@ -328,6 +436,7 @@ cudaError_t products_any(const Mesh &m, const double *v, int n, double Un, const
 
 size_t dft_smem_bytes(int L0, int L1, size_t csize) {
   const int nk = L0 * L1;
+  if (dft_in_registers(L0, L1)) return csize * ((size_t)dft_group_reg(L0, L1) * L0 * (L1 + 1) + L0 + L1);
   return csize * (2 * (size_t)dft_group(nk) * nk + L0 + L1);
 }
 
@@ -356,10 +465,12 @@ template <class C, class Tin, class Tout>
 cudaError_t dft_launch(const Tin *in, Tout *out, long narr, int L0, int L1, int sign, double scale, cudaStream_t st,
                        bool accumulate, const int *skip) {
   if (narr <= 0) return cudaSuccess;
-  const int nk = L0 * L1, P = dft_group(nk);
+  const int nk = L0 * L1;
+  const bool reg = dft_in_registers(L0, L1);
+  const int P = reg ? dft_group_reg(L0, L1) : dft_group(nk);
   cudaError_t pe = dft_prepare_t<C, Tin, Tout>(L0, L1);
   if (pe != cudaSuccess) return pe;
-  const int pts = P * nk;
+  const int pts = reg ? P * (L0 > L1 ? L0 : L1) : P * nk;   // the register path: sequences per pass
   const int threads = pts >= 256 ? 256 : ((pts + 31) / 32) * 32;
   const long groups = (narr + P - 1) / P, cap = (long)device_sms() * 8;
   const long blocks = groups < cap ? groups : cap;

@@ -825,6 +825,33 @@ __global__ void coef_kernel(int prec, const double2 *__restrict__ Sig, void *__r
   const size_t blk = (size_t)nb2 * nk;
   const size_t total = (size_t)(n + 1) * blk;
   double big = 0.0;
+  if (prec == KBE_PREC_C64 || prec == KBE_PREC_F16X2) {
+    // complex64 coefficients from FP32 arithmetic (their Sigma row is complex64
+    // values held in FP64): GB300's FP64 pipe made this kernel FP64-bound
+    const float fdt = (float)dt;
+    float fbig = 0.f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+      const size_t l = i / blk, r = i - l * blk;
+      const double2 dl = Sig[(l * 2) * blk + r], dg = Sig[(l * 2 + 1) * blk + r];
+      const float2 sl = make_float2((float)dl.x, (float)dl.y), sg = make_float2((float)dg.x, (float)dg.y);
+      const float w1 = (float)(dt * quad_omega(quad, n, (int)l));
+      const float2 c1 = make_float2(w1 * (sg.x - sl.x), w1 * (sg.y - sl.y));
+      const float2 c2 = make_float2(fdt * sl.x, fdt * sl.y);
+      const float2 c3 = make_float2(fmaf(fdt, sg.x, -c1.x), fmaf(fdt, sg.y, -c1.y));
+      float2 *cf = (float2 *)Cf;
+      cf[(l * 3) * blk + r] = c1;
+      cf[(l * 3 + 1) * blk + r] = c2;
+      cf[(l * 3 + 2) * blk + r] = c3;
+      fbig = fmaxf(fbig, fmaxf(fmaxf(fabsf(c1.x), fabsf(c1.y)), fmaxf(fabsf(c2.x), fabsf(c2.y))));
+    }
+    if (cmax) {   // blockDim is a multiple of 32
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) fbig = fmaxf(fbig, __shfl_xor_sync(0xffffffffu, fbig, off));
+      if ((threadIdx.x & 31) == 0 && fbig > 0.f) atomicMax(cmax, __float_as_uint(fbig));
+    }
+    return;
+  }
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
     const size_t l = i / blk, r = i - l * blk;

@@ -218,9 +218,13 @@ kbe_status evaluate_row(kbe_handle *h, int n, const int *skip = nullptr) {
   double2 *Hrow = frow(h, n);
   const double *Ul = h->Useq.size() == 1 ? nullptr : h->d_U;
   // the complex64 and split-FP16 forms hold Sigma in complex FP32 (their coefficient rows round
-  // it to complex64)
-  cudaError_t e = kbe::sigma_row(m, h->v.data(), n, U_at(h, n), Ul, Hrow, h->Sig, h->work, h->stream, skip,
-                                 h->cfg.precision == KBE_PREC_C64 || h->cfg.precision == KBE_PREC_F16X2);
+  // it to complex64); the complex64 form transforms row n from its complex64 history copy
+  const bool f32 = h->cfg.precision == KBE_PREC_C64 || h->cfg.precision == KBE_PREC_F16X2;
+  const float2 *h32 = h->cfg.precision == KBE_PREC_C64
+                          ? (const float2 *)((const char *)h->H + kbe::history_row_offset(m, KBE_PREC_C64, n))
+                          : nullptr;
+  cudaError_t e = kbe::sigma_row(m, h->v.data(), n, U_at(h, n), Ul, Hrow, h->Sig, h->work, h->stream, skip, f32,
+                                 h32, f32);
   if (e != cudaSuccess) return cuda_fail(h, e, "sigma_row");
   const bool timed = h->prof;
   if (timed) {
@@ -236,7 +240,7 @@ kbe_status evaluate_row(kbe_handle *h, int n, const int *skip = nullptr) {
     cudaEventRecord(h->ev[h->ev_used].first, h->stream);
   }
   e = kbe::launch_sweep(m, n, h->cfg.dt, h->cfg.precision, h->H, h->Sig, h->Ic, h->coef, h->stream, skip,
-                        h->cfg.quadrature, h->status, h->inject, h->cfg.nt_max + 1);
+                        h->cfg.quadrature, h->status, h->inject, h->cfg.nt_max + 1, f32);
   h->inject = 0;
   if (e != cudaSuccess) return cuda_fail(h, e, "collision sweep");
   if (timed) {

@@ -333,9 +333,14 @@ cudaError_t launch_sigma_products(const Mesh &m, const double *v, int n, double 
 size_t sigma_workspace_bytes(const Mesh &m, int n);
 // fp32: the transforms and products in complex FP32 (the complex64 history
 // form, whose coefficient rows round Sigma to complex64 anyway); Sig is FP64
+// fp32: complex64 transforms and products. Hrow32 (fp32 only, may be NULL):
+// row n as complex64 (G^<, dG) pairs, read instead of Grow. sig32: Sig is
+// written as complex64 (the coefficient rows of the complex64 and split-FP16
+// sweeps read it so: launch_sweep's sig32)
 cudaError_t sigma_row(const Mesh &m, const double *v_host, int n, double Un, const double *Ul_dev,
                       const double2 *Grow, double2 *Sig, double2 *work, cudaStream_t st,
-                      const int *skip = nullptr, bool fp32 = false);
+                      const int *skip = nullptr, bool fp32 = false, const float2 *Hrow32 = nullptr,
+                      bool sig32 = false);
 
 // a2 collision row. H is the history triangle in the precision's storage
 // (double2 / float4 hi-lo pairs / float2), each block holding G^< and
@@ -424,7 +429,7 @@ namespace kbe {
 cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const void *H,
                          const double2 *Sig, double2 *I, void *work, cudaStream_t st,
                          const int *skip = nullptr, int quad = kQuadTrapezoid, int *status = nullptr,
-                         int inject = 0, int cap = 0);
+                         int inject = 0, int cap = 0, bool sig32 = false);
 
 // a3 propagators / initial state / density
 struct HopTable {

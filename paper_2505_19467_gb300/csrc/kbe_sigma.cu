@@ -200,9 +200,20 @@ __device__ __forceinline__ float2 load_as(const double2 &v, float2 *) {
 __device__ __forceinline__ double2 load_as(const double2 &v, double2 *) { return v; }
 __device__ __forceinline__ double2 load_as(const float2 &v, double2 *) { return make_double2(v.x, v.y); }
 
+// element e of array A of the input; pair_nb2 > 0: the input is a row of
+// (G^<, dG) pairs (arrays [l][x][a b], x = 1 holding dG = G^< - G^>), read as
+// (G^<, G^> = G^< - dG)
+template <class C, class Tin>
+__device__ __forceinline__ C load_in(const Tin *__restrict__ src, long e, long A, long nk, int pair_nb2) {
+  const C v = load_as(src[e], (C *)nullptr);
+  if (pair_nb2 > 0 && (A / pair_nb2) % 2 == 1) return c_sub(load_as(src[e - (long)pair_nb2 * nk], (C *)nullptr), v);
+  return v;
+}
+
 template <class C, class Tin, class Tout>
 __global__ void dft_rows_kernel(const Tin *__restrict__ in, Tout *__restrict__ out, long narr, int L0, int L1,
-                                int sign, double scale, int accumulate, const int *__restrict__ skip) {
+                                int sign, double scale, int accumulate, const int *__restrict__ skip,
+                                int pair_nb2) {
   if (skip && *skip) return;
   extern __shared__ double2 sm_d2[];
   C *sm = reinterpret_cast<C *>(sm_d2);
@@ -235,7 +246,7 @@ __global__ void dft_rows_kernel(const Tin *__restrict__ in, Tout *__restrict__ o
     if (reg) {
       for (int e = threadIdx.x; e < pa * nk; e += blockDim.x) {
         const int row = e / L1;   // (array, k0)
-        x[row * W + (e - row * L1)] = load_as(src[e], (C *)nullptr);
+        x[row * W + (e - row * L1)] = load_in<C>(src, e, arr0 + e / nk, nk, pair_nb2);
       }
       __syncthreads();
       if (L1 > 1)   // axis 1: rows (array, k0), contiguous
@@ -255,7 +266,7 @@ __global__ void dft_rows_kernel(const Tin *__restrict__ in, Tout *__restrict__ o
       }
       continue;
     }
-    for (int e = threadIdx.x; e < pa * nk; e += blockDim.x) x[e] = c_from<C>(load_as_d(src[e]));
+    for (int e = threadIdx.x; e < pa * nk; e += blockDim.x) x[e] = load_in<C>(src, e, arr0 + e / nk, nk, pair_nb2);
     __syncthreads();
     if (L1 > 1) {   // axis 1: L0 contiguous sequences of length L1 per array
       if (is_pow2(L1)) fft_axis<C>(x, L1, 1, pa * L0, L0, L1, nk, tw1);
@@ -463,7 +474,7 @@ cudaError_t dft_prepare_t(int L0, int L1) {
 
 template <class C, class Tin, class Tout>
 cudaError_t dft_launch(const Tin *in, Tout *out, long narr, int L0, int L1, int sign, double scale, cudaStream_t st,
-                       bool accumulate, const int *skip) {
+                       bool accumulate, const int *skip, int pair_nb2 = 0) {
   if (narr <= 0) return cudaSuccess;
   const int nk = L0 * L1;
   const bool reg = dft_in_registers(L0, L1);
@@ -475,7 +486,7 @@ cudaError_t dft_launch(const Tin *in, Tout *out, long narr, int L0, int L1, int 
   const long groups = (narr + P - 1) / P, cap = (long)device_sms() * 8;
   const long blocks = groups < cap ? groups : cap;
   dft_rows_kernel<C, Tin, Tout><<<(unsigned)blocks, threads, dft_smem_bytes(L0, L1, sizeof(C)), st>>>(
-      in, out, narr, L0, L1, sign, scale, accumulate ? 1 : 0, skip);
+      in, out, narr, L0, L1, sign, scale, accumulate ? 1 : 0, skip, pair_nb2);
   return cudaGetLastError();
 }
 
@@ -488,6 +499,7 @@ cudaError_t dft_prepare(int L0, int L1) {
   cudaError_t e = dft_prepare_t<double2, double2, double2>(L0, L1);
   if (e == cudaSuccess) e = dft_prepare_t<float2, double2, float2>(L0, L1);
   if (e == cudaSuccess) e = dft_prepare_t<float2, float2, double2>(L0, L1);
+  if (e == cudaSuccess) e = dft_prepare_t<float2, float2, float2>(L0, L1);
   return e;
 }
 
@@ -509,16 +521,20 @@ size_t sigma_workspace_bytes(const Mesh &m, int n) {
 
 cudaError_t sigma_row(const Mesh &m, const double *v_host, int n, double Un, const double *Ul_dev,
                       const double2 *Grow, double2 *Sig, double2 *work, cudaStream_t st, const int *skip,
-                      bool fp32) {
+                      bool fp32, const float2 *Hrow32, bool sig32) {
   const size_t blk = (size_t)m.nb * m.nb * m.nk;
   const long narr = (long)(n + 1) * 2 * m.nb * m.nb;
   if (fp32) {   // complex64 transforms and products (half the workspace)
     float2 *GR = (float2 *)work;
     float2 *SR = GR + (size_t)(n + 1) * 2 * blk;
-    cudaError_t e = dft_launch<float2, double2, float2>(Grow, GR, narr, m.L0, m.L1, +1, 1.0 / m.nk, st, false, skip);
+    cudaError_t e = Hrow32 ? dft_launch<float2, float2, float2>(Hrow32, GR, narr, m.L0, m.L1, +1, 1.0 / m.nk, st,
+                                                                false, skip, m.nb * m.nb)
+                           : dft_launch<float2, double2, float2>(Grow, GR, narr, m.L0, m.L1, +1, 1.0 / m.nk, st,
+                                                                 false, skip);
     if (e != cudaSuccess) return e;
     e = products_any<float2>(m, v_host, n, Un, Ul_dev, GR, SR, st, skip);
     if (e != cudaSuccess) return e;
+    if (sig32) return dft_launch<float2, float2, float2>(SR, (float2 *)Sig, narr, m.L0, m.L1, -1, 1.0, st, false, skip);
     return dft_launch<float2, float2, double2>(SR, Sig, narr, m.L0, m.L1, -1, 1.0, st, false, skip);
   }
   double2 *GR = work;

@@ -820,7 +820,7 @@ __global__ void row_out_kernel(int prec, const double2 *__restrict__ fp64, const
 // tensor-core sweep's FP16 coefficient pairs)
 __global__ void coef_kernel(int prec, const double2 *__restrict__ Sig, void *__restrict__ Cf, int n,
                             int nk, int nb2, double dt, const int *__restrict__ skip, int quad,
-                            double *__restrict__ Cs, unsigned *__restrict__ cmax) {
+                            double *__restrict__ Cs, unsigned *__restrict__ cmax, int sig32 = 0) {
   if (skip && *skip) return;
   const size_t blk = (size_t)nb2 * nk;
   const size_t total = (size_t)(n + 1) * blk;
@@ -833,8 +833,15 @@ __global__ void coef_kernel(int prec, const double2 *__restrict__ Sig, void *__r
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (size_t)gridDim.x * blockDim.x) {
       const size_t l = i / blk, r = i - l * blk;
-      const double2 dl = Sig[(l * 2) * blk + r], dg = Sig[(l * 2 + 1) * blk + r];
-      const float2 sl = make_float2((float)dl.x, (float)dl.y), sg = make_float2((float)dg.x, (float)dg.y);
+      float2 sl, sg;
+      if (sig32) {   // the row as complex64 (sigma_row's sig32)
+        sl = ((const float2 *)Sig)[(l * 2) * blk + r];
+        sg = ((const float2 *)Sig)[(l * 2 + 1) * blk + r];
+      } else {
+        const double2 dl = Sig[(l * 2) * blk + r], dg = Sig[(l * 2 + 1) * blk + r];
+        sl = make_float2((float)dl.x, (float)dl.y);
+        sg = make_float2((float)dg.x, (float)dg.y);
+      }
       const float w1 = (float)(dt * quad_omega(quad, n, (int)l));
       const float2 c1 = make_float2(w1 * (sg.x - sl.x), w1 * (sg.y - sl.y));
       const float2 c2 = make_float2(fdt * sl.x, fdt * sl.y);
@@ -1859,8 +1866,9 @@ cudaError_t launch_sweep_batch(const SweepJob *jobs, int njobs, cudaStream_t st,
 
 cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const void *H,
                          const double2 *Sig, double2 *I, void *work, cudaStream_t st, const int *skip,
-                         int quad, int *status, int inject, int cap) {
+                         int quad, int *status, int inject, int cap, bool sig32) {
   if (!precision_supported(precision)) return cudaErrorInvalidValue;
+  if (sig32 && precision != KBE_PREC_C64 && precision != KBE_PREC_F16X2) return cudaErrorInvalidValue;
   if (cap <= 0) cap = n + 1;
   if (cap < n + 1) return cudaErrorInvalidValue;
   const size_t blk = (size_t)m.nb * m.nb * m.nk;
@@ -1874,7 +1882,8 @@ cudaError_t launch_sweep(const Mesh &m, int n, double dt, int precision, const v
     e = cudaMemsetAsync(cmax, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
   }
-  coef_kernel<<<grid_for(total), 256, 0, st>>>(precision, Sig, work, n, m.nk, m.nb * m.nb, dt, skip, quad, Cs, cmax);
+  coef_kernel<<<grid_for(total), 256, 0, st>>>(precision, Sig, work, n, m.nk, m.nb * m.nb, dt, skip, quad, Cs, cmax,
+                                              sig32 ? 1 : 0);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   switch (m.nb) {

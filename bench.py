@@ -46,7 +46,7 @@ WORKLOAD = ("c2: N_b=4, 8x8 mesh (n_k=64), N_t=512, dt=0.02, U=1.0, beta=20, "
             "Peierls pulse A0=0.3, HF + second Born, P(EC)^2E")
 # Roofline denominators of the sweep (the dominant kernel). The ALU peaks are
 # measured live by kbe_measure_fma_peaks (FP64 and FP32 FMA throughput); the
-# HBM peak is the driver-measured copy bandwidth in MEASURED_PEAKS.json. The
+# HBM peak is the measured copy bandwidth in MEASURED_PEAKS.json. The
 # FP64 form is bound by the FP64 pipe; the double-float form by FP32 issue (6
 # FP32 instructions per double-float flop: a complex multiply-add is 4
 # products x 12 instructions = 8 flop); the complex64 form streams half the
@@ -196,7 +196,7 @@ def time_trajectories(g, nt, steps, warmup, stream, sampler=None, dist=None):
 
 
 def hbm_peak():
-    """(GB/s, source) of the driver-measured copy bandwidth, else the fallback"""
+    """(GB/s, source) of the measured copy bandwidth, else the fallback"""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs: STREAM-style copy)"

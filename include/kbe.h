@@ -337,11 +337,12 @@ kbe_status kbe_batch_set_graphs(kbe_batch *b, int enable);
  * otherwise, or while a system has profiling or an injected fault on). Each
  * kbe_batch_step runs the steps stage-major: every system advances on its own
  * stream up to its next collision sweep (Eq. 6, the memory integrals of the
- * predictor-corrector step of Sec. 3), then the sweeps of all systems of one
- * sweep class (N_b, quadrature, kernel form) run as ONE persistent launch on
- * that class's stream: the CTAs walk the concatenated block lists of the
- * systems, each at its own autotuned l-split (kbe_autotune); then those
- * systems continue. Classes do not wait for one another. With
+ * predictor-corrector step of Sec. 3), then the sweeps of the systems of one
+ * sweep class (N_b, quadrature, kernel form) run as ONE persistent launch per
+ * lane (the systems of a class alternate between two lanes, each on its own
+ * stream): the CTAs walk the concatenated block lists of the lane's systems,
+ * each at its own autotuned l-split (kbe_autotune); then those systems
+ * continue. A launch waits only for the systems of its own lane. With
  * graphs on (kbe_batch_set_graphs) and a non-default stream the call is one
  * captured graph as before. Results are bitwise those of the stream-ordered
  * batch. Synchronises the batch's stream; enable = 0 switches back. */

@@ -14,10 +14,11 @@
 // In the persistent mode (kbe_batch_set_persistent, FP64 histories) the steps
 // are enqueued stage-major: every system runs its step up to its next collision
 // sweep on its own stream, then ONE persistent launch per sweep class (N_b,
-// quadrature, kernel form), on that class's own stream, runs the sweeps of all
-// systems of the class, walking the concatenation of their block lists (each
-// system's blocks at its own autotuned split), and the systems continue from
-// there; different classes do not wait for one another. With graphs on and a
+// quadrature, kernel form) and lane (the systems of a class alternate between
+// two lanes), on that lane's own stream, runs the sweeps of the lane's
+// systems, walking the concatenation of their block lists (each system's
+// blocks at its own autotuned split), and the systems continue from there; a
+// launch waits only for its own lane's systems. With graphs on and a
 // non-default stream the whole call is again one captured graph.
 // Admission is by
 // device memory: systems are taken in order while their allocation fits the
@@ -117,6 +118,7 @@ std::vector<int> step_counts(const kbe_batch *b, int nsteps) {
 
 // the sweep class of a job: the jobs of one class share one persistent launch
 int sweep_class(const kbe::SweepJob &j) { return (j.nb * 2 + j.quad) * 2 + j.f64m; }
+constexpr int kClassLanes = 2;
 
 cudaError_t class_stream(kbe_batch *b, int cls, cudaStream_t *out) {
   bool seen = false;
@@ -191,33 +193,41 @@ kbe_status persistent_enqueue(kbe_batch *b, const std::vector<int> &k) {
         }
       }
       if (group.empty()) continue;
-      // one launch per sweep class (N_b, quadrature, form), each on its own
-      // stream: a class waits only for its own systems, the classes overlap
+      // one launch per sweep class (N_b, quadrature, form) and lane, each on
+      // its own stream: the systems of a class alternate between kClassLanes
+      // lanes, and a launch waits only for the systems of its own lane
       std::vector<char> taken(group.size(), 0);
       for (size_t q0 = 0; q0 < group.size(); ++q0) {
         if (taken[q0]) continue;
-        const int cls = sweep_class(group[q0]);
-        cudaStream_t cs = nullptr;
-        cudaError_t e = class_stream(b, cls, &cs);
-        std::vector<kbe::SweepJob> sub;
-        std::vector<size_t> subw;
+        const int base = sweep_class(group[q0]);
+        std::vector<kbe::SweepJob> lane_jobs[kClassLanes];
+        std::vector<size_t> lane_who[kClassLanes];
+        int rank = 0;
         for (size_t q = q0; q < group.size(); ++q)
-          if (!taken[q] && sweep_class(group[q]) == cls) {
+          if (!taken[q] && sweep_class(group[q]) == base) {
             taken[q] = 1;
-            sub.push_back(group[q]);
-            subw.push_back(who[q]);
+            lane_jobs[rank % kClassLanes].push_back(group[q]);
+            lane_who[rank % kClassLanes].push_back(who[q]);
+            ++rank;
           }
-        for (size_t q = 0; q < subw.size() && e == cudaSuccess; ++q) {
-          e = cudaEventRecord(b->done[subw[q]], b->streams[subw[q]]);
-          if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, b->done[subw[q]], 0);
+        for (int ln = 0; ln < kClassLanes; ++ln) {
+          if (lane_jobs[ln].empty()) continue;
+          const std::vector<kbe::SweepJob> &sub = lane_jobs[ln];
+          const std::vector<size_t> &subw = lane_who[ln];
+          cudaStream_t cs = nullptr;
+          cudaError_t e = class_stream(b, base * kClassLanes + ln, &cs);
+          for (size_t q = 0; q < subw.size() && e == cudaSuccess; ++q) {
+            e = cudaEventRecord(b->done[subw[q]], b->streams[subw[q]]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, b->done[subw[q]], 0);
+          }
+          int nl = 0;
+          if (e == cudaSuccess) e = kbe::launch_sweep_batch(sub.data(), (int)sub.size(), cs, &nl);
+          if (e == cudaSuccess) e = cudaEventRecord(b->class_done, cs);
+          for (size_t q = 0; q < subw.size() && e == cudaSuccess; ++q)
+            e = cudaStreamWaitEvent(b->streams[subw[q]], b->class_done, 0);
+          if (e != cudaSuccess) return batch_fail(KBE_ERR_CUDA, std::string("batch sweep: ") + cudaGetErrorString(e));
+          b->sweep_launches += nl;
         }
-        int nl = 0;
-        if (e == cudaSuccess) e = kbe::launch_sweep_batch(sub.data(), (int)sub.size(), cs, &nl);
-        if (e == cudaSuccess) e = cudaEventRecord(b->class_done, cs);
-        for (size_t q = 0; q < subw.size() && e == cudaSuccess; ++q)
-          e = cudaStreamWaitEvent(b->streams[subw[q]], b->class_done, 0);
-        if (e != cudaSuccess) return batch_fail(KBE_ERR_CUDA, std::string("batch sweep: ") + cudaGetErrorString(e));
-        b->sweep_launches += nl;
       }
     }
   }

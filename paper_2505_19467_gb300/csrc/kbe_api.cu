@@ -18,6 +18,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kbe_internal.cuh"
 
 using kbe::Mesh;
@@ -100,6 +102,16 @@ struct kbe_handle {
 };
 
 namespace {
+
+// an NVTX range over one phase of a step, for timeline tools (nsys, ncu
+// --nvtx); the calls cost next to nothing when no tool is attached. The range
+// covers the host's enqueueing of the phase's kernels.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 thread_local std::string g_create_err;
 
@@ -214,6 +226,7 @@ kbe_status publish(kbe_handle *h, int i, const int *skip = nullptr) {
 }
 
 kbe_status evaluate_row(kbe_handle *h, int n, const int *skip = nullptr) {
+  NvtxRange nv("kbe: Sigma row + collision sweep");
   const Mesh &m = h->mesh;
   double2 *Hrow = frow(h, n);
   const double *Ul = h->Useq.size() == 1 ? nullptr : h->d_U;
@@ -257,6 +270,7 @@ kbe_status evaluate_row(kbe_handle *h, int n, const int *skip = nullptr) {
 kbe_status build_props(kbe_handle *h, int n, const double2 *ra, const double2 *rb, double ca, double cb,
                        double2 *hk = nullptr, double2 *Uk = nullptr, double2 *Vk = nullptr,
                        const int *skip = nullptr) {
+  NvtxRange nv("kbe: propagators");
   kbe::PropParams p{};
   p.A = A_at(h, n - 1);
   p.rho_a = ra;
@@ -278,6 +292,7 @@ kbe_status build_props(kbe_handle *h, int n, const double2 *ra, const double2 *r
 
 kbe_status update(kbe_handle *h, int n, double theta, const int *skip = nullptr,
                   unsigned long long *maxdiff = nullptr) {
+  NvtxRange nv("kbe: row update");
   double2 *prev = frow(h, n - 1);
   double2 *row = frow(h, n);
   // the update kernels also store row n into the history triangle ("publish")
@@ -314,6 +329,7 @@ kbe_status observables(kbe_handle *h, int n, const double2 *Irow) {
 }
 
 kbe_status one_step(kbe_handle *h) {
+  NvtxRange nv("kbe: step");
   const int n = h->n + 1;
   const int nb2 = h->nb2;
   double2 *r1 = h->rho + (size_t)(n - 1) * nb2;
@@ -411,11 +427,24 @@ size_t adj_carve(const kbe_config *cfg, const Mesh &m, char *base, AdjPtrs *p) {
 }
 
 // backward phase timing (profiling only): open() records the start event of
-// a phase, close() its end
+// a phase, close() its end; each phase is also an NVTX range (always, closed
+// on every exit path)
+constexpr const char *kBackwardPhase[4] = {"kbe_backward: recompute", "kbe_backward: collision transposes",
+                                           "kbe_backward: sigma transposes", "kbe_backward: update and h transposes"};
 struct PhaseTimer {
   kbe_handle *h;
   size_t cur = (size_t)-1;
+  bool nvtx_open = false;
+  explicit PhaseTimer(kbe_handle *hh) : h(hh) {}
+  PhaseTimer(const PhaseTimer &) = delete;
+  PhaseTimer &operator=(const PhaseTimer &) = delete;
+  ~PhaseTimer() {
+    if (nvtx_open) nvtxRangePop();
+  }
   void open(int phase, double flops = 0.0) {
+    if (nvtx_open) nvtxRangePop();
+    nvtxRangePushA(kBackwardPhase[phase]);
+    nvtx_open = true;
     if (!h->prof) return;
     if (h->bev_used == h->bev.size()) {
       kbe_handle::PhaseEv pe{};
@@ -429,6 +458,8 @@ struct PhaseTimer {
     cudaEventRecord(h->bev[cur].a, h->stream);
   }
   void close() {
+    if (nvtx_open) nvtxRangePop();
+    nvtx_open = false;
     if (!h->prof || cur == (size_t)-1) return;
     cudaEventRecord(h->bev[cur].b, h->stream);
     cur = (size_t)-1;
@@ -479,7 +510,7 @@ kbe_status backward_step(kbe_handle *h, const AdjPtrs &P, int n, int nc, double2
   const int n2 = n >= 2 ? n - 2 : 0;
   const double ca0 = n >= 2 ? 1.5 : 1.0, cb0 = n >= 2 ? -0.5 : 0.0;
 
-  PhaseTimer tm{h};
+  PhaseTimer tm(h);
   // ---- recompute step n (the forward's order and kernels) ----
   tm.open(0);
   KBE_TRY(cudaMemcpyAsync(P.save, histN, rowc * sizeof(double2), cudaMemcpyDeviceToDevice, st), "backward save");

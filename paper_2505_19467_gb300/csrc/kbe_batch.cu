@@ -28,6 +28,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kbe_internal.cuh"
 
 struct kbe_batch {
@@ -420,6 +422,10 @@ kbe_status kbe_batch_reset(kbe_batch *b) {
 
 kbe_status kbe_batch_step(kbe_batch *b, int nsteps) {
   if (!b || nsteps < 0) return batch_fail(KBE_ERR_ARG, "batch_step: bad arguments");
+  struct Range {   // an NVTX range over the call (timeline tools)
+    Range() { nvtxRangePushA("kbe: batch step"); }
+    ~Range() { nvtxRangePop(); }
+  } range;
   cudaError_t e;
   if (b->graphs && batch_capturable(b)) {
     kbe_status s = batch_graph_step(b, nsteps);

@@ -382,10 +382,13 @@ __global__ void update_rows_kernel(int n, int nk, double theta, const double2 *_
 #pragma unroll
     for (int c = 0; c < NB; ++c) {
       const size_t oc = (size_t)(c * NB + b) * nk + k;
-      double2 ib0 = c_scale(1.0 - theta, Ip[base + oc]), ib1 = c_scale(1.0 - theta, Ip[base + blk + oc]);
+      // Ibar = (1 - theta) Ip + theta Ic with real scalars (the same values as
+      // complex products with a zero imaginary part, at half the FP64 work)
+      double2 ib0 = Ip[base + oc], ib1 = Ip[base + blk + oc];
       if (theta != 0.0) {
-        ib0 = c_fma(make_double2(theta, 0.0), Ic[base + oc], ib0);
-        ib1 = c_fma(make_double2(theta, 0.0), Ic[base + blk + oc], ib1);
+        const double2 c0 = Ic[base + oc], c1 = Ic[base + blk + oc];
+        ib0 = make_double2(fma(theta, c0.x, (1.0 - theta) * ib0.x), fma(theta, c0.y, (1.0 - theta) * ib0.y));
+        ib1 = make_double2(fma(theta, c1.x, (1.0 - theta) * ib1.x), fma(theta, c1.y, (1.0 - theta) * ib1.y));
       }
       const double2 g0 = Gprev[base + oc], g1 = Gprev[base + blk + oc];
 #pragma unroll

@@ -555,6 +555,22 @@ BATCH_WINDOW = 128   # timed steps per system (every drawn N_t is >= 256)
 BATCH_MARGIN = 8 << 30
 
 
+def batch_admission(nbs, need, budget):
+    """The order the batched form hands its systems to kbe_batch_create (the
+    smallest system of each N_b class first, then the others ascending by
+    bytes) and what that call admits under `budget` bytes (its rule: in order,
+    each system that still fits). Returns (order, admitted indices, bytes)."""
+    n = len(nbs)
+    first = [min((i for i in range(n) if nbs[i] == c), key=lambda i: (need[i], i)) for c in sorted(set(nbs))]
+    order = first + sorted((i for i in range(n) if i not in first), key=lambda i: (need[i], i))
+    admitted, used = [], 0
+    for i in order:
+        if used + need[i] <= budget:
+            admitted.append(i)
+            used += need[i]
+    return order, admitted, used
+
+
 def batched_form(kbe, stream, args):
     """The uneven 64-system draw (seed 3: N_b in {2, 4, 6, 8, 12, 16}, 4x4..12x12
     meshes, N_t in [256, 1024]; FP64). Admission: systems allocated at their
@@ -570,18 +586,11 @@ def batched_form(kbe, stream, args):
     import torch
     systems = ki.batched(64)
     need = [kbe.memory_bytes(kbe.system_config(x)) for x in systems]
-    classes = sorted(set(x.nb for x in systems))
-    first = [min((i for i in range(len(systems)) if systems[i].nb == c), key=lambda i: need[i]) for c in classes]
-    order = first + sorted((i for i in range(len(systems)) if i not in first), key=lambda i: need[i])
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     free, tot = torch.cuda.mem_get_info()
     budget = max(0, free - BATCH_MARGIN)
-    expect, used = [], 0
-    for i in order:            # kbe_batch_create's rule: in order, while the allocation fits
-        if used + need[i] <= budget:
-            expect.append(i)
-            used += need[i]
+    order, expect, used = batch_admission([x.nb for x in systems], need, budget)
     tiles = {}
     for i in expect:           # one tuning per distinct shape (the table is per shape and row bucket)
         x = systems[i]

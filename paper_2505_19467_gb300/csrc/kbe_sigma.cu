@@ -108,8 +108,6 @@ __device__ __forceinline__ void store_as(float2 *p, float2 v) { *p = v; }
 __device__ __forceinline__ void add_as(double2 *p, double2 v) { *p = c_add(*p, v); }
 __device__ __forceinline__ void add_as(double2 *p, float2 v) { *p = c_add(*p, make_double2(v.x, v.y)); }
 __device__ __forceinline__ void add_as(float2 *p, float2 v) { *p = c_add(*p, v); }
-__device__ __forceinline__ double2 load_as_d(double2 v) { return v; }
-__device__ __forceinline__ double2 load_as_d(float2 v) { return make_double2(v.x, v.y); }
 
 // P arrays per CTA iteration (a power of two when n_k is one)
 __host__ __device__ __forceinline__ int dft_group(int nk) {
@@ -198,7 +196,6 @@ __device__ __forceinline__ float2 load_as(const double2 &v, float2 *) {
   return make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
 }
 __device__ __forceinline__ double2 load_as(const double2 &v, double2 *) { return v; }
-__device__ __forceinline__ double2 load_as(const float2 &v, double2 *) { return make_double2(v.x, v.y); }
 
 // element e of array A of the input; pair_nb2 > 0: the input is a row of
 // (G^<, dG) pairs (arrays [l][x][a b], x = 1 holding dG = G^< - G^>), read as

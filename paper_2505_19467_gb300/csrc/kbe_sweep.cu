@@ -89,7 +89,6 @@ struct ArithF64 {
   static __device__ __forceinline__ S scale(float f, const S &x) { return c_scale((double)f, x); }
   static __device__ __forceinline__ S scale_w(double f, const S &x) { return c_scale(f, x); }
   static __device__ __forceinline__ S add(const S &x, const S &y) { return c_add(x, y); }
-  static __device__ __forceinline__ double2 result(const A &a) { return a; }
   static __device__ __forceinline__ void store(double2 *o, size_t blkc, const A &x, const A &y) {
     o[0] = x;
     o[blkc] = c_add(x, y);

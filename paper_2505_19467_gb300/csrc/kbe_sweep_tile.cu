@@ -447,7 +447,6 @@ cudaError_t tile_prepare_nb() {
 }
 
 int tile_tm_of(int nb) { return nb == 2 ? tile_tm<2>() : nb == 4 ? tile_tm<4>() : tile_tm<8>(); }
-int tile_kt_of(int nb) { return nb == 2 ? TileCfg<2>::KT : nb == 4 ? TileCfg<4>::KT : TileCfg<8>::KT; }
 
 long tile_items(int n, int TM, int TI) {
   long p = 0;

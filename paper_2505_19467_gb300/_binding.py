@@ -504,8 +504,8 @@ class KBEBatch:
         _check(load().kbe_batch_set_graphs(self._b, int(enable)))
 
     def set_persistent(self, enable: bool = True):
-        """stage-major steps with the sweeps of all systems in one persistent
-        launch per (N_b, quadrature, form); FP64 histories (kbe_batch_set_persistent)"""
+        """stage-major steps with the sweeps of the systems in one persistent
+        launch per (N_b, quadrature, form) and lane; FP64 histories (kbe_batch_set_persistent)"""
         _check(load().kbe_batch_set_persistent(self._b, int(enable)))
 
     def sweep_launches(self) -> int:
